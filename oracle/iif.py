@@ -1,0 +1,183 @@
+"""IIF2 time step with a Newton implicit stage (oracle; test infrastructure only).
+
+Eq. krylov5 (IIF2):
+    U^{n+1} = exp(dt A) (U^n + dt/2 F(U^n)) + dt/2 F(U^{n+1}).
+For a system the diffusion is block diagonal across species, so exp(dt A)
+acts per species with that species' operator, one Krylov projection each.
+
+The implicit stage G(U) = U - dt/2 F(U) - W = 0 (W the exponential term) is
+solved by Newton's method, as Example 3 and Section 5 state.  Readings where
+the paper is silent:
+  * initial guess U = W;
+  * Newton matrix I - dt/2 J_F(U), J_F(U) w = P(f'(u_h) w_h);
+  * inner solver: conjugate gradients for a scalar equation (the matrix is
+    symmetric), restarted GMRES(50) with Givens rotations for systems; both
+    start from 0 and stop at relative residual INNER_TOL or INNER_MAX steps;
+  * outer stop ||G(U)||_2 <= NEWTON_TOL max(1, ||W||_2), at most NEWTON_MAX
+    iterations, otherwise NewtonError.
+"""
+import numpy as np
+
+from .krylov import BREAKDOWN_TOL, krylov_expv
+from .operator import sparse_matvec
+from .reaction import Reaction
+
+NEWTON_TOL = 1e-12
+NEWTON_MAX = 50
+INNER_TOL = 1e-13
+INNER_MAX = 500
+GMRES_RESTART = 50
+
+
+class NewtonError(RuntimeError):
+    pass
+
+
+def cg(apply, b, tol=INNER_TOL, maxit=INNER_MAX):
+    """Conjugate gradients from x = 0; returns (x, iterations)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    stop = (tol ** 2) * rr
+    it = 0
+    while it < maxit and rr > stop:
+        q = apply(p)
+        alpha = rr / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def gmres(apply, b, tol=INNER_TOL, maxit=INNER_MAX, restart=GMRES_RESTART):
+    """Restarted GMRES from x = 0 with CGS2 Arnoldi and Givens rotations."""
+    n = b.size
+    x = np.zeros_like(b)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return x, 0
+    it = 0
+    while it < maxit:
+        r = b - apply(x) if it else b.copy()
+        beta = float(np.linalg.norm(r))
+        if beta <= tol * bnorm:
+            break
+        m = min(restart, maxit - it)
+        V = np.zeros((n, m + 1))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[:, 0] = r / beta
+        used = 0
+        for j in range(m):
+            w = apply(V[:, j])
+            h1 = V[:, : j + 1].T @ w
+            w = w - V[:, : j + 1] @ h1
+            h2 = V[:, : j + 1].T @ w
+            w = w - V[:, : j + 1] @ h2
+            H[: j + 1, j] = h1 + h2
+            hn = float(np.linalg.norm(w))
+            H[j + 1, j] = hn
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            used = j + 1
+            it += 1
+            if abs(g[j + 1]) <= tol * bnorm or hn <= BREAKDOWN_TOL * den:
+                break
+            V[:, j + 1] = w / hn
+        y = np.zeros(used)
+        for i in range(used - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:used] @ y[i + 1:]) / H[i, i]
+        x = x + V[:, :used] @ y
+        if abs(g[used]) <= tol * bnorm:
+            break
+    return x, it
+
+
+class IIF2Solver:
+    """Sparse-grid Krylov IIF2 DG solver (Sections 2-3)."""
+
+    def __init__(self, idx, S, kappas, reaction, dt, M):
+        """S: 1D SIPG matrix; kappas: per species, a length-d diagonal."""
+        self.idx, self.S, self.dt, self.M = idx, S, dt, M
+        self.kappas = [np.asarray(k, dtype=np.float64) for k in kappas]
+        self.nspecies = len(self.kappas)
+        self.reaction = reaction
+        self.has_reaction = any(len(t) for t in reaction)
+        self.rx = Reaction(idx, reaction) if self.has_reaction else None
+        self.stats = {"newton": [], "inner": [], "m_eff": []}
+
+    def A(self, s):
+        return lambda x: sparse_matvec(self.idx, self.S, self.kappas[s], x)
+
+    def F(self, U):
+        if not self.has_reaction:
+            return [np.zeros_like(u) for u in U]
+        return self.rx.F(U)
+
+    def newton(self, W):
+        dt2 = 0.5 * self.dt
+        U = [w.copy() for w in W]
+        wnorm = float(np.sqrt(sum(float(w @ w) for w in W)))
+        stop = NEWTON_TOL * max(1.0, wnorm)
+        n = self.idx.dof
+        inner_total = 0
+        for it in range(NEWTON_MAX + 1):
+            Fu = self.F(U)
+            G = np.concatenate([U[s] - dt2 * Fu[s] - W[s] for s in range(self.nspecies)])
+            if float(np.linalg.norm(G)) <= stop:
+                return U, it, inner_total
+            if it == NEWTON_MAX:
+                break
+
+            def apply(x):
+                xs = [x[s * n:(s + 1) * n] for s in range(self.nspecies)]
+                Jx = self.rx.J(U, xs)
+                return np.concatenate([xs[s] - dt2 * Jx[s] for s in range(self.nspecies)])
+
+            if self.nspecies == 1:
+                delta, inner = cg(apply, -G)
+            else:
+                delta, inner = gmres(apply, -G)
+            inner_total += inner
+            for s in range(self.nspecies):
+                U[s] = U[s] + delta[s * n:(s + 1) * n]
+        raise NewtonError("Newton did not converge in %d iterations" % NEWTON_MAX)
+
+    def step(self, U):
+        """One IIF2 step (eq. krylov5); U is a list of per-species vectors."""
+        dt2 = 0.5 * self.dt
+        Fn = self.F(U)
+        W = []
+        for s in range(self.nspecies):
+            v = U[s] + dt2 * Fn[s]
+            w, m_eff = krylov_expv(self.A(s), v, self.dt, self.M)
+            self.stats["m_eff"].append(m_eff)
+            W.append(w)
+        if not self.has_reaction:
+            self.stats["newton"].append(0)
+            self.stats["inner"].append(0)
+            return W
+        Unew, it, inner = self.newton(W)
+        self.stats["newton"].append(it)
+        self.stats["inner"].append(inner)
+        return Unew
+
+    def run(self, U, nsteps):
+        U = [np.asarray(u, dtype=np.float64).copy() for u in U]
+        for _ in range(nsteps):
+            U = self.step(U)
+        return U

@@ -1,0 +1,124 @@
+"""Sparse-grid SIPG diffusion operator (oracle; test infrastructure only).
+
+Section 2.1, bilinear form B and eq. sp3, restricted to a constant diagonal
+diffusion tensor k = diag(kappa_1 .. kappa_d):
+
+  B(u, v) = sum_i kappa_i [ int d_i u d_i v
+                            - sum_{faces _|_ e_i} ({d_i u}[v] + {d_i v}[u])
+                            + (sigma / h) sum_{faces _|_ e_i} [u][v] ]
+
+with sigma = 20 and h = h_N = 2^-N on every face of the finest mesh (the
+penalty reading follows the energy norm of Section 2.2, which weights the
+faces by h_N).  Every sparse-grid function is a tensor product, the 1D basis
+is orthonormal (mass matrix I, eq. sp9) and the face integrals split into a
+1D trace term times 1D L2 products, so B is a Kronecker sum of one 1D matrix
+S per direction (the unidirectional principle of Section 4).  The
+semi-discrete system is dU/dt = A U + F(U) with A = -B (eq. krylov1).
+
+Jump and average in 1D (eq. sp3): at an interior face, [q] = q(x^-) - q(x^+)
+and {q} = (q(x^-) + q(x^+))/2.  Periodic: the face at x = 0 ~ 1 has x^- the
+trace from the last cell.  Zero Dirichlet: at x = 0, [q] = -q(0^+) and
+{q'} = q'(0^+); at x = 1, [q] = q(1^-) and {q'} = q'(1^-).
+"""
+import numpy as np
+
+from .basis import alpert_coefficients, gauss_legendre, hier_eval, hier_level_count, hier_size
+
+PERIODIC = 0
+DIRICHLET0 = 1
+
+
+def sipg_1d(N, k, bc=PERIODIC, sigma=20.0):
+    """1D SIPG matrix S[a, b] = b(v_b, v_a) in the hierarchical basis of V_N^k."""
+    alpert = alpert_coefficients(k)
+    H = hier_size(N, k)
+    ncell = 1 << N
+    h = 2.0 ** (-N)
+    # volume term: sum over finest cells of int v_a' v_b', (k+1)-point Gauss
+    xi, w = gauss_legendre(k + 1)
+    cells = np.repeat(np.arange(ncell), k + 1)
+    _, D = hier_eval(N, k, cells, np.tile(xi, ncell), alpert)
+    wq = np.tile(h * w / 2.0, ncell)
+    S = D.T @ (D * wq[:, None])
+    # face terms: jumps J_f(a) and derivative averages G_f(a) per face
+    if bc == PERIODIC:
+        faces = list(range(ncell))          # face f at x = f h; face 0 wraps
+    else:
+        faces = list(range(ncell + 1))
+    J = np.zeros((len(faces), H))
+    G = np.zeros((len(faces), H))
+    for i, f in enumerate(faces):
+        left_cell = (f - 1) % ncell if bc == PERIODIC else f - 1
+        right_cell = f % ncell if bc == PERIODIC else f
+        has_left = bc == PERIODIC or f > 0
+        has_right = bc == PERIODIC or f < ncell
+        vl = dl = vr = dr = np.zeros(H)
+        if has_left:
+            v, dv = hier_eval(N, k, [left_cell], [1.0], alpert)
+            vl, dl = v[0], dv[0]
+        if has_right:
+            v, dv = hier_eval(N, k, [right_cell], [-1.0], alpert)
+            vr, dr = v[0], dv[0]
+        if has_left and has_right:
+            J[i] = vl - vr
+            G[i] = 0.5 * (dl + dr)
+        elif has_right:                      # boundary x = 0, outward normal -1
+            J[i] = -vr
+            G[i] = dr
+        else:                                # boundary x = 1, outward normal +1
+            J[i] = vl
+            G[i] = dl
+    S = S - (G.T @ J + J.T @ G) + (sigma / h) * (J.T @ J)
+    return S
+
+
+def sparse_matvec(idx, S, kappa, x):
+    """y = A x with A = -sum_i kappa_i (S along direction i), restricted to the
+    sparse index set (Section 4, unidirectional principle).
+
+    For direction i and each tuple of the other levels l_{-i}, the blocks with
+    l_i = 0 .. N - |l_{-i}| stacked along axis i form fibers in the 1D
+    hierarchical index a_i < (k+1) 2^{N'}; S restricted to that leading
+    principal submatrix is applied along axis i.
+    """
+    d, N, k = idx.d, idx.N, idx.k
+    y = np.zeros_like(x)
+    for i in range(d):
+        groups = {}
+        for l in idx.tuples:
+            rest = l[:i] + l[i + 1:]
+            groups.setdefault(rest, []).append(l)
+        for rest, blocks in groups.items():
+            blocks = sorted(blocks, key=lambda l: l[i])
+            assert [l[i] for l in blocks] == list(range(len(blocks)))
+            stacked = np.concatenate([idx.block(x, l) for l in blocks], axis=i)
+            nf = stacked.shape[i]
+            res = np.moveaxis(np.tensordot(S[:nf, :nf], stacked, axes=([1], [i])), 0, i)
+            start = 0
+            for l in blocks:
+                c = hier_level_count(l[i], k)
+                sl = [slice(None)] * d
+                sl[i] = slice(start, start + c)
+                yb = idx.block(y, l)
+                yb -= kappa[i] * res[tuple(sl)]
+                start += c
+    return y
+
+
+def dense_full_operator(d, S, kappa):
+    """-sum_i kappa_i I x .. x S x .. x I on the full tensor space (tiny grids)."""
+    H = S.shape[0]
+    A = np.zeros((H ** d, H ** d))
+    for i in range(d):
+        term = np.ones((1, 1))
+        for m in range(d):
+            term = np.kron(term, S if m == i else np.eye(H))
+        A -= kappa[i] * term
+    return A
+
+
+def dense_sparse_operator(idx, S, kappa):
+    """The full tensor operator restricted to the sparse index set (tiny grids)."""
+    A = dense_full_operator(idx.d, S, kappa)
+    f = idx.flat_full_indices()
+    return A[np.ix_(f, f)]
