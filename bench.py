@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: sparse-grid DOF*steps/s of the Krylov IIF2 DG solver on one GB300.
+
+A bench step is one IIF2 time step of the 3D cubic reaction-diffusion workload
+(d = 3, level n = 6, degree k = 2, 18 576 DOF, f(u) = -100 u^3, diffusion
+diag(1, 0.5, 0.1), M = 30, dt = 0.005): reaction term, predictor, Arnoldi with
+CGS2 (30 matvecs), exp(dt H), basis combination and the Newton solve with CG.
+The timed steps start from the projected seeded initial state (20 steps = the
+whole configured solve).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                        [--impl native|reference] [--no-cpu-baseline]
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sparse-grid DOF*steps/s (IIF2, FP64-oracle-checked)"
+UNIT = "DOF*steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config():
+    from paper_1810_11111_gb300 import workloads
+    return workloads.cubic3d()
+
+
+def workload_desc(cfg):
+    return {"workload": "cubic3d: u_t = div(diag(1,0.5,0.1) grad u) - 100 u^3 on [0,1]^3, periodic, "
+                        "sparse grid level 6, degree 2, 8 seeded Fourier modes, IIF2 M=30 dt=0.005",
+            "d": cfg["d"], "level": cfg["n"], "degree": cfg["k"], "krylov_m": cfg["M"], "dt": cfg["dt"],
+            "species": len(cfg["kappas"])}
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- roofline ---
+
+def layout_sizes(d, n, k):
+    """Sizes of the partially transformed arrays R_0..R_d (see reaction.cu)."""
+    from itertools import product
+    H = (k + 1) << n
+
+    def count(l):
+        return (k + 1) * (1 if l == 0 else 1 << (l - 1))
+
+    def sparse_dof(dim):
+        if dim == 0:
+            return 1
+        return sum(int(np.prod([count(v) for v in t])) for t in product(range(n + 1), repeat=dim) if sum(t) <= n)
+
+    return [H ** i * sparse_dof(d - i) for i in range(d + 1)]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------ native arm ---
+
+def native(args, rank, world, local_rank):
+    import torch
+
+    from paper_1810_11111_gb300 import sgkiif
+    from paper_1810_11111_gb300.runner import Problem
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = workload_config()
+    prec = sgkiif.SGK_MIXED if args.precision == "mixed" else sgkiif.SGK_FP64
+    prob = Problem(cfg, prec, device=local_rank)
+    dof, S = prob.dof, prob.nspecies
+    elem = 4 if prec == sgkiif.SGK_MIXED else 8
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up with every kernel class timed, to find the dominant one
+    prob.ctx.profile(0x7F)
+    prob.reset()
+    for _ in range(args.warmup):
+        prob.solver.step(1)
+    warm = prob.ctx.profile_read()
+    dominant = max(warm, key=lambda c: warm[c][0])
+    dom_bit = sgkiif.Context.KERNEL_CLASSES.index(dominant)
+
+    # timed region: device time of each step, L2 flushed before each
+    prob.ctx.profile(1 << dom_bit)
+    prob.reset()
+    st0 = prob.solver.stats()
+    barrier()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(visible.split(",")[local_rank] if visible else local_rank)
+    clocks.start()
+    launches0 = prob.ctx.launches
+    total_ms = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0.record(stream)
+        prob.solver.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    launches = prob.ctx.launches - launches0
+    kprof = prob.ctx.profile_read()
+    prob.ctx.profile(0)
+    st1 = prob.solver.stats()
+    final = prob.state()
+
+    # accuracy against the FP64 GPU path (itself parity-tested against the oracle)
+    acc = None
+    if prec == sgkiif.SGK_MIXED:
+        ref = Problem(cfg, sgkiif.SGK_FP64, device=local_rank)
+        ref.reset()
+        ref.solver.step(args.steps)
+        rs = ref.state()
+        acc = float(np.sqrt(sum(np.sum((final[s] - rs[s]) ** 2) for s in range(S)) /
+                            sum(np.sum(rs[s] ** 2) for s in range(S))))
+        ref.close()
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory and the result back out
+    e2e = None
+    if not args.no_e2e:
+        host_in = [torch.from_numpy(u.cpu().numpy()).pin_memory() for u in prob.U0]
+        host_out = [torch.empty(dof, dtype=torch.float64).pin_memory() for _ in range(S)]
+        barrier()
+        t_ms = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0.record(stream)
+            for s in range(S):
+                sgkiif.sgk_solver_set_state(prob.solver.h, s, host_in[s].data_ptr(), 0)
+            prob.solver.step(1)
+            for s in range(S):
+                sgkiif.sgk_solver_get_state(prob.solver.h, s, host_out[s].data_ptr(), dof, 0)
+            e1.record(stream)
+            e1.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            host_in, host_out = host_out, host_in
+        t_max = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        e2e = {"value": dof * S * args.steps * world / (float(t_max) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": dof * S * 8, "d2h_bytes_per_step": dof * S * 8}
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t)
+    value = dof * S * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel class: algorithmic bytes per launch over
+    # its event-timed average launch time in the timed region
+    peaks, peak_kind = measured_peaks()
+    nF = args.steps * 1 + (st1["newton_iters"] - st0["newton_iters"]) + args.steps  # predictor + residuals
+    nJ = st1["inner_iters"] - st0["inner_iters"]
+    sizes = layout_sizes(cfg["d"], cfg["n"], cfg["k"])
+    full = sizes[-1]
+    ms, nl = kprof[dominant]
+    if dominant == "cell_quadrature":
+        algo = (nF * 2 * S * full + nJ * 3 * S * full) * elem
+    elif dominant in ("to_finest", "from_finest"):
+        algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(cfg["d"])) * elem
+    elif dominant == "matvec":
+        algo = (nl / cfg["d"]) * 2 * dof * elem
+    else:
+        algo = None
+    roofline = None
+    if algo is not None and nl > 0 and ms > 0:
+        per_launch = algo / nl
+        achieved = per_launch / (ms / nl / 1e3) / 1e9
+        roofline = {"kernel_class": dominant, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": peak_kind, "algorithmic_bytes_per_launch": per_launch,
+                    "avg_launch_us": ms / nl * 1e3, "launches": nl,
+                    "share_of_step_time": ms / total_ms if world == 1 else None}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 passes + f64 reductions" if prec == sgkiif.SGK_MIXED else "f64",
+           "data": "synthetic (seeded Fourier-mode initial data)",
+           "config": dict(workload_desc(cfg), l2="flushed (256 MB write) before every timed step",
+                          precision=args.precision, parallelism="replicas" if world > 1 else "single GPU"),
+           "rel_l2_vs_fp64": acc,
+           "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+           "host_wall_s": wall,
+           "solver": {"newton_iters": st1["newton_iters"] - st0["newton_iters"],
+                      "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
+           "kernel_ms_warmup": {c: round(v[0], 3) for c, v in warm.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+# --------------------------------------------------------- oracle timing ---
+
+def oracle_steps(cfg, max_steps, budget_s):
+    """Time full oracle IIF2 steps of the workload until max_steps or budget_s."""
+    from oracle.iif import IIF2Solver
+    from oracle.index_set import IndexSet
+    from oracle.operator import sipg_1d
+    from oracle.projection import project_separable
+    idx = IndexSet(cfg["d"], cfg["n"], cfg["k"])
+    init = cfg["init"][0]
+    U = [project_separable(idx, init["amp"], init["wavenum"], init["kind"], init["const"])]
+    sol = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"])
+    t0 = time.perf_counter()
+    done = 0
+    while done < max_steps and (done == 0 or time.perf_counter() - t0 < budget_s):
+        U = sol.run(U, 1)
+        done += 1
+    return done, time.perf_counter() - t0, idx.dof
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(cfg):
+    done, secs, dof = oracle_steps(cfg, 1, 0.0)
+    return {"value": dof * done / secs, "unit": UNIT, "cores": cores(), "kind": "oracle",
+            "sample": "first IIF2 step of the same workload (numpy FP64 oracle, %.1f s)" % secs}
+
+
+def reference(args, rank):
+    if rank != 0:
+        return None
+    cfg = workload_config()
+    done, secs, dof = oracle_steps(cfg, args.steps, 150.0)
+    value = dof * done / secs
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": 0, "ms_per_step": secs / done * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": dict(workload_desc(cfg), precision="fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle",
+                             "sample": "%d full IIF2 steps of the workload from the initial state "
+                                       "(capped at 150 s of CPU time; warm-up not needed)" % done},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = reference(args, rank)
+    else:
+        out = native(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

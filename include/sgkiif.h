@@ -1,0 +1,233 @@
+/*
+ * sgkiif.h -- C ABI of libsgkiif, a CUDA (sm_103a) implementation of the
+ * sparse-grid Krylov implicit-integration-factor DG method for
+ * reaction-diffusion equations u_t = div(k grad u) + f(u) on [0,1]^d
+ * (Liu, Cheng, Chen, Zhang, arXiv:1810.11111).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status: every call that can fail returns an int status (SGK_OK = 0).  No
+ *   C++ exception crosses this boundary.  The text of the last error of a
+ *   context is returned by sgk_last_error().
+ * Memory: the library owns every device buffer behind an opaque handle.  The
+ *   caller owns every host buffer and every device buffer it passes in
+ *   ("_dev" pointers are device pointers on the context's device, allocated
+ *   by the caller, e.g. through PyTorch).  Handles are destroyed by the
+ *   caller, children (solver, operator, index) before the context.
+ * Streams: all device work of a context is issued on the stream given to
+ *   sgk_ctx_create (0 = legacy default stream).  Calls returning host data
+ *   synchronise that stream; the others are asynchronous unless noted.
+ * Threads: a context and its children must be used by one host thread at a
+ *   time.
+ * Coefficient layout (sparse-grid vectors): the sparse-grid space is the sum
+ *   of W_l over level tuples |l|_1 <= n (Section 2.1, eq. sp13).  Tuples are
+ *   in lexicographic order with l_1 varying slowest; each tuple owns one
+ *   contiguous block, row-major over the local 1D indices
+ *   t_m = j_m (k+1) + p_m (dimension d fastest), where j_m is the support
+ *   cell and p_m the degree of the 1D function on level l_m (eq. sp9, sp14).
+ *   1D functions: level 0 = sqrt(2p+1) P_p(2x-1); level n >= 1 =
+ *   2^{n/2} f_p(2^n x - (2j+1)) with Alpert's multiwavelets f_p fixed by
+ *   vanishing moments (f_p orthogonal to x^i, i <= p+k) and the sign rule
+ *   "first right-half Legendre coefficient of magnitude > 1e-8, scanned from
+ *   degree k down, is positive".
+ * Species-stacked vectors hold species s at offset s * dof.
+ */
+#ifndef SGKIIF_H
+#define SGKIIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SGK_OK 0
+#define SGK_EINVAL 1        /* bad argument (null, out of range, mismatch) */
+#define SGK_ENOMEM 2        /* device or host allocation failed */
+#define SGK_EUNSUPPORTED 3  /* valid request outside what is implemented */
+#define SGK_ENEWTON 4       /* Newton did not converge; state rolled back */
+#define SGK_ETIMEOUT 5      /* a bounded device wait ran out */
+#define SGK_ECUDA 6         /* a CUDA runtime call failed */
+
+/* precision modes */
+#define SGK_FP64 0   /* all arithmetic in FP64 */
+#define SGK_MIXED 1  /* matvec, axpys, reaction/Jacobian passes in FP32;
+                        Gram-Schmidt inner products, norms, exp(tau H),
+                        Newton residual in FP64 */
+
+/* boundary conditions (Section 2.1, eq. sp3) */
+#define SGK_PERIODIC 0
+#define SGK_DIRICHLET0 1   /* homogeneous Dirichlet */
+
+/* time schemes (Section 3) */
+#define SGK_IIF2 2         /* eq. krylov5 */
+
+#define SGK_MAX_DIM 6
+#define SGK_MAX_LEVEL 12
+#define SGK_MAX_SPECIES 4
+#define SGK_MAX_KRYLOV 128
+
+typedef struct sgk_ctx sgk_ctx;
+typedef struct sgk_index sgk_index;
+typedef struct sgk_op sgk_op;
+typedef struct sgk_solver sgk_solver;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the default stream).  precision is SGK_FP64 or
+ * SGK_MIXED and selects the arithmetic of solvers created on this context.
+ * Errors: SGK_EINVAL (null out, bad precision), SGK_ECUDA (no such device). */
+int sgk_ctx_create(sgk_ctx** out, int device, void* cuda_stream, int precision);
+int sgk_ctx_destroy(sgk_ctx* ctx);
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+const char* sgk_last_error(const sgk_ctx* ctx);
+/* Number of kernel launches this context has issued since creation. */
+int64_t sgk_ctx_launch_count(const sgk_ctx* ctx);
+/* Kernel timing for benchmarks (no counterpart in the paper).  While bit i of
+ * mask is set, every launch of kernel class i is bracketed by two CUDA events
+ * on the context's stream.  Classes: 0 SIPG matvec, 1 change of basis to the
+ * finest grid, 2 its transpose, 3 cell quadrature of the reaction term,
+ * 4 inner products and Gram-Schmidt passes, 5 exp(tau H) e_1, 6 other vector
+ * kernels.  mask = 0 disables timing. */
+int sgk_ctx_profile(sgk_ctx* ctx, unsigned mask);
+/* Sum of event-timed milliseconds and launch counts per class (arrays of 7)
+ * since the previous read; synchronises the stream and resets the sums. */
+int sgk_ctx_profile_read(sgk_ctx* ctx, double* ms, int64_t* launches);
+
+/* -------------------------------------------------------------- index set */
+
+/* Build the sparse-grid index set {(l, j, p) : |l|_1 <= n} of degree-k
+ * multiwavelets in d dimensions (Section 2.1, eqs. sp10-sp14) on the device:
+ * enumerates the level tuples in the layout order above, their block sizes
+ * (k+1)^d prod_m max(1, 2^{l_m-1}) and block offsets, and the level hash
+ * (tuple -> block id).  d in [1, 6], n in [0, 12], k in [1, 3], else
+ * SGK_EINVAL. */
+int sgk_index_build(sgk_ctx* ctx, int d, int n, int k, sgk_index** out);
+int sgk_index_destroy(sgk_index* idx);
+/* Number of coefficients per species, (k+1)^d sum_l prod_m max(1,2^{l_m-1}). */
+int64_t sgk_index_dof(const sgk_index* idx);
+/* Number of level tuples, C(n+d, d). */
+int64_t sgk_index_ntuples(const sgk_index* idx);
+/* Copy the tuple table to host: levels[ntuples*d] (row per tuple) and
+ * offsets[ntuples+1] (block starts, offsets[ntuples] = dof).  cap is the
+ * number of tuples the buffers hold; SGK_EINVAL if cap < ntuples.
+ * Synchronises. */
+int sgk_index_export(const sgk_index* idx, int32_t* levels, int64_t* offsets, int64_t cap);
+/* Level hash: block id of each of `count` level tuples levels[count*d]
+ * (host arrays), -1 for tuples outside the set.  Runs on the device.
+ * Synchronises. */
+int sgk_index_lookup(const sgk_index* idx, const int32_t* levels, int64_t count, int64_t* block_ids);
+
+/* --------------------------------------------------------------- operator */
+
+/* Assemble the SIPG diffusion operator A = -B for k(x) = diag(kappa) with
+ * penalty sigma / h_n on every finest-mesh face (Section 2.1, bilinear form
+ * B; the paper takes sigma = 20).  The 1D matrix S (one per bc) is built
+ * once on the host in the hierarchical basis; A = -sum_i kappa_i S along
+ * direction i restricted to the index set (unidirectional principle,
+ * Section 4).  kappa: host array of d positive values.  bc: SGK_PERIODIC or
+ * SGK_DIRICHLET0.  Errors: SGK_EINVAL. */
+int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, int bc, double sigma,
+                          sgk_op** out);
+int sgk_operator_destroy(sgk_op* op);
+/* Copy the 1D hierarchical matrix S (size H x H, H = (k+1) 2^n, row-major,
+ * zeros included) to host `out` (cap >= H*H doubles).  Synchronises. */
+int sgk_operator_export_1d(const sgk_op* op, double* out, int64_t cap);
+/* y = A x on the device (eq. krylov1's A applied to a coefficient vector).
+ * x_dev, y_dev: caller-owned device arrays of dof elements, FP64 when
+ * precision == SGK_FP64 and FP32 when precision == SGK_MIXED; they must not
+ * overlap.  Asynchronous. */
+int sgk_matvec(const sgk_op* op, const void* x_dev, void* y_dev, int precision);
+
+/* ------------------------------------------------------------- projection */
+
+/* L2 projection (Theorem 2.4: u_h(0) = P u_0) of
+ *   u_0(x) = const_term + sum_t amp[t] prod_m g_{t,m}(2 pi wavenum[t*d+m] x_m)
+ * with g = sin for kind 0 and cos for kind 1, into coeffs_dev (device, FP64,
+ * dof elements).  amp, wavenum, kind are host arrays of nterms (times d)
+ * entries.  1D integrals use 12-point Gauss quadrature per finest cell.
+ * Asynchronous. */
+int sgk_project_separable(sgk_ctx* ctx, const sgk_index* idx, int nterms, const double* amp, const int* wavenum,
+                          const int* kind, double const_term, double* coeffs_dev);
+
+/* ---------------------------------------------------------------- solver */
+
+/* Polynomial reaction term: f_s(u) = sum over monomials m with species[m] == s
+ * of coef[m] prod_r u_r^{exps[m*nspecies + r]}.  Host arrays. */
+typedef struct sgk_reaction {
+    int nspecies;            /* 1 .. SGK_MAX_SPECIES */
+    int nmono;               /* number of monomials (0 = no reaction) */
+    const int* species;      /* [nmono] species whose f the monomial adds to */
+    const double* coef;      /* [nmono] */
+    const int* exps;         /* [nmono * nspecies] exponents, each 0..4 */
+} sgk_reaction;
+
+/* Newton / inner-solver options; zero fields take the defaults shown. */
+typedef struct sgk_newton_opts {
+    double tol;        /* outer stop ||G||_2 <= tol max(1, ||W||_2); 1e-12 (FP64), 1e-9 (mixed) */
+    int max_iter;      /* outer cap; 50 */
+    double inner_tol;  /* CG/GMRES relative residual; 1e-13 (FP64), 1e-6 (mixed) */
+    int inner_max;     /* inner iteration cap; 500 */
+    int gmres_restart; /* GMRES restart length (systems); 50 */
+} sgk_newton_opts;
+
+/* Create an IIF solver (scheme SGK_IIF2, eq. krylov5) for nspecies species on
+ * one index set; ops[s] is the diffusion operator of species s (all on the
+ * same index set).  krylov_m in [1, 128], dt > 0.  The reaction term uses
+ * finest-mesh Gauss quadrature with q = ceil((p k + k + 1)/2) points per
+ * direction for total polynomial degree p, i.e. the exact L2 projection of
+ * f(u_h).  The finest full grid must fit in device memory
+ * ((k+1) 2^n)^d nodal values per species); else SGK_ENOMEM.
+ * opts may be NULL.  Errors: SGK_EINVAL, SGK_ENOMEM, SGK_EUNSUPPORTED. */
+int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
+                      int krylov_m, double dt, const sgk_newton_opts* opts, sgk_solver** out);
+int sgk_solver_destroy(sgk_solver* s);
+/* Set the coefficients of one species (FP64, dof elements) from host memory
+ * (on_device = 0) or from a device array (on_device = 1). */
+int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int on_device);
+/* Take nsteps IIF2 steps.  Arnoldi breakdown truncates the Krylov basis and
+ * is not an error.  On Newton failure the state is rolled back to the start
+ * of the failing step and SGK_ENEWTON is returned.  Synchronises. */
+int sgk_solver_step(sgk_solver* s, int nsteps);
+/* Copy one species' coefficients (FP64) to host (on_device = 0) or to a
+ * device array (on_device = 1); cap >= dof.  Host copies synchronise. */
+int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t cap, int on_device);
+
+typedef struct sgk_stats {
+    int64_t steps;           /* steps taken since creation */
+    int64_t newton_iters;    /* total Newton corrections */
+    int64_t inner_iters;     /* total CG/GMRES iterations */
+    int64_t krylov_calls;    /* Krylov exponentials evaluated */
+    int64_t krylov_breakdowns; /* of which truncated by happy breakdown */
+    int last_m_eff;          /* Krylov dimension of the last exponential */
+    double last_newton_residual;
+} sgk_stats;
+int sgk_solver_stats(const sgk_solver* s, sgk_stats* out);
+
+/* Component entry points of the step, for testing and benchmarking.  All
+ * vectors are caller-owned device arrays, FP64, species-stacked.  They use
+ * the solver's precision mode internally and are asynchronous. */
+/* F(U) = (int f(u_h) v_a dx)_a, finest-grid Gauss quadrature (Section 4). */
+int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev);
+/* J_F(U) w = (int f'(u_h) w_h v_a dx)_a with the same quadrature. */
+int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, double* jw_dev);
+/* w = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v for species s (eqs.
+ * krylov7-krylov8, Arnoldi with classical Gram-Schmidt applied twice).
+ * m_eff (host, may be NULL) receives the Krylov dimension used.
+ * Synchronises when m_eff is not NULL. */
+int sgk_krylov_expv(sgk_solver* s, int species, const double* v_dev, double* w_dev, int* m_eff);
+/* Copy the Hessenberg matrix ((M+1) x M, row-major) and the Krylov basis
+ * (M+1 columns of dof, column-major, FP64) of the last sgk_krylov_expv call
+ * to host.  Either pointer may be NULL.  Synchronises. */
+int sgk_krylov_export(const sgk_solver* s, double* H, double* V, int64_t cap_V);
+/* y = exp(tau X) e_1 for the m x m row-major matrix X (host), by Pade(13)
+ * scaling and squaring on the device (Section 3; Higham 2005).  m in
+ * [1, 128].  y: host array of m doubles.  Synchronises. */
+int sgk_expm_e1(sgk_ctx* ctx, int m, const double* X, double tau, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGKIIF_H */

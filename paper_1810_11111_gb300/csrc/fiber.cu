@@ -1,0 +1,286 @@
+// Fiber engine: applies a 1D sparse matrix along one direction of a
+// sparse-grid (or partly full-grid) coefficient array.
+//
+// This is the unidirectional principle of Section 4: every direction-i
+// operation of the method -- the SIPG matvec (A = -sum_i kappa_i S along i),
+// the change of basis to the finest-cell Legendre basis used by the reaction
+// term, and its transpose -- acts on 1D fibers.  For direction i, the blocks
+// sharing the levels of the other directions form a group; stacked along i
+// they hold (outer x fiber x inner) arrays whose fiber index is the 1D
+// hierarchical index a_i < (k+1) 2^{N'}, N' = N - sum_{m != i} l_m (the
+// "chunked" side), or a finest-cell Legendre index y < (k+1) 2^N (the "full"
+// side).  Each chunk (one level) is contiguous, so a fiber tile is gathered
+// with unit-stride loads along the inner extent.
+//
+// Work items are (group, column range) tiles sized to fit shared memory; a
+// grid-stride loop over items sorted by cost keeps every SM busy.  A CTA
+// stages the source fibers of its tile in shared memory, then each output
+// element is a CSR row of the 1D matrix (truncated to the fiber's levels)
+// dotted with a tile column.
+#include <algorithm>
+
+#include "sgk_internal.h"
+
+namespace {
+
+__device__ __forceinline__ int level_of(int pos, int kp1) {
+    int q = pos / kp1;
+    return q == 0 ? 0 : 32 - __clz(q);
+}
+
+__device__ __forceinline__ long long chunk_addr(const FiberGroup& g, int o, int pos, int in, int kp1, int I) {
+    int l = level_of(pos, kp1);
+    int off = l ? (kp1 << (l - 1)) : 0;
+    int nl = l ? (kp1 << (l - 1)) : kp1;
+    return g.cbase[l] + (long long)o * nl * I + (long long)(pos - off) * I + in;
+}
+
+__device__ __forceinline__ long long full_addr(const FiberGroup& g, int o, int pos, int in, int H, int I) {
+    return g.fbase + ((long long)o * H + pos) * I + in;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict__ items, int nitems,
+                                                    const FiberGroup* __restrict__ groups, const T* __restrict__ src,
+                                                    T* __restrict__ dst, const int* __restrict__ rp,
+                                                    const int* __restrict__ ci, const T* __restrict__ cv, int H,
+                                                    int kp1, T alpha, int accumulate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    __shared__ FiberGroup sg;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const FiberItem item = items[it];
+        if (threadIdx.x < (int)(sizeof(FiberGroup) / sizeof(long long)))
+            reinterpret_cast<long long*>(&sg)[threadIdx.x] =
+                reinterpret_cast<const long long*>(groups + item.group)[threadIdx.x];
+        __syncthreads();
+        const int F = kp1 << (sg.nlev - 1);
+        const int src_len = MODE == FIBER_BWD ? H : F;
+        const int dst_len = MODE == FIBER_FWD ? H : F;
+        const int lim = MODE == FIBER_BWD ? H : F;
+        const int I = sg.I, nc = item.ncols, st = item.stride;
+        const bool posfast = I < 4;
+        for (int e = threadIdx.x; e < src_len * nc; e += blockDim.x) {
+            int pos, c;
+            if (posfast) {
+                c = e / src_len;
+                pos = e - c * src_len;
+            } else {
+                pos = e / nc;
+                c = e - pos * nc;
+            }
+            const int col = item.col0 + c;
+            const int o = col / I;
+            const int in = col - o * I;
+            const long long a = MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, kp1, I);
+            tile[pos * st + c] = src[a];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < dst_len * nc; e += blockDim.x) {
+            int pos, c;
+            if (posfast) {
+                c = e / dst_len;
+                pos = e - c * dst_len;
+            } else {
+                pos = e / nc;
+                c = e - pos * nc;
+            }
+            T acc = T(0);
+            const int q1 = rp[pos + 1];
+            for (int q = rp[pos]; q < q1; ++q) {
+                const int j = ci[q];
+                if (j >= lim) break;
+                acc += cv[q] * tile[j * st + c];
+            }
+            const int col = item.col0 + c;
+            const int o = col / I;
+            const int in = col - o * I;
+            const long long a = MODE == FIBER_FWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, kp1, I);
+            T v = alpha * acc;
+            if (accumulate) v += dst[a];
+            dst[a] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Host mirror of the kernel's address arithmetic, for plan validation.
+static long long chunk_addr_host(const FiberGroup& g, long long o, int pos, long long in, int kp1, int I) {
+    const int q = pos / kp1;
+    int l = 0;
+    while ((1 << l) <= q) ++l;  // l = 0 for q = 0, else floor(log2 q) + 1
+    const int off = l ? (kp1 << (l - 1)) : 0;
+    const int nl = l ? (kp1 << (l - 1)) : kp1;
+    return g.cbase[l] + o * nl * I + (long long)(pos - off) * I + in;
+}
+
+static void validate_item(const FiberGroup& g, const FiberItem& it, int kp1, int H, int mode, long long src_size,
+                          long long dst_size) {
+    const int F = kp1 << (g.nlev - 1);
+    SGK_REQUIRE(g.nlev >= 1 && g.nlev <= SGK_MAX_LEVEL + 1, SGK_EINVAL, "plan: bad level count");
+    SGK_REQUIRE(it.col0 >= 0 && it.ncols >= 1 && (long long)it.col0 + it.ncols <= (long long)g.O * g.I, SGK_EINVAL,
+                "plan: column range outside the group");
+    for (int side = 0; side < 2; ++side) {
+        const bool full = (side == 0) ? mode == FIBER_BWD : mode == FIBER_FWD;
+        const int len = full ? H : F;
+        const long long size = side == 0 ? src_size : dst_size;
+        for (int c = 0; c < it.ncols; ++c) {
+            const long long col = it.col0 + c;
+            const long long o = col / g.I, in = col % g.I;
+            // addresses are increasing in pos within a level chunk: check the
+            // first and last position of every chunk
+            for (int l = 0; l < (full ? 1 : g.nlev); ++l) {
+                int p0, p1;
+                if (full) {
+                    p0 = 0;
+                    p1 = len - 1;
+                } else {
+                    p0 = l ? (kp1 << (l - 1)) : 0;
+                    p1 = p0 + (l ? (kp1 << (l - 1)) : kp1) - 1;
+                }
+                for (int pos : {p0, p1}) {
+                    const long long a = full ? g.fbase + (o * H + pos) * g.I + in : chunk_addr_host(g, o, pos, in, kp1, g.I);
+                    SGK_REQUIRE(a >= 0 && a < size, SGK_EINVAL, "plan: address outside its buffer");
+                }
+            }
+        }
+    }
+}
+
+void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, int H, int mode, size_t elem_bytes,
+                   size_t smem_budget, long long src_size, long long dst_size, cudaStream_t s) {
+    std::vector<FiberItem> items;
+    std::vector<long long> cost;
+    plan.max_src_len = 0;
+    plan.max_cols = 0;
+    size_t smem = 0;
+    for (int gi = 0; gi < (int)groups.size(); ++gi) {
+        const FiberGroup& g = groups[gi];
+        const int F = kp1 << (g.nlev - 1);
+        const int src_len = mode == FIBER_BWD ? H : F;
+        const int dst_len = mode == FIBER_FWD ? H : F;
+        long long cols = (long long)g.O * g.I;
+        SGK_REQUIRE(cols < (1LL << 31), SGK_EUNSUPPORTED, "plan: too many fibers in one group");
+        long long fit = (long long)(smem_budget / ((size_t)src_len * elem_bytes)) - 1;
+        int maxc = (int)std::min<long long>(64, std::max<long long>(1, fit));
+        for (long long c0 = 0; c0 < cols; c0 += maxc) {
+            FiberItem it;
+            it.group = gi;
+            it.col0 = (int)c0;
+            it.ncols = (int)std::min<long long>(maxc, cols - c0);
+            it.stride = it.ncols | 1;
+            validate_item(g, it, kp1, H, mode, src_size, dst_size);
+            items.push_back(it);
+            cost.push_back((long long)std::max(src_len, dst_len) * it.ncols);
+            smem = std::max(smem, (size_t)src_len * it.stride * elem_bytes);
+        }
+        plan.max_src_len = std::max(plan.max_src_len, src_len);
+    }
+    // most expensive items first
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<FiberItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    plan.groups.upload(groups, s);
+    plan.items.upload(sorted, s);
+    plan.nitems = (int)sorted.size();
+    plan.smem_bytes = smem;
+    SGK_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
+                  const T* cv, int H, int kp1, T alpha, int accumulate) {
+    if (plan.nitems == 0) return;
+    const int grid = std::min(plan.nitems, ctx->num_sms * 8);
+    const size_t smem = plan.smem_bytes;
+    KTimer kt(ctx, mode);  // FIBER_MATVEC / FWD / BWD coincide with KC_MATVEC / FWD / BWD
+    switch (mode) {
+#define SGK_FIBER_CASE(M)                                                                                    \
+    case M: {                                                                                                \
+        if (smem > 48 * 1024)                                                                                \
+            SGK_CUDA_CHECK(cudaFuncSetAttribute(fiber_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                (int)smem));                                                 \
+        fiber_kernel<T, M><<<grid, 256, smem, ctx->stream>>>(plan.items.p, plan.nitems, plan.groups.p, src, dst, \
+                                                              rp, ci, cv, H, kp1, alpha, accumulate);        \
+        break;                                                                                               \
+    }
+        SGK_FIBER_CASE(FIBER_MATVEC)
+        SGK_FIBER_CASE(FIBER_FWD)
+        SGK_FIBER_CASE(FIBER_BWD)
+#undef SGK_FIBER_CASE
+    }
+    check_launch("fiber_kernel");
+    count_launch(ctx);
+}
+
+template void launch_fiber<double>(sgk_ctx*, const FiberPlan&, int, const double*, double*, const int*, const int*,
+                                   const double*, int, int, double, int);
+template void launch_fiber<float>(sgk_ctx*, const FiberPlan&, int, const float*, float*, const int*, const int*,
+                                  const float*, int, int, float, int);
+
+// ------------------------------------------------------------- operator ---
+
+// Rank of a tuple among lexicographic tuples of its length with sum <= n.
+static long long rank_host(const std::vector<int>& l, int n) {
+    int len = (int)l.size(), budget = n;
+    long long r = 0;
+    for (int m = 0; m < len; ++m) {
+        for (int v = 0; v < l[m]; ++v) r += tuple_count(len - m - 1, budget - v);
+        budget -= l[m];
+    }
+    return r;
+}
+
+void build_matvec_plans(sgk_op* op) {
+    const sgk_index* idx = op->idx;
+    const int d = idx->d, N = idx->n, kp1 = idx->k + 1;
+    for (int i = 0; i < d; ++i) {
+        std::vector<FiberGroup> groups;
+        for (int64_t t = 0; t < idx->ntuples; ++t) {
+            const int32_t* l = &idx->levels[t * d];
+            if (l[i] != 0) continue;
+            FiberGroup g{};
+            int rest = 0, O = 1, I = 1;
+            for (int m = 0; m < d; ++m)
+                if (m != i) {
+                    rest += l[m];
+                    if (m < i) O *= level_count(l[m], kp1);
+                    else I *= level_count(l[m], kp1);
+                }
+            g.nlev = N - rest + 1;
+            g.O = O;
+            g.I = I;
+            std::vector<int> lv(l, l + d);
+            for (int li = 0; li < g.nlev; ++li) {
+                lv[i] = li;
+                g.cbase[li] = idx->offsets[rank_host(lv, N)];
+            }
+            groups.push_back(g);
+        }
+        finalize_plan(op->plan[i][0], groups, kp1, op->H, FIBER_MATVEC, sizeof(double), 64 * 1024, idx->dof, idx->dof,
+                      op->ctx->stream);
+        finalize_plan(op->plan[i][1], groups, kp1, op->H, FIBER_MATVEC, sizeof(float), 64 * 1024, idx->dof, idx->dof,
+                      op->ctx->stream);
+    }
+}
+
+long long tuple_rank(const std::vector<int>& l, int n) { return rank_host(l, n); }
+
+template <typename T>
+void op_matvec(const sgk_op* op, const T* x, T* y) {
+    const int d = op->idx->d;
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    for (int i = 0; i < d; ++i) {
+        const T* vals = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->S.d_val.p)
+                                       : reinterpret_cast<const T*>(op->S.d_valf.p);
+        launch_fiber<T>(op->ctx, op->plan[i][prec], FIBER_MATVEC, x, y, op->S.d_ptr.p, op->S.d_col.p, vals, op->H,
+                        op->idx->k + 1, T(-op->kappa[i]), i > 0 ? 1 : 0);
+    }
+}
+
+template void op_matvec<double>(const sgk_op*, const double*, double*);
+template void op_matvec<float>(const sgk_op*, const float*, float*);

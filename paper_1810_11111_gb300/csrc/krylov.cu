@@ -1,0 +1,658 @@
+// Krylov approximation of exp(dt A) v (Section 3, eqs. krylov7-krylov8) and
+// the vector kernels of the Newton solve.
+//
+// Arnoldi uses classical Gram-Schmidt applied twice.  Inner products and
+// norms are accumulated in FP64 with deterministic two-stage reductions
+// (per-block partials, then one block summing them in a fixed order), so a
+// run is bitwise reproducible on a given device.  Every Arnoldi step runs
+// without a host round trip: breakdown (h_{j+1,j} <= 1e-12 ||H_{0:j+1,0:j+1}||_F)
+// sets a device flag that makes the remaining steps' kernels return at once.
+//
+// exp(tau H) e_1 is computed by one CTA with scaling and squaring and the
+// [13/13] Pade approximant (Higham, SIAM J. Matrix Anal. Appl. 26 (2005),
+// with the degree fixed at 13): s = max(0, ceil(log2(||tau H||_1 / theta_13))),
+// then (V - U) R = (V + U) by LU with partial pivoting, then R <- R^2 s times.
+#include <cmath>
+
+#include "sgk_krylov.h"
+
+namespace {
+
+constexpr double THETA13 = 5.371920351148152;  // Higham (2005), Table 2.3
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block in a fixed tree; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+template <typename TA, typename TB>
+__global__ void dot_partial_kernel(const TA* __restrict__ a, const TB* __restrict__ b, long long n,
+                                   double* __restrict__ partials, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// out = sum(partials) (mode 0), sqrt(sum) (mode 1)
+__global__ void reduce_final_kernel(const double* __restrict__ partials, int nb, double* __restrict__ out, int mode,
+                                    const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = mode == 1 ? sqrt(acc) : acc;
+}
+
+// partials[block][c] = sum_e V[c][e] w[e] over the block's elements, c < ncols
+template <typename T>
+__global__ void mdot_partial_kernel(const T* __restrict__ V, long long ldv, int ncols, const T* __restrict__ w,
+                                    long long n, double* __restrict__ partials, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    __shared__ double sh[32];
+    constexpr int CH = 8;
+    for (int c0 = 0; c0 < ncols; c0 += CH) {
+        double acc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const double wv = (double)w[i];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (c0 + c < ncols) acc[c] += (double)V[(c0 + c) * ldv + i] * wv;
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (c0 + c >= ncols) break;
+            const double s = block_sum(acc[c], sh);
+            if (threadIdx.x == 0) partials[(long long)blockIdx.x * ncols + c0 + c] = s;
+        }
+    }
+}
+
+__global__ void mdot_final_kernel(const double* __restrict__ partials, int nb, int ncols, double* __restrict__ out,
+                                  const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += partials[(long long)b * ncols + c];
+        out[c] = acc;
+    }
+}
+
+// w -= V[:, :ncols] h  (arithmetic in T)
+template <typename T>
+__global__ void gs_update_kernel(const T* __restrict__ V, long long ldv, int ncols, const double* __restrict__ h,
+                                 T* __restrict__ w, long long n, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    __shared__ T hs[SGK_MAX_KRYLOV + 1];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = (T)h[c];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int c = 0; c < ncols; ++c) acc += V[c * ldv + i] * hs[c];
+        w[i] -= acc;
+    }
+}
+
+// Start of an Arnoldi process: gamma = ||v||, flags reset, breakdown if v = 0.
+__global__ void krylov_init_kernel(const double* __restrict__ gamma2, KrylovScalars* __restrict__ ks) {
+    const double g = sqrt(*gamma2);
+    ks->gamma = g;
+    ks->inv_gamma = g > 0.0 ? 1.0 / g : 0.0;
+    ks->fro2 = 0.0;
+    ks->stop = g > 0.0 ? 0 : 1;
+    ks->m_eff = 0;
+    ks->breakdown = 0;
+}
+
+template <typename T>
+__global__ void scale_to_kernel(const double* __restrict__ x, T* __restrict__ y, long long n,
+                                const double* __restrict__ s, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    const double a = *s;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)(x[i] * a);
+}
+
+template <typename T>
+__global__ void scale_vec_kernel(const T* __restrict__ x, T* __restrict__ y, long long n,
+                                 const double* __restrict__ s, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    const T a = (T)(*s);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] * a;
+}
+
+// Column j of H from the two Gram-Schmidt passes, the norm of the remainder,
+// the breakdown test and 1 / h_{j+1,j}.
+__global__ void arnoldi_finalize_kernel(int j, int M, const double* __restrict__ h1, const double* __restrict__ h2,
+                                        const double* __restrict__ wnorm2, double* __restrict__ H,
+                                        KrylovScalars* __restrict__ ks) {
+    if (ks->stop) return;
+    double f = ks->fro2;
+    if (j >= 1) {
+        const double sub = H[(long long)j * M + (j - 1)];
+        f += sub * sub;
+    }
+    for (int i = 0; i <= j; ++i) {
+        const double v = h1[i] + h2[i];
+        H[(long long)i * M + j] = v;
+        f += v * v;
+    }
+    ks->fro2 = f;
+    const double beta = sqrt(*wnorm2);
+    H[(long long)(j + 1) * M + j] = beta;
+    if (beta <= 1e-12 * sqrt(f)) {
+        ks->m_eff = j + 1;
+        ks->stop = 1;
+        ks->breakdown = 1;
+    } else {
+        ks->inv_beta = 1.0 / beta;
+        ks->m_eff = j + 1;
+    }
+}
+
+// ---------------------------------------------------------- expm kernel ---
+
+__device__ void blk_matmul(const double* A, const double* B, double* C, int m) {
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc += A[i * m + k] * B[k * m + j];
+        C[idx] = acc;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) expm_e1_kernel(const double* __restrict__ Hh, int M, const int* __restrict__ m_p,
+                                                       int m_fixed, double tau, PadeCoef pc, double* __restrict__ ws,
+                                                       double* __restrict__ y) {
+    __shared__ double sh[32];
+    __shared__ int s_piv;
+    __shared__ int s_scale;
+    const int m = m_p ? *m_p : m_fixed;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) y[i] = 0.0;
+    __syncthreads();
+    if (m <= 0) return;
+    const int mm = m * m;
+    double* X = ws;
+    double* A2 = ws + 1 * mm;
+    double* A4 = ws + 2 * mm;
+    double* A6 = ws + 3 * mm;
+    double* U = ws + 4 * mm;
+    double* V = ws + 5 * mm;
+    double* T1 = ws + 6 * mm;
+    double* T2 = ws + 7 * mm;
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        X[idx] = tau * Hh[(long long)i * M + j];
+    }
+    __syncthreads();
+    // 1-norm: maximum absolute column sum
+    double colmax = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += fabs(X[i * m + j]);
+        colmax = fmax(colmax, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) colmax = fmax(colmax, __shfl_down_sync(0xffffffffu, colmax, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = colmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double nm = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) nm = fmax(nm, sh[w]);
+        int s = 0;
+        if (nm > 0.0) s = max(0, (int)ceil(log2(nm / THETA13)));
+        s_scale = s;
+    }
+    __syncthreads();
+    const int s = s_scale;
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) X[idx] = ldexp(X[idx], -s);
+    __syncthreads();
+    blk_matmul(X, X, A2, m);
+    blk_matmul(A2, A2, A4, m);
+    blk_matmul(A4, A2, A6, m);
+    const double* b = pc.c;
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) T1[idx] = b[13] * A6[idx] + b[11] * A4[idx] + b[9] * A2[idx];
+    __syncthreads();
+    blk_matmul(A6, T1, T2, m);
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        T2[idx] += b[7] * A6[idx] + b[5] * A4[idx] + b[3] * A2[idx] + (i == j ? b[1] : 0.0);
+    }
+    __syncthreads();
+    blk_matmul(X, T2, U, m);
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) T1[idx] = b[12] * A6[idx] + b[10] * A4[idx] + b[8] * A2[idx];
+    __syncthreads();
+    blk_matmul(A6, T1, V, m);
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        const double v = V[idx] + b[6] * A6[idx] + b[4] * A4[idx] + b[2] * A2[idx] + (i == j ? b[0] : 0.0);
+        const double u = U[idx];
+        T1[idx] = v - u;  // P
+        T2[idx] = v + u;  // Q (right-hand sides)
+    }
+    __syncthreads();
+    double* P = T1;
+    double* Q = T2;
+    // LU with partial pivoting of P, applied to Q
+    for (int k = 0; k < m; ++k) {
+        if (threadIdx.x == 0) {
+            int piv = k;
+            double best = fabs(P[k * m + k]);
+            for (int i = k + 1; i < m; ++i)
+                if (fabs(P[i * m + k]) > best) {
+                    best = fabs(P[i * m + k]);
+                    piv = i;
+                }
+            s_piv = piv;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        if (piv != k) {
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                double t = P[k * m + j];
+                P[k * m + j] = P[piv * m + j];
+                P[piv * m + j] = t;
+                t = Q[k * m + j];
+                Q[k * m + j] = Q[piv * m + j];
+                Q[piv * m + j] = t;
+            }
+            __syncthreads();
+        }
+        const double pkk = P[k * m + k];
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) P[i * m + k] /= pkk;
+        __syncthreads();
+        const int rows = m - k - 1;
+        for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
+            const int i = k + 1 + idx / m, j = idx - (idx / m) * m;
+            const double l = P[i * m + k];
+            Q[i * m + j] -= l * Q[k * m + j];
+            if (j > k) P[i * m + j] -= l * P[k * m + j];
+        }
+        __syncthreads();
+    }
+    // back substitution, all right-hand sides at once
+    for (int k = m - 1; k >= 0; --k) {
+        const double pkk = P[k * m + k];
+        for (int j = threadIdx.x; j < m; j += blockDim.x) Q[k * m + j] /= pkk;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * m; idx += blockDim.x) {
+            const int i = idx / m, j = idx - (idx / m) * m;
+            Q[i * m + j] -= P[i * m + k] * Q[k * m + j];
+        }
+        __syncthreads();
+    }
+    // squaring
+    double* R = Q;
+    double* Rn = U;
+    for (int t = 0; t < s; ++t) {
+        blk_matmul(R, R, Rn, m);
+        double* tmp = R;
+        R = Rn;
+        Rn = tmp;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = R[i * m];
+}
+
+// W = gamma V[:, :m_eff] y  (FP64 accumulation)
+template <typename T>
+__global__ void combine_kernel(const T* __restrict__ V, long long ldv, const KrylovScalars* __restrict__ ks,
+                               const double* __restrict__ y, double* __restrict__ W, long long n) {
+    __shared__ double ys[SGK_MAX_KRYLOV + 1];
+    const int m = ks->m_eff;
+    const double g = ks->gamma;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) ys[c] = y[c] * g;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < m; ++c) acc += (double)V[c * ldv + i] * ys[c];
+        W[i] = acc;
+    }
+}
+
+// ------------------------------------------------------ vector kernels ---
+
+template <typename TS, typename TD>
+__global__ void convert_kernel(const TS* __restrict__ x, TD* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (TD)x[i];
+}
+
+// z = a x + b y, scalars from the host
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                             double* __restrict__ z, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[i] = a * x[i] + b * y[i];
+}
+
+// G = U - c F - W
+__global__ void residual_kernel(const double* __restrict__ U, const double* __restrict__ F,
+                                const double* __restrict__ W, double c, double* __restrict__ G, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        G[i] = U[i] - c * F[i] - W[i];
+}
+
+// q = p - c Jp
+template <typename T>
+__global__ void jac_finish_kernel(const double* __restrict__ p, const T* __restrict__ Jp, double c,
+                                  double* __restrict__ q, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        q[i] = p[i] - c * (double)Jp[i];
+}
+
+// CG: alpha = rr / pq; x += alpha p; r -= alpha q
+__global__ void cg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                 const double* __restrict__ q, const double* __restrict__ rr,
+                                 const double* __restrict__ pq, long long n) {
+    const double alpha = *rr / *pq;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+    }
+}
+
+// CG: p = r + (rr_new / rr_old) p
+__global__ void cg_direction_kernel(double* __restrict__ p, const double* __restrict__ r,
+                                    const double* __restrict__ rr_new, const double* __restrict__ rr_old, long long n) {
+    const double beta = *rr_new / *rr_old;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = r[i] + beta * p[i];
+}
+
+// x += V[:, :m] y with y on the device
+__global__ void basis_accumulate_kernel(const double* __restrict__ V, long long ldv, int m,
+                                        const double* __restrict__ y, double* __restrict__ x, long long n) {
+    __shared__ double ys[SGK_MAX_KRYLOV + 1];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) ys[c] = y[c];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < m; ++c) acc += V[c * ldv + i] * ys[c];
+        x[i] += acc;
+    }
+}
+
+// GMRES: Givens rotations on column j of the (restart+1) x restart matrix
+// Hg (row-major, ld = restart), update of g; reports |g_{j+1}|, h_{j+1,j}
+// and the rotated diagonal to the host.
+__global__ void gmres_givens_kernel(int j, int ld, double* __restrict__ Hg, double* __restrict__ cs,
+                                    double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ h1,
+                                    const double* __restrict__ h2, const double* __restrict__ hn2,
+                                    double* __restrict__ report) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i <= j; ++i) Hg[i * ld + j] = h1[i] + h2[i];
+    const double hn = sqrt(*hn2);
+    Hg[(j + 1) * ld + j] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hg[i * ld + j] + sn[i] * Hg[(i + 1) * ld + j];
+        Hg[(i + 1) * ld + j] = -sn[i] * Hg[i * ld + j] + cs[i] * Hg[(i + 1) * ld + j];
+        Hg[i * ld + j] = t;
+    }
+    const double den = hypot(Hg[j * ld + j], Hg[(j + 1) * ld + j]);
+    cs[j] = Hg[j * ld + j] / den;
+    sn[j] = Hg[(j + 1) * ld + j] / den;
+    Hg[j * ld + j] = den;
+    Hg[(j + 1) * ld + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    report[0] = fabs(g[j + 1]);
+    report[1] = hn;
+    report[2] = den;
+    report[3] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+// GMRES: solve the triangular system H[:m,:m] y = g[:m]
+__global__ void gmres_solve_kernel(int m, int ld, const double* __restrict__ Hg, const double* __restrict__ g,
+                                   double* __restrict__ y) {
+    if (threadIdx.x != 0) return;
+    for (int i = m - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int c = i + 1; c < m; ++c) acc -= Hg[i * ld + c] * y[c];
+        y[i] = acc / Hg[i * ld + i];
+    }
+}
+
+__global__ void gmres_init_kernel(double* __restrict__ g, int len, const double* __restrict__ beta,
+                                  double* __restrict__ inv_beta) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        g[0] = *beta;
+        *inv_beta = 1.0 / *beta;
+    }
+}
+
+int grid_for(const sgk_ctx* ctx, long long n) {
+    long long b = (n + 255) / 256;
+    return (int)std::max(1LL, std::min<long long>(b, (long long)ctx->num_sms * 4));
+}
+
+}  // namespace
+
+int reduction_blocks(const sgk_ctx* ctx, int64_t n) {
+    long long b = (n + 1023) / 1024;
+    return (int)std::max(1LL, std::min<long long>(b, (long long)ctx->num_sms * 2));
+}
+
+// ------------------------------------------------------------ host API ---
+
+PadeCoef pade13_coefficients() {
+    // numerator coefficients of the [m/m] Pade approximant of e^x:
+    // c_j = (2m - j)! m! / ((2m)! j! (m - j)!)
+    PadeCoef pc;
+    const int m = 13;
+    long double f[27];
+    f[0] = 1;
+    for (int i = 1; i <= 26; ++i) f[i] = f[i - 1] * i;
+    for (int j = 0; j <= m; ++j) pc.c[j] = (double)(f[2 * m - j] * f[m] / (f[2 * m] * f[j] * f[m - j]));
+    return pc;
+}
+
+void vk_dot(sgk_ctx* ctx, const double* a, const double* b, long long n, double* partials, double* out, int mode,
+            const int* stop) {
+    KTimer kt(ctx, KC_REDUCE);
+    const int nb = reduction_blocks(ctx, n);
+    dot_partial_kernel<double, double><<<nb, RED_THREADS, 0, ctx->stream>>>(a, b, n, partials, stop);
+    reduce_final_kernel<<<1, RED_THREADS, 0, ctx->stream>>>(partials, nb, out, mode, stop);
+    check_launch("dot");
+    count_launch(ctx, 2);
+}
+
+template <typename T>
+void vk_dotT(sgk_ctx* ctx, const T* a, const T* b, long long n, double* partials, double* out, int mode,
+             const int* stop) {
+    KTimer kt(ctx, KC_REDUCE);
+    const int nb = reduction_blocks(ctx, n);
+    dot_partial_kernel<T, T><<<nb, RED_THREADS, 0, ctx->stream>>>(a, b, n, partials, stop);
+    reduce_final_kernel<<<1, RED_THREADS, 0, ctx->stream>>>(partials, nb, out, mode, stop);
+    check_launch("dotT");
+    count_launch(ctx, 2);
+}
+
+template <typename T>
+void vk_mdot(sgk_ctx* ctx, const T* V, long long ldv, int ncols, const T* w, long long n, double* partials,
+             double* out, const int* stop) {
+    KTimer kt(ctx, KC_REDUCE);
+    const int nb = reduction_blocks(ctx, n);
+    mdot_partial_kernel<T><<<nb, RED_THREADS, 0, ctx->stream>>>(V, ldv, ncols, w, n, partials, stop);
+    mdot_final_kernel<<<1, 256, 0, ctx->stream>>>(partials, nb, ncols, out, stop);
+    check_launch("mdot");
+    count_launch(ctx, 2);
+}
+
+template <typename T>
+void vk_gs_update(sgk_ctx* ctx, const T* V, long long ldv, int ncols, const double* h, T* w, long long n,
+                  const int* stop) {
+    KTimer kt(ctx, KC_REDUCE);
+    gs_update_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(V, ldv, ncols, h, w, n, stop);
+    check_launch("gs_update");
+    count_launch(ctx);
+}
+
+void vk_convert(sgk_ctx* ctx, const double* x, float* y, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    convert_kernel<double, float><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n);
+    check_launch("convert");
+    count_launch(ctx);
+}
+void vk_convert(sgk_ctx* ctx, const float* x, double* y, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    convert_kernel<float, double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n);
+    check_launch("convert");
+    count_launch(ctx);
+}
+void vk_axpby(sgk_ctx* ctx, double a, const double* x, double b, const double* y, double* z, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    axpby_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(a, x, b, y, z, n);
+    check_launch("axpby");
+    count_launch(ctx);
+}
+void vk_residual(sgk_ctx* ctx, const double* U, const double* F, const double* W, double c, double* G, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    residual_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(U, F, W, c, G, n);
+    check_launch("residual");
+    count_launch(ctx);
+}
+template <typename T>
+void vk_jac_finish(sgk_ctx* ctx, const double* p, const T* Jp, double c, double* q, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    jac_finish_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(p, Jp, c, q, n);
+    check_launch("jac_finish");
+    count_launch(ctx);
+}
+void vk_cg_update(sgk_ctx* ctx, double* x, double* r, const double* p, const double* q, const double* rr,
+                  const double* pq, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    cg_update_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, r, p, q, rr, pq, n);
+    check_launch("cg_update");
+    count_launch(ctx);
+}
+void vk_cg_direction(sgk_ctx* ctx, double* p, const double* r, const double* rr_new, const double* rr_old,
+                     long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    cg_direction_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(p, r, rr_new, rr_old, n);
+    check_launch("cg_direction");
+    count_launch(ctx);
+}
+void vk_basis_accumulate(sgk_ctx* ctx, const double* V, long long ldv, int m, const double* y, double* x,
+                         long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    basis_accumulate_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(V, ldv, m, y, x, n);
+    check_launch("basis_accumulate");
+    count_launch(ctx);
+}
+void vk_scale_from(sgk_ctx* ctx, const double* x, double* y, long long n, const double* s, const int* stop) {
+    KTimer kt(ctx, KC_VECTOR);
+    scale_to_kernel<double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n, s, stop);
+    check_launch("scale");
+    count_launch(ctx);
+}
+void gmres_givens(sgk_ctx* ctx, int j, int ld, double* Hg, double* cs, double* sn, double* g, const double* h1,
+                  const double* h2, const double* hn2, double* report) {
+    KTimer kt(ctx, KC_VECTOR);
+    gmres_givens_kernel<<<1, 32, 0, ctx->stream>>>(j, ld, Hg, cs, sn, g, h1, h2, hn2, report);
+    check_launch("gmres_givens");
+    count_launch(ctx);
+}
+void gmres_solve(sgk_ctx* ctx, int m, int ld, const double* Hg, const double* g, double* y) {
+    KTimer kt(ctx, KC_VECTOR);
+    gmres_solve_kernel<<<1, 32, 0, ctx->stream>>>(m, ld, Hg, g, y);
+    check_launch("gmres_solve");
+    count_launch(ctx);
+}
+void gmres_init(sgk_ctx* ctx, double* g, int len, const double* beta, double* inv_beta) {
+    KTimer kt(ctx, KC_VECTOR);
+    gmres_init_kernel<<<1, 64, 0, ctx->stream>>>(g, len, beta, inv_beta);
+    check_launch("gmres_init");
+    count_launch(ctx);
+}
+
+void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed, double tau, double* ws, double* y) {
+    KTimer kt(ctx, KC_EXPM);
+    expm_e1_kernel<<<1, 512, 0, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), ws, y);
+    check_launch("expm_e1");
+    count_launch(ctx);
+}
+
+template <typename T>
+void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<void(const T*, T*)>& matvec,
+                     const double* v, double* W, long long n, int M, double dt) {
+    KrylovScalars* ks = kw.ks;
+    const int* stop = &ks->stop;
+    // gamma = ||v||
+    vk_dot(ctx, v, v, n, kw.partials, kw.scal, 0, nullptr);
+    {
+        KTimer kt(ctx, KC_VECTOR);
+        krylov_init_kernel<<<1, 1, 0, ctx->stream>>>(kw.scal, ks);
+    }
+    check_launch("krylov_init");
+    count_launch(ctx);
+    {
+        KTimer kt(ctx, KC_VECTOR);
+        scale_to_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(v, kw.V, n, &ks->inv_gamma, stop);
+    }
+    check_launch("scale_to");
+    count_launch(ctx);
+    for (int j = 0; j < M; ++j) {
+        T* vj = kw.V + (long long)j * n;
+        matvec(vj, kw.w);
+        vk_mdot<T>(ctx, kw.V, n, j + 1, kw.w, n, kw.partials, kw.h1, stop);
+        vk_gs_update<T>(ctx, kw.V, n, j + 1, kw.h1, kw.w, n, stop);
+        vk_mdot<T>(ctx, kw.V, n, j + 1, kw.w, n, kw.partials, kw.h2, stop);
+        vk_gs_update<T>(ctx, kw.V, n, j + 1, kw.h2, kw.w, n, stop);
+        vk_dotT<T>(ctx, kw.w, kw.w, n, kw.partials, kw.scal + 1, 0, stop);
+        {
+            KTimer kt(ctx, KC_REDUCE);
+            arnoldi_finalize_kernel<<<1, 1, 0, ctx->stream>>>(j, M, kw.h1, kw.h2, kw.scal + 1, kw.H, ks);
+        }
+        check_launch("arnoldi_finalize");
+        count_launch(ctx);
+        {
+            KTimer kt(ctx, KC_VECTOR);
+            scale_vec_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.w, kw.V + (long long)(j + 1) * n, n,
+                                                                            &ks->inv_beta, stop);
+        }
+        check_launch("scale_vec");
+        count_launch(ctx);
+    }
+    expm_e1(ctx, kw.H, M, &ks->m_eff, 0, dt, kw.expm_ws, kw.y);
+    {
+        KTimer kt(ctx, KC_VECTOR);
+        combine_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.V, n, ks, kw.y, W, n);
+    }
+    check_launch("combine");
+    count_launch(ctx);
+}
+
+template void krylov_expv_dev<double>(sgk_ctx*, const KrylovWork<double>&,
+                                      const std::function<void(const double*, double*)>&, const double*, double*,
+                                      long long, int, double);
+template void krylov_expv_dev<float>(sgk_ctx*, const KrylovWork<float>&,
+                                     const std::function<void(const float*, float*)>&, const double*, double*,
+                                     long long, int, double);
+template void vk_mdot<double>(sgk_ctx*, const double*, long long, int, const double*, long long, double*, double*,
+                              const int*);
+template void vk_gs_update<double>(sgk_ctx*, const double*, long long, int, const double*, double*, long long,
+                                   const int*);
+template void vk_jac_finish<double>(sgk_ctx*, const double*, const double*, double, double*, long long);
+template void vk_jac_finish<float>(sgk_ctx*, const double*, const float*, double, double*, long long);

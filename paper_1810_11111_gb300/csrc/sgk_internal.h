@@ -1,0 +1,229 @@
+// Internal declarations shared by the libsgkiif translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sgkiif.h"
+
+// --------------------------------------------------------------- errors ---
+
+struct SgkError {
+    int code;
+    std::string msg;
+};
+
+#define SGK_CUDA_CHECK(call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw SgkError{SGK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};    \
+    } while (0)
+
+#define SGK_REQUIRE(cond, code, text)                  \
+    do {                                               \
+        if (!(cond)) throw SgkError{(code), (text)};   \
+    } while (0)
+
+// ---------------------------------------------------- device allocations ---
+
+// Owning device buffer (cudaMalloc / cudaFree); moves only.
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) return;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            throw SgkError{SGK_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+        }
+        n = count;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void upload(const T* host, size_t count, cudaStream_t s) {
+        if (count) SGK_CUDA_CHECK(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void upload(const std::vector<T>& v, cudaStream_t s) {
+        alloc(v.size());
+        upload(v.data(), v.size(), s);
+    }
+};
+
+// -------------------------------------------------------------- context ---
+
+// Kernel classes for the optional event timing (bit i of the profile mask).
+enum KernelClass {
+    KC_MATVEC = 0,   // fiber engine, SIPG matvec
+    KC_FWD = 1,      // fiber engine, hierarchical -> finest Legendre
+    KC_BWD = 2,      // fiber engine, transpose
+    KC_CELL = 3,     // cell quadrature of the reaction term / Jacobian
+    KC_REDUCE = 4,   // inner products, Gram-Schmidt passes
+    KC_EXPM = 5,     // exp(tau H) e_1
+    KC_VECTOR = 6,   // other vector kernels
+    KC_COUNT = 7
+};
+
+struct sgk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = SGK_FP64;
+    std::string last_error;
+    int64_t launches = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    // event timing
+    unsigned prof_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    ~sgk_ctx();
+};
+
+// Every kernel launch of the library goes through this counter.
+inline void count_launch(sgk_ctx* c, int n = 1) { c->launches += n; }
+void check_launch(const char* what);
+
+// Brackets the launches issued during its lifetime with CUDA events when the
+// class is selected in the context's profile mask.
+struct KTimer {
+    sgk_ctx* ctx;
+    int kc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(sgk_ctx* c, int k);
+    ~KTimer();
+};
+
+// ------------------------------------------------------------ index set ---
+
+struct sgk_index {
+    sgk_ctx* ctx = nullptr;
+    int d = 0, n = 0, k = 0;
+    int64_t dof = 0;
+    int64_t ntuples = 0;
+    std::vector<int32_t> levels;   // ntuples x d (host copy of the device table)
+    std::vector<int64_t> offsets;  // ntuples + 1
+    DevBuf<int32_t> d_levels;
+    DevBuf<int64_t> d_offsets;
+};
+
+// Number of tuples of length len with entries >= 0 and sum <= budget:
+// C(budget + len, len).
+int64_t tuple_count(int len, int budget);
+// Lexicographic tuples (first entry slowest) of length len with sum <= budget.
+std::vector<std::vector<int>> tuples_lex(int len, int budget);
+inline int level_count(int l, int kp1) { return l == 0 ? kp1 : kp1 << (l - 1); }
+inline int level_offset(int l, int kp1) { return l == 0 ? 0 : kp1 << (l - 1); }
+
+// -------------------------------------------------- 1D tables (host C++) ---
+
+// Sparse matrix in CSR form with sorted column indices, host and device
+// (FP64 and FP32 value copies).
+struct Csr {
+    int rows = 0, cols = 0;
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+    DevBuf<int> d_ptr, d_col;
+    DevBuf<double> d_val;
+    DevBuf<float> d_valf;
+    void upload(cudaStream_t s);
+};
+
+struct Tables1D {
+    int N = 0, k = 0, H = 0;
+    std::vector<double> alpert;  // (k+1) x 2(k+1) wavelet coefficients
+    Csr T;                       // H x H: hierarchical -> finest-cell Legendre
+    Csr Tt;                      // transpose of T
+};
+
+// Gauss-Legendre rule on [-1, 1] with q points (Newton on P_q, long double).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);
+// Alpert multiwavelet coefficients (rows p = 0..k over [left Legendre 0..k,
+// right Legendre 0..k]).
+std::vector<double> alpert_coefficients(int k);
+// Build T and its transpose for level N, degree k.
+void build_transform_tables(int N, int k, Tables1D& out);
+// 1D SIPG matrix in the hierarchical basis, dense row-major H x H.
+std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma);
+
+// --------------------------------------------------------- fiber engine ---
+
+struct FiberGroup {
+    long long cbase[SGK_MAX_LEVEL + 1];  // chunked side: start of each level's chunk
+    long long fbase;                     // full side: start of the block
+    int nlev;                            // levels 0..nlev-1 along the fiber
+    int I;                               // inner (contiguous) extent
+    int O;                               // outer extent
+    int pad;
+};
+
+struct FiberItem {
+    int group;
+    int col0;
+    int ncols;
+    int stride;  // smem column stride (ncols rounded to odd)
+};
+
+enum FiberMode { FIBER_MATVEC = 0, FIBER_FWD = 1, FIBER_BWD = 2 };
+
+struct FiberPlan {
+    DevBuf<FiberGroup> groups;
+    DevBuf<FiberItem> items;
+    int nitems = 0;
+    int max_src_len = 0;
+    int max_cols = 0;
+    size_t smem_bytes = 0;
+};
+
+// Host-side construction of a plan from groups (fills items, uploads).
+// Every address a work item can touch is checked on the host against the
+// source and destination sizes before the plan is uploaded.
+void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, int H, int mode, size_t elem_bytes,
+                   size_t smem_budget, long long src_size, long long dst_size, cudaStream_t s);
+
+template <typename T>
+void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
+                  const T* cv, int H, int kp1, T alpha, int accumulate);
+
+// ------------------------------------------------------------- operator ---
+
+struct sgk_op {
+    sgk_ctx* ctx = nullptr;
+    const sgk_index* idx = nullptr;
+    double kappa[SGK_MAX_DIM] = {0};
+    int bc = SGK_PERIODIC;
+    double sigma = 20.0;
+    int H = 0;
+    std::vector<double> S_dense;  // H x H host copy
+    Csr S;
+    FiberPlan plan[SGK_MAX_DIM][2];  // [dim][0 = fp64, 1 = fp32]
+};
+
+template <typename T>
+void op_matvec(const sgk_op* op, const T* x, T* y);
+
+// -------------------------------------------------------------- kernels ---
+
+// Deterministic reductions: partials per block, then one block sums them in
+// a fixed order.
+constexpr int RED_THREADS = 256;
+int reduction_blocks(const sgk_ctx* ctx, int64_t n);

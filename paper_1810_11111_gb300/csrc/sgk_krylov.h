@@ -1,0 +1,67 @@
+// Krylov exponential and vector kernels: shared declarations.
+#pragma once
+
+#include <functional>
+
+#include "sgk_internal.h"
+
+struct KrylovScalars {
+    double gamma;
+    double inv_gamma;
+    double inv_beta;
+    double fro2;
+    int stop;       // set by breakdown (or gamma == 0): later steps return at once
+    int m_eff;      // Krylov dimension reached
+    int breakdown;  // 1 if truncated by happy breakdown
+    int pad;
+};
+
+struct PadeCoef {
+    double c[14];
+};
+
+// Device workspace of one Krylov exponential; V holds M+1 columns of n.
+template <typename T>
+struct KrylovWork {
+    T* V = nullptr;
+    T* w = nullptr;
+    double* H = nullptr;      // (M+1) x M row-major
+    double* h1 = nullptr;     // M+1
+    double* h2 = nullptr;     // M+1
+    double* y = nullptr;      // M
+    double* scal = nullptr;   // [0] gamma^2, [1] ||w||^2
+    double* partials = nullptr;
+    double* expm_ws = nullptr;  // 8 M^2
+    KrylovScalars* ks = nullptr;
+};
+
+PadeCoef pade13_coefficients();
+void vk_dot(sgk_ctx* ctx, const double* a, const double* b, long long n, double* partials, double* out, int mode,
+            const int* stop);
+template <typename T>
+void vk_mdot(sgk_ctx* ctx, const T* V, long long ldv, int ncols, const T* w, long long n, double* partials,
+             double* out, const int* stop);
+template <typename T>
+void vk_gs_update(sgk_ctx* ctx, const T* V, long long ldv, int ncols, const double* h, T* w, long long n,
+                  const int* stop);
+void vk_convert(sgk_ctx* ctx, const double* x, float* y, long long n);
+void vk_convert(sgk_ctx* ctx, const float* x, double* y, long long n);
+void vk_axpby(sgk_ctx* ctx, double a, const double* x, double b, const double* y, double* z, long long n);
+void vk_residual(sgk_ctx* ctx, const double* U, const double* F, const double* W, double c, double* G, long long n);
+template <typename T>
+void vk_jac_finish(sgk_ctx* ctx, const double* p, const T* Jp, double c, double* q, long long n);
+void vk_cg_update(sgk_ctx* ctx, double* x, double* r, const double* p, const double* q, const double* rr,
+                  const double* pq, long long n);
+void vk_cg_direction(sgk_ctx* ctx, double* p, const double* r, const double* rr_new, const double* rr_old,
+                     long long n);
+void vk_basis_accumulate(sgk_ctx* ctx, const double* V, long long ldv, int m, const double* y, double* x,
+                         long long n);
+void vk_scale_from(sgk_ctx* ctx, const double* x, double* y, long long n, const double* s, const int* stop);
+void gmres_givens(sgk_ctx* ctx, int j, int ld, double* Hg, double* cs, double* sn, double* g, const double* h1,
+                  const double* h2, const double* hn2, double* report);
+void gmres_solve(sgk_ctx* ctx, int m, int ld, const double* Hg, const double* g, double* y);
+void gmres_init(sgk_ctx* ctx, double* g, int len, const double* beta, double* inv_beta);
+void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed, double tau, double* ws, double* y);
+template <typename T>
+void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<void(const T*, T*)>& matvec,
+                     const double* v, double* W, long long n, int M, double dt);

@@ -1,0 +1,40 @@
+// Finest-grid quadrature of the reaction term: shared declarations.
+#pragma once
+
+#include "sgk_internal.h"
+
+#define SGK_MAX_MONO 16
+
+// Polynomial reaction, device copy passed by value to kernels.
+struct ReactionDev {
+    int nspecies = 1;
+    int nmono = 0;
+    int species[SGK_MAX_MONO] = {0};
+    double coef[SGK_MAX_MONO] = {0};
+    int exps[SGK_MAX_MONO][SGK_MAX_SPECIES] = {{0}};
+};
+
+struct Quad {
+    const sgk_index* idx = nullptr;
+    int d = 0, N = 0, kp1 = 0, q = 0, H = 0, nspecies = 1, maxstage = 0;
+    Tables1D tab;
+    std::vector<std::vector<long long>> layout_offsets;  // R_i block offsets, i = 0..d
+    std::vector<long long> layout_size;                  // R_i total sizes
+    long long full_size = 0;                             // H^d
+    FiberPlan fwd[SGK_MAX_DIM][2], bwd[SGK_MAX_DIM][2];  // [direction][fp64, fp32]
+    DevBuf<double> B64, w64;
+    DevBuf<float> B32, w32;
+};
+
+int reaction_degree(const ReactionDev& rx);
+long long tuple_rank(const std::vector<int>& l, int n);
+void quad_build(Quad& Q, const sgk_index* idx, int q, int nspecies, bool need_jacobian);
+template <typename T>
+void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* tmp);
+template <typename T>
+void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out);
+template <typename T>
+void quad_cells(sgk_ctx* ctx, const Quad& Q, const ReactionDev& rx, bool jac, const T* const* u, const T* const* w,
+                T* const* out);
+void project_separable_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, int nterms, const double* amp,
+                           const int* wavenum, const int* kind, double c0, double* U);

@@ -1,0 +1,42 @@
+// IIF solver object: shared declarations.
+#pragma once
+
+#include "sgk_krylov.h"
+#include "sgk_quad.h"
+
+struct sgk_solver {
+    sgk_ctx* ctx = nullptr;
+    const sgk_index* idx = nullptr;
+    int nspecies = 1;
+    const sgk_op* ops[SGK_MAX_SPECIES] = {nullptr};
+    ReactionDev rx;
+    bool has_rx = false;
+    int M = 0;
+    double dt = 0.0;
+    sgk_newton_opts opts{};
+    int prec = SGK_FP64;
+    long long n = 0;  // dof per species
+    Quad Q;
+    bool unod_valid = false;
+    // state and Newton vectors (species-stacked FP64)
+    DevBuf<double> U, Uprev, W, vv, Fv, G, cg_x, cg_r, cg_p, cg_q;
+    // Krylov workspace
+    DevBuf<double> V64, w64;
+    DevBuf<float> V32, w32;
+    DevBuf<double> Hm, h1, h2, ky, scal, partials, expm_ws;
+    DevBuf<KrylovScalars> ks;
+    // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
+    DevBuf<double> q64, jw64;
+    DevBuf<float> q32, jw32;
+    // GMRES (systems)
+    DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
+    double* hscal = nullptr;  // pinned host scalars
+    sgk_stats stats{};
+    ~sgk_solver();
+};
+
+void solver_alloc(sgk_solver* s);
+int solver_step(sgk_solver* s, int nsteps);
+void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
+void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);
+void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W);

@@ -1,0 +1,385 @@
+// IIF2 time stepping (eq. krylov5) with a Newton implicit stage.
+//
+//   v_s   = U_s^n + dt/2 F_s(U^n)                    (predictor)
+//   W_s   = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v_s  (per species)
+//   solve G(U) = U - dt/2 F(U) - W = 0 by Newton from U = W:
+//         (I - dt/2 J_F(U)) delta = -G(U), U += delta,
+//   inner solver: CG for one species (symmetric), restarted GMRES for systems;
+//   outer stop ||G||_2 <= tol max(1, ||W||_2); on failure the step is undone.
+//
+// All vectors live on the device; the host only reads back the scalars that
+// decide loop exits.  In SGK_MIXED mode the matvec, Arnoldi basis, axpys of
+// the Gram-Schmidt passes and the reaction/Jacobian passes run in FP32; inner
+// products, norms, exp(dt H), the Newton residual vector and the state stay
+// FP64.  Because FP32 reaction passes put a floor under the residual, the
+// mixed outer loop also stops when ||G|| no longer halves and is below
+// 1e-6 max(1, ||W||) (the Newton iteration has reached that floor).
+#include <cmath>
+#include <cstring>
+
+#include "sgk_krylov.h"
+#include "sgk_quad.h"
+#include "sgk_solver.h"
+
+namespace {
+
+double read_scalar(sgk_solver* s, const double* dptr) {
+    SGK_CUDA_CHECK(cudaMemcpyAsync(s->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
+    SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
+    return s->hscal[0];
+}
+
+template <typename T>
+T* qbuf(sgk_solver* s) {
+    return sizeof(T) == 8 ? reinterpret_cast<T*>(s->q64.p) : reinterpret_cast<T*>(s->q32.p);
+}
+
+// quad buffer carving: [unod S][wnod S][tmp][spin S][spout S]
+template <typename T>
+struct QuadPtrs {
+    T* unod[SGK_MAX_SPECIES];
+    T* wnod[SGK_MAX_SPECIES];
+    T* tmp;
+    T* spin[SGK_MAX_SPECIES];
+    T* spout[SGK_MAX_SPECIES];
+};
+
+template <typename T>
+QuadPtrs<T> qptrs(sgk_solver* s) {
+    QuadPtrs<T> p{};
+    T* b = qbuf<T>(s);
+    const long long F = s->Q.full_size, n = s->n;
+    for (int i = 0; i < s->nspecies; ++i) p.unod[i] = b + i * F;
+    for (int i = 0; i < s->nspecies; ++i) p.wnod[i] = b + (s->nspecies + i) * F;
+    p.tmp = b + 2LL * s->nspecies * F;
+    T* sp = b + (2LL * s->nspecies + 1) * F;
+    for (int i = 0; i < s->nspecies; ++i) p.spin[i] = sp + i * n;
+    for (int i = 0; i < s->nspecies; ++i) p.spout[i] = sp + (s->nspecies + i) * n;
+    return p;
+}
+
+// F(U) for species-stacked FP64 U into FP64 F; leaves nodal U in unod.
+template <typename T>
+void evalF_T(sgk_solver* s, const double* U, double* F) {
+    QuadPtrs<T> p = qptrs<T>(s);
+    const long long n = s->n;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        const T* src;
+        if (sizeof(T) == 8) src = reinterpret_cast<const T*>(U + sp * n);
+        else {
+            vk_convert(s->ctx, U + sp * n, reinterpret_cast<float*>(p.spin[sp]), n);
+            src = p.spin[sp];
+        }
+        quad_forward<T>(s->ctx, s->Q, src, p.unod[sp], p.tmp);
+    }
+    quad_cells<T>(s->ctx, s->Q, s->rx, false, p.unod, nullptr, p.wnod);
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        if (sizeof(T) == 8) {
+            quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, reinterpret_cast<T*>(F + sp * n));
+        } else {
+            quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, p.spout[sp]);
+            vk_convert(s->ctx, reinterpret_cast<const float*>(p.spout[sp]), F + sp * n, n);
+        }
+    }
+    s->unod_valid = true;
+}
+
+// J_F(U) w for the U whose nodal values are cached in unod; output in T.
+template <typename T>
+void evalJ_T(sgk_solver* s, const double* w, T* out) {
+    QuadPtrs<T> p = qptrs<T>(s);
+    const long long n = s->n;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        const T* src;
+        if (sizeof(T) == 8) src = reinterpret_cast<const T*>(w + sp * n);
+        else {
+            vk_convert(s->ctx, w + sp * n, reinterpret_cast<float*>(p.spin[sp]), n);
+            src = p.spin[sp];
+        }
+        quad_forward<T>(s->ctx, s->Q, src, p.wnod[sp], p.tmp);
+    }
+    quad_cells<T>(s->ctx, s->Q, s->rx, true, p.unod, p.wnod, p.wnod);
+    for (int sp = 0; sp < s->nspecies; ++sp) quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, out + sp * n);
+}
+
+void evalF(sgk_solver* s, const double* U, double* F) {
+    if (s->prec == SGK_FP64) evalF_T<double>(s, U, F);
+    else evalF_T<float>(s, U, F);
+}
+
+// q = p - dt/2 J_F(U) p (stacked FP64)
+void apply_newton_matrix(sgk_solver* s, const double* pv, double* q) {
+    const long long N = s->n * s->nspecies;
+    if (s->prec == SGK_FP64) {
+        evalJ_T<double>(s, pv, s->jw64.p);
+        vk_jac_finish<double>(s->ctx, pv, s->jw64.p, 0.5 * s->dt, q, N);
+    } else {
+        evalJ_T<float>(s, pv, s->jw32.p);
+        vk_jac_finish<float>(s->ctx, pv, s->jw32.p, 0.5 * s->dt, q, N);
+    }
+}
+
+template <typename T>
+KrylovWork<T> krylov_work(sgk_solver* s, int species) {
+    KrylovWork<T> kw;
+    kw.V = sizeof(T) == 8 ? reinterpret_cast<T*>(s->V64.p) : reinterpret_cast<T*>(s->V32.p);
+    kw.w = sizeof(T) == 8 ? reinterpret_cast<T*>(s->w64.p) : reinterpret_cast<T*>(s->w32.p);
+    kw.H = s->Hm.p;
+    kw.h1 = s->h1.p;
+    kw.h2 = s->h2.p;
+    kw.y = s->ky.p;
+    kw.scal = s->scal.p;
+    kw.partials = s->partials.p;
+    kw.expm_ws = s->expm_ws.p;
+    kw.ks = s->ks.p + species;
+    return kw;
+}
+
+void cg_solve(sgk_solver* s, const double* G, double* x, int& iters) {
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    double* r = s->cg_r.p;
+    double* pv = s->cg_p.p;
+    double* q = s->cg_q.p;
+    double* rr = s->scal.p + 2;
+    double* rr_new = s->scal.p + 3;
+    double* pq = s->scal.p + 4;
+    SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
+    vk_axpby(ctx, -1.0, G, 0.0, G, r, N);
+    vk_axpby(ctx, -1.0, G, 0.0, G, pv, N);
+    vk_dot(ctx, r, r, N, s->partials.p, rr, 0, nullptr);
+    double rr_h = read_scalar(s, rr);
+    const double stop = s->opts.inner_tol * s->opts.inner_tol * rr_h;
+    iters = 0;
+    while (iters < s->opts.inner_max && rr_h > stop) {
+        apply_newton_matrix(s, pv, q);
+        vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
+        vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
+        vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
+        vk_cg_direction(ctx, pv, r, rr_new, rr, N);
+        rr_h = read_scalar(s, rr_new);
+        std::swap(rr, rr_new);
+        ++iters;
+    }
+}
+
+void gmres_solve_host(sgk_solver* s, const double* G, double* x, int& iters) {
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    const int restart = s->opts.gmres_restart;
+    double* b = s->cg_p.p;
+    double* r = s->cg_r.p;
+    double* w = s->cg_q.p;
+    double* V = s->gm_V.p;
+    double* beta = s->scal.p + 2;
+    double* hn2 = s->scal.p + 3;
+    double* rep = s->gm_report.p;
+    vk_axpby(ctx, -1.0, G, 0.0, G, b, N);
+    SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
+    vk_dot(ctx, b, b, N, s->partials.p, beta, 1, nullptr);
+    const double bnorm = read_scalar(s, beta);
+    iters = 0;
+    if (bnorm == 0.0) return;
+    const double tol = s->opts.inner_tol * bnorm;
+    while (iters < s->opts.inner_max) {
+        if (iters == 0) {
+            SGK_CUDA_CHECK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            apply_newton_matrix(s, x, w);
+            vk_axpby(ctx, 1.0, b, -1.0, w, r, N);
+        }
+        vk_dot(ctx, r, r, N, s->partials.p, beta, 1, nullptr);
+        const double beta_h = read_scalar(s, beta);
+        if (beta_h <= tol) break;
+        const int m = std::min(restart, s->opts.inner_max - iters);
+        gmres_init(ctx, s->gm_g.p, restart + 1, beta, s->scal.p + 5);
+        vk_scale_from(ctx, r, V, N, s->scal.p + 5, nullptr);
+        int used = 0;
+        double last_g = beta_h;
+        for (int j = 0; j < m; ++j) {
+            apply_newton_matrix(s, V + (long long)j * N, w);
+            vk_mdot<double>(ctx, V, N, j + 1, w, N, s->partials.p, s->h1.p, nullptr);
+            vk_gs_update<double>(ctx, V, N, j + 1, s->h1.p, w, N, nullptr);
+            vk_mdot<double>(ctx, V, N, j + 1, w, N, s->partials.p, s->h2.p, nullptr);
+            vk_gs_update<double>(ctx, V, N, j + 1, s->h2.p, w, N, nullptr);
+            vk_dot(ctx, w, w, N, s->partials.p, hn2, 0, nullptr);
+            gmres_givens(ctx, j, restart, s->gm_H.p, s->gm_cs.p, s->gm_sn.p, s->gm_g.p, s->h1.p, s->h2.p, hn2, rep);
+            SGK_CUDA_CHECK(cudaMemcpyAsync(s->hscal, rep, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            used = j + 1;
+            ++iters;
+            last_g = s->hscal[0];
+            if (s->hscal[0] <= tol || s->hscal[1] <= 1e-12 * s->hscal[2]) break;
+            vk_scale_from(ctx, w, V + (long long)(j + 1) * N, N, rep + 3, nullptr);
+        }
+        gmres_solve(ctx, used, restart, s->gm_H.p, s->gm_g.p, s->gm_y.p);
+        vk_basis_accumulate(ctx, V, N, used, s->gm_y.p, x, N);
+        if (last_g <= tol) break;
+    }
+}
+
+int newton(sgk_solver* s) {
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    const double dt2 = 0.5 * s->dt;
+    SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    vk_dot(ctx, s->W.p, s->W.p, N, s->partials.p, s->scal.p + 6, 1, nullptr);
+    const double wnorm = read_scalar(s, s->scal.p + 6);
+    const double stop = s->opts.tol * std::max(1.0, wnorm);
+    const double floor_accept = 1e-6 * std::max(1.0, wnorm);
+    double prev = INFINITY;
+    for (int it = 0; it <= s->opts.max_iter; ++it) {
+        evalF(s, s->U.p, s->Fv.p);
+        vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
+        vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
+        const double g = read_scalar(s, s->scal.p + 7);
+        s->stats.last_newton_residual = g;
+        if (!std::isfinite(g)) break;
+        if (g <= stop) return SGK_OK;
+        if (s->prec == SGK_MIXED && it >= 1 && g > 0.5 * prev && g <= floor_accept) return SGK_OK;
+        if (it == s->opts.max_iter) break;
+        prev = g;
+        int inner = 0;
+        if (s->nspecies == 1) cg_solve(s, s->G.p, s->cg_x.p, inner);
+        else gmres_solve_host(s, s->G.p, s->cg_x.p, inner);
+        s->stats.inner_iters += inner;
+        s->stats.newton_iters += 1;
+        vk_axpby(ctx, 1.0, s->U.p, 1.0, s->cg_x.p, s->U.p, N);
+    }
+    return SGK_ENEWTON;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ interface ---
+
+void solver_eval_reaction(sgk_solver* s, const double* U, double* F) {
+    SGK_REQUIRE(s->has_rx, SGK_EINVAL, "solver has no reaction term");
+    evalF(s, U, F);
+}
+
+void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw) {
+    SGK_REQUIRE(s->has_rx, SGK_EINVAL, "solver has no reaction term");
+    const long long n = s->n;
+    if (s->prec == SGK_FP64) {
+        QuadPtrs<double> p = qptrs<double>(s);
+        for (int sp = 0; sp < s->nspecies; ++sp) quad_forward<double>(s->ctx, s->Q, U + sp * n, p.unod[sp], p.tmp);
+        evalJ_T<double>(s, w, jw);
+    } else {
+        QuadPtrs<float> p = qptrs<float>(s);
+        for (int sp = 0; sp < s->nspecies; ++sp) {
+            vk_convert(s->ctx, U + sp * n, p.spin[sp], n);
+            quad_forward<float>(s->ctx, s->Q, p.spin[sp], p.unod[sp], p.tmp);
+        }
+        evalJ_T<float>(s, w, s->jw32.p);
+        vk_convert(s->ctx, s->jw32.p, jw, n * s->nspecies);
+    }
+    s->unod_valid = false;
+}
+
+void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) {
+    const sgk_op* op = s->ops[species];
+    const long long n = s->n;
+    if (s->prec == SGK_FP64) {
+        auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
+        krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
+    } else {
+        auto mv = [op](const float* x, float* y) { op_matvec<float>(op, x, y); };
+        krylov_expv_dev<float>(s->ctx, krylov_work<float>(s, species), mv, v, W, n, s->M, s->dt);
+    }
+    s->stats.krylov_calls += 1;
+}
+
+int solver_step(sgk_solver* s, int nsteps) {
+    sgk_ctx* ctx = s->ctx;
+    const long long n = s->n, N = n * s->nspecies;
+    const double dt2 = 0.5 * s->dt;
+    for (int step = 0; step < nsteps; ++step) {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (s->has_rx) {
+            evalF(s, s->U.p, s->Fv.p);
+            vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
+        }
+        const double* vsrc = s->has_rx ? s->vv.p : s->U.p;
+        for (int sp = 0; sp < s->nspecies; ++sp) solver_krylov_expv(s, sp, vsrc + sp * n, s->W.p + sp * n);
+        int rc = SGK_OK;
+        if (!s->has_rx) {
+            SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            rc = newton(s);
+        }
+        KrylovScalars ks[SGK_MAX_SPECIES];
+        SGK_CUDA_CHECK(cudaMemcpyAsync(ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+        SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (int sp = 0; sp < s->nspecies; ++sp) {
+            s->stats.krylov_breakdowns += ks[sp].breakdown;
+            s->stats.last_m_eff = ks[sp].m_eff;
+        }
+        if (rc != SGK_OK) {
+            SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            return rc;
+        }
+        s->stats.steps += 1;
+    }
+    return SGK_OK;
+}
+
+void solver_alloc(sgk_solver* s) {
+    const long long n = s->n, S = s->nspecies, N = n * S;
+    const int M = s->M;
+    s->U.alloc(N);
+    s->Uprev.alloc(N);
+    s->W.alloc(N);
+    s->vv.alloc(N);
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->U.p, 0, N * sizeof(double), s->ctx->stream));
+    if (s->prec == SGK_FP64) {
+        s->V64.alloc((M + 1) * n);
+        s->w64.alloc(n);
+    } else {
+        s->V32.alloc((M + 1) * n);
+        s->w32.alloc(n);
+    }
+    s->Hm.alloc((M + 1) * M);
+    s->h1.alloc(std::max(M, s->opts.gmres_restart) + 1);
+    s->h2.alloc(std::max(M, s->opts.gmres_restart) + 1);
+    s->ky.alloc(M + 1);
+    s->scal.alloc(16);
+    s->partials.alloc((size_t)reduction_blocks(s->ctx, N) * (std::max(M, s->opts.gmres_restart) + 1) + 16);
+    s->expm_ws.alloc(8 * (size_t)M * M);
+    s->ks.alloc(S);
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->Hm.p, 0, (M + 1) * M * sizeof(double), s->ctx->stream));
+    if (s->has_rx) {
+        s->Fv.alloc(N);
+        s->G.alloc(N);
+        s->cg_x.alloc(N);
+        s->cg_r.alloc(N);
+        s->cg_p.alloc(N);
+        s->cg_q.alloc(N);
+        const long long qsize = (2 * S + 1) * s->Q.full_size + 2 * S * n;
+        if (s->prec == SGK_FP64) {
+            s->q64.alloc(qsize);
+            s->jw64.alloc(N);
+        } else {
+            s->q32.alloc(qsize);
+            s->jw32.alloc(N);
+        }
+        if (S > 1) {
+            const int R = s->opts.gmres_restart;
+            s->gm_V.alloc((R + 1) * N);
+            s->gm_H.alloc((R + 1) * R);
+            s->gm_cs.alloc(R);
+            s->gm_sn.alloc(R);
+            s->gm_g.alloc(R + 1);
+            s->gm_y.alloc(R);
+            s->gm_report.alloc(4);
+        }
+    }
+    SGK_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void**>(&s->hscal), 16 * sizeof(double)));
+}
+
+sgk_solver::~sgk_solver() {
+    if (hscal) cudaFreeHost(hscal);
+}

@@ -1,0 +1,362 @@
+// One-time host construction of the 1D tables of the sparse-grid DG method:
+// Gauss-Legendre rules, Alpert multiwavelets, the change of basis T from the
+// 1D hierarchical basis of V_N^k to the finest-cell Legendre basis, and the
+// 1D SIPG matrix in the hierarchical basis (Section 2.1).  These run once per
+// index set / operator, before the time loop (Section 4: the 1D integrals are
+// computed once before the time evolution).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sgk_internal.h"
+
+typedef long double ld;
+
+namespace {
+
+// P_0..P_k and P_0'..P_k' at t by the three-term recurrence.
+void legendre_eval(int k, ld t, ld* P, ld* dP) {
+    P[0] = 1;
+    dP[0] = 0;
+    if (k >= 1) {
+        P[1] = t;
+        dP[1] = 1;
+    }
+    for (int r = 1; r < k; ++r) {
+        P[r + 1] = ((2 * r + 1) * t * P[r] - r * P[r - 1]) / (r + 1);
+        dP[r + 1] = dP[r - 1] + (2 * r + 1) * P[r];
+    }
+}
+
+void gauss_legendre_ld(int q, std::vector<ld>& x, std::vector<ld>& w) {
+    x.assign(q, 0);
+    w.assign(q, 0);
+    const ld pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < q; ++i) {
+        ld z = std::cos(pi * (i + 0.75L) / (q + 0.5L));
+        for (int it = 0; it < 100; ++it) {
+            ld p0 = 1, p1 = z;
+            for (int r = 1; r < q; ++r) {
+                ld p2 = ((2 * r + 1) * z * p1 - r * p0) / (r + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            ld pq = (q == 0) ? 1 : (q == 1 ? z : p1);
+            if (q == 1) p0 = 1;
+            ld dp = q * (z * pq - p0) / (z * z - 1);
+            ld dz = pq / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-19L) break;
+        }
+        ld p0 = 1, p1 = z;
+        for (int r = 1; r < q; ++r) {
+            ld p2 = ((2 * r + 1) * z * p1 - r * p0) / (r + 1);
+            p0 = p1;
+            p1 = p2;
+        }
+        ld pq = (q == 1) ? z : p1;
+        if (q == 1) p0 = 1;
+        ld dp = q * (z * pq - p0) / (z * z - 1);
+        x[q - 1 - i] = z;
+        w[q - 1 - i] = 2 / ((1 - z * z) * dp * dp);
+    }
+}
+
+// Value of the hierarchical function (level n, cell j, degree p) of V_N^k at
+// x = (cell + (xi+1)/2) h on the piece belonging to finest cell `cell`.
+ld hier_value(int N, int k, const std::vector<ld>& alp, int n, int j, int p, int cell, ld xi) {
+    std::vector<ld> P(k + 1), dP(k + 1);
+    ld h = std::ldexp((ld)1, -N);
+    ld x = (cell + (xi + 1) / 2) * h;
+    if (n == 0) {
+        legendre_eval(k, 2 * x - 1, P.data(), dP.data());
+        return std::sqrt((ld)(2 * p + 1)) * P[p];
+    }
+    int half = (cell >> (N - n)) & 1;
+    ld y = std::ldexp(x, n) - (2 * j + 1);
+    ld t = half == 0 ? 2 * y + 1 : 2 * y - 1;
+    legendre_eval(k, t, P.data(), dP.data());
+    ld v = 0;
+    for (int r = 0; r <= k; ++r) v += alp[p * 2 * (k + 1) + half * (k + 1) + r] * std::sqrt((ld)(2 * r + 1)) * P[r];
+    return std::ldexp(v, 0) * std::pow((ld)2, (ld)n / 2);
+}
+
+std::vector<ld> alpert_ld(int k) {
+    const int m = 2 * (k + 1);
+    const int nq = 2 * k + 6;
+    std::vector<ld> xi, w;
+    gauss_legendre_ld(nq, xi, w);
+    // moments of the piecewise Legendre basis: mom[i][b] = int y^i psi_b
+    std::vector<ld> mom((2 * k + 2) * m, 0);
+    std::vector<ld> P(k + 1), dP(k + 1);
+    for (int g = 0; g < nq; ++g) {
+        for (int half = 0; half < 2; ++half) {
+            ld y = half == 0 ? (xi[g] - 1) / 2 : (xi[g] + 1) / 2;
+            ld t = half == 0 ? 2 * y + 1 : 2 * y - 1;
+            legendre_eval(k, t, P.data(), dP.data());
+            ld yi = 1;
+            for (int i = 0; i < 2 * k + 2; ++i) {
+                for (int r = 0; r <= k; ++r)
+                    mom[i * m + half * (k + 1) + r] += w[g] / 2 * yi * std::sqrt((ld)(2 * r + 1)) * P[r];
+                yi *= y;
+            }
+        }
+    }
+    std::vector<ld> f((k + 1) * m, 0);
+    for (int p = k; p >= 0; --p) {
+        // constraints: moments 0..p+k and the wavelets already fixed
+        std::vector<std::vector<ld>> rows;
+        for (int i = 0; i <= p + k; ++i) rows.emplace_back(mom.begin() + i * m, mom.begin() + (i + 1) * m);
+        for (int pp = p + 1; pp <= k; ++pp) rows.emplace_back(f.begin() + pp * m, f.begin() + (pp + 1) * m);
+        // orthonormalise the constraint rows (modified Gram-Schmidt, twice)
+        std::vector<std::vector<ld>> Q;
+        for (auto r : rows) {
+            for (int pass = 0; pass < 2; ++pass)
+                for (auto& q : Q) {
+                    ld dot = 0;
+                    for (int b = 0; b < m; ++b) dot += q[b] * r[b];
+                    for (int b = 0; b < m; ++b) r[b] -= dot * q[b];
+                }
+            ld nrm = 0;
+            for (int b = 0; b < m; ++b) nrm += r[b] * r[b];
+            nrm = std::sqrt(nrm);
+            if (nrm > 1e-14L) {
+                for (int b = 0; b < m; ++b) r[b] /= nrm;
+                Q.push_back(r);
+            }
+        }
+        // the null direction: the unit vector with the largest remainder
+        std::vector<ld> best;
+        ld best_norm = -1;
+        for (int e = 0; e < m; ++e) {
+            std::vector<ld> v(m, 0);
+            v[e] = 1;
+            for (int pass = 0; pass < 2; ++pass)
+                for (auto& q : Q) {
+                    ld dot = 0;
+                    for (int b = 0; b < m; ++b) dot += q[b] * v[b];
+                    for (int b = 0; b < m; ++b) v[b] -= dot * q[b];
+                }
+            ld nrm = 0;
+            for (int b = 0; b < m; ++b) nrm += v[b] * v[b];
+            if (nrm > best_norm) {
+                best_norm = nrm;
+                best = v;
+            }
+        }
+        ld nrm = std::sqrt(best_norm);
+        for (int b = 0; b < m; ++b) best[b] /= nrm;
+        for (int r = k; r >= 0; --r) {
+            ld c = best[(k + 1) + r];
+            if (std::fabs(c) > 1e-8L) {
+                if (c < 0)
+                    for (int b = 0; b < m; ++b) best[b] = -best[b];
+                break;
+            }
+        }
+        std::copy(best.begin(), best.end(), f.begin() + p * m);
+    }
+    return f;
+}
+
+}  // namespace
+
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    std::vector<ld> xl, wl;
+    gauss_legendre_ld(q, xl, wl);
+    x.assign(xl.begin(), xl.end());
+    w.assign(wl.begin(), wl.end());
+}
+
+std::vector<double> alpert_coefficients(int k) {
+    std::vector<ld> f = alpert_ld(k);
+    return std::vector<double>(f.begin(), f.end());
+}
+
+void Csr::upload(cudaStream_t s) {
+    d_ptr.upload(ptr, s);
+    d_col.upload(col, s);
+    d_val.upload(val, s);
+    std::vector<float> vf(val.begin(), val.end());
+    d_valf.alloc(vf.size());
+    d_valf.upload(vf.data(), vf.size(), s);
+    // vf must outlive the async copy
+    SGK_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+void build_transform_tables(int N, int k, Tables1D& out) {
+    const int kp1 = k + 1;
+    const int ncell = 1 << N;
+    const int H = kp1 * ncell;
+    out.N = N;
+    out.k = k;
+    out.H = H;
+    std::vector<ld> alp = alpert_ld(k);
+    out.alpert.assign(alp.begin(), alp.end());
+    std::vector<ld> xi, w;
+    gauss_legendre_ld(kp1, xi, w);
+    const ld h = std::ldexp((ld)1, -N);
+    // Legendre basis of a finest cell at the Gauss points: h^{-1/2} sqrt(2r+1) P_r(xi)
+    std::vector<ld> Lg(kp1 * kp1), P(kp1), dP(kp1);
+    for (int g = 0; g < kp1; ++g) {
+        legendre_eval(k, xi[g], P.data(), dP.data());
+        for (int r = 0; r < kp1; ++r) Lg[g * kp1 + r] = std::sqrt((ld)(2 * r + 1)) * P[r] / std::sqrt(h);
+    }
+    Csr& T = out.T;
+    T.rows = T.cols = H;
+    T.ptr.assign(H + 1, 0);
+    T.col.clear();
+    T.val.clear();
+    for (int c = 0; c < ncell; ++c) {
+        for (int r = 0; r < kp1; ++r) {
+            for (int n = 0; n <= N; ++n) {
+                int j = n == 0 ? 0 : (c >> (N - n + 1));
+                for (int p = 0; p < kp1; ++p) {
+                    int a = level_offset(n, kp1) + j * kp1 + p;
+                    ld acc = 0;
+                    for (int g = 0; g < kp1; ++g)
+                        acc += h * w[g] / 2 * hier_value(N, k, alp, n, j, p, c, xi[g]) * Lg[g * kp1 + r];
+                    T.col.push_back(a);
+                    T.val.push_back((double)acc);
+                }
+            }
+            T.ptr[c * kp1 + r + 1] = (int)T.col.size();
+        }
+    }
+    // transpose (columns stay sorted because rows are visited in order)
+    Csr& Tt = out.Tt;
+    Tt.rows = Tt.cols = H;
+    Tt.ptr.assign(H + 1, 0);
+    for (int e = 0; e < (int)T.col.size(); ++e) Tt.ptr[T.col[e] + 1]++;
+    for (int a = 0; a < H; ++a) Tt.ptr[a + 1] += Tt.ptr[a];
+    Tt.col.assign(T.col.size(), 0);
+    Tt.val.assign(T.col.size(), 0);
+    std::vector<int> fill(Tt.ptr.begin(), Tt.ptr.end() - 1);
+    for (int y = 0; y < H; ++y)
+        for (int e = T.ptr[y]; e < T.ptr[y + 1]; ++e) {
+            int a = T.col[e];
+            Tt.col[fill[a]] = y;
+            Tt.val[fill[a]] = T.val[e];
+            fill[a]++;
+        }
+}
+
+std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma) {
+    // SIPG on the finest mesh in the cell-local orthonormal Legendre basis
+    // (closed form), then rotated: S = T^T S_L T.
+    const int k = tab.k, kp1 = k + 1, N = tab.N, H = tab.H;
+    const int nc = 1 << N;
+    const ld h = std::ldexp((ld)1, -N);
+    std::vector<ld> vr(kp1), vl(kp1), dr(kp1), dl(kp1), vol(kp1 * kp1, 0);
+    for (int r = 0; r < kp1; ++r) {
+        ld s = std::sqrt((ld)(2 * r + 1)) / std::sqrt(h);
+        ld sgn = (r % 2 == 0) ? 1 : -1;
+        vr[r] = s;
+        vl[r] = s * sgn;
+        dr[r] = (2 / h) * s * r * (r + 1) / 2;
+        dl[r] = -(2 / h) * s * sgn * r * (r + 1) / 2;
+    }
+    for (int a = 0; a < kp1; ++a)
+        for (int b = 0; b < kp1; ++b)
+            if ((a + b) % 2 == 0) {
+                int m = std::min(a, b);
+                vol[a * kp1 + b] = (2 / (h * h)) * std::sqrt((ld)(2 * a + 1)) * std::sqrt((ld)(2 * b + 1)) * m * (m + 1);
+            }
+    // S_L as a dense-row map: rows y, entries among 3 neighbouring cells
+    std::vector<std::vector<std::pair<int, ld>>> SL(H);
+    auto add = [&](int y, int y2, ld v) {
+        for (auto& e : SL[y])
+            if (e.first == y2) { e.second += v; return; }
+        SL[y].push_back({y2, v});
+    };
+    for (int c = 0; c < nc; ++c)
+        for (int a = 0; a < kp1; ++a)
+            for (int b = 0; b < kp1; ++b)
+                if (vol[a * kp1 + b] != 0) add(c * kp1 + a, c * kp1 + b, vol[a * kp1 + b]);
+    const int nfaces = bc == SGK_PERIODIC ? nc : nc + 1;
+    for (int f = 0; f < nfaces; ++f) {
+        std::vector<std::pair<int, ld>> J, G;
+        bool interior = bc == SGK_PERIODIC || (f > 0 && f < nc);
+        if (interior) {
+            int L = (f - 1 + nc) % nc, R = f % nc;
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({L * kp1 + r, vr[r]});
+                G.push_back({L * kp1 + r, dr[r] / 2});
+            }
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({R * kp1 + r, -vl[r]});
+                G.push_back({R * kp1 + r, dl[r] / 2});
+            }
+        } else if (f == 0) {
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({r, -vl[r]});
+                G.push_back({r, dl[r]});
+            }
+        } else {
+            int L = nc - 1;
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({L * kp1 + r, vr[r]});
+                G.push_back({L * kp1 + r, dr[r]});
+            }
+        }
+        // periodic with nc == 1: both traces belong to the same cell; merge
+        for (auto& a : J)
+            for (auto& b : J) add(a.first, b.first, (ld)sigma / h * a.second * b.second);
+        for (auto& a : G)
+            for (auto& b : J) {
+                add(a.first, b.first, -a.second * b.second);
+                add(b.first, a.first, -a.second * b.second);
+            }
+    }
+    // Z = S_L T (rows y), then S = T^T Z accumulated row by row
+    const Csr& T = tab.T;
+    const Csr& Tt = tab.Tt;
+    std::vector<std::vector<std::pair<int, ld>>> Z(H);
+    std::vector<ld> acc(H, 0);
+    std::vector<int> touched;
+    std::vector<char> mark(H, 0);
+    for (int y = 0; y < H; ++y) {
+        touched.clear();
+        for (auto& e : SL[y])
+            for (int q = T.ptr[e.first]; q < T.ptr[e.first + 1]; ++q) {
+                int b = T.col[q];
+                if (!mark[b]) { mark[b] = 1; touched.push_back(b); }
+                acc[b] += e.second * (ld)T.val[q];
+            }
+        for (int b : touched) {
+            Z[y].push_back({b, acc[b]});
+            acc[b] = 0;
+            mark[b] = 0;
+        }
+    }
+    std::vector<double> S((size_t)H * H, 0.0);
+    for (int a = 0; a < H; ++a) {
+        touched.clear();
+        for (int q = Tt.ptr[a]; q < Tt.ptr[a + 1]; ++q) {
+            int y = Tt.col[q];
+            ld t = Tt.val[q];
+            for (auto& e : Z[y]) {
+                if (!mark[e.first]) { mark[e.first] = 1; touched.push_back(e.first); }
+                acc[e.first] += t * e.second;
+            }
+        }
+        for (int b : touched) {
+            S[(size_t)a * H + b] = (double)acc[b];
+            acc[b] = 0;
+            mark[b] = 0;
+        }
+    }
+    // symmetrise (exact in exact arithmetic) and drop entries that vanish by
+    // orthogonality but carry rounding residue
+    for (int a = 0; a < H; ++a)
+        for (int b = a + 1; b < H; ++b) {
+            double m = 0.5 * (S[(size_t)a * H + b] + S[(size_t)b * H + a]);
+            S[(size_t)a * H + b] = S[(size_t)b * H + a] = m;
+        }
+    for (int a = 0; a < H; ++a)
+        for (int b = 0; b < H; ++b) {
+            double scale = std::sqrt(std::fabs(S[(size_t)a * H + a]) * std::fabs(S[(size_t)b * H + b]));
+            if (std::fabs(S[(size_t)a * H + b]) <= 1e-12 * scale) S[(size_t)a * H + b] = 0.0;
+        }
+    return S;
+}

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libsgkiif (C ABI in include/sgkiif.h).
+
+The module-level ``sgk_*`` callables are the C entry points with their
+argument types declared; the classes below only marshal arguments (device
+buffers are passed as raw pointers, e.g. ``tensor.data_ptr()``) and turn
+non-zero status codes into ``SgkError``.  Every computation runs in the CUDA
+library; if the library is not built, using it raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+SGK_OK, SGK_EINVAL, SGK_ENOMEM, SGK_EUNSUPPORTED, SGK_ENEWTON, SGK_ETIMEOUT, SGK_ECUDA = range(7)
+SGK_FP64, SGK_MIXED = 0, 1
+SGK_PERIODIC, SGK_DIRICHLET0 = 0, 1
+SGK_IIF2 = 2
+MAX_SPECIES = 4
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsgkiif.so")
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_i32_p = ctypes.POINTER(ctypes.c_int32)
+_c_i64_p = ctypes.POINTER(ctypes.c_int64)
+
+
+class sgk_reaction(ctypes.Structure):
+    _fields_ = [("nspecies", ctypes.c_int), ("nmono", ctypes.c_int), ("species", _c_int_p),
+                ("coef", _c_double_p), ("exps", _c_int_p)]
+
+
+class sgk_newton_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_max", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
+
+
+class sgk_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64),
+                ("krylov_calls", ctypes.c_int64), ("krylov_breakdowns", ctypes.c_int64),
+                ("last_m_eff", ctypes.c_int), ("last_newton_residual", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "sgk_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
+    "sgk_ctx_destroy": (ctypes.c_int, [_P]),
+    "sgk_last_error": (ctypes.c_char_p, [_P]),
+    "sgk_ctx_launch_count": (ctypes.c_int64, [_P]),
+    "sgk_ctx_profile": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "sgk_ctx_profile_read": (ctypes.c_int, [_P, _c_double_p, _c_i64_p]),
+    "sgk_index_build": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "sgk_index_destroy": (ctypes.c_int, [_P]),
+    "sgk_index_dof": (ctypes.c_int64, [_P]),
+    "sgk_index_ntuples": (ctypes.c_int64, [_P]),
+    "sgk_index_export": (ctypes.c_int, [_P, _c_i32_p, _c_i64_p, ctypes.c_int64]),
+    "sgk_index_lookup": (ctypes.c_int, [_P, _c_i32_p, ctypes.c_int64, _c_i64_p]),
+    "sgk_operator_assemble": (ctypes.c_int, [_P, _P, _c_double_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.POINTER(_P)]),
+    "sgk_operator_destroy": (ctypes.c_int, [_P]),
+    "sgk_operator_export_1d": (ctypes.c_int, [_P, _c_double_p, ctypes.c_int64]),
+    "sgk_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "sgk_project_separable": (ctypes.c_int, [_P, _P, ctypes.c_int, _c_double_p, _c_int_p, _c_int_p,
+                                             ctypes.c_double, _P]),
+    "sgk_solver_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(sgk_reaction),
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.POINTER(sgk_newton_opts), ctypes.POINTER(_P)]),
+    "sgk_solver_destroy": (ctypes.c_int, [_P]),
+    "sgk_solver_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "sgk_solver_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sgk_solver_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int]),
+    "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),
+    "sgk_reaction_eval": (ctypes.c_int, [_P, _P, _P]),
+    "sgk_jacobian_apply": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sgk_krylov_expv": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _c_int_p]),
+    "sgk_krylov_export": (ctypes.c_int, [_P, _c_double_p, _c_double_p, ctypes.c_int64]),
+    "sgk_expm_e1": (ctypes.c_int, [_P, ctypes.c_int, _c_double_p, ctypes.c_double, _c_double_p]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libsgkiif.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsgkiif.so is not built (run __graft_entry__.build()); no fallback exists")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+            globals()[name] = fn
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+class SgkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libsgkiif status %d: %s" % (code, msg))
+        self.code = code
+
+
+def _dptr(arr):
+    return arr.ctypes.data_as(_c_double_p)
+
+
+def _iptr(arr):
+    return arr.ctypes.data_as(_c_int_p)
+
+
+class Context:
+    def __init__(self, device=0, stream=None, precision=SGK_FP64):
+        load()
+        self.h = _P()
+        rc = sgk_ctx_create(ctypes.byref(self.h), int(device), stream, int(precision))
+        if rc:
+            raise SgkError(rc, "sgk_ctx_create failed")
+        self.precision = precision
+
+    def check(self, rc):
+        if rc:
+            raise SgkError(rc, sgk_last_error(self.h).decode())
+
+    @property
+    def launches(self):
+        return int(sgk_ctx_launch_count(self.h))
+
+    KERNEL_CLASSES = ("matvec", "to_finest", "from_finest", "cell_quadrature", "reductions", "expm", "vector")
+
+    def profile(self, mask):
+        self.check(sgk_ctx_profile(self.h, int(mask)))
+
+    def profile_read(self):
+        """{class: (milliseconds, launches)} since the previous read."""
+        ms = np.zeros(7)
+        n = np.zeros(7, dtype=np.int64)
+        self.check(sgk_ctx_profile_read(self.h, _dptr(ms), n.ctypes.data_as(_c_i64_p)))
+        return {c: (float(ms[i]), int(n[i])) for i, c in enumerate(self.KERNEL_CLASSES)}
+
+    def close(self):
+        if self.h:
+            sgk_ctx_destroy(self.h)
+            self.h = _P()
+
+    def expm_e1(self, X, tau):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        m = X.shape[0]
+        y = np.zeros(m)
+        self.check(sgk_expm_e1(self.h, m, _dptr(X), float(tau), _dptr(y)))
+        return y
+
+
+class IndexSet:
+    def __init__(self, ctx, d, n, k):
+        self.ctx, self.d, self.n, self.k = ctx, d, n, k
+        self.h = _P()
+        ctx.check(sgk_index_build(ctx.h, d, n, k, ctypes.byref(self.h)))
+        self.dof = int(sgk_index_dof(self.h))
+        self.ntuples = int(sgk_index_ntuples(self.h))
+
+    def export(self):
+        levels = np.zeros((self.ntuples, self.d), dtype=np.int32)
+        offsets = np.zeros(self.ntuples + 1, dtype=np.int64)
+        self.ctx.check(sgk_index_export(self.h, levels.ctypes.data_as(_c_i32_p),
+                                        offsets.ctypes.data_as(_c_i64_p), self.ntuples))
+        return levels, offsets
+
+    def lookup(self, levels):
+        levels = np.ascontiguousarray(levels, dtype=np.int32).reshape(-1, self.d)
+        out = np.zeros(levels.shape[0], dtype=np.int64)
+        self.ctx.check(sgk_index_lookup(self.h, levels.ctypes.data_as(_c_i32_p), levels.shape[0],
+                                        out.ctypes.data_as(_c_i64_p)))
+        return out
+
+    def project_separable(self, amp, wavenum, kind, const, out_ptr):
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        wavenum = np.ascontiguousarray(wavenum, dtype=np.int32).reshape(-1)
+        kind = np.ascontiguousarray(kind, dtype=np.int32).reshape(-1)
+        self.ctx.check(sgk_project_separable(self.ctx.h, self.h, len(amp), _dptr(amp), _iptr(wavenum),
+                                             _iptr(kind), float(const), out_ptr))
+
+    def close(self):
+        if self.h:
+            sgk_index_destroy(self.h)
+            self.h = _P()
+
+
+class Operator:
+    def __init__(self, ctx, idx, kappa, bc=SGK_PERIODIC, sigma=20.0):
+        self.ctx, self.idx = ctx, idx
+        kap = np.ascontiguousarray(kappa, dtype=np.float64)
+        self.h = _P()
+        ctx.check(sgk_operator_assemble(ctx.h, idx.h, _dptr(kap), int(bc), float(sigma), ctypes.byref(self.h)))
+        self.H = (idx.k + 1) << idx.n
+
+    def export_1d(self):
+        out = np.zeros((self.H, self.H))
+        self.ctx.check(sgk_operator_export_1d(self.h, _dptr(out), out.size))
+        return out
+
+    def matvec(self, x_ptr, y_ptr, precision=SGK_FP64):
+        self.ctx.check(sgk_matvec(self.h, x_ptr, y_ptr, int(precision)))
+
+    def close(self):
+        if self.h:
+            sgk_operator_destroy(self.h)
+            self.h = _P()
+
+
+def reaction_struct(terms, nspecies):
+    """terms: list per species of (coef, exponents) monomials."""
+    species, coef, exps = [], [], []
+    for s, mono in enumerate(terms):
+        for c, e in mono:
+            species.append(s)
+            coef.append(float(c))
+            exps.extend(int(v) for v in e)
+    keep = (np.array(species or [0], dtype=np.int32), np.array(coef or [0.0]),
+            np.array(exps or [0] * nspecies, dtype=np.int32))
+    st = sgk_reaction(nspecies, len(species), _iptr(keep[0]), _dptr(keep[1]), _iptr(keep[2]))
+    return st, keep
+
+
+class Solver:
+    def __init__(self, ctx, ops, reaction_terms, krylov_m, dt, opts=None):
+        self.ctx, self.ops = ctx, list(ops)
+        self.nspecies = len(self.ops)
+        self.dof = self.ops[0].idx.dof
+        arr = (_P * self.nspecies)(*[o.h for o in self.ops])
+        self._rx, self._keep = reaction_struct(reaction_terms, self.nspecies)
+        o = None
+        if opts:
+            o = sgk_newton_opts(opts.get("tol", 0.0), opts.get("max_iter", 0), opts.get("inner_tol", 0.0),
+                                opts.get("inner_max", 0), opts.get("gmres_restart", 0))
+        self.h = _P()
+        ctx.check(sgk_solver_create(ctx.h, self.nspecies, arr, ctypes.byref(self._rx), SGK_IIF2, int(krylov_m),
+                                    float(dt), ctypes.byref(o) if o else None, ctypes.byref(self.h)))
+
+    def set_state(self, species, coeffs=None, dev_ptr=None):
+        if dev_ptr is not None:
+            self.ctx.check(sgk_solver_set_state(self.h, species, dev_ptr, 1))
+        else:
+            c = np.ascontiguousarray(coeffs, dtype=np.float64)
+            assert c.size == self.dof
+            self.ctx.check(sgk_solver_set_state(self.h, species, c.ctypes.data, 0))
+
+    def get_state(self, species, dev_ptr=None):
+        if dev_ptr is not None:
+            self.ctx.check(sgk_solver_get_state(self.h, species, dev_ptr, self.dof, 1))
+            return None
+        out = np.zeros(self.dof)
+        self.ctx.check(sgk_solver_get_state(self.h, species, out.ctypes.data, self.dof, 0))
+        return out
+
+    def step(self, nsteps=1):
+        self.ctx.check(sgk_solver_step(self.h, int(nsteps)))
+
+    def stats(self):
+        st = sgk_stats()
+        self.ctx.check(sgk_solver_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in sgk_stats._fields_}
+
+    def reaction_eval(self, u_ptr, f_ptr):
+        self.ctx.check(sgk_reaction_eval(self.h, u_ptr, f_ptr))
+
+    def jacobian_apply(self, u_ptr, w_ptr, jw_ptr):
+        self.ctx.check(sgk_jacobian_apply(self.h, u_ptr, w_ptr, jw_ptr))
+
+    def krylov_expv(self, species, v_ptr, w_ptr):
+        m = ctypes.c_int(0)
+        self.ctx.check(sgk_krylov_expv(self.h, species, v_ptr, w_ptr, ctypes.byref(m)))
+        return m.value
+
+    def krylov_export(self, M):
+        H = np.zeros((M + 1, M))
+        V = np.zeros((M + 1, self.dof))
+        self.ctx.check(sgk_krylov_export(self.h, _dptr(H), _dptr(V), V.size))
+        return H, V
+
+    def close(self):
+        if self.h:
+            sgk_solver_destroy(self.h)
+            self.h = _P()

@@ -1,0 +1,391 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (relative, coefficient 2-norm unless stated):
+  * index set and level hash: bit-exact;
+  * FP64 path: 1D operator, matvec, projection, expm, reaction term and
+    Jacobian <= 1e-12 (pure FP64 arithmetic in different orders);
+    Krylov exponential and full IIF2 steps <= 1e-10 (Newton and inner
+    solvers stop at 1e-12 / 1e-13 on both sides);
+  * mixed path (FP32 matvec / reaction passes, FP64 reductions): <= 1e-6
+    for steps; component checks carry FP32 bounds stated in each test.
+Sizes span several work tiles and ragged fiber lengths; the 3D cubic
+workload at level 6 (the benchmarked configuration) is compared with a
+stored oracle step (tests/golden/cubic3d_step1.npz, written by
+tests/golden/make_cubic3d_step.py) and, for the reaction term and its
+Jacobian, with the oracle's full vectors.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.iif import IIF2Solver  # noqa: E402
+from oracle.index_set import IndexSet as OIndex  # noqa: E402
+from oracle.krylov import expm_pade13, krylov_expv  # noqa: E402
+from oracle.operator import DIRICHLET0, PERIODIC, sipg_1d, sparse_matvec  # noqa: E402
+from oracle.projection import project_separable  # noqa: E402
+from oracle.reaction import Reaction  # noqa: E402
+from paper_1810_11111_gb300 import sgkiif, workloads  # noqa: E402
+from paper_1810_11111_gb300.runner import Problem  # noqa: E402
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DEV = torch.device("cuda", 0)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctx64():
+    c = sgkiif.Context(0, torch.cuda.current_stream().cuda_stream, sgkiif.SGK_FP64)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx32():
+    c = sgkiif.Context(0, torch.cuda.current_stream().cuda_stream, sgkiif.SGK_MIXED)
+    yield c
+    c.close()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device=DEV).contiguous()
+
+
+# ------------------------------------------------------------ index set ---
+
+@pytest.mark.parametrize("d,n,k", [(1, 5, 1), (2, 4, 1), (3, 6, 2), (4, 5, 2), (2, 8, 2), (6, 3, 1), (3, 0, 3)])
+def test_index_set_bit_exact(ctx64, d, n, k):
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    ref = OIndex(d, n, k)
+    levels, offsets = idx.export()
+    assert idx.dof == ref.dof and idx.ntuples == len(ref.tuples)
+    assert np.array_equal(levels, ref.levels_array())
+    assert np.array_equal(offsets, ref.offsets)
+    idx.close()
+
+
+def test_level_hash_bit_exact(ctx64):
+    d, n = 4, 6
+    idx = sgkiif.IndexSet(ctx64, d, n, 1)
+    ref = OIndex(d, n, 1)
+    rng = np.random.default_rng(0)
+    q = rng.integers(-1, n + 2, size=(500, d)).astype(np.int32)
+    q[:100] = ref.levels_array()[rng.integers(0, len(ref.tuples), 100)]
+    got = idx.lookup(q)
+    want = np.array([ref.rank.get(tuple(int(v) for v in row), -1) for row in q])
+    assert np.array_equal(got, want)
+    idx.close()
+
+
+# ------------------------------------------------------------- operator ---
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("bc", [PERIODIC, DIRICHLET0])
+def test_operator_1d_matches_oracle(ctx64, k, bc):
+    n = 5
+    idx = sgkiif.IndexSet(ctx64, 1, n, k)
+    op = sgkiif.Operator(ctx64, idx, [1.0], bc)
+    S = op.export_1d()
+    R = sipg_1d(n, k, bc)
+    assert np.abs(S - R).max() <= 1e-12 * np.abs(R).max()
+    op.close()
+    idx.close()
+
+
+MATVEC_CASES = [(2, 4, 1, PERIODIC), (3, 6, 2, PERIODIC), (2, 7, 3, DIRICHLET0), (4, 4, 1, PERIODIC),
+                (3, 5, 1, DIRICHLET0), (1, 6, 2, PERIODIC)]
+
+
+@pytest.mark.parametrize("d,n,k,bc", MATVEC_CASES)
+def test_matvec_fp64(ctx64, d, n, k, bc):
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    kap = [1.0, 0.5, 0.1, 0.7][:d]
+    op = sgkiif.Operator(ctx64, idx, kap, bc)
+    ref = OIndex(d, n, k)
+    x = np.random.default_rng(d * 100 + n).standard_normal(idx.dof)
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    op.matvec(xd.data_ptr(), yd.data_ptr(), sgkiif.SGK_FP64)
+    torch.cuda.synchronize()
+    want = sparse_matvec(ref, sipg_1d(n, k, bc), kap, x)
+    assert rel(yd.cpu().numpy(), want) <= 1e-12
+    op.close()
+    idx.close()
+
+
+@pytest.mark.parametrize("d,n,k,bc", MATVEC_CASES[:3])
+def test_matvec_fp32(ctx64, d, n, k, bc):
+    # FP32 storage and accumulation: |error| <= c u_32 |A| |x| per row; for
+    # these operators that is below 1e-5 of ||A x||
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    kap = [1.0, 0.5, 0.1, 0.7][:d]
+    op = sgkiif.Operator(ctx64, idx, kap, bc)
+    ref = OIndex(d, n, k)
+    x = np.random.default_rng(5).standard_normal(idx.dof)
+    xd = dev(x, torch.float32)
+    yd = torch.empty_like(xd)
+    op.matvec(xd.data_ptr(), yd.data_ptr(), sgkiif.SGK_MIXED)
+    torch.cuda.synchronize()
+    want = sparse_matvec(ref, sipg_1d(n, k, bc), kap, x.astype(np.float32).astype(np.float64))
+    assert rel(yd.double().cpu().numpy(), want) <= 1e-5
+    op.close()
+    idx.close()
+
+
+# ----------------------------------------------------------- projection ---
+
+@pytest.mark.parametrize("d,n,k", [(2, 4, 1), (3, 6, 2), (4, 3, 3)])
+def test_projection(ctx64, d, n, k):
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    rng = np.random.default_rng(11)
+    amp, wn, kind = workloads.fourier_modes(rng, d)
+    out = torch.empty(idx.dof, dtype=torch.float64, device=DEV)
+    idx.project_separable(amp, wn, kind, 0.3, out.data_ptr())
+    want = project_separable(OIndex(d, n, k), amp, wn, kind, 0.3)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-13 * max(1.0, np.abs(want).max())
+    idx.close()
+
+
+# ----------------------------------------------------------------- expm ---
+
+@pytest.mark.parametrize("scale", [1e-3, 1.0, 30.0, 3000.0])
+def test_expm_e1(ctx64, scale):
+    rng = np.random.default_rng(int(scale * 7) % 1000)
+    X = rng.standard_normal((17, 17)) * scale / 17
+    y = ctx64.expm_e1(X, 1.0)
+    want = expm_pade13(X)[:, 0]
+    assert np.abs(y - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+
+
+def test_expm_e1_stiff_symmetric(ctx64):
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    X = (Q * -np.logspace(-1, 4, 30)) @ Q.T
+    y = ctx64.expm_e1(X, 0.5)
+    want = expm_pade13(0.5 * X)[:, 0]
+    assert np.abs(y - want).max() <= 1e-11
+
+
+# --------------------------------------------------------------- krylov ---
+
+def _krylov_problem(ctx, d, n, k, M, reaction=None):
+    cfg = dict(d=d, n=n, k=k, kappas=[[1.0, 0.5, 0.1, 0.7][:d]], reaction=reaction or [[]], M=M, dt=0.005,
+               init=[dict(amp=np.array([1.0]), wavenum=np.ones((1, d), np.int32), kind=np.zeros((1, d), np.int32))])
+    return cfg
+
+
+@pytest.mark.parametrize("d,n,k,M", [(2, 4, 1, 20), (3, 4, 2, 30), (2, 6, 1, 40)])
+def test_krylov_expv_fp64(ctx64, d, n, k, M):
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    kap = [1.0, 0.5, 0.1][:d]
+    op = sgkiif.Operator(ctx64, idx, kap)
+    sol = sgkiif.Solver(ctx64, [op], [[]], M, 0.01)
+    v = np.random.default_rng(2).standard_normal(idx.dof)
+    vd = dev(v)
+    wd = torch.empty_like(vd)
+    m_eff = sol.krylov_expv(0, vd.data_ptr(), wd.data_ptr())
+    ref = OIndex(d, n, k)
+    S = sipg_1d(n, k)
+    want, m_ref = krylov_expv(lambda x: sparse_matvec(ref, S, kap, x), v, 0.01, M)
+    assert m_eff == m_ref
+    assert rel(wd.cpu().numpy(), want) <= 1e-10
+    sol.close()
+    op.close()
+    idx.close()
+
+
+def test_krylov_breakdown_constant_mode(ctx64):
+    idx = sgkiif.IndexSet(ctx64, 3, 3, 2)
+    op = sgkiif.Operator(ctx64, idx, [1.0, 1.0, 1.0])
+    sol = sgkiif.Solver(ctx64, [op], [[]], 20, 0.1)
+    v = np.zeros(idx.dof)
+    v[0] = 2.5
+    vd = dev(v)
+    wd = torch.empty_like(vd)
+    assert sol.krylov_expv(0, vd.data_ptr(), wd.data_ptr()) == 1
+    assert np.abs(wd.cpu().numpy() - v).max() < 1e-12
+    z = torch.zeros_like(vd)
+    assert sol.krylov_expv(0, z.data_ptr(), wd.data_ptr()) == 0
+    assert float(wd.abs().max()) == 0.0
+    sol.close()
+    op.close()
+    idx.close()
+
+
+# ------------------------------------------------------------- reaction ---
+
+RX_CASES = [
+    (2, 4, 1, workloads.reaction_terms(workloads.CUBIC, 100.0)),
+    (3, 3, 2, workloads.reaction_terms(workloads.CUBIC, 37.0)),
+    (2, 3, 2, workloads.reaction_terms(workloads.SCHNAKENBERG)),
+    (1, 6, 3, [[(2.0, (2,)), (-1.0, (1,)), (0.5, (0,))]]),
+]
+
+
+@pytest.mark.parametrize("d,n,k,rx", RX_CASES)
+def test_reaction_and_jacobian_fp64(ctx64, d, n, k, rx):
+    S = len(rx)
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    ops = [sgkiif.Operator(ctx64, idx, [1.0] * d) for _ in range(S)]
+    sol = sgkiif.Solver(ctx64, ops, rx, 10, 0.01)
+    rng = np.random.default_rng(4)
+    U = [(1.0 if s == 0 else 0.9) * (np.arange(idx.dof) == 0) + 0.2 * rng.standard_normal(idx.dof)
+         for s in range(S)]
+    W = [rng.standard_normal(idx.dof) for _ in range(S)]
+    Ud, Wd = dev(np.concatenate(U)), dev(np.concatenate(W))
+    Fd, Jd = torch.empty_like(Ud), torch.empty_like(Ud)
+    sol.reaction_eval(Ud.data_ptr(), Fd.data_ptr())
+    sol.jacobian_apply(Ud.data_ptr(), Wd.data_ptr(), Jd.data_ptr())
+    torch.cuda.synchronize()
+    R = Reaction(OIndex(d, n, k), rx)
+    F, J = np.concatenate(R.F(U)), np.concatenate(R.J(U, W))
+    assert rel(Fd.cpu().numpy(), F) <= 1e-12
+    assert rel(Jd.cpu().numpy(), J) <= 1e-12
+    sol.close()
+    for o in ops:
+        o.close()
+    idx.close()
+
+
+def test_reaction_fp32(ctx32):
+    d, n, k = 3, 3, 2
+    rx = workloads.reaction_terms(workloads.CUBIC, 100.0)
+    idx = sgkiif.IndexSet(ctx32, d, n, k)
+    op = sgkiif.Operator(ctx32, idx, [1.0] * d)
+    sol = sgkiif.Solver(ctx32, [op], rx, 10, 0.01)
+    U = 0.3 * np.random.default_rng(6).standard_normal(idx.dof)
+    Ud = dev(U)
+    Fd = torch.empty_like(Ud)
+    sol.reaction_eval(Ud.data_ptr(), Fd.data_ptr())
+    torch.cuda.synchronize()
+    F = Reaction(OIndex(d, n, k), rx).F([U])[0]
+    assert rel(Fd.cpu().numpy(), F) <= 1e-5
+    sol.close()
+    op.close()
+    idx.close()
+
+
+# ------------------------------------------------------------ IIF steps ---
+
+def _oracle_run(cfg, U0, nsteps, bc=PERIODIC):
+    idx = OIndex(cfg["d"], cfg["n"], cfg["k"])
+    sol = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"], bc), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"])
+    return sol.run(U0, nsteps), sol.stats
+
+
+STEP_CASES = [
+    ("heat2d", workloads.heat2d(), 10),
+    ("cubic3d_small", workloads.cubic3d(n=3, k=2), 3),
+    ("schnak2d_small", workloads.schnak2d(n=4, k=1), 3),
+    ("cubic2d_k3", dict(workloads.cubic3d(n=4, k=3), d=2, kappas=[[1.0, 0.3]],
+                        init=[dict(amp=np.array([0.7, -0.4]), wavenum=np.array([[1, 2], [3, 1]], np.int32),
+                                   kind=np.array([[0, 1], [1, 0]], np.int32), const=0.1)]), 2),
+]
+
+
+@pytest.mark.parametrize("name,cfg,nsteps", STEP_CASES)
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_iif2_steps_match_oracle(name, cfg, nsteps, precision):
+    prob = Problem(cfg, precision)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(nsteps)
+    got = prob.state()
+    want, st = _oracle_run(cfg, U0, nsteps)
+    tol = 1e-10 if precision == sgkiif.SGK_FP64 else 1e-6
+    for s in range(len(want)):
+        assert rel(got[s], want[s]) <= tol, (name, s, rel(got[s], want[s]))
+    stats = prob.solver.stats()
+    assert stats["steps"] == nsteps
+    prob.close()
+
+
+def test_dirichlet_heat_steps():
+    cfg = dict(workloads.heat2d(), n=4, k=2)
+    prob = Problem(cfg, sgkiif.SGK_FP64, bc=sgkiif.SGK_DIRICHLET0)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(3)
+    want, _ = _oracle_run(cfg, U0, 3, DIRICHLET0)
+    assert rel(prob.state()[0], want[0]) <= 1e-10
+    prob.close()
+
+
+# ------------------------------------------ full-size benchmark workload ---
+
+def _golden():
+    path = os.path.join(GOLDEN, "cubic3d_step1.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden step not generated")
+    return np.load(path)
+
+
+@pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-10), (sgkiif.SGK_MIXED, 1e-6)])
+def test_cubic3d_full_size_step(precision, tol):
+    g = _golden()
+    prob = Problem(workloads.cubic3d(), precision)
+    assert np.abs(prob.U0[0].cpu().numpy() - g["U0"]).max() <= 1e-13
+    prob.solver.set_state(0, g["U0"])
+    prob.solver.step(1)
+    assert rel(prob.state()[0], g["U1"]) <= tol
+    prob.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-12), (sgkiif.SGK_MIXED, 1e-5)])
+def test_cubic3d_full_size_reaction_and_jacobian(precision, tol):
+    # the oracle's reaction pass at level 6 takes seconds, so the whole vector
+    # is compared (F and J at the stored initial state)
+    cfg = workloads.cubic3d()
+    g = _golden()
+    d, n, k = cfg["d"], cfg["n"], cfg["k"]
+    ctx = sgkiif.Context(0, torch.cuda.current_stream().cuda_stream, precision)
+    idx = sgkiif.IndexSet(ctx, d, n, k)
+    op = sgkiif.Operator(ctx, idx, cfg["kappas"][0])
+    sol = sgkiif.Solver(ctx, [op], cfg["reaction"], cfg["M"], cfg["dt"])
+    w = np.random.default_rng(9).standard_normal(idx.dof)
+    Ud, Wd = dev(g["U0"]), dev(w)
+    Fd, Jd = torch.empty_like(Ud), torch.empty_like(Ud)
+    sol.reaction_eval(Ud.data_ptr(), Fd.data_ptr())
+    sol.jacobian_apply(Ud.data_ptr(), Wd.data_ptr(), Jd.data_ptr())
+    torch.cuda.synchronize()
+    R = Reaction(OIndex(d, n, k), cfg["reaction"])
+    assert rel(Fd.cpu().numpy(), R.F([g["U0"]])[0]) <= tol
+    assert rel(Jd.cpu().numpy(), R.J([g["U0"]], [w])[0]) <= tol
+    sol.close()
+    op.close()
+    idx.close()
+    ctx.close()
+
+
+# ---------------------------------------------------------- error paths ---
+
+def test_invalid_arguments_are_rejected(ctx64):
+    h = sgkiif._P()
+    assert sgkiif.sgk_index_build(ctx64.h, 0, 3, 1, sgkiif.ctypes.byref(h)) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_index_build(ctx64.h, 3, 3, 4, sgkiif.ctypes.byref(h)) == sgkiif.SGK_EINVAL
+    assert b"k must be" in sgkiif.sgk_last_error(ctx64.h)
+    idx = sgkiif.IndexSet(ctx64, 2, 3, 1)
+    bad = np.array([1.0, -1.0])
+    assert sgkiif.sgk_operator_assemble(ctx64.h, idx.h, bad.ctypes.data_as(sgkiif._c_double_p), 0, 20.0,
+                                        sgkiif.ctypes.byref(h)) == sgkiif.SGK_EINVAL
+    idx.close()
+
+
+def test_newton_failure_rolls_back():
+    cfg = dict(workloads.cubic3d(n=3, k=1), opts={"max_iter": 1, "tol": 1e-15})
+    prob = Problem(cfg, sgkiif.SGK_FP64)
+    prob.reset()
+    before = prob.state()[0]
+    with pytest.raises(sgkiif.SgkError) as ei:
+        prob.solver.step(1)
+    assert ei.value.code == sgkiif.SGK_ENEWTON
+    assert np.array_equal(prob.state()[0], before)
+    prob.close()
