@@ -155,17 +155,21 @@ def native(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    # warm-up with every kernel class timed, to find the dominant one
-    prob.ctx.profile(0x7F)
+    # warm-up A: one step with every kernel class event-timed (individual
+    # launches) to find the dominant class; warm-up B: W steps as timed below
+    # (CUDA graphs are captured on first use)
+    prob.ctx.profile(0xFF)
+    prob.reset()
+    prob.solver.step(1)
+    warm = prob.ctx.profile_read()
+    prob.ctx.profile(0)
+    dominant = max(warm, key=lambda c: warm[c][0])
+    dom_bit = sgkiif.Context.KERNEL_CLASSES.index(dominant)
     prob.reset()
     for _ in range(args.warmup):
         prob.solver.step(1)
-    warm = prob.ctx.profile_read()
-    dominant = max(warm, key=lambda c: warm[c][0])
-    dom_bit = sgkiif.Context.KERNEL_CLASSES.index(dominant)
 
     # timed region: device time of each step, L2 flushed before each
-    prob.ctx.profile(1 << dom_bit)
     prob.reset()
     st0 = prob.solver.stats()
     barrier()
@@ -188,10 +192,27 @@ def native(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     launches = prob.ctx.launches - launches0
-    kprof = prob.ctx.profile_read()
-    prob.ctx.profile(0)
     st1 = prob.solver.stats()
     final = prob.state()
+
+    # the same K steps again with the dominant kernel class event-timed; kernel
+    # timing runs the graph-captured sequences as individual launches, so this
+    # pass is kept out of the headline number
+    prob.ctx.profile(1 << dom_bit)
+    prob.reset()
+    ps0 = prob.solver.stats()
+    barrier()
+    prof_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0.record(stream)
+        prob.solver.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        prof_ms += e0.elapsed_time(e1)
+    kprof = prob.ctx.profile_read()
+    prob.ctx.profile(0)
+    ps1 = prob.solver.stats()
 
     # accuracy against the FP64 GPU path (itself parity-tested against the oracle)
     acc = None
@@ -239,17 +260,23 @@ def native(args, rank, world, local_rank):
     # roofline of the dominant kernel class: algorithmic bytes per launch over
     # its event-timed average launch time in the timed region
     peaks, peak_kind = measured_peaks()
-    nF = args.steps * 1 + (st1["newton_iters"] - st0["newton_iters"]) + args.steps  # predictor + residuals
-    nJ = st1["inner_iters"] - st0["inner_iters"]
+    nF = args.steps * 1 + (ps1["newton_iters"] - ps0["newton_iters"]) + args.steps  # predictor + residuals
+    nJ = ps1["inner_iters"] - ps0["inner_iters"]
     sizes = layout_sizes(cfg["d"], cfg["n"], cfg["k"])
     full = sizes[-1]
     ms, nl = kprof[dominant]
+    # per pass of the reaction term: the fused last-direction (pencil) kernel
+    # reads R_{d-1}(U) (and R_{d-1}(w) for a Jacobian product) and writes
+    # G_{d-1}; the fiber transforms of directions 0..d-2 read R_i and write
+    # R_{i+1} (and the transpose); the Krylov matvec (FP64 in both modes)
+    # reads x and writes y
     if dominant == "cell_quadrature":
-        algo = (nF * 2 * S * full + nJ * 3 * S * full) * elem
+        last = sizes[cfg["d"] - 1]
+        algo = (nF * 2 * S * last + nJ * 3 * S * last) * elem
     elif dominant in ("to_finest", "from_finest"):
-        algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(cfg["d"])) * elem
+        algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(cfg["d"] - 1)) * elem
     elif dominant == "matvec":
-        algo = (nl / cfg["d"]) * 2 * dof * elem
+        algo = (nl / cfg["d"]) * 2 * dof * 8
     else:
         algo = None
     roofline = None
@@ -260,7 +287,9 @@ def native(args, rank, world, local_rank):
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": per_launch,
                     "avg_launch_us": ms / nl * 1e3, "launches": nl,
-                    "share_of_step_time": ms / total_ms if world == 1 else None}
+                    "share_of_profiled_step_time": ms / prof_ms,
+                    "timing": "CUDA events around each launch of the class, on the library stream, over a "
+                              "second pass of the same timed steps with graph replay off"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -272,6 +301,7 @@ def native(args, rank, world, local_rank):
            "rel_l2_vs_fp64": acc,
            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
            "host_wall_s": wall,
+           "profiled_pass_ms_per_step": prof_ms / args.steps,
            "solver": {"newton_iters": st1["newton_iters"] - st0["newton_iters"],
                       "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
            "kernel_ms_warmup": {c: round(v[0], 3) for c, v in warm.items()}}

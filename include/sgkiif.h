@@ -76,7 +76,10 @@ typedef struct sgk_solver sgk_solver;
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
- * (a cudaStream_t, or NULL for the default stream).  precision is SGK_FP64 or
+ * (a cudaStream_t; NULL makes the library create its own blocking stream,
+ * which stays ordered with the legacy default stream).  Repeated sequences
+ * (Krylov exponential, CG iteration, residual) are captured into CUDA graphs
+ * on this stream, so it must not be the legacy default stream itself.  precision is SGK_FP64 or
  * SGK_MIXED and selects the arithmetic of solvers created on this context.
  * Errors: SGK_EINVAL (null out, bad precision), SGK_ECUDA (no such device). */
 int sgk_ctx_create(sgk_ctx** out, int device, void* cuda_stream, int precision);
@@ -90,9 +93,12 @@ int64_t sgk_ctx_launch_count(const sgk_ctx* ctx);
  * on the context's stream.  Classes: 0 SIPG matvec, 1 change of basis to the
  * finest grid, 2 its transpose, 3 cell quadrature of the reaction term,
  * 4 inner products and Gram-Schmidt passes, 5 exp(tau H) e_1, 6 other vector
- * kernels.  mask = 0 disables timing. */
+ * kernels, 7 a whole Krylov exponential replayed as one CUDA graph.  While
+ * timing is enabled, sequences that are normally replayed as CUDA graphs run
+ * as individual launches so that each kernel can be timed.  mask = 0
+ * disables timing. */
 int sgk_ctx_profile(sgk_ctx* ctx, unsigned mask);
-/* Sum of event-timed milliseconds and launch counts per class (arrays of 7)
+/* Sum of event-timed milliseconds and launch counts per class (arrays of 8)
  * since the previous read; synchronises the stream and resets the sums. */
 int sgk_ctx_profile_read(sgk_ctx* ctx, double* ms, int64_t* launches);
 

@@ -2,9 +2,11 @@
 // entry point catches errors and turns them into a status code; the message
 // is kept on the context.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
+#include "sgk_pencil.h"
 #include "sgk_solver.h"
 
 void check_launch(const char* what) {
@@ -24,7 +26,7 @@ static cudaEvent_t take_event(sgk_ctx* c) {
 }
 
 KTimer::KTimer(sgk_ctx* c, int k) : ctx(c), kc(k) {
-    if (ctx->prof_mask & (1u << kc)) {
+    if (!ctx->capturing && (ctx->prof_mask & (1u << kc))) {
         a = take_event(ctx);
         b = take_event(ctx);
         cudaEventRecord(a, ctx->stream);
@@ -44,6 +46,7 @@ sgk_ctx::~sgk_ctx() {
         cudaEventDestroy(p.second.second);
     }
     for (auto e : ev_pool) cudaEventDestroy(e);
+    if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
 void build_index_on_device(sgk_index* idx);
@@ -99,6 +102,16 @@ int sgk_ctx_create(sgk_ctx** out, int device, void* cuda_stream, int precision) 
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)optin;
+    if (!c->stream) {
+        // a blocking stream: ordered with the legacy default stream, and
+        // capturable into CUDA graphs (the legacy stream itself is not)
+        if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            delete c;
+            return SGK_ECUDA;
+        }
+        c->own_stream = true;
+    }
     *out = c;
     return SGK_OK;
 }
@@ -335,6 +348,7 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
             }
         }
         s->has_rx = s->rx.nmono > 0;
+        s->use_graphs = std::getenv("SGK_NO_GRAPHS") == nullptr;
         const bool fp64 = s->prec == SGK_FP64;
         s->opts.tol = fp64 ? 1e-12 : 1e-10;
         s->opts.max_iter = 50;
@@ -354,6 +368,7 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
             const int q = std::max(1, (p * k + k + 1 + 1) / 2);
             SGK_REQUIRE(q <= 8, SGK_EUNSUPPORTED, "reaction degree too high for the quadrature tables");
             quad_build(s->Q, idx, q, nspecies, true);
+            s->Q.fused = pencil_supported(idx->d, idx->k + 1, q, nspecies) && std::getenv("SGK_NO_FUSED") == nullptr;
             const size_t elem = fp64 ? 8 : 4;
             const double need = (double)((2 * nspecies + 1) * s->Q.full_size) * elem;
             size_t free_b = 0, total_b = 0;
@@ -466,16 +481,8 @@ int sgk_krylov_export(const sgk_solver* s, double* H, double* V, int64_t cap_V) 
                                            s->ctx->stream));
         if (V) {
             SGK_REQUIRE(cap_V >= (M + 1) * n, SGK_EINVAL, "buffer too small for the basis");
-            if (s->prec == SGK_FP64) {
-                SGK_CUDA_CHECK(cudaMemcpyAsync(V, s->V64.p, (size_t)(M + 1) * n * sizeof(double),
-                                               cudaMemcpyDeviceToHost, s->ctx->stream));
-            } else {
-                std::vector<float> tmp((M + 1) * n);
-                SGK_CUDA_CHECK(cudaMemcpyAsync(tmp.data(), s->V32.p, tmp.size() * sizeof(float),
-                                               cudaMemcpyDeviceToHost, s->ctx->stream));
-                SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
-                for (size_t i = 0; i < tmp.size(); ++i) V[i] = tmp[i];
-            }
+            SGK_CUDA_CHECK(cudaMemcpyAsync(V, s->V64.p, (size_t)(M + 1) * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                           s->ctx->stream));
         }
         SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
         return SGK_OK;

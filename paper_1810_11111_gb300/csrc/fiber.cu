@@ -56,7 +56,6 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
         __syncthreads();
         const int F = kp1 << (sg.nlev - 1);
         const int src_len = MODE == FIBER_BWD ? H : F;
-        const int dst_len = MODE == FIBER_FWD ? H : F;
         const int lim = MODE == FIBER_BWD ? H : F;
         const int I = sg.I, nc = item.ncols, st = item.stride;
         const bool posfast = I < 4;
@@ -76,15 +75,17 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
             tile[pos * st + c] = src[a];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < dst_len * nc; e += blockDim.x) {
+        const int nr = item.nrows;
+        for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
             int pos, c;
             if (posfast) {
-                c = e / dst_len;
-                pos = e - c * dst_len;
+                c = e / nr;
+                pos = e - c * nr;
             } else {
                 pos = e / nc;
                 c = e - pos * nc;
             }
+            pos += item.row0;
             T acc = T(0);
             const int q1 = rp[pos + 1];
             for (int q = rp[pos]; q < q1; ++q) {
@@ -171,9 +172,17 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
             it.col0 = (int)c0;
             it.ncols = (int)std::min<long long>(maxc, cols - c0);
             it.stride = it.ncols | 1;
-            validate_item(g, it, kp1, H, mode, src_size, dst_size);
-            items.push_back(it);
-            cost.push_back((long long)std::max(src_len, dst_len) * it.ncols);
+            // split the output rows so that one item computes about 1024
+            // outputs (long fibers with few columns would otherwise serialise
+            // on one SM); every split item stages the whole source fiber
+            const int rows_per = std::max(1, std::min(dst_len, 1024 / it.ncols));
+            for (int r0 = 0; r0 < dst_len; r0 += rows_per) {
+                it.row0 = r0;
+                it.nrows = std::min(rows_per, dst_len - r0);
+                validate_item(g, it, kp1, H, mode, src_size, dst_size);
+                items.push_back(it);
+                cost.push_back((long long)src_len * it.ncols + (long long)it.nrows * it.ncols * 8);
+            }
             smem = std::max(smem, (size_t)src_len * it.stride * elem_bytes);
         }
         plan.max_src_len = std::max(plan.max_src_len, src_len);

@@ -379,6 +379,8 @@ __global__ void cg_direction_kernel(double* __restrict__ p, const double* __rest
         p[i] = r[i] + beta * p[i];
 }
 
+__global__ void copy_scalar_kernel(double* __restrict__ dst, const double* __restrict__ src) { *dst = *src; }
+
 // x += V[:, :m] y with y on the device
 __global__ void basis_accumulate_kernel(const double* __restrict__ V, long long ldv, int m,
                                         const double* __restrict__ y, double* __restrict__ x, long long n) {
@@ -552,6 +554,12 @@ void vk_cg_direction(sgk_ctx* ctx, double* p, const double* r, const double* rr_
     KTimer kt(ctx, KC_VECTOR);
     cg_direction_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(p, r, rr_new, rr_old, n);
     check_launch("cg_direction");
+    count_launch(ctx);
+}
+void vk_copy_scalar(sgk_ctx* ctx, double* dst, const double* src) {
+    KTimer kt(ctx, KC_VECTOR);
+    copy_scalar_kernel<<<1, 1, 0, ctx->stream>>>(dst, src);
+    check_launch("copy_scalar");
     count_launch(ctx);
 }
 void vk_basis_accumulate(sgk_ctx* ctx, const double* V, long long ldv, int m, const double* y, double* x,

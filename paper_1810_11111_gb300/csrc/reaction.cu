@@ -373,6 +373,8 @@ void quad_build(Quad& Q, const sgk_index* idx, int q, int nspecies, bool need_ja
         for (int r = 0; r < kp1; ++r) B[g * kp1 + r] = std::sqrt(2.0 * r + 1.0) * P[r] / std::sqrt(h);
         w1[g] = 0.5 * h * wg[g];
     }
+    Q.B_host = B;
+    Q.w_host = w1;
     Q.B64.upload(B, ctx->stream);
     Q.w64.upload(w1, ctx->stream);
     std::vector<float> Bf(B.begin(), B.end()), wf(w1.begin(), w1.end());
@@ -392,11 +394,11 @@ static const T* tvals(const Csr& c) {
 }
 
 template <typename T>
-void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* tmp) {
+void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* tmp, int ndims) {
     const int prec = sizeof(T) == 8 ? 0 : 1;
     const T* src = in;
-    for (int i = 0; i < Q.d; ++i) {
-        T* dst = ((Q.d - 1 - i) % 2 == 0) ? final_nodal : tmp;
+    for (int i = 0; i < ndims; ++i) {
+        T* dst = ((ndims - 1 - i) % 2 == 0) ? final_nodal : tmp;
         launch_fiber<T>(ctx, Q.fwd[i][prec], FIBER_FWD, src, dst, Q.tab.T.d_ptr.p, Q.tab.T.d_col.p, tvals<T>(Q.tab.T),
                         Q.H, Q.kp1, T(1), 0);
         src = dst;
@@ -404,11 +406,11 @@ void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* t
 }
 
 template <typename T>
-void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out) {
+void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out, int ndims) {
     const int prec = sizeof(T) == 8 ? 0 : 1;
     const T* src = moments;
-    for (int i = Q.d - 1; i >= 0; --i) {
-        T* dst = i == 0 ? out : (((Q.d - 1 - i) % 2 == 0) ? tmp : moments);
+    for (int i = ndims - 1; i >= 0; --i) {
+        T* dst = i == 0 ? out : (((ndims - 1 - i) % 2 == 0) ? tmp : moments);
         launch_fiber<T>(ctx, Q.bwd[i][prec], FIBER_BWD, src, dst, Q.tab.Tt.d_ptr.p, Q.tab.Tt.d_col.p,
                         tvals<T>(Q.tab.Tt), Q.H, Q.kp1, T(1), 0);
         src = dst;
@@ -461,10 +463,10 @@ void quad_cells(sgk_ctx* ctx, const Quad& Q, const ReactionDev& rx, bool jac, co
     count_launch(ctx);
 }
 
-template void quad_forward<double>(sgk_ctx*, const Quad&, const double*, double*, double*);
-template void quad_forward<float>(sgk_ctx*, const Quad&, const float*, float*, float*);
-template void quad_backward<double>(sgk_ctx*, const Quad&, double*, double*, double*);
-template void quad_backward<float>(sgk_ctx*, const Quad&, float*, float*, float*);
+template void quad_forward<double>(sgk_ctx*, const Quad&, const double*, double*, double*, int);
+template void quad_forward<float>(sgk_ctx*, const Quad&, const float*, float*, float*, int);
+template void quad_backward<double>(sgk_ctx*, const Quad&, double*, double*, double*, int);
+template void quad_backward<float>(sgk_ctx*, const Quad&, float*, float*, float*, int);
 template void quad_cells<double>(sgk_ctx*, const Quad&, const ReactionDev&, bool, const double* const*,
                                  const double* const*, double* const*);
 template void quad_cells<float>(sgk_ctx*, const Quad&, const ReactionDev&, bool, const float* const*,

@@ -81,7 +81,8 @@ enum KernelClass {
     KC_REDUCE = 4,   // inner products, Gram-Schmidt passes
     KC_EXPM = 5,     // exp(tau H) e_1
     KC_VECTOR = 6,   // other vector kernels
-    KC_COUNT = 7
+    KC_KRYLOV = 7,   // whole Krylov exponential (captured graph)
+    KC_COUNT = 8
 };
 
 struct sgk_ctx {
@@ -92,6 +93,8 @@ struct sgk_ctx {
     int64_t launches = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    bool own_stream = false;  // stream created by the library (caller passed NULL)
+    bool capturing = false;   // a CUDA graph is being captured on the stream
     // event timing
     unsigned prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -181,6 +184,8 @@ struct FiberItem {
     int col0;
     int ncols;
     int stride;  // smem column stride (ncols rounded to odd)
+    int row0;    // output rows [row0, row0 + nrows) of the fiber
+    int nrows;
 };
 
 enum FiberMode { FIBER_MATVEC = 0, FIBER_FWD = 1, FIBER_BWD = 2 };

@@ -54,6 +54,7 @@ void vk_cg_update(sgk_ctx* ctx, double* x, double* r, const double* p, const dou
                   const double* pq, long long n);
 void vk_cg_direction(sgk_ctx* ctx, double* p, const double* r, const double* rr_new, const double* rr_old,
                      long long n);
+void vk_copy_scalar(sgk_ctx* ctx, double* dst, const double* src);
 void vk_basis_accumulate(sgk_ctx* ctx, const double* V, long long ldv, int m, const double* y, double* x,
                          long long n);
 void vk_scale_from(sgk_ctx* ctx, const double* x, double* y, long long n, const double* s, const int* stop);

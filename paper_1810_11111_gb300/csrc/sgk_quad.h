@@ -24,15 +24,19 @@ struct Quad {
     FiberPlan fwd[SGK_MAX_DIM][2], bwd[SGK_MAX_DIM][2];  // [direction][fp64, fp32]
     DevBuf<double> B64, w64;
     DevBuf<float> B32, w32;
+    std::vector<double> B_host, w_host;  // q x (k+1) and q
+    bool fused = false;                  // last direction runs in the pencil kernel
 };
 
 int reaction_degree(const ReactionDev& rx);
 long long tuple_rank(const std::vector<int>& l, int n);
 void quad_build(Quad& Q, const sgk_index* idx, int q, int nspecies, bool need_jacobian);
+// Change of basis along directions 0..ndims-1 (ndims = d: to the full finest
+// grid) and its transpose.
 template <typename T>
-void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* tmp);
+void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* tmp, int ndims);
 template <typename T>
-void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out);
+void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out, int ndims);
 template <typename T>
 void quad_cells(sgk_ctx* ctx, const Quad& Q, const ReactionDev& rx, bool jac, const T* const* u, const T* const* w,
                 T* const* out);

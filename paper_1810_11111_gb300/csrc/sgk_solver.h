@@ -4,6 +4,13 @@
 #include "sgk_krylov.h"
 #include "sgk_quad.h"
 
+// An instantiated CUDA graph of a fixed launch sequence and the number of
+// kernels it holds.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int64_t nlaunch = 0;
+};
+
 struct sgk_solver {
     sgk_ctx* ctx = nullptr;
     const sgk_index* idx = nullptr;
@@ -31,6 +38,8 @@ struct sgk_solver {
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     double* hscal = nullptr;  // pinned host scalars
+    bool use_graphs = true;
+    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_resid, g_cg;
     sgk_stats stats{};
     ~sgk_solver();
 };

@@ -11,13 +11,15 @@
 // decide loop exits.  In SGK_MIXED mode the matvec, Arnoldi basis, axpys of
 // the Gram-Schmidt passes and the reaction/Jacobian passes run in FP32; inner
 // products, norms, exp(dt H), the Newton residual vector and the state stay
-// FP64.  Because FP32 reaction passes put a floor under the residual, the
-// mixed outer loop also stops when ||G|| no longer halves and is below
-// 1e-6 max(1, ||W||) (the Newton iteration has reached that floor).
+// FP64.  The Krylov exponential stays FP64 in both modes.  Because FP32
+// reaction passes put a floor under the residual, the mixed outer loop also
+// stops when ||G|| no longer halves and is below 1e-8 max(1, ||W||) (the
+// Newton iteration has reached that floor).
 #include <cmath>
 #include <cstring>
 
 #include "sgk_krylov.h"
+#include "sgk_pencil.h"
 #include "sgk_quad.h"
 #include "sgk_solver.h"
 
@@ -27,6 +29,42 @@ double read_scalar(sgk_solver* s, const double* dptr) {
     SGK_CUDA_CHECK(cudaMemcpyAsync(s->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
     SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
     return s->hscal[0];
+}
+
+// Runs body() through a cached CUDA graph: captured on first use (kernel
+// timers off, launches counted once), then replayed with one launch.
+template <class Body>
+void run_graph(sgk_solver* s, GraphCache& g, int kc, Body&& body) {
+    sgk_ctx* ctx = s->ctx;
+    if (!s->use_graphs || ctx->prof_mask) {  // kernel timing needs individual launches
+        body();
+        return;
+    }
+    if (!g.exec) {
+        const int64_t before = ctx->launches;
+        cudaGraph_t graph = nullptr;
+        ctx->capturing = true;
+        SGK_CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            body();
+        } catch (...) {
+            cudaStreamEndCapture(ctx->stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            ctx->capturing = false;
+            throw;
+        }
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        ctx->capturing = false;
+        SGK_CUDA_CHECK(e);
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        SGK_CUDA_CHECK(ei);
+        g.nlaunch = ctx->launches - before;
+        ctx->launches = before;
+    }
+    KTimer kt(ctx, kc);
+    SGK_CUDA_CHECK(cudaGraphLaunch(g.exec, ctx->stream));
+    count_launch(ctx, (int)g.nlaunch);
 }
 
 template <typename T>
@@ -58,7 +96,55 @@ QuadPtrs<T> qptrs(sgk_solver* s) {
     return p;
 }
 
-// F(U) for species-stacked FP64 U into FP64 F; leaves nodal U in unod.
+// Directions changed by the fiber engine: all d (unfused) or 0..d-2 (the
+// last one is fused with the cell quadrature in the pencil kernel).
+int fiber_dims(const sgk_solver* s) { return s->Q.fused ? s->Q.d - 1 : s->Q.d; }
+
+template <typename T>
+void forward_species(sgk_solver* s, const T* src, T* dst, T* tmp) {
+    const int nd = fiber_dims(s);
+    if (nd == 0) {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(dst, src, s->n * sizeof(T), cudaMemcpyDeviceToDevice, s->ctx->stream));
+        return;
+    }
+    quad_forward<T>(s->ctx, s->Q, src, dst, tmp, nd);
+}
+
+template <typename T>
+void backward_species(sgk_solver* s, T* mom, T* tmp, T* out) {
+    const int nd = fiber_dims(s);
+    if (nd == 0) {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(out, mom, s->n * sizeof(T), cudaMemcpyDeviceToDevice, s->ctx->stream));
+        return;
+    }
+    quad_backward<T>(s->ctx, s->Q, mom, tmp, out, nd);
+}
+
+template <typename T>
+void cell_pass(sgk_solver* s, bool jac, T* const* u, T* const* w, T* const* out) {
+    const Quad& Q = s->Q;
+    if (!Q.fused) {
+        quad_cells<T>(s->ctx, Q, s->rx, jac, u, w, out);
+        return;
+    }
+    PencilArgs a{};
+    a.H = Q.H;
+    a.N = Q.N;
+    a.ncell1 = 1 << Q.N;
+    a.npencils = 1;
+    for (int m = 0; m < Q.d - 1; ++m) a.npencils *= a.ncell1;
+    for (int l = 0; l <= Q.N; ++l) a.cbase[l] = Q.layout_offsets[Q.d - 1][l];
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        a.u[sp] = u[sp];
+        a.w[sp] = jac ? w[sp] : nullptr;
+        a.out[sp] = out[sp];
+    }
+    a.Tv = sizeof(T) == 8 ? (const void*)Q.tab.T.d_val.p : (const void*)Q.tab.T.d_valf.p;
+    pencil_launch<T>(s->ctx, a, Q.d, Q.kp1, Q.q, s->nspecies, jac, Q.B_host.data(), Q.w_host.data(), s->rx);
+}
+
+// F(U) for species-stacked FP64 U into FP64 F; caches the transformed U in
+// unod for the Jacobian products that follow.
 template <typename T>
 void evalF_T(sgk_solver* s, const double* U, double* F) {
     QuadPtrs<T> p = qptrs<T>(s);
@@ -70,21 +156,21 @@ void evalF_T(sgk_solver* s, const double* U, double* F) {
             vk_convert(s->ctx, U + sp * n, reinterpret_cast<float*>(p.spin[sp]), n);
             src = p.spin[sp];
         }
-        quad_forward<T>(s->ctx, s->Q, src, p.unod[sp], p.tmp);
+        forward_species<T>(s, src, p.unod[sp], p.tmp);
     }
-    quad_cells<T>(s->ctx, s->Q, s->rx, false, p.unod, nullptr, p.wnod);
+    cell_pass<T>(s, false, p.unod, nullptr, p.wnod);
     for (int sp = 0; sp < s->nspecies; ++sp) {
         if (sizeof(T) == 8) {
-            quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, reinterpret_cast<T*>(F + sp * n));
+            backward_species<T>(s, p.wnod[sp], p.tmp, reinterpret_cast<T*>(F + sp * n));
         } else {
-            quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, p.spout[sp]);
+            backward_species<T>(s, p.wnod[sp], p.tmp, p.spout[sp]);
             vk_convert(s->ctx, reinterpret_cast<const float*>(p.spout[sp]), F + sp * n, n);
         }
     }
     s->unod_valid = true;
 }
 
-// J_F(U) w for the U whose nodal values are cached in unod; output in T.
+// J_F(U) w for the U cached in unod; output in T.
 template <typename T>
 void evalJ_T(sgk_solver* s, const double* w, T* out) {
     QuadPtrs<T> p = qptrs<T>(s);
@@ -96,10 +182,10 @@ void evalJ_T(sgk_solver* s, const double* w, T* out) {
             vk_convert(s->ctx, w + sp * n, reinterpret_cast<float*>(p.spin[sp]), n);
             src = p.spin[sp];
         }
-        quad_forward<T>(s->ctx, s->Q, src, p.wnod[sp], p.tmp);
+        forward_species<T>(s, src, p.wnod[sp], p.tmp);
     }
-    quad_cells<T>(s->ctx, s->Q, s->rx, true, p.unod, p.wnod, p.wnod);
-    for (int sp = 0; sp < s->nspecies; ++sp) quad_backward<T>(s->ctx, s->Q, p.wnod[sp], p.tmp, out + sp * n);
+    cell_pass<T>(s, true, p.unod, p.wnod, p.wnod);
+    for (int sp = 0; sp < s->nspecies; ++sp) backward_species<T>(s, p.wnod[sp], p.tmp, out + sp * n);
 }
 
 void evalF(sgk_solver* s, const double* U, double* F) {
@@ -141,9 +227,9 @@ void cg_solve(sgk_solver* s, const double* G, double* x, int& iters) {
     double* r = s->cg_r.p;
     double* pv = s->cg_p.p;
     double* q = s->cg_q.p;
-    double* rr = s->scal.p + 2;
-    double* rr_new = s->scal.p + 3;
-    double* pq = s->scal.p + 4;
+    double* const rr = s->scal.p + 2;
+    double* const rr_new = s->scal.p + 3;
+    double* const pq = s->scal.p + 4;
     SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
     vk_axpby(ctx, -1.0, G, 0.0, G, r, N);
     vk_axpby(ctx, -1.0, G, 0.0, G, pv, N);
@@ -152,13 +238,15 @@ void cg_solve(sgk_solver* s, const double* G, double* x, int& iters) {
     const double stop = s->opts.inner_tol * s->opts.inner_tol * rr_h;
     iters = 0;
     while (iters < s->opts.inner_max && rr_h > stop) {
-        apply_newton_matrix(s, pv, q);
-        vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
-        vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
-        vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
-        vk_cg_direction(ctx, pv, r, rr_new, rr, N);
-        rr_h = read_scalar(s, rr_new);
-        std::swap(rr, rr_new);
+        run_graph(s, s->g_cg, KC_VECTOR, [&]() {
+            apply_newton_matrix(s, pv, q);
+            vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
+            vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
+            vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
+            vk_cg_direction(ctx, pv, r, rr_new, rr, N);
+            vk_copy_scalar(ctx, rr, rr_new);
+        });
+        rr_h = read_scalar(s, rr);
         ++iters;
     }
 }
@@ -226,12 +314,14 @@ int newton(sgk_solver* s) {
     vk_dot(ctx, s->W.p, s->W.p, N, s->partials.p, s->scal.p + 6, 1, nullptr);
     const double wnorm = read_scalar(s, s->scal.p + 6);
     const double stop = s->opts.tol * std::max(1.0, wnorm);
-    const double floor_accept = 1e-6 * std::max(1.0, wnorm);
+    const double floor_accept = 1e-8 * std::max(1.0, wnorm);
     double prev = INFINITY;
     for (int it = 0; it <= s->opts.max_iter; ++it) {
-        evalF(s, s->U.p, s->Fv.p);
-        vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
-        vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
+        run_graph(s, s->g_resid, KC_VECTOR, [&]() {
+            evalF(s, s->U.p, s->Fv.p);
+            vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
+            vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
+        });
         const double g = read_scalar(s, s->scal.p + 7);
         s->stats.last_newton_residual = g;
         if (!std::isfinite(g)) break;
@@ -263,13 +353,13 @@ void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, doub
     const long long n = s->n;
     if (s->prec == SGK_FP64) {
         QuadPtrs<double> p = qptrs<double>(s);
-        for (int sp = 0; sp < s->nspecies; ++sp) quad_forward<double>(s->ctx, s->Q, U + sp * n, p.unod[sp], p.tmp);
+        for (int sp = 0; sp < s->nspecies; ++sp) forward_species<double>(s, U + sp * n, p.unod[sp], p.tmp);
         evalJ_T<double>(s, w, jw);
     } else {
         QuadPtrs<float> p = qptrs<float>(s);
         for (int sp = 0; sp < s->nspecies; ++sp) {
             vk_convert(s->ctx, U + sp * n, p.spin[sp], n);
-            quad_forward<float>(s->ctx, s->Q, p.spin[sp], p.unod[sp], p.tmp);
+            forward_species<float>(s, p.spin[sp], p.unod[sp], p.tmp);
         }
         evalJ_T<float>(s, w, s->jw32.p);
         vk_convert(s->ctx, s->jw32.p, jw, n * s->nspecies);
@@ -280,14 +370,11 @@ void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, doub
 void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) {
     const sgk_op* op = s->ops[species];
     const long long n = s->n;
-    if (s->prec == SGK_FP64) {
-        auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
-        krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
-    } else {
-        auto mv = [op](const float* x, float* y) { op_matvec<float>(op, x, y); };
-        krylov_expv_dev<float>(s->ctx, krylov_work<float>(s, species), mv, v, W, n, s->M, s->dt);
-    }
-    s->stats.krylov_calls += 1;
+    // FP64 in both precision modes: an FP32 matvec inside Arnoldi costs a few
+    // 1e-6 of relative accuracy per exponential on these stiff operators
+    auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
+    krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
+    if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
 }
 
 int solver_step(sgk_solver* s, int nsteps) {
@@ -296,12 +383,20 @@ int solver_step(sgk_solver* s, int nsteps) {
     const double dt2 = 0.5 * s->dt;
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        if (s->has_rx) {
-            evalF(s, s->U.p, s->Fv.p);
-            vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
+        run_graph(s, s->g_pred, KC_VECTOR, [&]() {
+            if (s->has_rx) {
+                evalF(s, s->U.p, s->Fv.p);
+                vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
+            } else {
+                SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                               ctx->stream));
+            }
+        });
+        for (int sp = 0; sp < s->nspecies; ++sp) {
+            run_graph(s, s->g_krylov[sp], KC_KRYLOV,
+                      [&]() { solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n); });
+            s->stats.krylov_calls += s->use_graphs ? 1 : 0;
         }
-        const double* vsrc = s->has_rx ? s->vv.p : s->U.p;
-        for (int sp = 0; sp < s->nspecies; ++sp) solver_krylov_expv(s, sp, vsrc + sp * n, s->W.p + sp * n);
         int rc = SGK_OK;
         if (!s->has_rx) {
             SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -335,13 +430,8 @@ void solver_alloc(sgk_solver* s) {
     s->W.alloc(N);
     s->vv.alloc(N);
     SGK_CUDA_CHECK(cudaMemsetAsync(s->U.p, 0, N * sizeof(double), s->ctx->stream));
-    if (s->prec == SGK_FP64) {
-        s->V64.alloc((M + 1) * n);
-        s->w64.alloc(n);
-    } else {
-        s->V32.alloc((M + 1) * n);
-        s->w32.alloc(n);
-    }
+    s->V64.alloc((M + 1) * n);
+    s->w64.alloc(n);
     s->Hm.alloc((M + 1) * M);
     s->h1.alloc(std::max(M, s->opts.gmres_restart) + 1);
     s->h2.alloc(std::max(M, s->opts.gmres_restart) + 1);
@@ -382,4 +472,8 @@ void solver_alloc(sgk_solver* s) {
 
 sgk_solver::~sgk_solver() {
     if (hscal) cudaFreeHost(hscal);
+    for (GraphCache* g : {&g_pred, &g_resid, &g_cg})
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (auto& g : g_krylov)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
 }

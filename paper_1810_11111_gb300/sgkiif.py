@@ -131,15 +131,16 @@ class Context:
     def launches(self):
         return int(sgk_ctx_launch_count(self.h))
 
-    KERNEL_CLASSES = ("matvec", "to_finest", "from_finest", "cell_quadrature", "reductions", "expm", "vector")
+    KERNEL_CLASSES = ("matvec", "to_finest", "from_finest", "cell_quadrature", "reductions", "expm", "vector",
+                      "krylov_graph")
 
     def profile(self, mask):
         self.check(sgk_ctx_profile(self.h, int(mask)))
 
     def profile_read(self):
         """{class: (milliseconds, launches)} since the previous read."""
-        ms = np.zeros(7)
-        n = np.zeros(7, dtype=np.int64)
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
         self.check(sgk_ctx_profile_read(self.h, _dptr(ms), n.ctypes.data_as(_c_i64_p)))
         return {c: (float(ms[i]), int(n[i])) for i, c in enumerate(self.KERNEL_CLASSES)}
 
