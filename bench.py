@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP64 comparison run")
     return ap.parse_args()
 
 
@@ -216,7 +217,7 @@ def native(args, rank, world, local_rank):
 
     # accuracy against the FP64 GPU path (itself parity-tested against the oracle)
     acc = None
-    if prec == sgkiif.SGK_MIXED:
+    if prec == sgkiif.SGK_MIXED and not args.no_accuracy:
         ref = Problem(cfg, sgkiif.SGK_FP64, device=local_rank)
         ref.reset()
         ref.solver.step(args.steps)

@@ -368,7 +368,7 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
             const int q = std::max(1, (p * k + k + 1 + 1) / 2);
             SGK_REQUIRE(q <= 8, SGK_EUNSUPPORTED, "reaction degree too high for the quadrature tables");
             quad_build(s->Q, idx, q, nspecies, true);
-            s->Q.fused = pencil_supported(idx->d, idx->k + 1, q, nspecies) && std::getenv("SGK_NO_FUSED") == nullptr;
+            s->Q.fused = pencil_supported(idx->d, idx->k + 1, q, nspecies, s->rx) && std::getenv("SGK_NO_FUSED") == nullptr;
             const size_t elem = fp64 ? 8 : 4;
             const double need = (double)((2 * nspecies + 1) * s->Q.full_size) * elem;
             size_t free_b = 0, total_b = 0;

@@ -105,7 +105,171 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
     }
 }
 
+// Change of basis along one direction by the two-scale (pyramid) relations.
+// FWD: hierarchical fibers (levels 0..N') -> finest-cell Legendre
+// coefficients (levels refined up to Nfull with zero details above N').
+// BWD: the transpose, finest Legendre moments -> hierarchical coefficients of
+// levels 0..N'.  Shared memory per column: the source fiber and two
+// full-length work buffers; threads run over (cell, column) with the column
+// fastest, one level per barrier.
+template <typename T, int MODE, int KP1>
+__global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ items, int nitems,
+                                                  const FiberGroup* __restrict__ groups, const T* __restrict__ src,
+                                                  T* __restrict__ dst, const PyrFilt<T> flt, int H, int Nfull) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    __shared__ FiberGroup sg;
+    T Hm[2][KP1][KP1], Gm[2][KP1][KP1];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < KP1; ++r)
+#pragma unroll
+            for (int s = 0; s < KP1; ++s) {
+                Hm[h][r][s] = flt.H[h][r][s];
+                Gm[h][r][s] = flt.G[h][r][s];
+            }
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const FiberItem item = items[it];
+        if (threadIdx.x < (int)(sizeof(FiberGroup) / sizeof(long long)))
+            reinterpret_cast<long long*>(&sg)[threadIdx.x] =
+                reinterpret_cast<const long long*>(groups + item.group)[threadIdx.x];
+        __syncthreads();
+        const int Np = sg.nlev - 1;  // finest hierarchical level of the fiber
+        const int F = KP1 << Np;
+        const int I = sg.I, nc = item.ncols, st = item.stride;
+        const int src_len = MODE == FIBER_BWD ? H : F;
+        T* X = tile;
+        T* A = tile + (size_t)src_len * st;
+        T* B = A + (size_t)H * st;
+        for (int e = threadIdx.x; e < src_len * nc; e += blockDim.x) {
+            const int pos = e / nc, c = e - (e / nc) * nc;
+            const int col = item.col0 + c;
+            const int o = col / I, in = col - (col / I) * I;
+            const long long a = MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I);
+            X[pos * st + c] = src[a];
+        }
+        __syncthreads();
+        if (MODE == FIBER_FWD) {
+            const T* cur = X;
+            T* nxt = A;
+            for (int n = 1; n <= Nfull; ++n) {
+                const int npar = 1 << (n - 1);
+                const bool has_detail = n <= Np;
+                for (int e = threadIdx.x; e < npar * 2 * nc; e += blockDim.x) {
+                    const int c = e % nc;
+                    const int t = e / nc;
+                    const int h = t & 1, par = t >> 1;
+                    T pv[KP1], dv[KP1];
+#pragma unroll
+                    for (int r = 0; r < KP1; ++r) {
+                        pv[r] = cur[(par * KP1 + r) * st + c];
+                        dv[r] = has_detail ? X[((KP1 << (n - 1)) + par * KP1 + r) * st + c] : T(0);
+                    }
+#pragma unroll
+                    for (int s = 0; s < KP1; ++s) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int r = 0; r < KP1; ++r) acc += Hm[h][r][s] * pv[r] + Gm[h][r][s] * dv[r];
+                        nxt[((2 * par + h) * KP1 + s) * st + c] = acc;
+                    }
+                }
+                __syncthreads();
+                cur = nxt;
+                nxt = (nxt == A) ? B : A;
+            }
+            for (int e = threadIdx.x; e < H * nc; e += blockDim.x) {
+                const int pos = e / nc, c = e - (e / nc) * nc;
+                const int col = item.col0 + c;
+                const int o = col / I, in = col - (col / I) * I;
+                dst[full_addr(sg, o, pos, in, H, I)] = cur[pos * st + c];
+            }
+        } else {
+            // cur holds level-n scaling coefficients; details of levels <= Np
+            // go to B (hierarchical layout), the rest are discarded
+            T* cur = X;
+            T* nxt = A;
+            for (int n = Nfull; n >= 1; --n) {
+                const int npar = 1 << (n - 1);
+                for (int e = threadIdx.x; e < npar * nc; e += blockDim.x) {
+                    const int c = e % nc, par = e / nc;
+                    T x0[KP1], x1[KP1];
+#pragma unroll
+                    for (int s = 0; s < KP1; ++s) {
+                        x0[s] = cur[(2 * par * KP1 + s) * st + c];
+                        x1[s] = cur[((2 * par + 1) * KP1 + s) * st + c];
+                    }
+#pragma unroll
+                    for (int r = 0; r < KP1; ++r) {
+                        T sp = T(0), sd = T(0);
+#pragma unroll
+                        for (int s = 0; s < KP1; ++s) {
+                            sp += Hm[0][r][s] * x0[s] + Hm[1][r][s] * x1[s];
+                            sd += Gm[0][r][s] * x0[s] + Gm[1][r][s] * x1[s];
+                        }
+                        nxt[(par * KP1 + r) * st + c] = sp;
+                        if (n <= Np) B[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
+                    }
+                }
+                __syncthreads();
+                T* t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            for (int e = threadIdx.x; e < KP1 * nc; e += blockDim.x) {
+                const int r = e / nc, c = e - (e / nc) * nc;
+                B[r * st + c] = cur[r * st + c];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < F * nc; e += blockDim.x) {
+                const int pos = e / nc, c = e - (e / nc) * nc;
+                const int col = item.col0 + c;
+                const int o = col / I, in = col - (col / I) * I;
+                dst[chunk_addr(sg, o, pos, in, KP1, I)] = B[pos * st + c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+template <typename T>
+void launch_pyr(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, int H, int kp1,
+                const double* two_scale) {
+    if (plan.nitems == 0) return;
+    PyrFilt<T> f{};
+    for (int h = 0; h < 2; ++h)
+        for (int r = 0; r < kp1; ++r)
+            for (int s = 0; s < kp1; ++s) {
+                f.H[h][r][s] = (T)two_scale[h * kp1 * kp1 + r * kp1 + s];
+                f.G[h][r][s] = (T)two_scale[(2 + h) * kp1 * kp1 + r * kp1 + s];
+            }
+    int Nfull = 0;
+    while ((kp1 << Nfull) < H) ++Nfull;
+    const int grid = std::min(plan.nitems, ctx->num_sms * 8);
+    const size_t smem = plan.smem_bytes;
+    KTimer kt(ctx, mode);
+#define SGK_PYR_CASE(M, K)                                                                                   \
+    if (mode == M && kp1 == K) {                                                                             \
+        SGK_CUDA_CHECK(cudaFuncSetAttribute(pyr_kernel<T, M, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                            (int)smem));                                                     \
+        pyr_kernel<T, M, K><<<grid, 256, smem, ctx->stream>>>(plan.items.p, plan.nitems, plan.groups.p, src, dst, \
+                                                              f, H, Nfull);                                 \
+    }
+    SGK_PYR_CASE(FIBER_FWD, 2)
+    SGK_PYR_CASE(FIBER_FWD, 3)
+    SGK_PYR_CASE(FIBER_FWD, 4)
+    SGK_PYR_CASE(FIBER_BWD, 2)
+    SGK_PYR_CASE(FIBER_BWD, 3)
+    SGK_PYR_CASE(FIBER_BWD, 4)
+#undef SGK_PYR_CASE
+    check_launch("pyr_kernel");
+    count_launch(ctx);
+}
+
+template void launch_pyr<double>(sgk_ctx*, const FiberPlan&, int, const double*, double*, int, int, const double*);
+template void launch_pyr<float>(sgk_ctx*, const FiberPlan&, int, const float*, float*, int, int, const double*);
 
 // Host mirror of the kernel's address arithmetic, for plan validation.
 static long long chunk_addr_host(const FiberGroup& g, long long o, int pos, long long in, int kp1, int I) {
@@ -164,7 +328,11 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
         const int dst_len = mode == FIBER_FWD ? H : F;
         long long cols = (long long)g.O * g.I;
         SGK_REQUIRE(cols < (1LL << 31), SGK_EUNSUPPORTED, "plan: too many fibers in one group");
-        long long fit = (long long)(smem_budget / ((size_t)src_len * elem_bytes)) - 1;
+        // the change of basis runs the two-scale pyramid, which needs the
+        // source fiber plus two full-length work buffers per column
+        const bool pyr = mode != FIBER_MATVEC;
+        const int tile_rows = pyr ? src_len + 2 * H : src_len;
+        long long fit = (long long)(smem_budget / ((size_t)tile_rows * elem_bytes)) - 1;
         int maxc = (int)std::min<long long>(64, std::max<long long>(1, fit));
         for (long long c0 = 0; c0 < cols; c0 += maxc) {
             FiberItem it;
@@ -173,9 +341,12 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
             it.ncols = (int)std::min<long long>(maxc, cols - c0);
             it.stride = it.ncols | 1;
             // split the output rows so that one item computes about 1024
-            // outputs (long fibers with few columns would otherwise serialise
-            // on one SM); every split item stages the whole source fiber
-            const int rows_per = std::max(1, std::min(dst_len, 1024 / it.ncols));
+            // outputs, 128 in FP64 whose pipe is ~60x narrower (long fibers
+            // with few columns would otherwise serialise on one SM); every
+            // split item stages the whole source fiber.  A pyramid item
+            // computes whole fibers.
+            const int target = elem_bytes == 8 ? 128 : 1024;
+            const int rows_per = pyr ? dst_len : std::max(1, std::min(dst_len, target / it.ncols));
             for (int r0 = 0; r0 < dst_len; r0 += rows_per) {
                 it.row0 = r0;
                 it.nrows = std::min(rows_per, dst_len - r0);
@@ -183,7 +354,7 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
                 items.push_back(it);
                 cost.push_back((long long)src_len * it.ncols + (long long)it.nrows * it.ncols * 8);
             }
-            smem = std::max(smem, (size_t)src_len * it.stride * elem_bytes);
+            smem = std::max(smem, (size_t)tile_rows * it.stride * elem_bytes);
         }
         plan.max_src_len = std::max(plan.max_src_len, src_len);
     }

@@ -171,6 +171,188 @@ __global__ void arnoldi_finalize_kernel(int j, int M, const double* __restrict__
     }
 }
 
+// ------------------------------------------- fused Gram-Schmidt kernels ---
+//
+// FP64 adds have a 64-cycle dependent latency on this GPU, so reductions
+// keep several independent chains per thread: up to CH column sums at once,
+// reduced over the warp with interleaved shuffles.  Each kernel ends its
+// grid-wide reduction in the last block to finish (a counter in global
+// memory); that block sums the per-block partials in a fixed order, so the
+// result is deterministic.
+
+constexpr int CH = 8;
+
+// Block-wide sums of CH values per thread; results valid in threads 0..CH-1
+// (thread j holds the sum of value j).  sh: CH * 32 doubles.
+__device__ __forceinline__ void block_sum_multi(double (&v)[CH], double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < CH; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < CH; ++j) sh[j * 32 + wid] = v[j];
+    __syncthreads();
+    if (threadIdx.x < CH) {
+        double a = 0.0, b = 0.0;
+        int w = 0;
+        for (; w + 1 < nw; w += 2) {
+            a += sh[threadIdx.x * 32 + w];
+            b += sh[threadIdx.x * 32 + w + 1];
+        }
+        if (w < nw) a += sh[threadIdx.x * 32 + w];
+        v[0] = a + b;
+    }
+    __syncthreads();
+}
+
+// partial[block][c] = sum over this block's elements of V[c][i] w[i]
+template <typename T>
+__device__ void block_partial_dots(const T* __restrict__ V, long long ldv, int ncols, const T* w, long long n,
+                                   double* __restrict__ partials, double* sh) {
+    for (int c0 = 0; c0 < ncols; c0 += CH) {
+        double acc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const double wv = (double)w[i];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (c0 + c < ncols) acc[c] += (double)V[(c0 + c) * ldv + i] * wv;
+        }
+        block_sum_multi(acc, sh);
+        if (threadIdx.x < CH && c0 + (int)threadIdx.x < ncols)
+            partials[(long long)blockIdx.x * ncols + c0 + threadIdx.x] = acc[0];
+    }
+}
+
+// True in the last block to arrive; that block resets the counter.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) *counter = 0u;
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// out[c] = sum_b partials[b][c] in a fixed order (one warp per column)
+__device__ void final_columns(const double* partials, int nb, int ncols, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int c = wid; c < ncols; c += nw) {
+        double a = 0.0;
+        for (int b = lane; b < nb; b += 32) a += __ldcg(partials + (long long)b * ncols + c);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[c] = a;
+    }
+}
+
+// w -= V[:, :ncols] h on this thread's elements (four independent chains)
+template <typename T>
+__device__ __forceinline__ void block_update(const T* __restrict__ V, long long ldv, int ncols, const T* hs, T* w,
+                                             long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int c = 0;
+        for (; c + 3 < ncols; c += 4) {
+            a0 += V[c * ldv + i] * hs[c];
+            a1 += V[(c + 1) * ldv + i] * hs[c + 1];
+            a2 += V[(c + 2) * ldv + i] * hs[c + 2];
+            a3 += V[(c + 3) * ldv + i] * hs[c + 3];
+        }
+        for (; c < ncols; ++c) a0 += V[c * ldv + i] * hs[c];
+        w[i] -= (a0 + a1) + (a2 + a3);
+    }
+}
+
+// h1 = V^T w
+template <typename T>
+__global__ void arn_dots_kernel(const T* __restrict__ V, long long ldv, int ncols, const T* __restrict__ w, long long n,
+                                double* __restrict__ partials, unsigned* counter, double* __restrict__ h,
+                                const int* __restrict__ stop) {
+    if (*stop) return;
+    __shared__ double sh[CH * 32];
+    block_partial_dots(V, ldv, ncols, w, n, partials, sh);
+    if (last_block(counter)) final_columns(partials, gridDim.x, ncols, h);
+}
+
+// w -= V h1, then h2 = V^T w
+template <typename T>
+__global__ void arn_update_dots_kernel(const T* __restrict__ V, long long ldv, int ncols, const double* __restrict__ h1,
+                                       T* w, long long n, double* __restrict__ partials, unsigned* counter,
+                                       double* __restrict__ h2, const int* __restrict__ stop) {
+    if (*stop) return;
+    __shared__ double sh[CH * 32];
+    __shared__ T hs[SGK_MAX_KRYLOV + 1];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = (T)h1[c];
+    __syncthreads();
+    block_update(V, ldv, ncols, hs, w, n);
+    block_partial_dots(V, ldv, ncols, w, n, partials, sh);  // each thread rereads its own elements
+    if (last_block(counter)) final_columns(partials, gridDim.x, ncols, h2);
+}
+
+// w -= V h2, ||w||^2, and in the last block: column j of H, the breakdown
+// test and 1 / h_{j+1,j}
+template <typename T>
+__global__ void arn_update_norm_kernel(const T* __restrict__ V, long long ldv, int ncols, const double* __restrict__ h1,
+                                       const double* __restrict__ h2, T* w, long long n, double* __restrict__ partials,
+                                       unsigned* counter, double* __restrict__ H, int j, int M,
+                                       KrylovScalars* __restrict__ ks) {
+    if (ks->stop) return;
+    __shared__ double sh[CH * 32];
+    __shared__ T hs[SGK_MAX_KRYLOV + 1];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = (T)h2[c];
+    __syncthreads();
+    block_update(V, ldv, ncols, hs, w, n);
+    double acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+    int k = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double wv = (double)w[i];
+        acc[k] += wv * wv;
+        k = (k + 1) & (CH - 1);
+    }
+    double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = c == 0 ? t : 0.0;
+    block_sum_multi(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+    if (!last_block(counter)) return;
+    __shared__ double beta2;
+    final_columns(partials, gridDim.x, 1, &beta2);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double f = ks->fro2;
+    if (j >= 1) {
+        const double sub = H[(long long)j * M + (j - 1)];
+        f += sub * sub;
+    }
+    for (int i = 0; i <= j; ++i) {
+        const double v = h1[i] + h2[i];
+        H[(long long)i * M + j] = v;
+        f += v * v;
+    }
+    ks->fro2 = f;
+    const double beta = sqrt(beta2);
+    H[(long long)(j + 1) * M + j] = beta;
+    ks->m_eff = j + 1;
+    if (beta <= 1e-12 * sqrt(f)) {
+        ks->stop = 1;
+        ks->breakdown = 1;
+    } else {
+        ks->inv_beta = 1.0 / beta;
+    }
+}
+
 // ---------------------------------------------------------- expm kernel ---
 
 __device__ void blk_matmul(const double* A, const double* B, double* C, int m) {
@@ -452,8 +634,9 @@ int grid_for(const sgk_ctx* ctx, long long n) {
 }  // namespace
 
 int reduction_blocks(const sgk_ctx* ctx, int64_t n) {
-    long long b = (n + 1023) / 1024;
-    return (int)std::max(1LL, std::min<long long>(b, (long long)ctx->num_sms * 2));
+    // about one block per SM: FP64 throughput is per SM
+    long long b = (n + 127) / 128;
+    return (int)std::max(1LL, std::min<long long>(b, (long long)ctx->num_sms));
 }
 
 // ------------------------------------------------------------ host API ---
@@ -624,17 +807,19 @@ void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<
     for (int j = 0; j < M; ++j) {
         T* vj = kw.V + (long long)j * n;
         matvec(vj, kw.w);
-        vk_mdot<T>(ctx, kw.V, n, j + 1, kw.w, n, kw.partials, kw.h1, stop);
-        vk_gs_update<T>(ctx, kw.V, n, j + 1, kw.h1, kw.w, n, stop);
-        vk_mdot<T>(ctx, kw.V, n, j + 1, kw.w, n, kw.partials, kw.h2, stop);
-        vk_gs_update<T>(ctx, kw.V, n, j + 1, kw.h2, kw.w, n, stop);
-        vk_dotT<T>(ctx, kw.w, kw.w, n, kw.partials, kw.scal + 1, 0, stop);
         {
+            // classical Gram-Schmidt twice and the norm, three fused kernels
             KTimer kt(ctx, KC_REDUCE);
-            arnoldi_finalize_kernel<<<1, 1, 0, ctx->stream>>>(j, M, kw.h1, kw.h2, kw.scal + 1, kw.H, ks);
+            const int nb = reduction_blocks(ctx, n);
+            arn_dots_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.w, n, kw.partials, kw.counter, kw.h1,
+                                                            stop);
+            arn_update_dots_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.w, n, kw.partials,
+                                                                   kw.counter, kw.h2, stop);
+            arn_update_norm_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.h2, kw.w, n, kw.partials,
+                                                                   kw.counter, kw.H, j, M, ks);
         }
-        check_launch("arnoldi_finalize");
-        count_launch(ctx);
+        check_launch("arnoldi_cgs2");
+        count_launch(ctx, 3);
         {
             KTimer kt(ctx, KC_VECTOR);
             scale_vec_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.w, kw.V + (long long)(j + 1) * n, n,

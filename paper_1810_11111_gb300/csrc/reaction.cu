@@ -399,8 +399,7 @@ void quad_forward(sgk_ctx* ctx, const Quad& Q, const T* in, T* final_nodal, T* t
     const T* src = in;
     for (int i = 0; i < ndims; ++i) {
         T* dst = ((ndims - 1 - i) % 2 == 0) ? final_nodal : tmp;
-        launch_fiber<T>(ctx, Q.fwd[i][prec], FIBER_FWD, src, dst, Q.tab.T.d_ptr.p, Q.tab.T.d_col.p, tvals<T>(Q.tab.T),
-                        Q.H, Q.kp1, T(1), 0);
+        launch_pyr<T>(ctx, Q.fwd[i][prec], FIBER_FWD, src, dst, Q.H, Q.kp1, Q.tab.two_scale.data());
         src = dst;
     }
 }
@@ -411,8 +410,7 @@ void quad_backward(sgk_ctx* ctx, const Quad& Q, T* moments, T* tmp, T* out, int 
     const T* src = moments;
     for (int i = ndims - 1; i >= 0; --i) {
         T* dst = i == 0 ? out : (((ndims - 1 - i) % 2 == 0) ? tmp : moments);
-        launch_fiber<T>(ctx, Q.bwd[i][prec], FIBER_BWD, src, dst, Q.tab.Tt.d_ptr.p, Q.tab.Tt.d_col.p,
-                        tvals<T>(Q.tab.Tt), Q.H, Q.kp1, T(1), 0);
+        launch_pyr<T>(ctx, Q.bwd[i][prec], FIBER_BWD, src, dst, Q.H, Q.kp1, Q.tab.two_scale.data());
         src = dst;
     }
 }

@@ -156,6 +156,13 @@ struct Tables1D {
     std::vector<double> alpert;  // (k+1) x 2(k+1) wavelet coefficients
     Csr T;                       // H x H: hierarchical -> finest-cell Legendre
     Csr Tt;                      // transpose of T
+    // Two-scale filters, each (k+1) x (k+1) row-major: H_h[r][s] = <phi_r,
+    // phi^h_s> (parent Legendre against the Legendre basis of child h) and
+    // G_h[p][s] = <psi_p, phi^h_s> (wavelet against child h); stored as
+    // [H_0, H_1, G_0, G_1].  A child's coefficients are
+    // sum_r H_h[r][s] parent[r] + sum_p G_h[p][s] detail[p]; the transpose
+    // gives the parent and detail coefficients from the two children.
+    std::vector<double> two_scale;
 };
 
 // Gauss-Legendre rule on [-1, 1] with q points (Newton on P_q, long double).
@@ -208,6 +215,19 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
 template <typename T>
 void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
                   const T* cv, int H, int kp1, T alpha, int accumulate);
+
+// Two-scale filters for the pyramid kernels (entries beyond k+1 unused).
+template <typename T>
+struct PyrFilt {
+    T H[2][4][4];
+    T G[2][4][4];
+};
+
+// Change of basis along one direction (plan mode FIBER_FWD or FIBER_BWD) by
+// the two-scale pyramid; two_scale as in Tables1D.
+template <typename T>
+void launch_pyr(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, int H, int kp1,
+                const double* two_scale);
 
 // ------------------------------------------------------------- operator ---
 

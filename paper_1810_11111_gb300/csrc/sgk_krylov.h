@@ -33,6 +33,7 @@ struct KrylovWork {
     double* partials = nullptr;
     double* expm_ws = nullptr;  // 8 M^2
     KrylovScalars* ks = nullptr;
+    unsigned* counter = nullptr;  // last-block counter of the fused reductions (zero between kernels)
 };
 
 PadeCoef pade13_coefficients();

@@ -32,6 +32,7 @@ struct sgk_solver {
     DevBuf<float> V32, w32;
     DevBuf<double> Hm, h1, h2, ky, scal, partials, expm_ws;
     DevBuf<KrylovScalars> ks;
+    DevBuf<unsigned> counters;
     // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
     DevBuf<double> q64, jw64;
     DevBuf<float> q32, jw32;

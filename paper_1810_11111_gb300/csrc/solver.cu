@@ -139,8 +139,8 @@ void cell_pass(sgk_solver* s, bool jac, T* const* u, T* const* w, T* const* out)
         a.w[sp] = jac ? w[sp] : nullptr;
         a.out[sp] = out[sp];
     }
-    a.Tv = sizeof(T) == 8 ? (const void*)Q.tab.T.d_val.p : (const void*)Q.tab.T.d_valf.p;
-    pencil_launch<T>(s->ctx, a, Q.d, Q.kp1, Q.q, s->nspecies, jac, Q.B_host.data(), Q.w_host.data(), s->rx);
+    pencil_launch<T>(s->ctx, a, Q.d, Q.kp1, Q.q, s->nspecies, jac, Q.B_host.data(), Q.w_host.data(),
+                     Q.tab.two_scale.data(), s->rx);
 }
 
 // F(U) for species-stacked FP64 U into FP64 F; caches the transformed U in
@@ -218,6 +218,7 @@ KrylovWork<T> krylov_work(sgk_solver* s, int species) {
     kw.partials = s->partials.p;
     kw.expm_ws = s->expm_ws.p;
     kw.ks = s->ks.p + species;
+    kw.counter = s->counters.p;
     return kw;
 }
 
@@ -440,6 +441,8 @@ void solver_alloc(sgk_solver* s) {
     s->partials.alloc((size_t)reduction_blocks(s->ctx, N) * (std::max(M, s->opts.gmres_restart) + 1) + 16);
     s->expm_ws.alloc(8 * (size_t)M * M);
     s->ks.alloc(S);
+    s->counters.alloc(4);
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(unsigned), s->ctx->stream));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->Hm.p, 0, (M + 1) * M * sizeof(double), s->ctx->stream));
     if (s->has_rx) {
         s->Fv.alloc(N);

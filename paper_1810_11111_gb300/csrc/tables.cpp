@@ -223,6 +223,32 @@ void build_transform_tables(int N, int k, Tables1D& out) {
             T.ptr[c * kp1 + r + 1] = (int)T.col.size();
         }
     }
+    // two-scale filters on the reference parent [0,1] with children [0,1/2],
+    // [1/2,1]: parent phi_r(x) = sqrt(2r+1) P_r(2x-1), child h phi^h_s(x) =
+    // sqrt(2) sqrt(2s+1) P_s(4x-1-2h); the wavelets psi_p restricted to child
+    // h have Legendre coefficients alpert[p][h (k+1) + s] (dilation invariance)
+    {
+        std::vector<ld> gx, gw;
+        gauss_legendre_ld(kp1 + 1, gx, gw);
+        out.two_scale.assign(4 * kp1 * kp1, 0.0);
+        std::vector<ld> Pp(kp1), dPp(kp1), Pc(kp1), dPc(kp1);
+        for (int h = 0; h < 2; ++h) {
+            std::vector<ld> acc(kp1 * kp1, 0);
+            for (int g = 0; g < kp1 + 1; ++g) {
+                const ld x = (h + (gx[g] + 1) / 2) / 2;  // point in child h
+                legendre_eval(k, 2 * x - 1, Pp.data(), dPp.data());
+                legendre_eval(k, gx[g], Pc.data(), dPc.data());
+                for (int r = 0; r < kp1; ++r)
+                    for (int s = 0; s < kp1; ++s)
+                        acc[r * kp1 + s] += gw[g] / 4 * std::sqrt((ld)(2 * r + 1)) * Pp[r] * std::sqrt((ld)2) *
+                                            std::sqrt((ld)(2 * s + 1)) * Pc[s];
+            }
+            for (int i = 0; i < kp1 * kp1; ++i) out.two_scale[h * kp1 * kp1 + i] = (double)acc[i];
+            for (int p = 0; p < kp1; ++p)
+                for (int s = 0; s < kp1; ++s)
+                    out.two_scale[(2 + h) * kp1 * kp1 + p * kp1 + s] = (double)alp[p * 2 * kp1 + h * kp1 + s];
+        }
+    }
     // transpose (columns stay sorted because rows are visited in order)
     Csr& Tt = out.Tt;
     Tt.rows = Tt.cols = H;
