@@ -240,6 +240,19 @@ int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kapp
             S.ptr[a + 1] = (int)S.col.size();
         }
         S.upload(ctx->stream);
+        {
+            const int nl = idx->n + 1;
+            std::vector<int> rl((size_t)H * nl);
+            for (int a = 0; a < H; ++a)
+                for (int L = 0; L < nl; ++L) {
+                    const int lim = (idx->k + 1) << L;
+                    int c = 0;
+                    for (int e = S.ptr[a]; e < S.ptr[a + 1] && S.col[e] < lim; ++e) ++c;
+                    rl[(size_t)a * nl + L] = c;
+                }
+            op->rlen.upload(rl, ctx->stream);
+            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        }
         build_matvec_plans(op.get());
         *out = op.release();
         return SGK_OK;

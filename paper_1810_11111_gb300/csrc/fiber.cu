@@ -43,8 +43,9 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict__ items, int nitems,
                                                     const FiberGroup* __restrict__ groups, const T* __restrict__ src,
                                                     T* __restrict__ dst, const int* __restrict__ rp,
-                                                    const int* __restrict__ ci, const T* __restrict__ cv, int H,
-                                                    int kp1, T alpha, int accumulate) {
+                                                    const int* __restrict__ ci, const T* __restrict__ cv,
+                                                    const int* __restrict__ rlen, int nlev_max, int H, int kp1,
+                                                    T alpha, int accumulate) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     __shared__ FiberGroup sg;
@@ -86,13 +87,25 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
                 c = e - pos * nc;
             }
             pos += item.row0;
-            T acc = T(0);
-            const int q1 = rp[pos + 1];
-            for (int q = rp[pos]; q < q1; ++q) {
-                const int j = ci[q];
-                if (j >= lim) break;
-                acc += cv[q] * tile[j * st + c];
+            // row pos of the 1D matrix truncated to the fiber's levels: a
+            // fixed trip count (precomputed) so that the index and value
+            // loads are independent of each other and can be in flight
+            // together; four accumulators break the FMA dependency chain
+            const int q0 = rp[pos];
+            const int qe = q0 + rlen[pos * nlev_max + sg.nlev - 1];
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int q = q0;
+            for (; q + 3 < qe; q += 4) {
+                const int j0 = ci[q], j1 = ci[q + 1], j2 = ci[q + 2], j3 = ci[q + 3];
+                const T v0 = cv[q], v1 = cv[q + 1], v2 = cv[q + 2], v3 = cv[q + 3];
+                a0 += v0 * tile[j0 * st + c];
+                a1 += v1 * tile[j1 * st + c];
+                a2 += v2 * tile[j2 * st + c];
+                a3 += v3 * tile[j3 * st + c];
             }
+            for (; q < qe; ++q) a0 += cv[q] * tile[ci[q] * st + c];
+            const T acc = (a0 + a1) + (a2 + a3);
+            (void)lim;
             const int col = item.col0 + c;
             const int o = col / I;
             const int in = col - o * I;
@@ -373,7 +386,7 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
 
 template <typename T>
 void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
-                  const T* cv, int H, int kp1, T alpha, int accumulate) {
+                  const T* cv, const int* rlen, int nlev_max, int H, int kp1, T alpha, int accumulate) {
     if (plan.nitems == 0) return;
     const int grid = std::min(plan.nitems, ctx->num_sms * 8);
     const size_t smem = plan.smem_bytes;
@@ -385,7 +398,8 @@ void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T
             SGK_CUDA_CHECK(cudaFuncSetAttribute(fiber_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                 (int)smem));                                                 \
         fiber_kernel<T, M><<<grid, 256, smem, ctx->stream>>>(plan.items.p, plan.nitems, plan.groups.p, src, dst, \
-                                                              rp, ci, cv, H, kp1, alpha, accumulate);        \
+                                                              rp, ci, cv, rlen, nlev_max, H, kp1, alpha,     \
+                                                              accumulate);                                   \
         break;                                                                                               \
     }
         SGK_FIBER_CASE(FIBER_MATVEC)
@@ -398,9 +412,9 @@ void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T
 }
 
 template void launch_fiber<double>(sgk_ctx*, const FiberPlan&, int, const double*, double*, const int*, const int*,
-                                   const double*, int, int, double, int);
+                                   const double*, const int*, int, int, int, double, int);
 template void launch_fiber<float>(sgk_ctx*, const FiberPlan&, int, const float*, float*, const int*, const int*,
-                                  const float*, int, int, float, int);
+                                  const float*, const int*, int, int, int, float, int);
 
 // ------------------------------------------------------------- operator ---
 
@@ -457,8 +471,8 @@ void op_matvec(const sgk_op* op, const T* x, T* y) {
     for (int i = 0; i < d; ++i) {
         const T* vals = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->S.d_val.p)
                                        : reinterpret_cast<const T*>(op->S.d_valf.p);
-        launch_fiber<T>(op->ctx, op->plan[i][prec], FIBER_MATVEC, x, y, op->S.d_ptr.p, op->S.d_col.p, vals, op->H,
-                        op->idx->k + 1, T(-op->kappa[i]), i > 0 ? 1 : 0);
+        launch_fiber<T>(op->ctx, op->plan[i][prec], FIBER_MATVEC, x, y, op->S.d_ptr.p, op->S.d_col.p, vals,
+                        op->rlen.p, op->idx->n + 1, op->H, op->idx->k + 1, T(-op->kappa[i]), i > 0 ? 1 : 0);
     }
 }
 

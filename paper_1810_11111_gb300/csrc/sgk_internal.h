@@ -212,9 +212,12 @@ struct FiberPlan {
 void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, int H, int mode, size_t elem_bytes,
                    size_t smem_budget, long long src_size, long long dst_size, cudaStream_t s);
 
+// rlen[a * nlev_max + L]: entries of row a with column < (k+1) 2^L (rows of
+// the CSR matrix sorted by column), i.e. the row of the principal submatrix
+// of levels 0..L.
 template <typename T>
 void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
-                  const T* cv, int H, int kp1, T alpha, int accumulate);
+                  const T* cv, const int* rlen, int nlev_max, int H, int kp1, T alpha, int accumulate);
 
 // Two-scale filters for the pyramid kernels (entries beyond k+1 unused).
 template <typename T>
@@ -240,6 +243,7 @@ struct sgk_op {
     int H = 0;
     std::vector<double> S_dense;  // H x H host copy
     Csr S;
+    DevBuf<int> rlen;                // truncated row lengths of S per level
     FiberPlan plan[SGK_MAX_DIM][2];  // [dim][0 = fp64, 1 = fp32]
 };
 
