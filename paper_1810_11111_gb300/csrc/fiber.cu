@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     __shared__ FiberGroup sg;
+    static_assert(MODE == FIBER_MATVEC, "the change of basis runs in pyr_kernel");
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const FiberItem item = items[it];
         if (threadIdx.x < (int)(sizeof(FiberGroup) / sizeof(long long)))
@@ -56,43 +57,15 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
                 reinterpret_cast<const long long*>(groups + item.group)[threadIdx.x];
         __syncthreads();
         const int F = kp1 << (sg.nlev - 1);
-        const int src_len = MODE == FIBER_BWD ? H : F;
-        const int lim = MODE == FIBER_BWD ? H : F;
-        const int I = sg.I, nc = item.ncols, st = item.stride;
-        const bool posfast = I < 4;
-        for (int e = threadIdx.x; e < src_len * nc; e += blockDim.x) {
-            int pos, c;
-            if (posfast) {
-                c = e / src_len;
-                pos = e - c * src_len;
-            } else {
-                pos = e / nc;
-                c = e - pos * nc;
-            }
-            const int col = item.col0 + c;
-            const int o = col / I;
-            const int in = col - o * I;
-            const long long a = MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, kp1, I);
-            tile[pos * st + c] = src[a];
-        }
-        __syncthreads();
-        const int nr = item.nrows;
-        for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-            int pos, c;
-            if (posfast) {
-                c = e / nr;
-                pos = e - c * nr;
-            } else {
-                pos = e / nc;
-                c = e - pos * nc;
-            }
-            pos += item.row0;
-            // row pos of the 1D matrix truncated to the fiber's levels: a
-            // fixed trip count (precomputed) so that the index and value
-            // loads are independent of each other and can be in flight
-            // together; four accumulators break the FMA dependency chain
+        const int I = sg.I, nc = item.ncols, st = item.stride, nr = item.nrows;
+        const int* __restrict__ rl = rlen + sg.nlev - 1;
+        // row pos of the 1D matrix truncated to the fiber's levels: a fixed
+        // trip count (precomputed) so that the index and value loads are
+        // independent of each other and can be in flight together; four
+        // accumulators break the FMA dependency chain
+        auto row_dot = [&](int pos, int c) {
             const int q0 = rp[pos];
-            const int qe = q0 + rlen[pos * nlev_max + sg.nlev - 1];
+            const int qe = q0 + rl[pos * nlev_max];
             T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
             int q = q0;
             for (; q + 3 < qe; q += 4) {
@@ -104,15 +77,42 @@ __global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict_
                 a3 += v3 * tile[j3 * st + c];
             }
             for (; q < qe; ++q) a0 += cv[q] * tile[ci[q] * st + c];
-            const T acc = (a0 + a1) + (a2 + a3);
-            (void)lim;
-            const int col = item.col0 + c;
-            const int o = col / I;
-            const int in = col - o * I;
-            const long long a = MODE == FIBER_FWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, kp1, I);
+            return (a0 + a1) + (a2 + a3);
+        };
+        auto store = [&](long long a, T acc) {
             T v = alpha * acc;
             if (accumulate) v += dst[a];
             dst[a] = v;
+        };
+        if (I < 4) {
+            // short inner extent: a warp walks one fiber (contiguous within a
+            // level chunk), lanes over positions
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int c = wid; c < nc; c += nw) {
+                const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
+                for (int pos = lane; pos < F; pos += 32) tile[pos * st + c] = src[chunk_addr(sg, o, pos, in, kp1, I)];
+            }
+            __syncthreads();
+            for (int c = wid; c < nc; c += nw) {
+                const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
+                for (int r = lane; r < nr; r += 32) {
+                    const int pos = item.row0 + r;
+                    store(chunk_addr(sg, o, pos, in, kp1, I), row_dot(pos, c));
+                }
+            }
+        } else {
+            // consecutive threads on consecutive columns (contiguous inner
+            // extent); each thread keeps one column and strides over rows
+            const int c = threadIdx.x % nc, rg = threadIdx.x / nc, nrg = blockDim.x / nc;
+            const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
+            if (rg < nrg)
+                for (int pos = rg; pos < F; pos += nrg) tile[pos * st + c] = src[chunk_addr(sg, o, pos, in, kp1, I)];
+            __syncthreads();
+            if (rg < nrg)
+                for (int r = rg; r < nr; r += nrg) {
+                    const int pos = item.row0 + r;
+                    store(chunk_addr(sg, o, pos, in, kp1, I), row_dot(pos, c));
+                }
         }
         __syncthreads();
     }
@@ -155,29 +155,39 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
         T* X = tile;
         T* A = tile + (size_t)src_len * st;
         T* B = A + (size_t)H * st;
-        for (int e = threadIdx.x; e < src_len * nc; e += blockDim.x) {
-            const int pos = e / nc, c = e - (e / nc) * nc;
-            const int col = item.col0 + c;
-            const int o = col / I, in = col - (col / I) * I;
-            const long long a = MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I);
-            X[pos * st + c] = src[a];
-        }
+        // thread mapping: a warp per column for short inner extents (lanes
+        // over rows), otherwise one column per thread with rows strided;
+        // body(c, o, in, t) runs for t in [0, count) on every column
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int cf = threadIdx.x % nc, rg = threadIdx.x / nc, nrg = blockDim.x / nc;
+        auto for_ct = [&](int count, auto&& body) {
+            if (I < 4) {
+                for (int c = wid; c < nc; c += nw) {
+                    const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
+                    for (int t = lane; t < count; t += 32) body(c, o, in, t);
+                }
+            } else if (rg < nrg) {
+                const int col = item.col0 + cf, o = col / I, in = col - (col / I) * I;
+                for (int t = rg; t < count; t += nrg) body(cf, o, in, t);
+            }
+        };
+        for_ct(src_len, [&](int c, int o, int in, int pos) {
+            X[pos * st + c] = src[MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I)];
+        });
         __syncthreads();
         if (MODE == FIBER_FWD) {
             const T* cur = X;
             T* nxt = A;
             for (int n = 1; n <= Nfull; ++n) {
-                const int npar = 1 << (n - 1);
                 const bool has_detail = n <= Np;
-                for (int e = threadIdx.x; e < npar * 2 * nc; e += blockDim.x) {
-                    const int c = e % nc;
-                    const int t = e / nc;
+                const int doff = KP1 << (n - 1);
+                for_ct(2 << (n - 1), [&](int c, int, int, int t) {
                     const int h = t & 1, par = t >> 1;
                     T pv[KP1], dv[KP1];
 #pragma unroll
                     for (int r = 0; r < KP1; ++r) {
                         pv[r] = cur[(par * KP1 + r) * st + c];
-                        dv[r] = has_detail ? X[((KP1 << (n - 1)) + par * KP1 + r) * st + c] : T(0);
+                        dv[r] = has_detail ? X[(doff + par * KP1 + r) * st + c] : T(0);
                     }
 #pragma unroll
                     for (int s = 0; s < KP1; ++s) {
@@ -186,26 +196,21 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
                         for (int r = 0; r < KP1; ++r) acc += Hm[h][r][s] * pv[r] + Gm[h][r][s] * dv[r];
                         nxt[((2 * par + h) * KP1 + s) * st + c] = acc;
                     }
-                }
+                });
                 __syncthreads();
                 cur = nxt;
                 nxt = (nxt == A) ? B : A;
             }
-            for (int e = threadIdx.x; e < H * nc; e += blockDim.x) {
-                const int pos = e / nc, c = e - (e / nc) * nc;
-                const int col = item.col0 + c;
-                const int o = col / I, in = col - (col / I) * I;
-                dst[full_addr(sg, o, pos, in, H, I)] = cur[pos * st + c];
-            }
+            for_ct(H, [&](int c, int o, int in, int pos) { dst[full_addr(sg, o, pos, in, H, I)] = cur[pos * st + c]; });
         } else {
             // cur holds level-n scaling coefficients; details of levels <= Np
             // go to B (hierarchical layout), the rest are discarded
             T* cur = X;
             T* nxt = A;
             for (int n = Nfull; n >= 1; --n) {
-                const int npar = 1 << (n - 1);
-                for (int e = threadIdx.x; e < npar * nc; e += blockDim.x) {
-                    const int c = e % nc, par = e / nc;
+                const int doff = KP1 << (n - 1);
+                const bool keep = n <= Np;
+                for_ct(1 << (n - 1), [&](int c, int, int, int par) {
                     T x0[KP1], x1[KP1];
 #pragma unroll
                     for (int s = 0; s < KP1; ++s) {
@@ -221,25 +226,17 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
                             sd += Gm[0][r][s] * x0[s] + Gm[1][r][s] * x1[s];
                         }
                         nxt[(par * KP1 + r) * st + c] = sp;
-                        if (n <= Np) B[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
+                        if (keep) B[(doff + par * KP1 + r) * st + c] = sd;
                     }
-                }
+                });
                 __syncthreads();
                 T* t = cur;
                 cur = nxt;
                 nxt = t;
             }
-            for (int e = threadIdx.x; e < KP1 * nc; e += blockDim.x) {
-                const int r = e / nc, c = e - (e / nc) * nc;
-                B[r * st + c] = cur[r * st + c];
-            }
+            for_ct(KP1, [&](int c, int, int, int r) { B[r * st + c] = cur[r * st + c]; });
             __syncthreads();
-            for (int e = threadIdx.x; e < F * nc; e += blockDim.x) {
-                const int pos = e / nc, c = e - (e / nc) * nc;
-                const int col = item.col0 + c;
-                const int o = col / I, in = col - (col / I) * I;
-                dst[chunk_addr(sg, o, pos, in, KP1, I)] = B[pos * st + c];
-            }
+            for_ct(F, [&](int c, int o, int in, int pos) { dst[chunk_addr(sg, o, pos, in, KP1, I)] = B[pos * st + c]; });
         }
         __syncthreads();
     }
@@ -403,8 +400,8 @@ void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T
         break;                                                                                               \
     }
         SGK_FIBER_CASE(FIBER_MATVEC)
-        SGK_FIBER_CASE(FIBER_FWD)
-        SGK_FIBER_CASE(FIBER_BWD)
+        default:
+            throw SgkError{SGK_EINVAL, "launch_fiber: the change of basis runs in launch_pyr"};
 #undef SGK_FIBER_CASE
     }
     check_launch("fiber_kernel");

@@ -208,24 +208,28 @@ __device__ __forceinline__ void block_sum_multi(double (&v)[CH], double* sh) {
     __syncthreads();
 }
 
-// partial[block][c] = sum over this block's elements of V[c][i] w[i]
+// Each block owns GS_E consecutive elements (one per thread), stages the
+// (updated) vector slice in shared memory, and gives every warp whole
+// columns: a lane sums GS_E / 32 products and the warp reduces once per
+// column, so the reduction adds stay a small fraction of the FP64 work.
+constexpr int GS_E = 128;
+
+// partials[block][c] = sum_{t < GS_E} V[c][i0 + t] ws[t]
 template <typename T>
-__device__ void block_partial_dots(const T* __restrict__ V, long long ldv, int ncols, const T* w, long long n,
-                                   double* __restrict__ partials, double* sh) {
-    for (int c0 = 0; c0 < ncols; c0 += CH) {
-        double acc[CH];
+__device__ __forceinline__ void warp_column_dots(const T* __restrict__ V, long long ldv, int ncols, const T* ws,
+                                                 long long i0, double* __restrict__ partials) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < ncols; c += nw) {
+        const T* vc = V + c * ldv + i0;
+        double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) acc[c] = 0.0;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
-            const double wv = (double)w[i];
-#pragma unroll
-            for (int c = 0; c < CH; ++c)
-                if (c0 + c < ncols) acc[c] += (double)V[(c0 + c) * ldv + i] * wv;
+        for (int t = lane; t < GS_E; t += 64) {
+            a0 += (double)vc[t] * (double)ws[t];
+            a1 += (double)vc[t + 32] * (double)ws[t + 32];
         }
-        block_sum_multi(acc, sh);
-        if (threadIdx.x < CH && c0 + (int)threadIdx.x < ncols)
-            partials[(long long)blockIdx.x * ncols + c0 + threadIdx.x] = acc[0];
+        double a = a0 + a1;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) partials[(long long)blockIdx.x * ncols + c] = a;
     }
 }
 
@@ -248,84 +252,104 @@ __device__ void final_columns(const double* partials, int nb, int ncols, double*
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
     for (int c = wid; c < ncols; c += nw) {
-        double a = 0.0;
-        for (int b = lane; b < nb; b += 32) a += __ldcg(partials + (long long)b * ncols + c);
+        double a0 = 0.0, a1 = 0.0;
+        int b = lane;
+        for (; b + 32 < nb; b += 64) {
+            a0 += __ldcg(partials + (long long)b * ncols + c);
+            a1 += __ldcg(partials + (long long)(b + 32) * ncols + c);
+        }
+        if (b < nb) a0 += __ldcg(partials + (long long)b * ncols + c);
+        double a = a0 + a1;
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) out[c] = a;
     }
 }
 
-// w -= V[:, :ncols] h on this thread's elements (four independent chains)
+// ws[t] = w[i0 + t] after w -= V[:, :ncols] h on this block's slice (zero
+// beyond n); four independent FMA chains per element
 template <typename T>
-__device__ __forceinline__ void block_update(const T* __restrict__ V, long long ldv, int ncols, const T* hs, T* w,
-                                             long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        int c = 0;
-        for (; c + 3 < ncols; c += 4) {
-            a0 += V[c * ldv + i] * hs[c];
-            a1 += V[(c + 1) * ldv + i] * hs[c + 1];
-            a2 += V[(c + 2) * ldv + i] * hs[c + 2];
-            a3 += V[(c + 3) * ldv + i] * hs[c + 3];
+__device__ __forceinline__ void slice_update(const T* __restrict__ V, long long ldv, int ncols, const T* hs, T* w,
+                                             long long n, long long i0, T* ws, bool update) {
+    const long long i = i0 + threadIdx.x;
+    T v = T(0);
+    if (i < n) {
+        v = w[i];
+        if (update) {
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int c = 0;
+            for (; c + 3 < ncols; c += 4) {
+                a0 += V[c * ldv + i] * hs[c];
+                a1 += V[(c + 1) * ldv + i] * hs[c + 1];
+                a2 += V[(c + 2) * ldv + i] * hs[c + 2];
+                a3 += V[(c + 3) * ldv + i] * hs[c + 3];
+            }
+            for (; c < ncols; ++c) a0 += V[c * ldv + i] * hs[c];
+            v -= (a0 + a1) + (a2 + a3);
+            w[i] = v;
         }
-        for (; c < ncols; ++c) a0 += V[c * ldv + i] * hs[c];
-        w[i] -= (a0 + a1) + (a2 + a3);
     }
+    ws[threadIdx.x] = v;
+    __syncthreads();
 }
 
 // h1 = V^T w
 template <typename T>
-__global__ void arn_dots_kernel(const T* __restrict__ V, long long ldv, int ncols, const T* __restrict__ w, long long n,
-                                double* __restrict__ partials, unsigned* counter, double* __restrict__ h,
-                                const int* __restrict__ stop) {
+__global__ void __launch_bounds__(GS_E) arn_dots_kernel(const T* __restrict__ V, long long ldv, int ncols, T* w,
+                                                        long long n, double* __restrict__ partials, unsigned* counter,
+                                                        double* __restrict__ h, const int* __restrict__ stop) {
     if (*stop) return;
-    __shared__ double sh[CH * 32];
-    block_partial_dots(V, ldv, ncols, w, n, partials, sh);
+    __shared__ T ws[GS_E];
+    const long long i0 = (long long)blockIdx.x * GS_E;
+    slice_update<T>(V, ldv, ncols, nullptr, w, n, i0, ws, false);
+    // the last slice reads V beyond n only where ws is zero; V has M + 1
+    // full columns, so the reads stay inside the basis allocation
+    warp_column_dots<T>(V, ldv, ncols, ws, i0, partials);
     if (last_block(counter)) final_columns(partials, gridDim.x, ncols, h);
 }
 
 // w -= V h1, then h2 = V^T w
 template <typename T>
-__global__ void arn_update_dots_kernel(const T* __restrict__ V, long long ldv, int ncols, const double* __restrict__ h1,
-                                       T* w, long long n, double* __restrict__ partials, unsigned* counter,
-                                       double* __restrict__ h2, const int* __restrict__ stop) {
+__global__ void __launch_bounds__(GS_E) arn_update_dots_kernel(const T* __restrict__ V, long long ldv, int ncols,
+                                                               const double* __restrict__ h1, T* w, long long n,
+                                                               double* __restrict__ partials, unsigned* counter,
+                                                               double* __restrict__ h2, const int* __restrict__ stop) {
     if (*stop) return;
-    __shared__ double sh[CH * 32];
+    __shared__ T ws[GS_E];
     __shared__ T hs[SGK_MAX_KRYLOV + 1];
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = (T)h1[c];
     __syncthreads();
-    block_update(V, ldv, ncols, hs, w, n);
-    block_partial_dots(V, ldv, ncols, w, n, partials, sh);  // each thread rereads its own elements
+    const long long i0 = (long long)blockIdx.x * GS_E;
+    slice_update<T>(V, ldv, ncols, hs, w, n, i0, ws, true);
+    warp_column_dots<T>(V, ldv, ncols, ws, i0, partials);
     if (last_block(counter)) final_columns(partials, gridDim.x, ncols, h2);
 }
 
 // w -= V h2, ||w||^2, and in the last block: column j of H, the breakdown
 // test and 1 / h_{j+1,j}
 template <typename T>
-__global__ void arn_update_norm_kernel(const T* __restrict__ V, long long ldv, int ncols, const double* __restrict__ h1,
-                                       const double* __restrict__ h2, T* w, long long n, double* __restrict__ partials,
-                                       unsigned* counter, double* __restrict__ H, int j, int M,
-                                       KrylovScalars* __restrict__ ks) {
+__global__ void __launch_bounds__(GS_E) arn_update_norm_kernel(const T* __restrict__ V, long long ldv, int ncols,
+                                                               const double* __restrict__ h1,
+                                                               const double* __restrict__ h2, T* w, long long n,
+                                                               double* __restrict__ partials, unsigned* counter,
+                                                               double* __restrict__ H, int j, int M,
+                                                               KrylovScalars* __restrict__ ks) {
     if (ks->stop) return;
-    __shared__ double sh[CH * 32];
+    __shared__ T ws[GS_E];
     __shared__ T hs[SGK_MAX_KRYLOV + 1];
+    __shared__ double wsum[GS_E / 32];
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = (T)h2[c];
     __syncthreads();
-    block_update(V, ldv, ncols, hs, w, n);
-    double acc[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
-    int k = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double wv = (double)w[i];
-        acc[k] += wv * wv;
-        k = (k + 1) & (CH - 1);
+    const long long i0 = (long long)blockIdx.x * GS_E;
+    slice_update<T>(V, ldv, ncols, hs, w, n, i0, ws, true);
+    double a = (double)ws[threadIdx.x] * (double)ws[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < GS_E / 32; ++k) t += wsum[k];
+        partials[blockIdx.x] = t;
     }
-    double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-#pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = c == 0 ? t : 0.0;
-    block_sum_multi(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
     if (!last_block(counter)) return;
     __shared__ double beta2;
     final_columns(partials, gridDim.x, 1, &beta2);
@@ -810,12 +834,12 @@ void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<
         {
             // classical Gram-Schmidt twice and the norm, three fused kernels
             KTimer kt(ctx, KC_REDUCE);
-            const int nb = reduction_blocks(ctx, n);
-            arn_dots_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.w, n, kw.partials, kw.counter, kw.h1,
+            const int nb = (int)((n + GS_E - 1) / GS_E);
+            arn_dots_kernel<T><<<nb, GS_E, 0, ctx->stream>>>(kw.V, n, j + 1, kw.w, n, kw.partials, kw.counter, kw.h1,
                                                             stop);
-            arn_update_dots_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.w, n, kw.partials,
+            arn_update_dots_kernel<T><<<nb, GS_E, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.w, n, kw.partials,
                                                                    kw.counter, kw.h2, stop);
-            arn_update_norm_kernel<T><<<nb, 256, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.h2, kw.w, n, kw.partials,
+            arn_update_norm_kernel<T><<<nb, GS_E, 0, ctx->stream>>>(kw.V, n, j + 1, kw.h1, kw.h2, kw.w, n, kw.partials,
                                                                    kw.counter, kw.H, j, M, ks);
         }
         check_launch("arnoldi_cgs2");

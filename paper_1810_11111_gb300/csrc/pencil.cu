@@ -266,10 +266,8 @@ __global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, cons
             }
         }
         // 1. load the hierarchical fibers of every set into buffers 0..NSETS-1
-        for (int e = threadIdx.x; e < NSETS * fb; e += blockDim.x) {
-            const int a = e % H;
-            const int f = (e / H) % P;
-            const int set = e / fb;
+        // fiber offset of fiber f: o_f = obase + sum_m r_m H^{d-2-m}
+        auto fiber_offset = [&](int f) {
             long long o = obase, mul = 1;
             int rr = f;
 #pragma unroll
@@ -278,12 +276,23 @@ __global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, cons
                 rr /= KP1;
                 mul *= H;
             }
+            return o;
+        };
+        // address of position a of fiber offset o in the level-chunked layout
+        auto chunk = [&](long long o, int a) {
             const int q = a / KP1;
             const int l = q == 0 ? 0 : 32 - __clz(q);
             const int off = l ? (KP1 << (l - 1)) : 0;
             const int nl = l ? (KP1 << (l - 1)) : KP1;
+            return args.cbase[l] + o * nl + (a - off);
+        };
+#pragma unroll 1
+        for (int sf = 0; sf < NSETS * P; ++sf) {
+            const int set = sf / P, f = sf - (sf / P) * P;
+            const long long o = fiber_offset(f);
             const T* src = reinterpret_cast<const T*>(set < S ? args.u[set] : args.w[set - S]);
-            sm[e] = src[args.cbase[l] + o * nl + (a - off)];
+            T* dstp = sm + (size_t)sf * H;
+            for (int a = threadIdx.x; a < H; a += blockDim.x) dstp[a] = src[chunk(o, a)];
         }
         __syncthreads();
         // 2. reconstruct each set; buffers rotate: a set's input buffer is
@@ -350,22 +359,11 @@ __global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, cons
             // 5. store
             T* dst = reinterpret_cast<T*>(args.out[s]);
             const T* res = buf(rs);
-            for (int e = threadIdx.x; e < fb; e += blockDim.x) {
-                const int a = e % H;
-                const int f = e / H;
-                long long o = obase, mul = 1;
-                int rr = f;
-#pragma unroll
-                for (int m = D - 2; m >= 0; --m) {
-                    o += (rr % KP1) * mul;
-                    rr /= KP1;
-                    mul *= H;
-                }
-                const int q = a / KP1;
-                const int l = q == 0 ? 0 : 32 - __clz(q);
-                const int off = l ? (KP1 << (l - 1)) : 0;
-                const int nl = l ? (KP1 << (l - 1)) : KP1;
-                dst[args.cbase[l] + o * nl + (a - off)] = res[e];
+#pragma unroll 1
+            for (int f = 0; f < P; ++f) {
+                const long long o = fiber_offset(f);
+                const T* rp = res + (size_t)f * H;
+                for (int a = threadIdx.x; a < H; a += blockDim.x) dst[chunk(o, a)] = rp[a];
             }
             __syncthreads();
         }

@@ -431,14 +431,18 @@ void solver_alloc(sgk_solver* s) {
     s->W.alloc(N);
     s->vv.alloc(N);
     SGK_CUDA_CHECK(cudaMemsetAsync(s->U.p, 0, N * sizeof(double), s->ctx->stream));
-    s->V64.alloc((M + 1) * n);
+    // the fused Gram-Schmidt kernels read whole 128-element slices (past n in
+    // the last one, multiplied by zero): pad the basis and keep it finite
+    s->V64.alloc((M + 1) * n + 128);
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->V64.p, 0, s->V64.n * sizeof(double), s->ctx->stream));
     s->w64.alloc(n);
     s->Hm.alloc((M + 1) * M);
     s->h1.alloc(std::max(M, s->opts.gmres_restart) + 1);
     s->h2.alloc(std::max(M, s->opts.gmres_restart) + 1);
     s->ky.alloc(M + 1);
     s->scal.alloc(16);
-    s->partials.alloc((size_t)reduction_blocks(s->ctx, N) * (std::max(M, s->opts.gmres_restart) + 1) + 16);
+    const size_t nblk = std::max<size_t>(reduction_blocks(s->ctx, N), (size_t)((n + 127) / 128));
+    s->partials.alloc(nblk * (std::max(M, s->opts.gmres_restart) + 1) + 16);
     s->expm_ws.alloc(8 * (size_t)M * M);
     s->ks.alloc(S);
     s->counters.alloc(4);
