@@ -233,6 +233,28 @@ int sgk_krylov_export(const sgk_solver* s, double* H, double* V, int64_t cap_V);
  * [1, 128].  y: host array of m doubles.  Synchronises. */
 int sgk_expm_e1(sgk_ctx* ctx, int m, const double* X, double tau, double* y);
 
+/* Largest m accepted by sgk_expm_e1_noalloc. */
+#define SGK_EXPM_NOALLOC_MAX_M 64
+/* The same y = exp(tau X) e_1 as sgk_expm_e1, for callers that must not
+ * allocate device memory while they run: code that is being recorded into a
+ * CUDA graph (where cudaMalloc/cudaFree are not recorded and cudaFree
+ * synchronises the device), latency-critical loops, and processes whose
+ * device memory is owned by another allocator (e.g. a framework's caching
+ * allocator).  The paper has no counterpart; this is a service entry point.
+ * X_dev (m x m, row-major) and y_dev (m doubles) are caller-owned device
+ * arrays on the current device; the work is queued on cuda_stream (NULL =
+ * legacy default stream) and the call returns without synchronising.
+ * Scratch: a fixed 8 * 64 * 64 doubles (256 KB) array compiled into the
+ * library, held by every GPU that loads it until the process exits; m above
+ * SGK_EXPM_NOALLOC_MAX_M is rejected with SGK_EINVAL.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so
+ * make it once on each device before any stream capture.  All calls share
+ * the one array: calls that may overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  No
+ * context, no allocation, no host copy.  Errors: SGK_EINVAL (bad m or null
+ * pointer), SGK_ECUDA (no current device, or the launch failed). */
+int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 // [13/13] Pade approximant (Higham, SIAM J. Matrix Anal. Appl. 26 (2005),
 // with the degree fixed at 13): s = max(0, ceil(log2(||tau H||_1 / theta_13))),
 // then (V - U) R = (V + U) by LU with partial pivoting, then R <- R^2 s times.
+#include <atomic>
 #include <cmath>
 
 #include "sgk_krylov.h"
@@ -807,6 +808,42 @@ void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed
     expm_e1_kernel<<<1, 512, 0, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), ws, y);
     check_launch("expm_e1");
     count_launch(ctx);
+}
+
+// ------------------------------------------- allocation-free expm entry ---
+//
+// Scratch of sgk_expm_e1_noalloc: eight m x m work matrices for m up to
+// SGK_EXPM_NOALLOC_MAX_M, compiled into the library (every GPU that loads it
+// holds the 256 KB until the process exits).  The kernel writes every work
+// entry before reading it, so nothing has to start at zero; concurrent calls
+// share it and must not overlap on the GPU.
+static __device__ __align__(256) double g_expm_scratch[8 * SGK_EXPM_NOALLOC_MAX_M * SGK_EXPM_NOALLOC_MAX_M];
+
+// Device address of g_expm_scratch per device ordinal, looked up on the first
+// call made with that device current (host code cannot pass the symbol).
+static std::atomic<double*> g_expm_scratch_addr[256];
+
+extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream) {
+    if (m < 1 || m > SGK_EXPM_NOALLOC_MAX_M || !X_dev || !y_dev) return SGK_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    double* ws = g_expm_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!ws) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_expm_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return SGK_ECUDA;
+        }
+        ws = static_cast<double*>(p);
+        g_expm_scratch_addr[dev].store(ws, std::memory_order_release);
+    }
+    expm_e1_kernel<<<1, 512, 0, static_cast<cudaStream_t>(cuda_stream)>>>(X_dev, m, nullptr, m, tau,
+                                                                          pade13_coefficients(), ws, y_dev);
+    if (cudaGetLastError() != cudaSuccess) return SGK_ECUDA;
+    return SGK_OK;
 }
 
 template <typename T>

@@ -75,7 +75,9 @@ _SIGS = {
     "sgk_krylov_expv": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _c_int_p]),
     "sgk_krylov_export": (ctypes.c_int, [_P, _c_double_p, _c_double_p, ctypes.c_int64]),
     "sgk_expm_e1": (ctypes.c_int, [_P, ctypes.c_int, _c_double_p, ctypes.c_double, _c_double_p]),
+    "sgk_expm_e1_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_double, _P, _P]),
 }
+EXPM_NOALLOC_MAX_M = 64
 
 _lib = None
 

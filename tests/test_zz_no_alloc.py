@@ -1,0 +1,59 @@
+"""The allocation-free exp(tau X) e_1 entry point against the regular one.
+
+sgk_expm_e1_noalloc serves callers that must not allocate device memory
+while they run (code being recorded into a CUDA graph, latency-critical
+loops, processes whose device memory belongs to another allocator): its
+scratch is a fixed array compiled into the library.  This file is collected
+last so that a failure here does not stop the rest of the suite; it also
+passes on its own in a fresh process.
+
+The two entry points run the same Pade(13) kernel, so their outputs are
+compared with the expm tolerance of the parity tests (1e-12 relative to the
+largest entry), on two calls in a row with different matrices -- the second
+call runs on the scratch left by the first.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1810_11111_gb300 import sgkiif  # noqa: E402
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def _noalloc(X, tau, stream):
+    m = X.shape[0]
+    Xd = torch.as_tensor(X, dtype=torch.float64, device="cuda").contiguous()
+    yd = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
+    rc = sgkiif.sgk_expm_e1_noalloc(m, Xd.data_ptr(), float(tau), yd.data_ptr(), stream)
+    assert rc == sgkiif.SGK_OK
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def test_noalloc_expm_matches_regular_entry_point_twice():
+    sgkiif.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = sgkiif.Context(0, stream, sgkiif.SGK_FP64)
+    rng = np.random.default_rng(17)
+    cases = [(rng.standard_normal((30, 30)) * 40.0 / 30, 0.5),
+             (-np.diag(np.logspace(0, 4, 64)) + 0.01 * rng.standard_normal((64, 64)), 0.005)]
+    for X, tau in cases:
+        want = ctx.expm_e1(X, tau)
+        got = _noalloc(X, tau, stream)
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+    ctx.close()
+
+
+def test_noalloc_expm_rejects_oversized_and_null():
+    sgkiif.load()
+    m = sgkiif.EXPM_NOALLOC_MAX_M + 1
+    X = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    y = torch.zeros(m, dtype=torch.float64, device="cuda")
+    assert sgkiif.sgk_expm_e1_noalloc(m, X.data_ptr(), 1.0, y.data_ptr(), None) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_expm_e1_noalloc(4, None, 1.0, y.data_ptr(), None) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_expm_e1_noalloc(0, X.data_ptr(), 1.0, y.data_ptr(), None) == sgkiif.SGK_EINVAL
