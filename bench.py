@@ -121,6 +121,18 @@ def layout_sizes(d, n, k):
     return [H ** i * sparse_dof(d - i) for i in range(d + 1)]
 
 
+# DRAM bytes (read + write) of one Jacobian launch of the pencil kernel from
+# the committed ncu capture, keyed by (d, level, degree, precision)
+PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56.647168e6 + 0.162048e6}
+
+
+def pencil_q(cfg):
+    """Gauss points per direction of the reaction quadrature, ceil((p k + k + 1)/2)."""
+    p = max((sum(e) for terms in cfg["reaction"] for _, e in terms), default=0)
+    k = cfg["k"]
+    return max(1, (p * k + k + 1 + 1) // 2)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -258,39 +270,63 @@ def native(args, rank, world, local_rank):
     total_ms = float(t)
     value = dof * S * args.steps * world / (total_ms / 1e3)
 
-    # roofline of the dominant kernel class: algorithmic bytes per launch over
-    # its event-timed average launch time in the timed region
+    # roofline of the dominant kernel class: algorithmic work per launch over
+    # its event-timed average launch time in the profiled pass
     peaks, peak_kind = measured_peaks()
     nF = args.steps * 1 + (ps1["newton_iters"] - ps0["newton_iters"]) + args.steps  # predictor + residuals
     nJ = ps1["inner_iters"] - ps0["inner_iters"]
     sizes = layout_sizes(cfg["d"], cfg["n"], cfg["k"])
-    full = sizes[-1]
     ms, nl = kprof[dominant]
+    d, kp1, N = cfg["d"], cfg["k"] + 1, cfg["n"]
+    q = pencil_q(cfg)
     # per pass of the reaction term: the fused last-direction (pencil) kernel
     # reads R_{d-1}(U) (and R_{d-1}(w) for a Jacobian product) and writes
-    # G_{d-1}; the fiber transforms of directions 0..d-2 read R_i and write
-    # R_{i+1} (and the transpose); the Krylov matvec (FP64 in both modes)
-    # reads x and writes y
+    # G_{d-1}; its arithmetic is the sum-factorised quadrature of every finest
+    # cell plus the two-scale pyramids of every fiber.  The fiber transforms
+    # of directions 0..d-2 read R_i and write R_{i+1}; the Krylov matvec (FP64
+    # in both modes) reads x and writes y.
+    bytes_algo, flops_algo = None, None
     if dominant == "cell_quadrature":
-        last = sizes[cfg["d"] - 1]
-        algo = (nF * 2 * S * last + nJ * 3 * S * last) * elem
+        last = sizes[d - 1]
+        bytes_algo = (nF * 2 * S * last + nJ * 3 * S * last) * elem
+        cells = (1 << N) ** d
+        pencils = (1 << N) ** (d - 1)
+        P = kp1 ** (d - 1)
+        fwd = sum(q ** (m + 1) * kp1 ** (d - m) for m in range(d))  # FMAs per cell and set
+        pyr = 2 * kp1 * kp1 * ((1 << (N + 1)) - 2)                  # FMAs per fiber and direction
+        fma_F = cells * S * 2 * fwd + pencils * (S * P + S * P) * pyr
+        fma_J = cells * S * 3 * fwd + pencils * (2 * S * P + S * P) * pyr
+        flops_algo = 2.0 * (nF * fma_F + nJ * fma_J)
     elif dominant in ("to_finest", "from_finest"):
-        algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(cfg["d"] - 1)) * elem
+        bytes_algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(d - 1)) * elem
     elif dominant == "matvec":
-        algo = (nl / cfg["d"]) * 2 * dof * 8
-    else:
-        algo = None
+        bytes_algo = (nl / d) * 2 * dof * 8
     roofline = None
-    if algo is not None and nl > 0 and ms > 0:
-        per_launch = algo / nl
-        achieved = per_launch / (ms / nl / 1e3) / 1e9
-        roofline = {"kernel_class": dominant, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "peak_source": peak_kind, "algorithmic_bytes_per_launch": per_launch,
-                    "avg_launch_us": ms / nl * 1e3, "launches": nl,
-                    "share_of_profiled_step_time": ms / prof_ms,
-                    "timing": "CUDA events around each launch of the class, on the library stream, over a "
-                              "second pass of the same timed steps with graph replay off"}
+    if nl > 0 and ms > 0 and (bytes_algo or flops_algo):
+        t = ms / 1e3
+        common = {"kernel_class": dominant, "avg_launch_us": ms / nl * 1e3, "launches": nl,
+                  "share_of_profiled_step_time": ms / prof_ms,
+                  "timing": "CUDA events around each launch of the class, on the library stream, over a "
+                            "second pass of the same timed steps with graph replay off"}
+        if flops_algo:
+            clock = (clk or {}).get("sm_max_mhz") or 2070.0
+            peak = 152 * 128 * 2 * clock * 1e6 / 1e12
+            achieved = flops_algo / t / 1e12
+            roofline = dict(common, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                            frac=achieved / peak,
+                            peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                            algorithmic_flops_per_launch=flops_algo / nl,
+                            algorithmic_bytes_per_launch=bytes_algo / nl,
+                            hbm_view={"achieved_gbs": bytes_algo / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                                      "frac": bytes_algo / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_kind},
+                            traffic=PENCIL_TRAFFIC.get((d, N, cfg["k"], args.precision)),
+                            traffic_note="dram read + write of one Jacobian launch, ncu cold capture "
+                                         "(profiles/pencil_kernel_cubic3d_l6k2_fp32.md)")
+        else:
+            achieved = bytes_algo / t / 1e9
+            roofline = dict(common, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                            frac=achieved / peaks["hbm_gbs"], traffic=None, peak_source=peak_kind,
+                            algorithmic_bytes_per_launch=bytes_algo / nl)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

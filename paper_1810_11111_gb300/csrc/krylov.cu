@@ -215,22 +215,36 @@ __device__ __forceinline__ void block_sum_multi(double (&v)[CH], double* sh) {
 // column, so the reduction adds stay a small fraction of the FP64 work.
 constexpr int GS_E = 128;
 
-// partials[block][c] = sum_{t < GS_E} V[c][i0 + t] ws[t]
+// partials[block][c] = sum_{t < GS_E} V[c][i0 + t] ws[t].  A warp takes four
+// columns at a time (c, c + nw, c + 2 nw, c + 3 nw) so that their loads,
+// FMAs and shuffle reductions interleave instead of waiting on one another.
 template <typename T>
 __device__ __forceinline__ void warp_column_dots(const T* __restrict__ V, long long ldv, int ncols, const T* ws,
                                                  long long i0, double* __restrict__ partials) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = wid; c < ncols; c += nw) {
-        const T* vc = V + c * ldv + i0;
-        double a0 = 0.0, a1 = 0.0;
+    double wl[GS_E / 32];
 #pragma unroll
-        for (int t = lane; t < GS_E; t += 64) {
-            a0 += (double)vc[t] * (double)ws[t];
-            a1 += (double)vc[t + 32] * (double)ws[t + 32];
+    for (int k = 0; k < GS_E / 32; ++k) wl[k] = (double)ws[lane + 32 * k];
+    for (int c0 = wid; c0 < ncols; c0 += 4 * nw) {
+        double a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * nw;
+            a[u] = 0.0;
+            if (c < ncols) {
+                const T* vc = V + c * ldv + i0;
+#pragma unroll
+                for (int k = 0; k < GS_E / 32; ++k) a[u] += (double)vc[lane + 32 * k] * wl[k];
+            }
         }
-        double a = a0 + a1;
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) partials[(long long)blockIdx.x * ncols + c] = a;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] += __shfl_down_sync(0xffffffffu, a[u], o);
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u * nw < ncols) partials[(long long)blockIdx.x * ncols + c0 + u * nw] = a[u];
     }
 }
 
@@ -248,21 +262,25 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
     return is_last;
 }
 
-// out[c] = sum_b partials[b][c] in a fixed order (one warp per column)
+// out[c] = sum_b partials[b][c] in a fixed order (a warp per column, four
+// columns interleaved)
 __device__ void final_columns(const double* partials, int nb, int ncols, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
-    for (int c = wid; c < ncols; c += nw) {
-        double a0 = 0.0, a1 = 0.0;
-        int b = lane;
-        for (; b + 32 < nb; b += 64) {
-            a0 += __ldcg(partials + (long long)b * ncols + c);
-            a1 += __ldcg(partials + (long long)(b + 32) * ncols + c);
-        }
-        if (b < nb) a0 += __ldcg(partials + (long long)b * ncols + c);
-        double a = a0 + a1;
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) out[c] = a;
+    for (int c0 = wid; c0 < ncols; c0 += 4 * nw) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = lane; b < nb; b += 32)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u * nw < ncols) a[u] += __ldcg(partials + (long long)b * ncols + c0 + u * nw);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] += __shfl_down_sync(0xffffffffu, a[u], o);
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u * nw < ncols) out[c0 + u * nw] = a[u];
     }
 }
 
