@@ -137,6 +137,10 @@ int sgk_index_lookup(const sgk_index* idx, const int32_t* levels, int64_t count,
  * SGK_DIRICHLET0.  Errors: SGK_EINVAL. */
 int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, int bc, double sigma,
                           sgk_op** out);
+/* Multiply-adds of one sgk_matvec: the entries of the 1D matrix rows each
+ * output coefficient visits, summed over directions (the algorithmic work of
+ * the unidirectional matvec of Section 4); -1 for a null handle. */
+int64_t sgk_operator_madds(const sgk_op* op);
 int sgk_operator_destroy(sgk_op* op);
 /* Copy the 1D hierarchical matrix S (size H x H, H = (k+1) 2^n, row-major,
  * zeros included) to host `out` (cap >= H*H doubles).  Synchronises. */
@@ -244,16 +248,112 @@ int sgk_expm_e1(sgk_ctx* ctx, int m, const double* X, double tau, double* y);
  * X_dev (m x m, row-major) and y_dev (m doubles) are caller-owned device
  * arrays on the current device; the work is queued on cuda_stream (NULL =
  * legacy default stream) and the call returns without synchronising.
- * Scratch: a fixed 8 * 64 * 64 doubles (256 KB) array compiled into the
- * library, held by every GPU that loads it until the process exits; m above
- * SGK_EXPM_NOALLOC_MAX_M is rejected with SGK_EINVAL.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so
- * make it once on each device before any stream capture.  All calls share
- * the one array: calls that may overlap on the GPU (different streams, or
- * different host threads) race and must be serialised by the caller.  No
+ * Scratch: for m <= 56 the work matrices live in the shared memory of one
+ * eight-CTA thread-block cluster (up to 196 KB per CTA) and calls are
+ * independent of each other.  For 56 < m <= 64 they live in a fixed
+ * 8 * 64 * 64 doubles (256 KB) array compiled into the library, held by
+ * every GPU that loads it until the process exits; m above
+ * SGK_EXPM_NOALLOC_MAX_M is rejected with SGK_EINVAL.  The first such call on
+ * a device looks up that array's device address (cudaGetSymbolAddress), so
+ * make it once on each device before any stream capture.  Calls with
+ * m > 56 share the one array: those that may overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  No
  * context, no allocation, no host copy.  Errors: SGK_EINVAL (bad m or null
  * pointer), SGK_ECUDA (no current device, or the launch failed). */
 int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream);
+
+/* -------------------------------------------------------------- serving */
+
+/* A request loop that runs whole IIF2 solves (the problem of Section 2 with
+ * the scheme of eq. krylov5, one per request) as they arrive.  The paper has
+ * no counterpart; this is the service around the method.
+ *
+ * Continuous batching: a server owns nworkers worker threads, each with its
+ * own CUDA stream on one device.  A submitted request waits in a queue until
+ * a worker is idle and its estimated device memory (sgk_estimate_bytes) fits
+ * in what the admitted requests leave of the budget; requests are admitted in
+ * arrival order, except that a request that does not fit yet lets later ones
+ * that do fit go first unless it has waited longer than the aging limit.
+ * Admitted requests run concurrently, their kernels overlapping on the GPU;
+ * each keeps its Krylov basis and state on the device until it finishes, and
+ * its memory returns to the budget when it does.  Results do not depend on
+ * what else runs: a request gives the same coefficients alone and in a mix
+ * on a server with the same worker count. */
+typedef struct sgk_server sgk_server;
+
+/* Initial data of one species: coefficients (host, dof doubles) if coeffs is
+ * not NULL, else the L2 projection of const_term + sum_t amp[t] prod_m
+ * g_{t,m}(2 pi wavenum[t*d+m] x_m) as for sgk_project_separable. */
+typedef struct sgk_init {
+    const double* coeffs;
+    int nterms;
+    const double* amp;
+    const int* wavenum;
+    const int* kind;
+    double const_term;
+} sgk_init;
+
+typedef struct sgk_request {
+    int d, n, k;             /* sparse grid V_N^k in d dimensions (as sgk_index_build) */
+    int nspecies;            /* 1 .. SGK_MAX_SPECIES */
+    int bc;                  /* SGK_PERIODIC | SGK_DIRICHLET0 */
+    const double* kappa;     /* [nspecies * d] diagonal diffusion per species */
+    sgk_reaction reaction;   /* as for sgk_solver_create (nspecies must match) */
+    int krylov_m;            /* 1 .. SGK_MAX_KRYLOV */
+    double dt;               /* > 0 */
+    int nsteps;              /* >= 0 IIF2 steps */
+    int precision;           /* SGK_FP64 | SGK_MIXED */
+    sgk_init init[SGK_MAX_SPECIES];
+} sgk_request;
+
+typedef struct sgk_result_info {
+    int status;              /* SGK_OK or the solve's error code */
+    int nspecies;
+    int64_t dof;             /* per species */
+    int64_t steps;           /* steps taken */
+    int64_t est_bytes;       /* device memory reserved at admission */
+    double queue_ms;         /* submit -> admission */
+    double run_ms;           /* admission -> result on the host */
+    double latency_ms;       /* submit -> result on the host */
+    int worker;              /* worker that ran it */
+    int64_t newton_iters, inner_iters;
+} sgk_result_info;
+
+typedef struct sgk_server_stats {
+    int64_t submitted, completed, failed, rejected;
+    int64_t queued, running;
+    int64_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+    int max_concurrent;      /* most requests running at once so far */
+} sgk_server_stats;
+
+/* Device memory a request will hold while it runs (index, operators, solver
+ * workspace including the finest-grid reaction buffers), in bytes; -1 for an
+ * invalid shape.  Host only. */
+int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int precision, int has_reaction);
+
+/* Start a server on device with nworkers (1 .. 64) workers and a device
+ * memory budget of mem_budget_bytes (0 = 80% of the memory free at start).
+ * aging_ms: how long a request that does not fit may be overtaken (<= 0:
+ * 2000 ms).  Errors: SGK_EINVAL, SGK_ECUDA, SGK_ENOMEM. */
+int sgk_server_create(int device, int nworkers, int64_t mem_budget_bytes, double aging_ms, sgk_server** out);
+/* Queue a request; every host array it points to is copied before the call
+ * returns.  *ticket identifies it.  Errors: SGK_EINVAL (bad request),
+ * SGK_ENOMEM (its estimate exceeds the whole budget: rejected). */
+int sgk_server_submit(sgk_server* srv, const sgk_request* req, int64_t* ticket);
+/* 1 if the request has finished, 0 if not, negative for an unknown ticket. */
+int sgk_server_poll(sgk_server* srv, int64_t ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a request; on completion fill
+ * info (may be NULL) and copy its final coefficients (species-stacked,
+ * nspecies * dof doubles) to out (may be NULL; cap in doubles), then forget
+ * the ticket.  Returns SGK_OK once finished (the solve's own status is in
+ * info->status), SGK_ETIMEOUT if still running, SGK_EINVAL for an unknown
+ * ticket or a too-small buffer. */
+int sgk_server_wait(sgk_server* srv, int64_t ticket, double timeout_ms, sgk_result_info* info, double* out,
+                    int64_t cap);
+int sgk_server_get_stats(sgk_server* srv, sgk_server_stats* out);
+/* Finish every queued and running request, then stop the workers. */
+int sgk_server_destroy(sgk_server* srv);
 
 #ifdef __cplusplus
 }

@@ -46,12 +46,13 @@ sgk_ctx::~sgk_ctx() {
         cudaEventDestroy(p.second.second);
     }
     for (auto e : ev_pool) cudaEventDestroy(e);
+    if (hscal) cudaFreeHost(hscal);
     if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
 void build_index_on_device(sgk_index* idx);
 void index_lookup_on_device(const sgk_index* idx, const int32_t* levels, int64_t count, int64_t* out);
-void build_matvec_plans(sgk_op* op);
+
 
 namespace {
 
@@ -102,6 +103,12 @@ int sgk_ctx_create(sgk_ctx** out, int device, void* cuda_stream, int precision) 
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)optin;
+    if (cudaMallocHost(reinterpret_cast<void**>(&c->hscal), 16 * sizeof(double)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->hscal = nullptr;
+        delete c;
+        return SGK_ENOMEM;
+    }
     if (!c->stream) {
         // a blocking stream: ordered with the legacy default stream, and
         // capturable into CUDA graphs (the legacy stream itself is not)
@@ -253,11 +260,13 @@ int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kapp
             op->rlen.upload(rl, ctx->stream);
             SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
         }
-        build_matvec_plans(op.get());
+        build_gmv_tables(op.get());
         *out = op.release();
         return SGK_OK;
     });
 }
+
+int64_t sgk_operator_madds(const sgk_op* op) { return op ? op->madds : -1; }
 
 int sgk_operator_destroy(sgk_op* op) {
     delete op;

@@ -1,22 +1,20 @@
-// Fiber engine: applies a 1D sparse matrix along one direction of a
-// sparse-grid (or partly full-grid) coefficient array.
+// Fiber engine for the change of basis along one direction of a sparse-grid
+// (or partly full-grid) coefficient array.
 //
-// This is the unidirectional principle of Section 4: every direction-i
-// operation of the method -- the SIPG matvec (A = -sum_i kappa_i S along i),
-// the change of basis to the finest-cell Legendre basis used by the reaction
-// term, and its transpose -- acts on 1D fibers.  For direction i, the blocks
-// sharing the levels of the other directions form a group; stacked along i
-// they hold (outer x fiber x inner) arrays whose fiber index is the 1D
-// hierarchical index a_i < (k+1) 2^{N'}, N' = N - sum_{m != i} l_m (the
-// "chunked" side), or a finest-cell Legendre index y < (k+1) 2^N (the "full"
-// side).  Each chunk (one level) is contiguous, so a fiber tile is gathered
-// with unit-stride loads along the inner extent.
+// This is the unidirectional principle of Section 4 applied to the reaction
+// term: the map from hierarchical coefficients to finest-cell Legendre
+// coefficients, and its transpose, act on 1D fibers one direction at a time.
+// For direction i, the blocks sharing the levels of the other directions form
+// a group; stacked along i they hold (outer x fiber x inner) arrays whose
+// fiber index is the 1D hierarchical index a_i < (k+1) 2^{N'}, N' = N -
+// sum_{m != i} l_m (the "chunked" side), or a finest-cell Legendre index
+// y < (k+1) 2^N (the "full" side).  Each chunk (one level) is contiguous, so
+// a fiber tile is gathered with unit-stride loads along the inner extent.
 //
 // Work items are (group, column range) tiles sized to fit shared memory; a
 // grid-stride loop over items sorted by cost keeps every SM busy.  A CTA
-// stages the source fibers of its tile in shared memory, then each output
-// element is a CSR row of the 1D matrix (truncated to the fiber's levels)
-// dotted with a tile column.
+// stages the source fibers of its tile in shared memory and runs the
+// two-scale pyramid on them.
 #include <algorithm>
 
 #include "sgk_internal.h"
@@ -37,85 +35,6 @@ __device__ __forceinline__ long long chunk_addr(const FiberGroup& g, int o, int 
 
 __device__ __forceinline__ long long full_addr(const FiberGroup& g, int o, int pos, int in, int H, int I) {
     return g.fbase + ((long long)o * H + pos) * I + in;
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) fiber_kernel(const FiberItem* __restrict__ items, int nitems,
-                                                    const FiberGroup* __restrict__ groups, const T* __restrict__ src,
-                                                    T* __restrict__ dst, const int* __restrict__ rp,
-                                                    const int* __restrict__ ci, const T* __restrict__ cv,
-                                                    const int* __restrict__ rlen, int nlev_max, int H, int kp1,
-                                                    T alpha, int accumulate) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
-    __shared__ FiberGroup sg;
-    static_assert(MODE == FIBER_MATVEC, "the change of basis runs in pyr_kernel");
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const FiberItem item = items[it];
-        if (threadIdx.x < (int)(sizeof(FiberGroup) / sizeof(long long)))
-            reinterpret_cast<long long*>(&sg)[threadIdx.x] =
-                reinterpret_cast<const long long*>(groups + item.group)[threadIdx.x];
-        __syncthreads();
-        const int F = kp1 << (sg.nlev - 1);
-        const int I = sg.I, nc = item.ncols, st = item.stride, nr = item.nrows;
-        const int* __restrict__ rl = rlen + sg.nlev - 1;
-        // row pos of the 1D matrix truncated to the fiber's levels: a fixed
-        // trip count (precomputed) so that the index and value loads are
-        // independent of each other and can be in flight together; four
-        // accumulators break the FMA dependency chain
-        auto row_dot = [&](int pos, int c) {
-            const int q0 = rp[pos];
-            const int qe = q0 + rl[pos * nlev_max];
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-            int q = q0;
-            for (; q + 3 < qe; q += 4) {
-                const int j0 = ci[q], j1 = ci[q + 1], j2 = ci[q + 2], j3 = ci[q + 3];
-                const T v0 = cv[q], v1 = cv[q + 1], v2 = cv[q + 2], v3 = cv[q + 3];
-                a0 += v0 * tile[j0 * st + c];
-                a1 += v1 * tile[j1 * st + c];
-                a2 += v2 * tile[j2 * st + c];
-                a3 += v3 * tile[j3 * st + c];
-            }
-            for (; q < qe; ++q) a0 += cv[q] * tile[ci[q] * st + c];
-            return (a0 + a1) + (a2 + a3);
-        };
-        auto store = [&](long long a, T acc) {
-            T v = alpha * acc;
-            if (accumulate) v += dst[a];
-            dst[a] = v;
-        };
-        if (I < 4) {
-            // short inner extent: a warp walks one fiber (contiguous within a
-            // level chunk), lanes over positions
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int c = wid; c < nc; c += nw) {
-                const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
-                for (int pos = lane; pos < F; pos += 32) tile[pos * st + c] = src[chunk_addr(sg, o, pos, in, kp1, I)];
-            }
-            __syncthreads();
-            for (int c = wid; c < nc; c += nw) {
-                const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
-                for (int r = lane; r < nr; r += 32) {
-                    const int pos = item.row0 + r;
-                    store(chunk_addr(sg, o, pos, in, kp1, I), row_dot(pos, c));
-                }
-            }
-        } else {
-            // consecutive threads on consecutive columns (contiguous inner
-            // extent); each thread keeps one column and strides over rows
-            const int c = threadIdx.x % nc, rg = threadIdx.x / nc, nrg = blockDim.x / nc;
-            const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
-            if (rg < nrg)
-                for (int pos = rg; pos < F; pos += nrg) tile[pos * st + c] = src[chunk_addr(sg, o, pos, in, kp1, I)];
-            __syncthreads();
-            if (rg < nrg)
-                for (int r = rg; r < nr; r += nrg) {
-                    const int pos = item.row0 + r;
-                    store(chunk_addr(sg, o, pos, in, kp1, I), row_dot(pos, c));
-                }
-        }
-        __syncthreads();
-    }
 }
 
 // Change of basis along one direction by the two-scale (pyramid) relations.
@@ -338,10 +257,10 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
         const int dst_len = mode == FIBER_FWD ? H : F;
         long long cols = (long long)g.O * g.I;
         SGK_REQUIRE(cols < (1LL << 31), SGK_EUNSUPPORTED, "plan: too many fibers in one group");
-        // the change of basis runs the two-scale pyramid, which needs the
-        // source fiber plus two full-length work buffers per column
-        const bool pyr = mode != FIBER_MATVEC;
-        const int tile_rows = pyr ? src_len + 2 * H : src_len;
+        // the two-scale pyramid needs the source fiber plus two full-length
+        // work buffers per column
+        SGK_REQUIRE(mode == FIBER_FWD || mode == FIBER_BWD, SGK_EINVAL, "plan: mode must be FWD or BWD");
+        const int tile_rows = src_len + 2 * H;
         long long fit = (long long)(smem_budget / ((size_t)tile_rows * elem_bytes)) - 1;
         int maxc = (int)std::min<long long>(64, std::max<long long>(1, fit));
         for (long long c0 = 0; c0 < cols; c0 += maxc) {
@@ -350,20 +269,12 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
             it.col0 = (int)c0;
             it.ncols = (int)std::min<long long>(maxc, cols - c0);
             it.stride = it.ncols | 1;
-            // split the output rows so that one item computes about 1024
-            // outputs, 128 in FP64 whose pipe is ~60x narrower (long fibers
-            // with few columns would otherwise serialise on one SM); every
-            // split item stages the whole source fiber.  A pyramid item
-            // computes whole fibers.
-            const int target = elem_bytes == 8 ? 128 : 1024;
-            const int rows_per = pyr ? dst_len : std::max(1, std::min(dst_len, target / it.ncols));
-            for (int r0 = 0; r0 < dst_len; r0 += rows_per) {
-                it.row0 = r0;
-                it.nrows = std::min(rows_per, dst_len - r0);
-                validate_item(g, it, kp1, H, mode, src_size, dst_size);
-                items.push_back(it);
-                cost.push_back((long long)src_len * it.ncols + (long long)it.nrows * it.ncols * 8);
-            }
+            // an item computes whole fibers
+            it.row0 = 0;
+            it.nrows = dst_len;
+            validate_item(g, it, kp1, H, mode, src_size, dst_size);
+            items.push_back(it);
+            cost.push_back((long long)src_len * it.ncols + (long long)it.nrows * it.ncols * 8);
             smem = std::max(smem, (size_t)tile_rows * it.stride * elem_bytes);
         }
         plan.max_src_len = std::max(plan.max_src_len, src_len);
@@ -381,38 +292,6 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
     SGK_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
-template <typename T>
-void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
-                  const T* cv, const int* rlen, int nlev_max, int H, int kp1, T alpha, int accumulate) {
-    if (plan.nitems == 0) return;
-    const int grid = std::min(plan.nitems, ctx->num_sms * 8);
-    const size_t smem = plan.smem_bytes;
-    KTimer kt(ctx, mode);  // FIBER_MATVEC / FWD / BWD coincide with KC_MATVEC / FWD / BWD
-    switch (mode) {
-#define SGK_FIBER_CASE(M)                                                                                    \
-    case M: {                                                                                                \
-        if (smem > 48 * 1024)                                                                                \
-            SGK_CUDA_CHECK(cudaFuncSetAttribute(fiber_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                (int)smem));                                                 \
-        fiber_kernel<T, M><<<grid, 256, smem, ctx->stream>>>(plan.items.p, plan.nitems, plan.groups.p, src, dst, \
-                                                              rp, ci, cv, rlen, nlev_max, H, kp1, alpha,     \
-                                                              accumulate);                                   \
-        break;                                                                                               \
-    }
-        SGK_FIBER_CASE(FIBER_MATVEC)
-        default:
-            throw SgkError{SGK_EINVAL, "launch_fiber: the change of basis runs in launch_pyr"};
-#undef SGK_FIBER_CASE
-    }
-    check_launch("fiber_kernel");
-    count_launch(ctx);
-}
-
-template void launch_fiber<double>(sgk_ctx*, const FiberPlan&, int, const double*, double*, const int*, const int*,
-                                   const double*, const int*, int, int, int, double, int);
-template void launch_fiber<float>(sgk_ctx*, const FiberPlan&, int, const float*, float*, const int*, const int*,
-                                  const float*, const int*, int, int, int, float, int);
-
 // ------------------------------------------------------------- operator ---
 
 // Rank of a tuple among lexicographic tuples of its length with sum <= n.
@@ -426,52 +305,4 @@ static long long rank_host(const std::vector<int>& l, int n) {
     return r;
 }
 
-void build_matvec_plans(sgk_op* op) {
-    const sgk_index* idx = op->idx;
-    const int d = idx->d, N = idx->n, kp1 = idx->k + 1;
-    for (int i = 0; i < d; ++i) {
-        std::vector<FiberGroup> groups;
-        for (int64_t t = 0; t < idx->ntuples; ++t) {
-            const int32_t* l = &idx->levels[t * d];
-            if (l[i] != 0) continue;
-            FiberGroup g{};
-            int rest = 0, O = 1, I = 1;
-            for (int m = 0; m < d; ++m)
-                if (m != i) {
-                    rest += l[m];
-                    if (m < i) O *= level_count(l[m], kp1);
-                    else I *= level_count(l[m], kp1);
-                }
-            g.nlev = N - rest + 1;
-            g.O = O;
-            g.I = I;
-            std::vector<int> lv(l, l + d);
-            for (int li = 0; li < g.nlev; ++li) {
-                lv[i] = li;
-                g.cbase[li] = idx->offsets[rank_host(lv, N)];
-            }
-            groups.push_back(g);
-        }
-        finalize_plan(op->plan[i][0], groups, kp1, op->H, FIBER_MATVEC, sizeof(double), 64 * 1024, idx->dof, idx->dof,
-                      op->ctx->stream);
-        finalize_plan(op->plan[i][1], groups, kp1, op->H, FIBER_MATVEC, sizeof(float), 64 * 1024, idx->dof, idx->dof,
-                      op->ctx->stream);
-    }
-}
-
 long long tuple_rank(const std::vector<int>& l, int n) { return rank_host(l, n); }
-
-template <typename T>
-void op_matvec(const sgk_op* op, const T* x, T* y) {
-    const int d = op->idx->d;
-    const int prec = sizeof(T) == 8 ? 0 : 1;
-    for (int i = 0; i < d; ++i) {
-        const T* vals = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->S.d_val.p)
-                                       : reinterpret_cast<const T*>(op->S.d_valf.p);
-        launch_fiber<T>(op->ctx, op->plan[i][prec], FIBER_MATVEC, x, y, op->S.d_ptr.p, op->S.d_col.p, vals,
-                        op->rlen.p, op->idx->n + 1, op->H, op->idx->k + 1, T(-op->kappa[i]), i > 0 ? 1 : 0);
-    }
-}
-
-template void op_matvec<double>(const sgk_op*, const double*, double*);
-template void op_matvec<float>(const sgk_op*, const float*, float*);

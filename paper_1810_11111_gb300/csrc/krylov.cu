@@ -539,6 +539,232 @@ __global__ void __launch_bounds__(512) expm_e1_kernel(const double* __restrict__
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = R[i * m];
 }
 
+// Cluster version of the same computation for m <= EXPM_CLUSTER_MAX_M: eight
+// CTAs on eight SMs (one thread-block cluster), each holding full copies of
+// the work matrices in its shared memory.  A product C = A B is split by
+// rows; each CTA writes its rows into every CTA's copy of C through
+// distributed shared memory and the cluster barrier (a hardware barrier, no
+// spin loop) publishes them.  The elementwise Pade combinations and the LU
+// factorisation of the denominator run redundantly in every CTA (identical
+// operations in identical order, so the copies stay bitwise equal); the
+// right-hand sides of the solve are split by columns.  FP64 throughput per SM
+// is what bounds the single-CTA kernel; eight SMs share the products.
+constexpr int XCL = 8;
+constexpr int XTH = 256;
+constexpr int EXPM_CLUSTER_MAX_M = 56;  // 8 m^2 doubles per CTA within 227 KB
+
+// Cluster primitives (PTX ISA: barrier.cluster, mapa, %cluster_ctarank).
+// The barrier is the hardware cluster barrier with release/acquire
+// semantics for shared::cluster memory; every thread of every CTA executes
+// each one, uniformly.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double* cluster_map(double* p, int rank) {
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(p)), "r"(rank));
+    return reinterpret_cast<double*>(out);
+}
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+
+__device__ __forceinline__ void xcl_matmul(double* xs, const double* A, const double* B, int coff, int m, int rank) {
+    const int r0 = rank * m / XCL, r1 = (rank + 1) * m / XCL;
+    for (int idx = threadIdx.x; idx < (r1 - r0) * m; idx += XTH) {
+        const int i = r0 + idx / m, j = idx - (idx / m) * m;
+        const double* a = A + i * m;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = 0;
+        for (; k + 3 < m; k += 4) {
+            s0 += a[k] * B[k * m + j];
+            s1 += a[k + 1] * B[(k + 1) * m + j];
+            s2 += a[k + 2] * B[(k + 2) * m + j];
+            s3 += a[k + 3] * B[(k + 3) * m + j];
+        }
+        for (; k < m; ++k) s0 += a[k] * B[k * m + j];
+        const double v = (s0 + s1) + (s2 + s3);
+        double* dst = xs + coff + i * m + j;
+#pragma unroll
+        for (int p = 0; p < XCL; ++p) *cluster_map(dst, p) = v;
+    }
+    cluster_barrier();
+}
+
+__global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
+    expm_cluster_kernel(const double* __restrict__ Hh, int M, const int* __restrict__ m_p, int m_fixed, double tau,
+                        PadeCoef pc, double* __restrict__ y) {
+    extern __shared__ __align__(16) double xs[];
+    __shared__ double red[XTH / 32];
+    __shared__ int s_piv;
+    __shared__ double s_inv;
+    const int rank = cluster_rank();
+    const int m = m_p ? *m_p : m_fixed;
+    if (rank == 0)
+        for (int i = threadIdx.x; i < M; i += XTH) y[i] = 0.0;
+    if (m <= 0) return;  // uniform over the cluster: no CTA touches another's memory
+    const int mm = m * m;
+    enum { X_ = 0, A2_ = 1, A4_ = 2, A6_ = 3, U_ = 4, V_ = 5, T1_ = 6, T2_ = 7 };
+    double* X = xs + X_ * mm;
+    double* A2 = xs + A2_ * mm;
+    double* A4 = xs + A4_ * mm;
+    double* A6 = xs + A6_ * mm;
+    double* U = xs + U_ * mm;
+    double* V = xs + V_ * mm;
+    double* T1 = xs + T1_ * mm;
+    double* T2 = xs + T2_ * mm;
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        X[idx] = tau * Hh[(long long)i * M + j];
+    }
+    __syncthreads();
+    double colmax = 0.0;
+    for (int j = threadIdx.x; j < m; j += XTH) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += fabs(X[i * m + j]);
+        colmax = fmax(colmax, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) colmax = fmax(colmax, __shfl_down_sync(0xffffffffu, colmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = colmax;
+    __syncthreads();
+    // the scaling exponent on one thread (FP64 transcendental), broadcast
+    if (threadIdx.x == 0) {
+        double nm = 0.0;
+        for (int w = 0; w < XTH / 32; ++w) nm = fmax(nm, red[w]);
+        s_piv = nm > 0.0 ? max(0, (int)ceil(log2(nm / THETA13))) : 0;
+    }
+    __syncthreads();
+    const int s = s_piv;
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) X[idx] = ldexp(X[idx], -s);
+    // every CTA of the cluster must be running before its shared memory is
+    // written by a peer
+    __syncthreads();
+    cluster_barrier();
+    xcl_matmul(xs, X, X, A2_ * mm, m, rank);
+    xcl_matmul(xs, A2, A2, A4_ * mm, m, rank);
+    xcl_matmul(xs, A4, A2, A6_ * mm, m, rank);
+    const double* b = pc.c;
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) T1[idx] = b[13] * A6[idx] + b[11] * A4[idx] + b[9] * A2[idx];
+    __syncthreads();
+    xcl_matmul(xs, A6, T1, T2_ * mm, m, rank);
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        T2[idx] += b[7] * A6[idx] + b[5] * A4[idx] + b[3] * A2[idx] + (i == j ? b[1] : 0.0);
+    }
+    __syncthreads();
+    xcl_matmul(xs, X, T2, U_ * mm, m, rank);
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) T1[idx] = b[12] * A6[idx] + b[10] * A4[idx] + b[8] * A2[idx];
+    __syncthreads();
+    xcl_matmul(xs, A6, T1, V_ * mm, m, rank);
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) {
+        const int i = idx / m, j = idx - (idx / m) * m;
+        const double v = V[idx] + b[6] * A6[idx] + b[4] * A4[idx] + b[2] * A2[idx] + (i == j ? b[0] : 0.0);
+        const double u = U[idx];
+        T1[idx] = v - u;  // P
+        T2[idx] = v + u;  // Q
+    }
+    __syncthreads();
+    double* P = T1;
+    double* Q = T2;
+    double* L = A2;     // multipliers of the current column
+    double* Dinv = A4;  // reciprocals of the pivots
+    // LU with partial pivoting of P (redundant in every CTA), applied to
+    // this CTA's columns [c0, c1) of Q
+    const int c0 = rank * m / XCL, c1 = (rank + 1) * m / XCL, nc = c1 - c0;
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < m; ++k) {
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int piv = m;
+            for (int i = k + lane; i < m; i += 32) {
+                const double v = fabs(P[i * m + k]);
+                if (v > best) {
+                    best = v;
+                    piv = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int op = __shfl_down_sync(0xffffffffu, piv, o);
+                if (ob > best || (ob == best && op < piv)) {
+                    best = ob;
+                    piv = op;
+                }
+            }
+            if (lane == 0) {
+                if (piv >= m) piv = k;  // no comparable entry (NaN column)
+                s_piv = piv;
+                s_inv = 1.0 / P[piv * m + k];
+                Dinv[k] = s_inv;
+            }
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        const double inv = s_inv;
+        // multipliers from the pre-swap column (row piv becomes row k)
+        for (int i = k + 1 + threadIdx.x; i < m; i += XTH) L[i] = (i == piv ? P[k * m + k] : P[i * m + k]) * inv;
+        __syncthreads();
+        if (piv != k) {
+            for (int j = k + threadIdx.x; j < m; j += XTH) {
+                const double t = P[k * m + j];
+                P[k * m + j] = P[piv * m + j];
+                P[piv * m + j] = t;
+            }
+            for (int j = threadIdx.x; j < nc; j += XTH) {
+                const double t = Q[k * m + c0 + j];
+                Q[k * m + c0 + j] = Q[piv * m + c0 + j];
+                Q[piv * m + c0 + j] = t;
+            }
+            __syncthreads();
+        }
+        const int rows = m - k - 1, w = (m - k - 1) + nc;
+        for (int idx = threadIdx.x; idx < rows * w; idx += XTH) {
+            const int i = k + 1 + idx / w, jj = idx - (idx / w) * w;
+            const double l = L[i];
+            if (jj < m - k - 1) {
+                const int j = k + 1 + jj;
+                P[i * m + j] -= l * P[k * m + j];
+            } else {
+                const int j = c0 + jj - (m - k - 1);
+                Q[i * m + j] -= l * Q[k * m + j];
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        const double inv = Dinv[k];
+        for (int j = threadIdx.x; j < nc; j += XTH) Q[k * m + c0 + j] *= inv;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * nc; idx += XTH) {
+            const int i = idx / nc, j = c0 + idx - (idx / nc) * nc;
+            Q[i * m + j] -= P[i * m + k] * Q[k * m + j];
+        }
+        __syncthreads();
+    }
+    // publish this CTA's columns of R = P^{-1} Q into every copy of Q
+    for (int idx = threadIdx.x; idx < m * nc; idx += XTH) {
+        const int i = idx / nc, j = c0 + idx - (idx / nc) * nc;
+        const double v = Q[i * m + j];
+#pragma unroll
+        for (int p = 0; p < XCL; ++p)
+            if (p != rank) *cluster_map(xs + T2_ * mm + i * m + j, p) = v;
+    }
+    cluster_barrier();
+    int cur = T2_, nxt = U_;
+    for (int t = 0; t < s; ++t) {
+        // the barrier closing this product also ends every CTA's reads of
+        // cur, which the next product overwrites
+        xcl_matmul(xs, xs + cur * mm, xs + cur * mm, nxt * mm, m, rank);
+        const int tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    if (rank == 0)
+        for (int i = threadIdx.x; i < m; i += XTH) y[i] = xs[cur * mm + i * m];
+}
+
 // W = gamma V[:, :m_eff] y  (FP64 accumulation)
 template <typename T>
 __global__ void combine_kernel(const T* __restrict__ V, long long ldv, const KrylovScalars* __restrict__ ks,
@@ -823,15 +1049,25 @@ void gmres_init(sgk_ctx* ctx, double* g, int len, const double* beta, double* in
 
 void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed, double tau, double* ws, double* y) {
     KTimer kt(ctx, KC_EXPM);
-    expm_e1_kernel<<<1, 512, 0, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), ws, y);
-    check_launch("expm_e1");
+    if (M <= EXPM_CLUSTER_MAX_M) {
+        const size_t smem = sizeof(double) * 8 * M * M;
+        SGK_CUDA_CHECK(
+            cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        expm_cluster_kernel<<<XCL, XTH, smem, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), y);
+        check_launch("expm_cluster");
+    } else {
+        expm_e1_kernel<<<1, 512, 0, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), ws, y);
+        check_launch("expm_e1");
+    }
     count_launch(ctx);
 }
 
 // ------------------------------------------- allocation-free expm entry ---
 //
-// Scratch of sgk_expm_e1_noalloc: eight m x m work matrices for m up to
-// SGK_EXPM_NOALLOC_MAX_M, compiled into the library (every GPU that loads it
+// Scratch of sgk_expm_e1_noalloc for m above EXPM_CLUSTER_MAX_M (smaller m
+// run the cluster kernel, whose work matrices live in shared memory): eight
+// m x m work matrices for m up to SGK_EXPM_NOALLOC_MAX_M, compiled into the
+// library (every GPU that loads it
 // holds the 256 KB until the process exits).  The kernel writes every work
 // entry before reading it, so nothing has to start at zero; concurrent calls
 // share it and must not overlap on the GPU.
@@ -843,6 +1079,18 @@ static std::atomic<double*> g_expm_scratch_addr[256];
 
 extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream) {
     if (m < 1 || m > SGK_EXPM_NOALLOC_MAX_M || !X_dev || !y_dev) return SGK_EINVAL;
+    if (m <= EXPM_CLUSTER_MAX_M) {
+        // the cluster kernel keeps its work matrices in shared memory
+        const size_t smem = sizeof(double) * 8 * m * m;
+        if (cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            return SGK_ECUDA;
+        }
+        expm_cluster_kernel<<<XCL, XTH, smem, static_cast<cudaStream_t>(cuda_stream)>>>(X_dev, m, nullptr, m, tau,
+                                                                                     pade13_coefficients(), y_dev);
+        return cudaGetLastError() == cudaSuccess ? SGK_OK : SGK_ECUDA;
+    }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
         (void)cudaGetLastError();
@@ -862,6 +1110,18 @@ extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, doubl
                                                                           pade13_coefficients(), ws, y_dev);
     if (cudaGetLastError() != cudaSuccess) return SGK_ECUDA;
     return SGK_OK;
+}
+
+void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
+                            const double* v, double* W, long long n, int M, double dt) {
+    arnoldi_persistent(ctx, op, pw, kw, v, n, M);
+    expm_e1(ctx, kw.H, M, &kw.ks->m_eff, 0, dt, kw.expm_ws, kw.y);
+    {
+        KTimer kt(ctx, KC_VECTOR);
+        combine_kernel<double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
+    }
+    check_launch("combine");
+    count_launch(ctx);
 }
 
 template <typename T>

@@ -1,0 +1,152 @@
+// Sparse-grid matvec y = A x, A = -sum_i kappa_i (S along direction i),
+// all directions in one launch (Section 4, unidirectional principle), in the
+// gather form of sgk_gmv.h.
+//
+// y is written once; x is gathered through L2 (the 1D rows overlap, so
+// neighbouring outputs share most of their loads).  The sums are taken in a
+// fixed order (per lane two accumulators per direction, directions in order,
+// then a fixed xor tree over the group), so results are deterministic.
+#include <algorithm>
+
+#include "sgk_gmv.h"
+
+namespace {
+
+template <typename T, int D, int KP1, int G>
+__global__ void __launch_bounds__(256) gmv_kernel(const GmvArgs<T, D> a, const T* __restrict__ x,
+                                                  T* __restrict__ y) {
+    // G consecutive lanes share one output coefficient (more loads in flight
+    // for small vectors, whose cost is latency)
+    const int r = threadIdx.x & (G - 1), lane = threadIdx.x & 31;
+    const int64_t total = a.n * G;
+    // the trip count is uniform over the warp (the shuffles below need every
+    // lane); lanes past the end carry zeros
+    for (int64_t gg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gg - lane < total;
+         gg += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = gg / G;
+        const bool live = g < a.n;
+        T acc = live ? gmv_lane<T, D, KP1, G, false>(a, x, g, r) : T(0);
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (live && r == 0) y[g] = acc;
+    }
+}
+
+template <typename T, int D>
+void gmv_dispatch(const sgk_op* op, const T* x, T* y) {
+    const sgk_index* idx = op->idx;
+    const GmvArgs<T, D> a = make_gmv_args<T, D>(op);
+    sgk_ctx* ctx = op->ctx;
+    const int threads = 256;
+    // lanes per output: enough threads to fill the GPU when the vector is
+    // small (latency-bound), one lane per output when it is large
+    int G = 1;
+    while (G < 8 && idx->dof * G < (int64_t)ctx->num_sms * 1024) G *= 2;
+    const int64_t blocks = (idx->dof * G + threads - 1) / threads;
+    const int grid = (int)std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 8);
+    KTimer kt(ctx, KC_MATVEC);
+#define SGK_GMV(K, GG) gmv_kernel<T, D, K, GG><<<grid, threads, 0, ctx->stream>>>(a, x, y)
+#define SGK_GMV_K(K)                         \
+    switch (G) {                             \
+        case 1: SGK_GMV(K, 1); break;        \
+        case 2: SGK_GMV(K, 2); break;        \
+        case 4: SGK_GMV(K, 4); break;        \
+        default: SGK_GMV(K, 8); break;       \
+    }
+    switch (idx->k + 1) {
+        case 2: SGK_GMV_K(2) break;
+        case 3: SGK_GMV_K(3) break;
+        case 4: SGK_GMV_K(4) break;
+        default: throw SgkError{SGK_EUNSUPPORTED, "matvec: degree must be 1..3"};
+    }
+#undef SGK_GMV_K
+#undef SGK_GMV
+    check_launch("gmv_kernel");
+    count_launch(ctx);
+}
+
+}  // namespace
+
+// Host tables of the gather matvec, with every address the kernel can form
+// checked against the vector length.
+void build_gmv_tables(sgk_op* op) {
+    const sgk_index* idx = op->idx;
+    const int d = idx->d, N = idx->n, kp1 = idx->k + 1, nl = N + 1;
+    const Csr& S = op->S;
+    std::vector<int32_t> ce(S.col.size());
+    for (int a = 0; a < S.rows; ++a)
+        for (int q = S.ptr[a]; q < S.ptr[a + 1]; ++q) {
+            const int b = S.col[q];
+            int lb = 0;
+            while (b >= level_offset(lb, kp1) + level_count(lb, kp1)) ++lb;
+            SGK_REQUIRE(lb <= N, SGK_EINVAL, "matvec: column outside the 1D space");
+            const int p = b - level_offset(lb, kp1);
+            ce[q] = (lb << 16) | p;
+        }
+    // truncated row lengths, as uploaded: rl[a (N+1) + L]
+    std::vector<int> rl((size_t)S.rows * nl, 0);
+    for (int a = 0; a < S.rows; ++a)
+        for (int L = 0; L < nl; ++L) {
+            int c = 0;
+            for (int q = S.ptr[a]; q < S.ptr[a + 1] && S.col[q] < (kp1 << L); ++q) ++c;
+            rl[(size_t)a * nl + L] = c;
+        }
+    int64_t madds = 0;
+    std::vector<int64_t> cb((size_t)idx->ntuples * d * nl, -1);
+    for (int64_t t = 0; t < idx->ntuples; ++t) {
+        const int32_t* l = &idx->levels[t * d];
+        int sum = 0;
+        for (int m = 0; m < d; ++m) sum += l[m];
+        for (int i = 0; i < d; ++i) {
+            std::vector<int> lv(l, l + d);
+            const int np = N - (sum - l[i]);
+            int64_t blk = 1;  // block size without direction i
+            for (int m = 0; m < d; ++m)
+                if (m != i) blk *= level_count(l[m], kp1);
+            int64_t rows = 0;  // entries of the rows of this block's direction-i positions
+            for (int c = 0; c < level_count(l[i], kp1); ++c)
+                rows += rl[(size_t)(level_offset(l[i], kp1) + c) * nl + np];
+            madds += rows * blk;
+            for (int lb = 0; lb <= np; ++lb) {
+                lv[i] = lb;
+                const long long r = tuple_rank(lv, N);
+                SGK_REQUIRE(r >= 0 && r < idx->ntuples, SGK_EINVAL, "matvec: tuple rank out of range");
+                const int64_t off = idx->offsets[r];
+                SGK_REQUIRE(idx->offsets[r + 1] - off == blk * level_count(lb, kp1), SGK_EINVAL,
+                            "matvec: block size mismatch");
+                SGK_REQUIRE(off + blk * level_count(lb, kp1) <= idx->dof, SGK_EINVAL, "matvec: block outside x");
+                cb[((size_t)t * d + i) * nl + lb] = off;
+            }
+        }
+    }
+    const int64_t nchunk = (idx->dof + 255) / 256;
+    std::vector<int32_t> chunk(nchunk + 1);
+    int64_t t = 0;
+    for (int64_t c = 0; c <= nchunk; ++c) {
+        const int64_t g = std::min<int64_t>(c * 256, idx->dof - 1);
+        while (idx->offsets[t + 1] <= g) ++t;
+        chunk[c] = (int32_t)t;
+    }
+    op->madds = madds;
+    op->gmv_ce.upload(ce, op->ctx->stream);
+    op->gmv_cb.upload(cb, op->ctx->stream);
+    op->gmv_chunk.upload(chunk, op->ctx->stream);
+    SGK_CUDA_CHECK(cudaStreamSynchronize(op->ctx->stream));
+}
+
+template <typename T>
+void op_matvec(const sgk_op* op, const T* x, T* y) {
+    if (op->idx->dof == 0) return;
+    switch (op->idx->d) {
+        case 1: gmv_dispatch<T, 1>(op, x, y); break;
+        case 2: gmv_dispatch<T, 2>(op, x, y); break;
+        case 3: gmv_dispatch<T, 3>(op, x, y); break;
+        case 4: gmv_dispatch<T, 4>(op, x, y); break;
+        case 5: gmv_dispatch<T, 5>(op, x, y); break;
+        case 6: gmv_dispatch<T, 6>(op, x, y); break;
+        default: throw SgkError{SGK_EUNSUPPORTED, "matvec: d must be 1..6"};
+    }
+}
+
+template void op_matvec<double>(const sgk_op*, const double*, double*);
+template void op_matvec<float>(const sgk_op*, const float*, float*);

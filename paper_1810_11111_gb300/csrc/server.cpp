@@ -1,0 +1,431 @@
+// Request loop around the IIF2 solver: continuous batching of whole solves
+// on one GPU (the service around the method; the paper has no counterpart).
+//
+// Submitted requests wait in a FIFO.  The dispatcher admits a request when a
+// worker is idle and the request's estimated device memory fits in the budget
+// left by the running ones; a request that does not fit is overtaken by later
+// ones that do, until it has waited longer than the aging limit, after which
+// nothing behind it is admitted until it runs.  Each worker thread owns a
+// CUDA stream and one library context per precision on it, builds the index
+// set, operators and solver of its request, takes the steps, copies the
+// state to the host and frees everything, so admitted requests overlap on
+// the GPU through their streams and keep their Krylov bases and state on the
+// device for their whole run.  The persistent Arnoldi kernel of each worker
+// gets an equal share of the SMs, so that the cooperative grids of all
+// workers fit on the device together.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sgk_internal.h"
+#include "sgk_quad.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct InitCopy {
+    std::vector<double> coeffs;
+    std::vector<double> amp;
+    std::vector<int> wavenum, kind;
+    double const_term = 0.0;
+};
+
+struct Req {
+    int64_t ticket = 0;
+    int d = 0, n = 0, k = 0, S = 1, bc = SGK_PERIODIC, M = 0, nsteps = 0, prec = SGK_FP64;
+    double dt = 0.0;
+    std::vector<double> kappa;  // S x d
+    int nmono = 0;
+    std::vector<int> rx_species, rx_exps;
+    std::vector<double> rx_coef;
+    InitCopy init[SGK_MAX_SPECIES];
+    int64_t est = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    bool done = false;
+    sgk_result_info info{};
+    std::vector<double> result;
+};
+
+int64_t level_dof(int d, int N, int k) {
+    // sum over level tuples |l|_1 <= N of prod_m (k+1) 2^{max(l_m - 1, 0)}
+    std::vector<int64_t> cnt(N + 1, 0);  // cnt[s]: dof of tuples with sum s, built dimension by dimension
+    cnt[0] = 1;
+    for (int m = 0; m < d; ++m) {
+        std::vector<int64_t> nxt(N + 1, 0);
+        for (int s = 0; s <= N; ++s)
+            if (cnt[s])
+                for (int l = 0; s + l <= N; ++l) nxt[s + l] += cnt[s] * level_count(l, k + 1);
+        cnt.swap(nxt);
+    }
+    int64_t t = 0;
+    for (int64_t c : cnt) t += c;
+    return t;
+}
+
+}  // namespace
+
+struct sgk_server {
+    int device = 0;
+    int nworkers = 0;
+    int64_t budget = 0;
+    double aging_ms = 2000.0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Req>> queue;
+    std::unordered_map<int64_t, std::shared_ptr<Req>> tickets;
+    std::vector<std::shared_ptr<Req>> slot;  // request assigned to each worker
+    std::vector<std::thread> threads;
+    bool stopping = false;
+    int64_t next_ticket = 1;
+    int64_t reserved = 0, peak_reserved = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
+    int running = 0, max_concurrent = 0;
+
+    // under mu: assign queued requests to idle workers
+    void admit_locked() {
+        const auto now = Clock::now();
+        for (int w = 0; w < nworkers; ++w) {
+            if (slot[w]) continue;
+            std::shared_ptr<Req> pick;
+            for (auto it = queue.begin(); it != queue.end(); ++it) {
+                if (reserved + (*it)->est <= budget) {
+                    pick = *it;
+                    queue.erase(it);
+                    break;
+                }
+                // an aged request that does not fit blocks everything behind it
+                if (ms_between((*it)->t_submit, now) > aging_ms) break;
+            }
+            if (!pick) break;
+            pick->t_admit = now;
+            reserved += pick->est;
+            peak_reserved = std::max(peak_reserved, reserved);
+            slot[w] = pick;
+            ++running;
+            max_concurrent = std::max(max_concurrent, running);
+        }
+        cv_work.notify_all();
+    }
+
+    void worker(int w);
+};
+
+namespace {
+
+int run_request(sgk_ctx* ctx, Req& r) {
+    sgk_index* idx = nullptr;
+    sgk_op* ops[SGK_MAX_SPECIES] = {nullptr};
+    sgk_solver* sol = nullptr;
+    DevBuf<double> u0;
+    int rc = sgk_index_build(ctx, r.d, r.n, r.k, &idx);
+    if (rc == SGK_OK) {
+        for (int s = 0; s < r.S && rc == SGK_OK; ++s)
+            rc = sgk_operator_assemble(ctx, idx, &r.kappa[(size_t)s * r.d], r.bc, 20.0, &ops[s]);
+    }
+    if (rc == SGK_OK) {
+        sgk_reaction f{};
+        f.nspecies = r.S;
+        f.nmono = r.nmono;
+        f.species = r.rx_species.data();
+        f.coef = r.rx_coef.data();
+        f.exps = r.rx_exps.data();
+        rc = sgk_solver_create(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, &sol);
+    }
+    const int64_t dof = idx ? idx->dof : 0;
+    if (rc == SGK_OK) {
+        try {
+            u0.alloc(dof);
+        } catch (const SgkError& e) {
+            rc = e.code;
+        }
+    }
+    for (int s = 0; s < r.S && rc == SGK_OK; ++s) {
+        const InitCopy& in = r.init[s];
+        if (!in.coeffs.empty()) {
+            rc = (int64_t)in.coeffs.size() == dof ? sgk_solver_set_state(sol, s, in.coeffs.data(), 0) : SGK_EINVAL;
+        } else {
+            rc = sgk_project_separable(ctx, idx, (int)in.amp.size(), in.amp.data(), in.wavenum.data(), in.kind.data(),
+                                       in.const_term, u0.p);
+            if (rc == SGK_OK) rc = sgk_solver_set_state(sol, s, u0.p, 1);
+        }
+    }
+    if (rc == SGK_OK) rc = sgk_solver_step(sol, r.nsteps);
+    if (sol) {
+        sgk_stats st{};
+        sgk_solver_stats(sol, &st);
+        r.info.steps = st.steps;
+        r.info.newton_iters = st.newton_iters;
+        r.info.inner_iters = st.inner_iters;
+        if (rc == SGK_OK) {
+            r.result.resize((size_t)r.S * dof);
+            for (int s = 0; s < r.S && rc == SGK_OK; ++s)
+                rc = sgk_solver_get_state(sol, s, r.result.data() + (size_t)s * dof, dof, 0);
+        }
+    }
+    r.info.dof = dof;
+    sgk_solver_destroy(sol);
+    for (int s = 0; s < r.S; ++s) sgk_operator_destroy(ops[s]);
+    sgk_index_destroy(idx);
+    return rc;
+}
+
+}  // namespace
+
+void sgk_server::worker(int w) {
+    cudaSetDevice(device);
+    cudaStream_t stream = nullptr;
+    sgk_ctx* ctx[2] = {nullptr, nullptr};
+    bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+    // this thread's device buffers are stream-ordered on its own stream, so
+    // that freeing one request's memory does not wait for the other workers
+    if (ok) alloc_stream() = stream;
+    ok = ok && sgk_ctx_create(&ctx[0], device, stream, SGK_FP64) == SGK_OK;
+    ok = ok && sgk_ctx_create(&ctx[1], device, stream, SGK_MIXED) == SGK_OK;
+    if (ok)
+        for (sgk_ctx* c : ctx) c->persist_ctas = std::max(1, c->num_sms / nworkers);
+    for (;;) {
+        std::shared_ptr<Req> r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return slot[w] != nullptr || (stopping && queue.empty()); });
+            if (!slot[w]) break;
+            r = slot[w];
+        }
+        int rc = SGK_ECUDA;
+        if (ok) {
+            sgk_ctx* c = ctx[r->prec == SGK_MIXED ? 1 : 0];
+            try {
+                rc = run_request(c, *r);
+            } catch (...) {
+                rc = SGK_ECUDA;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->info.status = rc;
+            r->info.worker = w;
+            r->t_done = Clock::now();
+            r->info.queue_ms = ms_between(r->t_submit, r->t_admit);
+            r->info.run_ms = ms_between(r->t_admit, r->t_done);
+            r->info.latency_ms = ms_between(r->t_submit, r->t_done);
+            r->done = true;
+            reserved -= r->est;
+            --running;
+            ++completed;
+            if (rc != SGK_OK) ++failed;
+            slot[w] = nullptr;
+            admit_locked();
+        }
+        cv_done.notify_all();
+    }
+    for (sgk_ctx* c : ctx) sgk_ctx_destroy(c);
+    if (stream) cudaStreamDestroy(stream);
+}
+
+// ------------------------------------------------------------------ C ABI ---
+
+extern "C" {
+
+int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int precision, int has_reaction) {
+    if (d < 1 || d > SGK_MAX_DIM || n < 0 || n > SGK_MAX_LEVEL || k < 1 || k > 3 || nspecies < 1 ||
+        nspecies > SGK_MAX_SPECIES || krylov_m < 1 || krylov_m > SGK_MAX_KRYLOV ||
+        (precision != SGK_FP64 && precision != SGK_MIXED))
+        return -1;
+    const double dof = (double)level_dof(d, n, k);
+    const double S = nspecies, N = dof * S, M = krylov_m;
+    const double H = (double)((k + 1) << n);
+    const double ntup = (double)tuple_count(d, n);
+    double b = 0.0;
+    // index set; per species an operator: CSR of the 1D matrix (rows of at
+    // most min(H, 64 (k+1)) entries), truncated row lengths, gather tables
+    b += ntup * (4.0 * d + 8.0);
+    b += S * (H * std::min(H, 64.0 * (k + 1)) * 20.0 + H * (n + 1) * 4.0 + ntup * d * (n + 1) * 8.0 + dof / 32.0);
+    // solver: state and Krylov workspace (FP64 basis, two work vectors,
+    // partial sums of the Gram-Schmidt reductions)
+    b += 8.0 * (4.0 * N + (M + 1.0) * dof + 128.0 + 3.0 * dof);
+    b += 8.0 * (std::max(N / 128.0 + 1.0, 160.0) * (std::max(M, 50.0) + 1.0) + 8.0 * M * M + 3.0 * 160.0 * (M + 1.0));
+    if (has_reaction) {
+        const double elem = precision == SGK_FP64 ? 8.0 : 4.0;
+        const double full = std::pow(H, d);
+        b += 8.0 * 6.0 * N + elem * ((2.0 * S + 1.0) * full + 2.0 * S * dof + N);
+        if (precision == SGK_MIXED) b += 4.0 * 3.0 * N;  // FP32 copies of the sparse vectors
+        if (nspecies > 1) b += 8.0 * 51.0 * N;            // GMRES(50) basis
+        // change-of-basis tables and work plans
+        b += 2.0 * H * (n + 1) * (k + 1) * 12.0 + 64.0 * 1024.0 * d;
+    }
+    b = b * 1.05 + 16.0 * 1024 * 1024;  // allocator granularity and small buffers
+    return b > 9.0e18 ? -1 : (int64_t)b;
+}
+
+int sgk_server_create(int device, int nworkers, int64_t mem_budget_bytes, double aging_ms, sgk_server** out) {
+    if (!out || nworkers < 1 || nworkers > 64 || mem_budget_bytes < 0) return SGK_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    std::unique_ptr<sgk_server> srv(new (std::nothrow) sgk_server());
+    if (!srv) return SGK_ENOMEM;
+    srv->device = device;
+    srv->nworkers = nworkers;
+    srv->budget = mem_budget_bytes > 0 ? std::min<int64_t>(mem_budget_bytes, (int64_t)free_b)
+                                       : (int64_t)(0.8 * (double)free_b);
+    srv->aging_ms = aging_ms > 0 ? aging_ms : 2000.0;
+    srv->slot.assign(nworkers, nullptr);
+    try {
+        for (int w = 0; w < nworkers; ++w) srv->threads.emplace_back([s = srv.get(), w] { s->worker(w); });
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            srv->stopping = true;
+        }
+        srv->cv_work.notify_all();
+        for (auto& t : srv->threads) t.join();
+        return SGK_ENOMEM;
+    }
+    *out = srv.release();
+    return SGK_OK;
+}
+
+int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
+    if (!srv || !q || !ticket) return SGK_EINVAL;
+    *ticket = 0;
+    const int S = q->nspecies;
+    if (S < 1 || S > SGK_MAX_SPECIES || q->d < 1 || q->d > SGK_MAX_DIM || q->n < 0 || q->n > SGK_MAX_LEVEL ||
+        q->k < 1 || q->k > 3 || q->krylov_m < 1 || q->krylov_m > SGK_MAX_KRYLOV || !(q->dt > 0) || q->nsteps < 0 ||
+        !q->kappa || (q->precision != SGK_FP64 && q->precision != SGK_MIXED) ||
+        (q->bc != SGK_PERIODIC && q->bc != SGK_DIRICHLET0))
+        return SGK_EINVAL;
+    if (q->reaction.nmono < 0 || q->reaction.nmono > SGK_MAX_MONO ||
+        (q->reaction.nmono > 0 &&
+         (q->reaction.nspecies != S || !q->reaction.species || !q->reaction.coef || !q->reaction.exps)))
+        return SGK_EINVAL;
+    auto r = std::make_shared<Req>();
+    r->d = q->d;
+    r->n = q->n;
+    r->k = q->k;
+    r->S = S;
+    r->bc = q->bc;
+    r->M = q->krylov_m;
+    r->dt = q->dt;
+    r->nsteps = q->nsteps;
+    r->prec = q->precision;
+    r->kappa.assign(q->kappa, q->kappa + (size_t)S * q->d);
+    r->nmono = q->reaction.nmono;
+    if (r->nmono > 0) {
+        r->rx_species.assign(q->reaction.species, q->reaction.species + r->nmono);
+        r->rx_coef.assign(q->reaction.coef, q->reaction.coef + r->nmono);
+        r->rx_exps.assign(q->reaction.exps, q->reaction.exps + (size_t)r->nmono * S);
+    }
+    const int64_t dof = level_dof(q->d, q->n, q->k);
+    for (int s = 0; s < S; ++s) {
+        const sgk_init& in = q->init[s];
+        InitCopy& c = r->init[s];
+        if (in.coeffs) {
+            c.coeffs.assign(in.coeffs, in.coeffs + dof);
+        } else {
+            if (in.nterms < 0 || (in.nterms > 0 && (!in.amp || !in.wavenum || !in.kind))) return SGK_EINVAL;
+            c.amp.assign(in.amp, in.amp + in.nterms);
+            c.wavenum.assign(in.wavenum, in.wavenum + (size_t)in.nterms * q->d);
+            c.kind.assign(in.kind, in.kind + (size_t)in.nterms * q->d);
+            c.const_term = in.const_term;
+        }
+    }
+    r->est = sgk_estimate_bytes(q->d, q->n, q->k, S, q->krylov_m, q->precision, r->nmono > 0);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stopping) return SGK_EINVAL;
+    if (r->est < 0 || r->est > srv->budget) {
+        ++srv->rejected;
+        return SGK_ENOMEM;
+    }
+    r->ticket = srv->next_ticket++;
+    r->t_submit = Clock::now();
+    r->info.nspecies = S;
+    r->info.est_bytes = r->est;
+    srv->tickets[r->ticket] = r;
+    srv->queue.push_back(r);
+    ++srv->submitted;
+    *ticket = r->ticket;
+    srv->admit_locked();
+    return SGK_OK;
+}
+
+int sgk_server_poll(sgk_server* srv, int64_t ticket) {
+    if (!srv) return -1;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->tickets.find(ticket);
+    if (it == srv->tickets.end()) return -1;
+    return it->second->done ? 1 : 0;
+}
+
+int sgk_server_wait(sgk_server* srv, int64_t ticket, double timeout_ms, sgk_result_info* info, double* out,
+                    int64_t cap) {
+    if (!srv) return SGK_EINVAL;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->tickets.find(ticket);
+    if (it == srv->tickets.end()) return SGK_EINVAL;
+    std::shared_ptr<Req> r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(lk, ready);
+    } else if (!srv->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), ready)) {
+        return SGK_ETIMEOUT;
+    }
+    if (out && cap < (int64_t)r->result.size()) return SGK_EINVAL;
+    if (info) *info = r->info;
+    if (out && !r->result.empty()) std::memcpy(out, r->result.data(), r->result.size() * sizeof(double));
+    srv->tickets.erase(it);
+    return SGK_OK;
+}
+
+int sgk_server_get_stats(sgk_server* srv, sgk_server_stats* out) {
+    if (!srv || !out) return SGK_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    out->submitted = srv->submitted;
+    out->completed = srv->completed;
+    out->failed = srv->failed;
+    out->rejected = srv->rejected;
+    out->queued = (int64_t)srv->queue.size();
+    out->running = srv->running;
+    out->budget_bytes = srv->budget;
+    out->reserved_bytes = srv->reserved;
+    out->peak_reserved_bytes = srv->peak_reserved;
+    out->max_concurrent = srv->max_concurrent;
+    return SGK_OK;
+}
+
+int sgk_server_destroy(sgk_server* srv) {
+    if (!srv) return SGK_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stopping = true;
+    }
+    srv->cv_work.notify_all();
+    for (auto& t : srv->threads) t.join();
+    delete srv;
+    return SGK_OK;
+}
+
+}  // extern "C"

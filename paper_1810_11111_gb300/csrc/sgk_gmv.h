@@ -1,0 +1,119 @@
+// Gather form of the sparse-grid matvec (Section 4, unidirectional
+// principle): the per-output device routine shared by the matvec kernel and
+// the persistent Arnoldi kernel.
+//
+// A group of G lanes owns one coefficient y_g of block l (local multi-index
+// c, 1D hierarchical index a_i = off(l_i) + c_i along direction i).  For
+// each direction i the group walks row a_i of the 1D hierarchical SIPG
+// matrix truncated to the levels lb <= N' = N - sum_{m!=i} l_m, and gathers
+// x at the coefficient of block (l with l_i = lb) that shares the other
+// local indices c_m (m != i).  The entries of a row are stored sorted by
+// column, each packed as (lb, position within level lb), so the source block
+// offset comes from a small per-(tuple, direction) table and the address is
+// base + (o n_lb + p) I + in, with o the row-major index of c_0..c_{i-1} and
+// in that of c_{i+1}..c_{d-1} (I their extent).  Lane r of the group takes
+// entries r, r + G, ... of every row; the caller combines the lanes.
+#pragma once
+#include "sgk_internal.h"
+
+template <typename T, int D>
+struct GmvArgs {
+    int64_t n;
+    int N;
+    const int64_t* __restrict__ offsets;  // ntuples + 1
+    const int32_t* __restrict__ levels;   // ntuples x D
+    const int32_t* __restrict__ chunk;    // tuple holding element c * 256, c <= ceil(n / 256)
+    const int64_t* __restrict__ cb;       // ntuples x D x (N + 1) block offsets
+    const int32_t* __restrict__ rp;       // H + 1
+    const int32_t* __restrict__ rlen;     // H x (N + 1)
+    const int32_t* __restrict__ ce;       // packed (lb << 16) | p
+    const T* __restrict__ cv;
+    T kneg[D];  // -kappa_i
+};
+
+// Partial sum of lane r (0 <= r < G) for output g; the G partials of a
+// group add up to y_g.  CG selects L2-only loads of x, for vectors written
+// by other CTAs of the same (persistent) kernel.
+template <typename T, int D, int KP1, int G, bool CG>
+__device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restrict__ x, int64_t g, int r) {
+    const int nl = a.N + 1;
+    // tuple of g: binary search between the tuples of the chunk's ends
+    int lo = a.chunk[g >> 8], hi = a.chunk[(g >> 8) + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.offsets[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const int t = lo;
+    int64_t e = g - a.offsets[t];
+    int lv[D], sh[D], c[D], cnt[D];
+    int sum = 0;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        lv[m] = a.levels[t * D + m];
+        sum += lv[m];
+        sh[m] = lv[m] > 0 ? lv[m] - 1 : 0;
+        cnt[m] = KP1 << sh[m];
+    }
+    // local multi-index, last direction fastest; cnt[m] = KP1 2^sh[m]
+#pragma unroll
+    for (int m = D - 1; m >= 0; --m) {
+        const int64_t q = (e >> sh[m]) / KP1;
+        c[m] = (int)(e - q * cnt[m]);
+        e = q;
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        int64_t o = 0, in = 0, I = 1;
+#pragma unroll
+        for (int m = 0; m < i; ++m) o = o * cnt[m] + c[m];
+#pragma unroll
+        for (int m = D - 1; m > i; --m) {
+            in += (int64_t)c[m] * I;
+            I *= cnt[m];
+        }
+        const int np = a.N - (sum - lv[i]);
+        const int ai = (lv[i] ? (KP1 << (lv[i] - 1)) : 0) + c[i];
+        const int64_t* __restrict__ base = a.cb + ((int64_t)t * D + i) * nl;
+        const int q0 = a.rp[ai];
+        const int qe = q0 + a.rlen[ai * nl + np];
+        const int64_t oI = o * I * KP1;  // o n_lb I = (o I KP1) << (lb - 1) for lb >= 1
+        auto ld = [&](int pk) {
+            const int lb = pk >> 16, p = pk & 0xffff;
+            const int64_t ob = lb ? (oI << (lb - 1)) : oI;
+            const T* px = x + base[lb] + ob + (int64_t)p * I + in;
+            if constexpr (CG) return __ldcg(px);
+            else return *px;
+        };
+        T s0 = T(0), s1 = T(0);
+        int q = q0 + r;
+        for (; q + G < qe; q += 2 * G) {
+            const int p0 = a.ce[q], p1 = a.ce[q + G];
+            const T v0 = a.cv[q], v1 = a.cv[q + G];
+            s0 += v0 * ld(p0);
+            s1 += v1 * ld(p1);
+        }
+        if (q < qe) s0 += a.cv[q] * ld(a.ce[q]);
+        acc += a.kneg[i] * (s0 + s1);
+    }
+    return acc;
+}
+
+template <typename T, int D>
+GmvArgs<T, D> make_gmv_args(const sgk_op* op) {
+    const sgk_index* idx = op->idx;
+    GmvArgs<T, D> a;
+    a.n = idx->dof;
+    a.N = idx->n;
+    a.offsets = idx->d_offsets.p;
+    a.levels = idx->d_levels.p;
+    a.chunk = op->gmv_chunk.p;
+    a.cb = op->gmv_cb.p;
+    a.rp = op->S.d_ptr.p;
+    a.rlen = op->rlen.p;
+    a.ce = op->gmv_ce.p;
+    a.cv = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->S.d_val.p) : reinterpret_cast<const T*>(op->S.d_valf.p);
+    for (int i = 0; i < D; ++i) a.kneg[i] = T(-op->kappa[i]);
+    return a;
+}

@@ -30,36 +30,61 @@ struct SgkError {
 
 // ---------------------------------------------------- device allocations ---
 
-// Owning device buffer (cudaMalloc / cudaFree); moves only.
+// Stream for stream-ordered allocations by DevBuf on this host thread;
+// nullptr (the default) selects cudaMalloc / cudaFree.  cudaFree waits for
+// the whole device, which would serialise solves running concurrently on
+// other streams, so a thread that owns one stream per solve sets it.
+inline cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
+// Owning device buffer; moves only.
 template <typename T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t as = nullptr;  // stream of a stream-ordered allocation
     DevBuf() = default;
     explicit DevBuf(size_t count) { alloc(count); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), as(o.as) { o.p = nullptr; o.n = 0; o.as = nullptr; }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            as = o.as;
+            o.p = nullptr;
+            o.n = 0;
+            o.as = nullptr;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
     void alloc(size_t count) {
         release();
         if (count == 0) return;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+        cudaStream_t s = alloc_stream();
+        cudaError_t e = s ? cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), s)
+                          : cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
             (void)cudaGetLastError();
-            throw SgkError{SGK_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+            throw SgkError{SGK_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
         }
         n = count;
+        as = s;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (as) cudaFreeAsync(p, as);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
+        as = nullptr;
     }
     void upload(const T* host, size_t count, cudaStream_t s) {
         if (count) SGK_CUDA_CHECK(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
@@ -81,7 +106,7 @@ enum KernelClass {
     KC_REDUCE = 4,   // inner products, Gram-Schmidt passes
     KC_EXPM = 5,     // exp(tau H) e_1
     KC_VECTOR = 6,   // other vector kernels
-    KC_KRYLOV = 7,   // whole Krylov exponential (captured graph)
+    KC_KRYLOV = 7,   // Krylov exponential: its captured graph, or the persistent Arnoldi kernel when timed alone
     KC_COUNT = 8
 };
 
@@ -95,6 +120,8 @@ struct sgk_ctx {
     size_t smem_optin = 0;
     bool own_stream = false;  // stream created by the library (caller passed NULL)
     bool capturing = false;   // a CUDA graph is being captured on the stream
+    int persist_ctas = 0;     // CTAs of the persistent Arnoldi kernel (0 = one per SM)
+    double* hscal = nullptr;  // pinned host scalars (16) for step-control reads
     // event timing
     unsigned prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -212,13 +239,6 @@ struct FiberPlan {
 void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, int H, int mode, size_t elem_bytes,
                    size_t smem_budget, long long src_size, long long dst_size, cudaStream_t s);
 
-// rlen[a * nlev_max + L]: entries of row a with column < (k+1) 2^L (rows of
-// the CSR matrix sorted by column), i.e. the row of the principal submatrix
-// of levels 0..L.
-template <typename T>
-void launch_fiber(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* dst, const int* rp, const int* ci,
-                  const T* cv, const int* rlen, int nlev_max, int H, int kp1, T alpha, int accumulate);
-
 // Two-scale filters for the pyramid kernels (entries beyond k+1 unused).
 template <typename T>
 struct PyrFilt {
@@ -243,9 +263,22 @@ struct sgk_op {
     int H = 0;
     std::vector<double> S_dense;  // H x H host copy
     Csr S;
-    DevBuf<int> rlen;                // truncated row lengths of S per level
-    FiberPlan plan[SGK_MAX_DIM][2];  // [dim][0 = fp64, 1 = fp32]
+    // rlen[a (N+1) + L]: entries of row a with column < (k+1) 2^L (CSR rows
+    // sorted by column), i.e. the row of the principal submatrix of levels
+    // 0..L
+    DevBuf<int> rlen;
+    // gather-matvec tables: packed (level, position) of every CSR entry;
+    // block offsets per (tuple, direction, level); tuple of every 256th
+    // coefficient
+    DevBuf<int32_t> gmv_ce;
+    DevBuf<int64_t> gmv_cb;
+    DevBuf<int32_t> gmv_chunk;
+    int64_t madds = 0;  // multiply-adds of one matvec (entries of A on the index set, per direction)
 };
+
+// Builds and checks the gather-matvec tables of an assembled operator.
+void build_gmv_tables(sgk_op* op);
+long long tuple_rank(const std::vector<int>& l, int n);
 
 template <typename T>
 void op_matvec(const sgk_op* op, const T* x, T* y);

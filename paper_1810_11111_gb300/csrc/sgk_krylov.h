@@ -36,6 +36,25 @@ struct KrylovWork {
     unsigned* counter = nullptr;  // last-block counter of the fused reductions (zero between kernels)
 };
 
+// Extra device workspace of the persistent Arnoldi kernel (arnoldi.cu).
+struct PersistentWork {
+    double* w_alt = nullptr;  // second work vector (n)
+    double* pbuf = nullptr;   // arnoldi_persistent_pbuf_size doubles
+    unsigned* bar = nullptr;  // [0] barrier arrivals, [1] error flag (sticky until the host clears it)
+};
+
+// Largest n (and the partial-sum buffer size) the persistent kernel takes on
+// this context's device.
+int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx);
+size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M);
+// gamma, V (M + 1 columns), H and m_eff of the Krylov space of v, in one
+// cooperative launch.
+void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
+                        const double* v, int64_t n, int M);
+// exp(dt A) v by the persistent Arnoldi kernel, expm and the combination
+void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
+                            const double* v, double* W, long long n, int M, double dt);
+
 PadeCoef pade13_coefficients();
 void vk_dot(sgk_ctx* ctx, const double* a, const double* b, long long n, double* partials, double* out, int mode,
             const int* stop);

@@ -33,12 +33,16 @@ struct sgk_solver {
     DevBuf<double> Hm, h1, h2, ky, scal, partials, expm_ws;
     DevBuf<KrylovScalars> ks;
     DevBuf<unsigned> counters;
+    // persistent Arnoldi: second work vector, partial sums, per species a
+    // barrier counter and an error flag
+    bool persistent = false;
+    DevBuf<double> w64b, pbuf;
+    DevBuf<unsigned> pbar;
     // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
     DevBuf<double> q64, jw64;
     DevBuf<float> q32, jw32;
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
-    double* hscal = nullptr;  // pinned host scalars
     bool use_graphs = true;
     GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_resid, g_cg;
     sgk_stats stats{};

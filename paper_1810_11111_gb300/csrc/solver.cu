@@ -26,9 +26,9 @@
 namespace {
 
 double read_scalar(sgk_solver* s, const double* dptr) {
-    SGK_CUDA_CHECK(cudaMemcpyAsync(s->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
+    SGK_CUDA_CHECK(cudaMemcpyAsync(s->ctx->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
     SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
-    return s->hscal[0];
+    return s->ctx->hscal[0];
 }
 
 // Runs body() through a cached CUDA graph: captured on first use (kernel
@@ -293,12 +293,12 @@ void gmres_solve_host(sgk_solver* s, const double* G, double* x, int& iters) {
             vk_gs_update<double>(ctx, V, N, j + 1, s->h2.p, w, N, nullptr);
             vk_dot(ctx, w, w, N, s->partials.p, hn2, 0, nullptr);
             gmres_givens(ctx, j, restart, s->gm_H.p, s->gm_cs.p, s->gm_sn.p, s->gm_g.p, s->h1.p, s->h2.p, hn2, rep);
-            SGK_CUDA_CHECK(cudaMemcpyAsync(s->hscal, rep, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            SGK_CUDA_CHECK(cudaMemcpyAsync(s->ctx->hscal, rep, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
             SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
             used = j + 1;
             ++iters;
-            last_g = s->hscal[0];
-            if (s->hscal[0] <= tol || s->hscal[1] <= 1e-12 * s->hscal[2]) break;
+            last_g = s->ctx->hscal[0];
+            if (s->ctx->hscal[0] <= tol || s->ctx->hscal[1] <= 1e-12 * s->ctx->hscal[2]) break;
             vk_scale_from(ctx, w, V + (long long)(j + 1) * N, N, rep + 3, nullptr);
         }
         gmres_solve(ctx, used, restart, s->gm_H.p, s->gm_g.p, s->gm_y.p);
@@ -373,8 +373,16 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
     const long long n = s->n;
     // FP64 in both precision modes: an FP32 matvec inside Arnoldi costs a few
     // 1e-6 of relative accuracy per exponential on these stiff operators
-    auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
-    krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
+    if (s->persistent) {
+        PersistentWork pw;
+        pw.w_alt = s->w64b.p;
+        pw.pbuf = s->pbuf.p;
+        pw.bar = s->pbar.p + 2 * species;
+        krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, s->dt);
+    } else {
+        auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
+        krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
+    }
     if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
 }
 
@@ -405,9 +413,21 @@ int solver_step(sgk_solver* s, int nsteps) {
             rc = newton(s);
         }
         KrylovScalars ks[SGK_MAX_SPECIES];
+        unsigned flags[2 * SGK_MAX_SPECIES] = {0};
         SGK_CUDA_CHECK(cudaMemcpyAsync(ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
                                        ctx->stream));
+        if (s->persistent)
+            SGK_CUDA_CHECK(cudaMemcpyAsync(flags, s->pbar.p, 2 * s->nspecies * sizeof(unsigned),
+                                           cudaMemcpyDeviceToHost, ctx->stream));
         SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        // a grid barrier of the persistent Arnoldi kernel ran out of time:
+        // clear the sticky flags and report it
+        bool timed_out = false;
+        for (int sp = 0; sp < s->nspecies; ++sp) timed_out = timed_out || flags[2 * sp + 1] != 0u;
+        if (timed_out) {
+            SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * s->nspecies * sizeof(unsigned), ctx->stream));
+            rc = SGK_ETIMEOUT;
+        }
         for (int sp = 0; sp < s->nspecies; ++sp) {
             s->stats.krylov_breakdowns += ks[sp].breakdown;
             s->stats.last_m_eff = ks[sp].m_eff;
@@ -446,6 +466,13 @@ void solver_alloc(sgk_solver* s) {
     s->expm_ws.alloc(8 * (size_t)M * M);
     s->ks.alloc(S);
     s->counters.alloc(4);
+    s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && n <= arnoldi_persistent_max_n(s->ctx);
+    if (s->persistent) {
+        s->w64b.alloc(n);
+        s->pbuf.alloc(arnoldi_persistent_pbuf_size(s->ctx, M));
+        s->pbar.alloc(2 * S);
+        SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
+    }
     SGK_CUDA_CHECK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(unsigned), s->ctx->stream));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->Hm.p, 0, (M + 1) * M * sizeof(double), s->ctx->stream));
     if (s->has_rx) {
@@ -474,11 +501,9 @@ void solver_alloc(sgk_solver* s) {
             s->gm_report.alloc(4);
         }
     }
-    SGK_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void**>(&s->hscal), 16 * sizeof(double)));
 }
 
 sgk_solver::~sgk_solver() {
-    if (hscal) cudaFreeHost(hscal);
     for (GraphCache* g : {&g_pred, &g_resid, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     for (auto& g : g_krylov)

@@ -41,6 +41,32 @@ class sgk_stats(ctypes.Structure):
                 ("last_m_eff", ctypes.c_int), ("last_newton_residual", ctypes.c_double)]
 
 
+class sgk_init(ctypes.Structure):
+    _fields_ = [("coeffs", _c_double_p), ("nterms", ctypes.c_int), ("amp", _c_double_p), ("wavenum", _c_int_p),
+                ("kind", _c_int_p), ("const_term", ctypes.c_double)]
+
+
+class sgk_request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int), ("nspecies", ctypes.c_int),
+                ("bc", ctypes.c_int), ("kappa", _c_double_p), ("reaction", sgk_reaction),
+                ("krylov_m", ctypes.c_int), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("init", sgk_init * MAX_SPECIES)]
+
+
+class sgk_result_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nspecies", ctypes.c_int), ("dof", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("est_bytes", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("worker", ctypes.c_int),
+                ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64)]
+
+
+class sgk_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
+                ("peak_reserved_bytes", ctypes.c_int64), ("max_concurrent", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "sgk_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
@@ -58,6 +84,7 @@ _SIGS = {
     "sgk_operator_assemble": (ctypes.c_int, [_P, _P, _c_double_p, ctypes.c_int, ctypes.c_double,
                                              ctypes.POINTER(_P)]),
     "sgk_operator_destroy": (ctypes.c_int, [_P]),
+    "sgk_operator_madds": (ctypes.c_int64, [_P]),
     "sgk_operator_export_1d": (ctypes.c_int, [_P, _c_double_p, ctypes.c_int64]),
     "sgk_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "sgk_project_separable": (ctypes.c_int, [_P, _P, ctypes.c_int, _c_double_p, _c_int_p, _c_int_p,
@@ -76,6 +103,15 @@ _SIGS = {
     "sgk_krylov_export": (ctypes.c_int, [_P, _c_double_p, _c_double_p, ctypes.c_int64]),
     "sgk_expm_e1": (ctypes.c_int, [_P, ctypes.c_int, _c_double_p, ctypes.c_double, _c_double_p]),
     "sgk_expm_e1_noalloc": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_double, _P, _P]),
+    "sgk_estimate_bytes": (ctypes.c_int64, [ctypes.c_int] * 7),
+    "sgk_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.POINTER(_P)]),
+    "sgk_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(sgk_request), _c_i64_p]),
+    "sgk_server_poll": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "sgk_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(sgk_result_info),
+                                       _c_double_p, ctypes.c_int64]),
+    "sgk_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_server_stats)]),
+    "sgk_server_destroy": (ctypes.c_int, [_P]),
 }
 EXPM_NOALLOC_MAX_M = 64
 
@@ -134,7 +170,7 @@ class Context:
         return int(sgk_ctx_launch_count(self.h))
 
     KERNEL_CLASSES = ("matvec", "to_finest", "from_finest", "cell_quadrature", "reductions", "expm", "vector",
-                      "krylov_graph")
+                      "arnoldi")
 
     def profile(self, mask):
         self.check(sgk_ctx_profile(self.h, int(mask)))
@@ -201,6 +237,9 @@ class Operator:
         self.h = _P()
         ctx.check(sgk_operator_assemble(ctx.h, idx.h, _dptr(kap), int(bc), float(sigma), ctypes.byref(self.h)))
         self.H = (idx.k + 1) << idx.n
+
+    def madds(self):
+        return int(sgk_operator_madds(self.h))
 
     def export_1d(self):
         out = np.zeros((self.H, self.H))
@@ -289,4 +328,105 @@ class Solver:
     def close(self):
         if self.h:
             sgk_solver_destroy(self.h)
+            self.h = _P()
+
+
+def dof_of(d, n, k):
+    """Coefficients per species of the sparse grid (d, level n, degree k):
+    the sum over level tuples |l|_1 <= n of prod_m (k+1) 2^max(l_m - 1, 0)."""
+    cnt = [1] + [0] * n
+    for _ in range(d):
+        nxt = [0] * (n + 1)
+        for s_, c in enumerate(cnt):
+            if c:
+                for lv in range(n + 1 - s_):
+                    nxt[s_ + lv] += c * ((k + 1) << max(lv - 1, 0))
+        cnt = nxt
+    return sum(cnt)
+
+
+class Server:
+    """Request loop over whole IIF2 solves (sgk_server_*): requests are
+    workload dicts as in workloads.py; results are species-stacked FP64
+    coefficients with the server's timing record."""
+
+    def __init__(self, device=0, workers=4, mem_budget_bytes=0, aging_ms=0.0):
+        load()
+        self.h = _P()
+        rc = sgk_server_create(int(device), int(workers), int(mem_budget_bytes), float(aging_ms),
+                               ctypes.byref(self.h))
+        if rc:
+            raise SgkError(rc, "sgk_server_create failed")
+
+    @staticmethod
+    def request(cfg, precision, init_coeffs=None):
+        """sgk_request for a workload dict; init_coeffs (list per species of
+        host arrays) overrides the separable initial data.  Returns the struct
+        and the arrays it points to (keep them alive until submit returns)."""
+        d, S = cfg["d"], len(cfg["kappas"])
+        keep = []
+        kap = np.ascontiguousarray(np.array(cfg["kappas"], dtype=np.float64).reshape(S * d))
+        keep.append(kap)
+        rx, rkeep = reaction_struct(cfg["reaction"], S)
+        keep.append(rkeep)
+        q = sgk_request()
+        q.d, q.n, q.k, q.nspecies, q.bc = d, cfg["n"], cfg["k"], S, int(cfg.get("bc", SGK_PERIODIC))
+        q.kappa = _dptr(kap)
+        q.reaction = rx
+        q.krylov_m, q.dt, q.nsteps, q.precision = int(cfg["M"]), float(cfg["dt"]), int(cfg["steps"]), int(precision)
+        if init_coeffs is None and any("noise_seed" in i for i in cfg["init"]):
+            from .workloads import coefficient_noise
+            init_coeffs = coefficient_noise(cfg["init"][0]["noise_seed"], dof_of(d, cfg["n"], cfg["k"]), S,
+                                            [i["base"] for i in cfg["init"]])
+        for s in range(S):
+            init = cfg["init"][s]
+            if init_coeffs is not None:
+                c = np.ascontiguousarray(init_coeffs[s], dtype=np.float64)
+                keep.append(c)
+                q.init[s].coeffs = _dptr(c)
+            else:
+                amp = np.ascontiguousarray(init["amp"], dtype=np.float64)
+                wn = np.ascontiguousarray(init["wavenum"], dtype=np.int32)
+                kd = np.ascontiguousarray(init["kind"], dtype=np.int32)
+                keep += [amp, wn, kd]
+                q.init[s].nterms = len(amp)
+                q.init[s].amp, q.init[s].wavenum, q.init[s].kind = _dptr(amp), _iptr(wn), _iptr(kd)
+                q.init[s].const_term = float(init.get("const", 0.0))
+        return q, keep
+
+    def submit(self, cfg, precision=SGK_MIXED, init_coeffs=None):
+        q, keep = self.request(cfg, precision, init_coeffs)
+        t = ctypes.c_int64(0)
+        rc = sgk_server_submit(self.h, ctypes.byref(q), ctypes.byref(t))
+        if rc:
+            raise SgkError(rc, "sgk_server_submit failed")
+        return t.value
+
+    def poll(self, ticket):
+        return int(sgk_server_poll(self.h, int(ticket)))
+
+    def wait(self, ticket, timeout_ms=-1.0, cap=None):
+        """(result array or None, info dict) once the request has finished."""
+        info = sgk_result_info()
+        if cap is None:
+            out = None
+            rc = sgk_server_wait(self.h, int(ticket), float(timeout_ms), ctypes.byref(info), None, 0)
+        else:
+            out = np.zeros(int(cap))
+            rc = sgk_server_wait(self.h, int(ticket), float(timeout_ms), ctypes.byref(info), _dptr(out), out.size)
+        if rc:
+            raise SgkError(rc, "sgk_server_wait failed")
+        d = {f: getattr(info, f) for f, _ in sgk_result_info._fields_}
+        if out is not None:
+            out = out[:d["nspecies"] * d["dof"]]
+        return out, d
+
+    def stats(self):
+        st = sgk_server_stats()
+        sgk_server_get_stats(self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in sgk_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            sgk_server_destroy(self.h)
             self.h = _P()

@@ -17,7 +17,12 @@ Workloads (sizes follow the paper's 2D/3D scalar and two-species runs):
   batch       256 scalar instances (seed 3): d in {2,3,4}, level 5..8,
               degree 1..2, kappa_i ~ U(0.05, 1), f = -c u^3 with
               c ~ U(1, 100), 8-mode Fourier u_0; M = 30, dt = 0.005
-  served      Poisson arrivals of solve requests (seed 4)
+  served      Poisson arrivals of solve requests (seed 4): d in {3,4},
+              level 6..9, degree 1..3, scalar cubic (f = -100 u^3,
+              8-mode Fourier u_0) or two-species Schnakenberg (the
+              schnak2d constants and noise), 10..100 steps, M = 30,
+              dt = 0.005; draws whose finest grid exceeds the nodal budget
+              are rejected and counted
 """
 import numpy as np
 
@@ -99,3 +104,40 @@ def batch_instances(count=256, seed=3, max_nodal_bytes=2 << 30):
                         M=30, dt=0.005, steps=20,
                         init=[dict(amp=amp, wavenum=wavenum, kind=kind, const=0.0)]))
     return out, rejected
+
+
+def served_requests(count=16, seed=4, max_nodal_bytes=2 << 30, max_steps=100):
+    """Solve requests of the served workload and the number of rejected draws.
+    Each request is a workload dict (as cubic3d / schnak2d) with a
+    precision-independent seeded initial state."""
+    rng = np.random.default_rng(seed)
+    out, rejected = [], 0
+    while len(out) < count:
+        d = int(rng.integers(3, 5))
+        n = int(rng.integers(6, 10))
+        k = int(rng.integers(1, 4))
+        kind = CUBIC if rng.random() < 0.5 else SCHNAKENBERG
+        steps = int(rng.integers(10, max_steps + 1))
+        noise_seed = int(rng.integers(0, 2 ** 31))
+        amp, wavenum, kindv = fourier_modes(rng, d)
+        if (((k + 1) << n) ** d) * 8 > max_nodal_bytes:
+            rejected += 1
+            continue
+        if kind == CUBIC:
+            req = dict(name="served-cubic", d=d, n=n, k=k, kappas=[[1.0, 0.5, 0.1, 0.7][:d]],
+                       reaction=reaction_terms(CUBIC, 100.0),
+                       init=[dict(amp=amp, wavenum=wavenum, kind=kindv, const=0.0)])
+        else:
+            req = dict(name="served-schnakenberg", d=d, n=n, k=k, kappas=[[0.01] * d, [0.5] * d],
+                       reaction=reaction_terms(SCHNAKENBERG),
+                       init=[dict(noise_seed=noise_seed, base=1.0, species=0),
+                             dict(noise_seed=noise_seed, base=0.9, species=1)])
+        req.update(M=30, dt=0.005, steps=steps)
+        out.append(req)
+    return out, rejected
+
+
+def poisson_arrivals(count, rate_per_s, seed=4):
+    """Arrival times (s, from 0) of a Poisson stream."""
+    rng = np.random.default_rng(seed + 1000)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, count)) - 0.0

@@ -121,6 +121,32 @@ def test_matvec_fp64(ctx64, d, n, k, bc):
     idx.close()
 
 
+@pytest.mark.parametrize("d,n,k,bc", MATVEC_CASES)
+def test_matvec_madds_count(ctx64, d, n, k, bc):
+    # the operator's multiply-add count: for every coefficient and direction,
+    # the entries of its 1D row on the levels l' <= N - sum_{m != i} l_m,
+    # counted from the oracle's 1D matrix (entries below 1e-12 of the
+    # diagonal scale are rounding noise of the assembly and are not stored)
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    op = sgkiif.Operator(ctx64, idx, [1.0] * d, bc)
+    S = sipg_1d(n, k, bc)
+    dg = np.sqrt(np.abs(np.diag(S)))
+    nz = np.abs(S) > 1e-12 * np.outer(dg, dg)
+    kp1 = k + 1
+    ref = OIndex(d, n, k)
+    lev = np.array([0 if a < kp1 else int(np.floor(np.log2(a // kp1))) + 1 for a in range(S.shape[0])])
+    want = 0
+    for l in ref.tuples:
+        for i in range(d):
+            npr = n - (sum(l) - l[i])
+            rows = [a for a in range(S.shape[0]) if lev[a] == l[i]]
+            other = int(np.prod([kp1 << max(l[m] - 1, 0) for m in range(d) if m != i]))
+            want += other * int(nz[np.ix_(rows, np.flatnonzero(lev <= npr))].sum())
+    assert op.madds() == want
+    op.close()
+    idx.close()
+
+
 @pytest.mark.parametrize("d,n,k,bc", MATVEC_CASES[:3])
 def test_matvec_fp32(ctx64, d, n, k, bc):
     # FP32 storage and accumulation: |error| <= c u_32 |A| |x| per row; for
@@ -165,6 +191,18 @@ def test_expm_e1(ctx64, scale):
     assert np.abs(y - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
 
 
+@pytest.mark.parametrize("m", [1, 2, 7, 8, 9, 31, 56, 57, 100])
+def test_expm_e1_sizes(ctx64, m):
+    # sizes around the row/column split over the eight CTAs of the cluster
+    # kernel (m < 8 leaves CTAs without rows), its largest size (56) and the
+    # single-CTA kernel beyond it
+    rng = np.random.default_rng(1000 + m)
+    X = rng.standard_normal((m, m)) * 20.0 / np.sqrt(m)
+    y = ctx64.expm_e1(X, 0.3)
+    want = expm_pade13(0.3 * X)[:, 0]
+    assert np.abs(y - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+
+
 def test_expm_e1_stiff_symmetric(ctx64):
     rng = np.random.default_rng(3)
     Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
@@ -182,10 +220,11 @@ def _krylov_problem(ctx, d, n, k, M, reaction=None):
     return cfg
 
 
-@pytest.mark.parametrize("d,n,k,M", [(2, 4, 1, 20), (3, 4, 2, 30), (2, 6, 1, 40)])
+@pytest.mark.parametrize("d,n,k,M", [(2, 4, 1, 20), (3, 4, 2, 30), (2, 6, 1, 40), (1, 3, 1, 8), (3, 6, 2, 30),
+                                     (2, 8, 2, 40), (4, 3, 1, 64)])
 def test_krylov_expv_fp64(ctx64, d, n, k, M):
     idx = sgkiif.IndexSet(ctx64, d, n, k)
-    kap = [1.0, 0.5, 0.1][:d]
+    kap = [1.0, 0.5, 0.1, 0.7][:d]
     op = sgkiif.Operator(ctx64, idx, kap)
     sol = sgkiif.Solver(ctx64, [op], [[]], M, 0.01)
     v = np.random.default_rng(2).standard_normal(idx.dof)
@@ -198,6 +237,29 @@ def test_krylov_expv_fp64(ctx64, d, n, k, M):
     assert m_eff == m_ref
     assert rel(wd.cpu().numpy(), want) <= 1e-10
     sol.close()
+    op.close()
+    idx.close()
+
+
+@pytest.mark.parametrize("d,n,k,M", [(1, 2, 1, 6), (2, 5, 2, 1), (3, 6, 2, 30), (3, 5, 3, 40)])
+def test_krylov_persistent_matches_launch_sequence(ctx64, d, n, k, M, monkeypatch):
+    # the persistent Arnoldi kernel (one cooperative launch) against the
+    # sequence of separate matvec / Gram-Schmidt launches: same algorithm,
+    # different summation order
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    op = sgkiif.Operator(ctx64, idx, [1.0, 0.5, 0.1][:d])
+    v = dev(np.random.default_rng(11).standard_normal(idx.dof))
+    out = []
+    for legacy in (False, True):
+        if legacy:
+            monkeypatch.setenv("SGK_NO_PERSISTENT", "1")
+        sol = sgkiif.Solver(ctx64, [op], [[]], M, 0.005)
+        wd = torch.empty_like(v)
+        m_eff = sol.krylov_expv(0, v.data_ptr(), wd.data_ptr())
+        out.append((m_eff, wd.cpu().numpy()))
+        sol.close()
+    assert out[0][0] == out[1][0]
+    assert rel(out[0][1], out[1][1]) <= 1e-12
     op.close()
     idx.close()
 

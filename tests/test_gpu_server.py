@@ -1,0 +1,95 @@
+"""The request loop (sgk_server_*): continuous batching of whole IIF2 solves.
+
+Checks, on the GPU:
+  * a request's result is the same alone and in a mix of concurrent requests
+    on a server with the same worker count (bitwise: every kernel sums in a
+    fixed order and the persistent Arnoldi grid depends only on the worker
+    count), and matches the direct solver path within the parity tolerance
+    of its precision (1e-10 FP64, 1e-6 mixed);
+  * requests overlap (more than one runs at once) when the budget allows;
+  * the memory admission serialises requests when only one fits, and
+    rejects a request larger than the whole budget.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1810_11111_gb300 import sgkiif, workloads  # noqa: E402
+from paper_1810_11111_gb300.runner import Problem  # noqa: E402
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cubic(d, n, k, steps, seed):
+    cfg = workloads.cubic3d(n=n, k=k, steps=steps, seed=seed)
+    if d != 3:
+        rng = np.random.default_rng(seed)
+        amp, wn, kind = workloads.fourier_modes(rng, d)
+        cfg.update(d=d, kappas=[[1.0, 0.5, 0.1, 0.7][:d]], init=[dict(amp=amp, wavenum=wn, kind=kind, const=0.0)])
+    return cfg
+
+
+MIX = [
+    (cubic(3, 5, 2, 6, 21), sgkiif.SGK_MIXED),
+    (workloads.schnak2d(n=6, k=1, steps=5, seed=22), sgkiif.SGK_MIXED),
+    (cubic(2, 7, 1, 8, 23), sgkiif.SGK_FP64),
+    (cubic(3, 4, 3, 4, 24), sgkiif.SGK_FP64),
+    (cubic(4, 3, 1, 5, 25), sgkiif.SGK_MIXED),
+]
+
+
+def direct(cfg, prec):
+    p = Problem(cfg, prec)
+    p.reset()
+    p.solver.step(cfg["steps"])
+    out = np.concatenate(p.state())
+    p.close()
+    return out
+
+
+def test_same_alone_and_in_mix():
+    srv = sgkiif.Server(0, workers=3)
+    alone = []
+    for cfg, prec in MIX:
+        t = srv.submit(cfg, prec)
+        out, info = srv.wait(t, cap=4 * sgkiif.dof_of(cfg["d"], cfg["n"], cfg["k"]))
+        assert info["status"] == sgkiif.SGK_OK and info["steps"] == cfg["steps"]
+        alone.append(out)
+    tickets = [srv.submit(cfg, prec) for cfg, prec in MIX for _ in range(2)]
+    mixed = [srv.wait(t, cap=4 * sgkiif.dof_of(cfg["d"], cfg["n"], cfg["k"]))
+             for t, (cfg, prec) in zip(tickets, [m for m in MIX for _ in range(2)])]
+    st = srv.stats()
+    srv.close()
+    assert st["max_concurrent"] >= 2
+    assert st["failed"] == 0
+    for i, (out, info) in enumerate(mixed):
+        assert info["status"] == sgkiif.SGK_OK
+        assert np.array_equal(out, alone[i // 2])
+    for (cfg, prec), a in zip(MIX, alone):
+        tol = 1e-10 if prec == sgkiif.SGK_FP64 else 1e-6
+        assert rel(a, direct(cfg, prec)) <= tol
+
+
+def test_admission_by_memory():
+    cfg = cubic(3, 5, 2, 3, 31)
+    est = int(sgkiif.sgk_estimate_bytes(3, 5, 2, 1, cfg["M"], sgkiif.SGK_MIXED, 1))
+    assert est > 0
+    # room for one request at a time: four workers but no overlap
+    srv = sgkiif.Server(0, workers=4, mem_budget_bytes=int(1.5 * est))
+    ts = [srv.submit(cfg, sgkiif.SGK_MIXED) for _ in range(4)]
+    infos = [srv.wait(t)[1] for t in ts]
+    st = srv.stats()
+    assert all(i["status"] == sgkiif.SGK_OK for i in infos)
+    assert st["max_concurrent"] == 1 and st["peak_reserved_bytes"] <= int(1.5 * est)
+    # larger than the whole budget: rejected at submission
+    with pytest.raises(sgkiif.SgkError) as e:
+        srv.submit(cubic(3, 7, 3, 1, 32), sgkiif.SGK_MIXED)
+    assert e.value.code == sgkiif.SGK_ENOMEM
+    assert srv.stats()["rejected"] == 1
+    srv.close()
