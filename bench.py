@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--served-requests", type=int, default=12,
+                    help="requests of the served leg (0 skips it)")
+    ap.add_argument("--served-workers", type=int, default=4)
     return ap.parse_args()
 
 
@@ -363,12 +366,88 @@ def native(args, rank, world, local_rank):
            "solver": {"newton_iters": st1["newton_iters"] - st0["newton_iters"],
                       "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
            "kernel_ms_warmup": {c: round(v[0], 3) for c, v in warm.items()}}
+    prob.close()
+    if world == 1 and args.served_requests > 0:
+        out["served"] = served_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg)
-    prob.close()
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+# ----------------------------------------------------------- served leg ---
+
+def served_leg(args):
+    """Poisson stream of whole solve requests through the request server
+    (continuous batching over worker streams, memory admission), against the
+    same requests one at a time.  Latency is submit -> result on the host,
+    measured by the server; throughput counts DOF x species x steps of all
+    requests over first submission -> last completion."""
+    from paper_1810_11111_gb300 import sgkiif, workloads
+    reqs, rejected = workloads.served_requests(count=args.served_requests, seed=4, max_nodal_bytes=512 << 20)
+    work = [sgkiif.dof_of(r["d"], r["n"], r["k"]) * len(r["kappas"]) * r["steps"] for r in reqs]
+
+    failures = []
+
+    def record(info):
+        if info["status"] != sgkiif.SGK_OK:
+            failures.append("status %d: %s" % (info["status"], info["error"]))
+        return info["latency_ms"]
+
+    def one_at_a_time(prec):
+        srv = sgkiif.Server(0, workers=1)
+        lat, t0 = [], time.perf_counter()
+        for r in reqs:
+            _, info = srv.wait(srv.submit(r, prec))
+            lat.append(record(info))
+        wall = time.perf_counter() - t0
+        srv.close()
+        return lat, wall
+
+    def summary(lat, wall):
+        lat = np.sort(np.asarray(lat))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "dof_steps_per_s": float(sum(work) / wall), "wall_s": wall}
+
+    # warm: module loading and first-use costs of every kernel shape
+    srv = sgkiif.Server(0, workers=1)
+    for r in reqs:
+        srv.wait(srv.submit(dict(r, steps=1), sgkiif.SGK_MIXED))
+    srv.close()
+    lat_m, wall_m = one_at_a_time(sgkiif.SGK_MIXED)
+    mean_service_s = wall_m / len(reqs)
+    rate = 1.0 / mean_service_s  # offered load = the one-at-a-time capacity
+    arrivals = workloads.poisson_arrivals(len(reqs), rate, seed=4)
+    srv = sgkiif.Server(0, workers=args.served_workers)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, ta in zip(reqs, arrivals):
+        delay = ta - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(r, sgkiif.SGK_MIXED))
+    lat = []
+    for t in tickets:
+        _, info = srv.wait(t)
+        lat.append(record(info))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64)
+    served = summary(lat, wall)
+    base64 = summary(lat64, wall64)
+    return dict(served,
+                workload="served: %d requests (seed 4; d 3-4, level 6-9, degree 1-3, cubic or Schnakenberg, "
+                         "10-100 IIF2 steps, M 30, dt 0.005; draws above 512 MB of finest-grid FP64 nodal "
+                         "values rejected: %d of %d)" % (len(reqs), rejected, len(reqs) + rejected),
+                precision="mixed", workers=args.served_workers, arrival="poisson",
+                rate_per_s=rate, offered_load="one-at-a-time mixed capacity",
+                max_concurrent=st["max_concurrent"], peak_reserved_gb=st["peak_reserved_bytes"] / 1e9,
+                one_at_a_time_mixed=summary(lat_m, wall_m),
+                one_at_a_time_fp64=base64,
+                speedup_vs_fp64_one_at_a_time=served["dof_steps_per_s"] / base64["dof_steps_per_s"],
+                failed_requests=len(failures), first_failure=failures[0] if failures else None)
 
 
 # --------------------------------------------------------- oracle timing ---

@@ -318,6 +318,7 @@ typedef struct sgk_result_info {
     double latency_ms;       /* submit -> result on the host */
     int worker;              /* worker that ran it */
     int64_t newton_iters, inner_iters;
+    char error[160];         /* error text when status != SGK_OK, else empty */
 } sgk_result_info;
 
 typedef struct sgk_server_stats {

@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -128,15 +129,21 @@ struct sgk_server {
 
 namespace {
 
-int run_request(sgk_ctx* ctx, Req& r) {
+int run_request(sgk_ctx* ctx, Req& r, std::string& err) {
     sgk_index* idx = nullptr;
     sgk_op* ops[SGK_MAX_SPECIES] = {nullptr};
     sgk_solver* sol = nullptr;
     DevBuf<double> u0;
-    int rc = sgk_index_build(ctx, r.d, r.n, r.k, &idx);
+    // the first failing call's status and text (later calls reset the text)
+    auto chk = [&](int code) {
+        if (code != SGK_OK && err.empty()) err = ctx->last_error.empty() ? "status " + std::to_string(code)
+                                                                         : ctx->last_error;
+        return code;
+    };
+    int rc = chk(sgk_index_build(ctx, r.d, r.n, r.k, &idx));
     if (rc == SGK_OK) {
         for (int s = 0; s < r.S && rc == SGK_OK; ++s)
-            rc = sgk_operator_assemble(ctx, idx, &r.kappa[(size_t)s * r.d], r.bc, 20.0, &ops[s]);
+            rc = chk(sgk_operator_assemble(ctx, idx, &r.kappa[(size_t)s * r.d], r.bc, 20.0, &ops[s]));
     }
     if (rc == SGK_OK) {
         sgk_reaction f{};
@@ -145,7 +152,7 @@ int run_request(sgk_ctx* ctx, Req& r) {
         f.species = r.rx_species.data();
         f.coef = r.rx_coef.data();
         f.exps = r.rx_exps.data();
-        rc = sgk_solver_create(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, &sol);
+        rc = chk(sgk_solver_create(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, &sol));
     }
     const int64_t dof = idx ? idx->dof : 0;
     if (rc == SGK_OK) {
@@ -153,19 +160,21 @@ int run_request(sgk_ctx* ctx, Req& r) {
             u0.alloc(dof);
         } catch (const SgkError& e) {
             rc = e.code;
+            err = e.msg;
         }
     }
     for (int s = 0; s < r.S && rc == SGK_OK; ++s) {
         const InitCopy& in = r.init[s];
         if (!in.coeffs.empty()) {
-            rc = (int64_t)in.coeffs.size() == dof ? sgk_solver_set_state(sol, s, in.coeffs.data(), 0) : SGK_EINVAL;
+            rc = (int64_t)in.coeffs.size() == dof ? chk(sgk_solver_set_state(sol, s, in.coeffs.data(), 0))
+                                                  : chk(SGK_EINVAL);
         } else {
-            rc = sgk_project_separable(ctx, idx, (int)in.amp.size(), in.amp.data(), in.wavenum.data(), in.kind.data(),
-                                       in.const_term, u0.p);
-            if (rc == SGK_OK) rc = sgk_solver_set_state(sol, s, u0.p, 1);
+            rc = chk(sgk_project_separable(ctx, idx, (int)in.amp.size(), in.amp.data(), in.wavenum.data(),
+                                           in.kind.data(), in.const_term, u0.p));
+            if (rc == SGK_OK) rc = chk(sgk_solver_set_state(sol, s, u0.p, 1));
         }
     }
-    if (rc == SGK_OK) rc = sgk_solver_step(sol, r.nsteps);
+    if (rc == SGK_OK) rc = chk(sgk_solver_step(sol, r.nsteps));
     if (sol) {
         sgk_stats st{};
         sgk_solver_stats(sol, &st);
@@ -175,7 +184,7 @@ int run_request(sgk_ctx* ctx, Req& r) {
         if (rc == SGK_OK) {
             r.result.resize((size_t)r.S * dof);
             for (int s = 0; s < r.S && rc == SGK_OK; ++s)
-                rc = sgk_solver_get_state(sol, s, r.result.data() + (size_t)s * dof, dof, 0);
+                rc = chk(sgk_solver_get_state(sol, s, r.result.data() + (size_t)s * dof, dof, 0));
         }
     }
     r.info.dof = dof;
@@ -208,18 +217,25 @@ void sgk_server::worker(int w) {
             r = slot[w];
         }
         int rc = SGK_ECUDA;
+        std::string err = ok ? "" : "worker could not create its stream or contexts";
         if (ok) {
             sgk_ctx* c = ctx[r->prec == SGK_MIXED ? 1 : 0];
+            c->last_error.clear();
             try {
-                rc = run_request(c, *r);
+                rc = run_request(c, *r, err);
+            } catch (const std::exception& e) {
+                rc = SGK_ECUDA;
+                err = e.what();
             } catch (...) {
                 rc = SGK_ECUDA;
+                err = "unknown exception";
             }
         }
         {
             std::lock_guard<std::mutex> lk(mu);
             r->info.status = rc;
             r->info.worker = w;
+            std::snprintf(r->info.error, sizeof(r->info.error), "%s", err.c_str());
             r->t_done = Clock::now();
             r->info.queue_ms = ms_between(r->t_submit, r->t_admit);
             r->info.run_ms = ms_between(r->t_admit, r->t_done);

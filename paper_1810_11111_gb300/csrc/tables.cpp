@@ -379,10 +379,15 @@ std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma) {
             double m = 0.5 * (S[(size_t)a * H + b] + S[(size_t)b * H + a]);
             S[(size_t)a * H + b] = S[(size_t)b * H + a] = m;
         }
+    // (relative to the two diagonal entries, with a floor of 1e-14 of the
+    // largest diagonal entry for rows whose own diagonal vanishes: the
+    // constant mode under periodic conditions)
+    double dmax = 0.0;
+    for (int a = 0; a < H; ++a) dmax = std::max(dmax, std::fabs(S[(size_t)a * H + a]));
     for (int a = 0; a < H; ++a)
         for (int b = 0; b < H; ++b) {
             double scale = std::sqrt(std::fabs(S[(size_t)a * H + a]) * std::fabs(S[(size_t)b * H + b]));
-            if (std::fabs(S[(size_t)a * H + b]) <= 1e-12 * scale) S[(size_t)a * H + b] = 0.0;
+            if (std::fabs(S[(size_t)a * H + b]) <= std::max(1e-12 * scale, 1e-14 * dmax)) S[(size_t)a * H + b] = 0.0;
         }
     return S;
 }

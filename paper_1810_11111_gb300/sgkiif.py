@@ -57,7 +57,7 @@ class sgk_result_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("nspecies", ctypes.c_int), ("dof", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("est_bytes", ctypes.c_int64), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("worker", ctypes.c_int),
-                ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64)]
+                ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64), ("error", ctypes.c_char * 160)]
 
 
 class sgk_server_stats(ctypes.Structure):
@@ -417,6 +417,7 @@ class Server:
         if rc:
             raise SgkError(rc, "sgk_server_wait failed")
         d = {f: getattr(info, f) for f, _ in sgk_result_info._fields_}
+        d["error"] = d["error"].decode(errors="replace")
         if out is not None:
             out = out[:d["nspecies"] * d["dof"]]
         return out, d
