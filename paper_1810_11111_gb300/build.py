@@ -45,7 +45,7 @@ def build(verbose_ptxas=False, quiet=True):
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     srcs = sources()
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), srcs))
     objs = [r[0] for r in results]
     if verbose_ptxas:

@@ -1,0 +1,4 @@
+// Persistent Arnoldi kernel instantiated for d = 6 (see arnoldi.cu).
+#include "sgk_arnoldi.cuh"
+
+template void sgk_arn::arn_launch_k<6>(sgk_ctx*, const sgk_op*, const sgk_arn::ArnArgs&, int, size_t, int);

@@ -181,8 +181,7 @@ void launch_pyr(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* 
     KTimer kt(ctx, mode);
 #define SGK_PYR_CASE(M, K)                                                                                   \
     if (mode == M && kp1 == K) {                                                                             \
-        SGK_CUDA_CHECK(cudaFuncSetAttribute(pyr_kernel<T, M, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                            (int)smem));                                                     \
+        allow_max_dynamic_smem(ctx->smem_optin, pyr_kernel<T, M, K>);          \
         pyr_kernel<T, M, K><<<grid, 256, smem, ctx->stream>>>(plan.items.p, plan.nitems, plan.groups.p, src, dst, \
                                                               f, H, Nfull);                                 \
     }

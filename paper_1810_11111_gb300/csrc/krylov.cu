@@ -1051,8 +1051,7 @@ void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed
     KTimer kt(ctx, KC_EXPM);
     if (M <= EXPM_CLUSTER_MAX_M) {
         const size_t smem = sizeof(double) * 8 * M * M;
-        SGK_CUDA_CHECK(
-            cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_dynamic_smem(ctx->smem_optin, expm_cluster_kernel);
         expm_cluster_kernel<<<XCL, XTH, smem, ctx->stream>>>(H, M, m_dev, m_fixed, tau, pade13_coefficients(), y);
         check_launch("expm_cluster");
     } else {
@@ -1079,22 +1078,26 @@ static std::atomic<double*> g_expm_scratch_addr[256];
 
 extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream) {
     if (m < 1 || m > SGK_EXPM_NOALLOC_MAX_M || !X_dev || !y_dev) return SGK_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
     if (m <= EXPM_CLUSTER_MAX_M) {
         // the cluster kernel keeps its work matrices in shared memory
         const size_t smem = sizeof(double) * 8 * m * m;
-        if (cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(expm_cluster_kernel)) != cudaSuccess ||
+            cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
             (void)cudaGetLastError();
             return SGK_ECUDA;
         }
         expm_cluster_kernel<<<XCL, XTH, smem, static_cast<cudaStream_t>(cuda_stream)>>>(X_dev, m, nullptr, m, tau,
                                                                                      pade13_coefficients(), y_dev);
         return cudaGetLastError() == cudaSuccess ? SGK_OK : SGK_ECUDA;
-    }
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
-        (void)cudaGetLastError();
-        return SGK_ECUDA;
     }
     double* ws = g_expm_scratch_addr[dev].load(std::memory_order_acquire);
     if (!ws) {

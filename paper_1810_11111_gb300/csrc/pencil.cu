@@ -115,9 +115,13 @@ template <typename T, int D, int KP1, int Q, int S, bool JAC, int DIM>
 struct Quad {
     static constexpr int N = Pow<KP1, D - DIM>::v;
     static constexpr int NS = N / KP1;
+    // the innermost level (whose body is the point evaluation, where most
+    // of the arithmetic is) is unrolled so that its Gauss-table entries are
+    // compile-time operands; the outer levels stay loops
+    static constexpr int UNROLL = DIM == D - 1 ? Q : 1;
     __device__ __forceinline__ static void run(const QuadTab<T>& tb, const Poly<T, S>& P, const T (&Cu)[S][N],
                                                const T (&Cw)[S][N], T (&M)[S][N], T wt) {
-#pragma unroll 1
+#pragma unroll UNROLL
         for (int g = 0; g < Q; ++g) {
             T su[S][NS], sw[S][NS], sm[S][NS];
 #pragma unroll
@@ -393,7 +397,7 @@ void launch_one(sgk_ctx* ctx, const PencilArgs& a, const QuadTab<T>& tb, const d
     const int threads = std::min(256, std::max(64, a.H / KP1));
     const int grid = (int)std::min<long long>(a.npencils, (long long)ctx->num_sms * 16);
     auto kern = pencil_kernel<T, D, KP1, Q, S, JAC>;
-    SGK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem(ctx->smem_optin, kern);
     kern<<<grid, threads, smem, ctx->stream>>>(a, tb, F, poly);
 }
 

@@ -451,10 +451,10 @@ void quad_cells(sgk_ctx* ctx, const Quad& Q, const ReactionDev& rx, bool jac, co
     const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 4);
     KTimer kt(ctx, KC_CELL);
     if (jac) {
-        SGK_CUDA_CHECK(cudaFuncSetAttribute(cell_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_dynamic_smem(ctx->smem_optin, cell_kernel<T, 1>);
         cell_kernel<T, 1><<<grid, 256, smem, ctx->stream>>>(p);
     } else {
-        SGK_CUDA_CHECK(cudaFuncSetAttribute(cell_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_dynamic_smem(ctx->smem_optin, cell_kernel<T, 0>);
         cell_kernel<T, 0><<<grid, 256, smem, ctx->stream>>>(p);
     }
     check_launch("cell_kernel");

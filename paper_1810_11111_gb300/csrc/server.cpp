@@ -274,7 +274,7 @@ int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int 
     b += S * (H * std::min(H, 64.0 * (k + 1)) * 20.0 + H * (n + 1) * 4.0 + ntup * d * (n + 1) * 8.0 + dof / 32.0);
     // solver: state and Krylov workspace (FP64 basis, two work vectors,
     // partial sums of the Gram-Schmidt reductions)
-    b += 8.0 * (4.0 * N + (M + 1.0) * dof + 128.0 + 3.0 * dof);
+    b += 8.0 * (4.0 * N + 2.0 * (M + 1.0) * dof + 128.0 + 3.0 * dof);
     b += 8.0 * (std::max(N / 128.0 + 1.0, 160.0) * (std::max(M, 50.0) + 1.0) + 8.0 * M * M + 3.0 * 160.0 * (M + 1.0));
     if (has_reaction) {
         const double elem = precision == SGK_FP64 ? 8.0 : 4.0;

@@ -1,0 +1,424 @@
+// Persistent Arnoldi kernel (see arnoldi.cu): device code and launch
+// templates.  Each arnoldi_d<D>.cu instantiates arn_launch_k<D> for one
+// dimension, so that the variants compile in parallel.
+#pragma once
+#include <algorithm>
+
+#include "sgk_gmv.h"
+#include "sgk_krylov.h"
+
+namespace sgk_arn {
+
+constexpr int PT = 512;                        // threads per CTA, one CTA per SM
+constexpr int PNW = PT / 32;                   // warps per CTA
+constexpr unsigned BAR_SPIN_LIMIT = 1u << 21;  // polls of ~0.1-0.5 us each
+
+struct ArnArgs {
+    int64_t n;
+    int M;
+    int ldp;  // row stride of the partial-sum buffers (>= M + 1)
+    int E;    // slice length per CTA (ceil(n / gridDim.x))
+    int smem_vz;   // this CTA's slices of V and Z live in shared memory (and V also in HBM)
+    int smem_loc;  // the located rows of every output of the slice live in shared memory
+    const double* v;
+    double* V;  // column c at V + c n
+    double* w0;
+    double* w1;
+    double* Z;     // raw matvec outputs A v_c, column c at Z + c n (own slices only)
+    double* H;     // (M + 1) x M row-major
+    double* pbuf;  // 3 buffers of gridDim.x x ldp
+    unsigned* bar;  // [0] barrier arrivals (zero at launch), [1] error flag
+    KrylovScalars* ks;
+};
+
+// Dynamic shared memory of the kernel, in bytes.
+template <int D>
+size_t arn_smem_bytes(int E, int M, bool vz, bool loc) {
+    size_t b = sizeof(double) * (size_t)E;
+    if (vz) b += sizeof(double) * 2 * (size_t)(M + 1) * E;
+    if (loc) b += sizeof(GmvLoc<D>) * (size_t)E;
+    return b;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All CTAs arrive; returns false if the wait ran out or another CTA failed.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        for (unsigned it = 0;; ++it) {
+            if (ld_acquire(bar) >= target) break;
+            if (it >= BAR_SPIN_LIMIT || ld_acquire(bar + 1) != 0u) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!ok) atomicExch(bar + 1, 1u);
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// out[c] = sum over CTAs b of P[b ldp + c], c < ncols, identical in every
+// CTA.  Each thread sums a fixed subset of rows of one column (all its loads
+// issued at once), the subset sums go through shared memory and one thread
+// per column adds them in a fixed order: FP64 additions with every lane
+// busy, no shuffle trees.  P was written by other CTAs during this launch:
+// L2 loads.
+__device__ __forceinline__ void colsum(const double* P, int nb, int ldp, int ncols, double* out, double* tmp) {
+    // RS row slots per column; ncols * RS <= max(PT, 4 ncols)
+    const int RS = ncols <= PT / 32 ? 32 : (ncols <= PT / 16 ? 16 : (ncols <= PT / 8 ? 8 : 4));
+    for (int base = 0; base < ncols * RS; base += PT) {
+        const int t = base + threadIdx.x;
+        if (t < ncols * RS) {
+            const int c = t / RS, k0 = t - (t / RS) * RS;
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + RS * q;
+                v[q] = k < nb ? __ldcg(P + (int64_t)k * ldp + c) : 0.0;
+            }
+            // the trip count depends on nb and RS only: uniform, so the
+            // additions past the last row slot are not issued
+            double acc = v[0];
+#pragma unroll
+            for (int q = 1; q < 8; ++q)
+                if (RS * q < nb) acc += v[q];
+            for (int k = k0 + 8 * RS; k < nb; k += RS) acc += __ldcg(P + (int64_t)k * ldp + c);
+            tmp[t] = acc;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < ncols) {
+        const double* tc = tmp + threadIdx.x * RS;
+        double a0 = 0.0, a1 = 0.0;
+        for (int k = 0; k < RS; k += 2) {
+            a0 += tc[k];
+            a1 += tc[k + 1];
+        }
+        out[threadIdx.x] = a0 + a1;
+    }
+}
+
+// out[c] = sum_{u < ne} Vl[c vld + u] ws[u], c < ncols (this CTA's slice,
+// Vl/vld its basis columns in shared or global memory); with norm, also
+// out[ncols] = sum ws[u]^2.  A warp per column.
+__device__ __forceinline__ void slice_dots(const double* Vl, int64_t vld, int ncols, const double* ws, int ne,
+                                           double* out, bool norm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nt = ncols + (norm ? 1 : 0);
+    for (int c = wid; c < nt; c += PNW) {
+        const double* vc = c < ncols ? Vl + c * vld : ws;
+        double a = 0.0, b = 0.0;
+        int u = lane;
+        for (; u + 32 < ne; u += 64) {
+            a += vc[u] * ws[u];
+            b += vc[u + 32] * ws[u + 32];
+        }
+        if (u < ne) a += vc[u] * ws[u];
+        a = warp_sum(a + b);
+        if (lane == 0) out[c] = a;
+    }
+}
+
+// w -= V[:, :ncols] h on this CTA's slice, one thread per element (four
+// independent chains).  Writes the staged slice ws, the global w when w is
+// not null, and when vg is not null the next basis column w * inv to vg
+// (global, slice offset included) and vs (shared, or null).
+__device__ __forceinline__ void slice_update(const double* Vl, int64_t vld, int ncols, const double* h, double* w,
+                                             double* ws, int64_t lo, int ne, double* vg, double* vs, double inv) {
+    for (int u = threadIdx.x; u < ne; u += PT) {
+        const double* vi = Vl + u;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 3 < ncols; c += 4) {
+            a0 += vi[c * vld] * h[c];
+            a1 += vi[(c + 1) * vld] * h[c + 1];
+            a2 += vi[(c + 2) * vld] * h[c + 2];
+            a3 += vi[(c + 3) * vld] * h[c + 3];
+        }
+        for (; c < ncols; ++c) a0 += vi[c * vld] * h[c];
+        const double x = ws[u] - ((a0 + a1) + (a2 + a3));
+        ws[u] = x;
+        if (w) w[lo + u] = x;
+        if (vg) {
+            const double y = x * inv;
+            vg[u] = y;
+            if (vs) vs[u] = y;
+        }
+    }
+}
+
+// sum of x^2 over the staged slice, written by thread 0 to *out
+__device__ __forceinline__ void slice_norm2(const double* ws, int ne, double* red, double* out) {
+    double a = 0.0;
+    for (int u = threadIdx.x; u < ne; u += PT) a += ws[u] * ws[u];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double t = warp_sum(threadIdx.x < PNW ? red[threadIdx.x] : 0.0);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+template <int D, int KP1, int G>
+__global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
+    // dynamic shared memory: [ws: E][Vs: (M+1) E][Zs: (M+1) E][loc: E]
+    extern __shared__ __align__(16) double smem[];
+    __shared__ double h1[SGK_MAX_KRYLOV + 2];
+    __shared__ double h2[SGK_MAX_KRYLOV + 2];
+    __shared__ double red[PNW];
+    __shared__ double s_scal[4];
+    // column-sum staging: ncols x (row slots) <= max(PT, 4 (SGK_MAX_KRYLOV + 2))
+    __shared__ double ctmp[PT > 4 * (SGK_MAX_KRYLOV + 2) ? PT : 4 * (SGK_MAX_KRYLOV + 2)];
+    __shared__ int s_ok, s_flag;
+    const int nb = gridDim.x, b = blockIdx.x;
+    const int64_t n = a.n;
+    const int E = a.E;
+    const int64_t lo = std::min<int64_t>(n, (int64_t)b * E);
+    const int ne = (int)(std::min<int64_t>(n, lo + E) - lo);
+    double* const ws = smem;
+    double* const Vs = a.smem_vz ? smem + E : nullptr;
+    double* const Zs = a.smem_vz ? smem + E + (size_t)(a.M + 1) * E : nullptr;
+    GmvLoc<D>* const sloc =
+        a.smem_loc ? reinterpret_cast<GmvLoc<D>*>(smem + E + (a.smem_vz ? 2 * (size_t)(a.M + 1) * E : 0)) : nullptr;
+    // this slice's basis and raw-output columns: shared copies or HBM
+    const double* const Vl = a.smem_vz ? Vs : a.V + lo;
+    const int64_t vld = a.smem_vz ? E : n;
+    double* const Zl = a.smem_vz ? Zs : a.Z + lo;
+    const int64_t zld = a.smem_vz ? E : n;
+    double* const P0 = a.pbuf;                            // V^T w, first pass
+    double* const P1 = a.pbuf + (int64_t)nb * a.ldp;      // second pass and ||w'||^2
+    double* const P2 = a.pbuf + (int64_t)2 * nb * a.ldp;  // norms
+    unsigned epoch = 0;
+    auto barrier = [&]() {
+        ++epoch;
+        return grid_barrier(a.bar, epoch * (unsigned)nb, &s_ok);
+    };
+    const int r = threadIdx.x & (G - 1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    KrylovScalars* ks = a.ks;
+    if (sloc)
+        for (int u = threadIdx.x; u < ne; u += PT) gmv_locate<double, D, KP1>(ga, lo + u, sloc[u]);
+
+    // gamma = ||v||
+    for (int u = threadIdx.x; u < ne; u += PT) ws[u] = a.v[lo + u];
+    __syncthreads();
+    slice_norm2(ws, ne, red, P2 + (int64_t)b * a.ldp);
+    if (!barrier()) return;
+    colsum(P2, nb, a.ldp, 1, s_scal, ctmp);
+    __syncthreads();
+    // scalar FP64 work (square roots, reciprocals, the Frobenius norm of H)
+    // stays on warp 0 and is broadcast through shared memory: FP64 issue is
+    // about two operations per clock per SM on this part
+    if (threadIdx.x == 0) {
+        const double gamma = sqrt(s_scal[0]);
+        s_scal[1] = gamma > 0.0 ? 1.0 / gamma : 0.0;
+        if (b == 0) {
+            ks->gamma = gamma;
+            ks->inv_gamma = s_scal[1];
+            ks->fro2 = 0.0;
+            ks->stop = gamma > 0.0 ? 0 : 1;
+            ks->m_eff = 0;
+            ks->breakdown = 0;
+        }
+    }
+    __syncthreads();
+    if (!(s_scal[1] > 0.0)) return;  // gamma = 0: the same decision in every CTA
+    double scale = s_scal[1];
+    for (int u = threadIdx.x; u < ne; u += PT) {
+        const double y = ws[u] * scale;
+        a.V[lo + u] = y;
+        if (Vs) Vs[u] = y;
+    }
+    // the next matvec gathers x (written by all CTAs) and forms
+    // A v_j = scale (A x - corr), corr = sum_c hp_c A v_c over the previous
+    // step's columns: with the norm taken by Pythagoras, x is w' (complete at
+    // the second barrier) and A v_j = (A w' - A V h2) / beta, A V being the
+    // stored raw matvec outputs of the slice; after an explicit norm x is w''
+    const double* x = a.v;
+    int ncorr = 0;                 // columns of the correction (0: none)
+    double fro2 = 0.0, sub = 0.0;  // kept alike by every lane of warp 0
+    for (int j = 0; j < a.M; ++j) {
+        double* w = (j & 1) ? a.w1 : a.w0;
+        const int nc = j + 1;
+        // A v_j on this slice, staged in shared memory and kept in Z
+        for (int base = 0; base < ne; base += PT / G) {
+            const int u = base + (int)threadIdx.x / G;
+            double acc = 0.0;
+            if (u < ne) {
+                if (sloc) {
+                    acc = gmv_accumulate<double, D, G, true>(ga, x, sloc[u], r);
+                } else {
+                    GmvLoc<D> l1;
+                    gmv_locate<double, D, KP1>(ga, lo + u, l1);
+                    acc = gmv_accumulate<double, D, G, true>(ga, x, l1, r);
+                }
+                // the correction's columns are shared out over the group's
+                // lanes like the matrix rows
+                const double* zi = Zl + u;
+                for (int c = r; c < ncorr; c += G) acc -= h2[c] * zi[c * zld];
+            }
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (u < ne && r == 0) {
+                acc *= scale;
+                ws[u] = acc;
+                Zl[(int64_t)j * zld + u] = acc;
+            }
+        }
+        __syncthreads();
+        slice_dots(Vl, vld, nc, ws, ne, P0 + (int64_t)b * a.ldp, false);
+        if (!barrier()) return;
+        colsum(P0, nb, a.ldp, nc, h1, ctmp);
+        __syncthreads();
+        // w' = w - V h1, published for the next matvec
+        slice_update(Vl, vld, nc, h1, w, ws, lo, ne, nullptr, nullptr, 0.0);
+        __syncthreads();
+        // second pass: V^T w' and ||w'||^2 in one reduction
+        slice_dots(Vl, vld, nc, ws, ne, P1 + (int64_t)b * a.ldp, true);
+        if (!barrier()) return;
+        colsum(P1, nb, a.ldp, nc + 1, h2, ctmp);
+        __syncthreads();
+        // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal, w'' = w' - V h2);
+        // when the second pass removed more than 1e-3 of ||w'||^2 (near
+        // breakdown) the norm is summed explicitly instead
+        if (wid == 0) {
+            double part = 0.0, hh = 0.0;
+            for (int i = lane; i < nc; i += 32) {
+                const double hv = h1[i] + h2[i];
+                part += hv * hv;
+                hh += h2[i] * h2[i];
+            }
+            part = warp_sum(part);
+            hh = warp_sum(hh);
+            const double wn2 = h2[nc];
+            const double b2 = wn2 - hh;
+            if (lane == 0) {
+                s_flag = !(hh <= 1e-3 * wn2) || !(b2 > 0.0);
+                s_scal[0] = b2;
+                s_scal[2] = part;
+            }
+        }
+        __syncthreads();
+        const bool explicit_norm = s_flag != 0;
+        if (explicit_norm) {
+            // w'' in place (published), its norm through a third barrier
+            slice_update(Vl, vld, nc, h2, w, ws, lo, ne, nullptr, nullptr, 0.0);
+            __syncthreads();
+            slice_norm2(ws, ne, red, P2 + (int64_t)b * a.ldp);
+            if (!barrier()) return;
+            colsum(P2, nb, a.ldp, 1, s_scal, ctmp);
+            __syncthreads();
+        }
+        // column j of H and the breakdown test: warp 0 of every CTA, alike
+        if (wid == 0) {
+            const double b2 = s_scal[0];
+            const double f = fro2 + sub * sub + s_scal[2];
+            // one reciprocal square root on two lanes: 1/beta and sqrt(f)
+            const double xin = lane == 0 ? b2 : f;
+            const double rs = xin > 0.0 ? rsqrt(xin) : 0.0;
+            const double inv = __shfl_sync(0xffffffffu, rs, 0);
+            const double sf = f > 0.0 ? f * __shfl_sync(0xffffffffu, rs, 1) : 0.0;
+            const double beta = b2 > 0.0 ? b2 * inv : 0.0;
+            fro2 = f;
+            sub = beta;
+            const bool brk = !(beta > 1e-12 * sf);
+            if (b == 0)
+                for (int i = lane; i < nc; i += 32) a.H[(int64_t)i * a.M + j] = h1[i] + h2[i];
+            if (lane == 0) {
+                s_scal[1] = brk ? 0.0 : inv;
+                if (b == 0) {
+                    a.H[(int64_t)(j + 1) * a.M + j] = beta;
+                    ks->fro2 = f;
+                    ks->m_eff = j + 1;
+                    if (brk) {
+                        ks->stop = 1;
+                        ks->breakdown = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!(s_scal[1] > 0.0)) return;  // breakdown: the same decision in every CTA
+        scale = s_scal[1];
+        double* vg = a.V + (int64_t)(j + 1) * n + lo;
+        double* vs = Vs ? Vs + (int64_t)(j + 1) * E : nullptr;
+        if (explicit_norm) {
+            for (int u = threadIdx.x; u < ne; u += PT) {
+                const double y = ws[u] * scale;
+                vg[u] = y;
+                if (vs) vs[u] = y;
+            }
+            ncorr = 0;
+        } else {
+            // v_{j+1} = (w' - V h2) / beta on the slice; w' stays published
+            slice_update(Vl, vld, nc, h2, nullptr, ws, lo, ne, vg, vs, scale);
+            ncorr = nc;
+        }
+        x = w;
+        // the next step overwrites ws only after its matvec, which reads x
+        // (global) and nothing staged; h2 stays until the next second pass
+        __syncthreads();
+    }
+}
+
+template <int D, int KP1, int G>
+void arn_launch(sgk_ctx* ctx, const sgk_op* op, const ArnArgs& a, int nb, size_t smem) {
+    auto kern = arnoldi_kernel<D, KP1, G>;
+    const GmvArgs<double, D> ga = make_gmv_args<double, D>(op);
+    allow_max_dynamic_smem(ctx->smem_optin, kern);
+    int occ = 0;
+    SGK_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PT, smem));
+    SGK_REQUIRE(occ >= 1 && nb <= occ * ctx->num_sms, SGK_EUNSUPPORTED, "persistent Arnoldi grid does not fit");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SGK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, ga, a));
+}
+
+template <int D, int KP1>
+void arn_launch_g(sgk_ctx* ctx, const sgk_op* op, const ArnArgs& a, int nb, size_t smem, int G) {
+    switch (G) {
+        case 1: arn_launch<D, KP1, 1>(ctx, op, a, nb, smem); break;
+        case 2: arn_launch<D, KP1, 2>(ctx, op, a, nb, smem); break;
+        case 4: arn_launch<D, KP1, 4>(ctx, op, a, nb, smem); break;
+        default: arn_launch<D, KP1, 8>(ctx, op, a, nb, smem); break;
+    }
+}
+
+template <int D>
+void arn_launch_k(sgk_ctx* ctx, const sgk_op* op, const ArnArgs& a, int nb, size_t smem, int G) {
+    switch (op->idx->k + 1) {
+        case 2: arn_launch_g<D, 2>(ctx, op, a, nb, smem, G); break;
+        case 3: arn_launch_g<D, 3>(ctx, op, a, nb, smem, G); break;
+        case 4: arn_launch_g<D, 4>(ctx, op, a, nb, smem, G); break;
+        default: throw SgkError{SGK_EUNSUPPORTED, "persistent Arnoldi: degree must be 1..3"};
+    }
+}
+
+}  // namespace sgk_arn

@@ -31,11 +31,18 @@ struct GmvArgs {
     T kneg[D];  // -kappa_i
 };
 
-// Partial sum of lane r (0 <= r < G) for output g; the G partials of a
-// group add up to y_g.  CG selects L2-only loads of x, for vectors written
-// by other CTAs of the same (persistent) kernel.
-template <typename T, int D, int KP1, int G, bool CG>
-__device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restrict__ x, int64_t g, int r) {
+// Where output g's rows live: per direction the row range [q0, qe) of the
+// 1D matrix and the terms of the source address base[lb] + (oI << (lb-1))
+// + p I + in (oI = o I (k+1), lb >= 1; oI itself for lb = 0).
+template <int D>
+struct GmvLoc {
+    int cbrow[D];  // offset of the (tuple, direction) row of the block-offset table
+    int q0[D], qe[D];
+    int64_t oI[D], I[D], in[D];
+};
+
+template <typename T, int D, int KP1>
+__device__ __forceinline__ void gmv_locate(const GmvArgs<T, D>& a, int64_t g, GmvLoc<D>& L) {
     const int nl = a.N + 1;
     // tuple of g: binary search between the tuples of the chunk's ends
     int lo = a.chunk[g >> 8], hi = a.chunk[(g >> 8) + 1];
@@ -62,7 +69,6 @@ __device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restric
         c[m] = (int)(e - q * cnt[m]);
         e = q;
     }
-    T acc = T(0);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         int64_t o = 0, in = 0, I = 1;
@@ -75,10 +81,26 @@ __device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restric
         }
         const int np = a.N - (sum - lv[i]);
         const int ai = (lv[i] ? (KP1 << (lv[i] - 1)) : 0) + c[i];
-        const int64_t* __restrict__ base = a.cb + ((int64_t)t * D + i) * nl;
-        const int q0 = a.rp[ai];
-        const int qe = q0 + a.rlen[ai * nl + np];
-        const int64_t oI = o * I * KP1;  // o n_lb I = (o I KP1) << (lb - 1) for lb >= 1
+        L.cbrow[i] = (t * D + i) * nl;
+        L.q0[i] = a.rp[ai];
+        L.qe[i] = L.q0[i] + a.rlen[ai * nl + np];
+        L.oI[i] = o * I * KP1;
+        L.I[i] = I;
+        L.in[i] = in;
+    }
+}
+
+// Partial sum of lane r (0 <= r < G) of a located output; the G partials of
+// a group add up to y_g.  CG selects L2-only loads of x, for vectors written
+// by other CTAs of the same (persistent) kernel.
+template <typename T, int D, int G, bool CG>
+__device__ __forceinline__ T gmv_accumulate(const GmvArgs<T, D>& a, const T* __restrict__ x, const GmvLoc<D>& L,
+                                            int r) {
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const int64_t* __restrict__ base = a.cb + L.cbrow[i];
+        const int64_t oI = L.oI[i], I = L.I[i], in = L.in[i];
         auto ld = [&](int pk) {
             const int lb = pk >> 16, p = pk & 0xffff;
             const int64_t ob = lb ? (oI << (lb - 1)) : oI;
@@ -86,8 +108,9 @@ __device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restric
             if constexpr (CG) return __ldcg(px);
             else return *px;
         };
+        const int qe = L.qe[i];
         T s0 = T(0), s1 = T(0);
-        int q = q0 + r;
+        int q = L.q0[i] + r;
         for (; q + G < qe; q += 2 * G) {
             const int p0 = a.ce[q], p1 = a.ce[q + G];
             const T v0 = a.cv[q], v1 = a.cv[q + G];
@@ -98,6 +121,13 @@ __device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restric
         acc += a.kneg[i] * (s0 + s1);
     }
     return acc;
+}
+
+template <typename T, int D, int KP1, int G, bool CG>
+__device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restrict__ x, int64_t g, int r) {
+    GmvLoc<D> L;
+    gmv_locate<T, D, KP1>(a, g, L);
+    return gmv_accumulate<T, D, G, CG>(a, x, L, r);
 }
 
 template <typename T, int D>

@@ -129,6 +129,18 @@ struct sgk_ctx {
     ~sgk_ctx();
 };
 
+// Raises a kernel's dynamic shared-memory limit to the most the device allows
+// next to its static shared memory.  The value is the same on every call, so
+// threads launching the same kernel with different sizes (a server's workers)
+// cannot lower the limit under one another's launch.
+template <typename K>
+void allow_max_dynamic_smem(size_t smem_optin, K kern) {
+    cudaFuncAttributes fa;
+    SGK_CUDA_CHECK(cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(kern)));
+    SGK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(smem_optin - fa.sharedSizeBytes)));
+}
+
 // Every kernel launch of the library goes through this counter.
 inline void count_launch(sgk_ctx* c, int n = 1) { c->launches += n; }
 void check_launch(const char* what);

@@ -39,8 +39,10 @@ struct KrylovWork {
 // Extra device workspace of the persistent Arnoldi kernel (arnoldi.cu).
 struct PersistentWork {
     double* w_alt = nullptr;  // second work vector (n)
+    double* Z = nullptr;      // raw matvec outputs, (M + 1) n
     double* pbuf = nullptr;   // arnoldi_persistent_pbuf_size doubles
     unsigned* bar = nullptr;  // [0] barrier arrivals, [1] error flag (sticky until the host clears it)
+    int G = 0;                // lanes per output in the matvec (0: default)
 };
 
 // Largest n (and the partial-sum buffer size) the persistent kernel takes on
@@ -51,6 +53,11 @@ size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M);
 // cooperative launch.
 void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
                         const double* v, int64_t n, int M);
+// Times the candidate lane counts of the matvec on this operator and size
+// (scratch: n doubles of device memory) and returns the fastest; the runs
+// overwrite the Krylov workspace.  Not while a graph is being captured.
+int arnoldi_autotune(sgk_ctx* ctx, const sgk_op* op, PersistentWork pw, const KrylovWork<double>& kw, double* scratch,
+                     int64_t n, int M);
 // exp(dt A) v by the persistent Arnoldi kernel, expm and the combination
 void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
                             const double* v, double* W, long long n, int M, double dt);

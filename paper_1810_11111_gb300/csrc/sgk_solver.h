@@ -36,7 +36,8 @@ struct sgk_solver {
     // persistent Arnoldi: second work vector, partial sums, per species a
     // barrier counter and an error flag
     bool persistent = false;
-    DevBuf<double> w64b, pbuf;
+    int arn_G = 0;  // autotuned lanes per output of the persistent matvec
+    DevBuf<double> w64b, zbuf, pbuf;
     DevBuf<unsigned> pbar;
     // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
     DevBuf<double> q64, jw64;
@@ -45,6 +46,13 @@ struct sgk_solver {
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     bool use_graphs = true;
     GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_resid, g_cg;
+    // device-driven step: the whole IIF2 step (predictor, Krylov, Newton with
+    // CG) as one graph whose loops are conditional while-nodes
+    GraphCache g_step;
+    cudaStream_t aux[2] = {nullptr, nullptr};  // capture streams of the loop bodies
+    DevBuf<unsigned char> ctl;                 // StepCtl on the device
+    // kernels per segment of the step graph (for the launch count)
+    int64_t n_prefix = 0, n_resid = 0, n_cgpre = 0, n_cgbody = 0, n_adv = 0;
     sgk_stats stats{};
     ~sgk_solver();
 };

@@ -376,8 +376,10 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
     if (s->persistent) {
         PersistentWork pw;
         pw.w_alt = s->w64b.p;
+        pw.Z = s->zbuf.p;
         pw.pbuf = s->pbuf.p;
         pw.bar = s->pbar.p + 2 * species;
+        pw.G = s->arn_G;
         krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, s->dt);
     } else {
         auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
@@ -386,8 +388,272 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
     if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
 }
 
+// ------------------------------------------------ device-driven step ---
+//
+// With graphs on and one species (CG) or no reaction, a whole IIF2 step is
+// one CUDA graph: the Newton iteration and the CG iteration are conditional
+// while-nodes whose conditions are set by one-thread control kernels from the
+// residual norms, so a step needs one host synchronisation (to read the
+// outcome) instead of one per Newton and CG iteration.  The control logic is
+// that of the host loop: stop at ||G|| <= tol max(1, ||W||), the mixed-mode
+// acceptance of a stagnating residual below 1e-8 max(1, ||W||), at most
+// max_iter corrections, CG to a relative residual inner_tol.
+
+namespace {
+
+struct StepCtl {
+    double stop, floor_accept, prev, last_g, cg_stop;
+    int it, status, cg_iters, pad;
+    long long newton_iters, inner_iters;
+};
+
+__global__ void newton_init_kernel(StepCtl* c, const double* wnorm, double tol) {
+    const double w = fmax(1.0, *wnorm);
+    c->stop = tol * w;
+    c->floor_accept = 1e-8 * w;
+    c->prev = INFINITY;
+    c->last_g = 0.0;
+    c->it = 0;
+    c->status = SGK_ENEWTON;
+    c->cg_iters = 0;
+    c->newton_iters = 0;
+    c->inner_iters = 0;
+}
+
+__global__ void newton_control_kernel(StepCtl* c, const double* gnorm, cudaGraphConditionalHandle h, int max_iter,
+                                      int mixed) {
+    const double g = *gnorm;
+    c->last_g = g;
+    unsigned go = 0;
+    if (!isfinite(g)) c->status = SGK_ENEWTON;
+    else if (g <= c->stop) c->status = SGK_OK;
+    else if (mixed && c->it >= 1 && g > 0.5 * c->prev && g <= c->floor_accept) c->status = SGK_OK;
+    else if (c->it >= max_iter) c->status = SGK_ENEWTON;
+    else {
+        c->prev = g;
+        go = 1;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+__global__ void cg_init_kernel(StepCtl* c, const double* rr, double inner_tol, int inner_max,
+                               cudaGraphConditionalHandle h) {
+    const double r = *rr;
+    c->cg_stop = inner_tol * inner_tol * r;
+    c->cg_iters = 0;
+    cudaGraphSetConditional(h, (inner_max > 0 && r > c->cg_stop) ? 1u : 0u);
+}
+
+__global__ void cg_control_kernel(StepCtl* c, double* rr, const double* rr_new, int inner_max,
+                                  cudaGraphConditionalHandle h) {
+    const double r = *rr_new;
+    *rr = r;
+    c->cg_iters += 1;
+    cudaGraphSetConditional(h, (c->cg_iters < inner_max && r > c->cg_stop) ? 1u : 0u);
+}
+
+__global__ void newton_advance_kernel(StepCtl* c) {
+    c->inner_iters += c->cg_iters;
+    c->newton_iters += 1;
+    c->it += 1;
+}
+
+// Adds a while-node at the capture position of ctx->stream: pre(h) is
+// captured first (it sets the first condition), then the node, whose body
+// body(h) is captured on aux (ctx->stream points there meanwhile).
+template <typename Pre, typename Body>
+void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
+    cudaStream_t st = ctx->stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    SGK_CUDA_CHECK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    SGK_REQUIRE(cs == cudaStreamCaptureStatusActive, SGK_ECUDA, "step graph: stream is not capturing");
+    cudaGraphConditionalHandle h;
+    SGK_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    pre(h);
+    SGK_CUDA_CHECK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    SGK_CUDA_CHECK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    SGK_CUDA_CHECK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+    SGK_CUDA_CHECK(cudaStreamBeginCaptureToGraph(aux, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = aux;
+    try {
+        body(h);
+    } catch (...) {
+        ctx->stream = st;
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(aux, &tmp);
+        throw;
+    }
+    ctx->stream = st;
+    cudaGraph_t out = nullptr;
+    SGK_CUDA_CHECK(cudaStreamEndCapture(aux, &out));
+}
+
+bool step_graph_eligible(const sgk_solver* s) { return s->use_graphs && (!s->has_rx || s->nspecies == 1); }
+
+void build_step_graph(sgk_solver* s) {
+    sgk_ctx* ctx = s->ctx;
+    const long long n = s->n, N = n * s->nspecies;
+    const double dt2 = 0.5 * s->dt;
+    StepCtl* ctl = reinterpret_cast<StepCtl*>(s->ctl.p);
+    for (int i = 0; i < 2; ++i)
+        if (!s->aux[i]) SGK_CUDA_CHECK(cudaStreamCreateWithFlags(&s->aux[i], cudaStreamNonBlocking));
+    const int64_t before = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    ctx->capturing = true;
+    SGK_CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (s->has_rx) {
+            evalF(s, s->U.p, s->Fv.p);
+            vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
+        } else {
+            SGK_CUDA_CHECK(
+                cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        for (int sp = 0; sp < s->nspecies; ++sp) solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n);
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (s->has_rx) {
+            const int mixed = s->prec == SGK_MIXED ? 1 : 0;
+            double* const rr = s->scal.p + 2;
+            double* const rr_new = s->scal.p + 3;
+            double* const pq = s->scal.p + 4;
+            vk_dot(ctx, s->W.p, s->W.p, N, s->partials.p, s->scal.p + 6, 1, nullptr);
+            newton_init_kernel<<<1, 1, 0, ctx->stream>>>(ctl, s->scal.p + 6, s->opts.tol);
+            count_launch(ctx);
+            auto resid = [&](cudaGraphConditionalHandle h) {
+                evalF(s, s->U.p, s->Fv.p);
+                vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
+                vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
+                newton_control_kernel<<<1, 1, 0, ctx->stream>>>(ctl, s->scal.p + 7, h, s->opts.max_iter, mixed);
+                count_launch(ctx);
+            };
+            int64_t mark = 0;
+            capture_while(
+                ctx, s->aux[0],
+                [&](cudaGraphConditionalHandle h) {
+                    mark = ctx->launches;
+                    resid(h);
+                    s->n_resid = ctx->launches - mark;
+                },
+                [&](cudaGraphConditionalHandle hn) {
+                    s->n_prefix = ctx->launches - before;
+                    mark = ctx->launches;
+                    double* x = s->cg_x.p;
+                    double* r = s->cg_r.p;
+                    double* pv = s->cg_p.p;
+                    double* q = s->cg_q.p;
+                    capture_while(
+                        ctx, s->aux[1],
+                        [&](cudaGraphConditionalHandle hc) {
+                            SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
+                            vk_axpby(ctx, -1.0, s->G.p, 0.0, s->G.p, r, N);
+                            vk_axpby(ctx, -1.0, s->G.p, 0.0, s->G.p, pv, N);
+                            vk_dot(ctx, r, r, N, s->partials.p, rr, 0, nullptr);
+                            cg_init_kernel<<<1, 1, 0, ctx->stream>>>(ctl, rr, s->opts.inner_tol, s->opts.inner_max, hc);
+                            count_launch(ctx);
+                            s->n_cgpre = ctx->launches - mark;
+                        },
+                        [&](cudaGraphConditionalHandle hc) {
+                            mark = ctx->launches;
+                            apply_newton_matrix(s, pv, q);
+                            vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
+                            vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
+                            vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
+                            vk_cg_direction(ctx, pv, r, rr_new, rr, N);
+                            cg_control_kernel<<<1, 1, 0, ctx->stream>>>(ctl, rr, rr_new, s->opts.inner_max, hc);
+                            count_launch(ctx);
+                            s->n_cgbody = ctx->launches - mark;
+                        });
+                    mark = ctx->launches;
+                    vk_axpby(ctx, 1.0, s->U.p, 1.0, x, s->U.p, N);
+                    newton_advance_kernel<<<1, 1, 0, ctx->stream>>>(ctl);
+                    count_launch(ctx);
+                    s->n_adv = ctx->launches - mark;
+                    resid(hn);
+                });
+        } else {
+            s->n_prefix = ctx->launches - before;
+        }
+    } catch (...) {
+        cudaStreamEndCapture(ctx->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        ctx->capturing = false;
+        ctx->launches = before;
+        throw;
+    }
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->capturing = false;
+    ctx->launches = before;
+    SGK_CUDA_CHECK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&s->g_step.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SGK_CUDA_CHECK(ei);
+}
+
+// One device-driven step; returns the step's status.
+int device_step(sgk_solver* s) {
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    if (!s->g_step.exec) build_step_graph(s);
+    KTimer kt(ctx, KC_KRYLOV);
+    SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
+    StepCtl c{};
+    KrylovScalars ks[SGK_MAX_SPECIES];
+    unsigned flags[2 * SGK_MAX_SPECIES] = {0};
+    if (s->has_rx)
+        SGK_CUDA_CHECK(cudaMemcpyAsync(&c, s->ctl.p, sizeof(StepCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    SGK_CUDA_CHECK(cudaMemcpyAsync(ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    if (s->persistent)
+        SGK_CUDA_CHECK(cudaMemcpyAsync(flags, s->pbar.p, 2 * s->nspecies * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+    SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    int rc = s->has_rx ? c.status : SGK_OK;
+    count_launch(ctx, (int)(s->n_prefix + c.newton_iters * (s->n_cgpre + s->n_adv + s->n_resid) +
+                            c.inner_iters * s->n_cgbody));
+    s->stats.newton_iters += c.newton_iters;
+    s->stats.inner_iters += c.inner_iters;
+    if (s->has_rx) s->stats.last_newton_residual = c.last_g;
+    s->stats.krylov_calls += s->nspecies;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        s->stats.krylov_breakdowns += ks[sp].breakdown;
+        s->stats.last_m_eff = ks[sp].m_eff;
+    }
+    bool timed_out = false;
+    for (int sp = 0; sp < s->nspecies; ++sp) timed_out = timed_out || flags[2 * sp + 1] != 0u;
+    if (timed_out) {
+        SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * s->nspecies * sizeof(unsigned), ctx->stream));
+        rc = SGK_ETIMEOUT;
+    }
+    if (rc != SGK_OK) {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    return rc;
+}
+
+}  // namespace
+
 int solver_step(sgk_solver* s, int nsteps) {
     sgk_ctx* ctx = s->ctx;
+    if (step_graph_eligible(s) && !ctx->prof_mask) {
+        for (int step = 0; step < nsteps; ++step) {
+            const int rc = device_step(s);
+            if (rc != SGK_OK) return rc;
+            s->stats.steps += 1;
+        }
+        return SGK_OK;
+    }
     const long long n = s->n, N = n * s->nspecies;
     const double dt2 = 0.5 * s->dt;
     for (int step = 0; step < nsteps; ++step) {
@@ -466,11 +732,23 @@ void solver_alloc(sgk_solver* s) {
     s->expm_ws.alloc(8 * (size_t)M * M);
     s->ks.alloc(S);
     s->counters.alloc(4);
+    s->ctl.alloc(sizeof(StepCtl));
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->ctl.p, 0, sizeof(StepCtl), s->ctx->stream));
     s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && n <= arnoldi_persistent_max_n(s->ctx);
     if (s->persistent) {
         s->w64b.alloc(n);
+        s->zbuf.alloc((size_t)(M + 1) * n);
         s->pbuf.alloc(arnoldi_persistent_pbuf_size(s->ctx, M));
         s->pbar.alloc(2 * S);
+        SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
+        // tune the matvec's lanes per output on this operator and size (the
+        // runs use the Krylov workspace and W, which hold nothing yet)
+        PersistentWork pw;
+        pw.w_alt = s->w64b.p;
+        pw.Z = s->zbuf.p;
+        pw.pbuf = s->pbuf.p;
+        pw.bar = s->pbar.p;
+        s->arn_G = arnoldi_autotune(s->ctx, s->ops[0], pw, krylov_work<double>(s, 0), s->W.p, n, M);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
     }
     SGK_CUDA_CHECK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(unsigned), s->ctx->stream));
@@ -504,6 +782,9 @@ void solver_alloc(sgk_solver* s) {
 }
 
 sgk_solver::~sgk_solver() {
+    if (g_step.exec) cudaGraphExecDestroy(g_step.exec);
+    for (cudaStream_t& a : aux)
+        if (a) cudaStreamDestroy(a);
     for (GraphCache* g : {&g_pred, &g_resid, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     for (auto& g : g_krylov)
