@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=12,
                     help="requests of the served leg (0 skips it)")
     ap.add_argument("--served-workers", type=int, default=4)
+    ap.add_argument("--batch-instances", type=int, default=32,
+                    help="instances of the batched leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -125,8 +127,9 @@ def layout_sizes(d, n, k):
 
 
 # DRAM bytes (read + write) of one Jacobian launch of the pencil kernel from
-# the committed ncu capture, keyed by (d, level, degree, precision)
-PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56.647168e6 + 0.162048e6}
+# the committed ncu capture of the current kernel, keyed by (d, level,
+# degree, precision); empty until a capture of this kernel version exists
+PENCIL_TRAFFIC = {}
 
 
 def pencil_q(cfg):
@@ -345,7 +348,8 @@ def native(args, rank, world, local_rank):
                                       "frac": bytes_algo / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_kind},
                             traffic=PENCIL_TRAFFIC.get((d, N, cfg["k"], args.precision)),
                             traffic_note="dram read + write of one Jacobian launch, ncu cold capture "
-                                         "(profiles/pencil_kernel_cubic3d_l6k2_fp32.md)")
+                                         "(profiles/pencil_kernel_cubic3d_l6k2_fp32.md); null when no capture "
+                                         "of the current kernel exists")
         else:
             achieved = bytes_algo / t / 1e9
             roofline = dict(common, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
@@ -367,6 +371,8 @@ def native(args, rank, world, local_rank):
                       "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
            "kernel_ms_warmup": {c: round(v[0], 3) for c, v in warm.items()}}
     prob.close()
+    if world == 1 and args.batch_instances > 0:
+        out["batched"] = batched_leg(args)
     if world == 1 and args.served_requests > 0:
         out["served"] = served_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -374,6 +380,49 @@ def native(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+# ---------------------------------------------------------- batched leg ---
+
+def batched_leg(args):
+    """Independent scalar cubic instances of uneven size (seed 3) stepped
+    together through sgk_batch_* (device-driven step graphs on 8 streams),
+    against the same batch on one stream (instances one after another)."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif, workloads
+    insts, rejected = workloads.batch_instances(count=args.batch_instances, seed=3, max_nodal_bytes=256 << 20)
+    work_per_step = sum(sgkiif.dof_of(c["d"], c["n"], c["k"]) for c in insts)
+    steps = max(1, min(args.steps, 10))
+    res = {}
+    states = {}
+    for streams, prec in ((8, sgkiif.SGK_MIXED), (1, sgkiif.SGK_MIXED), (8, sgkiif.SGK_FP64)):
+        b = sgkiif.Batch(0, streams=streams)
+        for c in insts:
+            b.add(c, prec)
+        rc, _ = b.step(1)  # graph capture and first launches
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc2, st = b.step(steps)
+        wall = time.perf_counter() - t0
+        states[(streams, prec)] = [np.concatenate(b.state(i)) for i in range(len(insts))]
+        b.close()
+        res[(streams, prec)] = dict(dof_steps_per_s=work_per_step * steps / wall, wall_s=wall,
+                                    failed=sum(1 for x in st if x != sgkiif.SGK_OK), status=max(rc, rc2))
+    err = max(float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
+              for m, f in zip(states[(8, sgkiif.SGK_MIXED)], states[(8, sgkiif.SGK_FP64)]))
+    fp64 = res[(8, sgkiif.SGK_FP64)]
+    res = {8: res[(8, sgkiif.SGK_MIXED)], 1: res[(1, sgkiif.SGK_MIXED)]}
+    return dict(workload="batch: %d scalar cubic instances (seed 3; d 2-4, level 5-8, degree 1-2, kappa_i ~ "
+                         "U(0.05,1), f = -c u^3 with c ~ U(1,100), 8-mode Fourier u0; M 30, dt 0.005; draws above "
+                         "256 MB of finest-grid FP64 nodal values rejected: %d of %d)"
+                         % (len(insts), rejected, len(insts) + rejected),
+                precision="mixed", dof_total=work_per_step, steps=steps, streams=8,
+                dof_steps_per_s=res[8]["dof_steps_per_s"], wall_s=res[8]["wall_s"],
+                one_stream_dof_steps_per_s=res[1]["dof_steps_per_s"],
+                speedup_vs_one_stream=res[8]["dof_steps_per_s"] / res[1]["dof_steps_per_s"],
+                failed_instances=res[8]["failed"], fp64_dof_steps_per_s=fp64["dof_steps_per_s"],
+                max_rel_l2_vs_fp64=err,
+                timing="host wall clock around the batch steps (each step waits for every stream)")
 
 
 # ----------------------------------------------------------- served leg ---
@@ -395,12 +444,16 @@ def served_leg(args):
             failures.append("status %d: %s" % (info["status"], info["error"]))
         return info["latency_ms"]
 
-    def one_at_a_time(prec):
+    caps = [4 * sgkiif.dof_of(r["d"], r["n"], r["k"]) for r in reqs]
+
+    def one_at_a_time(prec, outs=None):
         srv = sgkiif.Server(0, workers=1)
         lat, t0 = [], time.perf_counter()
-        for r in reqs:
-            _, info = srv.wait(srv.submit(r, prec))
+        for r, cap in zip(reqs, caps):
+            out, info = srv.wait(srv.submit(r, prec), cap=cap)
             lat.append(record(info))
+            if outs is not None:
+                outs.append(out)
         wall = time.perf_counter() - t0
         srv.close()
         return lat, wall
@@ -427,14 +480,18 @@ def served_leg(args):
         if delay > 0:
             time.sleep(delay)
         tickets.append(srv.submit(r, sgkiif.SGK_MIXED))
-    lat = []
-    for t in tickets:
-        _, info = srv.wait(t)
+    lat, outs_served = [], []
+    for t, cap in zip(tickets, caps):
+        out, info = srv.wait(t, cap=cap)
         lat.append(record(info))
+        outs_served.append(out)
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
-    lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64)
+    outs64 = []
+    lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64)
+    err = max(float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
+              for m, f in zip(outs_served, outs64) if m.size and f.size)
     served = summary(lat, wall)
     base64 = summary(lat64, wall64)
     return dict(served,
@@ -447,7 +504,8 @@ def served_leg(args):
                 one_at_a_time_mixed=summary(lat_m, wall_m),
                 one_at_a_time_fp64=base64,
                 speedup_vs_fp64_one_at_a_time=served["dof_steps_per_s"] / base64["dof_steps_per_s"],
-                failed_requests=len(failures), first_failure=failures[0] if failures else None)
+                failed_requests=len(failures), first_failure=failures[0] if failures else None,
+                max_rel_l2_vs_fp64=err)
 
 
 # --------------------------------------------------------- oracle timing ---

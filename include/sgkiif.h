@@ -356,6 +356,40 @@ int sgk_server_get_stats(sgk_server* srv, sgk_server_stats* out);
 /* Finish every queued and running request, then stop the workers. */
 int sgk_server_destroy(sgk_server* srv);
 
+/* ------------------------------------------------------------- batching */
+
+/* Many independent IIF2 problems of uneven size stepped together on one
+ * device (the paper's method applied to each; no counterpart in the paper).
+ * Each instance owns its index set, operators and solver on its own library
+ * context; instances are spread round-robin over the batch's nstreams
+ * streams.  A batch step queues one device-driven step per active instance
+ * (a single CUDA graph each: predictor, one persistent cooperative Arnoldi
+ * launch per species, expm, and the Newton/CG loops as conditional graph
+ * nodes) and then waits for all streams once, so the instances' kernels
+ * overlap on the GPU.  The persistent Arnoldi grid of an instance is sized
+ * to its DOF (slices of at most slice_len coefficients per CTA, 0 = 384),
+ * so that small instances take few SMs; the lanes per output of its matvec
+ * are autotuned when the instance is added.  Results do not depend on the
+ * stream count or on the other instances. */
+typedef struct sgk_batch sgk_batch;
+
+/* Errors: SGK_EINVAL, SGK_ECUDA (no such device or stream creation failed). */
+int sgk_batch_create(int device, int nstreams, int slice_len, sgk_batch** out);
+/* Add an instance described by req (its nsteps is ignored); host arrays are
+ * read during the call.  *index receives the instance number (0, 1, ...).
+ * Errors: as sgk_index_build / sgk_operator_assemble / sgk_solver_create. */
+int sgk_batch_add(sgk_batch* b, const sgk_request* req, int* index);
+/* Take nsteps steps of every active instance.  status (may be NULL) receives
+ * per instance the status of its last step; an instance whose step fails is
+ * rolled back to the start of that step and takes no further steps.  Returns
+ * SGK_OK if every instance succeeded, else the first failing status. */
+int sgk_batch_step(sgk_batch* b, int nsteps, int* status);
+int64_t sgk_batch_dof(const sgk_batch* b, int index);
+int sgk_batch_count(const sgk_batch* b);
+/* Copy one species' coefficients of an instance to host memory (cap >= dof). */
+int sgk_batch_get_state(const sgk_batch* b, int index, int species, double* out, int64_t cap);
+int sgk_batch_destroy(sgk_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

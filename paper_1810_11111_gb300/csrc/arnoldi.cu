@@ -122,8 +122,9 @@ __global__ void tune_fill_kernel(double* x, int64_t n) {
 
 int arnoldi_autotune(sgk_ctx* ctx, const sgk_op* op, PersistentWork pw, const KrylovWork<double>& kw, double* scratch,
                      int64_t n, int M) {
-    // candidate lane counts per output, each timed on one full Arnoldi
-    // process of a fixed vector after a warm-up run; ties keep the larger G
+    // candidate lane counts per output, each timed (best of three) on full
+    // Arnoldi processes of a fixed vector after a warm-up run; ties keep the
+    // larger G
     tune_fill_kernel<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, ctx->stream>>>(scratch, n);
     check_launch("tune_fill");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -135,12 +136,16 @@ int arnoldi_autotune(sgk_ctx* ctx, const sgk_op* op, PersistentWork pw, const Kr
         for (int G : {8, 4, 2}) {
             pw.G = G;
             arnoldi_persistent(ctx, op, pw, kw, scratch, n, M);
-            SGK_CUDA_CHECK(cudaEventRecord(e0, ctx->stream));
-            arnoldi_persistent(ctx, op, pw, kw, scratch, n, M);
-            SGK_CUDA_CHECK(cudaEventRecord(e1, ctx->stream));
-            SGK_CUDA_CHECK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            SGK_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                SGK_CUDA_CHECK(cudaEventRecord(e0, ctx->stream));
+                arnoldi_persistent(ctx, op, pw, kw, scratch, n, M);
+                SGK_CUDA_CHECK(cudaEventRecord(e1, ctx->stream));
+                SGK_CUDA_CHECK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                SGK_CUDA_CHECK(cudaEventElapsedTime(&t, e0, e1));
+                ms = std::min(ms, t);
+            }
             if (ms < 0.97f * best_ms) {
                 best_ms = ms;
                 best = G;

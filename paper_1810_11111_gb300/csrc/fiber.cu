@@ -41,9 +41,18 @@ __device__ __forceinline__ long long full_addr(const FiberGroup& g, int o, int p
 // FWD: hierarchical fibers (levels 0..N') -> finest-cell Legendre
 // coefficients (levels refined up to Nfull with zero details above N').
 // BWD: the transpose, finest Legendre moments -> hierarchical coefficients of
-// levels 0..N'.  Shared memory per column: the source fiber and two
-// full-length work buffers; threads run over (cell, column) with the column
-// fastest, one level per barrier.
+// levels 0..N'.
+//
+// Each thread owns a subtree of 2^PD finest cells of one column (PD levels
+// below level t = Nfull - PD): FWD walks the t ancestors of its subtree root
+// from the level-0 coefficients and expands the subtree in registers; BWD
+// reduces its subtree in registers, writes the subtree's details and leaves
+// the root's scaling coefficients in shared memory, where one thread per
+// column finishes the t upper levels.  Shared memory holds the source tile,
+// the destination tile (stored with coalesced loads/stores) and, for BWD,
+// the subtree roots; two barriers per item instead of one per level.
+constexpr int PD = 3;
+
 template <typename T, int MODE, int KP1>
 __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ items, int nitems,
                                                   const FiberGroup* __restrict__ groups, const T* __restrict__ src,
@@ -61,6 +70,8 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
                 Hm[h][r][s] = flt.H[h][r][s];
                 Gm[h][r][s] = flt.G[h][r][s];
             }
+    const int De = Nfull < PD ? Nfull : PD;  // levels expanded in registers
+    const int t = Nfull - De;                // level of the subtree roots
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const FiberItem item = items[it];
         if (threadIdx.x < (int)(sizeof(FiberGroup) / sizeof(long long)))
@@ -71,91 +82,164 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
         const int F = KP1 << Np;
         const int I = sg.I, nc = item.ncols, st = item.stride;
         const int src_len = MODE == FIBER_BWD ? H : F;
+        const int dst_len = MODE == FIBER_FWD ? H : F;
         T* X = tile;
-        T* A = tile + (size_t)src_len * st;
-        T* B = A + (size_t)H * st;
-        // thread mapping: a warp per column for short inner extents (lanes
-        // over rows), otherwise one column per thread with rows strided;
-        // body(c, o, in, t) runs for t in [0, count) on every column
+        T* Y = tile + (size_t)src_len * st;
+        T* R = Y + (size_t)dst_len * st;  // BWD: subtree roots, (KP1 << t) rows
+        // load/store mapping: a warp per column for short inner extents
+        // (lanes over rows), otherwise one column per thread with rows
+        // strided; body(c, o, in, t) runs for t in [0, count) on every column
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         const int cf = threadIdx.x % nc, rg = threadIdx.x / nc, nrg = blockDim.x / nc;
         auto for_ct = [&](int count, auto&& body) {
             if (I < 4) {
                 for (int c = wid; c < nc; c += nw) {
                     const int col = item.col0 + c, o = col / I, in = col - (col / I) * I;
-                    for (int t = lane; t < count; t += 32) body(c, o, in, t);
+                    for (int q = lane; q < count; q += 32) body(c, o, in, q);
                 }
             } else if (rg < nrg) {
                 const int col = item.col0 + cf, o = col / I, in = col - (col / I) * I;
-                for (int t = rg; t < count; t += nrg) body(cf, o, in, t);
+                for (int q = rg; q < count; q += nrg) body(cf, o, in, q);
             }
         };
         for_ct(src_len, [&](int c, int o, int in, int pos) {
             X[pos * st + c] = src[MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I)];
         });
         __syncthreads();
+        const int units = nc << t;
         if (MODE == FIBER_FWD) {
-            const T* cur = X;
-            T* nxt = A;
-            for (int n = 1; n <= Nfull; ++n) {
-                const bool has_detail = n <= Np;
-                const int doff = KP1 << (n - 1);
-                for_ct(2 << (n - 1), [&](int c, int, int, int t) {
-                    const int h = t & 1, par = t >> 1;
-                    T pv[KP1], dv[KP1];
+            for (int u = threadIdx.x; u < units; u += blockDim.x) {
+                const int c = u % nc, j = u / nc;
+                T cell[1 << PD][KP1];
 #pragma unroll
-                    for (int r = 0; r < KP1; ++r) {
-                        pv[r] = cur[(par * KP1 + r) * st + c];
-                        dv[r] = has_detail ? X[(doff + par * KP1 + r) * st + c] : T(0);
-                    }
+                for (int r = 0; r < KP1; ++r) cell[0][r] = X[r * st + c];
+                // ancestors of the subtree root, level 1..t
+                for (int n = 1; n <= t; ++n) {
+                    const int an = j >> (t - n), h = an & 1, par = an >> 1;
+                    T d[KP1], q[KP1];
 #pragma unroll
-                    for (int s = 0; s < KP1; ++s) {
+                    for (int r = 0; r < KP1; ++r) d[r] = n <= Np ? X[((KP1 << (n - 1)) + par * KP1 + r) * st + c] : T(0);
+#pragma unroll
+                    for (int s2 = 0; s2 < KP1; ++s2) {
                         T acc = T(0);
 #pragma unroll
-                        for (int r = 0; r < KP1; ++r) acc += Hm[h][r][s] * pv[r] + Gm[h][r][s] * dv[r];
-                        nxt[((2 * par + h) * KP1 + s) * st + c] = acc;
-                    }
-                });
-                __syncthreads();
-                cur = nxt;
-                nxt = (nxt == A) ? B : A;
-            }
-            for_ct(H, [&](int c, int o, int in, int pos) { dst[full_addr(sg, o, pos, in, H, I)] = cur[pos * st + c]; });
-        } else {
-            // cur holds level-n scaling coefficients; details of levels <= Np
-            // go to B (hierarchical layout), the rest are discarded
-            T* cur = X;
-            T* nxt = A;
-            for (int n = Nfull; n >= 1; --n) {
-                const int doff = KP1 << (n - 1);
-                const bool keep = n <= Np;
-                for_ct(1 << (n - 1), [&](int c, int, int, int par) {
-                    T x0[KP1], x1[KP1];
-#pragma unroll
-                    for (int s = 0; s < KP1; ++s) {
-                        x0[s] = cur[(2 * par * KP1 + s) * st + c];
-                        x1[s] = cur[((2 * par + 1) * KP1 + s) * st + c];
-                    }
-#pragma unroll
-                    for (int r = 0; r < KP1; ++r) {
-                        T sp = T(0), sd = T(0);
-#pragma unroll
-                        for (int s = 0; s < KP1; ++s) {
-                            sp += Hm[0][r][s] * x0[s] + Hm[1][r][s] * x1[s];
-                            sd += Gm[0][r][s] * x0[s] + Gm[1][r][s] * x1[s];
+                        for (int r = 0; r < KP1; ++r) {
+                            // select, not index: a runtime index would put the
+                            // filters in local memory
+                            const T hf = h ? Hm[1][r][s2] : Hm[0][r][s2];
+                            const T gf = h ? Gm[1][r][s2] : Gm[0][r][s2];
+                            acc += hf * cell[0][r] + gf * d[r];
                         }
-                        nxt[(par * KP1 + r) * st + c] = sp;
-                        if (keep) B[(doff + par * KP1 + r) * st + c] = sd;
+                        q[s2] = acc;
                     }
-                });
-                __syncthreads();
-                T* t = cur;
-                cur = nxt;
-                nxt = t;
+#pragma unroll
+                    for (int r = 0; r < KP1; ++r) cell[0][r] = q[r];
+                }
+                // expand the subtree (children written over consumed parents)
+#pragma unroll
+                for (int l = 0; l < PD; ++l) {
+                    if (l < De) {
+                        const int n = t + l + 1;
+#pragma unroll
+                        for (int i = (1 << l) - 1; i >= 0; --i) {
+                            const int par = (j << l) + i;
+                            T d[KP1], p[KP1];
+#pragma unroll
+                            for (int r = 0; r < KP1; ++r) {
+                                p[r] = cell[i][r];
+                                d[r] = n <= Np ? X[((KP1 << (n - 1)) + par * KP1 + r) * st + c] : T(0);
+                            }
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                for (int s2 = 0; s2 < KP1; ++s2) {
+                                    T acc = T(0);
+#pragma unroll
+                                    for (int r = 0; r < KP1; ++r) acc += Hm[h][r][s2] * p[r] + Gm[h][r][s2] * d[r];
+                                    cell[2 * i + h][s2] = acc;
+                                }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < (1 << PD); ++i)
+                    if (i < (1 << De))
+#pragma unroll
+                        for (int s2 = 0; s2 < KP1; ++s2) Y[(((j << De) + i) * KP1 + s2) * st + c] = cell[i][s2];
             }
-            for_ct(KP1, [&](int c, int, int, int r) { B[r * st + c] = cur[r * st + c]; });
             __syncthreads();
-            for_ct(F, [&](int c, int o, int in, int pos) { dst[chunk_addr(sg, o, pos, in, KP1, I)] = B[pos * st + c]; });
+            for_ct(H, [&](int c, int o, int in, int pos) { dst[full_addr(sg, o, pos, in, H, I)] = Y[pos * st + c]; });
+        } else {
+            for (int u = threadIdx.x; u < units; u += blockDim.x) {
+                const int c = u % nc, j = u / nc;
+                T cell[1 << PD][KP1];
+#pragma unroll
+                for (int i = 0; i < (1 << PD); ++i)
+                    if (i < (1 << De))
+#pragma unroll
+                        for (int s2 = 0; s2 < KP1; ++s2) cell[i][s2] = X[(((j << De) + i) * KP1 + s2) * st + c];
+                // reduce the subtree (parents written over consumed children)
+#pragma unroll
+                for (int l = PD - 1; l >= 0; --l) {
+                    if (l < De) {
+                        const int n = t + l + 1;  // level of the children
+                        const bool keep = n <= Np;
+#pragma unroll
+                        for (int i = 0; i < (1 << l); ++i) {
+                            T x0[KP1], x1[KP1];
+#pragma unroll
+                            for (int s2 = 0; s2 < KP1; ++s2) {
+                                x0[s2] = cell[2 * i][s2];
+                                x1[s2] = cell[2 * i + 1][s2];
+                            }
+                            const int par = (j << l) + i;
+#pragma unroll
+                            for (int r = 0; r < KP1; ++r) {
+                                T sp = T(0), sd = T(0);
+#pragma unroll
+                                for (int s2 = 0; s2 < KP1; ++s2) {
+                                    sp += Hm[0][r][s2] * x0[s2] + Hm[1][r][s2] * x1[s2];
+                                    sd += Gm[0][r][s2] * x0[s2] + Gm[1][r][s2] * x1[s2];
+                                }
+                                cell[i][r] = sp;
+                                if (keep) Y[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < KP1; ++r) R[(j * KP1 + r) * st + c] = cell[0][r];
+            }
+            __syncthreads();
+            // the t upper levels: one thread per column, in place in R
+            for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+                for (int n = t; n >= 1; --n) {
+                    const bool keep = n <= Np;
+                    for (int par = 0; par < (1 << (n - 1)); ++par) {
+                        T x0[KP1], x1[KP1];
+#pragma unroll
+                        for (int s2 = 0; s2 < KP1; ++s2) {
+                            x0[s2] = R[((2 * par) * KP1 + s2) * st + c];
+                            x1[s2] = R[((2 * par + 1) * KP1 + s2) * st + c];
+                        }
+#pragma unroll
+                        for (int r = 0; r < KP1; ++r) {
+                            T sp = T(0), sd = T(0);
+#pragma unroll
+                            for (int s2 = 0; s2 < KP1; ++s2) {
+                                sp += Hm[0][r][s2] * x0[s2] + Hm[1][r][s2] * x1[s2];
+                                sd += Gm[0][r][s2] * x0[s2] + Gm[1][r][s2] * x1[s2];
+                            }
+                            R[(par * KP1 + r) * st + c] = sp;
+                            if (keep) Y[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < KP1; ++r) Y[r * st + c] = R[r * st + c];
+            }
+            __syncthreads();
+            for_ct(F, [&](int c, int o, int in, int pos) { dst[chunk_addr(sg, o, pos, in, KP1, I)] = Y[pos * st + c]; });
         }
         __syncthreads();
     }
@@ -256,10 +340,10 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
         const int dst_len = mode == FIBER_FWD ? H : F;
         long long cols = (long long)g.O * g.I;
         SGK_REQUIRE(cols < (1LL << 31), SGK_EUNSUPPORTED, "plan: too many fibers in one group");
-        // the two-scale pyramid needs the source fiber plus two full-length
-        // work buffers per column
+        // the pyramid kernel stages the source and destination fibers, and
+        // for BWD the subtree roots (k+1 rows per subtree of 8 finest cells)
         SGK_REQUIRE(mode == FIBER_FWD || mode == FIBER_BWD, SGK_EINVAL, "plan: mode must be FWD or BWD");
-        const int tile_rows = src_len + 2 * H;
+        const int tile_rows = src_len + dst_len + (mode == FIBER_BWD ? std::max(kp1, H >> 3) : 0);
         long long fit = (long long)(smem_budget / ((size_t)tile_rows * elem_bytes)) - 1;
         int maxc = (int)std::min<long long>(64, std::max<long long>(1, fit));
         for (long long c0 = 0; c0 < cols; c0 += maxc) {

@@ -25,9 +25,9 @@ __global__ void __launch_bounds__(256) gmv_kernel(const GmvArgs<T, D> a, const T
          gg += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = gg / G;
         const bool live = g < a.n;
-        T acc = live ? gmv_lane<T, D, KP1, G, false>(a, x, g, r) : T(0);
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        GmvLoc<D> L;
+        if (live) gmv_locate<T, D, KP1>(a, g, L);
+        const T acc = gmv_accumulate<T, D, G, false>(a, x, L, r, live);
         if (live && r == 0) y[g] = acc;
     }
 }
@@ -128,6 +128,16 @@ void build_gmv_tables(sgk_op* op) {
         chunk[c] = (int32_t)t;
     }
     op->madds = madds;
+    const size_t nnz = S.val.size();
+    std::vector<double> cvk(nnz * d);
+    std::vector<float> cvkf(nnz * d);
+    for (int i = 0; i < d; ++i)
+        for (size_t q = 0; q < nnz; ++q) {
+            cvk[i * nnz + q] = -op->kappa[i] * S.val[q];
+            cvkf[i * nnz + q] = (float)cvk[i * nnz + q];
+        }
+    op->gmv_cvk.upload(cvk, op->ctx->stream);
+    op->gmv_cvkf.upload(cvkf, op->ctx->stream);
     op->gmv_ce.upload(ce, op->ctx->stream);
     op->gmv_cb.upload(cb, op->ctx->stream);
     op->gmv_chunk.upload(chunk, op->ctx->stream);

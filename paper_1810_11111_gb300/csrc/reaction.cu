@@ -355,10 +355,10 @@ void quad_build(Quad& Q, const sgk_index* idx, int q, int nspecies, bool need_ja
             groups.push_back(fg);
         }
         const long long ri = Q.layout_size[i], ro = Q.layout_size[i + 1];
-        finalize_plan(Q.fwd[i][0], groups, kp1, H, FIBER_FWD, sizeof(double), 64 * 1024, ri, ro, ctx->stream);
-        finalize_plan(Q.fwd[i][1], groups, kp1, H, FIBER_FWD, sizeof(float), 64 * 1024, ri, ro, ctx->stream);
-        finalize_plan(Q.bwd[i][0], groups, kp1, H, FIBER_BWD, sizeof(double), 64 * 1024, ro, ri, ctx->stream);
-        finalize_plan(Q.bwd[i][1], groups, kp1, H, FIBER_BWD, sizeof(float), 64 * 1024, ro, ri, ctx->stream);
+        finalize_plan(Q.fwd[i][0], groups, kp1, H, FIBER_FWD, sizeof(double), 40 * 1024, ri, ro, ctx->stream);
+        finalize_plan(Q.fwd[i][1], groups, kp1, H, FIBER_FWD, sizeof(float), 40 * 1024, ri, ro, ctx->stream);
+        finalize_plan(Q.bwd[i][0], groups, kp1, H, FIBER_BWD, sizeof(double), 40 * 1024, ro, ri, ctx->stream);
+        finalize_plan(Q.bwd[i][1], groups, kp1, H, FIBER_BWD, sizeof(float), 40 * 1024, ro, ri, ctx->stream);
     }
     // Gauss tables: B[g][r] = h^{-1/2} sqrt(2r+1) P_r(xi_g); w1[g] = h w_g / 2
     std::vector<double> xg, wg;

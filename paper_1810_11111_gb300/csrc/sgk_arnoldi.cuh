@@ -262,23 +262,19 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         // A v_j on this slice, staged in shared memory and kept in Z
         for (int base = 0; base < ne; base += PT / G) {
             const int u = base + (int)threadIdx.x / G;
-            double acc = 0.0;
-            if (u < ne) {
-                if (sloc) {
-                    acc = gmv_accumulate<double, D, G, true>(ga, x, sloc[u], r);
-                } else {
-                    GmvLoc<D> l1;
-                    gmv_locate<double, D, KP1>(ga, lo + u, l1);
-                    acc = gmv_accumulate<double, D, G, true>(ga, x, l1, r);
-                }
-                // the correction's columns are shared out over the group's
-                // lanes like the matrix rows
-                const double* zi = Zl + u;
-                for (int c = r; c < ncorr; c += G) acc -= h2[c] * zi[c * zld];
+            const bool live = u < ne;
+            double acc;
+            // the correction's columns are dealt over the virtual lanes like
+            // the matrix rows (sum independent of G)
+            if (sloc) {
+                acc = gmv_accumulate<double, D, G, true>(ga, x, sloc[live ? u : 0], r, live, ncorr, h2,
+                                                         Zl + (live ? u : 0), zld);
+            } else {
+                GmvLoc<D> l1;
+                if (live) gmv_locate<double, D, KP1>(ga, lo + u, l1);
+                acc = gmv_accumulate<double, D, G, true>(ga, x, l1, r, live, ncorr, h2, Zl + (live ? u : 0), zld);
             }
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (u < ne && r == 0) {
+            if (live && r == 0) {
                 acc *= scale;
                 ws[u] = acc;
                 Zl[(int64_t)j * zld + u] = acc;

@@ -27,8 +27,8 @@ struct GmvArgs {
     const int32_t* __restrict__ rp;       // H + 1
     const int32_t* __restrict__ rlen;     // H x (N + 1)
     const int32_t* __restrict__ ce;       // packed (lb << 16) | p
-    const T* __restrict__ cv;
-    T kneg[D];  // -kappa_i
+    const T* __restrict__ cvk;  // -kappa_i S_q, direction i at cvk + i nnz
+    int64_t nnz;
 };
 
 // Where output g's rows live: per direction the row range [q0, qe) of the
@@ -90,44 +90,66 @@ __device__ __forceinline__ void gmv_locate(const GmvArgs<T, D>& a, int64_t g, Gm
     }
 }
 
-// Partial sum of lane r (0 <= r < G) of a located output; the G partials of
-// a group add up to y_g.  CG selects L2-only loads of x, for vectors written
-// by other CTAs of the same (persistent) kernel.
+// y_g for a located output, computed by the G lanes of a group (lane r of
+// G; G divides 8, the group is G consecutive lanes of a warp, every lane of
+// the warp calls this).  The sum does not depend on G: the entries of every
+// row are dealt to 8 virtual lanes (entry q to virtual lane q mod 8, two
+// chains each, directions in order), optionally minus a correction
+// sum_c h_c z_c whose columns are dealt the same way, and the 8 virtual sums
+// are added in one fixed binary tree -- physical lanes hold 8/G virtual
+// lanes, the lower tree levels are shuffles, the upper ones local.  The
+// result is returned in every lane of the group.  CG selects L2-only loads
+// of x, for vectors written by other CTAs of the same (persistent) kernel.
 template <typename T, int D, int G, bool CG>
 __device__ __forceinline__ T gmv_accumulate(const GmvArgs<T, D>& a, const T* __restrict__ x, const GmvLoc<D>& L,
-                                            int r) {
-    T acc = T(0);
+                                            int r, bool live, int ncorr = 0, const T* hc = nullptr,
+                                            const T* zc = nullptr, int64_t zld = 0) {
+    constexpr int VL = 8, PER = VL / G;
+    T b[PER];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const int64_t* __restrict__ base = a.cb + L.cbrow[i];
-        const int64_t oI = L.oI[i], I = L.I[i], in = L.in[i];
-        auto ld = [&](int pk) {
-            const int lb = pk >> 16, p = pk & 0xffff;
-            const int64_t ob = lb ? (oI << (lb - 1)) : oI;
-            const T* px = x + base[lb] + ob + (int64_t)p * I + in;
-            if constexpr (CG) return __ldcg(px);
-            else return *px;
-        };
-        const int qe = L.qe[i];
-        T s0 = T(0), s1 = T(0);
-        int q = L.q0[i] + r;
-        for (; q + G < qe; q += 2 * G) {
-            const int p0 = a.ce[q], p1 = a.ce[q + G];
-            const T v0 = a.cv[q], v1 = a.cv[q + G];
-            s0 += v0 * ld(p0);
-            s1 += v1 * ld(p1);
+    for (int k = 0; k < PER; ++k) b[k] = T(0);
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int v = r + k * G;
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int64_t* __restrict__ base = a.cb + L.cbrow[i];
+                const T* __restrict__ cv = a.cvk + i * a.nnz;
+                const int64_t oI = L.oI[i], I = L.I[i], in = L.in[i];
+                auto ld = [&](int pk) {
+                    const int lb = pk >> 16, p = pk & 0xffff;
+                    const int64_t ob = lb ? (oI << (lb - 1)) : oI;
+                    const T* px = x + base[lb] + ob + (int64_t)p * I + in;
+                    if constexpr (CG) return __ldcg(px);
+                    else return *px;
+                };
+                const int qe = L.qe[i];
+                int q = L.q0[i] + v;
+#pragma unroll 2
+                for (; q + VL < qe; q += 2 * VL) {
+                    const int p0 = a.ce[q], p1 = a.ce[q + VL];
+                    const T v0 = cv[q], v1 = cv[q + VL];
+                    s0 += v0 * ld(p0);
+                    s1 += v1 * ld(p1);
+                }
+                if (q < qe) s0 += cv[q] * ld(a.ce[q]);
+            }
+            T c0 = T(0);
+            for (int c = v; c < ncorr; c += VL) c0 += hc[c] * zc[c * zld];
+            b[k] = (s0 + s1) - c0;
         }
-        if (q < qe) s0 += a.cv[q] * ld(a.ce[q]);
-        acc += a.kneg[i] * (s0 + s1);
     }
-    return acc;
-}
-
-template <typename T, int D, int KP1, int G, bool CG>
-__device__ __forceinline__ T gmv_lane(const GmvArgs<T, D>& a, const T* __restrict__ x, int64_t g, int r) {
-    GmvLoc<D> L;
-    gmv_locate<T, D, KP1>(a, g, L);
-    return gmv_accumulate<T, D, G, CG>(a, x, L, r);
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[k] += __shfl_xor_sync(0xffffffffu, b[k], o);
+#pragma unroll
+    for (int m = 1; m < PER; m <<= 1)
+#pragma unroll
+        for (int k = 0; k + m < PER; k += 2 * m) b[k] += b[k + m];
+    return b[0];
 }
 
 template <typename T, int D>
@@ -143,7 +165,7 @@ GmvArgs<T, D> make_gmv_args(const sgk_op* op) {
     a.rp = op->S.d_ptr.p;
     a.rlen = op->rlen.p;
     a.ce = op->gmv_ce.p;
-    a.cv = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->S.d_val.p) : reinterpret_cast<const T*>(op->S.d_valf.p);
-    for (int i = 0; i < D; ++i) a.kneg[i] = T(-op->kappa[i]);
+    a.cvk = sizeof(T) == 8 ? reinterpret_cast<const T*>(op->gmv_cvk.p) : reinterpret_cast<const T*>(op->gmv_cvkf.p);
+    a.nnz = (int64_t)op->S.col.size();
     return a;
 }

@@ -285,6 +285,8 @@ struct sgk_op {
     DevBuf<int32_t> gmv_ce;
     DevBuf<int64_t> gmv_cb;
     DevBuf<int32_t> gmv_chunk;
+    DevBuf<double> gmv_cvk;  // -kappa_i S, one copy of the CSR values per direction
+    DevBuf<float> gmv_cvkf;  // the same in FP32
     int64_t madds = 0;  // multiply-adds of one matvec (entries of A on the index set, per direction)
 };
 

@@ -53,11 +53,20 @@ struct sgk_solver {
     DevBuf<unsigned char> ctl;                 // StepCtl on the device
     // kernels per segment of the step graph (for the launch count)
     int64_t n_prefix = 0, n_resid = 0, n_cgpre = 0, n_cgbody = 0, n_adv = 0;
+    void* hrec = nullptr;  // pinned host record of the last launched step
     sgk_stats stats{};
     ~sgk_solver();
 };
 
 void solver_alloc(sgk_solver* s);
+// Device-driven steps (one graph per step) are used when graphs are on, no
+// kernel timing is active and the implicit solve is CG (one species) or
+// absent.  solver_step_launch queues one such step on the solver's stream;
+// after that stream has been synchronised, solver_step_finish reads its
+// outcome (rolling the state back on failure) and returns the status.
+bool solver_device_steps(const sgk_solver* s);
+void solver_step_launch(sgk_solver* s);
+int solver_step_finish(sgk_solver* s);
 int solver_step(sgk_solver* s, int nsteps);
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);

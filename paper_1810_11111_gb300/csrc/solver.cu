@@ -600,24 +600,41 @@ void build_step_graph(sgk_solver* s) {
     SGK_CUDA_CHECK(ei);
 }
 
-// One device-driven step; returns the step's status.
-int device_step(sgk_solver* s) {
+// Pinned host record of one device-driven step: StepCtl, the Krylov
+// scalars and the barrier flags of every species.
+struct StepRecord {
+    StepCtl c;
+    KrylovScalars ks[SGK_MAX_SPECIES];
+    unsigned flags[2 * SGK_MAX_SPECIES];
+};
+
+}  // namespace
+
+// Queues one device-driven step (graph launch and the copies of its
+// outcome) without waiting.
+void solver_step_launch(sgk_solver* s) {
     sgk_ctx* ctx = s->ctx;
-    const long long N = s->n * s->nspecies;
     if (!s->g_step.exec) build_step_graph(s);
+    StepRecord* h = static_cast<StepRecord*>(s->hrec);
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
-    StepCtl c{};
-    KrylovScalars ks[SGK_MAX_SPECIES];
-    unsigned flags[2 * SGK_MAX_SPECIES] = {0};
     if (s->has_rx)
-        SGK_CUDA_CHECK(cudaMemcpyAsync(&c, s->ctl.p, sizeof(StepCtl), cudaMemcpyDeviceToHost, ctx->stream));
-    SGK_CUDA_CHECK(cudaMemcpyAsync(ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
+        SGK_CUDA_CHECK(cudaMemcpyAsync(&h->c, s->ctl.p, sizeof(StepCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    SGK_CUDA_CHECK(cudaMemcpyAsync(h->ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
                                    ctx->stream));
     if (s->persistent)
-        SGK_CUDA_CHECK(cudaMemcpyAsync(flags, s->pbar.p, 2 * s->nspecies * sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                       ctx->stream));
-    SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        SGK_CUDA_CHECK(cudaMemcpyAsync(h->flags, s->pbar.p, 2 * s->nspecies * sizeof(unsigned),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+// Completes a launched step once its stream has drained (the caller
+// synchronised it): statistics, and on failure the rollback of the state.
+int solver_step_finish(sgk_solver* s) {
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    StepRecord* h = static_cast<StepRecord*>(s->hrec);
+    StepCtl c{};
+    if (s->has_rx) c = h->c;
     int rc = s->has_rx ? c.status : SGK_OK;
     count_launch(ctx, (int)(s->n_prefix + c.newton_iters * (s->n_cgpre + s->n_adv + s->n_resid) +
                             c.inner_iters * s->n_cgbody));
@@ -626,11 +643,12 @@ int device_step(sgk_solver* s) {
     if (s->has_rx) s->stats.last_newton_residual = c.last_g;
     s->stats.krylov_calls += s->nspecies;
     for (int sp = 0; sp < s->nspecies; ++sp) {
-        s->stats.krylov_breakdowns += ks[sp].breakdown;
-        s->stats.last_m_eff = ks[sp].m_eff;
+        s->stats.krylov_breakdowns += h->ks[sp].breakdown;
+        s->stats.last_m_eff = h->ks[sp].m_eff;
     }
     bool timed_out = false;
-    for (int sp = 0; sp < s->nspecies; ++sp) timed_out = timed_out || flags[2 * sp + 1] != 0u;
+    if (s->persistent)
+        for (int sp = 0; sp < s->nspecies; ++sp) timed_out = timed_out || h->flags[2 * sp + 1] != 0u;
     if (timed_out) {
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * s->nspecies * sizeof(unsigned), ctx->stream));
         rc = SGK_ETIMEOUT;
@@ -638,19 +656,26 @@ int device_step(sgk_solver* s) {
     if (rc != SGK_OK) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        s->stats.steps += 1;
     }
     return rc;
 }
+
+bool solver_device_steps(const sgk_solver* s) { return step_graph_eligible(s) && !s->ctx->prof_mask; }
+
+namespace {
 
 }  // namespace
 
 int solver_step(sgk_solver* s, int nsteps) {
     sgk_ctx* ctx = s->ctx;
-    if (step_graph_eligible(s) && !ctx->prof_mask) {
+    if (solver_device_steps(s)) {
         for (int step = 0; step < nsteps; ++step) {
-            const int rc = device_step(s);
+            solver_step_launch(s);
+            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            const int rc = solver_step_finish(s);
             if (rc != SGK_OK) return rc;
-            s->stats.steps += 1;
         }
         return SGK_OK;
     }
@@ -733,6 +758,7 @@ void solver_alloc(sgk_solver* s) {
     s->ks.alloc(S);
     s->counters.alloc(4);
     s->ctl.alloc(sizeof(StepCtl));
+    SGK_CUDA_CHECK(cudaMallocHost(&s->hrec, sizeof(StepRecord)));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->ctl.p, 0, sizeof(StepCtl), s->ctx->stream));
     s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && n <= arnoldi_persistent_max_n(s->ctx);
     if (s->persistent) {
@@ -782,6 +808,7 @@ void solver_alloc(sgk_solver* s) {
 }
 
 sgk_solver::~sgk_solver() {
+    if (hrec) cudaFreeHost(hrec);
     if (g_step.exec) cudaGraphExecDestroy(g_step.exec);
     for (cudaStream_t& a : aux)
         if (a) cudaStreamDestroy(a);

@@ -112,6 +112,13 @@ _SIGS = {
                                        _c_double_p, ctypes.c_int64]),
     "sgk_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_server_stats)]),
     "sgk_server_destroy": (ctypes.c_int, [_P]),
+    "sgk_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "sgk_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(sgk_request), _c_int_p]),
+    "sgk_batch_step": (ctypes.c_int, [_P, ctypes.c_int, _c_int_p]),
+    "sgk_batch_dof": (ctypes.c_int64, [_P, ctypes.c_int]),
+    "sgk_batch_count": (ctypes.c_int, [_P]),
+    "sgk_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int64]),
+    "sgk_batch_destroy": (ctypes.c_int, [_P]),
 }
 EXPM_NOALLOC_MAX_M = 64
 
@@ -430,4 +437,50 @@ class Server:
     def close(self):
         if self.h:
             sgk_server_destroy(self.h)
+            self.h = _P()
+
+
+class Batch:
+    """Independent IIF2 problems stepped together (sgk_batch_*); instances
+    are workload dicts as for Server."""
+
+    def __init__(self, device=0, streams=8, slice_len=0):
+        load()
+        self.h = _P()
+        rc = sgk_batch_create(int(device), int(streams), int(slice_len), ctypes.byref(self.h))
+        if rc:
+            raise SgkError(rc, "sgk_batch_create failed")
+        self.nspecies = []
+
+    def add(self, cfg, precision=SGK_MIXED, init_coeffs=None):
+        q, keep = Server.request(cfg, precision, init_coeffs)
+        i = ctypes.c_int(-1)
+        rc = sgk_batch_add(self.h, ctypes.byref(q), ctypes.byref(i))
+        if rc:
+            raise SgkError(rc, "sgk_batch_add failed")
+        self.nspecies.append(len(cfg["kappas"]))
+        return i.value
+
+    def step(self, nsteps=1):
+        st = (ctypes.c_int * max(1, len(self.nspecies)))()
+        rc = sgk_batch_step(self.h, int(nsteps), st)
+        return rc, [st[i] for i in range(len(self.nspecies))]
+
+    def dof(self, i):
+        return int(sgk_batch_dof(self.h, int(i)))
+
+    def state(self, i):
+        n = self.dof(i)
+        out = []
+        for s in range(self.nspecies[i]):
+            a = np.zeros(n)
+            rc = sgk_batch_get_state(self.h, int(i), s, _dptr(a), n)
+            if rc:
+                raise SgkError(rc, "sgk_batch_get_state failed")
+            out.append(a)
+        return out
+
+    def close(self):
+        if self.h:
+            sgk_batch_destroy(self.h)
             self.h = _P()

@@ -50,3 +50,13 @@ def test_server_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert sgkiif.sgk_server_create(0, 2, 0, 0.0, ctypes.byref(h)) == sgkiif.SGK_ECUDA
     assert sgkiif.sgk_server_create(0, 0, 0, 0.0, ctypes.byref(h)) == sgkiif.SGK_EINVAL
+
+
+def test_batch_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert sgkiif.sgk_batch_create(0, 4, 0, ctypes.byref(h)) == sgkiif.SGK_ECUDA
+    assert sgkiif.sgk_batch_create(0, 0, 0, ctypes.byref(h)) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_batch_count(None) == -1 and sgkiif.sgk_batch_dof(None, 0) == -1
