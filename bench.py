@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--served-workers", type=int, default=4)
     ap.add_argument("--batch-instances", type=int, default=32,
                     help="instances of the batched leg (0 skips it)")
+    ap.add_argument("--no-matvec", action="store_true", help="skip the large stand-alone matvec leg")
     return ap.parse_args()
 
 
@@ -371,6 +372,8 @@ def native(args, rank, world, local_rank):
                       "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
            "kernel_ms_warmup": {c: round(v[0], 3) for c, v in warm.items()}}
     prob.close()
+    if world == 1 and not args.no_matvec:
+        out["matvec"] = matvec_leg(peaks, peak_kind)
     if world == 1 and args.batch_instances > 0:
         out["batched"] = batched_leg(args)
     if world == 1 and args.served_requests > 0:
@@ -379,6 +382,57 @@ def native(args, rank, world, local_rank):
         out["cpu_baseline"] = cpu_baseline(cfg)
     if dist is not None:
         dist.destroy_process_group()
+    return out
+
+
+# ----------------------------------------------------------- matvec leg ---
+
+def matvec_leg(peaks, peak_kind):
+    """The stand-alone sparse-grid matvec (sgk_matvec, one launch for all
+    directions) on the largest served shape, d = 4, level 9, degree 3
+    (6.8 M coefficients, 55 MB per FP64 vector), L2 flushed before every
+    launch.  Against the FP64 (nominal 1.25 TFLOP/s) and FP32 (152 x 128 x 2
+    x 2.07 GHz) rates and the measured HBM copy bandwidth."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgkiif.Context(dev.index, stream.cuda_stream, sgkiif.SGK_FP64)
+    idx = sgkiif.IndexSet(ctx, 4, 9, 3)
+    op = sgkiif.Operator(ctx, idx, [1.0, 0.5, 0.1, 0.7])
+    dof, madds = idx.dof, op.madds()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    out = {"workload": "sparse-grid matvec, d 4, level 9, degree 3, diag(1, 0.5, 0.1, 0.7), periodic",
+           "dof": dof, "madds_per_matvec": madds, "l2": "flushed (256 MB write) before every launch"}
+    for name, prec, dt, peak in (("fp64", sgkiif.SGK_FP64, torch.float64, 1.25),
+                                 ("fp32", sgkiif.SGK_MIXED, torch.float32, 152 * 128 * 2 * 2.07e9 / 1e12)):
+        x = torch.randn(dof, dtype=torch.float64, generator=g).to(dev).to(dt)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            op.matvec(x.data_ptr(), y.data_ptr(), prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        reps = 10
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0.record(stream)
+            op.matvec(x.data_ptr(), y.data_ptr(), prec)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        t = tot / reps / 1e3
+        es = x.element_size()
+        tf = 2.0 * madds / t / 1e12
+        gbs = 2.0 * dof * es / t / 1e9
+        out[name] = {"us_per_matvec": t * 1e6, "achieved_tflops": tf, "peak_tflops": peak, "frac_alu": tf / peak,
+                     "algorithmic_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_hbm": gbs / peaks["hbm_gbs"],
+                     "hbm_peak_source": peak_kind}
+    out["bound"] = "FP64 pipe (the part's FP64 rate is ~50x below what HBM feeds at this arithmetic intensity)"
+    op.close()
+    idx.close()
+    ctx.close()
     return out
 
 

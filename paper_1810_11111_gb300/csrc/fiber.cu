@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
         const int dst_len = MODE == FIBER_FWD ? H : F;
         T* X = tile;
         T* Y = tile + (size_t)src_len * st;
-        T* R = Y + (size_t)dst_len * st;  // BWD: subtree roots, (KP1 << t) rows
+        T* R = Y + (size_t)dst_len * st;  // BWD: subtree roots, (KP1 << t) rows, then a buffer of half that
         // load/store mapping: a warp per column for short inner extents
         // (lanes over rows), otherwise one column per thread with rows
         // strided; body(c, o, in, t) runs for t in [0, count) on every column
@@ -103,8 +103,10 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
             }
         };
         for_ct(src_len, [&](int c, int o, int in, int pos) {
-            X[pos * st + c] = src[MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I)];
+            async_copy(X + pos * st + c,
+                       src + (MODE == FIBER_BWD ? full_addr(sg, o, pos, in, H, I) : chunk_addr(sg, o, pos, in, KP1, I)));
         });
+        async_wait_all();
         __syncthreads();
         const int units = nc << t;
         if (MODE == FIBER_FWD) {
@@ -211,32 +213,40 @@ __global__ void __launch_bounds__(256) pyr_kernel(const FiberItem* __restrict__ 
                 for (int r = 0; r < KP1; ++r) R[(j * KP1 + r) * st + c] = cell[0][r];
             }
             __syncthreads();
-            // the t upper levels: one thread per column, in place in R
-            for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-                for (int n = t; n >= 1; --n) {
-                    const bool keep = n <= Np;
-                    for (int par = 0; par < (1 << (n - 1)); ++par) {
-                        T x0[KP1], x1[KP1];
+            // the t upper levels, one parent per thread and a barrier per
+            // level, alternating between R and R2
+            T* cur = R;
+            T* nxt = R + (size_t)(KP1 << t) * st;
+            for (int n = t; n >= 1; --n) {
+                const bool keep = n <= Np;
+                for (int u = threadIdx.x; u < (nc << (n - 1)); u += blockDim.x) {
+                    const int c = u % nc, par = u / nc;
+                    T x0[KP1], x1[KP1];
+#pragma unroll
+                    for (int s2 = 0; s2 < KP1; ++s2) {
+                        x0[s2] = cur[((2 * par) * KP1 + s2) * st + c];
+                        x1[s2] = cur[((2 * par + 1) * KP1 + s2) * st + c];
+                    }
+#pragma unroll
+                    for (int r = 0; r < KP1; ++r) {
+                        T sp = T(0), sd = T(0);
 #pragma unroll
                         for (int s2 = 0; s2 < KP1; ++s2) {
-                            x0[s2] = R[((2 * par) * KP1 + s2) * st + c];
-                            x1[s2] = R[((2 * par + 1) * KP1 + s2) * st + c];
+                            sp += Hm[0][r][s2] * x0[s2] + Hm[1][r][s2] * x1[s2];
+                            sd += Gm[0][r][s2] * x0[s2] + Gm[1][r][s2] * x1[s2];
                         }
-#pragma unroll
-                        for (int r = 0; r < KP1; ++r) {
-                            T sp = T(0), sd = T(0);
-#pragma unroll
-                            for (int s2 = 0; s2 < KP1; ++s2) {
-                                sp += Hm[0][r][s2] * x0[s2] + Hm[1][r][s2] * x1[s2];
-                                sd += Gm[0][r][s2] * x0[s2] + Gm[1][r][s2] * x1[s2];
-                            }
-                            R[(par * KP1 + r) * st + c] = sp;
-                            if (keep) Y[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
-                        }
+                        nxt[(par * KP1 + r) * st + c] = sp;
+                        if (keep) Y[((KP1 << (n - 1)) + par * KP1 + r) * st + c] = sd;
                     }
                 }
-#pragma unroll
-                for (int r = 0; r < KP1; ++r) Y[r * st + c] = R[r * st + c];
+                __syncthreads();
+                T* tmp = cur;
+                cur = nxt;
+                nxt = tmp;
+            }
+            for (int u = threadIdx.x; u < nc * KP1; u += blockDim.x) {
+                const int c = u % nc, r = u / nc;
+                Y[r * st + c] = cur[r * st + c];
             }
             __syncthreads();
             for_ct(F, [&](int c, int o, int in, int pos) { dst[chunk_addr(sg, o, pos, in, KP1, I)] = Y[pos * st + c]; });
@@ -330,6 +340,11 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
                    size_t smem_budget, long long src_size, long long dst_size, cudaStream_t s) {
     std::vector<FiberItem> items;
     std::vector<long long> cost;
+    // columns per item: at most what spreads the plan over about 2 x 152
+    // items (a GB300's SMs), so that small transforms still fill the GPU
+    long long total_cols = 0;
+    for (const FiberGroup& g : groups) total_cols += (long long)g.O * g.I;
+    const long long col_cap = std::max<long long>(1, (total_cols + 303) / 304);
     plan.max_src_len = 0;
     plan.max_cols = 0;
     size_t smem = 0;
@@ -342,10 +357,11 @@ void finalize_plan(FiberPlan& plan, std::vector<FiberGroup>& groups, int kp1, in
         SGK_REQUIRE(cols < (1LL << 31), SGK_EUNSUPPORTED, "plan: too many fibers in one group");
         // the pyramid kernel stages the source and destination fibers, and
         // for BWD the subtree roots (k+1 rows per subtree of 8 finest cells)
+        // twice (the upper levels alternate between two buffers)
         SGK_REQUIRE(mode == FIBER_FWD || mode == FIBER_BWD, SGK_EINVAL, "plan: mode must be FWD or BWD");
-        const int tile_rows = src_len + dst_len + (mode == FIBER_BWD ? std::max(kp1, H >> 3) : 0);
+        const int tile_rows = src_len + dst_len + (mode == FIBER_BWD ? 2 * std::max(kp1, H >> 3) : 0);
         long long fit = (long long)(smem_budget / ((size_t)tile_rows * elem_bytes)) - 1;
-        int maxc = (int)std::min<long long>(64, std::max<long long>(1, fit));
+        int maxc = (int)std::min<long long>(std::min<long long>(64, col_cap), std::max<long long>(1, fit));
         for (long long c0 = 0; c0 < cols; c0 += maxc) {
             FiberItem it;
             it.group = gi;

@@ -296,8 +296,9 @@ __global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, cons
             const long long o = fiber_offset(f);
             const T* src = reinterpret_cast<const T*>(set < S ? args.u[set] : args.w[set - S]);
             T* dstp = sm + (size_t)sf * H;
-            for (int a = threadIdx.x; a < H; a += blockDim.x) dstp[a] = src[chunk(o, a)];
+            for (int a = threadIdx.x; a < H; a += blockDim.x) async_copy(dstp + a, src + chunk(o, a));
         }
+        async_wait_all();
         __syncthreads();
         // 2. reconstruct each set; buffers rotate: a set's input buffer is
         //    free once its reconstruction is done

@@ -141,6 +141,22 @@ void allow_max_dynamic_smem(size_t smem_optin, K kern) {
                                         (int)(smem_optin - fa.sharedSizeBytes)));
 }
 
+// Asynchronous element copy global -> shared (PTX cp.async, 4 or 8 bytes):
+// the copies of a thread stay in flight together until async_wait_all; the
+// values never pass through registers.
+template <typename T>
+__device__ __forceinline__ void async_copy(T* smem_dst, const T* gmem_src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Every kernel launch of the library goes through this counter.
 inline void count_launch(sgk_ctx* c, int n = 1) { c->launches += n; }
 void check_launch(const char* what);
