@@ -462,8 +462,8 @@ def batched_leg(args):
         b.close()
         res[(streams, prec)] = dict(dof_steps_per_s=work_per_step * steps / wall, wall_s=wall,
                                     failed=sum(1 for x in st if x != sgkiif.SGK_OK), status=max(rc, rc2))
-    err = max(float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
-              for m, f in zip(states[(8, sgkiif.SGK_MIXED)], states[(8, sgkiif.SGK_FP64)]))
+    errs = np.array([float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
+                     for m, f in zip(states[(8, sgkiif.SGK_MIXED)], states[(8, sgkiif.SGK_FP64)])])
     fp64 = res[(8, sgkiif.SGK_FP64)]
     res = {8: res[(8, sgkiif.SGK_MIXED)], 1: res[(1, sgkiif.SGK_MIXED)]}
     return dict(workload="batch: %d scalar cubic instances (seed 3; d 2-4, level 5-8, degree 1-2, kappa_i ~ "
@@ -475,7 +475,11 @@ def batched_leg(args):
                 one_stream_dof_steps_per_s=res[1]["dof_steps_per_s"],
                 speedup_vs_one_stream=res[8]["dof_steps_per_s"] / res[1]["dof_steps_per_s"],
                 failed_instances=res[8]["failed"], fp64_dof_steps_per_s=fp64["dof_steps_per_s"],
-                max_rel_l2_vs_fp64=err,
+                rel_l2_vs_fp64={"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
+                                "max": float(errs.max()), "above_1e-6": int((errs > 1e-6).sum()),
+                                "note": "per instance after the timed steps; instances whose solution decays by "
+                                        "1e3 or more amplify the FP32 reaction error through the M = 30 Krylov "
+                                        "approximation (far from converged at dt rho(A) ~ 1e4)"},
                 timing="host wall clock around the batch steps (each step waits for every stream)")
 
 

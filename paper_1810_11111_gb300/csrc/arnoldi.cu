@@ -39,6 +39,8 @@ static int persistent_ctas(const sgk_ctx* ctx) {
     return ctx->persist_ctas > 0 ? std::min(ctx->persist_ctas, ctx->num_sms) : ctx->num_sms;
 }
 
+int arnoldi_persistent_ctas(const sgk_ctx* ctx) { return persistent_ctas(ctx); }
+
 int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx) {
     // the slice of w is staged in shared memory: at most 24 K doubles per CTA
     return (int64_t)persistent_ctas(ctx) * 24 * 1024;
@@ -62,7 +64,8 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     SGK_REQUIRE(n >= 1 && n <= arnoldi_persistent_max_n(ctx), SGK_EUNSUPPORTED, "persistent Arnoldi: n too large");
     SGK_REQUIRE(M >= 1 && M <= SGK_MAX_KRYLOV, SGK_EINVAL, "persistent Arnoldi: bad M");
     const int nb = persistent_ctas(ctx);
-    const int64_t E = (n + nb - 1) / nb;
+    const int64_t E = pw.bounds ? pw.E : (n + nb - 1) / nb;
+    SGK_REQUIRE(E >= 1 && E <= 24 * 1024, SGK_EUNSUPPORTED, "persistent Arnoldi: slice too long");
     // lanes per output in the matvec: the autotuned value, else eight (the
     // gathers are latency-bound; more lanes keep more of them in flight)
     const int G = pw.G > 0 ? pw.G : 8;
@@ -80,6 +83,7 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     a.pbuf = pw.pbuf;
     a.bar = pw.bar;
     a.ks = kw.ks;
+    a.bounds = pw.bounds;
     // shared memory: the slice of w always; the slices of V and Z (all
     // M + 1 columns) and the located rows of the slice's outputs when they
     // fit, which turns the Gram-Schmidt and correction loads into shared

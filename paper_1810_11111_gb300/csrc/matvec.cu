@@ -91,6 +91,7 @@ void build_gmv_tables(sgk_op* op) {
             for (int q = S.ptr[a]; q < S.ptr[a + 1] && S.col[q] < (kp1 << L); ++q) ++c;
             rl[(size_t)a * nl + L] = c;
         }
+    op->rlen_host = rl;
     int64_t madds = 0;
     std::vector<int64_t> cb((size_t)idx->ntuples * d * nl, -1);
     for (int64_t t = 0; t < idx->ntuples; ++t) {
@@ -142,6 +143,58 @@ void build_gmv_tables(sgk_op* op) {
     op->gmv_cb.upload(cb, op->ctx->stream);
     op->gmv_chunk.upload(chunk, op->ctx->stream);
     SGK_CUDA_CHECK(cudaStreamSynchronize(op->ctx->stream));
+}
+
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra) {
+    const sgk_index* idx = op->idx;
+    const int d = idx->d, N = idx->n, kp1 = idx->k + 1, nl = N + 1;
+    const std::vector<int>& rl = op->rlen_host;
+    // per tuple and direction the row lengths f_i(c) of its positions
+    auto fill = [&](const int32_t* l, std::vector<std::vector<int>>& f, std::vector<int>& cnt) {
+        int sum = 0;
+        for (int m = 0; m < d; ++m) sum += l[m];
+        f.assign(d, {});
+        cnt.assign(d, 0);
+        for (int i = 0; i < d; ++i) {
+            cnt[i] = level_count(l[i], kp1);
+            const int np = N - (sum - l[i]);
+            f[i].resize(cnt[i]);
+            for (int c = 0; c < cnt[i]; ++c) f[i][c] = rl[(size_t)(level_offset(l[i], kp1) + c) * nl + np];
+        }
+    };
+    std::vector<std::vector<int>> f;
+    std::vector<int> cnt;
+    double total = 0.0;
+    for (int64_t t = 0; t < idx->ntuples; ++t) {
+        fill(&idx->levels[t * d], f, cnt);
+        const int64_t blk = idx->offsets[t + 1] - idx->offsets[t];
+        for (int i = 0; i < d; ++i) {
+            int64_t s = 0;
+            for (int v : f[i]) s += v;
+            total += (double)s * (double)(blk / cnt[i]);
+        }
+        total += (double)extra * blk;
+    }
+    std::vector<int64_t> b(nb + 1, idx->dof);
+    b[0] = 0;
+    int k = 1;
+    double cum = 0.0;
+    std::vector<int> c(d);
+    for (int64_t t = 0; t < idx->ntuples && k < nb; ++t) {
+        fill(&idx->levels[t * d], f, cnt);
+        std::fill(c.begin(), c.end(), 0);
+        for (int64_t g = idx->offsets[t]; g < idx->offsets[t + 1] && k < nb; ++g) {
+            int cost = extra;
+            for (int i = 0; i < d; ++i) cost += f[i][c[i]];
+            cum += cost;
+            while (k < nb && cum >= total * k / nb) b[k++] = g + 1;
+            for (int m = d - 1; m >= 0; --m) {  // row-major odometer, last direction fastest
+                if (++c[m] < cnt[m]) break;
+                c[m] = 0;
+            }
+        }
+    }
+    return b;
 }
 
 template <typename T>

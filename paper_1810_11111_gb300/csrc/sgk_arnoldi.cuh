@@ -16,7 +16,7 @@ constexpr unsigned BAR_SPIN_LIMIT = 1u << 21;  // polls of ~0.1-0.5 us each
 struct ArnArgs {
     int64_t n;
     int M;
-    int ldp;  // row stride of the partial-sum buffers (>= M + 1)
+    int ldp;  // columns of each partial-sum buffer (>= M + 1), each column gridDim.x long
     int E;    // slice length per CTA (ceil(n / gridDim.x))
     int smem_vz;   // this CTA's slices of V and Z live in shared memory (and V also in HBM)
     int smem_loc;  // the located rows of every output of the slice live in shared memory
@@ -26,9 +26,10 @@ struct ArnArgs {
     double* w1;
     double* Z;     // raw matvec outputs A v_c, column c at Z + c n (own slices only)
     double* H;     // (M + 1) x M row-major
-    double* pbuf;  // 3 buffers of gridDim.x x ldp
+    double* pbuf;  // 3 buffers of ldp columns x gridDim.x
     unsigned* bar;  // [0] barrier arrivals (zero at launch), [1] error flag
     KrylovScalars* ks;
+    const int64_t* bounds;  // slice b = [bounds[b], bounds[b+1]) (work-balanced), or null: equal slices of E
 };
 
 // Dynamic shared memory of the kernel, in bytes.
@@ -75,13 +76,14 @@ __device__ __forceinline__ double warp_sum(double a) {
     return a;
 }
 
-// out[c] = sum over CTAs b of P[b ldp + c], c < ncols, identical in every
+// out[c] = sum over CTAs b of P[c nb + b], c < ncols (the partials are
+// stored column by column, so a column is one contiguous run), identical in every
 // CTA.  Each thread sums a fixed subset of rows of one column (all its loads
 // issued at once), the subset sums go through shared memory and one thread
 // per column adds them in a fixed order: FP64 additions with every lane
 // busy, no shuffle trees.  P was written by other CTAs during this launch:
 // L2 loads.
-__device__ __forceinline__ void colsum(const double* P, int nb, int ldp, int ncols, double* out, double* tmp) {
+__device__ __forceinline__ void colsum(const double* P, int nb, int ncols, double* out, double* tmp) {
     // RS row slots per column; ncols * RS <= max(PT, 4 ncols)
     const int RS = ncols <= PT / 32 ? 32 : (ncols <= PT / 16 ? 16 : (ncols <= PT / 8 ? 8 : 4));
     for (int base = 0; base < ncols * RS; base += PT) {
@@ -92,7 +94,7 @@ __device__ __forceinline__ void colsum(const double* P, int nb, int ldp, int nco
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int k = k0 + RS * q;
-                v[q] = k < nb ? __ldcg(P + (int64_t)k * ldp + c) : 0.0;
+                v[q] = k < nb ? __ldcg(P + (int64_t)c * nb + k) : 0.0;
             }
             // the trip count depends on nb and RS only: uniform, so the
             // additions past the last row slot are not issued
@@ -100,7 +102,7 @@ __device__ __forceinline__ void colsum(const double* P, int nb, int ldp, int nco
 #pragma unroll
             for (int q = 1; q < 8; ++q)
                 if (RS * q < nb) acc += v[q];
-            for (int k = k0 + 8 * RS; k < nb; k += RS) acc += __ldcg(P + (int64_t)k * ldp + c);
+            for (int k = k0 + 8 * RS; k < nb; k += RS) acc += __ldcg(P + (int64_t)c * nb + k);
             tmp[t] = acc;
         }
     }
@@ -120,7 +122,7 @@ __device__ __forceinline__ void colsum(const double* P, int nb, int ldp, int nco
 // Vl/vld its basis columns in shared or global memory); with norm, also
 // out[ncols] = sum ws[u]^2.  A warp per column.
 __device__ __forceinline__ void slice_dots(const double* Vl, int64_t vld, int ncols, const double* ws, int ne,
-                                           double* out, bool norm) {
+                                           double* out, int ostride, bool norm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nt = ncols + (norm ? 1 : 0);
     for (int c = wid; c < nt; c += PNW) {
@@ -133,7 +135,7 @@ __device__ __forceinline__ void slice_dots(const double* Vl, int64_t vld, int nc
         }
         if (u < ne) a += vc[u] * ws[u];
         a = warp_sum(a + b);
-        if (lane == 0) out[c] = a;
+        if (lane == 0) out[(int64_t)c * ostride] = a;
     }
 }
 
@@ -191,9 +193,9 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     __shared__ int s_ok, s_flag;
     const int nb = gridDim.x, b = blockIdx.x;
     const int64_t n = a.n;
-    const int E = a.E;
-    const int64_t lo = std::min<int64_t>(n, (int64_t)b * E);
-    const int ne = (int)(std::min<int64_t>(n, lo + E) - lo);
+    const int E = a.E;  // longest slice
+    const int64_t lo = a.bounds ? a.bounds[b] : std::min<int64_t>(n, (int64_t)b * E);
+    const int ne = (int)((a.bounds ? a.bounds[b + 1] : std::min<int64_t>(n, lo + E)) - lo);
     double* const ws = smem;
     double* const Vs = a.smem_vz ? smem + E : nullptr;
     double* const Zs = a.smem_vz ? smem + E + (size_t)(a.M + 1) * E : nullptr;
@@ -221,9 +223,9 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // gamma = ||v||
     for (int u = threadIdx.x; u < ne; u += PT) ws[u] = a.v[lo + u];
     __syncthreads();
-    slice_norm2(ws, ne, red, P2 + (int64_t)b * a.ldp);
+    slice_norm2(ws, ne, red, P2 + b);
     if (!barrier()) return;
-    colsum(P2, nb, a.ldp, 1, s_scal, ctmp);
+    colsum(P2, nb, 1, s_scal, ctmp);
     __syncthreads();
     // scalar FP64 work (square roots, reciprocals, the Frobenius norm of H)
     // stays on warp 0 and is broadcast through shared memory: FP64 issue is
@@ -281,17 +283,17 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             }
         }
         __syncthreads();
-        slice_dots(Vl, vld, nc, ws, ne, P0 + (int64_t)b * a.ldp, false);
+        slice_dots(Vl, vld, nc, ws, ne, P0 + b, nb, false);
         if (!barrier()) return;
-        colsum(P0, nb, a.ldp, nc, h1, ctmp);
+        colsum(P0, nb, nc, h1, ctmp);
         __syncthreads();
         // w' = w - V h1, published for the next matvec
         slice_update(Vl, vld, nc, h1, w, ws, lo, ne, nullptr, nullptr, 0.0);
         __syncthreads();
         // second pass: V^T w' and ||w'||^2 in one reduction
-        slice_dots(Vl, vld, nc, ws, ne, P1 + (int64_t)b * a.ldp, true);
+        slice_dots(Vl, vld, nc, ws, ne, P1 + b, nb, true);
         if (!barrier()) return;
-        colsum(P1, nb, a.ldp, nc + 1, h2, ctmp);
+        colsum(P1, nb, nc + 1, h2, ctmp);
         __syncthreads();
         // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal, w'' = w' - V h2);
         // when the second pass removed more than 1e-3 of ||w'||^2 (near
@@ -319,9 +321,9 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             // w'' in place (published), its norm through a third barrier
             slice_update(Vl, vld, nc, h2, w, ws, lo, ne, nullptr, nullptr, 0.0);
             __syncthreads();
-            slice_norm2(ws, ne, red, P2 + (int64_t)b * a.ldp);
+            slice_norm2(ws, ne, red, P2 + b);
             if (!barrier()) return;
-            colsum(P2, nb, a.ldp, 1, s_scal, ctmp);
+            colsum(P2, nb, 1, s_scal, ctmp);
             __syncthreads();
         }
         // column j of H and the breakdown test: warp 0 of every CTA, alike

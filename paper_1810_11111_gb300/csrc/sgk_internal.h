@@ -304,10 +304,16 @@ struct sgk_op {
     DevBuf<double> gmv_cvk;  // -kappa_i S, one copy of the CSR values per direction
     DevBuf<float> gmv_cvkf;  // the same in FP32
     int64_t madds = 0;  // multiply-adds of one matvec (entries of A on the index set, per direction)
+    std::vector<int> rlen_host;  // host copy of rlen
 };
 
 // Builds and checks the gather-matvec tables of an assembled operator.
 void build_gmv_tables(sgk_op* op);
+// Boundaries of nb contiguous slices of the coefficient vector with about
+// equal work for the persistent Arnoldi kernel: per coefficient its matvec
+// entries (all directions) plus 2 extra for the Gram-Schmidt passes
+// (extra = 2 M).  bounds[0] = 0, bounds[nb] = dof, non-decreasing.
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra);
 long long tuple_rank(const std::vector<int>& l, int n);
 
 template <typename T>

@@ -43,8 +43,12 @@ struct PersistentWork {
     double* pbuf = nullptr;   // arnoldi_persistent_pbuf_size doubles
     unsigned* bar = nullptr;  // [0] barrier arrivals, [1] error flag (sticky until the host clears it)
     int G = 0;                // lanes per output in the matvec (0: default)
+    const int64_t* bounds = nullptr;  // work-balanced slices (device, grid + 1 entries), or null
+    int64_t E = 0;                    // longest slice when bounds is set
 };
 
+// CTAs of the persistent kernel on this context.
+int arnoldi_persistent_ctas(const sgk_ctx* ctx);
 // Largest n (and the partial-sum buffer size) the persistent kernel takes on
 // this context's device.
 int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx);

@@ -39,6 +39,8 @@ struct sgk_solver {
     int arn_G = 0;  // autotuned lanes per output of the persistent matvec
     DevBuf<double> w64b, zbuf, pbuf;
     DevBuf<unsigned> pbar;
+    DevBuf<int64_t> abounds;  // work-balanced slices of the persistent kernel
+    int64_t aE = 0;           // longest of them
     // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
     DevBuf<double> q64, jw64;
     DevBuf<float> q32, jw32;

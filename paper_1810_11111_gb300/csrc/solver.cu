@@ -380,6 +380,8 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
         pw.pbuf = s->pbuf.p;
         pw.bar = s->pbar.p + 2 * species;
         pw.G = s->arn_G;
+        pw.bounds = s->abounds.p;
+        pw.E = s->aE;
         krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, s->dt);
     } else {
         auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
@@ -767,6 +769,14 @@ void solver_alloc(sgk_solver* s) {
         s->pbuf.alloc(arnoldi_persistent_pbuf_size(s->ctx, M));
         s->pbar.alloc(2 * S);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
+        // slices of about equal work (the species share one index set)
+        const std::vector<int64_t> bnd = arnoldi_slice_bounds(s->ops[0], arnoldi_persistent_ctas(s->ctx), 2 * M);
+        int64_t longest = 1;
+        for (size_t i = 0; i + 1 < bnd.size(); ++i) longest = std::max<int64_t>(longest, bnd[i + 1] - bnd[i]);
+        if (longest <= 24 * 1024) {  // else equal slices (the kernel stages a slice in shared memory)
+            s->aE = longest;
+            s->abounds.upload(bnd, s->ctx->stream);
+        }
         // tune the matvec's lanes per output on this operator and size (the
         // runs use the Krylov workspace and W, which hold nothing yet)
         PersistentWork pw;
@@ -774,6 +784,8 @@ void solver_alloc(sgk_solver* s) {
         pw.Z = s->zbuf.p;
         pw.pbuf = s->pbuf.p;
         pw.bar = s->pbar.p;
+        pw.bounds = s->abounds.p;
+        pw.E = s->aE;
         s->arn_G = arnoldi_autotune(s->ctx, s->ops[0], pw, krylov_work<double>(s, 0), s->W.p, n, M);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
     }
