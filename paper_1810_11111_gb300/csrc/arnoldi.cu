@@ -6,20 +6,26 @@
 // Each CTA owns a contiguous slice of the coefficient vector.  It computes
 // the matvec outputs of its slice (gather form, sgk_gmv.h) and at once the
 // partial inner products of that slice with the basis columns, so the
-// matvec and the first projection need no barrier between them.  Three grid
-// barriers per step publish (1) the partials of V^T w, (2) those of the
-// second pass, (3) those of ||w||^2; after each, every CTA sums the partials
-// of all CTAs itself, in a fixed order, so all CTAs hold bitwise equal
-// h1, h2 and beta and take the same breakdown decision without another
-// barrier.  The next matvec gathers the unnormalised w (final after barrier
-// 3) and scales its outputs by 1 / beta; the two w buffers alternate so that
-// those gathers never race with the writes of the next step.  Partial sums go
-// to three rotating buffers for the same reason.
+// matvec and the first projection need no barrier between them.  Two grid
+// barriers per step publish (1) V^T w, (2) V^T w' together with ||w'||^2
+// (the norm of w'' follows by Pythagoras; near breakdown a third barrier
+// sums it explicitly).  The cross-CTA sums are exact: every CTA adds its
+// partials, as 128-bit fixed-point integers, into integer accumulators with
+// atomic adds, and after the barrier every CTA reads the same totals, so all
+// CTAs hold bitwise equal h1, h2 and beta and take the same breakdown
+// decision without another barrier; the results do not depend on the order
+// in which CTAs arrive.  The next matvec gathers the unnormalised w' and
+// forms A v_{j+1} = (A w' - Z h2) / beta from the stored raw outputs Z; the
+// two w buffers alternate so that those gathers never race with the writes
+// of the next step.  Accumulator sets rotate over three buffers for the same
+// reason.
 //
 // Barriers are counters in global memory with a bounded wait: a CTA that
 // waits longer than the limit sets an error flag and returns, and every
 // other CTA sees the flag in its own wait and returns too; the host reports
 // SGK_ETIMEOUT.  The cooperative launch makes every CTA resident at once.
+#include <cmath>
+
 #include "sgk_arnoldi.cuh"
 
 namespace sgk_arn {
@@ -46,7 +52,11 @@ int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx) {
     return (int64_t)persistent_ctas(ctx) * 24 * 1024;
 }
 
-size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) { return (size_t)3 * ctx->num_sms * (M + 1); }
+size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) {
+    (void)M;
+    // per-CTA norm partials, then the three fixed-point accumulator sets
+    return (size_t)ctx->num_sms + 3 * sgk_arn::FX_COLS * sgk_arn::FX_LIMBS;
+}
 
 static size_t loc_bytes(int d) {
     switch (d) {
@@ -72,7 +82,6 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     ArnArgs a;
     a.n = n;
     a.M = M;
-    a.ldp = M + 1;
     a.E = (int)E;
     a.v = v;
     a.V = kw.V;
@@ -81,6 +90,18 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     a.Z = pw.Z;
     a.H = kw.H;
     a.pbuf = pw.pbuf;
+    a.acc = reinterpret_cast<unsigned long long*>(pw.pbuf + ctx->num_sms);
+    // fixed-point scales from the bound ||A v|| <= ||A|| for ||v|| = 1:
+    // |partial| <= 2^(e - 1) with e = ceil(log2 ||A||) + 1, entered as
+    // floor(p 2^(110 - e)), so |P| < 2^110; the squared norm likewise with 2e
+    {
+        const double an = op->anorm > 0.0 ? op->anorm : 1.0;
+        const int e = std::min(400, std::max(-400, (int)std::ceil(std::log2(an)) + 1));
+        a.sc_h = std::ldexp(1.0, 46 - e);
+        a.isc_h = std::ldexp(1.0, e - 110);
+        a.sc_n = std::ldexp(1.0, 46 - 2 * e);
+        a.isc_n = std::ldexp(1.0, 2 * e - 110);
+    }
     a.bar = pw.bar;
     a.ks = kw.ks;
     a.bounds = pw.bounds;

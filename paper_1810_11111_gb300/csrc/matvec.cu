@@ -7,6 +7,7 @@
 // fixed order (per lane two accumulators per direction, directions in order,
 // then a fixed xor tree over the group), so results are deterministic.
 #include <algorithm>
+#include <cmath>
 
 #include "sgk_gmv.h"
 
@@ -129,6 +130,22 @@ void build_gmv_tables(sgk_op* op) {
         chunk[c] = (int32_t)t;
     }
     op->madds = madds;
+    // ||A||_2 <= sum_i |kappa_i| ||S||_2 (A restricted from the full tensor
+    // operator to a subspace spanned by orthonormal basis functions), and
+    // ||S||_2 <= max(||S||_1, ||S||_inf)
+    {
+        std::vector<double> rs(S.rows, 0.0), cs(S.rows, 0.0);
+        for (int a = 0; a < S.rows; ++a)
+            for (int q = S.ptr[a]; q < S.ptr[a + 1]; ++q) {
+                rs[a] += std::fabs(S.val[q]);
+                if (S.col[q] < S.rows) cs[S.col[q]] += std::fabs(S.val[q]);
+            }
+        double sn = 0.0;
+        for (int a = 0; a < S.rows; ++a) sn = std::max(sn, std::max(rs[a], cs[a]));
+        double ks = 0.0;
+        for (int i = 0; i < d; ++i) ks += std::fabs(op->kappa[i]);
+        op->anorm = ks * sn;
+    }
     const size_t nnz = S.val.size();
     std::vector<double> cvk(nnz * d);
     std::vector<float> cvkf(nnz * d);

@@ -16,7 +16,6 @@ constexpr unsigned BAR_SPIN_LIMIT = 1u << 21;  // polls of ~0.1-0.5 us each
 struct ArnArgs {
     int64_t n;
     int M;
-    int ldp;  // columns of each partial-sum buffer (>= M + 1), each column gridDim.x long
     int E;    // slice length per CTA (ceil(n / gridDim.x))
     int smem_vz;   // this CTA's slices of V and Z live in shared memory (and V also in HBM)
     int smem_loc;  // the located rows of every output of the slice live in shared memory
@@ -26,11 +25,19 @@ struct ArnArgs {
     double* w1;
     double* Z;     // raw matvec outputs A v_c, column c at Z + c n (own slices only)
     double* H;     // (M + 1) x M row-major
-    double* pbuf;  // 3 buffers of ldp columns x gridDim.x
+    double* pbuf;  // gridDim.x per-CTA partials of a norm (gamma, explicit fallback)
+    unsigned long long* acc;  // 3 rotating sets of FX_COLS fixed-point accumulators (FX_LIMBS words each)
+    // fixed-point scales: a partial p of an inner product enters as
+    // floor(p sc 2^64), the sum is read back times isc; _h for the columns of
+    // V^T w (|p| <= ||A||), _n for ||w'||^2 (|p| <= ||A||^2)
+    double sc_h, isc_h, sc_n, isc_n;
     unsigned* bar;  // [0] barrier arrivals (zero at launch), [1] error flag
     KrylovScalars* ks;
     const int64_t* bounds;  // slice b = [bounds[b], bounds[b+1]) (work-balanced), or null: equal slices of E
 };
+
+constexpr int FX_COLS = SGK_MAX_KRYLOV + 2;  // columns of one accumulator set
+constexpr int FX_LIMBS = 4;                   // three 56-bit limbs and a count of invalid partials
 
 // Dynamic shared memory of the kernel, in bytes.
 template <int D>
@@ -78,7 +85,7 @@ __device__ __forceinline__ double warp_sum(double a) {
 
 // out[c] = sum over CTAs b of P[c nb + b], c < ncols (the partials are
 // stored column by column, so a column is one contiguous run), identical in every
-// CTA.  Each thread sums a fixed subset of rows of one column (all its loads
+// CTA; used for the norms of v and of an explicitly normalised w''.  Each thread sums a fixed subset of rows of one column (all its loads
 // issued at once), the subset sums go through shared memory and one thread
 // per column adds them in a fixed order: FP64 additions with every lane
 // busy, no shuffle trees.  P was written by other CTAs during this launch:
@@ -120,23 +127,92 @@ __device__ __forceinline__ void colsum(const double* P, int nb, int ncols, doubl
 
 // out[c] = sum_{u < ne} Vl[c vld + u] ws[u], c < ncols (this CTA's slice,
 // Vl/vld its basis columns in shared or global memory); with norm, also
-// out[ncols] = sum ws[u]^2.  A warp per column.
+// out[ncols] = sum ws[u]^2; out in shared memory, complete on return.  CH
+// threads per column (a power of two, the most with nt CH <= PT, at most 32)
+// sum strided elements in two chains; the CH partials of a column are added
+// through shared memory in a fixed tree (quarters by four threads, then the
+// four by one), so the FP64 work is spread over every warp of the CTA (FP64
+// issue is slow on this part: spreading it, not shortening chains, is what
+// pays).  tmp holds PT doubles, tmp2 4 (SGK_MAX_KRYLOV + 2).
 __device__ __forceinline__ void slice_dots(const double* Vl, int64_t vld, int ncols, const double* ws, int ne,
-                                           double* out, int ostride, bool norm) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                                           double* out, bool norm, double* tmp, double* tmp2) {
     const int nt = ncols + (norm ? 1 : 0);
-    for (int c = wid; c < nt; c += PNW) {
+    int CH = 32;
+    while (CH > 1 && nt * CH > PT) CH >>= 1;
+    const int t = threadIdx.x;
+    if (t < nt * CH) {
+        const int c = t / CH, k = t - (t / CH) * CH;
         const double* vc = c < ncols ? Vl + c * vld : ws;
         double a = 0.0, b = 0.0;
-        int u = lane;
-        for (; u + 32 < ne; u += 64) {
+        int u = k;
+        for (; u + CH < ne; u += 2 * CH) {
             a += vc[u] * ws[u];
-            b += vc[u + 32] * ws[u + 32];
+            b += vc[u + CH] * ws[u + CH];
         }
         if (u < ne) a += vc[u] * ws[u];
-        a = warp_sum(a + b);
-        if (lane == 0) out[(int64_t)c * ostride] = a;
+        tmp[t] = a + b;
     }
+    __syncthreads();
+    const int Q = CH < 4 ? CH : 4, per = CH / Q;
+    if (t < nt * Q) {
+        const double* p = tmp + t * per;  // column t / Q, quarter t % Q
+        double a = p[0];
+        for (int i = 1; i < per; ++i) a += p[i];
+        tmp2[t] = a;
+    }
+    __syncthreads();
+    if (t < nt) {
+        const double* p = tmp2 + t * Q;
+        out[t] = Q == 4 ? (p[0] + p[1]) + (p[2] + p[3]) : (Q == 2 ? p[0] + p[1] : p[0]);
+    }
+    __syncthreads();
+}
+
+// Exact sums across CTAs.  A partial p is taken as the 128-bit integer
+// P = trunc(p sc 2^64) (two's complement; sc a power of two chosen from a
+// bound on |p| so that |P| < 2^110) and added to per-column accumulators of
+// three 56-bit limbs with 64-bit integer atomic adds.  Integer addition is
+// associative: the total is exact whatever the order of arrival, and every
+// CTA reads back the same value, in every run.  A partial that is not
+// finite or outside the range is counted in the fourth word and makes the
+// column NaN.
+constexpr unsigned long long FX_M56 = (1ull << 56) - 1;
+
+__device__ __forceinline__ void fx_red(unsigned long long* a, double p, double sc) {
+    const double q = p * sc;  // |q| < 2^46 when the bound holds
+    const double aq = fabs(q);
+    if (!(aq < 1125899906842624.0)) {  // 2^50; false for NaN
+        atomicAdd(a + 3, 1ull);
+        return;
+    }
+    // |P| = H 2^64 + L: the integer part, and the fraction (exact for a
+    // non-negative double) scaled to 64 bits
+    const double hd = floor(aq);
+    unsigned long long H = __double2ull_rn(hd);
+    unsigned long long L = __double2ull_rd((aq - hd) * 18446744073709551616.0);
+    if (q < 0.0) {  // two's complement of the 128-bit magnitude
+        L = ~L + 1ull;
+        H = ~H + (L == 0ull ? 1ull : 0ull);
+    }
+    atomicAdd(a, L & FX_M56);
+    atomicAdd(a + 1, ((L >> 56) | (H << 8)) & FX_M56);
+    atomicAdd(a + 2, (unsigned long long)((long long)H >> 48));
+}
+
+// The accumulated sum times isc (L2 loads: the limbs were added by other CTAs).
+__device__ __forceinline__ double fx_value(const unsigned long long* a, double isc) {
+    const unsigned long long s0 = __ldcg(a), s1 = __ldcg(a + 1), s2 = __ldcg(a + 2), bad = __ldcg(a + 3);
+    if (bad != 0ull) return __longlong_as_double(0x7ff8000000000000ll);
+    // s0 + s1 2^56 + s2 2^112 (s2 signed) as hi 2^64 + lo
+    unsigned long long lo = s0 + (s1 << 56);
+    unsigned long long hi = (s1 >> 8) + (s2 << 48) + (lo < s0 ? 1ull : 0ull);
+    const bool neg = (long long)hi < 0;
+    if (neg) {  // magnitude, so that the conversion below keeps full relative precision
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double m = __ull2double_rn(hi) * 18446744073709551616.0 + __ull2double_rn(lo);
+    return (neg ? -m : m) * isc;
 }
 
 // w -= V[:, :ncols] h on this CTA's slice, one thread per element (four
@@ -186,10 +262,12 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     extern __shared__ __align__(16) double smem[];
     __shared__ double h1[SGK_MAX_KRYLOV + 2];
     __shared__ double h2[SGK_MAX_KRYLOV + 2];
+    __shared__ double sdot[SGK_MAX_KRYLOV + 2];  // this CTA's inner products
     __shared__ double red[PNW];
     __shared__ double s_scal[4];
-    // column-sum staging: ncols x (row slots) <= max(PT, 4 (SGK_MAX_KRYLOV + 2))
+    // column-sum and inner-product staging: <= max(PT, 4 (SGK_MAX_KRYLOV + 2))
     __shared__ double ctmp[PT > 4 * (SGK_MAX_KRYLOV + 2) ? PT : 4 * (SGK_MAX_KRYLOV + 2)];
+    __shared__ double ctmp2[4 * (SGK_MAX_KRYLOV + 2)];
     __shared__ int s_ok, s_flag;
     const int nb = gridDim.x, b = blockIdx.x;
     const int64_t n = a.n;
@@ -206,13 +284,37 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     const int64_t vld = a.smem_vz ? E : n;
     double* const Zl = a.smem_vz ? Zs : a.Z + lo;
     const int64_t zld = a.smem_vz ? E : n;
-    double* const P0 = a.pbuf;                            // V^T w, first pass
-    double* const P1 = a.pbuf + (int64_t)nb * a.ldp;      // second pass and ||w'||^2
-    double* const P2 = a.pbuf + (int64_t)2 * nb * a.ldp;  // norms
+    double* const P2 = a.pbuf;  // norms
     unsigned epoch = 0;
     auto barrier = [&]() {
         ++epoch;
         return grid_barrier(a.bar, epoch * (unsigned)nb, &s_ok);
+    };
+    // fixed-point reductions: phase p adds into set p % 3, read after its
+    // barrier; after the barrier of phase p every CTA is done reading set
+    // (p - 1) % 3, which CTA 0 then clears for phase p + 2 (its stores precede
+    // its arrival at the barrier before that phase's atomics)
+    unsigned fx_phase = 0;
+    auto fx_set = [&](unsigned p) { return a.acc + (size_t)(p % 3u) * FX_COLS * FX_LIMBS; };
+    // publish sdot[0..nt) (the last column with the norm scale when norm)
+    auto fx_publish = [&](int nt, bool norm) {
+        unsigned long long* set = fx_set(fx_phase);
+        if ((int)threadIdx.x < nt) {
+            const bool nc_col = norm && (int)threadIdx.x == nt - 1;
+            fx_red(set + (size_t)threadIdx.x * FX_LIMBS, sdot[threadIdx.x], nc_col ? a.sc_n : a.sc_h);
+        }
+    };
+    auto fx_read = [&](int nt, bool norm, double* out) {
+        const unsigned long long* set = fx_set(fx_phase);
+        if ((int)threadIdx.x < nt) {
+            const bool nc_col = norm && (int)threadIdx.x == nt - 1;
+            out[threadIdx.x] = fx_value(set + (size_t)threadIdx.x * FX_LIMBS, nc_col ? a.isc_n : a.isc_h);
+        }
+        if (b == 0) {
+            unsigned long long* old = fx_set(fx_phase + 2u);
+            for (int i = threadIdx.x; i < FX_COLS * FX_LIMBS; i += PT) old[i] = 0ull;
+        }
+        ++fx_phase;
     };
     const int r = threadIdx.x & (G - 1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -220,6 +322,10 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     if (sloc)
         for (int u = threadIdx.x; u < ne; u += PT) gmv_locate<double, D, KP1>(ga, lo + u, sloc[u]);
 
+    // the accumulator sets start cleared (before the first barrier; the
+    // first atomics follow the second)
+    if (b == 0)
+        for (int i = threadIdx.x; i < 3 * FX_COLS * FX_LIMBS; i += PT) a.acc[i] = 0ull;
     // gamma = ||v||
     for (int u = threadIdx.x; u < ne; u += PT) ws[u] = a.v[lo + u];
     __syncthreads();
@@ -283,17 +389,19 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             }
         }
         __syncthreads();
-        slice_dots(Vl, vld, nc, ws, ne, P0 + b, nb, false);
+        slice_dots(Vl, vld, nc, ws, ne, sdot, false, ctmp, ctmp2);
+        fx_publish(nc, false);
         if (!barrier()) return;
-        colsum(P0, nb, nc, h1, ctmp);
+        fx_read(nc, false, h1);
         __syncthreads();
         // w' = w - V h1, published for the next matvec
         slice_update(Vl, vld, nc, h1, w, ws, lo, ne, nullptr, nullptr, 0.0);
         __syncthreads();
         // second pass: V^T w' and ||w'||^2 in one reduction
-        slice_dots(Vl, vld, nc, ws, ne, P1 + b, nb, true);
+        slice_dots(Vl, vld, nc, ws, ne, sdot, true, ctmp, ctmp2);
+        fx_publish(nc + 1, true);
         if (!barrier()) return;
-        colsum(P1, nb, nc + 1, h2, ctmp);
+        fx_read(nc + 1, true, h2);
         __syncthreads();
         // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal, w'' = w' - V h2);
         // when the second pass removed more than 1e-3 of ||w'||^2 (near

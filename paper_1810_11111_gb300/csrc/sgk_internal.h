@@ -305,6 +305,8 @@ struct sgk_op {
     DevBuf<float> gmv_cvkf;  // the same in FP32
     int64_t madds = 0;  // multiply-adds of one matvec (entries of A on the index set, per direction)
     std::vector<int> rlen_host;  // host copy of rlen
+    // bound on ||A||_2 of the sparse-grid operator: sum_i |kappa_i| max(||S||_1, ||S||_inf)
+    double anorm = 0.0;
 };
 
 // Builds and checks the gather-matvec tables of an assembled operator.
