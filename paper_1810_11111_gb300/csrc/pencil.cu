@@ -7,16 +7,18 @@
 // (k+1)^{d-1} fibers of that cell's Legendre degrees, each of length
 // H = (k+1) 2^N along direction d-1.  In shared memory it
 //   1. reconstructs each fiber in the finest-cell Legendre basis with the
-//      two-scale relations, level by level: the children of a level-(n-1)
-//      cell get H_h^T (parent coefficients) + G_h^T (level-n wavelet
-//      coefficients), 2 (k+1)^2 FMAs per child cell;
+//      two-scale relations (the children of a level-(n-1) cell get
+//      H_h^T (parent coefficients) + G_h^T (level-n wavelet coefficients),
+//      2 (k+1)^2 FMAs per child cell), one thread per subtree of up to 8
+//      finest cells expanded in registers: one barrier per set;
 //   2. runs the cell quadrature with one thread per finest cell of the
 //      pencil: Legendre -> q^d Gauss points -> f(u) or f'(u) w times the
 //      weights -> Legendre moments, as nested sum-factorised loops whose
-//      indices are compile-time constants (registers only); f and f' are
-//      dense polynomials evaluated by Horner's rule;
+//      indices are compile-time constants; f and f' are dense polynomials
+//      evaluated by Horner's rule;
 //   3. decomposes the moments back to hierarchical coefficients with the
-//      transposed two-scale relations and stores them.
+//      transposed two-scale relations (subtrees of up to 3 levels reduced in
+//      registers, one barrier per 3 levels) and stores them.
 // Specialised for (d, k+1, q, species); other shapes use the unfused path.
 #include <algorithm>
 
@@ -165,210 +167,288 @@ struct Quad<T, D, KP1, Q, S, JAC, D> {
     }
 };
 
-// Reconstruct P fibers (hierarchical, levels 0..N, in `src`) to the finest
-// Legendre basis using scratch buffers a and b; returns the buffer holding
-// the result (a, b, or src when N = 0).
-template <typename T, int KP1, int P>
-__device__ T* reconstruct(T* src, T* a, T* b, int H, int N, const Filt<T, KP1>& F) {
-    const T* cur = src;
-    T* dst = a;
-    for (int n = 1; n <= N; ++n) {
-        const int npar = 1 << (n - 1);
-        for (int it = threadIdx.x; it < P * npar * 2; it += blockDim.x) {
-            const int h = it & 1;
-            const int c = (it >> 1) & (npar - 1);
-            const int f = (it >> 1) >> (n - 1);
-            const T* par = cur + f * H + c * KP1;
-            const T* det = src + f * H + (KP1 << (n - 1)) + c * KP1;
-            T pv[KP1], dv[KP1];
+// Outermost quadrature level with the cell's coefficients read from shared
+// memory (coefficient e = f (k+1) + r of the cell at pu[r PS + f]: fiber f,
+// position r along the pencil) instead of registers, which keeps only the
+// moments and the inner levels' partial sums live.
+template <typename T, int D, int KP1, int Q, int S, bool JAC, int PS>
+struct QuadTop {
+    static constexpr int NC = Pow<KP1, D>::v;
+    static constexpr int NS = NC / KP1;
+    // volatile: re-read at every Gauss point (hoisting the loads out of the
+    // loop would hold all of them in registers again)
+    __device__ __forceinline__ static T at(const T* p, int e) {
+        return reinterpret_cast<const volatile T*>(p)[(e % KP1) * PS + e / KP1];
+    }
+    __device__ __forceinline__ static void run(const QuadTab<T>& tb, const Poly<T, S>& P, const T* const (&pu)[S],
+                                               const T* const (&pw)[S], T (&M)[S][NC]) {
+#pragma unroll 1
+        for (int g = 0; g < Q; ++g) {
+            T su[S][NS], sw[S][NS], sm[S][NS];
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    T a = T(0), b = T(0);
+#pragma unroll
+                    for (int r = 0; r < KP1; ++r) {
+                        a += tb.B[g][r] * at(pu[s], r * NS + i);
+                        if (JAC) b += tb.B[g][r] * at(pw[s], r * NS + i);
+                    }
+                    su[s][i] = a;
+                    sw[s][i] = b;
+                    sm[s][i] = T(0);
+                }
+            Quad<T, D, KP1, Q, S, JAC, 1>::run(tb, P, su, sw, sm, tb.w[g]);
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int r = 0; r < KP1; ++r)
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) M[s][r * NS + i] += tb.B[g][r] * sm[s][i];
+        }
+    }
+};
+
+// Two-scale pyramids on register subtrees.  In shared memory a buffer holds
+// the P fibers of one set interleaved, position pos of fiber f at
+// pos PS + f (PS = P rounded up to odd: threads on consecutive fibers, or
+// on consecutive cells of one fiber, hit distinct banks).
+constexpr int PD = 3;  // levels of a subtree expanded or reduced in registers
+
+// Forward (hierarchical levels 0..N in X -> finest-cell Legendre
+// coefficients in Y) for the subtree of 2^De finest cells under node j of
+// level t = N - De of fiber f: walks the t ancestors of that node from the
+// level-0 coefficients, then expands the subtree, children over consumed
+// parents.
+template <typename T, int KP1, int PS>
+__device__ __forceinline__ void fwd_subtree(const T* X, T* Y, int f, int j, int t, int De, const Filt<T, KP1>& F) {
+    T cell[1 << PD][KP1];
+#pragma unroll
+    for (int r = 0; r < KP1; ++r) cell[0][r] = X[r * PS + f];
+    for (int n = 1; n <= t; ++n) {
+        const int an = j >> (t - n), h = an & 1, par = an >> 1;
+        T d[KP1], q[KP1];
+#pragma unroll
+        for (int r = 0; r < KP1; ++r) d[r] = X[((KP1 << (n - 1)) + par * KP1 + r) * PS + f];
+#pragma unroll
+        for (int s2 = 0; s2 < KP1; ++s2) {
+            T acc = T(0);
 #pragma unroll
             for (int r = 0; r < KP1; ++r) {
-                pv[r] = par[r];
-                dv[r] = det[r];
+                // select, not index: a runtime index would put the filters
+                // in local memory
+                const T hf = h ? F.H[1][r][s2] : F.H[0][r][s2];
+                const T gf = h ? F.G[1][r][s2] : F.G[0][r][s2];
+                acc += hf * cell[0][r] + gf * d[r];
             }
-            T* o = dst + f * H + (2 * c + h) * KP1;
+            q[s2] = acc;
+        }
 #pragma unroll
-            for (int s = 0; s < KP1; ++s) {
-                T acc = T(0);
+        for (int r = 0; r < KP1; ++r) cell[0][r] = q[r];
+    }
 #pragma unroll
-                for (int r = 0; r < KP1; ++r) acc += F.H[h][r][s] * pv[r] + F.G[h][r][s] * dv[r];
-                o[s] = acc;
+    for (int l = 0; l < PD; ++l) {
+        if (l < De) {
+            const int n = t + l + 1;
+#pragma unroll
+            for (int i = (1 << l) - 1; i >= 0; --i) {
+                const int par = (j << l) + i;
+                T d[KP1], p[KP1];
+#pragma unroll
+                for (int r = 0; r < KP1; ++r) {
+                    p[r] = cell[i][r];
+                    d[r] = X[((KP1 << (n - 1)) + par * KP1 + r) * PS + f];
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int s2 = 0; s2 < KP1; ++s2) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int r = 0; r < KP1; ++r) acc += F.H[h][r][s2] * p[r] + F.G[h][r][s2] * d[r];
+                        cell[2 * i + h][s2] = acc;
+                    }
             }
         }
-        __syncthreads();
-        cur = dst;
-        dst = (dst == a) ? b : a;
     }
-    return const_cast<T*>(cur);
+#pragma unroll
+    for (int i = 0; i < (1 << PD); ++i)
+        if (i < (1 << De))
+#pragma unroll
+            for (int s2 = 0; s2 < KP1; ++s2) Y[(((j << De) + i) * KP1 + s2) * PS + f] = cell[i][s2];
 }
 
-// Decompose P fibers of finest Legendre moments (in m, destroyed) into
-// hierarchical coefficients in res, using scratch a.
-template <typename T, int KP1, int P>
-__device__ void decompose(T* m, T* a, T* res, int H, int N, const Filt<T, KP1>& F) {
-    T* cur = m;
-    T* dst = a;
-    for (int n = N; n >= 1; --n) {
-        const int npar = 1 << (n - 1);
-        for (int it = threadIdx.x; it < P * npar; it += blockDim.x) {
-            const int c = it & (npar - 1);
-            const int f = it >> (n - 1);
-            const T* c0 = cur + f * H + 2 * c * KP1;
-            T x0[KP1], x1[KP1];
+// Transposed step for subtree j of fiber f: its 2^De nodes of level Lhi,
+// node m stored at position m stride of Mb (stride = (k+1) 2^{N - Lhi};
+// the finest cells are contiguous), reduced over De levels; the details of
+// levels Lhi - De + 1 .. Lhi go to Y (hierarchical layout) and the root
+// (level Lhi - De) in place over the first node, or to Y when it is level 0.
+template <typename T, int KP1, int PS>
+__device__ __forceinline__ void bwd_subtree(T* Mb, T* Y, int f, int j, int Lhi, int De, int stride,
+                                            const Filt<T, KP1>& F) {
+    T cell[1 << PD][KP1];
 #pragma unroll
-            for (int s = 0; s < KP1; ++s) {
-                x0[s] = c0[s];
-                x1[s] = c0[KP1 + s];
-            }
-            T* po = dst + f * H + c * KP1;
-            T* dout = res + f * H + (KP1 << (n - 1)) + c * KP1;
+    for (int i = 0; i < (1 << PD); ++i)
+        if (i < (1 << De))
 #pragma unroll
-            for (int r = 0; r < KP1; ++r) {
-                T sp = T(0), sd = T(0);
+            for (int s2 = 0; s2 < KP1; ++s2) cell[i][s2] = Mb[(((j << De) + i) * stride + s2) * PS + f];
 #pragma unroll
-                for (int s = 0; s < KP1; ++s) {
-                    sp += F.H[0][r][s] * x0[s] + F.H[1][r][s] * x1[s];
-                    sd += F.G[0][r][s] * x0[s] + F.G[1][r][s] * x1[s];
+    for (int l = PD - 1; l >= 0; --l) {
+        if (l < De) {
+            const int n = Lhi - De + l + 1;  // level of the children
+#pragma unroll
+            for (int i = 0; i < (1 << l); ++i) {
+                T x0[KP1], x1[KP1];
+#pragma unroll
+                for (int s2 = 0; s2 < KP1; ++s2) {
+                    x0[s2] = cell[2 * i][s2];
+                    x1[s2] = cell[2 * i + 1][s2];
                 }
-                po[r] = sp;
-                dout[r] = sd;
+                const int par = (j << l) + i;
+#pragma unroll
+                for (int r = 0; r < KP1; ++r) {
+                    T sp = T(0), sd = T(0);
+#pragma unroll
+                    for (int s2 = 0; s2 < KP1; ++s2) {
+                        sp += F.H[0][r][s2] * x0[s2] + F.H[1][r][s2] * x1[s2];
+                        sd += F.G[0][r][s2] * x0[s2] + F.G[1][r][s2] * x1[s2];
+                    }
+                    cell[i][r] = sp;
+                    Y[((KP1 << (n - 1)) + par * KP1 + r) * PS + f] = sd;
+                }
             }
         }
-        __syncthreads();
-        T* t = cur;
-        cur = dst;
-        dst = t;
     }
-    for (int it = threadIdx.x; it < P * KP1; it += blockDim.x) {
-        const int f = it / KP1, r = it % KP1;
-        res[f * H + r] = cur[f * H + r];
+    const bool top = Lhi == De;
+#pragma unroll
+    for (int r = 0; r < KP1; ++r) {
+        if (top) Y[r * PS + f] = cell[0][r];
+        else Mb[((j << De) * stride + r) * PS + f] = cell[0][r];
     }
-    __syncthreads();
 }
 
 template <typename T, int D, int KP1, int Q, int S, bool JAC>
 __global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, const QuadTab<T> tb,
                                                      const Filt<T, KP1> F, const Poly<T, S> poly) {
     constexpr int P = Pow<KP1, D - 1>::v;  // fibers per species and set
+    constexpr int PS = P | 1;              // odd fiber stride in shared memory
     constexpr int NC = Pow<KP1, D>::v;     // coefficients per cell
     constexpr int NSETS = JAC ? 2 * S : S;
-    constexpr int NBUF = NSETS + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_of[P];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int H = args.H, N = args.N;
-    const int fb = P * H;  // one buffer: P fibers
-    auto buf = [&](int i) { return sm + (size_t)i * fb; };
+    const int bs = H * PS;  // one buffer: the P fibers of one set
+    auto buf = [&](int i) { return sm + (size_t)i * bs; };
+    const int De = N < PD ? N : PD;  // levels of a forward subtree
+    const int t = N - De;            // level of the forward subtree roots
     for (long long pen = blockIdx.x; pen < args.npencils; pen += gridDim.x) {
-        long long obase = 0;
-        {
-            long long rem = pen, mul = 1;
+        // source offset of every fiber: o_f = obase + sum_m r_m H^{d-2-m}
+        if ((int)threadIdx.x < P) {
+            long long o = 0, rem = pen, mul = 1;
             for (int m = D - 2; m >= 0; --m) {
                 const long long c = rem % args.ncell1;
                 rem /= args.ncell1;
-                obase += c * KP1 * mul;
+                o += c * KP1 * mul;
                 mul *= H;
             }
-        }
-        // 1. load the hierarchical fibers of every set into buffers 0..NSETS-1
-        // fiber offset of fiber f: o_f = obase + sum_m r_m H^{d-2-m}
-        auto fiber_offset = [&](int f) {
-            long long o = obase, mul = 1;
-            int rr = f;
-#pragma unroll
+            int rr = threadIdx.x;
+            mul = 1;
             for (int m = D - 2; m >= 0; --m) {
                 o += (rr % KP1) * mul;
                 rr /= KP1;
                 mul *= H;
             }
-            return o;
-        };
-        // address of position a of fiber offset o in the level-chunked layout
-        auto chunk = [&](long long o, int a) {
+            s_of[threadIdx.x] = o;
+        }
+        __syncthreads();
+        // 1. load every set's hierarchical fibers into buffers 0..NSETS-1.
+        //    Position a of fiber offset o lives in the level-l chunk at
+        //    cbase[l] + o nl + (a - off); l, nl and a - off depend on a only
+        for (int a = threadIdx.x; a < H; a += blockDim.x) {
             const int q = a / KP1;
             const int l = q == 0 ? 0 : 32 - __clz(q);
             const int off = l ? (KP1 << (l - 1)) : 0;
-            const int nl = l ? (KP1 << (l - 1)) : KP1;
-            return args.cbase[l] + o * nl + (a - off);
-        };
-#pragma unroll 1
-        for (int sf = 0; sf < NSETS * P; ++sf) {
-            const int set = sf / P, f = sf - (sf / P) * P;
-            const long long o = fiber_offset(f);
-            const T* src = reinterpret_cast<const T*>(set < S ? args.u[set] : args.w[set - S]);
-            T* dstp = sm + (size_t)sf * H;
-            for (int a = threadIdx.x; a < H; a += blockDim.x) async_copy(dstp + a, src + chunk(o, a));
+            const long long nl = l ? (KP1 << (l - 1)) : KP1;
+            const long long base = args.cbase[l] + (a - off);
+#pragma unroll
+            for (int set = 0; set < NSETS; ++set) {
+                const T* src = reinterpret_cast<const T*>(set < S ? args.u[set] : args.w[set - S]) + base;
+                T* dst = buf(set) + a * PS;
+#pragma unroll
+                for (int f = 0; f < P; ++f) async_copy(dst + f, src + s_of[f] * nl);
+            }
         }
         async_wait_all();
         __syncthreads();
-        // 2. reconstruct each set; buffers rotate: a set's input buffer is
-        //    free once its reconstruction is done
-        int nod[NSETS];
-        int freeb[2] = {NSETS, NSETS + 1};
-#pragma unroll
+        // 2. forward pyramids, one set after the other: set 0 into the spare
+        //    buffer NSETS, set k >= 1 into buffer k-1 (freed by set k-1)
+        const int units = P << t;
+#pragma unroll 1
         for (int set = 0; set < NSETS; ++set) {
-            T* r = reconstruct<T, KP1, P>(buf(set), buf(freeb[0]), buf(freeb[1]), H, N, F);
-            const int ri = (int)((r - sm) / fb);
-            nod[set] = ri;
-            if (ri == freeb[0]) freeb[0] = set;
-            else if (ri == freeb[1]) freeb[1] = set;
+            const T* X = buf(set);
+            T* Y = buf(set == 0 ? NSETS : set - 1);
+            for (int u = threadIdx.x; u < units; u += blockDim.x)
+                fwd_subtree<T, KP1, PS>(X, Y, u % P, u / P, t, De, F);
+            __syncthreads();
         }
+        // nodal buffer of set k: NSETS for k = 0, k - 1 otherwise; buffer
+        // NSETS - 1 is free
         // 3. cell quadrature, one thread per finest cell along the pencil;
-        //    moments go to the input buffers of the u sets (all consumed)
-        int mom[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) mom[s] = -1;
-        {
-            int used = 0;
-            for (int i = 0; i < NBUF && used < S; ++i) {
-                bool busy = false;
-#pragma unroll
-                for (int set = 0; set < NSETS; ++set) busy |= (nod[set] == i);
-                if (!busy) mom[used++] = i;
-            }
-        }
+        //    the moments of species s overwrite its nodal u values (each
+        //    thread reads and writes only its own cell)
         const int ncell = H / KP1;
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-            T Cu[S][NC], Cw[S][NC], M[S][NC];
+            const T* pu[S];
+            const T* pw[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                pu[s] = buf(s == 0 ? NSETS : s - 1) + c * KP1 * PS;
+                pw[s] = JAC ? buf(S + s - 1) + c * KP1 * PS : pu[s];
+            }
+            T M[S][NC];
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    const int f = i / KP1, r = i % KP1;
-                    Cu[s][i] = buf(nod[s])[f * H + c * KP1 + r];
-                    Cw[s][i] = JAC ? buf(nod[S + s])[f * H + c * KP1 + r] : T(0);
-                    M[s][i] = T(0);
-                }
-            Quad<T, D, KP1, Q, S, JAC, 0>::run(tb, poly, Cu, Cw, M, T(1));
+                for (int i = 0; i < NC; ++i) M[s][i] = T(0);
+            QuadTop<T, D, KP1, Q, S, JAC, PS>::run(tb, poly, pu, pw, M);
 #pragma unroll
-            for (int s = 0; s < S; ++s)
+            for (int s = 0; s < S; ++s) {
+                T* mo = const_cast<T*>(pu[s]);
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    const int f = i / KP1, r = i % KP1;
-                    buf(mom[s])[f * H + c * KP1 + r] = M[s][i];
-                }
+                for (int i = 0; i < NC; ++i) mo[(i % KP1) * PS + i / KP1] = M[s][i];
+            }
         }
         __syncthreads();
-        // 4. decompose each species' moments (nodal buffers are free now)
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            int sc = -1, rs = -1;
-            for (int i = 0; i < NBUF; ++i) {
-                bool busy = false;
-#pragma unroll
-                for (int t = 0; t < S; ++t) busy |= (mom[t] == i);
-                if (busy) continue;
-                if (sc < 0) sc = i;
-                else if (rs < 0) rs = i;
-            }
-            decompose<T, KP1, P>(buf(mom[s]), buf(sc), buf(rs), H, N, F);
-            // 5. store
-            T* dst = reinterpret_cast<T*>(args.out[s]);
-            const T* res = buf(rs);
+        // 4. per species: backward pyramid (stages of up to PD levels, roots
+        //    kept in place between them) into the free buffer, then store
+        T* Y = buf(NSETS - 1);
 #pragma unroll 1
-            for (int f = 0; f < P; ++f) {
-                const long long o = fiber_offset(f);
-                const T* rp = res + (size_t)f * H;
-                for (int a = threadIdx.x; a < H; a += blockDim.x) dst[chunk(o, a)] = rp[a];
+        for (int s = 0; s < S; ++s) {
+            T* Mb = buf(s == 0 ? NSETS : s - 1);
+            for (int Lhi = N; Lhi > 0;) {
+                const int de = Lhi < PD ? Lhi : PD;
+                const int nu = P << (Lhi - de), stride = KP1 << (N - Lhi);
+                for (int u = threadIdx.x; u < nu; u += blockDim.x)
+                    bwd_subtree<T, KP1, PS>(Mb, Y, u % P, u / P, Lhi, de, stride, F);
+                __syncthreads();
+                Lhi -= de;
+            }
+            if (N == 0) {  // one cell: the moments are the coefficients
+                for (int u = threadIdx.x; u < KP1 * PS; u += blockDim.x) Y[u] = Mb[u];
+                __syncthreads();
+            }
+            T* dst = reinterpret_cast<T*>(args.out[s]);
+            for (int a = threadIdx.x; a < H; a += blockDim.x) {
+                const int q = a / KP1;
+                const int l = q == 0 ? 0 : 32 - __clz(q);
+                const int off = l ? (KP1 << (l - 1)) : 0;
+                const long long nl = l ? (KP1 << (l - 1)) : KP1;
+                T* d0 = dst + args.cbase[l] + (a - off);
+                const T* y = Y + a * PS;
+#pragma unroll
+                for (int f = 0; f < P; ++f) d0[s_of[f] * nl] = y[f];
             }
             __syncthreads();
         }
@@ -392,8 +472,8 @@ void launch_one(sgk_ctx* ctx, const PencilArgs& a, const QuadTab<T>& tb, const d
         poly.c[rxd.species[m]][idx] += (T)rxd.coef[m];
     }
     constexpr int P = Pow<KP1, D - 1>::v;
-    constexpr int NBUF = (JAC ? 2 * S : S) + 2;
-    const size_t smem = (size_t)NBUF * P * a.H * sizeof(T);
+    constexpr int NBUF = (JAC ? 2 * S : S) + 1;
+    const size_t smem = (size_t)NBUF * (P | 1) * a.H * sizeof(T);
     SGK_REQUIRE(smem <= ctx->smem_optin, SGK_EUNSUPPORTED, "pencil exceeds shared memory");
     const int threads = std::min(256, std::max(64, a.H / KP1));
     const int grid = (int)std::min<long long>(a.npencils, (long long)ctx->num_sms * 16);

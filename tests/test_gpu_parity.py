@@ -291,6 +291,13 @@ RX_CASES = [
     (3, 3, 2, workloads.reaction_terms(workloads.CUBIC, 37.0)),
     (2, 3, 2, workloads.reaction_terms(workloads.SCHNAKENBERG)),
     (1, 6, 3, [[(2.0, (2,)), (-1.0, (1,)), (0.5, (0,))]]),
+    # fused pencil shapes with fewer levels than one register subtree, a
+    # single cell, and the four-dimensional and degree-1 variants
+    (3, 1, 2, workloads.reaction_terms(workloads.CUBIC, 50.0)),
+    (2, 2, 2, workloads.reaction_terms(workloads.SCHNAKENBERG)),
+    (2, 0, 2, workloads.reaction_terms(workloads.CUBIC, 50.0)),
+    (4, 3, 1, workloads.reaction_terms(workloads.CUBIC, 50.0)),
+    (3, 4, 1, workloads.reaction_terms(workloads.CUBIC, 50.0)),
 ]
 
 
@@ -319,19 +326,23 @@ def test_reaction_and_jacobian_fp64(ctx64, d, n, k, rx):
     idx.close()
 
 
-def test_reaction_fp32(ctx32):
-    d, n, k = 3, 3, 2
+@pytest.mark.parametrize("d,n,k", [(3, 3, 2), (3, 1, 2), (4, 3, 1), (2, 5, 2)])
+def test_reaction_fp32(ctx32, d, n, k):
     rx = workloads.reaction_terms(workloads.CUBIC, 100.0)
     idx = sgkiif.IndexSet(ctx32, d, n, k)
     op = sgkiif.Operator(ctx32, idx, [1.0] * d)
     sol = sgkiif.Solver(ctx32, [op], rx, 10, 0.01)
-    U = 0.3 * np.random.default_rng(6).standard_normal(idx.dof)
-    Ud = dev(U)
-    Fd = torch.empty_like(Ud)
+    rng = np.random.default_rng(6)
+    U = 0.3 * rng.standard_normal(idx.dof)
+    W = rng.standard_normal(idx.dof)
+    Ud, Wd = dev(U), dev(W)
+    Fd, Jd = torch.empty_like(Ud), torch.empty_like(Ud)
     sol.reaction_eval(Ud.data_ptr(), Fd.data_ptr())
+    sol.jacobian_apply(Ud.data_ptr(), Wd.data_ptr(), Jd.data_ptr())
     torch.cuda.synchronize()
-    F = Reaction(OIndex(d, n, k), rx).F([U])[0]
-    assert rel(Fd.cpu().numpy(), F) <= 1e-5
+    R = Reaction(OIndex(d, n, k), rx)
+    assert rel(Fd.cpu().numpy(), R.F([U])[0]) <= 1e-5
+    assert rel(Jd.cpu().numpy(), R.J([U], [W])[0]) <= 1e-5
     sol.close()
     op.close()
     idx.close()
