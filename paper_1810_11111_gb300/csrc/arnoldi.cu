@@ -55,8 +55,10 @@ int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx) {
 size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) {
     (void)M;
     // per-CTA norm partials, then the three fixed-point accumulator sets
-    return (size_t)ctx->num_sms + 3 * sgk_arn::FX_COLS * sgk_arn::FX_LIMBS;
+    return (size_t)ctx->num_sms + 3 * sgk_arn::FX_SET;
 }
+
+int arnoldi_outputs_per_pass() { return PT / 8; }
 
 static size_t loc_bytes(int d) {
     switch (d) {
@@ -74,6 +76,8 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     SGK_REQUIRE(n >= 1 && n <= arnoldi_persistent_max_n(ctx), SGK_EUNSUPPORTED, "persistent Arnoldi: n too large");
     SGK_REQUIRE(M >= 1 && M <= SGK_MAX_KRYLOV, SGK_EINVAL, "persistent Arnoldi: bad M");
     const int nb = persistent_ctas(ctx);
+    // the fixed-point limb sums hold one term below 2^56 per CTA
+    SGK_REQUIRE(nb <= 255, SGK_EUNSUPPORTED, "persistent Arnoldi: more than 255 CTAs");
     const int64_t E = pw.bounds ? pw.E : (n + nb - 1) / nb;
     SGK_REQUIRE(E >= 1 && E <= 24 * 1024, SGK_EUNSUPPORTED, "persistent Arnoldi: slice too long");
     // lanes per output in the matvec: the autotuned value, else eight (the

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) gmv_kernel(const GmvArgs<T, D> a, const T
         const bool live = g < a.n;
         GmvLoc<D> L;
         if (live) gmv_locate<T, D, KP1>(a, g, L);
-        const T acc = gmv_accumulate<T, D, G, false>(a, x, L, r, live);
+        const T acc = gmv_accumulate<T, D, G, 0>(a, x, L, r, live);
         if (live && r == 0) y[g] = acc;
     }
 }
@@ -162,7 +162,7 @@ void build_gmv_tables(sgk_op* op) {
     SGK_CUDA_CHECK(cudaStreamSynchronize(op->ctx->stream));
 }
 
-std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra) {
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap) {
     const sgk_index* idx = op->idx;
     const int d = idx->d, N = idx->n, kp1 = idx->k + 1, nl = N + 1;
     const std::vector<int>& rl = op->rlen_host;
@@ -204,6 +204,9 @@ std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra) {
             int cost = extra;
             for (int i = 0; i < d; ++i) cost += f[i][c[i]];
             cum += cost;
+            // cut at the next equal share of the work, or where the slice
+            // reaches cap coefficients
+            if (g + 1 - b[k - 1] >= cap) b[k++] = g + 1;
             while (k < nb && cum >= total * k / nb) b[k++] = g + 1;
             for (int m = d - 1; m >= 0; --m) {  // row-major odometer, last direction fastest
                 if (++c[m] < cnt[m]) break;

@@ -38,6 +38,10 @@ struct ArnArgs {
 
 constexpr int FX_COLS = SGK_MAX_KRYLOV + 2;  // columns of one accumulator set
 constexpr int FX_LIMBS = 4;                   // three 56-bit limbs and a count of invalid partials
+// copies of every accumulator: CTA b adds into copy b % FX_COPIES, so that
+// the CTAs arriving together do not serialise on the same words
+constexpr int FX_COPIES = 8;
+constexpr int FX_SET = FX_COPIES * FX_COLS * FX_LIMBS;  // words of one set
 
 // Dynamic shared memory of the kernel, in bytes.
 template <int D>
@@ -199,11 +203,21 @@ __device__ __forceinline__ void fx_red(unsigned long long* a, double p, double s
     atomicAdd(a + 2, (unsigned long long)((long long)H >> 48));
 }
 
-// The accumulated sum times isc (L2 loads: the limbs were added by other CTAs).
+// The accumulated sum of one column (its FX_COPIES copies, FX_COLS
+// columns apart) times isc; L2 loads: the limbs were added by other CTAs.
 __device__ __forceinline__ double fx_value(const unsigned long long* a, double isc) {
-    const unsigned long long s0 = __ldcg(a), s1 = __ldcg(a + 1), s2 = __ldcg(a + 2), bad = __ldcg(a + 3);
+    unsigned long long s0 = 0ull, s1 = 0ull, s2 = 0ull, bad = 0ull;
+#pragma unroll
+    for (int k = 0; k < FX_COPIES; ++k) {
+        const unsigned long long* c = a + (size_t)k * FX_COLS * FX_LIMBS;
+        s0 += __ldcg(c);
+        s1 += __ldcg(c + 1);
+        s2 += __ldcg(c + 2);
+        bad += __ldcg(c + 3);
+    }
     if (bad != 0ull) return __longlong_as_double(0x7ff8000000000000ll);
-    // s0 + s1 2^56 + s2 2^112 (s2 signed) as hi 2^64 + lo
+    // s0 + s1 2^56 + s2 2^112 (s2 signed) as hi 2^64 + lo; the limb sums
+    // stay below 2^64: at most one term below 2^56 per CTA
     unsigned long long lo = s0 + (s1 << 56);
     unsigned long long hi = (s1 >> 8) + (s2 << 48) + (lo < s0 ? 1ull : 0ull);
     const bool neg = (long long)hi < 0;
@@ -295,10 +309,10 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // (p - 1) % 3, which CTA 0 then clears for phase p + 2 (its stores precede
     // its arrival at the barrier before that phase's atomics)
     unsigned fx_phase = 0;
-    auto fx_set = [&](unsigned p) { return a.acc + (size_t)(p % 3u) * FX_COLS * FX_LIMBS; };
+    auto fx_set = [&](unsigned p) { return a.acc + (size_t)(p % 3u) * FX_SET; };
     // publish sdot[0..nt) (the last column with the norm scale when norm)
     auto fx_publish = [&](int nt, bool norm) {
-        unsigned long long* set = fx_set(fx_phase);
+        unsigned long long* set = fx_set(fx_phase) + (size_t)(b % FX_COPIES) * FX_COLS * FX_LIMBS;
         if ((int)threadIdx.x < nt) {
             const bool nc_col = norm && (int)threadIdx.x == nt - 1;
             fx_red(set + (size_t)threadIdx.x * FX_LIMBS, sdot[threadIdx.x], nc_col ? a.sc_n : a.sc_h);
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         }
         if (b == 0) {
             unsigned long long* old = fx_set(fx_phase + 2u);
-            for (int i = threadIdx.x; i < FX_COLS * FX_LIMBS; i += PT) old[i] = 0ull;
+            for (int i = threadIdx.x; i < FX_SET; i += PT) old[i] = 0ull;
         }
         ++fx_phase;
     };
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // the accumulator sets start cleared (before the first barrier; the
     // first atomics follow the second)
     if (b == 0)
-        for (int i = threadIdx.x; i < 3 * FX_COLS * FX_LIMBS; i += PT) a.acc[i] = 0ull;
+        for (int i = threadIdx.x; i < 3 * FX_SET; i += PT) a.acc[i] = 0ull;
     // gamma = ||v||
     for (int u = threadIdx.x; u < ne; u += PT) ws[u] = a.v[lo + u];
     __syncthreads();
@@ -375,12 +389,12 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             // the correction's columns are dealt over the virtual lanes like
             // the matrix rows (sum independent of G)
             if (sloc) {
-                acc = gmv_accumulate<double, D, G, true>(ga, x, sloc[live ? u : 0], r, live, ncorr, h2,
+                acc = gmv_accumulate<double, D, G, 2>(ga, x, sloc[live ? u : 0], r, live, ncorr, h2,
                                                          Zl + (live ? u : 0), zld);
             } else {
                 GmvLoc<D> l1;
                 if (live) gmv_locate<double, D, KP1>(ga, lo + u, l1);
-                acc = gmv_accumulate<double, D, G, true>(ga, x, l1, r, live, ncorr, h2, Zl + (live ? u : 0), zld);
+                acc = gmv_accumulate<double, D, G, 2>(ga, x, l1, r, live, ncorr, h2, Zl + (live ? u : 0), zld);
             }
             if (live && r == 0) {
                 acc *= scale;

@@ -98,9 +98,12 @@ __device__ __forceinline__ void gmv_locate(const GmvArgs<T, D>& a, int64_t g, Gm
 // sum_c h_c z_c whose columns are dealt the same way, and the 8 virtual sums
 // are added in one fixed binary tree -- physical lanes hold 8/G virtual
 // lanes, the lower tree levels are shuffles, the upper ones local.  The
-// result is returned in every lane of the group.  CG selects L2-only loads
-// of x, for vectors written by other CTAs of the same (persistent) kernel.
-template <typename T, int D, int G, bool CG>
+// result is returned in every lane of the group.  LD selects the loads of
+// x: 0 plain (read-only for the kernel), 1 L2 only, 2 cached in L1 through
+// the coherent path (for vectors written by other CTAs of the same
+// persistent kernel and published by a barrier whose acquire made L1
+// current).
+template <typename T, int D, int G, int LD>
 __device__ __forceinline__ T gmv_accumulate(const GmvArgs<T, D>& a, const T* __restrict__ x, const GmvLoc<D>& L,
                                             int r, bool live, int ncorr = 0, const T* hc = nullptr,
                                             const T* zc = nullptr, int64_t zld = 0) {
@@ -122,7 +125,8 @@ __device__ __forceinline__ T gmv_accumulate(const GmvArgs<T, D>& a, const T* __r
                     const int lb = pk >> 16, p = pk & 0xffff;
                     const int64_t ob = lb ? (oI << (lb - 1)) : oI;
                     const T* px = x + base[lb] + ob + (int64_t)p * I + in;
-                    if constexpr (CG) return __ldcg(px);
+                    if constexpr (LD == 1) return __ldcg(px);
+                    else if constexpr (LD == 2) return __ldca(px);
                     else return *px;
                 };
                 const int qe = L.qe[i];

@@ -314,8 +314,9 @@ void build_gmv_tables(sgk_op* op);
 // Boundaries of nb contiguous slices of the coefficient vector with about
 // equal work for the persistent Arnoldi kernel: per coefficient its matvec
 // entries (all directions) plus 2 extra for the Gram-Schmidt passes
-// (extra = 2 M).  bounds[0] = 0, bounds[nb] = dof, non-decreasing.
-std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra);
+// (extra = 2 M); no slice but the last is longer than cap (the caller checks
+// the last).  bounds[0] = 0, bounds[nb] = dof, non-decreasing.
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap);
 long long tuple_rank(const std::vector<int>& l, int n);
 
 template <typename T>

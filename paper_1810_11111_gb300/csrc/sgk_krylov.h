@@ -53,6 +53,8 @@ int arnoldi_persistent_ctas(const sgk_ctx* ctx);
 // this context's device.
 int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx);
 size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M);
+// Outputs one pass of the persistent kernel's matvec covers at 8 lanes each.
+int arnoldi_outputs_per_pass();
 // gamma, V (M + 1 columns), H and m_eff of the Krylov space of v, in one
 // cooperative launch.
 void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,

@@ -769,11 +769,17 @@ void solver_alloc(sgk_solver* s) {
         s->pbuf.alloc(arnoldi_persistent_pbuf_size(s->ctx, M));
         s->pbar.alloc(2 * S);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
-        // slices of about equal work (the species share one index set)
-        const std::vector<int64_t> bnd = arnoldi_slice_bounds(s->ops[0], arnoldi_persistent_ctas(s->ctx), 2 * M);
+        // slices of about equal work (the species share one index set), none
+        // needing more matvec passes than equal slices do: a pass is the
+        // CTA's outputs at 8 lanes each, and the slowest CTA sets the pace
+        const int nbp = arnoldi_persistent_ctas(s->ctx);
+        const int64_t per = arnoldi_outputs_per_pass();
+        const int64_t cap = ((n + nbp - 1) / nbp + per - 1) / per * per;
+        const std::vector<int64_t> bnd = arnoldi_slice_bounds(s->ops[0], nbp, 2 * M, cap);
         int64_t longest = 1;
         for (size_t i = 0; i + 1 < bnd.size(); ++i) longest = std::max<int64_t>(longest, bnd[i + 1] - bnd[i]);
-        if (longest <= 24 * 1024) {  // else equal slices (the kernel stages a slice in shared memory)
+        // else equal slices (the kernel stages a slice in shared memory)
+        if (longest <= cap && longest <= 24 * 1024) {
             s->aE = longest;
             s->abounds.upload(bnd, s->ctx->stream);
         }
