@@ -226,7 +226,11 @@ int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, 
 /* w = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v for species s (eqs.
  * krylov7-krylov8, Arnoldi with classical Gram-Schmidt applied twice).
  * m_eff (host, may be NULL) receives the Krylov dimension used.
- * Synchronises when m_eff is not NULL. */
+ * Synchronises.  SGK_ETIMEOUT: a grid barrier of the persistent Arnoldi
+ * kernel ran out of time (w is then undefined; the solver stays usable).
+ * Setting the environment variable SGK_TEST_BARRIER_STALL makes those
+ * barriers wait for one CTA more than the grid has, so that the bounded
+ * waits run out (failure test). */
 int sgk_krylov_expv(sgk_solver* s, int species, const double* v_dev, double* w_dev, int* m_eff);
 /* Copy the Hessenberg matrix ((M+1) x M, row-major) and the Krylov basis
  * (M+1 columns of dof, column-major, FP64) of the last sgk_krylov_expv call

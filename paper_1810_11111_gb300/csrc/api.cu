@@ -482,11 +482,18 @@ int sgk_krylov_expv(sgk_solver* s, int species, const double* v_dev, double* w_d
         SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
         set_device(s->ctx);
         solver_krylov_expv(s, species, v_dev, w_dev);
-        if (m_eff) {
-            KrylovScalars ks;
-            SGK_CUDA_CHECK(cudaMemcpyAsync(&ks, s->ks.p + species, sizeof(ks), cudaMemcpyDeviceToHost, s->ctx->stream));
+        KrylovScalars ks{};
+        unsigned flags[2] = {0u, 0u};
+        SGK_CUDA_CHECK(cudaMemcpyAsync(&ks, s->ks.p + species, sizeof(ks), cudaMemcpyDeviceToHost, s->ctx->stream));
+        if (s->persistent)
+            SGK_CUDA_CHECK(cudaMemcpyAsync(flags, s->pbar.p + 2 * species, sizeof(flags), cudaMemcpyDeviceToHost,
+                                           s->ctx->stream));
+        SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
+        if (m_eff) *m_eff = ks.m_eff;
+        if (flags[1] != 0u) {  // a grid barrier of the persistent kernel ran out of time
+            SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p + 2 * species, 0, 2 * sizeof(unsigned), s->ctx->stream));
             SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
-            *m_eff = ks.m_eff;
+            throw SgkError{SGK_ETIMEOUT, "persistent Arnoldi: a grid barrier wait ran out"};
         }
         return SGK_OK;
     });

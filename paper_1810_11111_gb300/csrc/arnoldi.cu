@@ -25,6 +25,7 @@
 // other CTA sees the flag in its own wait and returns too; the host reports
 // SGK_ETIMEOUT.  The cooperative launch makes every CTA resident at once.
 #include <cmath>
+#include <cstdlib>
 
 #include "sgk_arnoldi.cuh"
 
@@ -107,6 +108,10 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
         a.isc_n = std::ldexp(1.0, 2 * e - 110);
     }
     a.bar = pw.bar;
+    // failure injection on the host: with SGK_TEST_BARRIER_STALL set, every
+    // barrier waits for one arrival more than the grid has, so the bounded
+    // waits run out and the launch ends with the error flag set
+    a.bar_extra = std::getenv("SGK_TEST_BARRIER_STALL") ? 1u : 0u;
     a.ks = kw.ks;
     a.bounds = pw.bounds;
     // shared memory: the slice of w always; the slices of V and Z (all

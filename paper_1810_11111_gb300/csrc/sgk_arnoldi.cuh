@@ -11,7 +11,7 @@ namespace sgk_arn {
 
 constexpr int PT = 512;                        // threads per CTA, one CTA per SM
 constexpr int PNW = PT / 32;                   // warps per CTA
-constexpr unsigned BAR_SPIN_LIMIT = 1u << 21;  // polls of ~0.1-0.5 us each
+constexpr unsigned BAR_SPIN_LIMIT = 1u << 21;  // polls (an L2 round trip each, ~0.2-0.5 us): about a second
 
 struct ArnArgs {
     int64_t n;
@@ -32,6 +32,7 @@ struct ArnArgs {
     // V^T w (|p| <= ||A||), _n for ||w'||^2 (|p| <= ||A||^2)
     double sc_h, isc_h, sc_n, isc_n;
     unsigned* bar;  // [0] barrier arrivals (zero at launch), [1] error flag
+    unsigned bar_extra;  // added to every barrier target: 0, or 1 to make the waits run out (failure test)
     KrylovScalars* ks;
     const int64_t* bounds;  // slice b = [bounds[b], bounds[b+1]) (work-balanced), or null: equal slices of E
 };
@@ -58,23 +59,34 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // All CTAs arrive; returns false if the wait ran out or another CTA failed.
+// Thread 0 arrives with a release add (cumulative over the CTA's writes,
+// which the CTA barrier before it orders) and polls with acquire loads,
+// whose acquire the CTA barrier after it passes on to every thread; the
+// error flag is looked at every 256 polls.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        red_release_add(bar, 1u);
         int ok = 1;
         for (unsigned it = 0;; ++it) {
             if (ld_acquire(bar) >= target) break;
-            if (it >= BAR_SPIN_LIMIT || ld_acquire(bar + 1) != 0u) {
+            if ((it & 255u) == 255u && (it >= BAR_SPIN_LIMIT || ld_relaxed(bar + 1) != 0u)) {
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
         }
         if (!ok) atomicExch(bar + 1, 1u);
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     unsigned epoch = 0;
     auto barrier = [&]() {
         ++epoch;
-        return grid_barrier(a.bar, epoch * (unsigned)nb, &s_ok);
+        return grid_barrier(a.bar, epoch * (unsigned)nb + a.bar_extra, &s_ok);
     };
     // fixed-point reductions: phase p adds into set p % 3, read after its
     // barrier; after the barrier of phase p every CTA is done reading set
@@ -318,17 +330,21 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             fx_red(set + (size_t)threadIdx.x * FX_LIMBS, sdot[threadIdx.x], nc_col ? a.sc_n : a.sc_h);
         }
     };
+    // after reading phase p: CTA 0 clears set (p + 2) % 3, next phase
+    auto fx_done = [&]() {
+        if (b == 0) {
+            unsigned long long* old = fx_set(fx_phase + 2u);
+            for (int i = threadIdx.x; i < FX_SET; i += PT) old[i] = 0ull;
+        }
+        ++fx_phase;
+    };
     auto fx_read = [&](int nt, bool norm, double* out) {
         const unsigned long long* set = fx_set(fx_phase);
         if ((int)threadIdx.x < nt) {
             const bool nc_col = norm && (int)threadIdx.x == nt - 1;
             out[threadIdx.x] = fx_value(set + (size_t)threadIdx.x * FX_LIMBS, nc_col ? a.isc_n : a.isc_h);
         }
-        if (b == 0) {
-            unsigned long long* old = fx_set(fx_phase + 2u);
-            for (int i = threadIdx.x; i < FX_SET; i += PT) old[i] = 0ull;
-        }
-        ++fx_phase;
+        fx_done();
     };
     const int r = threadIdx.x & (G - 1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -415,43 +431,10 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         slice_dots(Vl, vld, nc, ws, ne, sdot, true, ctmp, ctmp2);
         fx_publish(nc + 1, true);
         if (!barrier()) return;
-        fx_read(nc + 1, true, h2);
-        __syncthreads();
-        // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal, w'' = w' - V h2);
-        // when the second pass removed more than 1e-3 of ||w'||^2 (near
-        // breakdown) the norm is summed explicitly instead
-        if (wid == 0) {
-            double part = 0.0, hh = 0.0;
-            for (int i = lane; i < nc; i += 32) {
-                const double hv = h1[i] + h2[i];
-                part += hv * hv;
-                hh += h2[i] * h2[i];
-            }
-            part = warp_sum(part);
-            hh = warp_sum(hh);
-            const double wn2 = h2[nc];
-            const double b2 = wn2 - hh;
-            if (lane == 0) {
-                s_flag = !(hh <= 1e-3 * wn2) || !(b2 > 0.0);
-                s_scal[0] = b2;
-                s_scal[2] = part;
-            }
-        }
-        __syncthreads();
-        const bool explicit_norm = s_flag != 0;
-        if (explicit_norm) {
-            // w'' in place (published), its norm through a third barrier
-            slice_update(Vl, vld, nc, h2, w, ws, lo, ne, nullptr, nullptr, 0.0);
-            __syncthreads();
-            slice_norm2(ws, ne, red, P2 + b);
-            if (!barrier()) return;
-            colsum(P2, nb, 1, s_scal, ctmp);
-            __syncthreads();
-        }
-        // column j of H and the breakdown test: warp 0 of every CTA, alike
-        if (wid == 0) {
-            const double b2 = s_scal[0];
-            const double f = fro2 + sub * sub + s_scal[2];
+        // column j of H and the breakdown test from ||w''||^2 = b2 and
+        // part = ||h1 + h2||^2: warp 0 of every CTA, every lane alike
+        auto hcol = [&](double b2, double part) {
+            const double f = fro2 + sub * sub + part;
             // one reciprocal square root on two lanes: 1/beta and sqrt(f)
             const double xin = lane == 0 ? b2 : f;
             const double rs = xin > 0.0 ? rsqrt(xin) : 0.0;
@@ -475,8 +458,61 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
                     }
                 }
             }
+        };
+        // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal, w'' = w' - V h2);
+        // when the second pass removed more than 1e-3 of ||w'||^2 (near
+        // breakdown) the norm is summed explicitly instead.  With at most 32
+        // columns warp 0 reads h2 itself and, in the common case, finishes
+        // the column at once: one CTA barrier for the whole scalar part
+        auto pyth = [&](double part, double hh, double wn2) {
+            const double b2 = wn2 - hh;
+            const bool flag = !(hh <= 1e-3 * wn2) || !(b2 > 0.0);
+            if (lane == 0) {
+                s_flag = flag;
+                s_scal[0] = b2;
+                s_scal[2] = part;
+            }
+            if (!flag) hcol(b2, part);
+        };
+        if (nc + 1 <= 32) {
+            if (wid == 0) {
+                const unsigned long long* set = fx_set(fx_phase);
+                const double hv2 =
+                    lane <= nc ? fx_value(set + (size_t)lane * FX_LIMBS, lane == nc ? a.isc_n : a.isc_h) : 0.0;
+                if (lane <= nc) h2[lane] = hv2;
+                __syncwarp();
+                const double hv = lane < nc ? h1[lane] + hv2 : 0.0;
+                const double part = warp_sum(hv * hv);
+                const double hh = warp_sum(lane < nc ? hv2 * hv2 : 0.0);
+                pyth(part, hh, __shfl_sync(0xffffffffu, hv2, nc));
+            }
+            fx_done();
+        } else {
+            fx_read(nc + 1, true, h2);
+            __syncthreads();
+            if (wid == 0) {
+                double part = 0.0, hh = 0.0;
+                for (int i = lane; i < nc; i += 32) {
+                    const double hv = h1[i] + h2[i];
+                    part += hv * hv;
+                    hh += h2[i] * h2[i];
+                }
+                pyth(warp_sum(part), warp_sum(hh), h2[nc]);
+            }
         }
         __syncthreads();
+        const bool explicit_norm = s_flag != 0;
+        if (explicit_norm) {
+            // w'' in place (published), its norm through a third barrier
+            slice_update(Vl, vld, nc, h2, w, ws, lo, ne, nullptr, nullptr, 0.0);
+            __syncthreads();
+            slice_norm2(ws, ne, red, P2 + b);
+            if (!barrier()) return;
+            colsum(P2, nb, 1, s_scal, ctmp);
+            __syncthreads();
+            if (wid == 0) hcol(s_scal[0], s_scal[2]);
+            __syncthreads();
+        }
         if (!(s_scal[1] > 0.0)) return;  // breakdown: the same decision in every CTA
         scale = s_scal[1];
         double* vg = a.V + (int64_t)(j + 1) * n + lo;

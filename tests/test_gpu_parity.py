@@ -266,6 +266,33 @@ def test_krylov_persistent_matches_launch_sequence(ctx64, d, n, k, M, monkeypatc
     idx.close()
 
 
+def test_persistent_barrier_timeout_is_reported(ctx64, monkeypatch):
+    # failure injected on the host: every grid barrier of the persistent
+    # Arnoldi kernel waits for one CTA more than the grid has, so the bounded
+    # waits run out (about a second); the call reports SGK_ETIMEOUT, and the
+    # next call on the same solver runs normally
+    d, n, k, M = 2, 4, 1, 10
+    kap = [1.0, 0.5]
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    op = sgkiif.Operator(ctx64, idx, kap)
+    sol = sgkiif.Solver(ctx64, [op], [[]], M, 0.01)
+    v = np.random.default_rng(9).standard_normal(idx.dof)
+    vd = dev(v)
+    wd = torch.empty_like(vd)
+    monkeypatch.setenv("SGK_TEST_BARRIER_STALL", "1")
+    with pytest.raises(sgkiif.SgkError) as err:
+        sol.krylov_expv(0, vd.data_ptr(), wd.data_ptr())
+    assert err.value.code == sgkiif.SGK_ETIMEOUT
+    monkeypatch.delenv("SGK_TEST_BARRIER_STALL")
+    m_eff = sol.krylov_expv(0, vd.data_ptr(), wd.data_ptr())
+    want, m_ref = krylov_expv(lambda x: sparse_matvec(OIndex(d, n, k), sipg_1d(n, k), kap, x), v, 0.01, M)
+    assert m_eff == m_ref
+    assert rel(wd.cpu().numpy(), want) <= 1e-10
+    sol.close()
+    op.close()
+    idx.close()
+
+
 def test_krylov_breakdown_constant_mode(ctx64):
     idx = sgkiif.IndexSet(ctx64, 3, 3, 2)
     op = sgkiif.Operator(ctx64, idx, [1.0, 1.0, 1.0])
