@@ -127,10 +127,14 @@ def layout_sizes(d, n, k):
     return [H ** i * sparse_dof(d - i) for i in range(d + 1)]
 
 
-# DRAM bytes (read + write) of one Jacobian launch of the pencil kernel from
-# the committed ncu capture of the current kernel, keyed by (d, level,
-# degree, precision); empty until a capture of this kernel version exists
-PENCIL_TRAFFIC = {}
+# DRAM bytes (read + write) of one launch from the committed ncu captures of
+# the current kernels (cold, L2 flushed by ncu before the launch); a key is
+# removed when the kernel changes.  Jacobian pencil launch, keyed by (d,
+# level, degree, precision): profiles/pencil_kernel_cubic3d_l6k2_fp32.md
+PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56661504 + 68608}
+# one persistent Arnoldi launch (one exponential), keyed by (d, level,
+# degree, M): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md
+ARNOLDI_TRAFFIC = {(3, 6, 2, 30): 6492160 + 83712}
 
 
 def pencil_q(cfg):
@@ -329,7 +333,10 @@ def native(args, rank, world, local_rank):
                             hbm_view={"achieved_gbs": nl * bytes_algo / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
                                       "frac": nl * bytes_algo / t / 1e9 / peaks["hbm_gbs"],
                                       "peak_source": peak_kind},
-                            traffic=None)
+                            traffic=ARNOLDI_TRAFFIC.get((d, N, cfg["k"], cfg["M"])),
+                            traffic_note="dram read + write of one launch, ncu cold capture "
+                                         "(profiles/arnoldi_kernel_cubic3d_l6k2_m30.md); null when no capture "
+                                         "of the current kernel exists")
         elif flops_algo:
             clock = (clk or {}).get("sm_max_mhz") or 2070.0
             peak = 152 * 128 * 2 * clock * 1e6 / 1e12

@@ -59,7 +59,40 @@ size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) {
     return (size_t)ctx->num_sms + 3 * sgk_arn::FX_SET;
 }
 
-int arnoldi_outputs_per_pass() { return PT / 8; }
+static size_t smem_budget(const sgk_ctx* ctx) {
+    // the kernel's static shared memory stays below 12 KB
+    return ctx->smem_optin > 16 * 1024 ? ctx->smem_optin - 12 * 1024 : 32 * 1024;
+}
+
+std::vector<int64_t> arnoldi_balanced_bounds(const sgk_ctx* ctx, const sgk_op* op, int M, int64_t* E,
+                                             int64_t* list_ent) {
+    const int nb = persistent_ctas(ctx);
+    const int64_t n = op->idx->dof;
+    const int d = op->idx->d;
+    const int64_t per = PT / 8;  // outputs of one matvec pass at 8 lanes each
+    // no more matvec passes than equal slices need (a pass costs about as
+    // much as 8 K gather entries)
+    const int64_t cap_len = std::min<int64_t>(((n + nb - 1) / nb + per - 1) / per * per, 24 * 1024);
+    // shared memory left for the entries with the longest slice's w, V, Z
+    // and entry offsets staged
+    const size_t fixed = sizeof(double) * ((size_t)cap_len + 2 * (size_t)(M + 1) * (size_t)(cap_len | 1)) +
+                         sgk_arn::arn_eoff_bytes((int)cap_len, d);
+    const size_t budget = smem_budget(ctx);
+    int64_t cap_ent = (op->gmv_ecnt_host.empty() || fixed >= budget) ? (int64_t(1) << 40)
+                                                                      : (int64_t)((budget - fixed) / sizeof(int2));
+    std::vector<int64_t> b = arnoldi_slice_bounds(op, nb, 2 * M, cap_len, cap_ent);
+    *E = 0;
+    *list_ent = 0;
+    for (size_t i = 0; i + 1 < b.size(); ++i) {
+        *E = std::max<int64_t>(*E, b[i + 1] - b[i]);
+        if (!op->gmv_ecnt_host.empty()) {
+            int64_t e = 0;
+            for (int64_t g = b[i]; g < b[i + 1]; ++g) e += op->gmv_ecnt_host[g];
+            *list_ent = std::max(*list_ent, e);
+        }
+    }
+    return b;
+}
 
 static size_t loc_bytes(int d) {
     switch (d) {
@@ -115,17 +148,40 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     a.ks = kw.ks;
     a.bounds = pw.bounds;
     // shared memory: the slice of w always; the slices of V and Z (all
-    // M + 1 columns) and the located rows of the slice's outputs when they
-    // fit, which turns the Gram-Schmidt and correction loads into shared
-    // loads (global stores do not allocate in L1)
-    const size_t budget = ctx->smem_optin > 16 * 1024 ? ctx->smem_optin - 12 * 1024 : 32 * 1024;
-    size_t smem = sizeof(double) * (size_t)E;
-    const size_t vz = sizeof(double) * 2 * (size_t)(M + 1) * E;
-    const size_t lb = loc_bytes(op->idx->d) * (size_t)E;
-    a.smem_vz = smem + vz <= budget;
-    if (a.smem_vz) smem += vz;
-    a.smem_loc = smem + lb <= budget;
-    if (a.smem_loc) smem += lb;
+    // M + 1 columns) and the slice's pre-located gathers (else the located
+    // rows of its outputs) when they fit, which turns the Gram-Schmidt,
+    // correction and gather-address loads into shared loads (an acquire at a
+    // grid barrier empties L1)
+    const int d = op->idx->d;
+    int64_t list_ent = pw.bounds ? pw.list_ent : 0;
+    if (!pw.bounds && !op->gmv_ecnt_host.empty())
+        for (int bb = 0; bb < nb; ++bb) {
+            int64_t e = 0;
+            for (int64_t g = std::min<int64_t>(n, bb * E); g < std::min<int64_t>(n, (bb + 1) * E); ++g)
+                e += op->gmv_ecnt_host[g];
+            list_ent = std::max(list_ent, e);
+        }
+    const bool has_list = !op->gmv_ecnt_host.empty() && op->gmv_ent.p != nullptr;
+    const size_t budget = smem_budget(ctx);
+    const size_t ws = sizeof(double) * (size_t)E;
+    const size_t vz = sizeof(double) * 2 * (size_t)(M + 1) * (size_t)(E | 1);  // odd column stride
+    const size_t lb = loc_bytes(d) * (size_t)E;
+    const size_t lst = sgk_arn::arn_eoff_bytes((int)E, d) + sizeof(int2) * (size_t)std::max<int64_t>(list_ent, 1);
+    a.eoff = has_list ? op->gmv_eoff.p : nullptr;
+    a.ent = has_list ? op->gmv_ent.p : nullptr;
+    a.smem_vz = 0;
+    a.smem_loc = 0;
+    a.list_cap = 0;
+    if (has_list && ws + vz + lst <= budget) {
+        a.smem_vz = 1;
+        a.list_cap = (int)std::max<int64_t>(list_ent, 1);
+    } else if (has_list && ws + lst <= budget) {
+        a.list_cap = (int)std::max<int64_t>(list_ent, 1);
+    } else {
+        a.smem_vz = ws + vz <= budget;
+        a.smem_loc = ws + (a.smem_vz ? vz : 0) + lb <= budget;
+    }
+    const size_t smem = ws + (a.smem_vz ? vz : 0) + (a.list_cap ? lst : 0) + (a.smem_loc ? lb : 0);
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaMemsetAsync(pw.bar, 0, sizeof(unsigned), ctx->stream));
     switch (op->idx->d) {

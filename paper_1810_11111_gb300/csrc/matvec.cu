@@ -154,6 +154,60 @@ void build_gmv_tables(sgk_op* op) {
             cvk[i * nnz + q] = -op->kappa[i] * S.val[q];
             cvkf[i * nnz + q] = (float)cvk[i * nnz + q];
         }
+    // pre-located gathers: the host mirror of gmv_locate and of the address
+    // formed per entry in gmv_accumulate
+    op->gmv_ecnt_host.clear();
+    std::vector<int32_t> eoff;  // alive until the stream synchronisation below
+    std::vector<int2> ent;
+    if (madds <= GMV_LIST_MAX && idx->dof * d < (int64_t(1) << 31) && (int64_t)nnz * d < (int64_t(1) << 31)) {
+        eoff.resize((size_t)idx->dof * d + 1);
+        ent.reserve((size_t)madds);
+        op->gmv_ecnt_host.resize(idx->dof);
+        for (int64_t t = 0; t < idx->ntuples; ++t) {
+            const int32_t* lv = &idx->levels[t * d];
+            int sum = 0;
+            std::vector<int> sh(d), cnt(d), c(d);
+            for (int m = 0; m < d; ++m) {
+                sum += lv[m];
+                sh[m] = lv[m] > 0 ? lv[m] - 1 : 0;
+                cnt[m] = kp1 << sh[m];
+            }
+            for (int64_t g = idx->offsets[t]; g < idx->offsets[t + 1]; ++g) {
+                int64_t e = g - idx->offsets[t];
+                for (int m = d - 1; m >= 0; --m) {
+                    const int64_t q = (e >> sh[m]) / kp1;
+                    c[m] = (int)(e - q * cnt[m]);
+                    e = q;
+                }
+                const size_t first = ent.size();
+                for (int i = 0; i < d; ++i) {
+                    eoff[(size_t)g * d + i] = (int32_t)ent.size();
+                    int64_t o = 0, in = 0, I = 1;
+                    for (int m = 0; m < i; ++m) o = o * cnt[m] + c[m];
+                    for (int m = d - 1; m > i; --m) {
+                        in += (int64_t)c[m] * I;
+                        I *= cnt[m];
+                    }
+                    const int np = N - (sum - lv[i]);
+                    const int ai = (lv[i] ? (kp1 << (lv[i] - 1)) : 0) + c[i];
+                    const int q0 = S.ptr[ai], qe = q0 + rl[(size_t)ai * nl + np];
+                    const int64_t oI = o * I * kp1;
+                    for (int q = q0; q < qe; ++q) {
+                        const int lb = ce[q] >> 16, pp = ce[q] & 0xffff;
+                        const int64_t ob = lb ? (oI << (lb - 1)) : oI;
+                        const int64_t xi = cb[((size_t)t * d + i) * nl + lb] + ob + (int64_t)pp * I + in;
+                        SGK_REQUIRE(xi >= 0 && xi < idx->dof, SGK_EINVAL, "matvec: gather outside x");
+                        ent.push_back(make_int2((int)xi, (int)((int64_t)i * nnz + q)));
+                    }
+                }
+                op->gmv_ecnt_host[g] = (int32_t)(ent.size() - first);
+            }
+        }
+        eoff[(size_t)idx->dof * d] = (int32_t)ent.size();
+        SGK_REQUIRE((int64_t)ent.size() == madds, SGK_EINVAL, "matvec: entry list size mismatch");
+        op->gmv_eoff.upload(eoff, op->ctx->stream);
+        op->gmv_ent.upload(ent, op->ctx->stream);
+    }
     op->gmv_cvk.upload(cvk, op->ctx->stream);
     op->gmv_cvkf.upload(cvkf, op->ctx->stream);
     op->gmv_ce.upload(ce, op->ctx->stream);
@@ -162,58 +216,70 @@ void build_gmv_tables(sgk_op* op) {
     SGK_CUDA_CHECK(cudaStreamSynchronize(op->ctx->stream));
 }
 
-std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap) {
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap_len, int64_t cap_ent) {
     const sgk_index* idx = op->idx;
     const int d = idx->d, N = idx->n, kp1 = idx->k + 1, nl = N + 1;
-    const std::vector<int>& rl = op->rlen_host;
-    // per tuple and direction the row lengths f_i(c) of its positions
-    auto fill = [&](const int32_t* l, std::vector<std::vector<int>>& f, std::vector<int>& cnt) {
-        int sum = 0;
-        for (int m = 0; m < d; ++m) sum += l[m];
-        f.assign(d, {});
-        cnt.assign(d, 0);
-        for (int i = 0; i < d; ++i) {
-            cnt[i] = level_count(l[i], kp1);
-            const int np = N - (sum - l[i]);
-            f[i].resize(cnt[i]);
-            for (int c = 0; c < cnt[i]; ++c) f[i][c] = rl[(size_t)(level_offset(l[i], kp1) + c) * nl + np];
-        }
-    };
-    std::vector<std::vector<int>> f;
-    std::vector<int> cnt;
-    double total = 0.0;
-    for (int64_t t = 0; t < idx->ntuples; ++t) {
-        fill(&idx->levels[t * d], f, cnt);
-        const int64_t blk = idx->offsets[t + 1] - idx->offsets[t];
-        for (int i = 0; i < d; ++i) {
-            int64_t s = 0;
-            for (int v : f[i]) s += v;
-            total += (double)s * (double)(blk / cnt[i]);
-        }
-        total += (double)extra * blk;
-    }
-    std::vector<int64_t> b(nb + 1, idx->dof);
-    b[0] = 0;
-    int k = 1;
-    double cum = 0.0;
-    std::vector<int> c(d);
-    for (int64_t t = 0; t < idx->ntuples && k < nb; ++t) {
-        fill(&idx->levels[t * d], f, cnt);
-        std::fill(c.begin(), c.end(), 0);
-        for (int64_t g = idx->offsets[t]; g < idx->offsets[t + 1] && k < nb; ++g) {
-            int cost = extra;
-            for (int i = 0; i < d; ++i) cost += f[i][c[i]];
-            cum += cost;
-            // cut at the next equal share of the work, or where the slice
-            // reaches cap coefficients
-            if (g + 1 - b[k - 1] >= cap) b[k++] = g + 1;
-            while (k < nb && cum >= total * k / nb) b[k++] = g + 1;
-            for (int m = d - 1; m >= 0; --m) {  // row-major odometer, last direction fastest
-                if (++c[m] < cnt[m]) break;
-                c[m] = 0;
+    const int64_t n = idx->dof;
+    // entries of every output (the per-output matvec work)
+    std::vector<int32_t> ecnt = op->gmv_ecnt_host;
+    if ((int64_t)ecnt.size() != n) {
+        const std::vector<int>& rl = op->rlen_host;
+        ecnt.assign(n, 0);
+        std::vector<int> c(d), sh(d), cnt(d);
+        for (int64_t t = 0; t < idx->ntuples; ++t) {
+            const int32_t* lv = &idx->levels[t * d];
+            int sum = 0;
+            for (int m = 0; m < d; ++m) {
+                sum += lv[m];
+                sh[m] = lv[m] > 0 ? lv[m] - 1 : 0;
+                cnt[m] = kp1 << sh[m];
+            }
+            std::fill(c.begin(), c.end(), 0);
+            for (int64_t g = idx->offsets[t]; g < idx->offsets[t + 1]; ++g) {
+                int e = 0;
+                for (int i = 0; i < d; ++i)
+                    e += rl[(size_t)((lv[i] ? (kp1 << (lv[i] - 1)) : 0) + c[i]) * nl + N - (sum - lv[i])];
+                ecnt[g] = e;
+                for (int m = d - 1; m >= 0; --m) {  // row-major odometer, last direction fastest
+                    if (++c[m] < cnt[m]) break;
+                    c[m] = 0;
+                }
             }
         }
     }
+    // contiguous slices minimising the largest cost (entries + extra per
+    // output) under the caps: the greedy cut is optimal for a given bound,
+    // and the least feasible bound is found by bisection
+    auto fits = [&](int64_t C, std::vector<int64_t>* out) {
+        int k = 0;
+        int64_t cc = 0, cl = 0, ce = 0;
+        if (out) (*out)[0] = 0;
+        for (int64_t g = 0; g < n; ++g) {
+            const int64_t w = ecnt[g] + extra;
+            if (ecnt[g] > cap_ent || w > C) return false;
+            if (cl > 0 && (cc + w > C || cl + 1 > cap_len || ce + ecnt[g] > cap_ent)) {
+                if (++k >= nb) return false;
+                if (out) (*out)[k] = g;
+                cc = cl = ce = 0;
+            }
+            cc += w;
+            ++cl;
+            ce += ecnt[g];
+        }
+        if (out)
+            for (int j = k + 1; j <= nb; ++j) (*out)[j] = n;
+        return true;
+    };
+    int64_t lo = 0, hi = 0;
+    for (int64_t g = 0; g < n; ++g) hi += ecnt[g] + extra;
+    if (n == 0 || !fits(hi, nullptr)) return {};
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (fits(mid, nullptr)) hi = mid;
+        else lo = mid;
+    }
+    std::vector<int64_t> b(nb + 1, n);
+    fits(hi, &b);
     return b;
 }
 

@@ -19,6 +19,9 @@ struct ArnArgs {
     int E;    // slice length per CTA (ceil(n / gridDim.x))
     int smem_vz;   // this CTA's slices of V and Z live in shared memory (and V also in HBM)
     int smem_loc;  // the located rows of every output of the slice live in shared memory
+    int list_cap;  // > 0: the slice's pre-located gather entries (at most list_cap) live in shared memory
+    const int* eoff;   // pre-located gathers (see sgk_op::gmv_eoff), or null
+    const int2* ent;
     const double* v;
     double* V;  // column c at V + c n
     double* w0;
@@ -44,14 +47,9 @@ constexpr int FX_LIMBS = 4;                   // three 56-bit limbs and a count 
 constexpr int FX_COPIES = 8;
 constexpr int FX_SET = FX_COPIES * FX_COLS * FX_LIMBS;  // words of one set
 
-// Dynamic shared memory of the kernel, in bytes.
-template <int D>
-size_t arn_smem_bytes(int E, int M, bool vz, bool loc) {
-    size_t b = sizeof(double) * (size_t)E;
-    if (vz) b += sizeof(double) * 2 * (size_t)(M + 1) * E;
-    if (loc) b += sizeof(GmvLoc<D>) * (size_t)E;
-    return b;
-}
+// Bytes of the staged entry offsets of a slice of E outputs (D per output
+// and one end), rounded up to 16.
+__host__ __device__ inline size_t arn_eoff_bytes(int E, int d) { return ((sizeof(int) * ((size_t)E * d + 1)) + 15) / 16 * 16; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -284,7 +282,7 @@ __device__ __forceinline__ void slice_norm2(const double* ws, int ne, double* re
 
 template <int D, int KP1, int G>
 __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
-    // dynamic shared memory: [ws: E][Vs: (M+1) E][Zs: (M+1) E][loc: E]
+    // dynamic shared memory: [ws: E][Vs: (M+1) Es][Zs: (M+1) Es][located rows, or gather offsets and entries]
     extern __shared__ __align__(16) double smem[];
     __shared__ double h1[SGK_MAX_KRYLOV + 2];
     __shared__ double h2[SGK_MAX_KRYLOV + 2];
@@ -301,15 +299,22 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     const int64_t lo = a.bounds ? a.bounds[b] : std::min<int64_t>(n, (int64_t)b * E);
     const int ne = (int)((a.bounds ? a.bounds[b + 1] : std::min<int64_t>(n, lo + E)) - lo);
     double* const ws = smem;
+    // shared columns of V and Z have an odd stride: the lanes of one output
+    // read different columns of Z at the same row without bank conflicts
+    const int Es = E | 1;
     double* const Vs = a.smem_vz ? smem + E : nullptr;
-    double* const Zs = a.smem_vz ? smem + E + (size_t)(a.M + 1) * E : nullptr;
-    GmvLoc<D>* const sloc =
-        a.smem_loc ? reinterpret_cast<GmvLoc<D>*>(smem + E + (a.smem_vz ? 2 * (size_t)(a.M + 1) * E : 0)) : nullptr;
+    double* const Zs = a.smem_vz ? smem + E + (size_t)(a.M + 1) * Es : nullptr;
+    unsigned char* const tail = reinterpret_cast<unsigned char*>(smem + E + (a.smem_vz ? 2 * (size_t)(a.M + 1) * Es : 0));
+    GmvLoc<D>* const sloc = a.smem_loc ? reinterpret_cast<GmvLoc<D>*>(tail) : nullptr;
+    // pre-located gathers of the slice: offsets rebased to the slice's first
+    // entry, then the entries
+    int* const seoff = a.list_cap > 0 ? reinterpret_cast<int*>(tail) : nullptr;
+    int2* const sent = a.list_cap > 0 ? reinterpret_cast<int2*>(tail + arn_eoff_bytes(E, D)) : nullptr;
     // this slice's basis and raw-output columns: shared copies or HBM
     const double* const Vl = a.smem_vz ? Vs : a.V + lo;
-    const int64_t vld = a.smem_vz ? E : n;
+    const int64_t vld = a.smem_vz ? Es : n;
     double* const Zl = a.smem_vz ? Zs : a.Z + lo;
-    const int64_t zld = a.smem_vz ? E : n;
+    const int64_t zld = a.smem_vz ? Es : n;
     double* const P2 = a.pbuf;  // norms
     unsigned epoch = 0;
     auto barrier = [&]() {
@@ -351,6 +356,15 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     KrylovScalars* ks = a.ks;
     if (sloc)
         for (int u = threadIdx.x; u < ne; u += PT) gmv_locate<double, D, KP1>(ga, lo + u, sloc[u]);
+    if (seoff) {
+        const int e0 = a.eoff[lo * D], ecount = a.eoff[(lo + ne) * D] - e0;
+        if (ecount > a.list_cap) {  // the host sized the list for every slice; fail rather than overrun
+            if (threadIdx.x == 0) atomicExch(a.bar + 1, 1u);
+            return;
+        }
+        for (int i = threadIdx.x; i <= ne * D; i += PT) seoff[i] = a.eoff[lo * D + i] - e0;
+        for (int i = threadIdx.x; i < ecount; i += PT) sent[i] = a.ent[e0 + i];
+    }
 
     // the accumulator sets start cleared (before the first barrier; the
     // first atomics follow the second)
@@ -404,7 +418,10 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             double acc;
             // the correction's columns are dealt over the virtual lanes like
             // the matrix rows (sum independent of G)
-            if (sloc) {
+            if (seoff) {
+                acc = gmv_accumulate_list<D, G>(seoff + (live ? u : 0) * D, sent, ga.cvk, x, r, live, ncorr, h2,
+                                                Zl + (live ? u : 0), zld);
+            } else if (sloc) {
                 acc = gmv_accumulate<double, D, G, 2>(ga, x, sloc[live ? u : 0], r, live, ncorr, h2,
                                                          Zl + (live ? u : 0), zld);
             } else {
@@ -516,7 +533,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         if (!(s_scal[1] > 0.0)) return;  // breakdown: the same decision in every CTA
         scale = s_scal[1];
         double* vg = a.V + (int64_t)(j + 1) * n + lo;
-        double* vs = Vs ? Vs + (int64_t)(j + 1) * E : nullptr;
+        double* vs = Vs ? Vs + (int64_t)(j + 1) * Es : nullptr;
         if (explicit_norm) {
             for (int u = threadIdx.x; u < ne; u += PT) {
                 const double y = ws[u] * scale;

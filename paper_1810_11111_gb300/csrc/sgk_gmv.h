@@ -156,6 +156,56 @@ __device__ __forceinline__ T gmv_accumulate(const GmvArgs<T, D>& a, const T* __r
     return b[0];
 }
 
+// The same sum from a pre-located entry list (shared memory): eo[i] ..
+// eo[i + 1] are direction i's entries {index of x, index into cvk} of this
+// output in row order, dealt to the virtual lanes exactly as above, so the
+// result is bitwise that of gmv_accumulate.  x is read through L1 on the
+// coherent path (written by other CTAs, published by a barrier).
+template <int D, int G>
+__device__ __forceinline__ double gmv_accumulate_list(const int* eo, const int2* ent,
+                                                      const double* __restrict__ cvk, const double* x, int r,
+                                                      bool live, int ncorr, const double* hc, const double* zc,
+                                                      int64_t zld) {
+    constexpr int VL = 8, PER = VL / G;
+    double b[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) b[k] = 0.0;
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int v = r + k * G;
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int qe = eo[i + 1];
+                int q = eo[i] + v;
+#pragma unroll 2
+                for (; q + VL < qe; q += 2 * VL) {
+                    const int2 e0 = ent[q], e1 = ent[q + VL];
+                    s0 += __ldg(cvk + e0.y) * __ldca(x + e0.x);
+                    s1 += __ldg(cvk + e1.y) * __ldca(x + e1.x);
+                }
+                if (q < qe) {
+                    const int2 e0 = ent[q];
+                    s0 += __ldg(cvk + e0.y) * __ldca(x + e0.x);
+                }
+            }
+            double c0 = 0.0;
+            for (int c = v; c < ncorr; c += VL) c0 += hc[c] * zc[c * zld];
+            b[k] = (s0 + s1) - c0;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[k] += __shfl_xor_sync(0xffffffffu, b[k], o);
+#pragma unroll
+    for (int m = 1; m < PER; m <<= 1)
+#pragma unroll
+        for (int k = 0; k + m < PER; k += 2 * m) b[k] += b[k + m];
+    return b[0];
+}
+
 template <typename T, int D>
 GmvArgs<T, D> make_gmv_args(const sgk_op* op) {
     const sgk_index* idx = op->idx;

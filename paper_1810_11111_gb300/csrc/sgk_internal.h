@@ -307,16 +307,25 @@ struct sgk_op {
     std::vector<int> rlen_host;  // host copy of rlen
     // bound on ||A||_2 of the sparse-grid operator: sum_i |kappa_i| max(||S||_1, ||S||_inf)
     double anorm = 0.0;
+    // pre-located gathers (built when the operator has at most
+    // GMV_LIST_MAX entries): for output g and direction i the entries
+    // gmv_eoff[g d + i] .. gmv_eoff[g d + i + 1] of gmv_ent, each {index of
+    // x, index into gmv_cvk}, in row order; gmv_ecnt_host[g] = entries of g
+    DevBuf<int32_t> gmv_eoff;
+    DevBuf<int2> gmv_ent;
+    std::vector<int32_t> gmv_ecnt_host;
 };
+constexpr int64_t GMV_LIST_MAX = int64_t(1) << 24;
 
 // Builds and checks the gather-matvec tables of an assembled operator.
 void build_gmv_tables(sgk_op* op);
-// Boundaries of nb contiguous slices of the coefficient vector with about
-// equal work for the persistent Arnoldi kernel: per coefficient its matvec
-// entries (all directions) plus 2 extra for the Gram-Schmidt passes
-// (extra = 2 M); no slice but the last is longer than cap (the caller checks
-// the last).  bounds[0] = 0, bounds[nb] = dof, non-decreasing.
-std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap);
+// Boundaries of nb contiguous slices of the coefficient vector for the
+// persistent Arnoldi kernel, minimising the largest slice cost (per output
+// its matvec entries, all directions, plus extra for the Gram-Schmidt
+// passes, extra = 2 M), with at most cap_len outputs and cap_ent entries per
+// slice.  bounds[0] = 0, bounds[nb] = dof, non-decreasing; empty when the
+// caps cannot be met with nb slices.
+std::vector<int64_t> arnoldi_slice_bounds(const sgk_op* op, int nb, int extra, int64_t cap_len, int64_t cap_ent);
 long long tuple_rank(const std::vector<int>& l, int n);
 
 template <typename T>

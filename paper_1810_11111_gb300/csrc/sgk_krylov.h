@@ -1,5 +1,6 @@
 // Krylov exponential and vector kernels: shared declarations.
 #pragma once
+#include <vector>
 
 #include <functional>
 
@@ -45,6 +46,7 @@ struct PersistentWork {
     int G = 0;                // lanes per output in the matvec (0: default)
     const int64_t* bounds = nullptr;  // work-balanced slices (device, grid + 1 entries), or null
     int64_t E = 0;                    // longest slice when bounds is set
+    int64_t list_ent = 0;             // most pre-located gather entries of a slice when bounds is set
 };
 
 // CTAs of the persistent kernel on this context.
@@ -53,8 +55,12 @@ int arnoldi_persistent_ctas(const sgk_ctx* ctx);
 // this context's device.
 int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx);
 size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M);
-// Outputs one pass of the persistent kernel's matvec covers at 8 lanes each.
-int arnoldi_outputs_per_pass();
+// Work-balanced slices for the persistent kernel (arnoldi_slice_bounds with
+// the caps that keep the slice's pre-located gathers and Krylov columns in
+// shared memory); empty when no such partition exists.  E and list_ent
+// receive the longest slice and its most gather entries.
+std::vector<int64_t> arnoldi_balanced_bounds(const sgk_ctx* ctx, const sgk_op* op, int M, int64_t* E,
+                                             int64_t* list_ent);
 // gamma, V (M + 1 columns), H and m_eff of the Krylov space of v, in one
 // cooperative launch.
 void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,

@@ -41,6 +41,7 @@ struct sgk_solver {
     DevBuf<unsigned> pbar;
     DevBuf<int64_t> abounds;  // work-balanced slices of the persistent kernel
     int64_t aE = 0;           // longest of them
+    int64_t alist = 0;        // most pre-located gather entries of one of them
     // reaction passes: [unod S][wnod S][tmp][spin S][spout S], T = double or float
     DevBuf<double> q64, jw64;
     DevBuf<float> q32, jw32;

@@ -382,6 +382,7 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
         pw.G = s->arn_G;
         pw.bounds = s->abounds.p;
         pw.E = s->aE;
+        pw.list_ent = s->alist;
         krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, s->dt);
     } else {
         auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
@@ -769,18 +770,12 @@ void solver_alloc(sgk_solver* s) {
         s->pbuf.alloc(arnoldi_persistent_pbuf_size(s->ctx, M));
         s->pbar.alloc(2 * S);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
-        // slices of about equal work (the species share one index set), none
-        // needing more matvec passes than equal slices do: a pass is the
-        // CTA's outputs at 8 lanes each, and the slowest CTA sets the pace
-        const int nbp = arnoldi_persistent_ctas(s->ctx);
-        const int64_t per = arnoldi_outputs_per_pass();
-        const int64_t cap = ((n + nbp - 1) / nbp + per - 1) / per * per;
-        const std::vector<int64_t> bnd = arnoldi_slice_bounds(s->ops[0], nbp, 2 * M, cap);
-        int64_t longest = 1;
-        for (size_t i = 0; i + 1 < bnd.size(); ++i) longest = std::max<int64_t>(longest, bnd[i + 1] - bnd[i]);
-        // else equal slices (the kernel stages a slice in shared memory)
-        if (longest <= cap && longest <= 24 * 1024) {
-            s->aE = longest;
+        // slices of about equal work (the species share one index set)
+        int64_t E = 0, lent = 0;
+        const std::vector<int64_t> bnd = arnoldi_balanced_bounds(s->ctx, s->ops[0], M, &E, &lent);
+        if (!bnd.empty() && E >= 1 && E <= 24 * 1024) {  // else equal slices
+            s->aE = E;
+            s->alist = lent;
             s->abounds.upload(bnd, s->ctx->stream);
         }
         // tune the matvec's lanes per output on this operator and size (the
@@ -792,6 +787,7 @@ void solver_alloc(sgk_solver* s) {
         pw.bar = s->pbar.p;
         pw.bounds = s->abounds.p;
         pw.E = s->aE;
+        pw.list_ent = s->alist;
         s->arn_G = arnoldi_autotune(s->ctx, s->ops[0], pw, krylov_work<double>(s, 0), s->W.p, n, M);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
     }
