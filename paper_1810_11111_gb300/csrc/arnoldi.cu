@@ -49,8 +49,8 @@ static int persistent_ctas(const sgk_ctx* ctx) {
 int arnoldi_persistent_ctas(const sgk_ctx* ctx) { return persistent_ctas(ctx); }
 
 int64_t arnoldi_persistent_max_n(const sgk_ctx* ctx) {
-    // the slice of w is staged in shared memory: at most 24 K doubles per CTA
-    return (int64_t)persistent_ctas(ctx) * 24 * 1024;
+    // two slices of w are staged in shared memory: at most 12 K doubles each
+    return (int64_t)persistent_ctas(ctx) * 12 * 1024;
 }
 
 size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) {
@@ -72,10 +72,10 @@ std::vector<int64_t> arnoldi_balanced_bounds(const sgk_ctx* ctx, const sgk_op* o
     const int64_t per = PT / 8;  // outputs of one matvec pass at 8 lanes each
     // no more matvec passes than equal slices need (a pass costs about as
     // much as 8 K gather entries)
-    const int64_t cap_len = std::min<int64_t>(((n + nb - 1) / nb + per - 1) / per * per, 24 * 1024);
+    const int64_t cap_len = std::min<int64_t>(((n + nb - 1) / nb + per - 1) / per * per, 12 * 1024);
     // shared memory left for the entries with the longest slice's w, V, Z
     // and entry offsets staged
-    const size_t fixed = sizeof(double) * ((size_t)cap_len + 2 * (size_t)(M + 1) * (size_t)(cap_len | 1)) +
+    const size_t fixed = sizeof(double) * (2 * (size_t)cap_len + 2 * (size_t)(M + 1) * (size_t)(cap_len | 1)) +
                          sgk_arn::arn_eoff_bytes((int)cap_len, d);
     const size_t budget = smem_budget(ctx);
     int64_t cap_ent = (op->gmv_ecnt_host.empty() || fixed >= budget) ? (int64_t(1) << 40)
@@ -113,7 +113,7 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     // the fixed-point limb sums hold one term below 2^56 per CTA
     SGK_REQUIRE(nb <= 255, SGK_EUNSUPPORTED, "persistent Arnoldi: more than 255 CTAs");
     const int64_t E = pw.bounds ? pw.E : (n + nb - 1) / nb;
-    SGK_REQUIRE(E >= 1 && E <= 24 * 1024, SGK_EUNSUPPORTED, "persistent Arnoldi: slice too long");
+    SGK_REQUIRE(E >= 1 && E <= 12 * 1024, SGK_EUNSUPPORTED, "persistent Arnoldi: slice too long");
     // lanes per output in the matvec: the autotuned value, else eight (the
     // gathers are latency-bound; more lanes keep more of them in flight)
     const int G = pw.G > 0 ? pw.G : 8;
@@ -163,7 +163,7 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
         }
     const bool has_list = !op->gmv_ecnt_host.empty() && op->gmv_ent.p != nullptr;
     const size_t budget = smem_budget(ctx);
-    const size_t ws = sizeof(double) * (size_t)E;
+    const size_t ws = sizeof(double) * 2 * (size_t)E;  // two staged slices of w
     const size_t vz = sizeof(double) * 2 * (size_t)(M + 1) * (size_t)(E | 1);  // odd column stride
     const size_t lb = loc_bytes(d) * (size_t)E;
     const size_t lst = sgk_arn::arn_eoff_bytes((int)E, d) + sizeof(int2) * (size_t)std::max<int64_t>(list_ent, 1);

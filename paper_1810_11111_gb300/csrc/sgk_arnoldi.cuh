@@ -282,7 +282,8 @@ __device__ __forceinline__ void slice_norm2(const double* ws, int ne, double* re
 
 template <int D, int KP1, int G>
 __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
-    // dynamic shared memory: [ws: E][Vs: (M+1) Es][Zs: (M+1) Es][located rows, or gather offsets and entries]
+    // dynamic shared memory: [w slices: 2 E][Vs: (M+1) Es][Zs: (M+1) Es][located rows, or gather offsets
+    // and entries]
     extern __shared__ __align__(16) double smem[];
     __shared__ double h1[SGK_MAX_KRYLOV + 2];
     __shared__ double h2[SGK_MAX_KRYLOV + 2];
@@ -298,13 +299,17 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     const int E = a.E;  // longest slice
     const int64_t lo = a.bounds ? a.bounds[b] : std::min<int64_t>(n, (int64_t)b * E);
     const int ne = (int)((a.bounds ? a.bounds[b + 1] : std::min<int64_t>(n, lo + E)) - lo);
-    double* const ws = smem;
+    // the staged slice of w, two buffers alternating by step: the update of
+    // step j (v_{j+1} from w') runs during the matvec of step j + 1
+    double* const wsb0 = smem;
+    double* const wsb1 = smem + E;
     // shared columns of V and Z have an odd stride: the lanes of one output
     // read different columns of Z at the same row without bank conflicts
     const int Es = E | 1;
-    double* const Vs = a.smem_vz ? smem + E : nullptr;
-    double* const Zs = a.smem_vz ? smem + E + (size_t)(a.M + 1) * Es : nullptr;
-    unsigned char* const tail = reinterpret_cast<unsigned char*>(smem + E + (a.smem_vz ? 2 * (size_t)(a.M + 1) * Es : 0));
+    double* const Vs = a.smem_vz ? smem + 2 * E : nullptr;
+    double* const Zs = a.smem_vz ? smem + 2 * E + (size_t)(a.M + 1) * Es : nullptr;
+    unsigned char* const tail =
+        reinterpret_cast<unsigned char*>(smem + 2 * E + (a.smem_vz ? 2 * (size_t)(a.M + 1) * Es : 0));
     GmvLoc<D>* const sloc = a.smem_loc ? reinterpret_cast<GmvLoc<D>*>(tail) : nullptr;
     // pre-located gathers of the slice: offsets rebased to the slice's first
     // entry, then the entries
@@ -371,9 +376,9 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     if (b == 0)
         for (int i = threadIdx.x; i < 3 * FX_SET; i += PT) a.acc[i] = 0ull;
     // gamma = ||v||
-    for (int u = threadIdx.x; u < ne; u += PT) ws[u] = a.v[lo + u];
+    for (int u = threadIdx.x; u < ne; u += PT) wsb0[u] = a.v[lo + u];
     __syncthreads();
-    slice_norm2(ws, ne, red, P2 + b);
+    slice_norm2(wsb0, ne, red, P2 + b);
     if (!barrier()) return;
     colsum(P2, nb, 1, s_scal, ctmp);
     __syncthreads();
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     if (!(s_scal[1] > 0.0)) return;  // gamma = 0: the same decision in every CTA
     double scale = s_scal[1];
     for (int u = threadIdx.x; u < ne; u += PT) {
-        const double y = ws[u] * scale;
+        const double y = wsb0[u] * scale;
         a.V[lo + u] = y;
         if (Vs) Vs[u] = y;
     }
@@ -408,8 +413,29 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     const double* x = a.v;
     int ncorr = 0;                 // columns of the correction (0: none)
     double fro2 = 0.0, sub = 0.0;  // kept alike by every lane of warp 0
+    // the pending update of the previous step: v_{pj+1} on the slice from
+    // that step's staged w (w' - V h2, or w'' after an explicit norm) times
+    // pscale, into column pj + 1 of V (global and shared)
+    int pj = -1, pnc = 0;
+    bool pexpl = false;
+    double pscale = 0.0;
+    auto pending_update = [&]() {
+        double* const wp = (pj & 1) ? wsb1 : wsb0;
+        double* vg = a.V + (int64_t)(pj + 1) * n + lo;
+        double* vs = Vs ? Vs + (int64_t)(pj + 1) * Es : nullptr;
+        if (pexpl) {
+            for (int u = threadIdx.x; u < ne; u += PT) {
+                const double y = wp[u] * pscale;
+                vg[u] = y;
+                if (vs) vs[u] = y;
+            }
+        } else {
+            slice_update(Vl, vld, pnc, h2, nullptr, wp, lo, ne, vg, vs, pscale);
+        }
+    };
     for (int j = 0; j < a.M; ++j) {
         double* w = (j & 1) ? a.w1 : a.w0;
+        double* const ws = (j & 1) ? wsb1 : wsb0;
         const int nc = j + 1;
         // A v_j on this slice, staged in shared memory and kept in Z
         for (int base = 0; base < ne; base += PT / G) {
@@ -435,6 +461,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
                 Zl[(int64_t)j * zld + u] = acc;
             }
         }
+        if (pj >= 0) pending_update();
         __syncthreads();
         slice_dots(Vl, vld, nc, ws, ne, sdot, false, ctmp, ctmp2);
         fx_publish(nc, false);
@@ -532,25 +559,17 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         }
         if (!(s_scal[1] > 0.0)) return;  // breakdown: the same decision in every CTA
         scale = s_scal[1];
-        double* vg = a.V + (int64_t)(j + 1) * n + lo;
-        double* vs = Vs ? Vs + (int64_t)(j + 1) * Es : nullptr;
-        if (explicit_norm) {
-            for (int u = threadIdx.x; u < ne; u += PT) {
-                const double y = ws[u] * scale;
-                vg[u] = y;
-                if (vs) vs[u] = y;
-            }
-            ncorr = 0;
-        } else {
-            // v_{j+1} = (w' - V h2) / beta on the slice; w' stays published
-            slice_update(Vl, vld, nc, h2, nullptr, ws, lo, ne, vg, vs, scale);
-            ncorr = nc;
-        }
+        // v_{j+1} is formed during the next step's matvec (which gathers w',
+        // published, and needs no column of V); the inner products after it
+        // read column j + 1
+        pj = j;
+        pnc = nc;
+        pexpl = explicit_norm;
+        pscale = scale;
+        ncorr = explicit_norm ? 0 : nc;
         x = w;
-        // the next step overwrites ws only after its matvec, which reads x
-        // (global) and nothing staged; h2 stays until the next second pass
-        __syncthreads();
     }
+    if (pj >= 0) pending_update();  // the last column, v_M
 }
 
 template <int D, int KP1, int G>

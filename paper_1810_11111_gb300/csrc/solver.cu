@@ -773,7 +773,7 @@ void solver_alloc(sgk_solver* s) {
         // slices of about equal work (the species share one index set)
         int64_t E = 0, lent = 0;
         const std::vector<int64_t> bnd = arnoldi_balanced_bounds(s->ctx, s->ops[0], M, &E, &lent);
-        if (!bnd.empty() && E >= 1 && E <= 24 * 1024) {  // else equal slices
+        if (!bnd.empty() && E >= 1 && E <= 12 * 1024) {  // else equal slices
             s->aE = E;
             s->alist = lent;
             s->abounds.upload(bnd, s->ctx->stream);
