@@ -600,6 +600,9 @@ __global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
     __shared__ double red[XTH / 32];
     __shared__ int s_piv;
     __shared__ double s_inv;
+    __shared__ int s_perm[2][EXPM_CLUSTER_MAX_M];
+    __shared__ int s_lpiv[2];
+    __shared__ double s_linv[2];
     const int rank = cluster_rank();
     const int m = m_p ? *m_p : m_fixed;
     if (rank == 0)
@@ -620,24 +623,41 @@ __global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
         X[idx] = tau * Hh[(long long)i * M + j];
     }
     __syncthreads();
+    // ||X||_1: eight threads per column (consecutive lanes) sum strided
+    // rows, then xor shuffles within the eight and a maximum over columns
     double colmax = 0.0;
-    for (int j = threadIdx.x; j < m; j += XTH) {
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) s += fabs(X[i * m + j]);
-        colmax = fmax(colmax, s);
+    for (int base = 0; base < m * 8; base += XTH) {
+        const int t = base + threadIdx.x, j = t >> 3, part = t & 7;
+        double cs = 0.0;
+        if (j < m)
+            for (int i = part; i < m; i += 8) cs += fabs(X[i * m + j]);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        colmax = fmax(colmax, cs);
     }
-    for (int o = 16; o > 0; o >>= 1) colmax = fmax(colmax, __shfl_down_sync(0xffffffffu, colmax, o));
+    for (int o = 8; o < 32; o <<= 1) colmax = fmax(colmax, __shfl_xor_sync(0xffffffffu, colmax, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = colmax;
     __syncthreads();
-    // the scaling exponent on one thread (FP64 transcendental), broadcast
+    // the scaling exponent s = ceil(log2(||X||_1 / theta_13)), read off the
+    // binary exponent of the ratio (exact: x = f 2^e with f in [1/2, 1) has
+    // ceil(log2 x) = e, or e - 1 when f = 1/2), and the factor 2^-s
     if (threadIdx.x == 0) {
         double nm = 0.0;
         for (int w = 0; w < XTH / 32; ++w) nm = fmax(nm, red[w]);
-        s_piv = nm > 0.0 ? max(0, (int)ceil(log2(nm / THETA13))) : 0;
+        int sc = 0;
+        const double ratio = nm / THETA13;
+        if (ratio > 1.0) {
+            int e = 0;
+            const double f = frexp(ratio, &e);
+            sc = f == 0.5 ? e - 1 : e;
+        }
+        s_piv = sc;
+        s_inv = ldexp(1.0, -sc);
     }
     __syncthreads();
     const int s = s_piv;
-    for (int idx = threadIdx.x; idx < mm; idx += XTH) X[idx] = ldexp(X[idx], -s);
+    const double s_fac = s_inv;
+    for (int idx = threadIdx.x; idx < mm; idx += XTH) X[idx] *= s_fac;
     // every CTA of the cluster must be running before its shared memory is
     // written by a peer
     __syncthreads();
@@ -668,88 +688,170 @@ __global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
     __syncthreads();
     double* P = T1;
     double* Q = T2;
-    double* L = A2;     // multipliers of the current column
-    double* Dinv = A4;  // reciprocals of the pivots
-    // LU with partial pivoting of P (redundant in every CTA), applied to
-    // this CTA's columns [c0, c1) of Q
+    double* Dinv = A4;  // reciprocals of the pivots, by position
+    // LU with partial pivoting of P (redundant in every CTA, identical
+    // operations in identical order), applied to this CTA's columns [c0, c1)
+    // of Q.  Rows are not moved: perm maps a position to its row (two
+    // buffers, the step's mapping read from one and the next written to the
+    // other).  Each step is one CTA barrier: warp 0 first eliminates column
+    // k + 1 and finds its pivot and reciprocal (look-ahead) while the other
+    // warps eliminate the remaining columns and the right-hand sides.
     const int c0 = rank * m / XCL, c1 = (rank + 1) * m / XCL, nc = c1 - c0;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // multipliers by position, two buffers (the step's and the next one's)
+    double* const Lbuf = A2;
+    // On warp 0: the pivot of column kk over positions i >= kk under the map
+    // rowof (largest |P|, compared as the bit patterns of |x|, which order
+    // like the values; NaN never wins, ties go to the lowest position), its
+    // reciprocal, and the multipliers P[row(i)][kk] / pivot of the positions
+    // below it; the position and reciprocal go to slot sl, the multipliers to
+    // buffer sl.
+    auto pivot = [&](int kk, auto&& rowof, int sl) {
+        // per lane its best position (first of its rows), keys as 32-bit
+        // halves for the warp max-reductions; key 0 with has = false for a
+        // lane without a comparable entry
+        unsigned long long best = 0ull;
+        int pos = m;
+        for (int i = kk + lane; i < m; i += 32) {
+            const unsigned long long bits =
+                (unsigned long long)__double_as_longlong(P[rowof(i) * m + kk]) & 0x7fffffffffffffffull;
+            if (bits <= 0x7ff0000000000000ull && (pos == m || bits > best)) {
+                best = bits;
+                pos = i;
+            }
+        }
+        const bool has = pos < m;
+        const unsigned hi = has ? (unsigned)(best >> 32) + 1u : 0u;  // +1: below every real key
+        const unsigned hmax = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned lo = hi == hmax ? (unsigned)best : 0u;
+        const unsigned lmax = __reduce_max_sync(0xffffffffu, hi == hmax ? lo : 0u);
+        // the winners hold (hmax, lmax); positions grow with the lane within
+        // a round of 32 rows and each lane keeps its first, so the lowest
+        // winning lane holds the lowest winning position... unless a lane's
+        // own first row is in a later round than another winner's: take the
+        // minimum position over the winners
+        const bool win = hmax != 0u && hi == hmax && lo == lmax;
+        pos = (int)__reduce_min_sync(0xffffffffu, win ? (unsigned)pos : 0xffffffffu);
+        if (hmax == 0u || pos >= m) pos = kk;  // no comparable entry (NaN column)
+        const int rp = rowof(pos), rkk = rowof(kk);
+        const double pv = P[rp * m + kk];
+        // 1 / pv: an FP32 seed refined by two Newton steps r <- r + r (1 - pv r)
+        // (quadratic convergence, 2^-24 -> 2^-48 -> below one ulp); the
+        // division when pv is outside the FP32 range
+        double inv;
+        const double apv = fabs(pv);
+        if (apv > 1e-30 && apv < 1e30) {
+            double r = (double)__frcp_rn((float)pv);
+            r = fma(r, fma(-pv, r, 1.0), r);
+            r = fma(r, fma(-pv, r, 1.0), r);
+            inv = r;
+        } else {
+            inv = 1.0 / pv;
+        }
+        if (lane == 0) {
+            s_lpiv[sl] = pos;
+            s_linv[sl] = inv;
+        }
+        // positions below kk after exchanging kk and pos
+        double* const Lm = Lbuf + sl * m;
+        for (int i = kk + 1 + lane; i < m; i += 32) {
+            const int ri = i == pos ? rkk : rowof(i);
+            Lm[i] = P[ri * m + kk] * inv;
+        }
+    };
+    for (int i = threadIdx.x; i < m; i += XTH) s_perm[0][i] = i;
+    __syncthreads();
+    if (wid == 0) pivot(0, [&](int i) { return i; }, 0);
+    __syncthreads();
     for (int k = 0; k < m; ++k) {
-        if (threadIdx.x < 32) {
-            double best = -1.0;
-            int piv = m;
-            for (int i = k + lane; i < m; i += 32) {
-                const double v = fabs(P[i * m + k]);
-                if (v > best) {
-                    best = v;
-                    piv = i;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_down_sync(0xffffffffu, best, o);
-                const int op = __shfl_down_sync(0xffffffffu, piv, o);
-                if (ob > best || (ob == best && op < piv)) {
-                    best = ob;
-                    piv = op;
-                }
-            }
-            if (lane == 0) {
-                if (piv >= m) piv = k;  // no comparable entry (NaN column)
-                s_piv = piv;
-                s_inv = 1.0 / P[piv * m + k];
-                Dinv[k] = s_inv;
-            }
-        }
-        __syncthreads();
-        const int piv = s_piv;
-        const double inv = s_inv;
-        // multipliers from the pre-swap column (row piv becomes row k)
-        for (int i = k + 1 + threadIdx.x; i < m; i += XTH) L[i] = (i == piv ? P[k * m + k] : P[i * m + k]) * inv;
-        __syncthreads();
-        if (piv != k) {
-            for (int j = k + threadIdx.x; j < m; j += XTH) {
-                const double t = P[k * m + j];
-                P[k * m + j] = P[piv * m + j];
-                P[piv * m + j] = t;
-            }
-            for (int j = threadIdx.x; j < nc; j += XTH) {
-                const double t = Q[k * m + c0 + j];
-                Q[k * m + c0 + j] = Q[piv * m + c0 + j];
-                Q[piv * m + c0 + j] = t;
-            }
-            __syncthreads();
-        }
-        const int rows = m - k - 1, w = (m - k - 1) + nc;
-        for (int idx = threadIdx.x; idx < rows * w; idx += XTH) {
-            const int i = k + 1 + idx / w, jj = idx - (idx / w) * w;
-            const double l = L[i];
-            if (jj < m - k - 1) {
-                const int j = k + 1 + jj;
-                P[i * m + j] -= l * P[k * m + j];
-            } else {
-                const int j = c0 + jj - (m - k - 1);
-                Q[i * m + j] -= l * Q[k * m + j];
-            }
-        }
-        __syncthreads();
-    }
-    for (int k = m - 1; k >= 0; --k) {
-        const double inv = Dinv[k];
-        for (int j = threadIdx.x; j < nc; j += XTH) Q[k * m + c0 + j] *= inv;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < k * nc; idx += XTH) {
-            const int i = idx / nc, j = c0 + idx - (idx / nc) * nc;
-            Q[i * m + j] -= P[i * m + k] * Q[k * m + j];
-        }
-        __syncthreads();
-    }
-    // publish this CTA's columns of R = P^{-1} Q into every copy of Q
-    for (int idx = threadIdx.x; idx < m * nc; idx += XTH) {
-        const int i = idx / nc, j = c0 + idx - (idx / nc) * nc;
-        const double v = Q[i * m + j];
+        const int cur_b = k & 1;
+        const int* perm = s_perm[cur_b];
+        const int piv = s_lpiv[cur_b];
+        const double inv = s_linv[cur_b];
+        const int rowk = perm[piv], rowp = perm[k];
+        // position -> row for this step (positions k and piv exchanged)
+        auto rowof = [&](int i) { return i == k ? rowk : (i == piv ? rowp : perm[i]); };
+        if (threadIdx.x == 0) Dinv[k] = inv;
+        for (int i = threadIdx.x; i < m; i += XTH) s_perm[cur_b ^ 1][i] = rowof(i);
+        const double* pk = P + rowk * m;  // the pivot row
+        const int rows = m - k - 1;
+        const int wcols = m - k - 2 > 0 ? m - k - 2 : 0;
+        // multipliers of this step (written by warp 0 in the previous one)
+        const double* const Lcur = Lbuf + cur_b * m;
+        double lreg[(EXPM_CLUSTER_MAX_M + 31) / 32];
+        if (wid == 0) {
+            // column k + 1, then its pivot and the next multipliers
 #pragma unroll
-        for (int p = 0; p < XCL; ++p)
-            if (p != rank) *cluster_map(xs + T2_ * mm + i * m + j, p) = v;
+            for (int q = 0; q < (EXPM_CLUSTER_MAX_M + 31) / 32; ++q) {
+                const int i = k + 1 + lane + 32 * q;
+                lreg[q] = i < m ? Lcur[i] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < (EXPM_CLUSTER_MAX_M + 31) / 32; ++q) {
+                const int i = k + 1 + lane + 32 * q;
+                if (i < m && k + 1 < m) P[rowof(i) * m + k + 1] -= lreg[q] * pk[k + 1];
+            }
+            __syncwarp();
+            if (k + 1 < m) pivot(k + 1, rowof, cur_b ^ 1);
+        } else if ((wid & 3) != 0) {
+            // columns k + 2 .. m - 1 of P and the c1 - c0 right-hand sides,
+            // (rows x w) items over the warps that do not share warp 0's
+            // sub-partition (warp w runs on sub-partition w mod 4), so that
+            // warp 0's FP64 chain does not queue behind their FP64 work
+            const int w = wcols + nc;
+            const int wk = wid - 1 - wid / 4, nthr = (XTH / 32 - XTH / 128) * 32;
+            for (int idx = wk * 32 + lane; idx < rows * w; idx += nthr) {
+                const int i = k + 1 + idx / w, jj = idx - (idx / w) * w;
+                const int ri = rowof(i);
+                const double l = Lcur[i];
+                if (jj < wcols) {
+                    const int j = k + 2 + jj;
+                    P[ri * m + j] -= l * pk[j];
+                } else {
+                    const int j = c0 + jj - wcols;
+                    Q[ri * m + j] -= l * Q[rowk * m + j];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // back substitution U x = Q' for each own column: one warp per column,
+    // lanes over positions (x in registers), the solved entry broadcast by
+    // shuffle; perm holds the final position -> row map
+    {
+        const int* perm = s_perm[m & 1];
+        constexpr int PL = (EXPM_CLUSTER_MAX_M + 31) / 32;  // positions per lane
+        for (int cc = wid; cc < nc; cc += XTH / 32) {
+            const int j = c0 + cc;
+            double x[PL];
+#pragma unroll
+            for (int q = 0; q < PL; ++q) {
+                const int i = lane + 32 * q;
+                x[q] = i < m ? Q[perm[i] * m + j] : 0.0;
+            }
+            for (int k = m - 1; k >= 0; --k) {
+                const int ql = k >> 5, kl = k & 31;
+                double xk = 0.0;
+#pragma unroll
+                for (int q = 0; q < PL; ++q)
+                    if (q == ql) xk = x[q];
+                xk = __shfl_sync(0xffffffffu, xk, kl) * Dinv[k];
+#pragma unroll
+                for (int q = 0; q < PL; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < k) x[q] -= P[perm[i] * m + k] * xk;
+                    else if (i == k) x[q] = xk;
+                }
+            }
+            // publish this column of R = P^{-1} Q into every CTA's copy of Q
+#pragma unroll
+            for (int q = 0; q < PL; ++q) {
+                const int i = lane + 32 * q;
+                if (i < m)
+#pragma unroll
+                    for (int pr = 0; pr < XCL; ++pr) *cluster_map(xs + T2_ * mm + i * m + j, pr) = x[q];
+            }
+        }
     }
     cluster_barrier();
     int cur = T2_, nxt = U_;
