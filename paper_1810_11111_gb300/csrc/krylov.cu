@@ -21,23 +21,8 @@ namespace {
 
 constexpr double THETA13 = 5.371920351148152;  // Higham (2005), Table 2.3
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the block in a fixed tree; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
-    if (wid == 0) v = warp_sum(v);
-    __syncthreads();
-    return v;
-}
+__device__ __forceinline__ double warp_sum(double v) { return warp_sum_f64(v); }
+__device__ __forceinline__ double block_sum(double v, double* sh) { return block_sum_f64(v, sh); }
 
 template <typename TA, typename TB>
 __global__ void dot_partial_kernel(const TA* __restrict__ a, const TB* __restrict__ b, long long n,

@@ -336,4 +336,26 @@ void op_matvec(const sgk_op* op, const T* x, T* y);
 // Deterministic reductions: partials per block, then one block sums them in
 // a fixed order.
 constexpr int RED_THREADS = 256;
+
+#ifdef __CUDACC__
+// FP64 sum over a warp (down-shuffle tree; result in lane 0).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 sum over the block in a fixed tree; result valid in thread 0.  Every
+// thread of the block calls it (it synchronises the block).
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_f64(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum_f64(v);
+    __syncthreads();
+    return v;
+}
+#endif
 int reduction_blocks(const sgk_ctx* ctx, int64_t n);

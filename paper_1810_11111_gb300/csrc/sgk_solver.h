@@ -33,6 +33,7 @@ struct sgk_solver {
     DevBuf<double> Hm, h1, h2, ky, scal, partials, expm_ws;
     DevBuf<KrylovScalars> ks;
     DevBuf<unsigned> counters;
+    DevBuf<unsigned> fcnt;  // arrival counters of the fused Newton / CG kernels (zero between launches)
     // persistent Arnoldi: second work vector, partial sums, per species a
     // barrier counter and an error flag
     bool persistent = false;

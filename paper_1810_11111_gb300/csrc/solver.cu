@@ -8,10 +8,11 @@
 //   outer stop ||G||_2 <= tol max(1, ||W||_2); on failure the step is undone.
 //
 // All vectors live on the device; the host only reads back the scalars that
-// decide loop exits.  In SGK_MIXED mode the matvec, Arnoldi basis, axpys of
-// the Gram-Schmidt passes and the reaction/Jacobian passes run in FP32; inner
-// products, norms, exp(dt H), the Newton residual vector and the state stay
-// FP64.  The Krylov exponential stays FP64 in both modes.  Because FP32
+// decide loop exits (none at all in the device-driven step).  In SGK_MIXED
+// mode the reaction and Jacobian passes run in FP32; the Krylov exponential
+// (matvec, basis, exp(dt H)), inner products, norms, the Newton residual
+// vector and the state stay FP64.  The Newton and CG vector steps are fused
+// with their inner products and control decisions.  Because FP32
 // reaction passes put a floor under the residual, the mixed outer loop also
 // stops when ||G|| no longer halves and is below 1e-8 max(1, ||W||) (the
 // Newton iteration has reached that floor).
@@ -24,6 +25,225 @@
 #include "sgk_solver.h"
 
 namespace {
+
+struct StepCtl {
+    double stop, floor_accept, prev, last_g, cg_stop;
+    int it, status, cg_iters, pad;
+    long long newton_iters, inner_iters;
+};
+
+// The step's control logic (that of the host loop), on one device thread.
+__device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol) {
+    const double w = fmax(1.0, wnorm);
+    c->stop = tol * w;
+    c->floor_accept = 1e-8 * w;
+    c->prev = INFINITY;
+    c->last_g = 0.0;
+    c->it = 0;
+    c->status = SGK_ENEWTON;
+    c->cg_iters = 0;
+    c->newton_iters = 0;
+    c->inner_iters = 0;
+}
+
+// returns 1 to take another Newton correction
+__device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_iter, int mixed) {
+    c->last_g = g;
+    unsigned go = 0;
+    if (!isfinite(g)) c->status = SGK_ENEWTON;
+    else if (g <= c->stop) c->status = SGK_OK;
+    else if (mixed && c->it >= 1 && g > 0.5 * c->prev && g <= c->floor_accept) c->status = SGK_OK;
+    else if (c->it >= max_iter) c->status = SGK_ENEWTON;
+    else {
+        c->prev = g;
+        go = 1;
+    }
+    return go;
+}
+
+__device__ __forceinline__ unsigned cg_begin(StepCtl* c, double r, double inner_tol, int inner_max) {
+    c->cg_stop = inner_tol * inner_tol * r;
+    c->cg_iters = 0;
+    return (inner_max > 0 && r > c->cg_stop) ? 1u : 0u;
+}
+
+__device__ __forceinline__ unsigned cg_continue(StepCtl* c, double r, int inner_max) {
+    c->cg_iters += 1;
+    return (c->cg_iters < inner_max && r > c->cg_stop) ? 1u : 0u;
+}
+
+__device__ __forceinline__ void newton_advance(StepCtl* c) {
+    c->inner_iters += c->cg_iters;
+    c->newton_iters += 1;
+    c->it += 1;
+}
+
+// Deterministic FP64 sum completed by the last block to arrive: every block
+// stores its partial, counts itself in, and the block that arrives last sums
+// the partials in index order with the tree of the two-kernel reduction
+// (reduce_final), so the value is bitwise that of vk_dot on the same grid;
+// it resets the counter and calls fin(total) on thread 0.
+template <typename Fin>
+__device__ __forceinline__ void finish_sum(double acc, double* partials, unsigned* counter, Fin&& fin) {
+    __shared__ double sh[32];
+    __shared__ int s_last;
+    acc = block_sum_f64(acc, sh);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partials + i);
+    t = block_sum_f64(t, sh);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        fin(t);
+    }
+}
+
+// The last block to arrive runs fin() on thread 0 (no sum).
+template <typename Fin>
+__device__ __forceinline__ void finish_last(unsigned* counter, Fin&& fin) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        *counter = 0u;
+        fin();
+    }
+}
+
+#define SGK_GRID_STRIDE(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// The Newton / CG vector steps fused with their inner products and, in the
+// device-driven step (ctl not null), with the control decisions.  Each runs
+// on the grid of vk_dot (reduction_blocks x RED_THREADS), so its elementwise
+// results and sums are bitwise those of the separate kernels.
+
+// out = ||W|| and the Newton set-up
+__global__ void norm_init_kernel(const double* __restrict__ W, long long n, double* partials, unsigned* cnt,
+                                 double* out, StepCtl* ctl, double tol) {
+    double acc = 0.0;
+    SGK_GRID_STRIDE(i, n) acc += W[i] * W[i];
+    finish_sum(acc, partials, cnt, [&](double t) {
+        const double wn = sqrt(t);
+        *out = wn;
+        if (ctl) newton_init(ctl, wn, tol);
+    });
+}
+
+// G = U - c F - W, out = ||G|| and the Newton decision
+__global__ void residual_norm_kernel(const double* __restrict__ U, const double* __restrict__ F,
+                                     const double* __restrict__ W, double c, double* __restrict__ G, long long n,
+                                     double* partials, unsigned* cnt, double* out, StepCtl* ctl,
+                                     cudaGraphConditionalHandle h, int max_iter, int mixed) {
+    double acc = 0.0;
+    SGK_GRID_STRIDE(i, n) {
+        const double g = U[i] - c * F[i] - W[i];
+        G[i] = g;
+        acc += g * g;
+    }
+    finish_sum(acc, partials, cnt, [&](double t) {
+        const double g = sqrt(t);
+        *out = g;
+        if (ctl) cudaGraphSetConditional(h, newton_decide(ctl, g, max_iter, mixed));
+    });
+}
+
+// CG start: x = 0, r = p = -G, rr = r.r and the first CG decision
+__global__ void cg_start_kernel(const double* __restrict__ G, double* __restrict__ x, double* __restrict__ r,
+                                double* __restrict__ p, long long n, double* partials, unsigned* cnt, double* rr,
+                                StepCtl* ctl, double inner_tol, int inner_max, cudaGraphConditionalHandle h) {
+    double acc = 0.0;
+    SGK_GRID_STRIDE(i, n) {
+        const double g = G[i];
+        const double v = -1.0 * g + 0.0 * g;  // the axpby(-1, G, 0, G) of the unfused form
+        x[i] = 0.0;
+        r[i] = v;
+        p[i] = v;
+        acc += v * v;
+    }
+    finish_sum(acc, partials, cnt, [&](double t) {
+        *rr = t;
+        if (ctl) cudaGraphSetConditional(h, cg_begin(ctl, t, inner_tol, inner_max));
+    });
+}
+
+// q = p - c Jp and pq = p.q
+template <typename T>
+__global__ void jac_finish_dot_kernel(const double* __restrict__ p, const T* __restrict__ Jp, double c,
+                                      double* __restrict__ q, long long n, double* partials, unsigned* cnt,
+                                      double* pq) {
+    double acc = 0.0;
+    SGK_GRID_STRIDE(i, n) {
+        const double v = p[i] - c * (double)Jp[i];
+        q[i] = v;
+        acc += p[i] * v;
+    }
+    finish_sum(acc, partials, cnt, [&](double t) { *pq = t; });
+}
+
+// alpha = rr / pq; x += alpha p; r -= alpha q; rr_new = r.r
+__global__ void cg_update_dot_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                     const double* __restrict__ q, const double* rr, const double* pq, long long n,
+                                     double* partials, unsigned* cnt, double* rr_new) {
+    const double alpha = *rr / *pq;
+    double acc = 0.0;
+    SGK_GRID_STRIDE(i, n) {
+        x[i] += alpha * p[i];
+        const double v = r[i] - alpha * q[i];
+        r[i] = v;
+        acc += v * v;
+    }
+    finish_sum(acc, partials, cnt, [&](double t) { *rr_new = t; });
+}
+
+// p = r + (rr_new / rr) p; then rr = rr_new (after every block has read rr)
+// and the next CG decision
+__global__ void cg_direction_kernel(double* __restrict__ p, const double* __restrict__ r, const double* rr_new,
+                                    double* rr, long long n, unsigned* cnt, StepCtl* ctl, int inner_max,
+                                    cudaGraphConditionalHandle h) {
+    const double beta = *rr_new / *rr;
+    SGK_GRID_STRIDE(i, n) p[i] = r[i] + beta * p[i];
+    finish_last(cnt, [&]() {
+        const double v = *rr_new;
+        *rr = v;
+        if (ctl) cudaGraphSetConditional(h, cg_continue(ctl, v, inner_max));
+    });
+}
+
+// U += x and the Newton advance
+__global__ void newton_step_kernel(double* __restrict__ U, const double* __restrict__ x, long long n, unsigned* cnt,
+                                   StepCtl* ctl) {
+    SGK_GRID_STRIDE(i, n) U[i] = 1.0 * U[i] + 1.0 * x[i];
+    finish_last(cnt, [&]() {
+        if (ctl) newton_advance(ctl);
+    });
+}
+
+#undef SGK_GRID_STRIDE
+
+// fused-kernel counters of a solver (each zero between launches)
+enum { FC_NORM, FC_RESID, FC_CGSTART, FC_JAC, FC_CGUPD, FC_CGDIR, FC_STEP, FC_COUNT };
+
+// Launch a fused kernel on the grid of vk_dot (so sums match it bitwise).
+template <typename K, typename... Args>
+void launch_fused(sgk_solver* s, long long N, const char* what, K kern, Args... args) {
+    KTimer kt(s->ctx, KC_VECTOR);
+    kern<<<reduction_blocks(s->ctx, N), RED_THREADS, 0, s->ctx->stream>>>(args...);
+    check_launch(what);
+    count_launch(s->ctx);
+}
 
 double read_scalar(sgk_solver* s, const double* dptr) {
     SGK_CUDA_CHECK(cudaMemcpyAsync(s->ctx->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
@@ -194,14 +414,22 @@ void evalF(sgk_solver* s, const double* U, double* F) {
 }
 
 // q = p - dt/2 J_F(U) p (stacked FP64)
-void apply_newton_matrix(sgk_solver* s, const double* pv, double* q) {
+// q = p - dt/2 J_F(U) p (stacked FP64); with pq also pq = p.q
+void apply_newton_matrix(sgk_solver* s, const double* pv, double* q, double* pq = nullptr) {
     const long long N = s->n * s->nspecies;
+    const double c = 0.5 * s->dt;
+    double* const part = s->partials.p;
+    unsigned* const cnt = s->fcnt.p + FC_JAC;
     if (s->prec == SGK_FP64) {
         evalJ_T<double>(s, pv, s->jw64.p);
-        vk_jac_finish<double>(s->ctx, pv, s->jw64.p, 0.5 * s->dt, q, N);
+        if (pq) launch_fused(s, N, "jac_finish_dot", jac_finish_dot_kernel<double>, pv, (const double*)s->jw64.p, c, q,
+                             N, part, cnt, pq);
+        else vk_jac_finish<double>(s->ctx, pv, s->jw64.p, c, q, N);
     } else {
         evalJ_T<float>(s, pv, s->jw32.p);
-        vk_jac_finish<float>(s->ctx, pv, s->jw32.p, 0.5 * s->dt, q, N);
+        if (pq) launch_fused(s, N, "jac_finish_dot", jac_finish_dot_kernel<float>, pv, (const float*)s->jw32.p, c, q,
+                             N, part, cnt, pq);
+        else vk_jac_finish<float>(s->ctx, pv, s->jw32.p, c, q, N);
     }
 }
 
@@ -231,21 +459,18 @@ void cg_solve(sgk_solver* s, const double* G, double* x, int& iters) {
     double* const rr = s->scal.p + 2;
     double* const rr_new = s->scal.p + 3;
     double* const pq = s->scal.p + 4;
-    SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
-    vk_axpby(ctx, -1.0, G, 0.0, G, r, N);
-    vk_axpby(ctx, -1.0, G, 0.0, G, pv, N);
-    vk_dot(ctx, r, r, N, s->partials.p, rr, 0, nullptr);
+    launch_fused(s, N, "cg_start", cg_start_kernel, G, x, r, pv, N, s->partials.p, s->fcnt.p + FC_CGSTART, rr,
+                 (StepCtl*)nullptr, 0.0, 0, cudaGraphConditionalHandle{});
     double rr_h = read_scalar(s, rr);
     const double stop = s->opts.inner_tol * s->opts.inner_tol * rr_h;
     iters = 0;
     while (iters < s->opts.inner_max && rr_h > stop) {
         run_graph(s, s->g_cg, KC_VECTOR, [&]() {
-            apply_newton_matrix(s, pv, q);
-            vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
-            vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
-            vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
-            vk_cg_direction(ctx, pv, r, rr_new, rr, N);
-            vk_copy_scalar(ctx, rr, rr_new);
+            apply_newton_matrix(s, pv, q, pq);
+            launch_fused(s, N, "cg_update", cg_update_dot_kernel, x, r, (const double*)pv, (const double*)q,
+                         (const double*)rr, (const double*)pq, N, s->partials.p, s->fcnt.p + FC_CGUPD, rr_new);
+            launch_fused(s, N, "cg_direction", cg_direction_kernel, pv, (const double*)r, (const double*)rr_new, rr,
+                         N, s->fcnt.p + FC_CGDIR, (StepCtl*)nullptr, 0, cudaGraphConditionalHandle{});
         });
         rr_h = read_scalar(s, rr);
         ++iters;
@@ -312,7 +537,8 @@ int newton(sgk_solver* s) {
     const long long N = s->n * s->nspecies;
     const double dt2 = 0.5 * s->dt;
     SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    vk_dot(ctx, s->W.p, s->W.p, N, s->partials.p, s->scal.p + 6, 1, nullptr);
+    launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p, s->fcnt.p + FC_NORM,
+                 s->scal.p + 6, (StepCtl*)nullptr, 0.0);
     const double wnorm = read_scalar(s, s->scal.p + 6);
     const double stop = s->opts.tol * std::max(1.0, wnorm);
     const double floor_accept = 1e-8 * std::max(1.0, wnorm);
@@ -320,8 +546,9 @@ int newton(sgk_solver* s) {
     for (int it = 0; it <= s->opts.max_iter; ++it) {
         run_graph(s, s->g_resid, KC_VECTOR, [&]() {
             evalF(s, s->U.p, s->Fv.p);
-            vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
-            vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
+            launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
+                         (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID, s->scal.p + 7,
+                         (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0, 0);
         });
         const double g = read_scalar(s, s->scal.p + 7);
         s->stats.last_newton_residual = g;
@@ -335,7 +562,8 @@ int newton(sgk_solver* s) {
         else gmres_solve_host(s, s->G.p, s->cg_x.p, inner);
         s->stats.inner_iters += inner;
         s->stats.newton_iters += 1;
-        vk_axpby(ctx, 1.0, s->U.p, 1.0, s->cg_x.p, s->U.p, N);
+        launch_fused(s, N, "newton_step", newton_step_kernel, s->U.p, (const double*)s->cg_x.p, N,
+                     s->fcnt.p + FC_STEP, (StepCtl*)nullptr);
     }
     return SGK_ENEWTON;
 }
@@ -403,63 +631,6 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
 // max_iter corrections, CG to a relative residual inner_tol.
 
 namespace {
-
-struct StepCtl {
-    double stop, floor_accept, prev, last_g, cg_stop;
-    int it, status, cg_iters, pad;
-    long long newton_iters, inner_iters;
-};
-
-__global__ void newton_init_kernel(StepCtl* c, const double* wnorm, double tol) {
-    const double w = fmax(1.0, *wnorm);
-    c->stop = tol * w;
-    c->floor_accept = 1e-8 * w;
-    c->prev = INFINITY;
-    c->last_g = 0.0;
-    c->it = 0;
-    c->status = SGK_ENEWTON;
-    c->cg_iters = 0;
-    c->newton_iters = 0;
-    c->inner_iters = 0;
-}
-
-__global__ void newton_control_kernel(StepCtl* c, const double* gnorm, cudaGraphConditionalHandle h, int max_iter,
-                                      int mixed) {
-    const double g = *gnorm;
-    c->last_g = g;
-    unsigned go = 0;
-    if (!isfinite(g)) c->status = SGK_ENEWTON;
-    else if (g <= c->stop) c->status = SGK_OK;
-    else if (mixed && c->it >= 1 && g > 0.5 * c->prev && g <= c->floor_accept) c->status = SGK_OK;
-    else if (c->it >= max_iter) c->status = SGK_ENEWTON;
-    else {
-        c->prev = g;
-        go = 1;
-    }
-    cudaGraphSetConditional(h, go);
-}
-
-__global__ void cg_init_kernel(StepCtl* c, const double* rr, double inner_tol, int inner_max,
-                               cudaGraphConditionalHandle h) {
-    const double r = *rr;
-    c->cg_stop = inner_tol * inner_tol * r;
-    c->cg_iters = 0;
-    cudaGraphSetConditional(h, (inner_max > 0 && r > c->cg_stop) ? 1u : 0u);
-}
-
-__global__ void cg_control_kernel(StepCtl* c, double* rr, const double* rr_new, int inner_max,
-                                  cudaGraphConditionalHandle h) {
-    const double r = *rr_new;
-    *rr = r;
-    c->cg_iters += 1;
-    cudaGraphSetConditional(h, (c->cg_iters < inner_max && r > c->cg_stop) ? 1u : 0u);
-}
-
-__global__ void newton_advance_kernel(StepCtl* c) {
-    c->inner_iters += c->cg_iters;
-    c->newton_iters += 1;
-    c->it += 1;
-}
 
 // Adds a while-node at the capture position of ctx->stream: pre(h) is
 // captured first (it sets the first condition), then the node, whose body
@@ -530,15 +701,13 @@ void build_step_graph(sgk_solver* s) {
             double* const rr = s->scal.p + 2;
             double* const rr_new = s->scal.p + 3;
             double* const pq = s->scal.p + 4;
-            vk_dot(ctx, s->W.p, s->W.p, N, s->partials.p, s->scal.p + 6, 1, nullptr);
-            newton_init_kernel<<<1, 1, 0, ctx->stream>>>(ctl, s->scal.p + 6, s->opts.tol);
-            count_launch(ctx);
+            launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p,
+                         s->fcnt.p + FC_NORM, s->scal.p + 6, ctl, s->opts.tol);
             auto resid = [&](cudaGraphConditionalHandle h) {
                 evalF(s, s->U.p, s->Fv.p);
-                vk_residual(ctx, s->U.p, s->Fv.p, s->W.p, dt2, s->G.p, N);
-                vk_dot(ctx, s->G.p, s->G.p, N, s->partials.p, s->scal.p + 7, 1, nullptr);
-                newton_control_kernel<<<1, 1, 0, ctx->stream>>>(ctl, s->scal.p + 7, h, s->opts.max_iter, mixed);
-                count_launch(ctx);
+                launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
+                             (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID,
+                             s->scal.p + 7, ctl, h, s->opts.max_iter, mixed);
             };
             int64_t mark = 0;
             capture_while(
@@ -558,29 +727,25 @@ void build_step_graph(sgk_solver* s) {
                     capture_while(
                         ctx, s->aux[1],
                         [&](cudaGraphConditionalHandle hc) {
-                            SGK_CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), ctx->stream));
-                            vk_axpby(ctx, -1.0, s->G.p, 0.0, s->G.p, r, N);
-                            vk_axpby(ctx, -1.0, s->G.p, 0.0, s->G.p, pv, N);
-                            vk_dot(ctx, r, r, N, s->partials.p, rr, 0, nullptr);
-                            cg_init_kernel<<<1, 1, 0, ctx->stream>>>(ctl, rr, s->opts.inner_tol, s->opts.inner_max, hc);
-                            count_launch(ctx);
+                            launch_fused(s, N, "cg_start", cg_start_kernel, (const double*)s->G.p, x, r, pv, N,
+                                         s->partials.p, s->fcnt.p + FC_CGSTART, rr, ctl, s->opts.inner_tol,
+                                         s->opts.inner_max, hc);
                             s->n_cgpre = ctx->launches - mark;
                         },
                         [&](cudaGraphConditionalHandle hc) {
                             mark = ctx->launches;
-                            apply_newton_matrix(s, pv, q);
-                            vk_dot(ctx, pv, q, N, s->partials.p, pq, 0, nullptr);
-                            vk_cg_update(ctx, x, r, pv, q, rr, pq, N);
-                            vk_dot(ctx, r, r, N, s->partials.p, rr_new, 0, nullptr);
-                            vk_cg_direction(ctx, pv, r, rr_new, rr, N);
-                            cg_control_kernel<<<1, 1, 0, ctx->stream>>>(ctl, rr, rr_new, s->opts.inner_max, hc);
-                            count_launch(ctx);
+                            apply_newton_matrix(s, pv, q, pq);
+                            launch_fused(s, N, "cg_update", cg_update_dot_kernel, x, r, (const double*)pv,
+                                         (const double*)q, (const double*)rr, (const double*)pq, N, s->partials.p,
+                                         s->fcnt.p + FC_CGUPD, rr_new);
+                            launch_fused(s, N, "cg_direction", cg_direction_kernel, pv, (const double*)r,
+                                         (const double*)rr_new, rr, N, s->fcnt.p + FC_CGDIR, ctl,
+                                         s->opts.inner_max, hc);
                             s->n_cgbody = ctx->launches - mark;
                         });
                     mark = ctx->launches;
-                    vk_axpby(ctx, 1.0, s->U.p, 1.0, x, s->U.p, N);
-                    newton_advance_kernel<<<1, 1, 0, ctx->stream>>>(ctl);
-                    count_launch(ctx);
+                    launch_fused(s, N, "newton_step", newton_step_kernel, s->U.p, (const double*)x, N,
+                                 s->fcnt.p + FC_STEP, ctl);
                     s->n_adv = ctx->launches - mark;
                     resid(hn);
                 });
@@ -760,6 +925,8 @@ void solver_alloc(sgk_solver* s) {
     s->expm_ws.alloc(8 * (size_t)M * M);
     s->ks.alloc(S);
     s->counters.alloc(4);
+    s->fcnt.alloc(FC_COUNT);
+    SGK_CUDA_CHECK(cudaMemsetAsync(s->fcnt.p, 0, FC_COUNT * sizeof(unsigned), s->ctx->stream));
     s->ctl.alloc(sizeof(StepCtl));
     SGK_CUDA_CHECK(cudaMallocHost(&s->hrec, sizeof(StepRecord)));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->ctl.p, 0, sizeof(StepCtl), s->ctx->stream));
