@@ -418,9 +418,13 @@ int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int o
     return guarded(s->ctx, [&]() {
         SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
         set_device(s->ctx);
-        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p + species * s->n, coeffs, s->n * sizeof(double),
-                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                       s->ctx->stream));
+        const double* src = coeffs;
+        if (!on_device) {  // staged in the predictor's buffer (free between steps)
+            SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p + species * s->n, coeffs, s->n * sizeof(double),
+                                           cudaMemcpyHostToDevice, s->ctx->stream));
+            src = s->vv.p + species * s->n;
+        }
+        solver_set_state(s, species, src);
         if (!on_device) SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
         return SGK_OK;
     });

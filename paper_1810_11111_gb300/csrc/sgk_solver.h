@@ -49,7 +49,12 @@ struct sgk_solver {
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     bool use_graphs = true;
-    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_resid, g_cg;
+    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
+    // Fv holds F(U) for the current U (a host-driven or device-driven step
+    // ended with an accepted residual evaluation there); cleared whenever U
+    // changes otherwise
+    bool fv_valid = false;
+    int64_t n_predf = 0;        // launches of the predictor's F in the step graph
     // device-driven step: the whole IIF2 step (predictor, Krylov, Newton with
     // CG) as one graph whose loops are conditional while-nodes
     GraphCache g_step;
@@ -69,6 +74,12 @@ void solver_alloc(sgk_solver* s);
 // after that stream has been synchronised, solver_step_finish reads its
 // outcome (rolling the state back on failure) and returns the status.
 bool solver_device_steps(const sgk_solver* s);
+// U was written from outside a step (or rolled back): the cached F(U) no
+// longer applies
+void solver_state_changed(sgk_solver* s);
+// U_species = src (device, n values); keeps the cached F(U) on the device when
+// nothing changed
+void solver_set_state(sgk_solver* s, int species, const double* src_dev);
 void solver_step_launch(sgk_solver* s);
 int solver_step_finish(sgk_solver* s);
 int solver_step(sgk_solver* s, int nsteps);

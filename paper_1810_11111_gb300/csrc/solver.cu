@@ -28,7 +28,10 @@ namespace {
 
 struct StepCtl {
     double stop, floor_accept, prev, last_g, cg_stop;
-    int it, status, cg_iters, pad;
+    int it, status, cg_iters;
+    int fvalid;  // Fv holds F(U) for the current U (Newton accepted at its last residual evaluation)
+    int pred_skipped;  // this step took F(U^n) from Fv
+    int pad;
     long long newton_iters, inner_iters;
 };
 
@@ -42,6 +45,7 @@ __device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol
     c->it = 0;
     c->status = SGK_ENEWTON;
     c->cg_iters = 0;
+    c->fvalid = 0;  // U becomes W; the predictor has used the previous F
     c->newton_iters = 0;
     c->inner_iters = 0;
 }
@@ -58,6 +62,8 @@ __device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_
         c->prev = g;
         go = 1;
     }
+    // accepted at this evaluation: F(U) of the new state is in Fv
+    c->fvalid = c->status == SGK_OK ? 1 : 0;
     return go;
 }
 
@@ -103,6 +109,25 @@ __device__ __forceinline__ void finish_sum(double acc, double* partials, unsigne
         *counter = 0u;
         fin(t);
     }
+}
+
+// Condition of the predictor's F evaluation: run it unless Fv already holds
+// F(U) (the previous step ended with an accepted residual evaluation at U,
+// which is the same computation).
+__global__ void predictor_if_kernel(StepCtl* c, cudaGraphConditionalHandle h) {
+    c->pred_skipped = c->fvalid;
+    cudaGraphSetConditional(h, c->fvalid ? 0u : 1u);
+}
+
+// U[i] = src[i]; any bitwise change of U clears the cached-F flag
+__global__ void set_state_kernel(double* __restrict__ U, const double* __restrict__ src, long long n, StepCtl* c) {
+    bool changed = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        changed |= __double_as_longlong(v) != __double_as_longlong(U[i]);
+        U[i] = v;
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicExch(&c->fvalid, 0);
 }
 
 // The last block to arrive runs fin() on thread 0 (no sum).
@@ -636,7 +661,7 @@ namespace {
 // captured first (it sets the first condition), then the node, whose body
 // body(h) is captured on aux (ctx->stream points there meanwhile).
 template <typename Pre, typename Body>
-void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
+void capture_cond(sgk_ctx* ctx, cudaStream_t aux, cudaGraphConditionalNodeType type, Pre&& pre, Body&& body) {
     cudaStream_t st = ctx->stream;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaGraph_t g = nullptr;
@@ -651,7 +676,7 @@ void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.type = type;
     p.conditional.size = 1;
     cudaGraphNode_t node = nullptr;
     SGK_CUDA_CHECK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
@@ -672,6 +697,11 @@ void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
     SGK_CUDA_CHECK(cudaStreamEndCapture(aux, &out));
 }
 
+template <typename Pre, typename Body>
+void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
+    capture_cond(ctx, aux, cudaGraphCondTypeWhile, pre, body);
+}
+
 bool step_graph_eligible(const sgk_solver* s) { return s->use_graphs && (!s->has_rx || s->nspecies == 1); }
 
 void build_step_graph(sgk_solver* s) {
@@ -688,7 +718,19 @@ void build_step_graph(sgk_solver* s) {
     try {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         if (s->has_rx) {
-            evalF(s, s->U.p, s->Fv.p);
+            // F(U^n) for the predictor, unless the last step left it in Fv
+            capture_cond(
+                ctx, s->aux[0], cudaGraphCondTypeIf,
+                [&](cudaGraphConditionalHandle h) {
+                    predictor_if_kernel<<<1, 1, 0, ctx->stream>>>(ctl, h);
+                    check_launch("predictor_if");
+                    count_launch(ctx);
+                },
+                [&](cudaGraphConditionalHandle) {
+                    const int64_t m0 = ctx->launches;
+                    evalF(s, s->U.p, s->Fv.p);
+                    s->n_predf = ctx->launches - m0;
+                });
             vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
         } else {
             SGK_CUDA_CHECK(
@@ -804,8 +846,8 @@ int solver_step_finish(sgk_solver* s) {
     StepCtl c{};
     if (s->has_rx) c = h->c;
     int rc = s->has_rx ? c.status : SGK_OK;
-    count_launch(ctx, (int)(s->n_prefix + c.newton_iters * (s->n_cgpre + s->n_adv + s->n_resid) +
-                            c.inner_iters * s->n_cgbody));
+    count_launch(ctx, (int)(s->n_prefix - (s->has_rx && c.pred_skipped ? s->n_predf : 0) +
+                            c.newton_iters * (s->n_cgpre + s->n_adv + s->n_resid) + c.inner_iters * s->n_cgbody));
     s->stats.newton_iters += c.newton_iters;
     s->stats.inner_iters += c.inner_iters;
     if (s->has_rx) s->stats.last_newton_residual = c.last_g;
@@ -823,14 +865,39 @@ int solver_step_finish(sgk_solver* s) {
     }
     if (rc != SGK_OK) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        solver_state_changed(s);
         SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     } else {
         s->stats.steps += 1;
+        s->fv_valid = s->has_rx;
     }
     return rc;
 }
 
 bool solver_device_steps(const sgk_solver* s) { return step_graph_eligible(s) && !s->ctx->prof_mask; }
+
+void solver_set_state(sgk_solver* s, int species, const double* src_dev) {
+    const long long n = s->n;
+    if (s->has_rx && s->ctl.p) {
+        // the device keeps the cached F(U) when the new state equals the old
+        set_state_kernel<<<reduction_blocks(s->ctx, n), RED_THREADS, 0, s->ctx->stream>>>(
+            s->U.p + species * n, src_dev, n, reinterpret_cast<StepCtl*>(s->ctl.p));
+        check_launch("set_state");
+        count_launch(s->ctx);
+        s->fv_valid = false;  // host-driven steps do not read the device flag
+    } else {
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p + species * n, src_dev, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       s->ctx->stream));
+        solver_state_changed(s);
+    }
+}
+
+void solver_state_changed(sgk_solver* s) {
+    s->fv_valid = false;
+    if (s->ctl.p)
+        SGK_CUDA_CHECK(
+            cudaMemsetAsync(&reinterpret_cast<StepCtl*>(s->ctl.p)->fvalid, 0, sizeof(int), s->ctx->stream));
+}
 
 namespace {
 
@@ -851,9 +918,12 @@ int solver_step(sgk_solver* s, int nsteps) {
     const double dt2 = 0.5 * s->dt;
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        run_graph(s, s->g_pred, KC_VECTOR, [&]() {
+        // F(U^n) for the predictor, unless the last step left it in Fv; the
+        // device-side flag of the step graph is stale after a host-driven step
+        const bool have_f = s->fv_valid;
+        run_graph(s, have_f ? s->g_pred_f : s->g_pred, KC_VECTOR, [&]() {
             if (s->has_rx) {
-                evalF(s, s->U.p, s->Fv.p);
+                if (!have_f) evalF(s, s->U.p, s->Fv.p);
                 vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
             } else {
                 SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -894,10 +964,19 @@ int solver_step(sgk_solver* s, int nsteps) {
         if (rc != SGK_OK) {
             SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
                                            ctx->stream));
+            solver_state_changed(s);
             SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
             return rc;
         }
         s->stats.steps += 1;
+        // newton() returns OK right after the residual evaluation at the final
+        // U; the step graph's flag says the same
+        if (s->has_rx) {
+            static const int one = 1;
+            SGK_CUDA_CHECK(cudaMemcpyAsync(&reinterpret_cast<StepCtl*>(s->ctl.p)->fvalid, &one, sizeof(int),
+                                           cudaMemcpyHostToDevice, ctx->stream));
+            s->fv_valid = true;
+        }
     }
     return SGK_OK;
 }
@@ -993,7 +1072,7 @@ sgk_solver::~sgk_solver() {
     if (g_step.exec) cudaGraphExecDestroy(g_step.exec);
     for (cudaStream_t& a : aux)
         if (a) cudaStreamDestroy(a);
-    for (GraphCache* g : {&g_pred, &g_resid, &g_cg})
+    for (GraphCache* g : {&g_pred, &g_pred_f, &g_resid, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     for (auto& g : g_krylov)
         if (g.exec) cudaGraphExecDestroy(g.exec);
