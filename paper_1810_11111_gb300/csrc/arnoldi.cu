@@ -60,8 +60,8 @@ size_t arnoldi_persistent_pbuf_size(const sgk_ctx* ctx, int M) {
 }
 
 static size_t smem_budget(const sgk_ctx* ctx) {
-    // the kernel's static shared memory stays below 12 KB
-    return ctx->smem_optin > 16 * 1024 ? ctx->smem_optin - 12 * 1024 : 32 * 1024;
+    // the kernel's static shared memory stays below 13 KB
+    return ctx->smem_optin > 16 * 1024 ? ctx->smem_optin - 13 * 1024 : 32 * 1024;
 }
 
 std::vector<int64_t> arnoldi_balanced_bounds(const sgk_ctx* ctx, const sgk_op* op, int M, int64_t* E,
@@ -182,6 +182,10 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
         a.smem_loc = ws + (a.smem_vz ? vz : 0) + lb <= budget;
     }
     const size_t smem = ws + (a.smem_vz ? vz : 0) + (a.list_cap ? lst : 0) + (a.smem_loc ? lb : 0);
+    // mixed precision: the matvec in double-float arithmetic (~1e-14
+    // relative; FP64 issue on this part is 1/64 of FP32), with the gather lists
+    a.cvk2 = op->gmv_cvk2.p;
+    a.df = ctx->precision == SGK_MIXED && a.list_cap > 0 && op->gmv_cvk2.p != nullptr;
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaMemsetAsync(pw.bar, 0, sizeof(unsigned), ctx->stream));
     switch (op->idx->d) {

@@ -149,10 +149,14 @@ void build_gmv_tables(sgk_op* op) {
     const size_t nnz = S.val.size();
     std::vector<double> cvk(nnz * d);
     std::vector<float> cvkf(nnz * d);
+    std::vector<float2> cvk2(nnz * d);
     for (int i = 0; i < d; ++i)
         for (size_t q = 0; q < nnz; ++q) {
-            cvk[i * nnz + q] = -op->kappa[i] * S.val[q];
-            cvkf[i * nnz + q] = (float)cvk[i * nnz + q];
+            const double v = -op->kappa[i] * S.val[q];
+            cvk[i * nnz + q] = v;
+            cvkf[i * nnz + q] = (float)v;
+            const float hi = (float)v;
+            cvk2[i * nnz + q] = make_float2(hi, (float)(v - (double)hi));
         }
     // pre-located gathers: the host mirror of gmv_locate and of the address
     // formed per entry in gmv_accumulate
@@ -210,6 +214,7 @@ void build_gmv_tables(sgk_op* op) {
     }
     op->gmv_cvk.upload(cvk, op->ctx->stream);
     op->gmv_cvkf.upload(cvkf, op->ctx->stream);
+    op->gmv_cvk2.upload(cvk2, op->ctx->stream);
     op->gmv_ce.upload(ce, op->ctx->stream);
     op->gmv_cb.upload(cb, op->ctx->stream);
     op->gmv_chunk.upload(chunk, op->ctx->stream);

@@ -22,6 +22,11 @@ struct ArnArgs {
     int list_cap;  // > 0: the slice's pre-located gather entries (at most list_cap) live in shared memory
     const int* eoff;   // pre-located gathers (see sgk_op::gmv_eoff), or null
     const int2* ent;
+    // double-float matvec (mixed precision; needs the gather lists and the
+    // shared V/Z slices): operator values as (hi, lo) pairs; the gathered
+    // vectors (w0, w1) and Z then hold (hi, lo) pairs instead of doubles
+    const float2* cvk2;
+    int df;
     const double* v;
     double* V;  // column c at V + c n
     double* w0;
@@ -241,10 +246,12 @@ __device__ __forceinline__ double fx_value(const unsigned long long* a, double i
 
 // w -= V[:, :ncols] h on this CTA's slice, one thread per element (four
 // independent chains).  Writes the staged slice ws, the global w when w is
-// not null, and when vg is not null the next basis column w * inv to vg
-// (global, slice offset included) and vs (shared, or null).
+// not null (or its double-float pair to wdf when that is not null), and when
+// vg is not null the next basis column w * inv to vg (global, slice offset
+// included) and vs (shared, or null).
 __device__ __forceinline__ void slice_update(const double* Vl, int64_t vld, int ncols, const double* h, double* w,
-                                             double* ws, int64_t lo, int ne, double* vg, double* vs, double inv) {
+                                             double* ws, int64_t lo, int ne, double* vg, double* vs, double inv,
+                                             float2* wdf = nullptr) {
     for (int u = threadIdx.x; u < ne; u += PT) {
         const double* vi = Vl + u;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -259,6 +266,7 @@ __device__ __forceinline__ void slice_update(const double* Vl, int64_t vld, int 
         const double x = ws[u] - ((a0 + a1) + (a2 + a3));
         ws[u] = x;
         if (w) w[lo + u] = x;
+        if (wdf) wdf[lo + u] = df_to_float2(df_from_double(x));
         if (vg) {
             const double y = x * inv;
             vg[u] = y;
@@ -280,7 +288,7 @@ __device__ __forceinline__ void slice_norm2(const double* ws, int ne, double* re
     }
 }
 
-template <int D, int KP1, int G>
+template <int D, int KP1, int G, bool DF>
 __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
     // dynamic shared memory: [w slices: 2 E][Vs: (M+1) Es][Zs: (M+1) Es][located rows, or gather offsets
     // and entries]
@@ -294,6 +302,9 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     __shared__ double ctmp[PT > 4 * (SGK_MAX_KRYLOV + 2) ? PT : 4 * (SGK_MAX_KRYLOV + 2)];
     __shared__ double ctmp2[4 * (SGK_MAX_KRYLOV + 2)];
     __shared__ int s_ok, s_flag;
+    // double-float matvec: the correction's coefficients and the step's scale
+    __shared__ float2 h2df[DF ? SGK_MAX_KRYLOV + 2 : 1];
+    __shared__ float2 s_scaldf;
     const int nb = gridDim.x, b = blockIdx.x;
     const int64_t n = a.n;
     const int E = a.E;  // longest slice
@@ -320,6 +331,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     const int64_t vld = a.smem_vz ? Es : n;
     double* const Zl = a.smem_vz ? Zs : a.Z + lo;
     const int64_t zld = a.smem_vz ? Es : n;
+    float2* const Zdf = reinterpret_cast<float2*>(Zl);  // Z as (hi, lo) pairs (double-float matvec)
     double* const P2 = a.pbuf;  // norms
     unsigned epoch = 0;
     auto barrier = [&]() {
@@ -375,8 +387,12 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // first atomics follow the second)
     if (b == 0)
         for (int i = threadIdx.x; i < 3 * FX_SET; i += PT) a.acc[i] = 0ull;
-    // gamma = ||v||
-    for (int u = threadIdx.x; u < ne; u += PT) wsb0[u] = a.v[lo + u];
+    // gamma = ||v||; with the double-float matvec, v's pairs for the first
+    // gathers go to w1 (free until the second step writes it)
+    for (int u = threadIdx.x; u < ne; u += PT) {
+        wsb0[u] = a.v[lo + u];
+        if (DF) reinterpret_cast<float2*>(a.w1)[lo + u] = df_to_float2(df_from_double(a.v[lo + u]));
+    }
     __syncthreads();
     slice_norm2(wsb0, ne, red, P2 + b);
     if (!barrier()) return;
@@ -388,6 +404,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     if (threadIdx.x == 0) {
         const double gamma = sqrt(s_scal[0]);
         s_scal[1] = gamma > 0.0 ? 1.0 / gamma : 0.0;
+        if (DF) s_scaldf = df_to_float2(df_from_double(s_scal[1]));
         if (b == 0) {
             ks->gamma = gamma;
             ks->inv_gamma = s_scal[1];
@@ -411,6 +428,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // the second barrier) and A v_j = (A w' - A V h2) / beta, A V being the
     // stored raw matvec outputs of the slice; after an explicit norm x is w''
     const double* x = a.v;
+    const float2* xdf = reinterpret_cast<const float2*>(a.w1);
     int ncorr = 0;                 // columns of the correction (0: none)
     double fro2 = 0.0, sub = 0.0;  // kept alike by every lane of warp 0
     // the pending update of the previous step: v_{pj+1} on the slice from
@@ -444,7 +462,16 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
             double acc;
             // the correction's columns are dealt over the virtual lanes like
             // the matrix rows (sum independent of G)
-            if (seoff) {
+            if (DF) {
+                df64 ad = gmv_accumulate_list_df<D, G>(seoff + (live ? u : 0) * D, sent, a.cvk2, xdf, r, live,
+                                                       ncorr, h2df, Zdf + (live ? u : 0), zld);
+                if (live && r == 0) {
+                    ad = df_mul(ad, df_from_float2(s_scaldf));
+                    ws[u] = df_to_double(ad);
+                    Zdf[(int64_t)j * zld + u] = df_to_float2(ad);
+                }
+                continue;
+            } else if (seoff) {
                 acc = gmv_accumulate_list<D, G>(seoff + (live ? u : 0) * D, sent, ga.cvk, x, r, live, ncorr, h2,
                                                 Zl + (live ? u : 0), zld);
             } else if (sloc) {
@@ -469,7 +496,8 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         fx_read(nc, false, h1);
         __syncthreads();
         // w' = w - V h1, published for the next matvec
-        slice_update(Vl, vld, nc, h1, w, ws, lo, ne, nullptr, nullptr, 0.0);
+        slice_update(Vl, vld, nc, h1, DF ? nullptr : w, ws, lo, ne, nullptr, nullptr, 0.0,
+                     DF ? reinterpret_cast<float2*>(w) : nullptr);
         __syncthreads();
         // second pass: V^T w' and ||w'||^2 in one reduction
         slice_dots(Vl, vld, nc, ws, ne, sdot, true, ctmp, ctmp2);
@@ -492,6 +520,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
                 for (int i = lane; i < nc; i += 32) a.H[(int64_t)i * a.M + j] = h1[i] + h2[i];
             if (lane == 0) {
                 s_scal[1] = brk ? 0.0 : inv;
+                if (DF) s_scaldf = df_to_float2(df_from_double(brk ? 0.0 : inv));
                 if (b == 0) {
                     a.H[(int64_t)(j + 1) * a.M + j] = beta;
                     ks->fro2 = f;
@@ -524,6 +553,7 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
                 const double hv2 =
                     lane <= nc ? fx_value(set + (size_t)lane * FX_LIMBS, lane == nc ? a.isc_n : a.isc_h) : 0.0;
                 if (lane <= nc) h2[lane] = hv2;
+                if (DF && lane < nc) h2df[lane] = df_to_float2(df_from_double(hv2));
                 __syncwarp();
                 const double hv = lane < nc ? h1[lane] + hv2 : 0.0;
                 const double part = warp_sum(hv * hv);
@@ -534,6 +564,8 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         } else {
             fx_read(nc + 1, true, h2);
             __syncthreads();
+            if (DF)
+                for (int i = threadIdx.x; i < nc; i += PT) h2df[i] = df_to_float2(df_from_double(h2[i]));
             if (wid == 0) {
                 double part = 0.0, hh = 0.0;
                 for (int i = lane; i < nc; i += 32) {
@@ -548,7 +580,8 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         const bool explicit_norm = s_flag != 0;
         if (explicit_norm) {
             // w'' in place (published), its norm through a third barrier
-            slice_update(Vl, vld, nc, h2, w, ws, lo, ne, nullptr, nullptr, 0.0);
+            slice_update(Vl, vld, nc, h2, DF ? nullptr : w, ws, lo, ne, nullptr, nullptr, 0.0,
+                         DF ? reinterpret_cast<float2*>(w) : nullptr);
             __syncthreads();
             slice_norm2(ws, ne, red, P2 + b);
             if (!barrier()) return;
@@ -568,13 +601,14 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         pscale = scale;
         ncorr = explicit_norm ? 0 : nc;
         x = w;
+        xdf = reinterpret_cast<const float2*>(w);
     }
     if (pj >= 0) pending_update();  // the last column, v_M
 }
 
 template <int D, int KP1, int G>
 void arn_launch(sgk_ctx* ctx, const sgk_op* op, const ArnArgs& a, int nb, size_t smem) {
-    auto kern = arnoldi_kernel<D, KP1, G>;
+    auto kern = a.df ? arnoldi_kernel<D, KP1, G, true> : arnoldi_kernel<D, KP1, G, false>;
     const GmvArgs<double, D> ga = make_gmv_args<double, D>(op);
     allow_max_dynamic_smem(ctx->smem_optin, kern);
     int occ = 0;

@@ -14,6 +14,7 @@
 // in that of c_{i+1}..c_{d-1} (I their extent).  Lane r of the group takes
 // entries r, r + G, ... of every row; the caller combines the lanes.
 #pragma once
+#include "sgk_df64.h"
 #include "sgk_internal.h"
 
 template <typename T, int D>
@@ -203,6 +204,54 @@ __device__ __forceinline__ double gmv_accumulate_list(const int* eo, const int2*
     for (int m = 1; m < PER; m <<= 1)
 #pragma unroll
         for (int k = 0; k + m < PER; k += 2 * m) b[k] += b[k + m];
+    return b[0];
+}
+
+// The same sum in double-float arithmetic (sgk_df64.h) from double-float
+// copies of the values (cvk2), of x and of the correction's columns and
+// coefficients: the same entries in the same virtual lanes and order, each
+// product and sum with ~48-bit significands instead of FP64 operations.
+template <int D, int G>
+__device__ __forceinline__ df64 gmv_accumulate_list_df(const int* eo, const int2* ent, const float2* __restrict__ cvk2,
+                                                       const float2* x, int r, bool live, int ncorr,
+                                                       const float2* hc, const float2* zc, int64_t zld) {
+    constexpr int VL = 8, PER = VL / G;
+    df64 b[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) b[k] = df_make(0.f, 0.f);
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int v = r + k * G;
+            df64 s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int qe = eo[i + 1];
+                int q = eo[i] + v;
+#pragma unroll 2
+                for (; q + VL < qe; q += 2 * VL) {
+                    const int2 e0 = ent[q], e1 = ent[q + VL];
+                    s0 = df_add(s0, df_mul(df_from_float2(__ldg(cvk2 + e0.y)), df_from_float2(__ldca(x + e0.x))));
+                    s1 = df_add(s1, df_mul(df_from_float2(__ldg(cvk2 + e1.y)), df_from_float2(__ldca(x + e1.x))));
+                }
+                if (q < qe) {
+                    const int2 e0 = ent[q];
+                    s0 = df_add(s0, df_mul(df_from_float2(__ldg(cvk2 + e0.y)), df_from_float2(__ldca(x + e0.x))));
+                }
+            }
+            df64 c0 = df_make(0.f, 0.f);
+            for (int c = v; c < ncorr; c += VL) c0 = df_add(c0, df_mul(df_from_float2(hc[c]), df_from_float2(zc[c * zld])));
+            b[k] = df_add(df_add(s0, s1), df_neg(c0));
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[k] = df_add(b[k], df_shfl_xor(b[k], o));
+#pragma unroll
+    for (int m = 1; m < PER; m <<= 1)
+#pragma unroll
+        for (int k = 0; k + m < PER; k += 2 * m) b[k] = df_add(b[k], b[k + m]);
     return b[0];
 }
 

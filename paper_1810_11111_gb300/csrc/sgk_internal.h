@@ -303,6 +303,7 @@ struct sgk_op {
     DevBuf<int32_t> gmv_chunk;
     DevBuf<double> gmv_cvk;  // -kappa_i S, one copy of the CSR values per direction
     DevBuf<float> gmv_cvkf;  // the same in FP32
+    DevBuf<float2> gmv_cvk2;  // the same as double-float pairs (hi, lo), hi + lo = the FP64 value to 2^-48
     int64_t madds = 0;  // multiply-adds of one matvec (entries of A on the index set, per direction)
     std::vector<int> rlen_host;  // host copy of rlen
     // bound on ||A||_2 of the sparse-grid operator: sum_i |kappa_i| max(||S||_1, ||S||_inf)
