@@ -1,7 +1,15 @@
-"""IIF2 time step with a Newton implicit stage (oracle; test infrastructure only).
+"""IIF2 and IIF3 time steps with a Newton implicit stage (oracle; test
+infrastructure only).
 
 Eq. krylov5 (IIF2):
     U^{n+1} = exp(dt A) (U^n + dt/2 F(U^n)) + dt/2 F(U^{n+1}).
+Eq. krylov6 (IIF3):
+    U^{n+1} = exp(dt A) U^n
+              + dt (5/12 F(U^{n+1}) + 2/3 exp(dt A) F(U^n) - 1/12 exp(2 dt A) F(U^{n-1})).
+Reading for IIF3: the two exp(dt A) terms are one Krylov projection of
+U^n + 2/3 dt F(U^n) (as IIF2 projects U^n + dt/2 F(U^n)), and exp(2 dt A)
+F(U^{n-1}) is a second projection with time 2 dt; the first step, which has
+no F(U^{n-1}), is an IIF2 step.
 For a system the diffusion is block diagonal across species, so exp(dt A)
 acts per species with that species' operator, one Krylov projection each.
 
@@ -128,8 +136,9 @@ class IIF2Solver:
             return [np.zeros_like(u) for u in U]
         return self.rx.F(U)
 
-    def newton(self, W):
-        dt2 = 0.5 * self.dt
+    def newton(self, W, c=None):
+        """Solve U - c F(U) = W (c = dt/2 for IIF2)."""
+        dt2 = 0.5 * self.dt if c is None else c
         U = [w.copy() for w in W]
         wnorm = float(np.sqrt(sum(float(w @ w) for w in W)))
         stop = NEWTON_TOL * max(1.0, wnorm)
@@ -181,3 +190,34 @@ class IIF2Solver:
         for _ in range(nsteps):
             U = self.step(U)
         return U
+
+
+class IIF3Solver(IIF2Solver):
+    """Sparse-grid Krylov IIF3 DG solver (eq. krylov6), IIF2 for the first step."""
+
+    def __init__(self, *args, **kw):
+        super().__init__(*args, **kw)
+        self.F_prev = None  # F(U^{n-1}) of the last step
+
+    def step(self, U):
+        dt = self.dt
+        Fn = self.F(U)
+        if self.F_prev is None:
+            Unew = super().step(U)  # computes F(U^n) again: the same values
+            self.F_prev = Fn
+            return Unew
+        W = []
+        for s in range(self.nspecies):
+            w1, m1 = krylov_expv(self.A(s), U[s] + (2.0 / 3.0) * dt * Fn[s], dt, self.M)
+            w2, m2 = krylov_expv(self.A(s), self.F_prev[s], 2.0 * dt, self.M)
+            self.stats["m_eff"] += [m1, m2]
+            W.append(w1 - (dt / 12.0) * w2)
+        self.F_prev = Fn
+        if not self.has_reaction:
+            self.stats["newton"].append(0)
+            self.stats["inner"].append(0)
+            return W
+        Unew, it, inner = self.newton(W, 5.0 / 12.0 * dt)
+        self.stats["newton"].append(it)
+        self.stats["inner"].append(inner)
+        return Unew

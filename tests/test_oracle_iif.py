@@ -12,6 +12,12 @@
   recoverable) and converge at second order.
 * Cubic reaction: the discrete L2 norm does not increase, the constant mode is
   conserved for pure periodic diffusion, and a Newton cap raises NewtonError.
+* IIF3 (eq. krylov6): F = 0 gives exp(dt A) U; for f = -b u the steps follow
+  the three-term recurrence
+  (1 + 5/12 b dt) U^{n+1} = E (1 - 2/3 b dt) U^n + 1/12 b dt E^(2) U^{n-1}
+  (E = exp(dt A), E^(2) = exp(2 dt A), dense), after an IIF2 first step; and
+  Example 4 with P2 (Table 7) agrees with the printed errors within a factor
+  2 and converges at an order above 2.4.
 """
 import os
 
@@ -21,7 +27,7 @@ import scipy.linalg as sla
 
 from oracle import iif
 from oracle.index_set import IndexSet
-from oracle.iif import IIF2Solver, NewtonError
+from oracle.iif import IIF2Solver, IIF3Solver, NewtonError
 from oracle.operator import dense_sparse_operator, sipg_1d
 from oracle.projection import project_separable
 
@@ -141,3 +147,55 @@ def test_newton_cap_raises(monkeypatch):
     sol = IIF2Solver(idx, sipg_1d(2, 1), [[1.0, 1.0]], [[(-100.0, (3,))]], 0.01, 10)
     with pytest.raises(NewtonError):
         sol.run([U], 1)
+
+
+# ------------------------------------------------------------------ IIF3 ---
+
+def test_iif3_heat_is_dense_exponential():
+    idx = IndexSet(2, 2, 1)
+    S = sipg_1d(2, 1)
+    kap = [1.0, 0.6]
+    U0 = np.random.default_rng(5).standard_normal(idx.dof)
+    U = IIF3Solver(idx, S, [kap], [[]], 0.02, idx.dof).run([U0], 3)[0]
+    ref = sla.expm(3 * 0.02 * dense_sparse_operator(idx, S, kap)) @ U0
+    assert np.linalg.norm(U - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_iif3_linear_reaction_recurrence():
+    idx = IndexSet(2, 2, 2)
+    S = sipg_1d(2, 2)
+    kap = [0.3, 0.9]
+    b, dt = 40.0, 0.01
+    U0 = np.random.default_rng(6).standard_normal(idx.dof)
+    sol = IIF3Solver(idx, S, [kap], [[(-b, (1,))]], dt, idx.dof)
+    got = sol.run([U0], 4)[0]
+    A = dense_sparse_operator(idx, S, kap)
+    E, E2 = sla.expm(dt * A), sla.expm(2 * dt * A)
+    prev, cur = U0, E @ ((1 - b * dt / 2) * U0) / (1 + b * dt / 2)  # IIF2 first step
+    for _ in range(3):
+        nxt = (E @ ((1 - 2.0 / 3.0 * b * dt) * cur) + b * dt / 12.0 * (E2 @ prev)) / (1 + 5.0 / 12.0 * b * dt)
+        prev, cur = cur, nxt
+    assert np.linalg.norm(got - cur) < 1e-11 * np.linalg.norm(cur)
+    assert sol.stats["newton"] == [1, 1, 1, 1]
+
+
+def test_example4_p2_iif3_against_table7():
+    d, a, b, c, T = 2, 1.0, 100.0, 1.0, 1.0
+    kd = 1 / (4 * d * np.pi ** 2)
+    rx = [[(-b, (1, 0)), (1.0, (0, 1))], [(-c, (0, 1))]]
+    errs = []
+    for N, dof, paper_u, paper_v in _rows("paper_example4_p2_errors.txt"):
+        N = int(N)
+        if N > 6:  # N = 7 takes ~25 s of oracle time; the order is pinned by N = 5, 6
+            continue
+        idx = IndexSet(d, N, 2)
+        assert idx.dof == dof
+        P = project_separable(idx, [1.0], [[1, 1]], [[1, 1]])
+        dt = 2.0 ** -N
+        sol = IIF3Solver(idx, sipg_1d(N, 2), [[kd * a] * d, [kd * a] * d], rx, dt, 25)
+        U = sol.run([2.0 * P, (b - c) * P], int(round(T / dt)))
+        eu = _l2_error(U[0], np.exp(-(b + a) * T) + np.exp(-(c + a) * T), P, 0.25)
+        ev = _l2_error(U[1], (b - c) * np.exp(-(c + a) * T), P, 0.25)
+        assert paper_u / 2 < eu < paper_u * 2 and paper_v / 2 < ev < paper_v * 2, (N, eu, ev)
+        errs.append(eu)
+    assert np.log2(errs[0] / errs[1]) > 2.4
