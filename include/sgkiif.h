@@ -62,6 +62,7 @@ extern "C" {
 
 /* time schemes (Section 3) */
 #define SGK_IIF2 2         /* eq. krylov5 */
+#define SGK_IIF3 3         /* eq. krylov6 */
 
 #define SGK_MAX_DIM 6
 #define SGK_MAX_LEVEL 12
@@ -183,9 +184,12 @@ typedef struct sgk_newton_opts {
     int gmres_restart; /* GMRES restart length (systems); 50 */
 } sgk_newton_opts;
 
-/* Create an IIF solver (scheme SGK_IIF2, eq. krylov5) for nspecies species on
- * one index set; ops[s] is the diffusion operator of species s (all on the
- * same index set).  krylov_m in [1, 128], dt > 0.  The reaction term uses
+/* Create an IIF solver for nspecies species on one index set: scheme
+ * SGK_IIF2 (eq. krylov5) or SGK_IIF3 (eq. krylov6: exp(dt A) applied to
+ * U^n + 2/3 dt F(U^n) in one Krylov projection, exp(2 dt A) F(U^{n-1}) in a
+ * second, Newton weight 5/12 dt; the first step after creation or
+ * sgk_solver_set_state has no F(U^{n-1}) and is an IIF2 step).  ops[s] is the
+ * diffusion operator of species s (all on the same index set).  krylov_m in [1, 128], dt > 0.  The reaction term uses
  * finest-mesh Gauss quadrature with q = ceil((p k + k + 1)/2) points per
  * direction for total polynomial degree p, i.e. the exact L2 projection of
  * f(u_h).  The finest full grid must fit in device memory

@@ -331,7 +331,8 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
     *out = nullptr;
     return guarded(ctx, [&]() {
         SGK_REQUIRE(nspecies >= 1 && nspecies <= SGK_MAX_SPECIES, SGK_EINVAL, "nspecies must be in [1, 4]");
-        SGK_REQUIRE(scheme == SGK_IIF2, SGK_EUNSUPPORTED, "only SGK_IIF2 is implemented");
+        SGK_REQUIRE(scheme == SGK_IIF2 || scheme == SGK_IIF3, SGK_EUNSUPPORTED,
+                    "scheme must be SGK_IIF2 or SGK_IIF3");
         SGK_REQUIRE(krylov_m >= 1 && krylov_m <= SGK_MAX_KRYLOV, SGK_EINVAL, "krylov_m must be in [1, 128]");
         SGK_REQUIRE(dt > 0 && std::isfinite(dt), SGK_EINVAL, "dt must be positive");
         const sgk_index* idx = nullptr;
@@ -349,6 +350,8 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
         for (int i = 0; i < nspecies; ++i) s->ops[i] = ops[i];
         s->M = krylov_m;
         s->dt = dt;
+        s->scheme = scheme;
+        s->newton_c = 0.5 * dt;
         s->prec = ctx->precision;
         s->n = idx->dof;
         s->rx.nspecies = nspecies;

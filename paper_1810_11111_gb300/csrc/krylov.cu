@@ -852,7 +852,8 @@ __global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
         for (int i = threadIdx.x; i < m; i += XTH) y[i] = xs[cur * mm + i * m];
 }
 
-// W = gamma V[:, :m_eff] y  (FP64 accumulation)
+// W = gamma V[:, :m_eff] y  (FP64 accumulation, four chains over the
+// columns: FP64 dependent latency is long on this part)
 template <typename T>
 __global__ void combine_kernel(const T* __restrict__ V, long long ldv, const KrylovScalars* __restrict__ ks,
                                const double* __restrict__ y, double* __restrict__ W, long long n) {
@@ -862,10 +863,23 @@ __global__ void combine_kernel(const T* __restrict__ V, long long ldv, const Kry
     for (int c = threadIdx.x; c < m; c += blockDim.x) ys[c] = y[c] * g;
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < m; ++c) acc += (double)V[c * ldv + i] * ys[c];
-        W[i] = acc;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 3 < m; c += 4) {
+            a0 += (double)V[c * ldv + i] * ys[c];
+            a1 += (double)V[(c + 1) * ldv + i] * ys[c + 1];
+            a2 += (double)V[(c + 2) * ldv + i] * ys[c + 2];
+            a3 += (double)V[(c + 3) * ldv + i] * ys[c + 3];
+        }
+        for (; c < m; ++c) a0 += (double)V[c * ldv + i] * ys[c];
+        W[i] = (a0 + a1) + (a2 + a3);
     }
+}
+
+// blocks of 128 threads for the combination: at least one per SM
+int combine_grid(const sgk_ctx* ctx, long long n) {
+    const long long b = (n + 127) / 128;
+    return (int)std::max(1LL, std::min<long long>(b, (long long)ctx->num_sms * 8));
 }
 
 // ------------------------------------------------------ vector kernels ---
@@ -1208,7 +1222,7 @@ void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork
     expm_e1(ctx, kw.H, M, &kw.ks->m_eff, 0, dt, kw.expm_ws, kw.y);
     {
         KTimer kt(ctx, KC_VECTOR);
-        combine_kernel<double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
+        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
     }
     check_launch("combine");
     count_launch(ctx);
@@ -1260,7 +1274,7 @@ void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<
     expm_e1(ctx, kw.H, M, &ks->m_eff, 0, dt, kw.expm_ws, kw.y);
     {
         KTimer kt(ctx, KC_VECTOR);
-        combine_kernel<T><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(kw.V, n, ks, kw.y, W, n);
+        combine_kernel<T><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, ks, kw.y, W, n);
     }
     check_launch("combine");
     count_launch(ctx);

@@ -328,9 +328,12 @@ __device__ __forceinline__ void bwd_subtree(T* Mb, T* Y, int f, int j, int Lhi, 
     }
 }
 
+// Register limit per element type: 128 for FP32 (eight 64-thread CTAs per
+// SM, no spills; a 96-register cap with spills measured slower), the
+// architectural 255 for FP64 (its cell loops need them).
 template <typename T, int D, int KP1, int Q, int S, bool JAC>
-__global__ void __launch_bounds__(256) pencil_kernel(const PencilArgs args, const QuadTab<T> tb,
-                                                     const Filt<T, KP1> F, const Poly<T, S> poly) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? 128 : 255)
+    pencil_kernel(const PencilArgs args, const QuadTab<T> tb, const Filt<T, KP1> F, const Poly<T, S> poly) {
     constexpr int P = Pow<KP1, D - 1>::v;  // fibers per species and set
     constexpr int PS = P | 1;              // odd fiber stride in shared memory
     constexpr int NC = Pow<KP1, D>::v;     // coefficients per cell

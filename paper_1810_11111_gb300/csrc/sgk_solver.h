@@ -20,6 +20,12 @@ struct sgk_solver {
     bool has_rx = false;
     int M = 0;
     double dt = 0.0;
+    int scheme = SGK_IIF2;
+    double newton_c = 0.0;  // c of the implicit stage U - c F(U) = W (dt/2 IIF2, 5/12 dt IIF3)
+    // IIF3: F(U^{n-1}) of the last step (valid when have_fprev), the staged
+    // F(U^n) of the running step, and exp(2 dt A) F(U^{n-1})
+    DevBuf<double> Fprev, Fstage, W2;
+    bool have_fprev = false;
     sgk_newton_opts opts{};
     int prec = SGK_FP64;
     long long n = 0;  // dof per species
@@ -49,7 +55,7 @@ struct sgk_solver {
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     bool use_graphs = true;
-    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
+    GraphCache g_krylov[SGK_MAX_SPECIES], g_krylov2[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
     // Fv holds F(U) for the current U (a host-driven or device-driven step
     // ended with an accepted residual evaluation there); cleared whenever U
     // changes otherwise
@@ -85,4 +91,4 @@ int solver_step_finish(sgk_solver* s);
 int solver_step(sgk_solver* s, int nsteps);
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);
-void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W);
+void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau = -1.0);

@@ -442,7 +442,7 @@ void evalF(sgk_solver* s, const double* U, double* F) {
 // q = p - dt/2 J_F(U) p (stacked FP64); with pq also pq = p.q
 void apply_newton_matrix(sgk_solver* s, const double* pv, double* q, double* pq = nullptr) {
     const long long N = s->n * s->nspecies;
-    const double c = 0.5 * s->dt;
+    const double c = s->newton_c;
     double* const part = s->partials.p;
     unsigned* const cnt = s->fcnt.p + FC_JAC;
     if (s->prec == SGK_FP64) {
@@ -560,7 +560,7 @@ void gmres_solve_host(sgk_solver* s, const double* G, double* x, int& iters) {
 int newton(sgk_solver* s) {
     sgk_ctx* ctx = s->ctx;
     const long long N = s->n * s->nspecies;
-    const double dt2 = 0.5 * s->dt;
+    const double dt2 = s->newton_c;
     SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p, s->fcnt.p + FC_NORM,
                  s->scal.p + 6, (StepCtl*)nullptr, 0.0);
@@ -621,7 +621,9 @@ void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, doub
     s->unod_valid = false;
 }
 
-void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) {
+// W = exp(tau A_s) v by the Krylov projection (tau < 0: tau = dt)
+void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau) {
+    if (tau < 0.0) tau = s->dt;
     const sgk_op* op = s->ops[species];
     const long long n = s->n;
     // FP64 in both precision modes: an FP32 matvec inside Arnoldi costs a few
@@ -636,10 +638,10 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W) 
         pw.bounds = s->abounds.p;
         pw.E = s->aE;
         pw.list_ent = s->alist;
-        krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, s->dt);
+        krylov_expv_persistent(s->ctx, op, pw, krylov_work<double>(s, species), v, W, n, s->M, tau);
     } else {
         auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
-        krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, s->dt);
+        krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, tau);
     }
     if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
 }
@@ -702,7 +704,9 @@ void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
     capture_cond(ctx, aux, cudaGraphCondTypeWhile, pre, body);
 }
 
-bool step_graph_eligible(const sgk_solver* s) { return s->use_graphs && (!s->has_rx || s->nspecies == 1); }
+bool step_graph_eligible(const sgk_solver* s) {
+    return s->use_graphs && s->scheme == SGK_IIF2 && (!s->has_rx || s->nspecies == 1);
+}
 
 void build_step_graph(sgk_solver* s) {
     sgk_ctx* ctx = s->ctx;
@@ -878,6 +882,7 @@ bool solver_device_steps(const sgk_solver* s) { return step_graph_eligible(s) &&
 
 void solver_set_state(sgk_solver* s, int species, const double* src_dev) {
     const long long n = s->n;
+    s->have_fprev = false;  // a new state has no F(U^{n-1}): IIF3 restarts with an IIF2 step
     if (s->has_rx && s->ctl.p) {
         // the device keeps the cached F(U) when the new state equals the old
         set_state_kernel<<<reduction_blocks(s->ctx, n), RED_THREADS, 0, s->ctx->stream>>>(
@@ -915,16 +920,32 @@ int solver_step(sgk_solver* s, int nsteps) {
         return SGK_OK;
     }
     const long long n = s->n, N = n * s->nspecies;
-    const double dt2 = 0.5 * s->dt;
+    // restores the solver's graph setting when a step ends, however it ends
+    struct GraphsSetting {
+        sgk_solver* s;
+        bool v;
+        ~GraphsSetting() { s->use_graphs = v; }
+    };
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        // IIF3 from its second step (eq. krylov6): W = exp(dt A)(U^n + 2/3 dt
+        // F(U^n)) - dt/12 exp(2 dt A) F(U^{n-1}) and the weight 5/12 dt;
+        // otherwise (IIF2, or IIF3 without F(U^{n-1})) W = exp(dt A)(U^n + dt/2
+        // F(U^n)) and dt/2.  The graph caches of an IIF3 solver hold the IIF3
+        // weights, so its IIF2 start runs without them.
+        const bool iif3 = s->scheme == SGK_IIF3 && s->has_rx;
+        const bool third = iif3 && s->have_fprev;
+        const double cpred = third ? 2.0 / 3.0 * s->dt : 0.5 * s->dt;
+        s->newton_c = third ? 5.0 / 12.0 * s->dt : 0.5 * s->dt;
+        GraphsSetting keep{s, s->use_graphs};
+        if (iif3 && !third) s->use_graphs = false;
         // F(U^n) for the predictor, unless the last step left it in Fv; the
         // device-side flag of the step graph is stale after a host-driven step
         const bool have_f = s->fv_valid;
         run_graph(s, have_f ? s->g_pred_f : s->g_pred, KC_VECTOR, [&]() {
             if (s->has_rx) {
                 if (!have_f) evalF(s, s->U.p, s->Fv.p);
-                vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
+                vk_axpby(ctx, 1.0, s->U.p, cpred, s->Fv.p, s->vv.p, N);
             } else {
                 SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
                                                ctx->stream));
@@ -935,6 +956,18 @@ int solver_step(sgk_solver* s, int nsteps) {
                       [&]() { solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n); });
             s->stats.krylov_calls += s->use_graphs ? 1 : 0;
         }
+        if (third)
+            for (int sp = 0; sp < s->nspecies; ++sp) {
+                run_graph(s, s->g_krylov2[sp], KC_KRYLOV, [&]() {
+                    solver_krylov_expv(s, sp, s->Fprev.p + sp * n, s->W2.p + sp * n, 2.0 * s->dt);
+                    vk_axpby(ctx, 1.0, s->W.p + sp * n, -s->dt / 12.0, s->W2.p + sp * n, s->W.p + sp * n, n);
+                });
+                s->stats.krylov_calls += s->use_graphs ? 1 : 0;
+            }
+        // F(U^n) becomes F(U^{n-1}) of the next step if this one succeeds
+        if (iif3)
+            SGK_CUDA_CHECK(
+                cudaMemcpyAsync(s->Fstage.p, s->Fv.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         int rc = SGK_OK;
         if (!s->has_rx) {
             SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -969,6 +1002,11 @@ int solver_step(sgk_solver* s, int nsteps) {
             return rc;
         }
         s->stats.steps += 1;
+        if (iif3) {
+            SGK_CUDA_CHECK(
+                cudaMemcpyAsync(s->Fprev.p, s->Fstage.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+            s->have_fprev = true;
+        }
         // newton() returns OK right after the residual evaluation at the final
         // U; the step graph's flag says the same
         if (s->has_rx) {
@@ -988,6 +1026,11 @@ void solver_alloc(sgk_solver* s) {
     s->Uprev.alloc(N);
     s->W.alloc(N);
     s->vv.alloc(N);
+    if (s->scheme == SGK_IIF3) {
+        s->Fprev.alloc(N);
+        s->Fstage.alloc(N);
+        s->W2.alloc(N);
+    }
     SGK_CUDA_CHECK(cudaMemsetAsync(s->U.p, 0, N * sizeof(double), s->ctx->stream));
     // the fused Gram-Schmidt kernels read whole 128-element slices (past n in
     // the last one, multiplied by zero): pad the basis and keep it finite
@@ -1074,6 +1117,8 @@ sgk_solver::~sgk_solver() {
         if (a) cudaStreamDestroy(a);
     for (GraphCache* g : {&g_pred, &g_pred_f, &g_resid, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (auto& g : g_krylov2)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& g : g_krylov)
         if (g.exec) cudaGraphExecDestroy(g.exec);
 }

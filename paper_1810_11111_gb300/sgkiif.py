@@ -15,6 +15,7 @@ SGK_OK, SGK_EINVAL, SGK_ENOMEM, SGK_EUNSUPPORTED, SGK_ENEWTON, SGK_ETIMEOUT, SGK
 SGK_FP64, SGK_MIXED = 0, 1
 SGK_PERIODIC, SGK_DIRICHLET0 = 0, 1
 SGK_IIF2 = 2
+SGK_IIF3 = 3
 MAX_SPECIES = 4
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsgkiif.so")
@@ -277,7 +278,7 @@ def reaction_struct(terms, nspecies):
 
 
 class Solver:
-    def __init__(self, ctx, ops, reaction_terms, krylov_m, dt, opts=None):
+    def __init__(self, ctx, ops, reaction_terms, krylov_m, dt, opts=None, scheme=SGK_IIF2):
         self.ctx, self.ops = ctx, list(ops)
         self.nspecies = len(self.ops)
         self.dof = self.ops[0].idx.dof
@@ -288,7 +289,7 @@ class Solver:
             o = sgk_newton_opts(opts.get("tol", 0.0), opts.get("max_iter", 0), opts.get("inner_tol", 0.0),
                                 opts.get("inner_max", 0), opts.get("gmres_restart", 0))
         self.h = _P()
-        ctx.check(sgk_solver_create(ctx.h, self.nspecies, arr, ctypes.byref(self._rx), SGK_IIF2, int(krylov_m),
+        ctx.check(sgk_solver_create(ctx.h, self.nspecies, arr, ctypes.byref(self._rx), int(scheme), int(krylov_m),
                                     float(dt), ctypes.byref(o) if o else None, ctypes.byref(self.h)))
 
     def set_state(self, species, coeffs=None, dev_ptr=None):

@@ -21,7 +21,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle.iif import IIF2Solver  # noqa: E402
+from oracle.iif import IIF2Solver, IIF3Solver  # noqa: E402
 from oracle.index_set import IndexSet as OIndex  # noqa: E402
 from oracle.krylov import expm_pade13, krylov_expv  # noqa: E402
 from oracle.operator import DIRICHLET0, PERIODIC, sipg_1d, sparse_matvec  # noqa: E402
@@ -407,6 +407,34 @@ def test_iif2_steps_match_oracle(name, cfg, nsteps, precision):
         assert rel(got[s], want[s]) <= tol, (name, s, rel(got[s], want[s]))
     stats = prob.solver.stats()
     assert stats["steps"] == nsteps
+    prob.close()
+
+
+@pytest.mark.parametrize("name,cfg,nsteps", [STEP_CASES[0], STEP_CASES[1], STEP_CASES[2]])
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_iif3_steps_match_oracle(name, cfg, nsteps, precision):
+    # eq. krylov6: an IIF2 first step, then IIF3 steps (two Krylov
+    # projections, one over 2 dt, Newton weight 5/12 dt); the scalar case
+    # takes the CG path, the two-species case GMRES
+    cfg = dict(cfg, scheme=sgkiif.SGK_IIF3)
+    nsteps = max(nsteps, 4)
+    prob = Problem(cfg, precision)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(nsteps)
+    got = prob.state()
+    idx = OIndex(cfg["d"], cfg["n"], cfg["k"])
+    want = IIF3Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"],
+                      cfg["M"]).run(U0, nsteps)
+    tol = 1e-10 if precision == sgkiif.SGK_FP64 else 1e-6
+    for s in range(len(want)):
+        assert rel(got[s], want[s]) <= tol, (name, s, rel(got[s], want[s]))
+    assert prob.solver.stats()["steps"] == nsteps
+    # a new state restarts with an IIF2 step: the same steps again give the same state
+    prob.reset()
+    prob.solver.step(nsteps)
+    for s in range(len(want)):
+        assert rel(prob.state()[s], got[s]) <= 1e-13
     prob.close()
 
 
