@@ -13,6 +13,13 @@ no F(U^{n-1}), is an IIF2 step.
 For a system the diffusion is block diagonal across species, so exp(dt A)
 acts per species with that species' operator, one Krylov projection each.
 
+Source terms (Examples 2 and 3): the equation u_t = k Lap u + f(u) + s(x, t)
+puts the projection of s(., t) into F, so F(U, t) = P f(u_h) + P s(., t).
+Every source used here is a sum of terms e^{lambda t} g(x) with g separable,
+so P s(., t) = sum_m e^{lambda_m t} S_m with S_m = P g_m fixed vectors.  In
+both schemes every F is taken at the time of its argument: F(U^n) at t^n,
+F(U^{n+1}) (the Newton stage) at t^{n+1} = t^n + dt, F(U^{n-1}) at t^{n-1}.
+
 The implicit stage G(U) = U - dt/2 F(U) - W = 0 (W the exponential term) is
 solved by Newton's method, as Example 3 and Section 5 state.  Readings where
 the paper is silent:
@@ -118,26 +125,41 @@ def gmres(apply, b, tol=INNER_TOL, maxit=INNER_MAX, restart=GMRES_RESTART):
 class IIF2Solver:
     """Sparse-grid Krylov IIF2 DG solver (Sections 2-3)."""
 
-    def __init__(self, idx, S, kappas, reaction, dt, M):
-        """S: 1D SIPG matrix; kappas: per species, a length-d diagonal."""
+    def __init__(self, idx, S, kappas, reaction, dt, M, sources=None, t0=0.0):
+        """S: 1D SIPG matrix; kappas: per species, a length-d diagonal;
+        sources: per species a list of (lambda, S_m) pairs (the source
+        P s(., t) = sum_m e^{lambda t} S_m), or None; t0: the time of the
+        state passed to run()."""
         self.idx, self.S, self.dt, self.M = idx, S, dt, M
         self.kappas = [np.asarray(k, dtype=np.float64) for k in kappas]
         self.nspecies = len(self.kappas)
         self.reaction = reaction
         self.has_reaction = any(len(t) for t in reaction)
         self.rx = Reaction(idx, reaction) if self.has_reaction else None
+        self.sources = sources if sources is not None else [[] for _ in range(self.nspecies)]
+        self.has_source = any(len(t) for t in self.sources)
+        self.has_F = self.has_reaction or self.has_source
+        self.t = float(t0)
         self.stats = {"newton": [], "inner": [], "m_eff": []}
 
     def A(self, s):
         return lambda x: sparse_matvec(self.idx, self.S, self.kappas[s], x)
 
-    def F(self, U):
+    def F(self, U, t):
+        """F(U, t) = P f(u_h) + P s(., t)."""
+        out = self.rx.F(U) if self.has_reaction else [np.zeros_like(u) for u in U]
+        for s in range(self.nspecies):
+            for lam, Sm in self.sources[s]:
+                out[s] = out[s] + np.exp(lam * t) * Sm
+        return out
+
+    def J(self, U, xs):
         if not self.has_reaction:
-            return [np.zeros_like(u) for u in U]
-        return self.rx.F(U)
+            return [np.zeros_like(x) for x in xs]
+        return self.rx.J(U, xs)
 
     def newton(self, W, c=None):
-        """Solve U - c F(U) = W (c = dt/2 for IIF2)."""
+        """Solve U - c F(U, t^{n+1}) = W (c = dt/2 for IIF2)."""
         dt2 = 0.5 * self.dt if c is None else c
         U = [w.copy() for w in W]
         wnorm = float(np.sqrt(sum(float(w @ w) for w in W)))
@@ -145,7 +167,7 @@ class IIF2Solver:
         n = self.idx.dof
         inner_total = 0
         for it in range(NEWTON_MAX + 1):
-            Fu = self.F(U)
+            Fu = self.F(U, self.t + self.dt)
             G = np.concatenate([U[s] - dt2 * Fu[s] - W[s] for s in range(self.nspecies)])
             if float(np.linalg.norm(G)) <= stop:
                 return U, it, inner_total
@@ -154,7 +176,7 @@ class IIF2Solver:
 
             def apply(x):
                 xs = [x[s * n:(s + 1) * n] for s in range(self.nspecies)]
-                Jx = self.rx.J(U, xs)
+                Jx = self.J(U, xs)
                 return np.concatenate([xs[s] - dt2 * Jx[s] for s in range(self.nspecies)])
 
             if self.nspecies == 1:
@@ -169,20 +191,24 @@ class IIF2Solver:
     def step(self, U):
         """One IIF2 step (eq. krylov5); U is a list of per-species vectors."""
         dt2 = 0.5 * self.dt
-        Fn = self.F(U)
+        Fn = self.F(U, self.t)
         W = []
         for s in range(self.nspecies):
             v = U[s] + dt2 * Fn[s]
             w, m_eff = krylov_expv(self.A(s), v, self.dt, self.M)
             self.stats["m_eff"].append(m_eff)
             W.append(w)
-        if not self.has_reaction:
-            self.stats["newton"].append(0)
-            self.stats["inner"].append(0)
-            return W
-        Unew, it, inner = self.newton(W)
+        return self.finish(W, dt2)
+
+    def finish(self, W, c):
+        """The implicit stage of a step whose exponential term is W; advances t."""
+        if not self.has_F:
+            Unew, it, inner = W, 0, 0
+        else:
+            Unew, it, inner = self.newton(W, c)
         self.stats["newton"].append(it)
         self.stats["inner"].append(inner)
+        self.t += self.dt
         return Unew
 
     def run(self, U, nsteps):
@@ -201,7 +227,7 @@ class IIF3Solver(IIF2Solver):
 
     def step(self, U):
         dt = self.dt
-        Fn = self.F(U)
+        Fn = self.F(U, self.t)
         if self.F_prev is None:
             Unew = super().step(U)  # computes F(U^n) again: the same values
             self.F_prev = Fn
@@ -213,11 +239,4 @@ class IIF3Solver(IIF2Solver):
             self.stats["m_eff"] += [m1, m2]
             W.append(w1 - (dt / 12.0) * w2)
         self.F_prev = Fn
-        if not self.has_reaction:
-            self.stats["newton"].append(0)
-            self.stats["inner"].append(0)
-            return W
-        Unew, it, inner = self.newton(W, 5.0 / 12.0 * dt)
-        self.stats["newton"].append(it)
-        self.stats["inner"].append(inner)
-        return Unew
+        return self.finish(W, 5.0 / 12.0 * dt)

@@ -12,6 +12,11 @@
   recoverable) and converge at second order.
 * Cubic reaction: the discrete L2 norm does not increase, the constant mode is
   conserved for pure periodic diffusion, and a Newton cap raises NewtonError.
+* Sources (Examples 2 and 3): for f = -b u plus a source e^{lambda t} S the
+  IIF2 and IIF3 steps follow their closed-form recurrences with every F taken
+  at the time of its argument (dense expm); Example 2 (periodic, f = u) and
+  Example 3 (zero Dirichlet, f = u^2, Newton) agree with Tables 5 and 6 (P1
+  with IIF2, P2 with IIF3) within a factor 2 and converge at order.
 * IIF3 (eq. krylov6): F = 0 gives exp(dt A) U; for f = -b u the steps follow
   the three-term recurrence
   (1 + 5/12 b dt) U^{n+1} = E (1 - 2/3 b dt) U^n + 1/12 b dt E^(2) U^{n-1}
@@ -28,7 +33,7 @@ import scipy.linalg as sla
 from oracle import iif
 from oracle.index_set import IndexSet
 from oracle.iif import IIF2Solver, IIF3Solver, NewtonError
-from oracle.operator import dense_sparse_operator, sipg_1d
+from oracle.operator import DIRICHLET0, PERIODIC, dense_sparse_operator, sipg_1d
 from oracle.projection import project_separable
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -199,3 +204,97 @@ def test_example4_p2_iif3_against_table7():
         assert paper_u / 2 < eu < paper_u * 2 and paper_v / 2 < ev < paper_v * 2, (N, eu, ev)
         errs.append(eu)
     assert np.log2(errs[0] / errs[1]) > 2.4
+
+
+# --------------------------------------------------------------- sources ---
+
+def test_linear_reaction_with_source_closed_form():
+    # f = -b u, source e^{lam t} S from t0: IIF2 gives
+    # (1 + b dt/2) U^{n+1} = E((1 - b dt/2) U^n + dt/2 e^{lam t_n} S) + dt/2 e^{lam t_{n+1}} S
+    idx = IndexSet(2, 2, 2)
+    S1 = sipg_1d(2, 2)
+    kap = [0.3, 0.9]
+    b, lam, dt, t0 = 40.0, -1.7, 0.01, 0.3
+    rng = np.random.default_rng(7)
+    U0, Sv = rng.standard_normal(idx.dof), rng.standard_normal(idx.dof)
+    sol = IIF2Solver(idx, S1, [kap], [[(-b, (1,))]], dt, idx.dof, sources=[[(lam, Sv)]], t0=t0)
+    got = sol.run([U0], 3)[0]
+    E = sla.expm(dt * dense_sparse_operator(idx, S1, kap))
+    U, t = U0, t0
+    for _ in range(3):
+        U = (E @ ((1 - b * dt / 2) * U + dt / 2 * np.exp(lam * t) * Sv)
+             + dt / 2 * np.exp(lam * (t + dt)) * Sv) / (1 + b * dt / 2)
+        t += dt
+    assert np.linalg.norm(got - U) < 1e-11 * np.linalg.norm(U)
+    assert abs(sol.t - (t0 + 3 * dt)) < 1e-15
+
+
+def test_iif3_source_recurrence():
+    idx = IndexSet(2, 2, 1)
+    S1 = sipg_1d(2, 1)
+    kap = [0.7, 0.2]
+    b, lam, dt = 25.0, -2.0, 0.02
+    rng = np.random.default_rng(8)
+    U0, Sv = rng.standard_normal(idx.dof), rng.standard_normal(idx.dof)
+    sol = IIF3Solver(idx, S1, [kap], [[(-b, (1,))]], dt, idx.dof, sources=[[(lam, Sv)]])
+    got = sol.run([U0], 4)[0]
+    A = dense_sparse_operator(idx, S1, kap)
+    E, E2 = sla.expm(dt * A), sla.expm(2 * dt * A)
+
+    def F(U, t):
+        return -b * U + np.exp(lam * t) * Sv
+
+    prev = U0
+    cur = (E @ (U0 + dt / 2 * F(U0, 0.0)) + dt / 2 * np.exp(lam * dt) * Sv) / (1 + b * dt / 2)
+    for n in range(1, 4):
+        t = n * dt
+        rhs = E @ (cur + 2.0 / 3.0 * dt * F(cur, t)) - dt / 12.0 * (E2 @ F(prev, t - dt)) \
+            + 5.0 / 12.0 * dt * np.exp(lam * (t + dt)) * Sv
+        prev, cur = cur, rhs / (1 + 5.0 / 12.0 * b * dt)
+    assert np.linalg.norm(got - cur) < 1e-11 * np.linalg.norm(cur)
+
+
+def _sin_product_squared(idx):
+    """P prod sin^2(2 pi x_i), expanded as prod (1/2 - 1/2 cos(4 pi x_i))."""
+    d = idx.d
+    amps, wns = [], []
+    for mask in range(1 << d):
+        amps.append(0.5 ** d * (-1) ** bin(mask).count("1"))
+        wns.append([2 if (mask >> i) & 1 else 0 for i in range(d)])
+    return project_separable(idx, amps, wns, [[1] * d] * len(amps))
+
+
+def _examples23(golden, nonlinear):
+    rows = [r for r in _rows(golden) if r[0] == 2]
+    for degree, nmax, min_order in ((1, 6, 1.8), (2, 5, 2.4)):
+        errs = []
+        for d, k, N, dof, T, paper in rows:
+            d, k, N = int(d), int(k), int(N)
+            if k != degree or N < nmax - 2 or N > nmax:
+                continue
+            idx = IndexSet(d, N, k)
+            assert idx.dof == dof
+            P = project_separable(idx, [1.0], [[1] * d], [[0] * d])
+            kd = 1 / (4 * d * np.pi ** 2)
+            if nonlinear:
+                rx, src, bc = [[(1.0, (2,))]], [[(-2.0, -_sin_product_squared(idx))]], DIRICHLET0
+            else:
+                rx, src, bc = [[(1.0, (1,))]], [[(-1.0, -P)]], PERIODIC
+            dt = 2.0 ** -N
+            cls = IIF2Solver if k == 1 else IIF3Solver
+            sol = cls(idx, sipg_1d(N, k, bc), [[kd] * d], rx, dt, 25, sources=src)
+            U = sol.run([P], int(round(T / dt)))[0]
+            e = _l2_error(U, np.exp(-T), P, 0.5 ** d)
+            assert paper / 2 < e < paper * 2, (k, N, e, paper)
+            errs.append(e)
+        assert len(errs) == 3
+        for e0, e1 in zip(errs, errs[1:]):
+            assert np.log2(e0 / e1) > min_order, errs
+
+
+def test_example2_against_table5():
+    _examples23("paper_example2_errors.txt", nonlinear=False)
+
+
+def test_example3_against_table6():
+    _examples23("paper_example3_errors.txt", nonlinear=True)
