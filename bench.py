@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=32,
                     help="instances of the batched leg (0 skips it)")
     ap.add_argument("--no-matvec", action="store_true", help="skip the large stand-alone matvec leg")
+    ap.add_argument("--no-iif3", action="store_true", help="skip the IIF3 leg")
     return ap.parse_args()
 
 
@@ -133,8 +134,9 @@ def layout_sizes(d, n, k):
 # level, degree, precision): profiles/pencil_kernel_cubic3d_l6k2_fp32.md
 PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56661504 + 68608}
 # one persistent Arnoldi launch (one exponential), keyed by (d, level,
-# degree, M): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md
-ARNOLDI_TRAFFIC = {(3, 6, 2, 30): 6492160 + 83712}
+# degree, M, precision): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md (the
+# mixed-precision variant, double-float gather)
+ARNOLDI_TRAFFIC = {(3, 6, 2, 30, "mixed"): 6503168 + 59392}
 
 
 def pencil_q(cfg):
@@ -333,7 +335,7 @@ def native(args, rank, world, local_rank):
                             hbm_view={"achieved_gbs": nl * bytes_algo / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
                                       "frac": nl * bytes_algo / t / 1e9 / peaks["hbm_gbs"],
                                       "peak_source": peak_kind},
-                            traffic=ARNOLDI_TRAFFIC.get((d, N, cfg["k"], cfg["M"])),
+                            traffic=ARNOLDI_TRAFFIC.get((d, N, cfg["k"], cfg["M"], args.precision)),
                             traffic_note="dram read + write of one launch, ncu cold capture "
                                          "(profiles/arnoldi_kernel_cubic3d_l6k2_m30.md); null when no capture "
                                          "of the current kernel exists")
@@ -375,6 +377,8 @@ def native(args, rank, world, local_rank):
     prob.close()
     if world == 1 and not args.no_matvec:
         out["matvec"] = matvec_leg(peaks, peak_kind)
+    if world == 1 and not args.no_iif3:
+        out["iif3"] = iif3_leg(cfg, args)
     if world == 1 and args.batch_instances > 0:
         out["batched"] = batched_leg(args)
     if world == 1 and args.served_requests > 0:
@@ -383,6 +387,49 @@ def native(args, rank, world, local_rank):
         out["cpu_baseline"] = cpu_baseline(cfg)
     if dist is not None:
         dist.destroy_process_group()
+    return out
+
+
+# ------------------------------------------------------------- IIF3 leg ---
+
+def iif3_leg(cfg, args):
+    """The same workload stepped with IIF3 (eq. krylov6: a second Krylov
+    projection over 2 dt per step, Newton weight 5/12 dt; the first step is
+    IIF2), in mixed precision, device-timed over K steps from the initial
+    state with the L2 flushed before each, and its distance to the FP64
+    IIF3 path after those steps.  IIF3 steps are host-driven (one graph per
+    phase instead of one per step)."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif
+    from paper_1810_11111_gb300.runner import Problem
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    c3 = dict(cfg, scheme=sgkiif.SGK_IIF3)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {"workload": "as the headline, scheme IIF3", "steps": args.steps}
+    states = {}
+    for name, prec in (("mixed", sgkiif.SGK_MIXED), ("fp64", sgkiif.SGK_FP64)):
+        prob = Problem(c3, prec)
+        prob.reset()
+        prob.solver.step(2)  # graph capture of every phase outside the timing
+        prob.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0.record(stream)
+            prob.solver.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        states[name] = prob.state()
+        out[name] = {"ms_per_step": tot / args.steps,
+                     "dof_steps_per_s": prob.dof * prob.nspecies * args.steps / (tot / 1e3)}
+        prob.close()
+    num = sum(float(np.sum((states["mixed"][s] - states["fp64"][s]) ** 2)) for s in range(len(states["fp64"])))
+    den = sum(float(np.sum(states["fp64"][s] ** 2)) for s in range(len(states["fp64"])))
+    out["rel_l2_mixed_vs_fp64"] = float(np.sqrt(num / den))
     return out
 
 

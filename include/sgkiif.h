@@ -67,6 +67,7 @@ extern "C" {
 #define SGK_MAX_DIM 6
 #define SGK_MAX_LEVEL 12
 #define SGK_MAX_SPECIES 4
+#define SGK_MAX_SOURCE_TERMS 8
 #define SGK_MAX_KRYLOV 128
 
 typedef struct sgk_ctx sgk_ctx;
@@ -201,13 +202,35 @@ int sgk_solver_destroy(sgk_solver* s);
 /* Set the coefficients of one species (FP64, dof elements) from host memory
  * (on_device = 0) or from a device array (on_device = 1). */
 int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int on_device);
-/* Take nsteps IIF2 steps.  Arnoldi breakdown truncates the Krylov basis and
+/* Take nsteps steps of the solver's scheme.  Arnoldi breakdown truncates the Krylov basis and
  * is not an error.  On Newton failure the state is rolled back to the start
  * of the failing step and SGK_ENEWTON is returned.  Synchronises. */
 int sgk_solver_step(sgk_solver* s, int nsteps);
 /* Copy one species' coefficients (FP64) to host (on_device = 0) or to a
  * device array (on_device = 1); cap >= dof.  Host copies synchronise. */
 int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t cap, int on_device);
+
+/* Source term of species s for u_t = div(k grad u) + f(u) + s(x, t)
+ * (Examples 2 and 3, Section 4), given as nterms terms e^{lambda_m t} g_m(x):
+ * the scheme's F becomes F(U, t) = P f(u_h) + sum_m e^{lambda_m t} S_m with
+ * S_m = P g_m, the caller's projected coefficient vectors (for separable g_m
+ * from sgk_project_separable).  Every F is taken at the time of its argument:
+ * F(U^n) at t^n, the Newton stage F(U^{n+1}) at t^n + dt, and IIF3's
+ * F(U^{n-1}) at t^n - dt.
+ * lambda: host array of nterms finite values.  coeffs_dev: device array of
+ * nterms * dof FP64 values, term m at offset m * dof; the solver copies it
+ * (the caller keeps ownership).  nterms = 0 removes the species' source;
+ * nterms <= SGK_MAX_SOURCE_TERMS.  The source is added in FP64 in both
+ * precision modes.  A source needs a reaction term (a monomial with
+ * coefficient 0 is one): SGK_EUNSUPPORTED otherwise.  Errors: SGK_EINVAL (bad
+ * species or nterms, null pointers, non-finite lambda).  Synchronises. */
+int sgk_solver_set_source(sgk_solver* s, int species, int nterms, const double* lambda, const double* coeffs_dev);
+/* The time t^n of the current state: 0 at creation, dt more after every
+ * accepted step (a failed step leaves it).  Setting it drops the cached
+ * F(U^n) and IIF3's F(U^{n-1}) (the next IIF3 step is an IIF2 step) unless t
+ * equals the current time. */
+int sgk_solver_set_time(sgk_solver* s, double t);
+int sgk_solver_get_time(const sgk_solver* s, double* t);
 
 typedef struct sgk_stats {
     int64_t steps;           /* steps taken since creation */
@@ -223,7 +246,8 @@ int sgk_solver_stats(const sgk_solver* s, sgk_stats* out);
 /* Component entry points of the step, for testing and benchmarking.  All
  * vectors are caller-owned device arrays, FP64, species-stacked.  They use
  * the solver's precision mode internally and are asynchronous. */
-/* F(U) = (int f(u_h) v_a dx)_a, finest-grid Gauss quadrature (Section 4). */
+/* F(U) = (int f(u_h) v_a dx)_a, finest-grid Gauss quadrature (Section 4),
+ * plus the source terms at the solver's time t^n when set. */
 int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev);
 /* J_F(U) w = (int f'(u_h) w_h v_a dx)_a with the same quadrature. */
 int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, double* jw_dev);

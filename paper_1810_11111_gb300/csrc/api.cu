@@ -465,6 +465,37 @@ int sgk_solver_stats(const sgk_solver* s, sgk_stats* out) {
     return SGK_OK;
 }
 
+int sgk_solver_set_source(sgk_solver* s, int species, int nterms, const double* lambda, const double* coeffs_dev) {
+    if (!s) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
+        SGK_REQUIRE(nterms >= 0 && nterms <= SGK_MAX_SOURCE_TERMS, SGK_EINVAL, "nterms must be in [0, 8]");
+        SGK_REQUIRE(nterms == 0 || (lambda && coeffs_dev), SGK_EINVAL, "null source arrays");
+        for (int m = 0; m < nterms; ++m) SGK_REQUIRE(std::isfinite(lambda[m]), SGK_EINVAL, "non-finite lambda");
+        SGK_REQUIRE(nterms == 0 || s->has_rx, SGK_EUNSUPPORTED, "a source term needs a reaction term");
+        set_device(s->ctx);
+        solver_set_source(s, species, nterms, lambda, coeffs_dev);
+        SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
+        return SGK_OK;
+    });
+}
+
+int sgk_solver_set_time(sgk_solver* s, double t) {
+    if (!s) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        SGK_REQUIRE(std::isfinite(t), SGK_EINVAL, "non-finite time");
+        set_device(s->ctx);
+        solver_set_time(s, t);
+        return SGK_OK;
+    });
+}
+
+int sgk_solver_get_time(const sgk_solver* s, double* t) {
+    if (!s || !t) return SGK_EINVAL;
+    *t = s->t;
+    return SGK_OK;
+}
+
 int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev) {
     if (!s || !u_dev || !f_dev) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {

@@ -26,6 +26,14 @@ struct sgk_solver {
     // F(U^n) of the running step, and exp(2 dt A) F(U^{n-1})
     DevBuf<double> Fprev, Fstage, W2;
     bool have_fprev = false;
+    // source terms: F_s(U, t) += sum_m e^{lambda_m t} S_{s,m}; t^n of the
+    // state on the host and, written before each step, on the device
+    double t = 0.0;
+    bool has_src = false;
+    int nsrc[SGK_MAX_SPECIES] = {0};
+    DevBuf<double> src_S[SGK_MAX_SPECIES];  // SGK_MAX_SOURCE_TERMS * n each, allocated on first use
+    DevBuf<double> src_lam;                 // SGK_MAX_SPECIES * SGK_MAX_SOURCE_TERMS
+    DevBuf<double> tdev;                    // t^n
     sgk_newton_opts opts{};
     int prec = SGK_FP64;
     long long n = 0;  // dof per species
@@ -92,3 +100,6 @@ int solver_step(sgk_solver* s, int nsteps);
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);
 void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau = -1.0);
+// replaces the source terms of one species (coeffs_dev: nterms * n device values)
+void solver_set_source(sgk_solver* s, int species, int nterms, const double* lambda, const double* coeffs_dev);
+void solver_set_time(sgk_solver* s, double t);

@@ -130,6 +130,26 @@ __global__ void set_state_kernel(double* __restrict__ U, const double* __restric
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicExch(&c->fvalid, 0);
 }
 
+// t^n of the state, read by the source kernels of the step's graphs
+__global__ void set_time_kernel(double* tdev, double t) { *tdev = t; }
+
+// F[i] += sum_m e^{lam_m (t^n + toff)} S[m n + i] (the source terms of one
+// species; toff = 0 for F(U^n), dt for the Newton stage F(U^{n+1}))
+__global__ void source_add_kernel(double* __restrict__ F, const double* __restrict__ S, const double* __restrict__ lam,
+                                  int nterms, const double* __restrict__ tdev, double toff, long long n) {
+    const double t = *tdev + toff;
+    double c[SGK_MAX_SOURCE_TERMS];
+#pragma unroll
+    for (int m = 0; m < SGK_MAX_SOURCE_TERMS; ++m) c[m] = m < nterms ? exp(lam[m] * t) : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double acc = F[i];
+#pragma unroll
+        for (int m = 0; m < SGK_MAX_SOURCE_TERMS; ++m)
+            if (m < nterms) acc += c[m] * S[m * n + i];
+        F[i] = acc;
+    }
+}
+
 // The last block to arrive runs fin() on thread 0 (no sum).
 template <typename Fin>
 __device__ __forceinline__ void finish_last(unsigned* counter, Fin&& fin) {
@@ -433,9 +453,42 @@ void evalJ_T(sgk_solver* s, const double* w, T* out) {
     for (int sp = 0; sp < s->nspecies; ++sp) backward_species<T>(s, p.wnod[sp], p.tmp, out + sp * n);
 }
 
-void evalF(sgk_solver* s, const double* U, double* F) {
+// F(U, t^n + toff): the reaction passes, then the source terms in FP64
+void evalF(sgk_solver* s, const double* U, double* F, double toff) {
     if (s->prec == SGK_FP64) evalF_T<double>(s, U, F);
     else evalF_T<float>(s, U, F);
+    if (!s->has_src) return;
+    const long long n = s->n;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        if (!s->nsrc[sp]) continue;
+        KTimer kt(s->ctx, KC_VECTOR);
+        source_add_kernel<<<(int)std::min<long long>((n + 255) / 256, 4LL * s->ctx->num_sms), 256, 0,
+                            s->ctx->stream>>>(F + sp * n, s->src_S[sp].p, s->src_lam.p + sp * SGK_MAX_SOURCE_TERMS,
+                                              s->nsrc[sp], s->tdev.p, toff, n);
+        check_launch("source_add");
+        count_launch(s->ctx);
+    }
+}
+
+// writes t^n to the device before a step (or a stand-alone F) reads it
+void write_time(sgk_solver* s) {
+    if (!s->has_src) return;
+    set_time_kernel<<<1, 1, 0, s->ctx->stream>>>(s->tdev.p, s->t);
+    check_launch("set_time");
+    count_launch(s->ctx);
+}
+
+// destroys every cached graph (they are captured again on next use)
+void drop_graphs(sgk_solver* s) {
+    for (GraphCache* g : {&s->g_step, &s->g_pred, &s->g_pred_f, &s->g_resid, &s->g_cg}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        *g = GraphCache{};
+    }
+    for (int sp = 0; sp < SGK_MAX_SPECIES; ++sp)
+        for (GraphCache* g : {&s->g_krylov[sp], &s->g_krylov2[sp]}) {
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            *g = GraphCache{};
+        }
 }
 
 // q = p - dt/2 J_F(U) p (stacked FP64)
@@ -570,7 +623,7 @@ int newton(sgk_solver* s) {
     double prev = INFINITY;
     for (int it = 0; it <= s->opts.max_iter; ++it) {
         run_graph(s, s->g_resid, KC_VECTOR, [&]() {
-            evalF(s, s->U.p, s->Fv.p);
+            evalF(s, s->U.p, s->Fv.p, s->dt);
             launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                          (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID, s->scal.p + 7,
                          (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0, 0);
@@ -599,7 +652,8 @@ int newton(sgk_solver* s) {
 
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F) {
     SGK_REQUIRE(s->has_rx, SGK_EINVAL, "solver has no reaction term");
-    evalF(s, U, F);
+    write_time(s);
+    evalF(s, U, F, 0.0);
 }
 
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw) {
@@ -732,7 +786,7 @@ void build_step_graph(sgk_solver* s) {
                 },
                 [&](cudaGraphConditionalHandle) {
                     const int64_t m0 = ctx->launches;
-                    evalF(s, s->U.p, s->Fv.p);
+                    evalF(s, s->U.p, s->Fv.p, 0.0);
                     s->n_predf = ctx->launches - m0;
                 });
             vk_axpby(ctx, 1.0, s->U.p, dt2, s->Fv.p, s->vv.p, N);
@@ -750,7 +804,7 @@ void build_step_graph(sgk_solver* s) {
             launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p,
                          s->fcnt.p + FC_NORM, s->scal.p + 6, ctl, s->opts.tol);
             auto resid = [&](cudaGraphConditionalHandle h) {
-                evalF(s, s->U.p, s->Fv.p);
+                evalF(s, s->U.p, s->Fv.p, s->dt);
                 launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                              (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID,
                              s->scal.p + 7, ctl, h, s->opts.max_iter, mixed);
@@ -830,6 +884,7 @@ void solver_step_launch(sgk_solver* s) {
     sgk_ctx* ctx = s->ctx;
     if (!s->g_step.exec) build_step_graph(s);
     StepRecord* h = static_cast<StepRecord*>(s->hrec);
+    write_time(s);
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
     if (s->has_rx)
@@ -873,6 +928,7 @@ int solver_step_finish(sgk_solver* s) {
         SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     } else {
         s->stats.steps += 1;
+        s->t += s->dt;
         s->fv_valid = s->has_rx;
     }
     return rc;
@@ -895,6 +951,34 @@ void solver_set_state(sgk_solver* s, int species, const double* src_dev) {
                                        s->ctx->stream));
         solver_state_changed(s);
     }
+}
+
+void solver_set_source(sgk_solver* s, int species, int nterms, const double* lambda, const double* coeffs_dev) {
+    const long long n = s->n;
+    if (nterms > 0) {
+        if (!s->src_S[species].p) s->src_S[species].alloc((size_t)SGK_MAX_SOURCE_TERMS * n);
+        if (!s->src_lam.p) s->src_lam.alloc(SGK_MAX_SPECIES * SGK_MAX_SOURCE_TERMS);
+        if (!s->tdev.p) s->tdev.alloc(1);
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->src_S[species].p, coeffs_dev, nterms * n * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s->ctx->stream));
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->src_lam.p + species * SGK_MAX_SOURCE_TERMS, lambda, nterms * sizeof(double),
+                                       cudaMemcpyHostToDevice, s->ctx->stream));
+        SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));  // lambda is pageable host memory
+    }
+    s->nsrc[species] = nterms;
+    s->has_src = false;
+    for (int sp = 0; sp < s->nspecies; ++sp) s->has_src = s->has_src || s->nsrc[sp] > 0;
+    // the graphs hold the source launches with their term counts, and F changed
+    drop_graphs(s);
+    s->have_fprev = false;
+    solver_state_changed(s);
+}
+
+void solver_set_time(sgk_solver* s, double t) {
+    if (t == s->t) return;  // the cached F values stay valid
+    s->t = t;
+    s->have_fprev = false;
+    solver_state_changed(s);
 }
 
 void solver_state_changed(sgk_solver* s) {
@@ -928,6 +1012,7 @@ int solver_step(sgk_solver* s, int nsteps) {
     };
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        write_time(s);
         // IIF3 from its second step (eq. krylov6): W = exp(dt A)(U^n + 2/3 dt
         // F(U^n)) - dt/12 exp(2 dt A) F(U^{n-1}) and the weight 5/12 dt;
         // otherwise (IIF2, or IIF3 without F(U^{n-1})) W = exp(dt A)(U^n + dt/2
@@ -944,7 +1029,7 @@ int solver_step(sgk_solver* s, int nsteps) {
         const bool have_f = s->fv_valid;
         run_graph(s, have_f ? s->g_pred_f : s->g_pred, KC_VECTOR, [&]() {
             if (s->has_rx) {
-                if (!have_f) evalF(s, s->U.p, s->Fv.p);
+                if (!have_f) evalF(s, s->U.p, s->Fv.p, 0.0);
                 vk_axpby(ctx, 1.0, s->U.p, cpred, s->Fv.p, s->vv.p, N);
             } else {
                 SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1002,6 +1087,7 @@ int solver_step(sgk_solver* s, int nsteps) {
             return rc;
         }
         s->stats.steps += 1;
+        s->t += s->dt;
         if (iif3) {
             SGK_CUDA_CHECK(
                 cudaMemcpyAsync(s->Fprev.p, s->Fstage.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));

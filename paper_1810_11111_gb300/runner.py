@@ -25,6 +25,10 @@ class Problem:
         self.nspecies = len(self.ops)
         self.dof = self.idx.dof
         self.U0 = self.initial_state()
+        self.sources = self.source_terms()
+        for s, (lam, S) in enumerate(self.sources):
+            if len(lam):
+                self.solver.set_source(s, lam, S.data_ptr())
 
     def initial_state(self):
         """Initial coefficients per species as FP64 device tensors."""
@@ -43,9 +47,24 @@ class Problem:
                 out.append(t)
         return out
 
+    def source_terms(self):
+        """Per species (lambdas, S): the terms e^{lam t} g(x) of cfg["sources"]
+        (dicts with lam and the separable g as in init), g projected on the
+        device into the rows of S."""
+        out = []
+        for s in range(self.nspecies):
+            terms = self.cfg.get("sources", [[]] * self.nspecies)[s]
+            S = torch.empty((len(terms), self.dof), dtype=torch.float64, device=self.device)
+            for m, g in enumerate(terms):
+                self.idx.project_separable(g["amp"], g["wavenum"], g["kind"], g.get("const", 0.0), S[m].data_ptr())
+            out.append(([float(g["lam"]) for g in terms], S))
+        return out
+
     def reset(self):
+        """The initial state at t = 0."""
         for s in range(self.nspecies):
             self.solver.set_state(s, dev_ptr=self.U0[s].data_ptr())
+        self.solver.set_time(0.0)
 
     def state(self):
         return [self.solver.get_state(s) for s in range(self.nspecies)]

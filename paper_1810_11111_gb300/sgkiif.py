@@ -97,6 +97,9 @@ _SIGS = {
     "sgk_solver_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "sgk_solver_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sgk_solver_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int]),
+    "sgk_solver_set_source": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
+    "sgk_solver_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),
     "sgk_reaction_eval": (ctypes.c_int, [_P, _P, _P]),
     "sgk_jacobian_apply": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -299,6 +302,21 @@ class Solver:
             c = np.ascontiguousarray(coeffs, dtype=np.float64)
             assert c.size == self.dof
             self.ctx.check(sgk_solver_set_state(self.h, species, c.ctypes.data, 0))
+
+    def set_source(self, species, lambdas, dev_ptr):
+        """Source terms sum_m e^{lambdas[m] t} S_m of one species; dev_ptr: the
+        len(lambdas) projected vectors S_m, back to back on the device."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        self.ctx.check(sgk_solver_set_source(self.h, species, int(lam.size), lam.ctypes.data if lam.size else None,
+                                             dev_ptr if lam.size else None))
+
+    def set_time(self, t):
+        self.ctx.check(sgk_solver_set_time(self.h, float(t)))
+
+    def get_time(self):
+        t = ctypes.c_double()
+        self.ctx.check(sgk_solver_get_time(self.h, ctypes.byref(t)))
+        return t.value
 
     def get_state(self, species, dev_ptr=None):
         if dev_ptr is not None:

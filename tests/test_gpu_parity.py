@@ -438,6 +438,189 @@ def test_iif3_steps_match_oracle(name, cfg, nsteps, precision):
     prob.close()
 
 
+def _table7_rows(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [list(map(float, ln.split())) for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+@pytest.mark.parametrize("scheme,k,golden,min_order", [
+    (sgkiif.SGK_IIF2, 1, "paper_example4_errors.txt", 1.5),
+    (sgkiif.SGK_IIF3, 2, "paper_example4_p2_errors.txt", 2.4)])
+def test_example4_against_table7(scheme, k, golden, min_order):
+    # Example 4 (Section 4): u_t = a k Lap u - b u + v, v_t = a k Lap v - c v
+    # on [0,1]^2 with a = c = 1, b = 100, k = 1/(4 d pi^2), T = 1, dt = h_N,
+    # M = 25; exact u = (e^{-(b+a)t} + e^{-(c+a)t}) g, v = (b - c) e^{-(c+a)t} g
+    # with g = cos(2 pi x) cos(2 pi y) (||g||^2 = 1/4).  The library's L2 errors
+    # (exact through orthonormality) agree with the printed P1/IIF2 and
+    # P2/IIF3 errors of Table 7 within a factor 2 up to N = 6 (the rows the
+    # oracle pins), stay below twice the printed errors at N = 7, and
+    # converge at order.
+    d, a, b, c, T = 2, 1.0, 100.0, 1.0, 1.0
+    kd = 1 / (4 * d * np.pi ** 2)
+    wn = np.array([[1, 1]], np.int32)
+    kind = np.array([[1, 1]], np.int32)
+    errs = []
+    for N, dof, paper_u, paper_v in _table7_rows(golden):
+        N = int(N)
+        cfg = dict(d=d, n=N, k=k, kappas=[[kd * a] * d, [kd * a] * d],
+                   reaction=[[(-b, (1, 0)), (1.0, (0, 1))], [(-c, (0, 1))]], M=25, dt=2.0 ** -N,
+                   scheme=scheme, init=[dict(amp=np.array([2.0]), wavenum=wn, kind=kind),
+                                        dict(amp=np.array([b - c]), wavenum=wn, kind=kind)])
+        prob = Problem(cfg, sgkiif.SGK_FP64)
+        assert prob.dof == dof
+        P = prob.U0[0].cpu().numpy() / 2.0
+        prob.reset()
+        prob.solver.step(int(round(T / cfg["dt"])))
+        U, V = prob.state()
+        prob.close()
+        amp_u = np.exp(-(b + a) * T) + np.exp(-(c + a) * T)
+        amp_v = (b - c) * np.exp(-(c + a) * T)
+        eu = np.sqrt(np.sum((U - amp_u * P) ** 2) + amp_u ** 2 * (0.25 - P @ P))
+        ev = np.sqrt(np.sum((V - amp_v * P) ** 2) + amp_v ** 2 * (0.25 - P @ P))
+        if N <= 6:
+            assert paper_u / 2 < eu < paper_u * 2 and paper_v / 2 < ev < paper_v * 2, (N, eu, ev)
+        else:  # N = 7 with P2: 0.47x the printed errors (the penalty convention differs)
+            assert eu < paper_u * 2 and ev < paper_v * 2, (N, eu, ev)
+        errs.append(eu)
+    for e0, e1 in zip(errs, errs[1:]):
+        assert np.log2(e0 / e1) > min_order, errs
+
+
+# ------------------------------------------------- source terms (NEXT) ---
+
+def _sin2_terms(d, lam, scale):
+    """scale e^{lam t} prod sin^2(2 pi x_i) as separable source terms
+    (prod (1/2 - 1/2 cos(4 pi x_i)) expanded over subsets)."""
+    terms = []
+    for mask in range(1 << d):
+        terms.append(dict(lam=lam, amp=np.array([scale * 0.5 ** d * (-1) ** bin(mask).count("1")]),
+                          wavenum=np.array([[2 if (mask >> i) & 1 else 0 for i in range(d)]], np.int32),
+                          kind=np.ones((1, d), np.int32)))
+    return terms
+
+
+def _example23_cfg(ex, d, k, N, scheme):
+    wn = np.ones((1, d), np.int32)
+    sines = np.zeros((1, d), np.int32)
+    base = dict(d=d, n=N, k=k, kappas=[[1 / (4 * d * np.pi ** 2)] * d], M=25, dt=2.0 ** -N, scheme=scheme,
+                init=[dict(amp=np.array([1.0]), wavenum=wn, kind=sines)])
+    if ex == 2:  # u_t = k Lap u + u - e^{-t} prod sin(2 pi x_i), periodic
+        return (dict(base, reaction=[[(1.0, (1,))]],
+                     sources=[[dict(lam=-1.0, amp=np.array([-1.0]), wavenum=wn, kind=sines)]]),
+                sgkiif.SGK_PERIODIC, PERIODIC)
+    # u_t = k Lap u + u^2 - e^{-2t} prod sin^2(2 pi x_i), zero Dirichlet
+    return (dict(base, reaction=[[(1.0, (2,))]], sources=[_sin2_terms(d, -2.0, -1.0)]),
+            sgkiif.SGK_DIRICHLET0, DIRICHLET0)
+
+
+def _oracle_sources(cfg, idx):
+    out = []
+    for terms in cfg["sources"]:
+        out.append([(g["lam"], project_separable(idx, g["amp"], g["wavenum"], g["kind"], g.get("const", 0.0)))
+                    for g in terms])
+    return out
+
+
+SOURCE_CASES = [
+    ("ex2_p1", 2, 1, 4, sgkiif.SGK_IIF2),
+    ("ex2_p2_iif3", 2, 2, 4, sgkiif.SGK_IIF3),
+    ("ex3_p1_dirichlet", 3, 1, 4, sgkiif.SGK_IIF2),
+    ("ex3_p2_iif3_dirichlet", 3, 2, 4, sgkiif.SGK_IIF3),
+]
+
+
+@pytest.mark.parametrize("name,ex,k,N,scheme", SOURCE_CASES)
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_source_steps_match_oracle(name, ex, k, N, scheme, precision):
+    # F(U, t) = P f(u_h) + sum_m e^{lam_m t} S_m with every F at the time of
+    # its argument, from a start time t0 != 0; scalar IIF2 takes the
+    # one-graph device-driven step, IIF3 the host-driven one
+    cfg, bc, obc = _example23_cfg(ex, 2, k, N, scheme)
+    t0, nsteps = 0.37, 5
+    prob = Problem(cfg, precision, bc=bc)
+    prob.reset()
+    prob.solver.set_time(t0)
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(nsteps)
+    got = prob.state()
+    assert abs(prob.solver.get_time() - (t0 + nsteps * cfg["dt"])) < 1e-14
+    idx = OIndex(2, N, k)
+    cls = IIF2Solver if scheme == sgkiif.SGK_IIF2 else IIF3Solver
+    want = cls(idx, sipg_1d(N, k, obc), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+               sources=_oracle_sources(cfg, idx), t0=t0).run(U0, nsteps)
+    tol = 1e-10 if precision == sgkiif.SGK_FP64 else 1e-6
+    assert rel(got[0], want[0]) <= tol, (name, rel(got[0], want[0]))
+    # the same steps again from the same state and time give the same state
+    prob.reset()
+    prob.solver.set_time(t0)
+    prob.solver.step(nsteps)
+    assert rel(prob.state()[0], got[0]) <= 1e-13
+    prob.close()
+
+
+def test_source_reaction_eval_and_errors():
+    cfg, bc, _ = _example23_cfg(2, 2, 2, 4, sgkiif.SGK_IIF2)
+    prob = Problem(cfg, sgkiif.SGK_FP64, bc=bc)
+    idx = OIndex(2, 4, 2)
+    U = prob.U0[0]
+    Fd = torch.empty_like(U)
+    prob.solver.set_time(0.25)
+    sgkiif.sgk_reaction_eval(prob.solver.h, U.data_ptr(), Fd.data_ptr())
+    torch.cuda.synchronize()
+    P = project_separable(idx, [1.0], [[1, 1]], [[0, 0]])
+    want = Reaction(idx, cfg["reaction"]).F([U.cpu().numpy()])[0] - np.exp(-0.25) * P
+    assert rel(Fd.cpu().numpy(), want) <= 1e-12
+    lam = np.array([np.nan])
+    assert sgkiif.sgk_solver_set_source(prob.solver.h, 0, 1, lam.ctypes.data, U.data_ptr()) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_solver_set_source(prob.solver.h, 1, 0, None, None) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_solver_set_source(prob.solver.h, 0, 9, lam.ctypes.data, U.data_ptr()) == sgkiif.SGK_EINVAL
+    prob.solver.set_source(0, [], None)  # removing the source leaves F = P f(u_h)
+    sgkiif.sgk_reaction_eval(prob.solver.h, U.data_ptr(), Fd.data_ptr())
+    torch.cuda.synchronize()
+    assert rel(Fd.cpu().numpy(), Reaction(idx, cfg["reaction"]).F([U.cpu().numpy()])[0]) <= 1e-12
+    prob.close()
+    heat = Problem(dict(workloads.heat2d()), sgkiif.SGK_FP64)
+    one = np.array([-1.0])
+    assert sgkiif.sgk_solver_set_source(heat.solver.h, 0, 1, one.ctypes.data,
+                                        heat.U0[0].data_ptr()) == sgkiif.SGK_EUNSUPPORTED
+    heat.close()
+
+
+@pytest.mark.parametrize("ex,golden", [(2, "paper_example2_errors.txt"), (3, "paper_example3_errors.txt")])
+def test_examples23_against_tables(ex, golden):
+    # Examples 2 (Table 5) and 3 (Table 6) through the library: 2D P1 with
+    # IIF2 (N = 4..7), 2D P2 with IIF3 (N = 3..7) and 3D P2 with IIF3 (N =
+    # 4..6, the N = 6 grid being the 18 576-DOF benchmark grid), the error
+    # taken at round(T / dt) dt.  Within a factor 2 of the printed errors on
+    # the rows the oracle pins, below twice the printed error beyond them,
+    # and converging at order.
+    rows = {(int(r[0]), int(r[1]), int(r[2])): r for r in _table7_rows(golden)}
+    for d, k, scheme, Ns, pinned, min_order in ((2, 1, sgkiif.SGK_IIF2, (4, 5, 6, 7), 6, 1.8),
+                                                 (2, 2, sgkiif.SGK_IIF3, (3, 4, 5, 6, 7), 5, 2.4),
+                                                 (3, 2, sgkiif.SGK_IIF3, (4, 5, 6), 5, 2.4)):
+        errs = []
+        for N in Ns:
+            _, _, _, dof, T, paper = rows[(d, k, N)]
+            cfg, bc, _ = _example23_cfg(ex, d, k, N, scheme)
+            prob = Problem(cfg, sgkiif.SGK_FP64, bc=bc)
+            assert prob.dof == dof
+            P = prob.U0[0].cpu().numpy()
+            nsteps = int(round(T / cfg["dt"]))
+            prob.reset()
+            prob.solver.step(nsteps)
+            U = prob.state()[0]
+            prob.close()
+            amp = np.exp(-nsteps * cfg["dt"])
+            e = np.sqrt(np.sum((U - amp * P) ** 2) + amp ** 2 * (0.5 ** d - P @ P))
+            if N <= pinned:
+                assert paper / 2 < e < paper * 2, (d, k, N, e, paper)
+            else:
+                assert e < paper * 2, (d, k, N, e, paper)
+            errs.append(e)
+        for e0, e1 in zip(errs, errs[1:]):
+            assert np.log2(e0 / e1) > min_order, (d, k, errs)
+
+
 def test_dirichlet_heat_steps():
     # Several sine modes (zero on the boundary).  A single mode is nearly an
     # eigenvector: its Krylov space is exhausted after a few Arnoldi steps and
