@@ -10,6 +10,14 @@ Reading for IIF3: the two exp(dt A) terms are one Krylov projection of
 U^n + 2/3 dt F(U^n) (as IIF2 projects U^n + dt/2 F(U^n)), and exp(2 dt A)
 F(U^{n-1}) is a second projection with time 2 dt; the first step, which has
 no F(U^{n-1}), is an IIF2 step.
+Eq. krylov3 (r-th order, IIFr):
+    U^{n+1} = exp(dt A) U^n + dt (alpha_1 F(U^{n+1})
+              + sum_{i=0}^{r-2} alpha_{-i} exp((i+1) dt A) F(U^{n-i})),
+with the alphas of eq. krylov4: the integrals over [0, dt] of the Lagrange
+basis polynomials on the nodes tau = -k dt, k = -1..r-2.  The same reading:
+the i = 0 term joins exp(dt A) U^n in one projection, every other i is a
+projection over (i+1) dt, and a step uses the highest order its history of
+past F values allows (IIF2, IIF3, ... up to r after a new state).
 For a system the diffusion is block diagonal across species, so exp(dt A)
 acts per species with that species' operator, one Krylov projection each.
 
@@ -240,3 +248,49 @@ class IIF3Solver(IIF2Solver):
             W.append(w1 - (dt / 12.0) * w2)
         self.F_prev = Fn
         return self.finish(W, 5.0 / 12.0 * dt)
+
+
+def iif_alpha(r):
+    """[alpha_1, alpha_0, alpha_{-1}, ..., alpha_{-(r-2)}] of eq. krylov4.
+
+    alpha_{-i} = (1/dt) int_0^dt prod_{k=-1..r-2, k != i} (tau + k dt) / ((k - i) dt) dtau;
+    with s = tau / dt each factor is (s + k) / (k - i), integrated over [0, 1].
+    """
+    nodes = list(range(-1, r - 1))
+    out = []
+    for i in nodes:
+        poly = np.poly1d([1.0])
+        for k in nodes:
+            if k != i:
+                poly = poly * np.poly1d([1.0 / (k - i), k / (k - i)])
+        prim = poly.integ()
+        out.append(float(prim(1.0) - prim(0.0)))
+    return out
+
+
+class IIFSolver(IIF2Solver):
+    """Sparse-grid Krylov IIFr DG solver (eqs. krylov3, krylov4), r >= 2; the
+    first steps after a new state use the orders their history allows."""
+
+    def __init__(self, *args, order=3, **kw):
+        super().__init__(*args, **kw)
+        assert order >= 2
+        self.order = order
+        self.F_hist = []  # F(U^{n-1}), F(U^{n-2}), ... of the last steps
+
+    def step(self, U):
+        dt = self.dt
+        Fn = self.F(U, self.t)
+        r = min(self.order, 2 + len(self.F_hist))
+        alpha = iif_alpha(r)
+        W = []
+        for s in range(self.nspecies):
+            w, m = krylov_expv(self.A(s), U[s] + alpha[1] * dt * Fn[s], dt, self.M)
+            self.stats["m_eff"].append(m)
+            for i in range(1, r - 1):
+                wi, mi = krylov_expv(self.A(s), self.F_hist[i - 1][s], (i + 1) * dt, self.M)
+                self.stats["m_eff"].append(mi)
+                w = w + alpha[i + 1] * dt * wi
+            W.append(w)
+        self.F_hist = ([Fn] + self.F_hist)[: self.order - 2]
+        return self.finish(W, alpha[0] * dt)

@@ -18,6 +18,11 @@
   Example 3 (zero Dirichlet, f = u^2, Newton) agree with Tables 5 and 6 (P1
   with IIF2, P2 with IIF3; 2D, and 3D with P2, where the error is taken at
   round(T / dt) dt) within a factor 2 and converge at order.
+* IIFr (eqs. krylov3, krylov4): the alphas equal the Adams-Moulton
+  coefficients (the same Lagrange integrals, e.g. Hairer, Norsett, Wanner,
+  Solving ODEs I, Section III.1, Table 1.2); r = 2 and 3 reproduce the IIF2
+  and IIF3 solvers (start-up included); with exact history values the global
+  error of a linear problem falls as dt^r, r = 2..5.
 * IIF3 (eq. krylov6): F = 0 gives exp(dt A) U; for f = -b u the steps follow
   the three-term recurrence
   (1 + 5/12 b dt) U^{n+1} = E (1 - 2/3 b dt) U^n + 1/12 b dt E^(2) U^{n-1}
@@ -33,7 +38,7 @@ import scipy.linalg as sla
 
 from oracle import iif
 from oracle.index_set import IndexSet
-from oracle.iif import IIF2Solver, IIF3Solver, NewtonError
+from oracle.iif import IIF2Solver, IIF3Solver, IIFSolver, NewtonError, iif_alpha
 from oracle.operator import DIRICHLET0, PERIODIC, dense_sparse_operator, sipg_1d
 from oracle.projection import project_separable
 
@@ -308,3 +313,55 @@ def test_example2_against_table5():
 
 def test_example3_against_table6():
     _examples23("paper_example3_errors.txt", nonlinear=True)
+
+
+# ------------------------------------------------------------------ IIFr ---
+
+# Adams-Moulton coefficients beta_{k}, beta_{k-1}, ..., beta_0 of the implicit
+# (r-1)-step method of order r, as printed in ODE textbooks
+_ADAMS_MOULTON = {
+    2: ((1, 2), (1, 2)),
+    3: ((5, 12), (8, 12), (-1, 12)),
+    4: ((9, 24), (19, 24), (-5, 24), (1, 24)),
+    5: ((251, 720), (646, 720), (-264, 720), (106, 720), (-19, 720)),
+    6: ((475, 1440), (1427, 1440), (-798, 1440), (482, 1440), (-173, 1440), (27, 1440)),
+}
+
+
+def test_iif_alpha_is_adams_moulton():
+    for r, coefs in _ADAMS_MOULTON.items():
+        got = iif_alpha(r)
+        assert len(got) == r
+        for g, (num, den) in zip(got, coefs):
+            assert abs(g - num / den) < 1e-14, (r, got)
+
+
+def test_iifr_reduces_to_iif2_and_iif3():
+    idx = IndexSet(2, 3, 1)
+    S = sipg_1d(3, 1)
+    rng = np.random.default_rng(9)
+    U0 = 0.3 * rng.standard_normal(idx.dof)
+    args = (idx, S, [[0.4, 0.7]], [[(-30.0, (3,)), (2.0, (1,))]], 0.01, 20)
+    for order, cls in ((2, IIF2Solver), (3, IIF3Solver)):
+        want = cls(*args).run([U0], 4)[0]
+        got = IIFSolver(*args, order=order).run([U0], 4)[0]
+        assert np.linalg.norm(got - want) < 1e-13 * np.linalg.norm(want), order
+
+
+def test_iifr_temporal_order():
+    # u' = A u - b u with exact exponentials (M = dof); history seeded with
+    # the exact solution at t = -dt, -2 dt, ... so every step has order r
+    idx = IndexSet(2, 2, 1)
+    S = sipg_1d(2, 1)
+    kap, b, T = [0.01, 0.02], 3.0, 0.4
+    A = dense_sparse_operator(idx, S, kap)
+    U0 = np.random.default_rng(10).standard_normal(idx.dof)
+    exact = lambda t: sla.expm(t * (A - b * np.eye(idx.dof))) @ U0  # noqa: E731
+    for r in (2, 3, 4, 5):
+        errs = []
+        for dt in (0.04, 0.02):
+            sol = IIFSolver(idx, S, [kap], [[(-b, (1,))]], dt, idx.dof, order=r)
+            sol.F_hist = [[-b * exact(-i * dt)] for i in range(1, r - 1)]
+            U = sol.run([U0], int(round(T / dt)))[0]
+            errs.append(np.linalg.norm(U - exact(T)))
+        assert np.log2(errs[0] / errs[1]) > r - 0.25, (r, errs)
