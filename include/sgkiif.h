@@ -63,6 +63,7 @@ extern "C" {
 /* time schemes (Section 3) */
 #define SGK_IIF2 2         /* eq. krylov5 */
 #define SGK_IIF3 3         /* eq. krylov6 */
+#define SGK_IIF_MAX_ORDER 6 /* schemes 2..6: the r-th order IIF of eqs. krylov3, krylov4 */
 
 #define SGK_MAX_DIM 6
 #define SGK_MAX_LEVEL 12
@@ -185,20 +186,31 @@ typedef struct sgk_newton_opts {
     int gmres_restart; /* GMRES restart length (systems); 50 */
 } sgk_newton_opts;
 
-/* Create an IIF solver for nspecies species on one index set: scheme
- * SGK_IIF2 (eq. krylov5) or SGK_IIF3 (eq. krylov6: exp(dt A) applied to
- * U^n + 2/3 dt F(U^n) in one Krylov projection, exp(2 dt A) F(U^{n-1}) in a
- * second, Newton weight 5/12 dt; the first step after creation or
- * sgk_solver_set_state has no F(U^{n-1}) and is an IIF2 step).  ops[s] is the
- * diffusion operator of species s (all on the same index set).  krylov_m in [1, 128], dt > 0.  The reaction term uses
- * finest-mesh Gauss quadrature with q = ceil((p k + k + 1)/2) points per
- * direction for total polynomial degree p, i.e. the exact L2 projection of
- * f(u_h).  The finest full grid must fit in device memory
+/* Create an IIF solver for nspecies species on one index set.  scheme is
+ * the order r of the IIF scheme (eqs. krylov3, krylov4), 2 <= r <=
+ * SGK_IIF_MAX_ORDER: SGK_IIF2 (eq. krylov5), SGK_IIF3 (eq. krylov6), ...
+ * The exp(dt A) terms of U^n and F(U^n) are one Krylov projection of
+ * U^n + alpha_0 dt F(U^n); every older F(U^{n-i}) is a projection over
+ * (i+1) dt; the Newton weight is alpha_1 dt.  A step uses the highest order
+ * its history of F values allows: the first step after creation,
+ * sgk_solver_set_state, sgk_solver_set_time or sgk_solver_set_source is an
+ * IIF2 step, the next an IIF3 step, and so on up to r (with this start-up
+ * the global order is min(r, 3)).  ops[s] is the diffusion operator of
+ * species s (all on the same index set).  krylov_m in [1, 128], dt > 0.  The
+ * reaction term uses finest-mesh Gauss quadrature with q = ceil((p k + k + 1)/2)
+ * points per direction for total polynomial degree p, i.e. the exact L2
+ * projection of f(u_h).  The finest full grid must fit in device memory
  * ((k+1) 2^n)^d nodal values per species); else SGK_ENOMEM.
- * opts may be NULL.  Errors: SGK_EINVAL, SGK_ENOMEM, SGK_EUNSUPPORTED. */
+ * opts may be NULL.  Errors: SGK_EINVAL, SGK_ENOMEM, SGK_EUNSUPPORTED (scheme
+ * out of range). */
 int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
                       int krylov_m, double dt, const sgk_newton_opts* opts, sgk_solver** out);
 int sgk_solver_destroy(sgk_solver* s);
+/* The weights of the r-th order IIF scheme (eq. krylov4) into alpha[0..r-1]:
+ * alpha_1, alpha_0, alpha_{-1}, ..., alpha_{-(r-2)} (the integrals over one
+ * step of the Lagrange basis polynomials on the nodes t^{n+1}, t^n, ...,
+ * t^{n+2-r}).  Host-only; 2 <= r <= SGK_IIF_MAX_ORDER, else SGK_EINVAL. */
+int sgk_iif_alpha(int r, double* alpha);
 /* Set the coefficients of one species (FP64, dof elements) from host memory
  * (on_device = 0) or from a device array (on_device = 1). */
 int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int on_device);

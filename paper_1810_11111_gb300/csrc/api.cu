@@ -331,8 +331,8 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
     *out = nullptr;
     return guarded(ctx, [&]() {
         SGK_REQUIRE(nspecies >= 1 && nspecies <= SGK_MAX_SPECIES, SGK_EINVAL, "nspecies must be in [1, 4]");
-        SGK_REQUIRE(scheme == SGK_IIF2 || scheme == SGK_IIF3, SGK_EUNSUPPORTED,
-                    "scheme must be SGK_IIF2 or SGK_IIF3");
+        SGK_REQUIRE(scheme >= SGK_IIF2 && scheme <= SGK_IIF_MAX_ORDER, SGK_EUNSUPPORTED,
+                    "scheme must be an IIF order in [2, 6]");
         SGK_REQUIRE(krylov_m >= 1 && krylov_m <= SGK_MAX_KRYLOV, SGK_EINVAL, "krylov_m must be in [1, 128]");
         SGK_REQUIRE(dt > 0 && std::isfinite(dt), SGK_EINVAL, "dt must be positive");
         const sgk_index* idx = nullptr;
@@ -462,6 +462,12 @@ int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t 
 int sgk_solver_stats(const sgk_solver* s, sgk_stats* out) {
     if (!s || !out) return SGK_EINVAL;
     *out = s->stats;
+    return SGK_OK;
+}
+
+int sgk_iif_alpha(int r, double* alpha) {
+    if (r < 2 || r > SGK_IIF_MAX_ORDER || !alpha) return SGK_EINVAL;
+    iif_alpha(r, alpha);
     return SGK_OK;
 }
 

@@ -21,11 +21,12 @@ struct sgk_solver {
     int M = 0;
     double dt = 0.0;
     int scheme = SGK_IIF2;
-    double newton_c = 0.0;  // c of the implicit stage U - c F(U) = W (dt/2 IIF2, 5/12 dt IIF3)
-    // IIF3: F(U^{n-1}) of the last step (valid when have_fprev), the staged
-    // F(U^n) of the running step, and exp(2 dt A) F(U^{n-1})
-    DevBuf<double> Fprev, Fstage, W2;
-    bool have_fprev = false;
+    double newton_c = 0.0;  // c of the implicit stage U - c F(U) = W (alpha_1 dt: dt/2 IIF2, 5/12 dt IIF3)
+    // IIFr, r > 2: F(U^{n-1}), ..., F(U^{n-r+2}) of the last steps (nhist of
+    // them valid, N values each), the staged F(U^n) of the running step, and
+    // exp((i+1) dt A) F(U^{n-i})
+    DevBuf<double> Fhist, Fstage, W2;
+    int nhist = 0;
     // source terms: F_s(U, t) += sum_m e^{lambda_m t} S_{s,m}; t^n of the
     // state on the host and, written before each step, on the device
     double t = 0.0;
@@ -63,7 +64,8 @@ struct sgk_solver {
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     bool use_graphs = true;
-    GraphCache g_krylov[SGK_MAX_SPECIES], g_krylov2[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
+    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
+    GraphCache g_krylovh[SGK_MAX_SPECIES][SGK_IIF_MAX_ORDER - 2];  // the history projections of IIFr
     // Fv holds F(U) for the current U (a host-driven or device-driven step
     // ended with an accepted residual evaluation there); cleared whenever U
     // changes otherwise
@@ -82,6 +84,8 @@ struct sgk_solver {
 };
 
 void solver_alloc(sgk_solver* s);
+// alpha_1, alpha_0, alpha_{-1}, ..., alpha_{-(r-2)} of eq. krylov4
+void iif_alpha(int r, double* alpha);
 // Device-driven steps (one graph per step) are used when graphs are on, no
 // kernel timing is active and the implicit solve is CG (one species) or
 // absent.  solver_step_launch queues one such step on the solver's stream;

@@ -484,11 +484,14 @@ void drop_graphs(sgk_solver* s) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         *g = GraphCache{};
     }
-    for (int sp = 0; sp < SGK_MAX_SPECIES; ++sp)
-        for (GraphCache* g : {&s->g_krylov[sp], &s->g_krylov2[sp]}) {
-            if (g->exec) cudaGraphExecDestroy(g->exec);
-            *g = GraphCache{};
+    for (int sp = 0; sp < SGK_MAX_SPECIES; ++sp) {
+        if (s->g_krylov[sp].exec) cudaGraphExecDestroy(s->g_krylov[sp].exec);
+        s->g_krylov[sp] = GraphCache{};
+        for (GraphCache& g : s->g_krylovh[sp]) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = GraphCache{};
         }
+    }
 }
 
 // q = p - dt/2 J_F(U) p (stacked FP64)
@@ -938,7 +941,7 @@ bool solver_device_steps(const sgk_solver* s) { return step_graph_eligible(s) &&
 
 void solver_set_state(sgk_solver* s, int species, const double* src_dev) {
     const long long n = s->n;
-    s->have_fprev = false;  // a new state has no F(U^{n-1}): IIF3 restarts with an IIF2 step
+    s->nhist = 0;  // a new state has no F(U^{n-1}): IIFr restarts with an IIF2 step
     if (s->has_rx && s->ctl.p) {
         // the device keeps the cached F(U) when the new state equals the old
         set_state_kernel<<<reduction_blocks(s->ctx, n), RED_THREADS, 0, s->ctx->stream>>>(
@@ -970,14 +973,14 @@ void solver_set_source(sgk_solver* s, int species, int nterms, const double* lam
     for (int sp = 0; sp < s->nspecies; ++sp) s->has_src = s->has_src || s->nsrc[sp] > 0;
     // the graphs hold the source launches with their term counts, and F changed
     drop_graphs(s);
-    s->have_fprev = false;
+    s->nhist = 0;
     solver_state_changed(s);
 }
 
 void solver_set_time(sgk_solver* s, double t) {
     if (t == s->t) return;  // the cached F values stay valid
     s->t = t;
-    s->have_fprev = false;
+    s->nhist = 0;
     solver_state_changed(s);
 }
 
@@ -1013,17 +1016,20 @@ int solver_step(sgk_solver* s, int nsteps) {
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         write_time(s);
-        // IIF3 from its second step (eq. krylov6): W = exp(dt A)(U^n + 2/3 dt
-        // F(U^n)) - dt/12 exp(2 dt A) F(U^{n-1}) and the weight 5/12 dt;
-        // otherwise (IIF2, or IIF3 without F(U^{n-1})) W = exp(dt A)(U^n + dt/2
-        // F(U^n)) and dt/2.  The graph caches of an IIF3 solver hold the IIF3
-        // weights, so its IIF2 start runs without them.
-        const bool iif3 = s->scheme == SGK_IIF3 && s->has_rx;
-        const bool third = iif3 && s->have_fprev;
-        const double cpred = third ? 2.0 / 3.0 * s->dt : 0.5 * s->dt;
-        s->newton_c = third ? 5.0 / 12.0 * s->dt : 0.5 * s->dt;
+        // IIFr (eqs. krylov3, krylov4) at the highest order r the history
+        // allows: W = exp(dt A)(U^n + alpha_0 dt F(U^n)) + sum_{i=1}^{r-2}
+        // alpha_{-i} dt exp((i+1) dt A) F(U^{n-i}), Newton weight alpha_1 dt
+        // (IIF2: dt/2 and dt/2; IIF3: 2/3, -1/12 and 5/12).  The graph caches
+        // hold the weights of the full order, so start-up steps run without
+        // them.
+        const int r_full = s->has_rx ? s->scheme : SGK_IIF2;
+        const int r = std::min(r_full, 2 + s->nhist);
+        double alpha[SGK_IIF_MAX_ORDER];
+        iif_alpha(r, alpha);
+        const double cpred = alpha[1] * s->dt;
+        s->newton_c = alpha[0] * s->dt;
         GraphsSetting keep{s, s->use_graphs};
-        if (iif3 && !third) s->use_graphs = false;
+        if (r < r_full) s->use_graphs = false;
         // F(U^n) for the predictor, unless the last step left it in Fv; the
         // device-side flag of the step graph is stale after a host-driven step
         const bool have_f = s->fv_valid;
@@ -1041,16 +1047,16 @@ int solver_step(sgk_solver* s, int nsteps) {
                       [&]() { solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n); });
             s->stats.krylov_calls += s->use_graphs ? 1 : 0;
         }
-        if (third)
+        for (int i = 1; i <= r - 2; ++i)
             for (int sp = 0; sp < s->nspecies; ++sp) {
-                run_graph(s, s->g_krylov2[sp], KC_KRYLOV, [&]() {
-                    solver_krylov_expv(s, sp, s->Fprev.p + sp * n, s->W2.p + sp * n, 2.0 * s->dt);
-                    vk_axpby(ctx, 1.0, s->W.p + sp * n, -s->dt / 12.0, s->W2.p + sp * n, s->W.p + sp * n, n);
+                run_graph(s, s->g_krylovh[sp][i - 1], KC_KRYLOV, [&]() {
+                    solver_krylov_expv(s, sp, s->Fhist.p + (i - 1) * N + sp * n, s->W2.p + sp * n, (i + 1) * s->dt);
+                    vk_axpby(ctx, 1.0, s->W.p + sp * n, alpha[i + 1] * s->dt, s->W2.p + sp * n, s->W.p + sp * n, n);
                 });
                 s->stats.krylov_calls += s->use_graphs ? 1 : 0;
             }
         // F(U^n) becomes F(U^{n-1}) of the next step if this one succeeds
-        if (iif3)
+        if (r_full > 2)
             SGK_CUDA_CHECK(
                 cudaMemcpyAsync(s->Fstage.p, s->Fv.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         int rc = SGK_OK;
@@ -1088,10 +1094,14 @@ int solver_step(sgk_solver* s, int nsteps) {
         }
         s->stats.steps += 1;
         s->t += s->dt;
-        if (iif3) {
+        if (r_full > 2) {
+            // shift the history by one step: F(U^{n-i}) -> slot i, F(U^n) -> slot 0
+            for (int k = std::min(s->nhist, r_full - 3); k >= 1; --k)
+                SGK_CUDA_CHECK(cudaMemcpyAsync(s->Fhist.p + k * N, s->Fhist.p + (k - 1) * N, N * sizeof(double),
+                                               cudaMemcpyDeviceToDevice, ctx->stream));
             SGK_CUDA_CHECK(
-                cudaMemcpyAsync(s->Fprev.p, s->Fstage.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-            s->have_fprev = true;
+                cudaMemcpyAsync(s->Fhist.p, s->Fstage.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+            s->nhist = std::min(s->nhist + 1, r_full - 2);
         }
         // newton() returns OK right after the residual evaluation at the final
         // U; the step graph's flag says the same
@@ -1105,6 +1115,25 @@ int solver_step(sgk_solver* s, int nsteps) {
     return SGK_OK;
 }
 
+void iif_alpha(int r, double* alpha) {
+    // In the scaled time s = tau / dt the basis polynomial of node -i (i =
+    // -1..r-2) is prod_{k != i} (s + k) / (k - i); its coefficients are built
+    // factor by factor (ascending powers) and integrated over [0, 1].
+    for (int a = 0; a < r; ++a) {
+        const int i = a - 1;
+        double c[SGK_IIF_MAX_ORDER + 1] = {1.0};
+        int deg = 0;
+        for (int k = -1; k <= r - 2; ++k) {
+            if (k == i) continue;
+            for (int p = deg + 1; p >= 0; --p) c[p] = ((p > 0 ? c[p - 1] : 0.0) + k * c[p]) / (k - i);
+            ++deg;
+        }
+        double integral = 0.0;
+        for (int p = deg; p >= 0; --p) integral += c[p] / (p + 1);
+        alpha[a] = integral;
+    }
+}
+
 void solver_alloc(sgk_solver* s) {
     const long long n = s->n, S = s->nspecies, N = n * S;
     const int M = s->M;
@@ -1112,8 +1141,8 @@ void solver_alloc(sgk_solver* s) {
     s->Uprev.alloc(N);
     s->W.alloc(N);
     s->vv.alloc(N);
-    if (s->scheme == SGK_IIF3) {
-        s->Fprev.alloc(N);
+    if (s->scheme > SGK_IIF2) {
+        s->Fhist.alloc((size_t)(s->scheme - 2) * N);
         s->Fstage.alloc(N);
         s->W2.alloc(N);
     }
@@ -1203,8 +1232,9 @@ sgk_solver::~sgk_solver() {
         if (a) cudaStreamDestroy(a);
     for (GraphCache* g : {&g_pred, &g_pred_f, &g_resid, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
-    for (auto& g : g_krylov2)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& gs : g_krylovh)
+        for (auto& g : gs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& g : g_krylov)
         if (g.exec) cudaGraphExecDestroy(g.exec);
 }

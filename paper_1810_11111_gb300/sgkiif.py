@@ -16,6 +16,7 @@ SGK_FP64, SGK_MIXED = 0, 1
 SGK_PERIODIC, SGK_DIRICHLET0 = 0, 1
 SGK_IIF2 = 2
 SGK_IIF3 = 3
+SGK_IIF_MAX_ORDER = 6
 MAX_SPECIES = 4
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsgkiif.so")
@@ -98,6 +99,7 @@ _SIGS = {
     "sgk_solver_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sgk_solver_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int]),
     "sgk_solver_set_source": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "sgk_iif_alpha": (ctypes.c_int, [ctypes.c_int, _P]),
     "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
     "sgk_solver_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),

@@ -56,3 +56,21 @@ def test_context_creation_without_gpu_fails_cleanly(lib):
     from paper_1810_11111_gb300 import sgkiif
     h = ctypes.c_void_p()
     assert sgkiif.sgk_ctx_create(ctypes.byref(h), 0, None, 0) == sgkiif.SGK_ECUDA
+
+
+def test_iif_alpha_is_adams_moulton(lib):
+    # eq. krylov4's weights are the Adams-Moulton coefficients (the same
+    # Lagrange integrals; textbook values), computed by the library's host code
+    import numpy as np
+
+    from paper_1810_11111_gb300 import sgkiif
+    table = {2: (1 / 2, 1 / 2), 3: (5 / 12, 8 / 12, -1 / 12), 4: (9 / 24, 19 / 24, -5 / 24, 1 / 24),
+             5: (251 / 720, 646 / 720, -264 / 720, 106 / 720, -19 / 720),
+             6: (475 / 1440, 1427 / 1440, -798 / 1440, 482 / 1440, -173 / 1440, 27 / 1440)}
+    for r, want in table.items():
+        out = np.zeros(r)
+        assert sgkiif.sgk_iif_alpha(r, out.ctypes.data) == sgkiif.SGK_OK
+        assert np.max(np.abs(out - np.array(want))) < 1e-15, (r, out)
+    out = np.zeros(8)
+    for r in (1, 7):
+        assert sgkiif.sgk_iif_alpha(r, out.ctypes.data) == sgkiif.SGK_EINVAL

@@ -21,7 +21,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle.iif import IIF2Solver, IIF3Solver  # noqa: E402
+from oracle.iif import IIF2Solver, IIF3Solver, IIFSolver  # noqa: E402
 from oracle.index_set import IndexSet as OIndex  # noqa: E402
 from oracle.krylov import expm_pade13, krylov_expv  # noqa: E402
 from oracle.operator import DIRICHLET0, PERIODIC, sipg_1d, sparse_matvec  # noqa: E402
@@ -619,6 +619,43 @@ def test_examples23_against_tables(ex, golden):
             errs.append(e)
         for e0, e1 in zip(errs, errs[1:]):
             assert np.log2(e0 / e1) > min_order, (d, k, errs)
+
+
+@pytest.mark.parametrize("order", [4, 5, 6])
+@pytest.mark.parametrize("name,cfg", [("cubic3d_small", STEP_CASES[1][1]), ("schnak2d_small", STEP_CASES[2][1])])
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_iifr_steps_match_oracle(order, name, cfg, precision):
+    # eqs. krylov3, krylov4 at order r: start-up at orders 2, 3, ..., then
+    # r - 1 Krylov projections per species and step (cached graphs once the
+    # history is full)
+    cfg = dict(cfg, scheme=order)
+    nsteps = order + 2
+    prob = Problem(cfg, precision)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(nsteps)
+    got = prob.state()
+    idx = OIndex(cfg["d"], cfg["n"], cfg["k"])
+    want = IIFSolver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                     order=order).run(U0, nsteps)
+    tol = 1e-10 if precision == sgkiif.SGK_FP64 else 1e-6
+    for s in range(len(want)):
+        assert rel(got[s], want[s]) <= tol, (name, order, s, rel(got[s], want[s]))
+    prob.close()
+
+
+def test_iifr_with_source_matches_oracle():
+    cfg, bc, obc = _example23_cfg(3, 2, 2, 4, 5)
+    prob = Problem(cfg, sgkiif.SGK_FP64, bc=bc)
+    prob.reset()
+    prob.solver.set_time(0.1)
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(7)
+    idx = OIndex(2, 4, 2)
+    want = IIFSolver(idx, sipg_1d(4, 2, obc), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                     sources=_oracle_sources(cfg, idx), t0=0.1, order=5).run(U0, 7)
+    assert rel(prob.state()[0], want[0]) <= 1e-10
+    prob.close()
 
 
 def test_dirichlet_heat_steps():
