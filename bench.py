@@ -156,6 +156,19 @@ def measured_peaks():
 
 # ------------------------------------------------------------ native arm ---
 
+def aggregate(units, ms, dist, device):
+    """Whole-job throughput of independent replicas: the units of all ranks
+    over the slowest rank's time (ms); returns (units/s, max ms)."""
+    if dist is None:
+        return units / (ms / 1e3), ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u) / (float(t) / 1e3), float(t)
+
+
 def native(args, rank, world, local_rank):
     import torch
 
@@ -267,17 +280,11 @@ def native(args, rank, world, local_rank):
             e1.synchronize()
             t_ms += e0.elapsed_time(e1)
             host_in, host_out = host_out, host_in
-        t_max = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        e2e = {"value": dof * S * args.steps * world / (float(t_max) / 1e3), "unit": UNIT,
+        e2e_value, _ = aggregate(dof * S * args.steps, t_ms, dist, dev)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": dof * S * 8, "d2h_bytes_per_step": dof * S * 8}
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t)
-    value = dof * S * args.steps * world / (total_ms / 1e3)
+    value, total_ms = aggregate(dof * S * args.steps, total_ms, dist, dev)
 
     # roofline of the dominant kernel class: algorithmic work per launch over
     # its event-timed average launch time in the profiled pass
