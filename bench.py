@@ -132,7 +132,7 @@ def layout_sizes(d, n, k):
 # the current kernels (cold, L2 flushed by ncu before the launch); a key is
 # removed when the kernel changes.  Jacobian pencil launch, keyed by (d,
 # level, degree, precision): profiles/pencil_kernel_cubic3d_l6k2_fp32.md
-PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56661504 + 68608}
+PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56661504 + 58112}
 # one persistent Arnoldi launch (one exponential), keyed by (d, level,
 # degree, M, precision): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md (the
 # mixed-precision variant, double-float gather)
