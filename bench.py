@@ -210,18 +210,22 @@ def native(args, rank, world, local_rank):
     clocks = ClockSampler(visible.split(",")[local_rank] if visible else local_rank)
     clocks.start()
     launches0 = prob.ctx.launches
-    total_ms = 0.0
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # the steps are queued (sgk_solver_step_async), so the host enqueues the
+    # next flush and step while the GPU runs the current one; each step's
+    # device time is still bracketed by its own pair of events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
-        e0.record(stream)
-        prob.solver.step(1)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+        ev[i][0].record(stream)
+        prob.solver.step_async(1)
+        ev[i][1].record(stream)
+    prob.solver.wait()
+    torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     barrier()
     clk = clocks.stop()
     launches = prob.ctx.launches - launches0

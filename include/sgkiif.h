@@ -218,6 +218,22 @@ int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int o
  * is not an error.  On Newton failure the state is rolled back to the start
  * of the failing step and SGK_ENEWTON is returned.  Synchronises. */
 int sgk_solver_step(sgk_solver* s, int nsteps);
+/* Queue nsteps steps without waiting for them, for callers that keep the GPU
+ * busy while the host prepares more work.  Applies when the step is one
+ * device-driven graph (IIF2 with one species or no reaction, graphs on, no
+ * kernel timing); otherwise the steps run synchronously, as in
+ * sgk_solver_step, and a failure is returned at once.  Up to 32 steps are
+ * queued (fewer when 32 saved states would exceed 256 MB); beyond that the
+ * call waits for the queued ones.  Each queued step saves the state it starts
+ * from, so a failing step is rolled back as in sgk_solver_step and the steps
+ * queued after it are discarded.  The outcome is reported by
+ * sgk_solver_wait; every other call on the solver first finishes the queued
+ * steps (sgk_solver_step also reports a pending failure). */
+int sgk_solver_step_async(sgk_solver* s, int nsteps);
+/* Wait for the queued steps.  Returns SGK_OK, or the status of the first
+ * failing one (SGK_ENEWTON, SGK_ETIMEOUT), with the state rolled back to
+ * the start of that step. */
+int sgk_solver_wait(sgk_solver* s);
 /* Copy one species' coefficients (FP64) to host (on_device = 0) or to a
  * device array (on_device = 1); cap >= dof.  Host copies synchronise. */
 int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t cap, int on_device);

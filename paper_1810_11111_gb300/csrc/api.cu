@@ -421,6 +421,7 @@ int sgk_solver_set_state(sgk_solver* s, int species, const double* coeffs, int o
     return guarded(s->ctx, [&]() {
         SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
         set_device(s->ctx);
+        solver_drain(s);
         const double* src = coeffs;
         if (!on_device) {  // staged in the predictor's buffer (free between steps)
             SGK_CUDA_CHECK(cudaMemcpyAsync(s->vv.p + species * s->n, coeffs, s->n * sizeof(double),
@@ -437,7 +438,10 @@ int sgk_solver_step(sgk_solver* s, int nsteps) {
     if (!s || nsteps < 0) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {
         set_device(s->ctx);
-        const int rc = solver_step(s, nsteps);
+        solver_drain(s);
+        int rc = s->async_rc;  // a queued step failed: report it before stepping on
+        s->async_rc = SGK_OK;
+        if (rc == SGK_OK) rc = solver_step(s, nsteps);
         if (rc == SGK_ENEWTON) s->ctx->last_error = "Newton did not converge; state rolled back";
         SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
         if (rc != SGK_OK) throw SgkError{rc, s->ctx->last_error};
@@ -451,6 +455,7 @@ int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t 
         SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
         SGK_REQUIRE(cap >= s->n, SGK_EINVAL, "buffer too small");
         set_device(s->ctx);
+        solver_drain(const_cast<sgk_solver*>(s));
         SGK_CUDA_CHECK(cudaMemcpyAsync(out, s->U.p + species * s->n, s->n * sizeof(double),
                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                        s->ctx->stream));
@@ -461,8 +466,37 @@ int sgk_solver_get_state(const sgk_solver* s, int species, double* out, int64_t 
 
 int sgk_solver_stats(const sgk_solver* s, sgk_stats* out) {
     if (!s || !out) return SGK_EINVAL;
-    *out = s->stats;
-    return SGK_OK;
+    return guarded(s->ctx, [&]() {
+        set_device(s->ctx);
+        solver_drain(const_cast<sgk_solver*>(s));
+        *out = s->stats;
+        return SGK_OK;
+    });
+}
+
+int sgk_solver_step_async(sgk_solver* s, int nsteps) {
+    if (!s || nsteps < 0) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        set_device(s->ctx);
+        const int rc = solver_step_async(s, nsteps);  // the synchronous fallback reports at once
+        if (rc == SGK_ENEWTON) s->ctx->last_error = "Newton did not converge; state rolled back";
+        if (rc != SGK_OK) throw SgkError{rc, s->ctx->last_error};
+        return SGK_OK;
+    });
+}
+
+int sgk_solver_wait(sgk_solver* s) {
+    if (!s) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        set_device(s->ctx);
+        solver_drain(s);
+        const int rc = s->async_rc;
+        s->async_rc = SGK_OK;
+        if (rc != SGK_OK)
+            throw SgkError{rc, rc == SGK_ENEWTON ? "Newton did not converge; state rolled back"
+                                                 : "a queued step failed; state rolled back"};
+        return SGK_OK;
+    });
 }
 
 int sgk_iif_alpha(int r, double* alpha) {
@@ -480,6 +514,7 @@ int sgk_solver_set_source(sgk_solver* s, int species, int nterms, const double* 
         for (int m = 0; m < nterms; ++m) SGK_REQUIRE(std::isfinite(lambda[m]), SGK_EINVAL, "non-finite lambda");
         SGK_REQUIRE(nterms == 0 || s->has_rx, SGK_EUNSUPPORTED, "a source term needs a reaction term");
         set_device(s->ctx);
+        solver_drain(s);
         solver_set_source(s, species, nterms, lambda, coeffs_dev);
         SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
         return SGK_OK;
@@ -491,6 +526,7 @@ int sgk_solver_set_time(sgk_solver* s, double t) {
     return guarded(s->ctx, [&]() {
         SGK_REQUIRE(std::isfinite(t), SGK_EINVAL, "non-finite time");
         set_device(s->ctx);
+        solver_drain(s);
         solver_set_time(s, t);
         return SGK_OK;
     });
@@ -506,6 +542,7 @@ int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev) {
     if (!s || !u_dev || !f_dev) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {
         set_device(s->ctx);
+        solver_drain(s);
         solver_eval_reaction(s, u_dev, f_dev);
         return SGK_OK;
     });
@@ -515,6 +552,7 @@ int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, 
     if (!s || !u_dev || !w_dev || !jw_dev) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {
         set_device(s->ctx);
+        solver_drain(s);
         solver_jacobian_apply(s, u_dev, w_dev, jw_dev);
         return SGK_OK;
     });
@@ -525,6 +563,7 @@ int sgk_krylov_expv(sgk_solver* s, int species, const double* v_dev, double* w_d
     return guarded(s->ctx, [&]() {
         SGK_REQUIRE(species >= 0 && species < s->nspecies, SGK_EINVAL, "bad species");
         set_device(s->ctx);
+        solver_drain(s);
         solver_krylov_expv(s, species, v_dev, w_dev);
         KrylovScalars ks{};
         unsigned flags[2] = {0u, 0u};
@@ -547,6 +586,7 @@ int sgk_krylov_export(const sgk_solver* s, double* H, double* V, int64_t cap_V) 
     if (!s) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {
         set_device(s->ctx);
+        solver_drain(const_cast<sgk_solver*>(s));
         const long long n = s->n;
         const int M = s->M;
         if (H)

@@ -4,6 +4,9 @@
 #include "sgk_krylov.h"
 #include "sgk_quad.h"
 
+// most device-driven steps queued without waiting
+constexpr int SGK_ASYNC_SLOTS = 32;
+
 // An instantiated CUDA graph of a fixed launch sequence and the number of
 // kernels it holds.
 struct GraphCache {
@@ -78,7 +81,13 @@ struct sgk_solver {
     DevBuf<unsigned char> ctl;                 // StepCtl on the device
     // kernels per segment of the step graph (for the launch count)
     int64_t n_prefix = 0, n_resid = 0, n_cgpre = 0, n_cgbody = 0, n_adv = 0;
-    void* hrec = nullptr;  // pinned host record of the last launched step
+    // pinned host records of launched device-driven steps: slot 0 for a
+    // synchronous step, slots 0..nqueued-1 for queued ones
+    void* hrec = nullptr;
+    int nqueued = 0;      // steps queued by solver_step_async, not yet finished
+    int ring_slots = 0;   // capacity of the queue
+    DevBuf<double> ring;  // the state before each queued step (ring_slots x N), for the rollback
+    int async_rc = 0;     // first failure among finished queued steps, reported by sgk_solver_wait
     sgk_stats stats{};
     ~sgk_solver();
 };
@@ -98,8 +107,15 @@ void solver_state_changed(sgk_solver* s);
 // U_species = src (device, n values); keeps the cached F(U) on the device when
 // nothing changed
 void solver_set_state(sgk_solver* s, int species, const double* src_dev);
-void solver_step_launch(sgk_solver* s);
-int solver_step_finish(sgk_solver* s);
+// slot: the host record that receives the step's outcome; restore: the state
+// to roll back to on failure (null: the step graph's own copy)
+void solver_step_launch(sgk_solver* s, int slot = 0);
+int solver_step_finish(sgk_solver* s, int slot = 0, const double* restore = nullptr);
+// Queue nsteps device-driven steps without waiting (synchronous steps when
+// the solver is not device-driven); solver_drain finishes the queued ones in
+// order and keeps the first failure for sgk_solver_wait.
+int solver_step_async(sgk_solver* s, int nsteps);
+void solver_drain(sgk_solver* s);
 int solver_step(sgk_solver* s, int nsteps);
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);

@@ -883,10 +883,10 @@ struct StepRecord {
 
 // Queues one device-driven step (graph launch and the copies of its
 // outcome) without waiting.
-void solver_step_launch(sgk_solver* s) {
+void solver_step_launch(sgk_solver* s, int slot) {
     sgk_ctx* ctx = s->ctx;
     if (!s->g_step.exec) build_step_graph(s);
-    StepRecord* h = static_cast<StepRecord*>(s->hrec);
+    StepRecord* h = static_cast<StepRecord*>(s->hrec) + slot;
     write_time(s);
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
@@ -901,10 +901,10 @@ void solver_step_launch(sgk_solver* s) {
 
 // Completes a launched step once its stream has drained (the caller
 // synchronised it): statistics, and on failure the rollback of the state.
-int solver_step_finish(sgk_solver* s) {
+int solver_step_finish(sgk_solver* s, int slot, const double* restore) {
     sgk_ctx* ctx = s->ctx;
     const long long N = s->n * s->nspecies;
-    StepRecord* h = static_cast<StepRecord*>(s->hrec);
+    StepRecord* h = static_cast<StepRecord*>(s->hrec) + slot;
     StepCtl c{};
     if (s->has_rx) c = h->c;
     int rc = s->has_rx ? c.status : SGK_OK;
@@ -926,7 +926,8 @@ int solver_step_finish(sgk_solver* s) {
         rc = SGK_ETIMEOUT;
     }
     if (rc != SGK_OK) {
-        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, restore ? restore : s->Uprev.p, N * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
         solver_state_changed(s);
         SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     } else {
@@ -935,6 +936,51 @@ int solver_step_finish(sgk_solver* s) {
         s->fv_valid = s->has_rx;
     }
     return rc;
+}
+
+int solver_step_async(sgk_solver* s, int nsteps) {
+    if (!solver_device_steps(s)) return solver_step(s, nsteps);
+    if (s->async_rc != SGK_OK) return SGK_OK;  // a queued step failed: nothing more runs until it is reported
+    sgk_ctx* ctx = s->ctx;
+    const long long N = s->n * s->nspecies;
+    if (!s->ring.p) {
+        // up to 32 queued steps, and at most 256 MB of saved states
+        const long long cap = (256LL << 20) / (N * (long long)sizeof(double));
+        s->ring_slots = (int)std::max(1LL, std::min<long long>(SGK_ASYNC_SLOTS, cap));
+        s->ring.alloc((size_t)s->ring_slots * N);
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        if (s->nqueued == s->ring_slots) {
+            solver_drain(s);
+            if (s->async_rc != SGK_OK) break;
+        }
+        const int slot = s->nqueued;
+        SGK_CUDA_CHECK(cudaMemcpyAsync(s->ring.p + slot * N, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+        solver_step_launch(s, slot);
+        ++s->nqueued;
+    }
+    return SGK_OK;
+}
+
+void solver_drain(sgk_solver* s) {
+    if (s->nqueued == 0) return;
+    const long long N = s->n * s->nspecies;
+    const int q = s->nqueued;
+    s->nqueued = 0;
+    SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
+    for (int slot = 0; slot < q; ++slot) {
+        const int rc = solver_step_finish(s, slot, s->ring.p + slot * N);
+        if (rc != SGK_OK) {
+            // the state is that before the failing step; the steps queued
+            // after it are discarded, and so are any barrier flags they left
+            if (s->persistent)
+                SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * s->nspecies * sizeof(unsigned), s->ctx->stream));
+            SGK_CUDA_CHECK(cudaStreamSynchronize(s->ctx->stream));
+            if (s->async_rc == SGK_OK) s->async_rc = rc;
+            break;
+        }
+    }
 }
 
 bool solver_device_steps(const sgk_solver* s) { return step_graph_eligible(s) && !s->ctx->prof_mask; }
@@ -1165,7 +1211,7 @@ void solver_alloc(sgk_solver* s) {
     s->fcnt.alloc(FC_COUNT);
     SGK_CUDA_CHECK(cudaMemsetAsync(s->fcnt.p, 0, FC_COUNT * sizeof(unsigned), s->ctx->stream));
     s->ctl.alloc(sizeof(StepCtl));
-    SGK_CUDA_CHECK(cudaMallocHost(&s->hrec, sizeof(StepRecord)));
+    SGK_CUDA_CHECK(cudaMallocHost(&s->hrec, SGK_ASYNC_SLOTS * sizeof(StepRecord)));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->ctl.p, 0, sizeof(StepCtl), s->ctx->stream));
     s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && n <= arnoldi_persistent_max_n(s->ctx);
     if (s->persistent) {

@@ -100,6 +100,8 @@ _SIGS = {
     "sgk_solver_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int]),
     "sgk_solver_set_source": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "sgk_iif_alpha": (ctypes.c_int, [ctypes.c_int, _P]),
+    "sgk_solver_step_async": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sgk_solver_wait": (ctypes.c_int, [_P]),
     "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
     "sgk_solver_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),
@@ -330,6 +332,12 @@ class Solver:
 
     def step(self, nsteps=1):
         self.ctx.check(sgk_solver_step(self.h, int(nsteps)))
+
+    def step_async(self, nsteps=1):
+        self.ctx.check(sgk_solver_step_async(self.h, int(nsteps)))
+
+    def wait(self):
+        self.ctx.check(sgk_solver_wait(self.h))
 
     def stats(self):
         st = sgk_stats()

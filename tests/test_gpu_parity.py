@@ -660,6 +660,45 @@ def test_iifr_with_source_matches_oracle():
     prob.close()
 
 
+def test_async_steps_match_sync_steps():
+    # queued device-driven steps give the same states and statistics as
+    # synchronous ones, also past the 32-step queue
+    for cfg, nsteps in ((workloads.cubic3d(n=4, k=2), 5), (workloads.cubic3d(n=3, k=1), 40)):
+        for prec in (sgkiif.SGK_FP64, sgkiif.SGK_MIXED):
+            a = Problem(cfg, prec)
+            a.reset()
+            a.solver.step(nsteps)
+            sa, st_a = a.state(), a.solver.stats()
+            a.close()
+            b = Problem(cfg, prec)
+            b.reset()
+            b.solver.step_async(nsteps - 2)
+            b.solver.step_async(2)
+            b.solver.wait()
+            sb, st_b = b.state(), b.solver.stats()
+            b.close()
+            assert np.array_equal(sa[0], sb[0])
+            for key in ("steps", "newton_iters", "inner_iters", "krylov_calls"):
+                assert st_a[key] == st_b[key], key
+
+
+def test_async_failure_rolls_back():
+    # every step fails (a residual of 1e-300 is out of reach): the first
+    # queued one is rolled back, the later ones are discarded
+    cfg = dict(workloads.cubic3d(n=3, k=1), opts={"max_iter": 1, "tol": 1e-300})
+    prob = Problem(cfg, sgkiif.SGK_FP64)
+    prob.reset()
+    before = prob.state()[0]
+    prob.solver.step_async(3)
+    with pytest.raises(sgkiif.SgkError) as ei:
+        prob.solver.wait()
+    assert ei.value.code == sgkiif.SGK_ENEWTON
+    assert np.array_equal(prob.state()[0], before)
+    assert prob.solver.stats()["steps"] == 0
+    prob.solver.wait()  # nothing pending
+    prob.close()
+
+
 def test_dirichlet_heat_steps():
     # Several sine modes (zero on the boundary).  A single mode is nearly an
     # eigenvector: its Krylov space is exhausted after a few Arnoldi steps and
