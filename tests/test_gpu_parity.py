@@ -699,6 +699,24 @@ def test_async_failure_rolls_back():
     prob.close()
 
 
+def test_async_barrier_timeout_rolls_back(monkeypatch):
+    # failure injected on the host after set-up: the step graph captured
+    # with SGK_TEST_BARRIER_STALL set waits for one CTA more than the grid
+    # has at every barrier, so the queued steps time out (about a second
+    # each); the wait reports SGK_ETIMEOUT and the state is the starting one
+    prob = Problem(workloads.heat2d(), sgkiif.SGK_FP64)
+    prob.reset()
+    before = prob.state()[0]
+    monkeypatch.setenv("SGK_TEST_BARRIER_STALL", "1")
+    prob.solver.step_async(2)
+    with pytest.raises(sgkiif.SgkError) as ei:
+        prob.solver.wait()
+    assert ei.value.code == sgkiif.SGK_ETIMEOUT
+    assert np.array_equal(prob.state()[0], before)
+    assert prob.solver.stats()["steps"] == 0
+    prob.close()
+
+
 def test_dirichlet_heat_steps():
     # Several sine modes (zero on the boundary).  A single mode is nearly an
     # eigenvector: its Krylov space is exhausted after a few Arnoldi steps and
