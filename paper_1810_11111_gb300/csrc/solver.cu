@@ -14,8 +14,9 @@
 // vector and the state stay FP64.  The Newton and CG vector steps are fused
 // with their inner products and control decisions.  Because FP32
 // reaction passes put a floor under the residual, the mixed outer loop also
-// stops when ||G|| no longer halves and is below 1e-8 max(1, ||W||) (the
-// Newton iteration has reached that floor).
+// stops when ||G|| no longer halves and is below 1e-7 max(1, ||W||) (the
+// Newton iteration has reached that floor: stiff instances, c ~ 100 with
+// |u| ~ 1, stall at 2e-8).
 #include <cmath>
 #include <cstring>
 
@@ -39,7 +40,7 @@ struct StepCtl {
 __device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol) {
     const double w = fmax(1.0, wnorm);
     c->stop = tol * w;
-    c->floor_accept = 1e-8 * w;
+    c->floor_accept = 1e-7 * w;
     c->prev = INFINITY;
     c->last_g = 0.0;
     c->it = 0;
@@ -622,7 +623,7 @@ int newton(sgk_solver* s) {
                  s->scal.p + 6, (StepCtl*)nullptr, 0.0);
     const double wnorm = read_scalar(s, s->scal.p + 6);
     const double stop = s->opts.tol * std::max(1.0, wnorm);
-    const double floor_accept = 1e-8 * std::max(1.0, wnorm);
+    const double floor_accept = 1e-7 * std::max(1.0, wnorm);
     double prev = INFINITY;
     for (int it = 0; it <= s->opts.max_iter; ++it) {
         run_graph(s, s->g_resid, KC_VECTOR, [&]() {
@@ -711,7 +712,7 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, 
 // residual norms, so a step needs one host synchronisation (to read the
 // outcome) instead of one per Newton and CG iteration.  The control logic is
 // that of the host loop: stop at ||G|| <= tol max(1, ||W||), the mixed-mode
-// acceptance of a stagnating residual below 1e-8 max(1, ||W||), at most
+// acceptance of a stagnating residual below 1e-7 max(1, ||W||), at most
 // max_iter corrections, CG to a relative residual inner_tol.
 
 namespace {
