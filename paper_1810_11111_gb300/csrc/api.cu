@@ -534,8 +534,12 @@ int sgk_solver_set_time(sgk_solver* s, double t) {
 
 int sgk_solver_get_time(const sgk_solver* s, double* t) {
     if (!s || !t) return SGK_EINVAL;
-    *t = s->t;
-    return SGK_OK;
+    return guarded(s->ctx, [&]() {
+        set_device(s->ctx);
+        solver_drain(const_cast<sgk_solver*>(s));  // queued steps advance the time when they finish
+        *t = s->t;
+        return SGK_OK;
+    });
 }
 
 int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev) {
