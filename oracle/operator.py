@@ -122,3 +122,78 @@ def dense_sparse_operator(idx, S, kappa):
     A = dense_full_operator(idx.d, S, kappa)
     f = idx.flat_full_indices()
     return A[np.ix_(f, f)]
+
+
+# ------------------------------------------- full diffusion tensor (NEXT) ---
+
+def cross_blocks_1d(N, k, bc=PERIODIC):
+    """1D pieces of the mixed-derivative part of the SIPG form of Section 2
+    for a constant SPD tensor K, in the hierarchical basis of V_N^k:
+        P[a, b] = sum over finest cells of int v_a' v_b dx
+                  (derivative of the test function, value of the trial one),
+        E[a, b] = sum over faces of [v_a] {v_b}
+                  (jump of the test function, average of the trial values),
+    with [v] = v(x-) - v(x+) on interior faces and, for zero Dirichlet, the
+    one-sided trace times the outward normal on the two boundary faces (and
+    the one-sided trace as the average)."""
+    alpert = alpert_coefficients(k)
+    H = hier_size(N, k)
+    ncell = 1 << N
+    h = 2.0 ** (-N)
+    xi, w = gauss_legendre(k + 1)
+    cells = np.repeat(np.arange(ncell), k + 1)
+    V, D = hier_eval(N, k, cells, np.tile(xi, ncell), alpert)
+    wq = np.tile(h * w / 2.0, ncell)
+    P = D.T @ (V * wq[:, None])
+    faces = list(range(ncell)) if bc == PERIODIC else list(range(ncell + 1))
+    E = np.zeros((H, H))
+    for f in faces:
+        left_cell = (f - 1) % ncell if bc == PERIODIC else f - 1
+        right_cell = f % ncell if bc == PERIODIC else f
+        has_left = bc == PERIODIC or f > 0
+        has_right = bc == PERIODIC or f < ncell
+        vl = vr = np.zeros(H)
+        if has_left:
+            vl = hier_eval(N, k, [left_cell], [1.0], alpert)[0][0]
+        if has_right:
+            vr = hier_eval(N, k, [right_cell], [-1.0], alpert)[0][0]
+        if has_left and has_right:
+            J, A = vl - vr, 0.5 * (vl + vr)
+        elif has_right:
+            J, A = -vr, vr
+        else:
+            J, A = vl, vl
+        E += np.outer(J, A)
+    return P, E
+
+
+def dense_full_operator_general(d, S, P, E, K):
+    """A = -(sum_i K_ii S_i + sum_{i<j} K_ij B_ij) on the full tensor space
+    (tiny grids), with B_ij the mixed terms of the form: the volume integrals
+    K_ij int (d_j u d_i v + d_i u d_j v), the face integrals of the averaged
+    tangential derivative of u against the normal jump of v, and their
+    symmetric counterparts.  In 1D factors (test index first, direction i
+    then j):
+        B_ij = P x P^T + P^T x P - E x P^T - P^T x E - E^T x P - P x E^T."""
+    K = np.asarray(K, dtype=np.float64)
+    H = S.shape[0]
+    A = dense_full_operator(d, S, np.diag(K))
+    pairs = [(P, P.T), (P.T, P), (-E, P.T), (-P.T, E), (-E.T, P), (-P, E.T)]
+    for i in range(d):
+        for j in range(i + 1, d):
+            if K[i, j] == 0.0:
+                continue
+            for X, Y in pairs:
+                term = np.ones((1, 1))
+                for m in range(d):
+                    term = np.kron(term, X if m == i else (Y if m == j else np.eye(H)))
+                A -= K[i, j] * term
+    return A
+
+
+def dense_sparse_operator_general(idx, S, P, E, K):
+    """The full-tensor operator of dense_full_operator_general restricted to
+    the sparse index set (the Galerkin matrix of the sparse space)."""
+    A = dense_full_operator_general(idx.d, S, P, E, K)
+    f = idx.flat_full_indices()
+    return A[np.ix_(f, f)]
