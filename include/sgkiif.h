@@ -154,6 +154,21 @@ int sgk_operator_export_1d(const sgk_op* op, double* out, int64_t cap);
  * overlap.  Asynchronous. */
 int sgk_matvec(const sgk_op* op, const void* x_dev, void* y_dev, int precision);
 
+/* The 1D pieces of the mixed-derivative terms of the SIPG form of Section 2
+ * for a full constant SPD diffusion tensor K (off-diagonal K_ij), in the
+ * hierarchical basis of level n, degree k (H = (k+1) 2^n):
+ *   P[a*H + b] = sum over finest cells of int v_a' v_b dx,
+ *   E[a*H + b] = sum over faces of [v_a] {v_b} (jump of v_a, left trace minus
+ *                right trace, one-sided times the outward normal on
+ *                zero-Dirichlet boundary faces; average of the traces of v_b,
+ *                one-sided on boundary faces).
+ * Per pair i < j the operator adds -K_ij times
+ *   P x P^T + P^T x P - E x P^T - P^T x E - E^T x P - P x E^T
+ * (factors along directions i and j).  Host-only (the matvec with these
+ * terms is not provided yet); P and E are host arrays of cap >= H*H doubles.
+ * n <= 10.  Errors: SGK_EINVAL (arguments), SGK_ENOMEM. */
+int sgk_cross_blocks_1d(int n, int k, int bc, double* P, double* E, int64_t cap);
+
 /* ------------------------------------------------------------- projection */
 
 /* L2 projection (Theorem 2.4: u_h(0) = P u_0) of

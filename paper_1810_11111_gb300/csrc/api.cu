@@ -295,6 +295,24 @@ int sgk_operator_export_1d(const sgk_op* op, double* out, int64_t cap) {
     });
 }
 
+int sgk_cross_blocks_1d(int n, int k, int bc, double* P, double* E, int64_t cap) {
+    if (!P || !E || n < 0 || n > 10 || k < 1 || k > 3 || (bc != SGK_PERIODIC && bc != SGK_DIRICHLET0))
+        return SGK_EINVAL;
+    const int64_t H = (int64_t)(k + 1) << n;
+    if (cap < H * H) return SGK_EINVAL;
+    try {
+        Tables1D tab;
+        build_transform_tables(n, k, tab);
+        std::vector<double> p, e;
+        build_cross_hier(tab, bc, p, e);
+        std::memcpy(P, p.data(), sizeof(double) * H * H);
+        std::memcpy(E, e.data(), sizeof(double) * H * H);
+    } catch (...) {
+        return SGK_ENOMEM;
+    }
+    return SGK_OK;
+}
+
 int sgk_matvec(const sgk_op* op, const void* x_dev, void* y_dev, int precision) {
     if (!op || !x_dev || !y_dev || x_dev == y_dev) return SGK_EINVAL;
     return guarded(op->ctx, [&]() {

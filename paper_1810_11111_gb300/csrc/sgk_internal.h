@@ -229,6 +229,10 @@ std::vector<double> alpert_coefficients(int k);
 void build_transform_tables(int N, int k, Tables1D& out);
 // 1D SIPG matrix in the hierarchical basis, dense row-major H x H.
 std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma);
+// The 1D pieces of the mixed-derivative terms for a full diffusion tensor,
+// dense H x H in the hierarchical basis: P[a][b] = int v_a' v_b over the
+// finest cells, E[a][b] = sum over faces of [v_a] {v_b}.
+void build_cross_hier(const Tables1D& tab, int bc, std::vector<double>& P, std::vector<double>& E);
 
 // --------------------------------------------------------- fiber engine ---
 

@@ -391,3 +391,95 @@ std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma) {
         }
     return S;
 }
+
+namespace {
+
+// A = T^T A_L T for a matrix A_L given by rows over the finest-cell Legendre
+// index (dense H x H output, rows and columns hierarchical).
+std::vector<double> rotate_dense(const Tables1D& tab, const std::vector<std::vector<std::pair<int, ld>>>& AL) {
+    const int H = tab.H;
+    std::vector<ld> Z((size_t)H * H, 0);  // A_L T
+    for (int y = 0; y < H; ++y)
+        for (auto& e : AL[y])
+            for (int q = tab.T.ptr[e.first]; q < tab.T.ptr[e.first + 1]; ++q)
+                Z[(size_t)y * H + tab.T.col[q]] += e.second * (ld)tab.T.val[q];
+    std::vector<double> out((size_t)H * H, 0.0);
+    std::vector<ld> acc(H);
+    for (int a = 0; a < H; ++a) {
+        std::fill(acc.begin(), acc.end(), (ld)0);
+        for (int q = tab.Tt.ptr[a]; q < tab.Tt.ptr[a + 1]; ++q) {
+            const ld t = tab.Tt.val[q];
+            const ld* z = &Z[(size_t)tab.Tt.col[q] * H];
+            for (int b = 0; b < H; ++b) acc[b] += t * z[b];
+        }
+        for (int b = 0; b < H; ++b) out[(size_t)a * H + b] = (double)acc[b];
+    }
+    return out;
+}
+
+}  // namespace
+
+void build_cross_hier(const Tables1D& tab, int bc, std::vector<double>& P, std::vector<double>& E) {
+    // Finest-cell Legendre basis L_r = h^{-1/2} sqrt(2r+1) P_r(xi):
+    // int L_a' L_b over a cell = 2 sqrt((2a+1)(2b+1)) / h for b < a with a + b
+    // odd (int_{-1}^{1} P_a' P_b = 2 there, 0 otherwise); traces at the right
+    // and left cell ends h^{-1/2} sqrt(2r+1) and (-1)^r times that.
+    const int k = tab.k, kp1 = k + 1, N = tab.N, H = tab.H;
+    const int nc = 1 << N;
+    const ld h = std::ldexp((ld)1, -N);
+    std::vector<ld> vr(kp1), vl(kp1);
+    for (int r = 0; r < kp1; ++r) {
+        vr[r] = std::sqrt((ld)(2 * r + 1)) / std::sqrt(h);
+        vl[r] = (r % 2 == 0) ? vr[r] : -vr[r];
+    }
+    std::vector<std::vector<std::pair<int, ld>>> PL(H), EL(H);
+    for (int c = 0; c < nc; ++c)
+        for (int a = 0; a < kp1; ++a)
+            for (int b = 0; b < a; ++b)
+                if ((a + b) % 2 == 1)
+                    PL[c * kp1 + a].push_back(
+                        {c * kp1 + b, 2 * std::sqrt((ld)(2 * a + 1)) * std::sqrt((ld)(2 * b + 1)) / h});
+    // faces: jump of the test function (left trace minus right trace) against
+    // the average of the trial traces; one-sided with the outward normal on
+    // zero-Dirichlet boundary faces
+    const int nfaces = bc == SGK_PERIODIC ? nc : nc + 1;
+    for (int f = 0; f < nfaces; ++f) {
+        std::vector<std::pair<int, ld>> J, A;
+        const bool interior = bc == SGK_PERIODIC || (f > 0 && f < nc);
+        if (interior) {
+            const int L = (f - 1 + nc) % nc, R = f % nc;
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({L * kp1 + r, vr[r]});
+                A.push_back({L * kp1 + r, vr[r] / 2});
+            }
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({R * kp1 + r, -vl[r]});
+                A.push_back({R * kp1 + r, vl[r] / 2});
+            }
+        } else if (f == 0) {
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({r, -vl[r]});
+                A.push_back({r, vl[r]});
+            }
+        } else {
+            for (int r = 0; r < kp1; ++r) {
+                J.push_back({(nc - 1) * kp1 + r, vr[r]});
+                A.push_back({(nc - 1) * kp1 + r, vr[r]});
+            }
+        }
+        // periodic with nc == 1: both sides are the same cell, so entries add
+        for (auto& a : J)
+            for (auto& b : A) {
+                bool merged = false;
+                for (auto& e : EL[a.first])
+                    if (e.first == b.first) {
+                        e.second += a.second * b.second;
+                        merged = true;
+                        break;
+                    }
+                if (!merged) EL[a.first].push_back({b.first, a.second * b.second});
+            }
+    }
+    P = rotate_dense(tab, PL);
+    E = rotate_dense(tab, EL);
+}

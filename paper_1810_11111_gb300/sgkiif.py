@@ -100,6 +100,7 @@ _SIGS = {
     "sgk_solver_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int]),
     "sgk_solver_set_source": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "sgk_iif_alpha": (ctypes.c_int, [ctypes.c_int, _P]),
+    "sgk_cross_blocks_1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int64]),
     "sgk_solver_step_async": (ctypes.c_int, [_P, ctypes.c_int]),
     "sgk_solver_wait": (ctypes.c_int, [_P]),
     "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),

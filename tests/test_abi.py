@@ -74,3 +74,24 @@ def test_iif_alpha_is_adams_moulton(lib):
     out = np.zeros(8)
     for r in (1, 7):
         assert sgkiif.sgk_iif_alpha(r, out.ctypes.data) == sgkiif.SGK_EINVAL
+
+
+def test_cross_blocks_match_the_oracle(lib):
+    # the library's host tables for the mixed-derivative terms (built from
+    # closed-form Legendre traces in C++) against the oracle's direct
+    # evaluation of the hierarchical functions; no GPU involved
+    import numpy as np
+
+    from oracle.operator import DIRICHLET0, PERIODIC, cross_blocks_1d
+    from paper_1810_11111_gb300 import sgkiif
+    for n, k in ((0, 1), (1, 2), (3, 1), (4, 2), (3, 3)):
+        for bc, obc in ((sgkiif.SGK_PERIODIC, PERIODIC), (sgkiif.SGK_DIRICHLET0, DIRICHLET0)):
+            H = (k + 1) << n
+            P = np.zeros(H * H)
+            E = np.zeros(H * H)
+            assert sgkiif.sgk_cross_blocks_1d(n, k, bc, P.ctypes.data, E.ctypes.data, H * H) == sgkiif.SGK_OK
+            Pw, Ew = cross_blocks_1d(n, k, obc)
+            for got, want in ((P.reshape(H, H), Pw), (E.reshape(H, H), Ew)):
+                assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), (n, k, bc)
+    out = np.zeros(4)
+    assert sgkiif.sgk_cross_blocks_1d(1, 1, 0, out.ctypes.data, out.ctypes.data, 4) == sgkiif.SGK_EINVAL
