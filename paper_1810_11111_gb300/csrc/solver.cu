@@ -1,4 +1,5 @@
-// IIF2 time stepping (eq. krylov5) with a Newton implicit stage.
+// IIF time stepping with a Newton implicit stage: IIF2 (eq. krylov5) and the
+// r-th order schemes of eqs. krylov3, krylov4 (IIF3 is eq. krylov6).
 //
 //   v_s   = U_s^n + dt/2 F_s(U^n)                    (predictor)
 //   W_s   = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v_s  (per species)
@@ -6,6 +7,10 @@
 //         (I - dt/2 J_F(U)) delta = -G(U), U += delta,
 //   inner solver: CG for one species (symmetric), restarted GMRES for systems;
 //   outer stop ||G||_2 <= tol max(1, ||W||_2); on failure the step is undone.
+// For order r the predictor weight dt/2 becomes alpha_0 dt, each older
+// F(U^{n-i}) adds alpha_{-i} dt exp((i+1) dt A_s) F_s(U^{n-i}) to W_s, and
+// the Newton weight is alpha_1 dt.  F(U, t) includes the source terms at the
+// time of its argument.
 //
 // All vectors live on the device; the host only reads back the scalars that
 // decide loop exits (none at all in the device-driven step).  In SGK_MIXED
