@@ -22,7 +22,7 @@ trace from the last cell.  Zero Dirichlet: at x = 0, [q] = -q(0^+) and
 """
 import numpy as np
 
-from .basis import alpert_coefficients, gauss_legendre, hier_eval, hier_level_count, hier_size
+from .basis import alpert_coefficients, gauss_legendre, hier_eval, hier_level_count, hier_level_offset, hier_size
 
 PERIODIC = 0
 DIRICHLET0 = 1
@@ -197,3 +197,52 @@ def dense_sparse_operator_general(idx, S, P, E, K):
     A = dense_full_operator_general(idx.d, S, P, E, K)
     f = idx.flat_full_indices()
     return A[np.ix_(f, f)]
+
+
+def sparse_matvec_general(idx, S, P, E, K, x):
+    """y = A x for the full-tensor operator of dense_full_operator_general,
+    restricted to the sparse index set, without forming it.  The diagonal
+    part is sparse_matvec.  For a pair i < j and each tuple of the other
+    levels, the blocks with l_i + l_j <= N - |rest| form a triangle of the 2D
+    hierarchical index space (a_i, a_j); x is placed on the full square
+    (zero outside the triangle), the six Kronecker products act along the
+    two axes, and the result is read back on the triangle: the Galerkin
+    matrix of the sparse space is the full one restricted to its indices."""
+    K = np.asarray(K, dtype=np.float64)
+    d, N, k = idx.d, idx.N, idx.k
+    y = sparse_matvec(idx, S, np.diag(K), x)
+    pairs = [(P, P.T), (P.T, P), (-E, P.T), (-P.T, E), (-E.T, P), (-P, E.T)]
+    for i in range(d):
+        for j in range(i + 1, d):
+            if K[i, j] == 0.0:
+                continue
+            groups = {}
+            for l in idx.tuples:
+                rest = tuple(l[m] for m in range(d) if m not in (i, j))
+                groups.setdefault(rest, []).append(l)
+            for rest, blocks in groups.items():
+                L = N - sum(rest)
+                Hs = hier_level_offset(L, k) + hier_level_count(L, k)
+                shape = [idx.block(x, blocks[0]).shape[m] for m in range(d)]
+                shape[i] = shape[j] = Hs
+                full = np.zeros(shape)
+                for l in blocks:
+                    o_i, o_j = hier_level_offset(l[i], k), hier_level_offset(l[j], k)
+                    c_i, c_j = hier_level_count(l[i], k), hier_level_count(l[j], k)
+                    sl = [slice(None)] * d
+                    sl[i] = slice(o_i, o_i + c_i)
+                    sl[j] = slice(o_j, o_j + c_j)
+                    full[tuple(sl)] = idx.block(x, l)
+                res = np.zeros_like(full)
+                for X, Y in pairs:
+                    t = np.moveaxis(np.tensordot(X[:Hs, :Hs], full, axes=([1], [i])), 0, i)
+                    res += np.moveaxis(np.tensordot(Y[:Hs, :Hs], t, axes=([1], [j])), 0, j)
+                for l in blocks:
+                    o_i, o_j = hier_level_offset(l[i], k), hier_level_offset(l[j], k)
+                    c_i, c_j = hier_level_count(l[i], k), hier_level_count(l[j], k)
+                    sl = [slice(None)] * d
+                    sl[i] = slice(o_i, o_i + c_i)
+                    sl[j] = slice(o_j, o_j + c_j)
+                    yb = idx.block(y, l)
+                    yb -= K[i, j] * res[tuple(sl)]
+    return y

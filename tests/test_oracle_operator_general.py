@@ -83,3 +83,17 @@ def test_periodic_rayleigh_quotient_converges():
     assert errs[-1] < 2e-4, errs
     for e0, e1 in zip(errs, errs[1:]):
         assert np.log2(e0 / e1) > 3.0, errs
+
+
+def test_matrix_free_matvec_equals_the_restricted_matrix():
+    # two implementations of the same definition: the dense full-tensor
+    # matrix restricted to the index set, and the per-pair triangle form
+    from oracle.operator import sparse_matvec_general
+    rng = np.random.default_rng(17)
+    for d, N, k, bc in ((2, 4, 1, PERIODIC), (2, 3, 2, DIRICHLET0), (3, 3, 1, PERIODIC), (3, 2, 2, DIRICHLET0)):
+        K = _spd(d, rng)
+        idx, A = _operator(d, N, k, K, bc)
+        P, E = cross_blocks_1d(N, k, bc)
+        x = rng.standard_normal(idx.dof)
+        y = sparse_matvec_general(idx, sipg_1d(N, k, bc), P, E, K, x)
+        assert np.linalg.norm(y - A @ x) <= 1e-12 * np.linalg.norm(A @ x), (d, N, k, bc)
