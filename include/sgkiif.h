@@ -52,9 +52,13 @@ extern "C" {
 
 /* precision modes */
 #define SGK_FP64 0   /* all arithmetic in FP64 */
-#define SGK_MIXED 1  /* matvec, axpys, reaction/Jacobian passes in FP32;
-                        Gram-Schmidt inner products, norms, exp(tau H),
-                        Newton residual in FP64 */
+#define SGK_MIXED 1  /* solvers: the Jacobian products J_F(U) w of the
+                        Newton inner solve in FP32; the Krylov matvec in
+                        double-float arithmetic (pairs of FP32 numbers, about
+                        48 significand bits); every F(U) (predictor and
+                        Newton residual), the Gram-Schmidt inner products and
+                        norms, exp(tau H), the state and the Newton residual
+                        in FP64.  sgk_matvec with SGK_MIXED is plain FP32. */
 
 /* boundary conditions (Section 2.1, eq. sp3) */
 #define SGK_PERIODIC 0
@@ -91,6 +95,13 @@ int sgk_ctx_destroy(sgk_ctx* ctx);
 const char* sgk_last_error(const sgk_ctx* ctx);
 /* Number of kernel launches this context has issued since creation. */
 int64_t sgk_ctx_launch_count(const sgk_ctx* ctx);
+/* Target architecture of the library's device code as the runtime sees it
+ * (cudaFuncGetAttributes binaryVersion of one of its kernels, major * 10 +
+ * minor: 103 for sm_103a) in *arch.  No counterpart in the paper; a check
+ * that the loaded binary is the one built for this GPU.  Errors: SGK_EINVAL
+ * (null arch), SGK_ECUDA (no device, or no image of the kernels loads on
+ * it). */
+int sgk_binary_arch(int* arch);
 /* Kernel timing for benchmarks (no counterpart in the paper).  While bit i of
  * mask is set, every launch of kernel class i is bracketed by two CUDA events
  * on the context's stream.  Classes: 0 SIPG matvec, 1 change of basis to the
@@ -119,6 +130,10 @@ int sgk_index_destroy(sgk_index* idx);
 int64_t sgk_index_dof(const sgk_index* idx);
 /* Number of level tuples, C(n+d, d). */
 int64_t sgk_index_ntuples(const sgk_index* idx);
+/* The same count as sgk_index_dof without building anything (host only, no
+ * device needed): (k+1)^d sum_{|l|_1 <= n} prod_m max(1, 2^{l_m-1}), the
+ * dimension of the space of eq. sp14.  -1 for d, n or k out of range. */
+int64_t sgk_dof(int d, int n, int k);
 /* Copy the tuple table to host: levels[ntuples*d] (row per tuple) and
  * offsets[ntuples+1] (block starts, offsets[ntuples] = dof).  cap is the
  * number of tuples the buffers hold; SGK_EINVAL if cap < ntuples.
@@ -137,9 +152,25 @@ int sgk_index_lookup(const sgk_index* idx, const int32_t* levels, int64_t count,
  * once on the host in the hierarchical basis; A = -sum_i kappa_i S along
  * direction i restricted to the index set (unidirectional principle,
  * Section 4).  kappa: host array of d positive values.  bc: SGK_PERIODIC or
- * SGK_DIRICHLET0.  Errors: SGK_EINVAL. */
+ * SGK_DIRICHLET0.  Errors: SGK_EINVAL.  For a tensor with off-diagonal
+ * entries see sgk_operator_assemble_full. */
 int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, int bc, double sigma,
                           sgk_op** out);
+/* The same operator for a full constant symmetric positive definite
+ * diffusion tensor K (Section 2.1: the PDE's k(x) constant with off-diagonal
+ * entries; the bilinear form B with k grad u . grad v and the face terms of
+ * eq. sp3).  K: host array d x d, row-major, symmetric, positive definite
+ * (checked by a Cholesky factorisation), else SGK_EINVAL.  The diagonal
+ * enters as for sgk_operator_assemble; every pair i < j with K_ij != 0 adds
+ * -K_ij B_ij, B_ij = P x P^T + P^T x P - E x P^T - P^T x E - E^T x P -
+ * P x E^T in 1D factors along i and j (P: test-function derivative against
+ * trial value over the finest cells; E: test jump against trial average over
+ * the faces), restricted to the index set.  sgk_matvec applies it in two
+ * launches (the diagonal gather, then the mixed terms); solvers on such an
+ * operator run the Arnoldi process as a sequence of launches instead of the
+ * persistent kernel. */
+int sgk_operator_assemble_full(sgk_ctx* ctx, const sgk_index* idx, const double* K, int bc, double sigma,
+                               sgk_op** out);
 /* Multiply-adds of one sgk_matvec: the entries of the 1D matrix rows each
  * output coefficient visits, summed over directions (the algorithmic work of
  * the unidirectional matvec of Section 4); -1 for a null handle. */
@@ -179,6 +210,21 @@ int sgk_cross_blocks_1d(int n, int k, int bc, double* P, double* E, int64_t cap)
  * Asynchronous. */
 int sgk_project_separable(sgk_ctx* ctx, const sgk_index* idx, int nterms, const double* amp, const int* wavenum,
                           const int* kind, double const_term, double* coeffs_dev);
+/* Load vector of non-zero Dirichlet data (Section 2.1: the boundary term of
+ * L(v) for u = g on dOmega): b_a = -int_{dOmega} (k grad v_a . n - sigma/h
+ * v_a) g ds, h the finest mesh size, k = diag(kappa), for g the restriction
+ * to the boundary of const_term + sum_t amp[t] prod_m g_{t,m}(2 pi
+ * wavenum[t*d+m] x_m), g = sin (kind 0) or cos (kind 1) -- the family of
+ * sgk_project_separable.  The paper prints the penalty part with a plus
+ * sign; the sign taken here is the one under which smooth solutions satisfy
+ * the scheme (exact for polynomial data of degree <= k).  With the
+ * zero-Dirichlet operator (SGK_DIRICHLET0, same kappa and sigma) the
+ * semi-discrete system is dU/dt = A U + F(U) + b; data e^{lambda t} g(x)
+ * enter a solver as the source term (lambda, b) (sgk_solver_set_source).
+ * kappa: host array of d positive values; b_dev: caller-owned device array
+ * of dof doubles.  Synchronises.  Errors: SGK_EINVAL. */
+int sgk_dirichlet_load(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, double sigma, int nterms,
+                       const double* amp, const int* wavenum, const int* kind, double const_term, double* b_dev);
 
 /* ---------------------------------------------------------------- solver */
 
@@ -194,7 +240,9 @@ typedef struct sgk_reaction {
 
 /* Newton / inner-solver options; zero fields take the defaults shown. */
 typedef struct sgk_newton_opts {
-    double tol;        /* outer stop ||G||_2 <= tol max(1, ||W||_2); 1e-12 (FP64), 1e-9 (mixed) */
+    double tol;        /* outer stop ||G||_2 <= tol max(||W||_2, ||G(W)||_2), relative to
+                          the stage's scale (W the exponential term, G(W) the first
+                          residual); 1e-12 */
     int max_iter;      /* outer cap; 50 */
     double inner_tol;  /* CG/GMRES relative residual; 1e-13 (FP64), 1e-6 (mixed) */
     int inner_max;     /* inner iteration cap; 500 */
@@ -290,9 +338,11 @@ int sgk_solver_stats(const sgk_solver* s, sgk_stats* out);
  * vectors are caller-owned device arrays, FP64, species-stacked.  They use
  * the solver's precision mode internally and are asynchronous. */
 /* F(U) = (int f(u_h) v_a dx)_a, finest-grid Gauss quadrature (Section 4),
- * plus the source terms at the solver's time t^n when set. */
+ * plus the source terms at the solver's time t^n when set; FP64 in both
+ * precision modes. */
 int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev);
-/* J_F(U) w = (int f'(u_h) w_h v_a dx)_a with the same quadrature. */
+/* J_F(U) w = (int f'(u_h) w_h v_a dx)_a with the same quadrature (FP32
+ * passes in SGK_MIXED). */
 int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, double* jw_dev);
 /* w = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v for species s (eqs.
  * krylov7-krylov8, Arnoldi with classical Gram-Schmidt applied twice).
@@ -328,14 +378,17 @@ int sgk_expm_e1(sgk_ctx* ctx, int m, const double* X, double tau, double* y);
  * independent of each other.  For 56 < m <= 64 they live in a fixed
  * 8 * 64 * 64 doubles (256 KB) array compiled into the library, held by
  * every GPU that loads it until the process exits; m above
- * SGK_EXPM_NOALLOC_MAX_M is rejected with SGK_EINVAL.  The first such call on
- * a device looks up that array's device address (cudaGetSymbolAddress), so
- * make it once on each device before any stream capture.  Calls with
- * m > 56 share the one array: those that may overlap on the GPU (different
- * streams, or different host threads) race and must be serialised by the
- * caller.  No
+ * SGK_EXPM_NOALLOC_MAX_M is rejected with SGK_EINVAL.  The first call on a
+ * device does a one-time set-up there: it looks up that array's device
+ * address (cudaGetSymbolAddress) and raises the cluster kernel's
+ * shared-memory limit (cudaFuncSetAttribute), so make one call on each
+ * device before any stream capture.  The set-up is kept per device and made
+ * again if the device's context changes (after cudaDeviceReset), so that an
+ * address from a destroyed context is never used.  Calls with m > 56 share
+ * the one array: those that may overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  No
  * context, no allocation, no host copy.  Errors: SGK_EINVAL (bad m or null
- * pointer), SGK_ECUDA (no current device, or the launch failed). */
+ * pointer), SGK_ECUDA (no current device, or the set-up or launch failed). */
 int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream);
 
 /* -------------------------------------------------------------- serving */
@@ -408,6 +461,24 @@ typedef struct sgk_server_stats {
  * invalid shape.  Host only. */
 int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int precision, int has_reaction);
 
+/* Estimated arithmetic of one IIF2 step of a problem, for sharding
+ * independent instances across GPUs (no counterpart in the paper): per
+ * species the Arnoldi process (M matvecs of 2 (entries per row) DOF operations and
+ * the two Gram-Schmidt passes, 4 M^2 DOF) and, with a reaction, about three
+ * finest-grid passes (predictor, residual and one Jacobian product: the
+ * sum-factorised quadrature of (2^n)^d cells).  Relative units: only ratios
+ * between instances matter.  -1 for an invalid shape.  Host only. */
+double sgk_estimate_work(int d, int n, int k, int nspecies, int krylov_m, int has_reaction);
+/* Split `count` independent work items of estimated cost cost[i] >= 0 over
+ * nparts parts (ranks) so that the largest part sum is small: the items in
+ * order of decreasing cost (ties by index), each to the part with the
+ * smallest sum so far (ties by part index) -- the longest-processing-time
+ * rule, at most 4/3 of the optimum.  part_of[count] receives each item's
+ * part; deterministic, so every rank computes the same split without
+ * communicating.  Errors: SGK_EINVAL (null arrays, count < 0, nparts < 1, a
+ * negative or non-finite cost).  Host only. */
+int sgk_partition(int count, const double* cost, int nparts, int* part_of);
+
 /* Start a server on device with nworkers (1 .. 64) workers and a device
  * memory budget of mem_budget_bytes (0 = 80% of the memory free at start).
  * aging_ms: how long a request that does not fit may be overtaken (<= 0:
@@ -434,18 +505,23 @@ int sgk_server_destroy(sgk_server* srv);
 /* ------------------------------------------------------------- batching */
 
 /* Many independent IIF2 problems of uneven size stepped together on one
- * device (the paper's method applied to each; no counterpart in the paper).
- * Each instance owns its index set, operators and solver on its own library
- * context; instances are spread round-robin over the batch's nstreams
- * streams.  A batch step queues one device-driven step per active instance
- * (a single CUDA graph each: predictor, one persistent cooperative Arnoldi
- * launch per species, expm, and the Newton/CG loops as conditional graph
- * nodes) and then waits for all streams once, so the instances' kernels
- * overlap on the GPU.  The persistent Arnoldi grid of an instance is sized
- * to its DOF (slices of at most slice_len coefficients per CTA, 0 = 384),
- * so that small instances take few SMs; the lanes per output of its matvec
- * are autotuned when the instance is added.  Results do not depend on the
- * stream count or on the other instances. */
+ * device (the paper's method applied to each, eqs. krylov5-krylov8 per
+ * instance; no counterpart in the paper).  Each instance owns its index set,
+ * operators and solver on its own library context; instances are spread
+ * round-robin over the batch's nstreams streams.  A batch step runs the
+ * Arnoldi processes (eqs. krylov7, krylov8) of all single-species instances
+ * with d in 2..4 in one persistent cooperative launch per kernel class
+ * (d, degree, lanes per output, arithmetic): each CTA walks a device work
+ * list of (instance, slice) items, built once by list scheduling, so that
+ * instances of uneven size share the SMs within one grid.  Around it, per
+ * instance on its stream, one CUDA graph before (predictor) and one after
+ * (exp(tau H) e_1, combination, and the Newton/CG loops as conditional
+ * graph nodes).  Other instances take one whole-step graph each.  The host
+ * waits for all streams once per batch step.  The Arnoldi grid of an
+ * instance is sized to its DOF (slices of at most slice_len coefficients
+ * per CTA, 0 = 384); the lanes per output of its matvec are autotuned when
+ * the instance is added.  Results do not depend on the stream count, on
+ * the batched launch or on the other instances. */
 typedef struct sgk_batch sgk_batch;
 
 /* Errors: SGK_EINVAL, SGK_ECUDA (no such device or stream creation failed). */
@@ -464,6 +540,12 @@ int sgk_batch_count(const sgk_batch* b);
 /* Copy one species' coefficients of an instance to host memory (cap >= dof). */
 int sgk_batch_get_state(const sgk_batch* b, int index, int species, double* out, int64_t cap);
 int sgk_batch_destroy(sgk_batch* b);
+/* on = 0: run every instance's Arnoldi process inside its own whole-step
+ * graph instead of the batched launches (for comparison); default 1. */
+int sgk_batch_set_fused(sgk_batch* b, int on);
+/* Kernels launched by the batched Arnoldi path so far (barrier reset and one
+ * per class and batch step); -1 for a null handle. */
+int64_t sgk_batch_launches(const sgk_batch* b);
 
 #ifdef __cplusplus
 }

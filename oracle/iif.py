@@ -36,8 +36,12 @@ the paper is silent:
   * inner solver: conjugate gradients for a scalar equation (the matrix is
     symmetric), restarted GMRES(50) with Givens rotations for systems; both
     start from 0 and stop at relative residual INNER_TOL or INNER_MAX steps;
-  * outer stop ||G(U)||_2 <= NEWTON_TOL max(1, ||W||_2), at most NEWTON_MAX
-    iterations, otherwise NewtonError.
+  * outer stop relative to the scale of the stage: ||G(U)||_2 <= NEWTON_TOL
+    max(||W||_2, ||G(W)||_2) (the second term only matters when W = 0), at
+    most NEWTON_MAX iterations, otherwise NewtonError.  A relative rule fixes
+    the implicit stage to NEWTON_TOL of the state's size at every scale; an
+    absolute floor (max(1, ||W||)) would leave states that have decayed far
+    below 1 fixed only to 1e-12 in absolute terms.
 """
 import numpy as np
 
@@ -171,13 +175,16 @@ class IIF2Solver:
         dt2 = 0.5 * self.dt if c is None else c
         U = [w.copy() for w in W]
         wnorm = float(np.sqrt(sum(float(w @ w) for w in W)))
-        stop = NEWTON_TOL * max(1.0, wnorm)
+        stop = None
         n = self.idx.dof
         inner_total = 0
         for it in range(NEWTON_MAX + 1):
             Fu = self.F(U, self.t + self.dt)
             G = np.concatenate([U[s] - dt2 * Fu[s] - W[s] for s in range(self.nspecies)])
-            if float(np.linalg.norm(G)) <= stop:
+            g = float(np.linalg.norm(G))
+            if stop is None:  # first evaluation, at U = W
+                stop = NEWTON_TOL * max(wnorm, g)
+            if g <= stop:
                 return U, it, inner_total
             if it == NEWTON_MAX:
                 break

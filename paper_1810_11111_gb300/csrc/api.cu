@@ -52,6 +52,10 @@ sgk_ctx::~sgk_ctx() {
 
 void build_index_on_device(sgk_index* idx);
 void index_lookup_on_device(const sgk_index* idx, const int32_t* levels, int64_t count, int64_t* out);
+int64_t level_dof(int d, int N, int k);
+
+// empty kernel whose attributes tell which device image of the library loaded
+__global__ void binary_probe_kernel() {}
 
 
 namespace {
@@ -132,6 +136,17 @@ const char* sgk_last_error(const sgk_ctx* ctx) { return ctx ? ctx->last_error.c_
 
 int64_t sgk_ctx_launch_count(const sgk_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int sgk_binary_arch(int* arch) {
+    if (!arch) return SGK_EINVAL;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(binary_probe_kernel)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    *arch = fa.binaryVersion;
+    return SGK_OK;
+}
+
 int sgk_ctx_profile(sgk_ctx* ctx, unsigned mask) {
     if (!ctx) return SGK_EINVAL;
     ctx->prof_mask = mask & ((1u << KC_COUNT) - 1);
@@ -185,6 +200,11 @@ int sgk_index_destroy(sgk_index* idx) {
 }
 
 int64_t sgk_index_dof(const sgk_index* idx) { return idx ? idx->dof : -1; }
+
+int64_t sgk_dof(int d, int n, int k) {
+    if (d < 1 || d > SGK_MAX_DIM || n < 0 || n > SGK_MAX_LEVEL || k < 1 || k > 3) return -1;
+    return level_dof(d, n, k);
+}
 int64_t sgk_index_ntuples(const sgk_index* idx) { return idx ? idx->ntuples : -1; }
 
 int sgk_index_export(const sgk_index* idx, int32_t* levels, int64_t* offsets, int64_t cap) {
@@ -211,10 +231,9 @@ int sgk_index_lookup(const sgk_index* idx, const int32_t* levels, int64_t count,
     });
 }
 
-int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, int bc, double sigma,
-                          sgk_op** out) {
-    if (!ctx || !idx || !kappa || !out) return SGK_EINVAL;
-    *out = nullptr;
+namespace {
+int operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, const double* Kfull, int bc,
+                      double sigma, sgk_op** out) {
     return guarded(ctx, [&]() {
         SGK_REQUIRE(bc == SGK_PERIODIC || bc == SGK_DIRICHLET0, SGK_EINVAL, "bc must be periodic or Dirichlet");
         SGK_REQUIRE(sigma > 0 && std::isfinite(sigma), SGK_EINVAL, "sigma must be positive");
@@ -261,9 +280,53 @@ int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kapp
             SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
         }
         build_gmv_tables(op.get());
+        if (Kfull) {
+            for (int e = 0; e < idx->d * idx->d; ++e) op->K[e] = Kfull[e];
+            build_cross_tables(op.get(), Kfull);
+        }
         *out = op.release();
         return SGK_OK;
     });
+}
+}  // namespace
+
+int sgk_operator_assemble(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, int bc, double sigma,
+                          sgk_op** out) {
+    if (!ctx || !idx || !kappa || !out) return SGK_EINVAL;
+    *out = nullptr;
+    return operator_assemble(ctx, idx, kappa, nullptr, bc, sigma, out);
+}
+
+int sgk_operator_assemble_full(sgk_ctx* ctx, const sgk_index* idx, const double* K, int bc, double sigma,
+                               sgk_op** out) {
+    if (!ctx || !idx || !K || !out) return SGK_EINVAL;
+    *out = nullptr;
+    const int d = idx->d;
+    // symmetric positive definite: Cholesky on the host
+    double L[SGK_MAX_DIM * SGK_MAX_DIM] = {0};
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+            if (!std::isfinite(K[i * d + j]) || K[i * d + j] != K[j * d + i]) {
+                ctx->last_error = "K must be finite and symmetric";
+                return SGK_EINVAL;
+            }
+    for (int j = 0; j < d; ++j) {
+        double s = K[j * d + j];
+        for (int m = 0; m < j; ++m) s -= L[j * d + m] * L[j * d + m];
+        if (!(s > 0.0)) {
+            ctx->last_error = "K must be positive definite";
+            return SGK_EINVAL;
+        }
+        L[j * d + j] = std::sqrt(s);
+        for (int i = j + 1; i < d; ++i) {
+            double t = K[i * d + j];
+            for (int m = 0; m < j; ++m) t -= L[i * d + m] * L[j * d + m];
+            L[i * d + j] = t / L[j * d + j];
+        }
+    }
+    double kd[SGK_MAX_DIM];
+    for (int i = 0; i < d; ++i) kd[i] = K[i * d + i];
+    return operator_assemble(ctx, idx, kd, K, bc, sigma, out);
 }
 
 int64_t sgk_operator_madds(const sgk_op* op) { return op ? op->madds : -1; }
@@ -343,6 +406,23 @@ int sgk_project_separable(sgk_ctx* ctx, const sgk_index* idx, int nterms, const 
     });
 }
 
+int sgk_dirichlet_load(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, double sigma, int nterms,
+                       const double* amp, const int* wavenum, const int* kind, double const_term, double* b_dev) {
+    if (!ctx || !idx || !kappa || !b_dev || nterms < 0 || (nterms > 0 && (!amp || !wavenum || !kind))) return SGK_EINVAL;
+    return guarded(ctx, [&]() {
+        SGK_REQUIRE(sigma > 0.0, SGK_EINVAL, "sigma must be positive");
+        for (int i = 0; i < idx->d; ++i) SGK_REQUIRE(kappa[i] > 0.0, SGK_EINVAL, "kappa must be positive");
+        for (int t = 0; t < nterms * idx->d; ++t)
+            SGK_REQUIRE(kind[t] == 0 || kind[t] == 1, SGK_EINVAL, "kind must be 0 (sin) or 1 (cos)");
+        set_device(ctx);
+        Tables1D tab;
+        build_transform_tables(idx->n, idx->k, tab);
+        tab.Tt.upload(ctx->stream);
+        dirichlet_load_dev(ctx, idx, tab, kappa, sigma, nterms, amp, wavenum, kind, const_term, b_dev);
+        return SGK_OK;
+    });
+}
+
 int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
                       int krylov_m, double dt, const sgk_newton_opts* opts, sgk_solver** out) {
     if (!ctx || !ops || !out) return SGK_EINVAL;
@@ -393,7 +473,10 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
         s->has_rx = s->rx.nmono > 0;
         s->use_graphs = std::getenv("SGK_NO_GRAPHS") == nullptr;
         const bool fp64 = s->prec == SGK_FP64;
-        s->opts.tol = fp64 ? 1e-12 : 1e-10;
+        // the oracle's outer tolerance in both modes (F is FP64-accurate in
+        // both); the mixed inner solve, whose Jacobian products are FP32,
+        // stops at 1e-6: a tighter solve of an FP32 operator buys nothing
+        s->opts.tol = 1e-12;
         s->opts.max_iter = 50;
         s->opts.inner_tol = fp64 ? 1e-13 : 1e-6;
         s->opts.inner_max = 500;

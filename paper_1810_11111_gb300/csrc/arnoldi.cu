@@ -39,6 +39,7 @@ extern template void arn_launch_k<6>(sgk_ctx*, const sgk_op*, const ArnArgs&, in
 }  // namespace sgk_arn
 
 using sgk_arn::ArnArgs;
+using sgk_arn::ArnPrep;
 using sgk_arn::PT;
 using sgk_arn::arn_launch_k;
 
@@ -105,7 +106,9 @@ static size_t loc_bytes(int d) {
     }
 }
 
-void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
+// The launch arguments of one Arnoldi process (shared memory layout, slices,
+// fixed-point scales, arithmetic) for the persistent kernel on ctx's grid.
+ArnPrep arnoldi_prepare(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
                         const double* v, int64_t n, int M) {
     SGK_REQUIRE(n >= 1 && n <= arnoldi_persistent_max_n(ctx), SGK_EUNSUPPORTED, "persistent Arnoldi: n too large");
     SGK_REQUIRE(M >= 1 && M <= SGK_MAX_KRYLOV, SGK_EINVAL, "persistent Arnoldi: bad M");
@@ -186,6 +189,22 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
     // relative; FP64 issue on this part is 1/64 of FP32), with the gather lists
     a.cvk2 = op->gmv_cvk2.p;
     a.df = ctx->precision == SGK_MIXED && a.list_cap > 0 && op->gmv_cvk2.p != nullptr;
+    ArnPrep out;
+    out.a = a;
+    out.smem = smem;
+    out.nb = nb;
+    out.G = G;
+    out.d = d;
+    out.kp1 = op->idx->k + 1;
+    return out;
+}
+
+void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
+                        const double* v, int64_t n, int M) {
+    const ArnPrep p = arnoldi_prepare(ctx, op, pw, kw, v, n, M);
+    const ArnArgs& a = p.a;
+    const int nb = p.nb, G = p.G;
+    const size_t smem = p.smem;
     KTimer kt(ctx, KC_KRYLOV);
     SGK_CUDA_CHECK(cudaMemsetAsync(pw.bar, 0, sizeof(unsigned), ctx->stream));
     switch (op->idx->d) {

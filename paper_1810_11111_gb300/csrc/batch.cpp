@@ -3,10 +3,19 @@
 //
 // Every instance has its own context (so that its persistent Arnoldi grid
 // can be sized to its DOF), index set, operators and solver; the contexts
-// share the batch's streams round-robin.  A batch step queues one
-// device-driven step per active instance (one CUDA graph each) and then
-// synchronises every stream once, so instances overlap on the GPU and the
-// host pays one wait per stream and batch step.
+// share the batch's streams round-robin.  A batch step runs, for the
+// instances whose step can be split (one species, persistent Arnoldi):
+//   1. per instance, on its stream, the first half of its device-driven step
+//      (state copy, predictor, v = U + dt/2 F(U)) as one CUDA graph;
+//   2. on the batch stream, after all of those, the Arnoldi processes of
+//      every instance in one persistent cooperative launch per kernel class
+//      (arnoldi_batch_*: a device work list of (instance, slice) items per
+//      CTA, so one grid barrier schedule serves all instances of a class);
+//   3. per instance, on its stream, the second half (exp(dt H) e_1, the
+//      combination, the Newton solve) as one CUDA graph.
+// Other device-driven instances take whole-step graphs on their streams;
+// the rest (systems, host-driven) step one by one.  The host waits once per
+// stream and batch step.
 #include <algorithm>
 #include <memory>
 #include <vector>
@@ -15,6 +24,7 @@
 
 #include "sgk_internal.h"
 #include "sgk_quad.h"
+#include "sgk_krylov.h"
 #include "sgk_solver.h"
 
 namespace {
@@ -40,12 +50,26 @@ struct Instance {
 struct sgk_batch {
     int device = 0;
     int slice_len = 384;
+    bool fused = true;  // batched Arnoldi launches (else whole-step graphs per instance)
     std::vector<cudaStream_t> streams;
+    cudaStream_t bstream = nullptr;  // the batched Arnoldi launches
+    std::vector<cudaEvent_t> ev;     // one per stream, joins them into bstream
+    cudaEvent_t evb = nullptr;       // forks bstream back to the streams
+    int num_sms = 0;
+    size_t smem_optin = 0;
     std::vector<std::unique_ptr<Instance>> inst;
+    ArnBatchPlan* plan = nullptr;
+    std::vector<Instance*> plan_set;  // instances of the plan, in job order
+    int64_t batched_launches = 0;
     ~sgk_batch() {
+        arnoldi_batch_free(plan);
         inst.clear();
         for (cudaStream_t s : streams)
             if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (evb) cudaEventDestroy(evb);
+        if (bstream) cudaStreamDestroy(bstream);
     }
 };
 
@@ -65,12 +89,24 @@ int sgk_batch_create(int device, int nstreams, int slice_len, sgk_batch** out) {
     if (slice_len > 0) b->slice_len = slice_len;
     for (int i = 0; i < nstreams; ++i) {
         cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             (void)cudaGetLastError();
             return SGK_ECUDA;
         }
         b->streams.push_back(s);
+        b->ev.push_back(e);
     }
+    int optin = 0;
+    if (cudaStreamCreateWithFlags(&b->bstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->evb, cudaEventDisableTiming) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    b->smem_optin = (size_t)optin;
     *out = b.release();
     return SGK_OK;
 }
@@ -119,16 +155,56 @@ int sgk_batch_add(sgk_batch* b, const sgk_request* q, int* index) {
     return SGK_OK;
 }
 
+int sgk_batch_set_fused(sgk_batch* b, int on) {
+    if (!b) return SGK_EINVAL;
+    b->fused = on != 0;
+    return SGK_OK;
+}
+
+int64_t sgk_batch_launches(const sgk_batch* b) { return b ? b->batched_launches : -1; }
+
 int sgk_batch_step(sgk_batch* b, int nsteps, int* status) {
     if (!b || nsteps < 0) return SGK_EINVAL;
     cudaSetDevice(b->device);
     int first = SGK_OK;
     try {
         for (int step = 0; step < nsteps; ++step) {
-            // queue every device-driven step, then the others run alone
-            std::vector<Instance*> queued;
+            // the split instances share the batched Arnoldi launches; the
+            // plan is rebuilt when that set changes (an instance failed)
+            std::vector<Instance*> split, queued;
+            if (b->fused)
+                for (auto& in : b->inst)
+                    if (in->status == SGK_OK && solver_split_eligible(in->sol) &&
+                        arnoldi_batch_supports(solver_arnoldi_job(in->sol)))
+                        split.push_back(in.get());
+            if (split != b->plan_set) {
+                arnoldi_batch_free(b->plan);
+                b->plan = nullptr;
+                b->plan_set.clear();
+                if (!split.empty()) {
+                    std::vector<ArnJob> jobs;
+                    for (Instance* in : split) jobs.push_back(solver_arnoldi_job(in->sol));
+                    b->plan = arnoldi_batch_plan(jobs, b->num_sms, b->smem_optin, b->bstream);
+                    b->plan_set = split;
+                }
+            }
+            if (!split.empty()) {
+                for (Instance* in : split) solver_step_launch_pre(in->sol);
+                for (size_t i = 0; i < b->streams.size(); ++i) {
+                    SGK_CUDA_CHECK(cudaEventRecord(b->ev[i], b->streams[i]));
+                    SGK_CUDA_CHECK(cudaStreamWaitEvent(b->bstream, b->ev[i], 0));
+                }
+                b->batched_launches += arnoldi_batch_launch(b->plan, b->bstream);
+                SGK_CUDA_CHECK(cudaEventRecord(b->evb, b->bstream));
+                for (cudaStream_t s : b->streams) SGK_CUDA_CHECK(cudaStreamWaitEvent(s, b->evb, 0));
+                for (Instance* in : split) {
+                    solver_step_launch_post(in->sol);
+                    queued.push_back(in);
+                }
+            }
+            // the other device-driven steps, whole
             for (auto& in : b->inst) {
-                if (in->status != SGK_OK) continue;
+                if (in->status != SGK_OK || std::find(split.begin(), split.end(), in.get()) != split.end()) continue;
                 if (solver_device_steps(in->sol)) {
                     solver_step_launch(in->sol);
                     queued.push_back(in.get());

@@ -17,6 +17,7 @@
 // two-scale pyramid on them.
 #include <algorithm>
 
+#include "sgk_dfloat.h"
 #include "sgk_internal.h"
 
 namespace {
@@ -292,6 +293,7 @@ void launch_pyr(sgk_ctx* ctx, const FiberPlan& plan, int mode, const T* src, T* 
 
 template void launch_pyr<double>(sgk_ctx*, const FiberPlan&, int, const double*, double*, int, int, const double*);
 template void launch_pyr<float>(sgk_ctx*, const FiberPlan&, int, const float*, float*, int, int, const double*);
+template void launch_pyr<dfloat>(sgk_ctx*, const FiberPlan&, int, const dfloat*, dfloat*, int, int, const double*);
 
 // Host mirror of the kernel's address arithmetic, for plan validation.
 static long long chunk_addr_host(const FiberGroup& g, long long o, int pos, long long in, int kp1, int I) {

@@ -14,7 +14,9 @@
 // then (V - U) R = (V + U) by LU with partial pivoting, then R <- R^2 s times.
 #include <atomic>
 #include <cmath>
+#include <mutex>
 
+#include "sgk_dfloat.h"
 #include "sgk_krylov.h"
 
 namespace {
@@ -1076,6 +1078,37 @@ void vk_convert(sgk_ctx* ctx, const float* x, double* y, long long n) {
     check_launch("convert");
     count_launch(ctx);
 }
+// double-float conversions (split, pair sum in FP64, pair sum in FP32)
+__global__ void df_split_kernel(const double* __restrict__ x, dfloat* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = df_split(x[i]);
+}
+__global__ void df_value_kernel(const dfloat* __restrict__ x, double* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = df_value(x[i]);
+}
+__global__ void df_float_kernel(const dfloat* __restrict__ x, float* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = df_float(x[i]);
+}
+void vk_convert(sgk_ctx* ctx, const double* x, dfloat* y, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    df_split_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n);
+    check_launch("df_split");
+    count_launch(ctx);
+}
+void vk_convert(sgk_ctx* ctx, const dfloat* x, double* y, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    df_value_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n);
+    check_launch("df_value");
+    count_launch(ctx);
+}
+void vk_convert(sgk_ctx* ctx, const dfloat* x, float* y, long long n) {
+    KTimer kt(ctx, KC_VECTOR);
+    df_float_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, y, n);
+    check_launch("df_float");
+    count_launch(ctx);
+}
 void vk_axpby(sgk_ctx* ctx, double a, const double* x, double b, const double* y, double* z, long long n) {
     KTimer kt(ctx, KC_VECTOR);
     axpby_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(a, x, b, y, z, n);
@@ -1173,9 +1206,49 @@ void expm_e1(sgk_ctx* ctx, const double* H, int M, const int* m_dev, int m_fixed
 // share it and must not overlap on the GPU.
 static __device__ __align__(256) double g_expm_scratch[8 * SGK_EXPM_NOALLOC_MAX_M * SGK_EXPM_NOALLOC_MAX_M];
 
-// Device address of g_expm_scratch per device ordinal, looked up on the first
-// call made with that device current (host code cannot pass the symbol).
-static std::atomic<double*> g_expm_scratch_addr[256];
+// Per-device set-up of sgk_expm_e1_noalloc, made by the first call on a
+// device and again whenever that device's context is not the one the set-up
+// was made in (after a cudaDeviceReset the runtime creates a new primary
+// context, in which the symbol may live at another address and function
+// attributes start over).  Host code cannot pass g_expm_scratch itself (its
+// name there is a host-side stand-in), so the set-up looks up the device
+// address with cudaGetSymbolAddress; it also raises the cluster kernel's
+// dynamic shared-memory limit once instead of on every call.
+struct NoallocSetup {
+    std::mutex mu;
+    unsigned long long ctx_id = 0;  // context of the set-up (0: none yet, or ids unavailable)
+    bool done = false;
+    double* scratch = nullptr;
+};
+static NoallocSetup g_noalloc_setup[256];
+
+// Unique id of the calling thread's current context (cuCtxGetCurrent and
+// cuCtxGetId through the runtime's driver entry points, so that the library
+// does not link the driver library itself); 0 when the driver does not
+// provide them.
+static unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        (void)cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, void* cuda_stream) {
     if (m < 1 || m > SGK_EXPM_NOALLOC_MAX_M || !X_dev || !y_dev) return SGK_EINVAL;
@@ -1184,36 +1257,56 @@ extern "C" int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, doubl
         (void)cudaGetLastError();
         return SGK_ECUDA;
     }
+    // 0 when this thread has not used the device through the runtime yet:
+    // the set-up below binds the context, and its id is stored after it
+    const unsigned long long ctx_id = current_context_id();
+    NoallocSetup& su = g_noalloc_setup[dev];
+    double* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(su.mu);
+        if (!su.done || su.ctx_id != ctx_id) {
+            su.done = false;
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_expm_scratch) != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return SGK_ECUDA;
+            }
+            su.scratch = static_cast<double*>(p);
+            int optin = 0;
+            cudaFuncAttributes fa;
+            if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(expm_cluster_kernel)) != cudaSuccess ||
+                cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return SGK_ECUDA;
+            }
+            su.ctx_id = current_context_id();
+            su.done = true;
+        }
+        ws = su.scratch;
+    }
     if (m <= EXPM_CLUSTER_MAX_M) {
         // the cluster kernel keeps its work matrices in shared memory
         const size_t smem = sizeof(double) * 8 * m * m;
-        int optin = 0;
-        cudaFuncAttributes fa;
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(expm_cluster_kernel)) != cudaSuccess ||
-            cudaFuncSetAttribute(expm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return SGK_ECUDA;
-        }
         expm_cluster_kernel<<<XCL, XTH, smem, static_cast<cudaStream_t>(cuda_stream)>>>(X_dev, m, nullptr, m, tau,
                                                                                      pade13_coefficients(), y_dev);
         return cudaGetLastError() == cudaSuccess ? SGK_OK : SGK_ECUDA;
-    }
-    double* ws = g_expm_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!ws) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_expm_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return SGK_ECUDA;
-        }
-        ws = static_cast<double*>(p);
-        g_expm_scratch_addr[dev].store(ws, std::memory_order_release);
     }
     expm_e1_kernel<<<1, 512, 0, static_cast<cudaStream_t>(cuda_stream)>>>(X_dev, m, nullptr, m, tau,
                                                                           pade13_coefficients(), ws, y_dev);
     if (cudaGetLastError() != cudaSuccess) return SGK_ECUDA;
     return SGK_OK;
+}
+
+void krylov_finish(sgk_ctx* ctx, const KrylovWork<double>& kw, double* W, long long n, int M, double dt) {
+    expm_e1(ctx, kw.H, M, &kw.ks->m_eff, 0, dt, kw.expm_ws, kw.y);
+    {
+        KTimer kt(ctx, KC_VECTOR);
+        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
+    }
+    check_launch("combine");
+    count_launch(ctx);
 }
 
 void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,

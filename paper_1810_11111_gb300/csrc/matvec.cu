@@ -300,6 +300,7 @@ void op_matvec(const sgk_op* op, const T* x, T* y) {
         case 6: gmv_dispatch<T, 6>(op, x, y); break;
         default: throw SgkError{SGK_EUNSUPPORTED, "matvec: d must be 1..6"};
     }
+    op_cross_matvec<T>(op, x, y);
 }
 
 template void op_matvec<double>(const sgk_op*, const double*, double*);

@@ -21,7 +21,9 @@
 //      registers, one barrier per 3 levels) and stores them.
 // Specialised for (d, k+1, q, species); other shapes use the unfused path.
 #include <algorithm>
+#include <type_traits>
 
+#include "sgk_dfloat.h"
 #include "sgk_pencil.h"
 
 namespace {
@@ -178,7 +180,7 @@ struct QuadTop {
     // volatile: re-read at every Gauss point (hoisting the loads out of the
     // loop would hold all of them in registers again)
     __device__ __forceinline__ static T at(const T* p, int e) {
-        return reinterpret_cast<const volatile T*>(p)[(e % KP1) * PS + e / KP1];
+        return volatile_read(p + (e % KP1) * PS + e / KP1);
     }
     __device__ __forceinline__ static void run(const QuadTab<T>& tb, const Poly<T, S>& P, const T* const (&pu)[S],
                                                const T* const (&pw)[S], T (&M)[S][NC]) {
@@ -468,12 +470,15 @@ void launch_one(sgk_ctx* ctx, const PencilArgs& a, const QuadTab<T>& tb, const d
                 F.H[h][r][s] = (T)two_scale[h * KP1 * KP1 + r * KP1 + s];
                 F.G[h][r][s] = (T)two_scale[(2 + h) * KP1 * KP1 + r * KP1 + s];
             }
-    Poly<T, S> poly{};
+    double pc[S][Pow<PDEG, S>::v] = {};
     for (int m = 0; m < rxd.nmono; ++m) {
         int idx = 0;
         for (int r = 0; r < S; ++r) idx = idx * PDEG + rxd.exps[m][r];
-        poly.c[rxd.species[m]][idx] += (T)rxd.coef[m];
+        pc[rxd.species[m]][idx] += rxd.coef[m];
     }
+    Poly<T, S> poly{};
+    for (int sp = 0; sp < S; ++sp)
+        for (int i = 0; i < Pow<PDEG, S>::v; ++i) poly.c[sp][i] = (T)pc[sp][i];
     constexpr int P = Pow<KP1, D - 1>::v;
     constexpr int NBUF = (JAC ? 2 * S : S) + 1;
     const size_t smem = (size_t)NBUF * (P | 1) * a.H * sizeof(T);
@@ -535,8 +540,15 @@ void pencil_launch(sgk_ctx* ctx, const PencilArgs& a, int d, int kp1, int q, int
                    const double* w, const double* two_scale, const ReactionDev& rx) {
     const QuadTab<T> tb = make_tab<T>(B, w, q, kp1);
     KTimer kt(ctx, KC_CELL);
-    const bool ok = jac ? dispatch<T, true>(ctx, d, kp1, q, S, a, tb, two_scale, rx)
-                        : dispatch<T, false>(ctx, d, kp1, q, S, a, tb, two_scale, rx);
+    bool ok = false;
+    if constexpr (std::is_same<T, dfloat>::value) {
+        // double-float serves the F passes only (Jacobian products stay FP32)
+        SGK_REQUIRE(!jac, SGK_EUNSUPPORTED, "no double-float Jacobian pencil");
+        ok = dispatch<T, false>(ctx, d, kp1, q, S, a, tb, two_scale, rx);
+    } else {
+        ok = jac ? dispatch<T, true>(ctx, d, kp1, q, S, a, tb, two_scale, rx)
+                 : dispatch<T, false>(ctx, d, kp1, q, S, a, tb, two_scale, rx);
+    }
     SGK_REQUIRE(ok, SGK_EUNSUPPORTED, "no fused pencil kernel for this shape");
     check_launch("pencil_kernel");
     count_launch(ctx);
@@ -546,3 +558,5 @@ template void pencil_launch<double>(sgk_ctx*, const PencilArgs&, int, int, int, 
                                     const double*, const double*, const ReactionDev&);
 template void pencil_launch<float>(sgk_ctx*, const PencilArgs&, int, int, int, int, bool, const double*,
                                    const double*, const double*, const ReactionDev&);
+template void pencil_launch<dfloat>(sgk_ctx*, const PencilArgs&, int, int, int, int, bool, const double*,
+                                    const double*, const double*, const ReactionDev&);

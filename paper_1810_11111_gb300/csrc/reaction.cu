@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "sgk_dfloat.h"
 #include "sgk_quad.h"
 
 namespace {
@@ -281,6 +282,54 @@ __global__ void proj_product_kernel(long long dof, int d, int kp1, int H, long l
     }
 }
 
+// b[e] = sum_t amp_t sum_i sum_c g_{t,i}(c) beta_{i,c}[a_i(e)] prod_{m != i}
+// P1[t][m][a_m(e)], plus for the constant c0 the same with the factors of
+// 1 (projection e_0, value 1 at both faces): the load of boundary data that
+// is the restriction of a separable sum.
+__global__ void dirichlet_load_kernel(long long dof, int d, int kp1, int H, long long ntuples,
+                                      const int* __restrict__ levels, const long long* __restrict__ offsets,
+                                      int nterms, const double* __restrict__ amp, const double* __restrict__ P1,
+                                      const double* __restrict__ gface, const double* __restrict__ beta, double c0,
+                                      double* __restrict__ b) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < dof;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = ntuples;  // offsets[lo] <= e < offsets[hi]
+        while (hi - lo > 1) {
+            const long long mid = (lo + hi) / 2;
+            if (offsets[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        long long loc = e - offsets[lo];
+        int a[SGK_MAX_DIM];
+        for (int m = d - 1; m >= 0; --m) {
+            const int l = levels[lo * d + m];
+            const int nl = l == 0 ? kp1 : kp1 << (l - 1);
+            const int t = (int)(loc % nl);
+            loc /= nl;
+            a[m] = (l == 0 ? 0 : kp1 << (l - 1)) + t;
+        }
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) {
+            const double b0 = beta[((long long)i * 2 + 0) * H + a[i]], b1 = beta[((long long)i * 2 + 1) * H + a[i]];
+            for (int t = 0; t < nterms; ++t) {
+                const double gf = gface[t * d + i];
+                if (gf == 0.0) continue;
+                double prod = amp[t] * gf * (b0 + b1);
+                for (int m = 0; m < d; ++m)
+                    if (m != i) prod *= P1[((long long)t * d + m) * H + a[m]];
+                acc += prod;
+            }
+            if (c0 != 0.0) {
+                bool rest0 = true;
+                for (int m = 0; m < d; ++m)
+                    if (m != i && a[m] != 0) rest0 = false;
+                if (rest0) acc += c0 * (b0 + b1);
+            }
+        }
+        b[e] = acc;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host side ---
@@ -465,43 +514,106 @@ template void quad_forward<double>(sgk_ctx*, const Quad&, const double*, double*
 template void quad_forward<float>(sgk_ctx*, const Quad&, const float*, float*, float*, int);
 template void quad_backward<double>(sgk_ctx*, const Quad&, double*, double*, double*, int);
 template void quad_backward<float>(sgk_ctx*, const Quad&, float*, float*, float*, int);
+template void quad_forward<dfloat>(sgk_ctx*, const Quad&, const dfloat*, dfloat*, dfloat*, int);
+template void quad_backward<dfloat>(sgk_ctx*, const Quad&, dfloat*, dfloat*, dfloat*, int);
 template void quad_cells<double>(sgk_ctx*, const Quad&, const ReactionDev&, bool, const double* const*,
                                  const double* const*, double* const*);
 template void quad_cells<float>(sgk_ctx*, const Quad&, const ReactionDev&, bool, const float* const*,
                                 const float* const*, float* const*);
 
-void project_separable_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, int nterms, const double* amp,
-                           const int* wavenum, const int* kind, double c0, double* U) {
+// P1[(t d + m) H + a] = int g_{t,m}(2 pi w_{t,m} x) v_a(x) dx, the 1D
+// projections of the factors of a separable sum (12-point Gauss per finest
+// cell, then the transposed change of basis); damp receives amp.
+static void separable_factors_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, int nterms,
+                                  const double* amp, const int* wavenum, const int* kind, DevBuf<double>& damp,
+                                  DevBuf<double>& P1) {
     const int d = idx->d, N = idx->n, kp1 = idx->k + 1, H = kp1 << N;
+    if (nterms <= 0) return;
     std::vector<double> xg, wg;
     gauss_legendre(12, xg, wg);
-    DevBuf<double> dx, dw, damp, fine, P1;
+    DevBuf<double> dx, dw, fine;
     DevBuf<int> dwn, dkind;
     dx.upload(xg, ctx->stream);
     dw.upload(wg, ctx->stream);
-    const long long nvec = (long long)std::max(nterms, 1) * d;
-    if (nterms > 0) {
-        std::vector<int> wn(wavenum, wavenum + (size_t)nterms * d), kd(kind, kind + (size_t)nterms * d);
-        std::vector<double> am(amp, amp + nterms);
-        dwn.upload(wn, ctx->stream);
-        dkind.upload(kd, ctx->stream);
-        damp.upload(am, ctx->stream);
-        fine.alloc(nvec * H);
-        P1.alloc(nvec * H);
-        const int grid = (int)std::min<long long>((nvec * H + 255) / 256, ctx->num_sms * 8LL);
-        proj_fine_kernel<<<grid, 256, 0, ctx->stream>>>(nterms, d, N, kp1, dwn.p, dkind.p, dx.p, dw.p, 12, fine.p);
-        check_launch("proj_fine_kernel");
-        proj_hier_kernel<<<grid, 256, 0, ctx->stream>>>(nvec, H, tab.Tt.d_ptr.p, tab.Tt.d_col.p, tab.Tt.d_val.p,
-                                                         fine.p, P1.p);
-        check_launch("proj_hier_kernel");
-        count_launch(ctx, 2);
-        SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));  // host vectors above go out of scope
-    }
+    const long long nvec = (long long)nterms * d;
+    std::vector<int> wn(wavenum, wavenum + (size_t)nterms * d), kd(kind, kind + (size_t)nterms * d);
+    std::vector<double> am(amp, amp + nterms);
+    dwn.upload(wn, ctx->stream);
+    dkind.upload(kd, ctx->stream);
+    damp.upload(am, ctx->stream);
+    fine.alloc(nvec * H);
+    P1.alloc(nvec * H);
+    const int grid = (int)std::min<long long>((nvec * H + 255) / 256, ctx->num_sms * 8LL);
+    proj_fine_kernel<<<grid, 256, 0, ctx->stream>>>(nterms, d, N, kp1, dwn.p, dkind.p, dx.p, dw.p, 12, fine.p);
+    check_launch("proj_fine_kernel");
+    proj_hier_kernel<<<grid, 256, 0, ctx->stream>>>(nvec, H, tab.Tt.d_ptr.p, tab.Tt.d_col.p, tab.Tt.d_val.p,
+                                                     fine.p, P1.p);
+    check_launch("proj_hier_kernel");
+    count_launch(ctx, 2);
+    SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));  // host vectors above go out of scope
+}
+
+void project_separable_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, int nterms, const double* amp,
+                           const int* wavenum, const int* kind, double c0, double* U) {
+    const int d = idx->d, N = idx->n, kp1 = idx->k + 1, H = kp1 << N;
+    DevBuf<double> damp, P1;
+    separable_factors_dev(ctx, idx, tab, nterms, amp, wavenum, kind, damp, P1);
     const int grid = (int)std::min<long long>((idx->dof + 255) / 256, ctx->num_sms * 8LL);
     proj_product_kernel<<<grid, 256, 0, ctx->stream>>>(idx->dof, d, kp1, H, idx->ntuples, idx->d_levels.p,
                                                         reinterpret_cast<const long long*>(idx->d_offsets.p), nterms,
                                                         damp.p, P1.p, c0, U);
     check_launch("proj_product_kernel");
+    count_launch(ctx);
+    SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    (void)N;
+}
+
+void dirichlet_load_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, const double* kappa, double sigma,
+                        int nterms, const double* amp, const int* wavenum, const int* kind, double c0, double* b) {
+    const int d = idx->d, N = idx->n, kp1 = idx->k + 1, H = kp1 << N;
+    const double h = std::ldexp(1.0, -N);
+    // one-sided traces v(0+), v'(0+), v(1-), v'(1-) of every 1D hierarchical
+    // function from its Legendre coefficients on the first and last finest
+    // cells (phi_p = h^{-1/2} sqrt(2p+1) P_p(2(x - x_c)/h - 1):
+    // P_p(-1) = (-1)^p, P_p'(-1) = (-1)^{p+1} p(p+1)/2, P_p(1) = 1,
+    // P_p'(1) = p(p+1)/2)
+    std::vector<double> v0(H, 0.0), d0(H, 0.0), v1(H, 0.0), d1(H, 0.0);
+    const double rh = 1.0 / std::sqrt(h);
+    for (int a = 0; a < H; ++a)
+        for (int e = tab.Tt.ptr[a]; e < tab.Tt.ptr[a + 1]; ++e) {
+            const int y = tab.Tt.col[e], p = y % kp1;
+            const double t = tab.Tt.val[e], nrm = rh * std::sqrt(2.0 * p + 1.0), dp = 0.5 * p * (p + 1);
+            const double sgn = (p % 2) ? -1.0 : 1.0;
+            if (y < kp1) {
+                v0[a] += t * nrm * sgn;
+                d0[a] += t * nrm * (-sgn) * dp * 2.0 / h;
+            }
+            if (y >= H - kp1) {
+                v1[a] += t * nrm;
+                d1[a] += t * nrm * dp * 2.0 / h;
+            }
+        }
+    // per direction i and face c (outward normal -1 at 0, +1 at 1):
+    // beta = -kappa_i (n v' - sigma/h v), the face factor of the load
+    std::vector<double> beta((size_t)d * 2 * H);
+    for (int i = 0; i < d; ++i)
+        for (int a = 0; a < H; ++a) {
+            beta[((size_t)i * 2 + 0) * H + a] = -kappa[i] * (-d0[a] - sigma / h * v0[a]);
+            beta[((size_t)i * 2 + 1) * H + a] = -kappa[i] * (d1[a] - sigma / h * v1[a]);
+        }
+    // the data's factors at the faces: sin(2 pi w c) = 0, cos(2 pi w c) = 1
+    // for integer w and c in {0, 1}
+    std::vector<double> gface((size_t)std::max(nterms, 1) * d, 0.0);
+    for (int t = 0; t < nterms * d; ++t) gface[t] = kind[t] == 1 ? 1.0 : 0.0;
+    DevBuf<double> damp, P1, dbeta, dgf;
+    separable_factors_dev(ctx, idx, tab, nterms, amp, wavenum, kind, damp, P1);
+    dbeta.upload(beta, ctx->stream);
+    dgf.upload(gface, ctx->stream);
+    const int grid = (int)std::min<long long>((idx->dof + 255) / 256, ctx->num_sms * 8LL);
+    dirichlet_load_kernel<<<grid, 256, 0, ctx->stream>>>(idx->dof, d, kp1, H, idx->ntuples, idx->d_levels.p,
+                                                          reinterpret_cast<const long long*>(idx->d_offsets.p),
+                                                          nterms, damp.p, P1.p, dgf.p, dbeta.p, c0, b);
+    check_launch("dirichlet_load_kernel");
     count_launch(ctx);
     SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
 }

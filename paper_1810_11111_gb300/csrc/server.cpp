@@ -63,8 +63,11 @@ struct Req {
     std::vector<double> result;
 };
 
+
+}  // namespace
+
+// sum over level tuples |l|_1 <= N of prod_m (k+1) 2^{max(l_m - 1, 0)}
 int64_t level_dof(int d, int N, int k) {
-    // sum over level tuples |l|_1 <= N of prod_m (k+1) 2^{max(l_m - 1, 0)}
     std::vector<int64_t> cnt(N + 1, 0);  // cnt[s]: dof of tuples with sum s, built dimension by dimension
     cnt[0] = 1;
     for (int m = 0; m < d; ++m) {
@@ -79,7 +82,42 @@ int64_t level_dof(int d, int N, int k) {
     return t;
 }
 
-}  // namespace
+extern "C" double sgk_estimate_work(int d, int n, int k, int nspecies, int krylov_m, int has_reaction) {
+    if (d < 1 || d > SGK_MAX_DIM || n < 0 || n > SGK_MAX_LEVEL || k < 1 || k > 3 || nspecies < 1 ||
+        nspecies > SGK_MAX_SPECIES || krylov_m < 1 || krylov_m > SGK_MAX_KRYLOV)
+        return -1.0;
+    const double dof = (double)level_dof(d, n, k), M = krylov_m, kp1 = k + 1;
+    // a row of the 1D matrix along one direction visits about 13 entries
+    // (measured on the index sets of this library's workloads)
+    double w = M * (2.0 * 13.0 * d * dof) + 4.0 * M * M * dof;
+    if (has_reaction) {
+        const double cells = std::pow(2.0, (double)n * d);
+        const int q = 2 * k + 1;  // Gauss points of a cubic reaction, ceil((3k + k + 1) / 2)
+        double per_cell = 0.0;  // sum-factorised stages, forward and back
+        for (int m = 0; m < d; ++m) per_cell += 2.0 * std::pow((double)q, m + 1) * std::pow(kp1, d - m);
+        w += 3.0 * 2.0 * cells * per_cell;
+    }
+    return w * nspecies;
+}
+
+extern "C" int sgk_partition(int count, const double* cost, int nparts, int* part_of) {
+    if (count < 0 || nparts < 1 || (count > 0 && (!cost || !part_of))) return SGK_EINVAL;
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) {
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) return SGK_EINVAL;
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(nparts, 0.0);
+    for (int i : order) {
+        int best = 0;
+        for (int p = 1; p < nparts; ++p)
+            if (load[p] < load[best]) best = p;
+        part_of[i] = best;
+        load[best] += cost[i];
+    }
+    return SGK_OK;
+}
 
 struct sgk_server {
     int device = 0;
@@ -280,7 +318,9 @@ int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int 
         const double elem = precision == SGK_FP64 ? 8.0 : 4.0;
         const double full = std::pow(H, d);
         b += 8.0 * 6.0 * N + elem * ((2.0 * S + 1.0) * full + 2.0 * S * dof + N);
-        if (precision == SGK_MIXED) b += 4.0 * 3.0 * N;  // FP32 copies of the sparse vectors
+        // mixed: the FP32 buffers of the Jacobian products above, the FP64
+        // ones of F and FP32 copies of the sparse vectors
+        if (precision == SGK_MIXED) b += 8.0 * ((2.0 * S + 1.0) * full + 2.0 * S * dof) + 4.0 * 3.0 * N;
         if (nspecies > 1) b += 8.0 * 51.0 * N;            // GMRES(50) basis
         // change-of-basis tables and work plans
         b += 2.0 * H * (n + 1) * (k + 1) * 12.0 + 64.0 * 1024.0 * d;

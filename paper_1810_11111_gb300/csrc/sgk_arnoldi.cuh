@@ -288,8 +288,12 @@ __device__ __forceinline__ void slice_norm2(const double* ws, int ne, double* re
     }
 }
 
+// The Arnoldi process of one exponential on a grid of nb CTAs of which this
+// CTA is number b (slice b).  Every CTA of the grid calls it with the same
+// arguments; a failed barrier or a breakdown returns from it in every CTA.
 template <int D, int KP1, int G, bool DF>
-__global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
+__device__ __forceinline__ void arnoldi_body(const GmvArgs<double, D>& ga, const ArnArgs& a, const int nb,
+                                             const int b) {
     // dynamic shared memory: [w slices: 2 E][Vs: (M+1) Es][Zs: (M+1) Es][located rows, or gather offsets
     // and entries]
     extern __shared__ __align__(16) double smem[];
@@ -305,7 +309,6 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
     // double-float matvec: the correction's coefficients and the step's scale
     __shared__ float2 h2df[DF ? SGK_MAX_KRYLOV + 2 : 1];
     __shared__ float2 s_scaldf;
-    const int nb = gridDim.x, b = blockIdx.x;
     const int64_t n = a.n;
     const int E = a.E;  // longest slice
     const int64_t lo = a.bounds ? a.bounds[b] : std::min<int64_t>(n, (int64_t)b * E);
@@ -604,6 +607,111 @@ __global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D>
         xdf = reinterpret_cast<const float2*>(w);
     }
     if (pj >= 0) pending_update();  // the last column, v_M
+}
+
+template <int D, int KP1, int G, bool DF>
+__global__ void __launch_bounds__(PT, 1) arnoldi_kernel(const GmvArgs<double, D> ga, const ArnArgs a) {
+    arnoldi_body<D, KP1, G, DF>(ga, a, gridDim.x, blockIdx.x);
+}
+
+// Many independent Arnoldi processes in one cooperative launch.  CTA c runs
+// the work items item_off[c] .. item_off[c+1]-1 in order; item (i, b) makes
+// it slice b of instance i's grid of nb[i] CTAs.  The host builds the lists
+// from one global order of the instances (each instance's slices take the
+// same position in every list that holds them), and every CTA is resident,
+// so no CTA waits on an instance that cannot start: an instance's barriers
+// only involve the CTAs of its own items.
+template <int D>
+struct ArnMulti {
+    const int* item_off;  // gridDim.x + 1
+    const int2* items;    // (instance, slice)
+    const GmvArgs<double, D>* ga;
+    const ArnArgs* aa;
+    const int* nb;
+};
+
+template <int D, int KP1, int G, bool DF>
+__global__ void __launch_bounds__(PT, 1) arnoldi_multi_kernel(const ArnMulti<D> m) {
+    __shared__ ArnArgs s_a;
+    __shared__ GmvArgs<double, D> s_ga;
+    __shared__ int s_nb;
+    const int first = m.item_off[blockIdx.x], last = m.item_off[blockIdx.x + 1];
+    for (int it = first; it < last; ++it) {
+        const int2 w = m.items[it];
+        __syncthreads();  // the previous item is done with shared memory
+        {
+            const int* src = reinterpret_cast<const int*>(m.aa + w.x);
+            int* dst = reinterpret_cast<int*>(&s_a);
+            for (int i = threadIdx.x; i < (int)(sizeof(ArnArgs) / sizeof(int)); i += PT) dst[i] = src[i];
+            const int* gsrc = reinterpret_cast<const int*>(m.ga + w.x);
+            int* gdst = reinterpret_cast<int*>(&s_ga);
+            for (int i = threadIdx.x; i < (int)(sizeof(GmvArgs<double, D>) / sizeof(int)); i += PT) gdst[i] = gsrc[i];
+            if (threadIdx.x == 0) s_nb = m.nb[w.x];
+        }
+        __syncthreads();
+        arnoldi_body<D, KP1, G, DF>(s_ga, s_a, s_nb, w.y);
+    }
+}
+
+// Launch arguments of one Arnoldi process (arnoldi_prepare).
+struct ArnPrep {
+    ArnArgs a;
+    size_t smem = 0;
+    int nb = 0, G = 0, d = 0, kp1 = 0;
+};
+
+// Device copies of the matvec arguments of a list of operators (d = D).
+template <int D>
+void arn_multi_upload_ga(const std::vector<const sgk_op*>& ops, DevBuf<unsigned char>& buf, cudaStream_t st) {
+    std::vector<GmvArgs<double, D>> v;
+    v.reserve(ops.size());
+    for (const sgk_op* op : ops) v.push_back(make_gmv_args<double, D>(op));
+    buf.alloc(v.size() * sizeof(GmvArgs<double, D>));
+    buf.upload(reinterpret_cast<const unsigned char*>(v.data()), buf.n, st);
+}
+
+template <int D, int KP1, int G>
+void arn_multi_launch(cudaStream_t st, bool df, const ArnMulti<D>& m, int grid, size_t smem, size_t smem_optin,
+                      int num_sms) {
+    auto kern = df ? arnoldi_multi_kernel<D, KP1, G, true> : arnoldi_multi_kernel<D, KP1, G, false>;
+    allow_max_dynamic_smem(smem_optin, kern);
+    int occ = 0;
+    SGK_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PT, smem));
+    SGK_REQUIRE(occ >= 1 && grid <= occ * num_sms, SGK_EUNSUPPORTED, "batched Arnoldi grid does not fit");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SGK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, m));
+}
+
+// Batched launch for d = D: degree (k + 1 = kp1) and lanes per output (4 or
+// 8) select the kernel; ga points at the device GmvArgs<double, D> array.
+template <int D>
+void arn_multi_launch_k(cudaStream_t st, int kp1, int G, bool df, const int* item_off, const int2* items,
+                        const void* ga, const ArnArgs* aa, const int* nb, int grid, size_t smem, size_t smem_optin,
+                        int num_sms) {
+    ArnMulti<D> m;
+    m.item_off = item_off;
+    m.items = items;
+    m.ga = static_cast<const GmvArgs<double, D>*>(ga);
+    m.aa = aa;
+    m.nb = nb;
+#define SGK_ARN_MULTI(K, GG)                                                            \
+    if (kp1 == K && G == GG) {                                                          \
+        arn_multi_launch<D, K, GG>(st, df, m, grid, smem, smem_optin, num_sms);         \
+        return;                                                                         \
+    }
+    SGK_ARN_MULTI(2, 4) SGK_ARN_MULTI(2, 8) SGK_ARN_MULTI(3, 4) SGK_ARN_MULTI(3, 8) SGK_ARN_MULTI(4, 4)
+    SGK_ARN_MULTI(4, 8)
+#undef SGK_ARN_MULTI
+    throw SgkError{SGK_EUNSUPPORTED, "batched Arnoldi: no kernel for this degree and lane count"};
 }
 
 template <int D, int KP1, int G>

@@ -319,6 +319,18 @@ struct sgk_op {
     DevBuf<int32_t> gmv_eoff;
     DevBuf<int2> gmv_ent;
     std::vector<int32_t> gmv_ecnt_host;
+    // mixed-derivative terms of a full diffusion tensor (cross.cu): the
+    // direction pairs (i, j) with K_ij != 0 and K_ij; the 1D factors Q, P^T,
+    // E^T, P as CSR (pointers per matrix, H + 1 each) with truncated row
+    // lengths per level; per (tuple, pair) the base of its block-offset
+    // table, (L + 1)^2 entries indexed by the changed levels of i and j
+    int npairs = 0;
+    double K[SGK_MAX_DIM * SGK_MAX_DIM] = {0};
+    DevBuf<int> x_pairs, x_ptr, x_col, x_rlen;
+    DevBuf<double> x_kij, x_val;
+    DevBuf<float> x_valf;
+    DevBuf<int64_t> x_grp, x_off;
+    int64_t x_nnz = 0;
 };
 constexpr int64_t GMV_LIST_MAX = int64_t(1) << 24;
 
@@ -335,6 +347,11 @@ long long tuple_rank(const std::vector<int>& l, int n);
 
 template <typename T>
 void op_matvec(const sgk_op* op, const T* x, T* y);
+// Tables and application (y -= the mixed-derivative terms) of a full
+// constant diffusion tensor K (d x d, row-major, symmetric).
+void build_cross_tables(sgk_op* op, const double* K);
+template <typename T>
+void op_cross_matvec(const sgk_op* op, const T* x, T* y);
 
 // -------------------------------------------------------------- kernels ---
 

@@ -1,5 +1,7 @@
 // Krylov exponential and vector kernels: shared declarations.
 #pragma once
+
+struct dfloat;
 #include <vector>
 
 #include <functional>
@@ -70,6 +72,34 @@ void arnoldi_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw
 // overwrite the Krylov workspace.  Not while a graph is being captured.
 int arnoldi_autotune(sgk_ctx* ctx, const sgk_op* op, PersistentWork pw, const KrylovWork<double>& kw, double* scratch,
                      int64_t n, int M);
+// One Arnoldi process of a batch of independent instances (its context,
+// operator, workspaces and input vector).
+struct ArnJob {
+    sgk_ctx* ctx = nullptr;
+    const sgk_op* op = nullptr;
+    PersistentWork pw;
+    KrylovWork<double> kw;
+    const double* v = nullptr;
+    int64_t n = 0;
+    int M = 0;
+};
+struct ArnBatchPlan;
+// Whether an instance can join a batched launch (d 2..4, degree 1..3, a
+// persistent-size vector).
+bool arnoldi_batch_supports(const ArnJob& j);
+// Schedules the jobs' Arnoldi processes into one cooperative launch per
+// kernel class and uploads the work lists; the plan holds device memory
+// until arnoldi_batch_free.
+ArnBatchPlan* arnoldi_batch_plan(const std::vector<ArnJob>& jobs, int num_sms, size_t smem_optin, cudaStream_t st);
+// Queues the plan's launches on st (the barrier counters reset first);
+// returns the number of kernels launched.
+int arnoldi_batch_launch(const ArnBatchPlan* plan, cudaStream_t st);
+int arnoldi_batch_classes(const ArnBatchPlan* plan);
+void arnoldi_batch_free(ArnBatchPlan* plan);
+// expm and the combination W = gamma V y after an Arnoldi process (the rest
+// of krylov_expv_persistent)
+void krylov_finish(sgk_ctx* ctx, const KrylovWork<double>& kw, double* W, long long n, int M, double dt);
+
 // exp(dt A) v by the persistent Arnoldi kernel, expm and the combination
 void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork& pw, const KrylovWork<double>& kw,
                             const double* v, double* W, long long n, int M, double dt);
@@ -85,6 +115,9 @@ void vk_gs_update(sgk_ctx* ctx, const T* V, long long ldv, int ncols, const doub
                   const int* stop);
 void vk_convert(sgk_ctx* ctx, const double* x, float* y, long long n);
 void vk_convert(sgk_ctx* ctx, const float* x, double* y, long long n);
+void vk_convert(sgk_ctx* ctx, const double* x, dfloat* y, long long n);
+void vk_convert(sgk_ctx* ctx, const dfloat* x, double* y, long long n);
+void vk_convert(sgk_ctx* ctx, const dfloat* x, float* y, long long n);
 void vk_axpby(sgk_ctx* ctx, double a, const double* x, double b, const double* y, double* z, long long n);
 void vk_residual(sgk_ctx* ctx, const double* U, const double* F, const double* W, double c, double* G, long long n);
 template <typename T>

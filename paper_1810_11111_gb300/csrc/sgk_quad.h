@@ -42,3 +42,8 @@ void quad_cells(sgk_ctx* ctx, const Quad& Q, const ReactionDev& rx, bool jac, co
                 T* const* out);
 void project_separable_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, int nterms, const double* amp,
                            const int* wavenum, const int* kind, double c0, double* U);
+// Load of non-zero Dirichlet data g (the restriction to the boundary of
+// c0 + sum_t amp_t prod_m g_{t,m}(2 pi w x_m), as for the projection) on the
+// device: b_a = -int_{dOmega} (k grad v_a . n - sigma/h v_a) g ds.
+void dirichlet_load_dev(sgk_ctx* ctx, const sgk_index* idx, const Tables1D& tab, const double* kappa, double sigma,
+                        int nterms, const double* amp, const int* wavenum, const int* kind, double c0, double* b);

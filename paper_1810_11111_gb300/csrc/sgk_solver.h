@@ -77,6 +77,11 @@ struct sgk_solver {
     // device-driven step: the whole IIF2 step (predictor, Krylov, Newton with
     // CG) as one graph whose loops are conditional while-nodes
     GraphCache g_step;
+    // the same step in two graphs around an Arnoldi process run elsewhere
+    // (batched launch); n_pre kernels in the first
+    GraphCache g_pre, g_post;
+    int64_t n_pre = 0;
+    bool split_last = false;  // the last launched step used the two graphs
     cudaStream_t aux[2] = {nullptr, nullptr};  // capture streams of the loop bodies
     DevBuf<unsigned char> ctl;                 // StepCtl on the device
     // kernels per segment of the step graph (for the launch count)
@@ -111,6 +116,18 @@ void solver_set_state(sgk_solver* s, int species, const double* src_dev);
 // to roll back to on failure (null: the step graph's own copy)
 void solver_step_launch(sgk_solver* s, int slot = 0);
 int solver_step_finish(sgk_solver* s, int slot = 0, const double* restore = nullptr);
+// The same device-driven step with its Arnoldi process run by the caller
+// (one species, persistent Arnoldi): solver_step_launch_pre queues the state
+// copy, the predictor and v = U + dt/2 F(U); the caller then runs the
+// Arnoldi process of solver_arnoldi_job(s) (after pre, on any stream
+// ordered with it); solver_step_launch_post queues exp(dt H) e_1, the
+// combination and the Newton solve and the outcome copies;
+// solver_step_finish completes it as for solver_step_launch.
+bool solver_split_eligible(const sgk_solver* s);
+ArnJob solver_arnoldi_job(sgk_solver* s);
+void solver_step_launch_pre(sgk_solver* s);
+void solver_step_launch_post(sgk_solver* s, int slot = 0);
+void solver_krylov_finish(sgk_solver* s, int species, double* W);
 // Queue nsteps device-driven steps without waiting (synchronous steps when
 // the solver is not device-driven); solver_drain finishes the queued ones in
 // order and keeps the first failure for sgk_solver_wait.

@@ -6,7 +6,8 @@
 //   solve G(U) = U - dt/2 F(U) - W = 0 by Newton from U = W:
 //         (I - dt/2 J_F(U)) delta = -G(U), U += delta,
 //   inner solver: CG for one species (symmetric), restarted GMRES for systems;
-//   outer stop ||G||_2 <= tol max(1, ||W||_2); on failure the step is undone.
+//   outer stop ||G||_2 <= tol max(||W||_2, ||G(W)||_2) (relative to the
+//   stage's scale); on failure the step is undone.
 // For order r the predictor weight dt/2 becomes alpha_0 dt, each older
 // F(U^{n-i}) adds alpha_{-i} dt exp((i+1) dt A_s) F_s(U^{n-i}) to W_s, and
 // the Newton weight is alpha_1 dt.  F(U, t) includes the source terms at the
@@ -14,17 +15,20 @@
 //
 // All vectors live on the device; the host only reads back the scalars that
 // decide loop exits (none at all in the device-driven step).  In SGK_MIXED
-// mode the reaction and Jacobian passes run in FP32; the Krylov exponential
-// (matvec, basis, exp(dt H)), inner products, norms, the Newton residual
-// vector and the state stay FP64.  The Newton and CG vector steps are fused
-// with their inner products and control decisions.  Because FP32
-// reaction passes put a floor under the residual, the mixed outer loop also
-// stops when ||G|| no longer halves and is below 1e-7 max(1, ||W||) (the
-// Newton iteration has reached that floor: stiff instances, c ~ 100 with
-// |u| ~ 1, stall at 2e-8).
+// mode only the Jacobian products J_F(U) w of the inner solver run in FP32
+// (on an FP32 copy of the transformed U); every F that fixes the answer --
+// the predictor's F(U^n) and the Newton residual's F(U) -- runs in FP64, so
+// Newton's fixed point is that of the FP64 path and the outer stop is the
+// same ||G||_2 <= tol max(||W||_2, ||G(W)||_2) in both modes (an inexact Jacobian only
+// changes the convergence rate).  The Krylov exponential keeps its
+// double-float matvec and FP64 reductions, and the inner products, norms and
+// state stay FP64.  The Newton and CG vector steps are fused with their
+// inner products and control decisions.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
+#include "sgk_dfloat.h"
 #include "sgk_krylov.h"
 #include "sgk_pencil.h"
 #include "sgk_quad.h"
@@ -33,7 +37,7 @@
 namespace {
 
 struct StepCtl {
-    double stop, floor_accept, prev, last_g, cg_stop;
+    double stop, last_g, cg_stop, wnorm, tol;
     int it, status, cg_iters;
     int fvalid;  // Fv holds F(U) for the current U (Newton accepted at its last residual evaluation)
     int pred_skipped;  // this step took F(U^n) from Fv
@@ -43,10 +47,9 @@ struct StepCtl {
 
 // The step's control logic (that of the host loop), on one device thread.
 __device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol) {
-    const double w = fmax(1.0, wnorm);
-    c->stop = tol * w;
-    c->floor_accept = 1e-7 * w;
-    c->prev = INFINITY;
+    c->wnorm = wnorm;
+    c->tol = tol;
+    c->stop = 0.0;  // set at the first residual evaluation
     c->last_g = 0.0;
     c->it = 0;
     c->status = SGK_ENEWTON;
@@ -57,17 +60,16 @@ __device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol
 }
 
 // returns 1 to take another Newton correction
-__device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_iter, int mixed) {
+__device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_iter) {
     c->last_g = g;
+    // the stop is relative to the stage's scale, max(||W||, ||G(W)||), fixed
+    // at the first evaluation (U = W)
+    if (c->it == 0) c->stop = c->tol * fmax(c->wnorm, g);
     unsigned go = 0;
     if (!isfinite(g)) c->status = SGK_ENEWTON;
     else if (g <= c->stop) c->status = SGK_OK;
-    else if (mixed && c->it >= 1 && g > 0.5 * c->prev && g <= c->floor_accept) c->status = SGK_OK;
     else if (c->it >= max_iter) c->status = SGK_ENEWTON;
-    else {
-        c->prev = g;
-        go = 1;
-    }
+    else go = 1;
     // accepted at this evaluation: F(U) of the new state is in Fv
     c->fvalid = c->status == SGK_OK ? 1 : 0;
     return go;
@@ -197,7 +199,7 @@ __global__ void norm_init_kernel(const double* __restrict__ W, long long n, doub
 __global__ void residual_norm_kernel(const double* __restrict__ U, const double* __restrict__ F,
                                      const double* __restrict__ W, double c, double* __restrict__ G, long long n,
                                      double* partials, unsigned* cnt, double* out, StepCtl* ctl,
-                                     cudaGraphConditionalHandle h, int max_iter, int mixed) {
+                                     cudaGraphConditionalHandle h, int max_iter) {
     double acc = 0.0;
     SGK_GRID_STRIDE(i, n) {
         const double g = U[i] - c * F[i] - W[i];
@@ -207,7 +209,7 @@ __global__ void residual_norm_kernel(const double* __restrict__ U, const double*
     finish_sum(acc, partials, cnt, [&](double t) {
         const double g = sqrt(t);
         *out = g;
-        if (ctl) cudaGraphSetConditional(h, newton_decide(ctl, g, max_iter, mixed));
+        if (ctl) cudaGraphSetConditional(h, newton_decide(ctl, g, max_iter));
     });
 }
 
@@ -395,7 +397,8 @@ template <typename T>
 void cell_pass(sgk_solver* s, bool jac, T* const* u, T* const* w, T* const* out) {
     const Quad& Q = s->Q;
     if (!Q.fused) {
-        quad_cells<T>(s->ctx, Q, s->rx, jac, u, w, out);
+        if constexpr (std::is_same<T, dfloat>::value) SGK_REQUIRE(false, SGK_EUNSUPPORTED, "double-float cell pass");
+        else quad_cells<T>(s->ctx, Q, s->rx, jac, u, w, out);
         return;
     }
     PencilArgs a{};
@@ -459,10 +462,33 @@ void evalJ_T(sgk_solver* s, const double* w, T* out) {
     for (int sp = 0; sp < s->nspecies; ++sp) backward_species<T>(s, p.wnod[sp], p.tmp, out + sp * n);
 }
 
-// F(U, t^n + toff): the reaction passes, then the source terms in FP64
+// F(U) in double-float arithmetic (the fused pencil path): U split into
+// FP32 pairs, the FP64 work buffers and plans reused for the pairs, the
+// result summed back to FP64; caches the transformed U (pairs) in unod.
+void evalF_df(sgk_solver* s, const double* U, double* F) {
+    QuadPtrs<dfloat> p = qptrs<dfloat>(s);
+    const long long n = s->n;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        vk_convert(s->ctx, U + sp * n, p.spin[sp], n);
+        forward_species<dfloat>(s, p.spin[sp], p.unod[sp], p.tmp);
+    }
+    cell_pass<dfloat>(s, false, p.unod, nullptr, p.wnod);
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        backward_species<dfloat>(s, p.wnod[sp], p.tmp, p.spout[sp]);
+        vk_convert(s->ctx, p.spout[sp], F + sp * n, n);
+    }
+    s->unod_valid = true;
+}
+
+// The reaction passes of every F that fixes the answer: FP64, or in mixed
+// mode double-float where the fused pencil kernel serves the shape.
+bool df_reaction(const sgk_solver* s) { return s->prec == SGK_MIXED && s->Q.fused; }
+
+// F(U, t^n + toff): the reaction passes (about 1e-14 relative accuracy in
+// both precision modes), then the source terms in FP64
 void evalF(sgk_solver* s, const double* U, double* F, double toff) {
-    if (s->prec == SGK_FP64) evalF_T<double>(s, U, F);
-    else evalF_T<float>(s, U, F);
+    if (df_reaction(s)) evalF_df(s, U, F);
+    else evalF_T<double>(s, U, F);
     if (!s->has_src) return;
     const long long n = s->n;
     for (int sp = 0; sp < s->nspecies; ++sp) {
@@ -486,7 +512,7 @@ void write_time(sgk_solver* s) {
 
 // destroys every cached graph (they are captured again on next use)
 void drop_graphs(sgk_solver* s) {
-    for (GraphCache* g : {&s->g_step, &s->g_pred, &s->g_pred_f, &s->g_resid, &s->g_cg}) {
+    for (GraphCache* g : {&s->g_step, &s->g_pre, &s->g_post, &s->g_pred, &s->g_pred_f, &s->g_resid, &s->g_cg}) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         *g = GraphCache{};
     }
@@ -500,7 +526,16 @@ void drop_graphs(sgk_solver* s) {
     }
 }
 
-// q = p - dt/2 J_F(U) p (stacked FP64)
+// Before the Jacobian products of an inner solve: in mixed mode the FP32
+// passes read an FP32 copy of the transformed U that the last F evaluation
+// (FP64, at the same U) left in the FP64 buffers.
+void jac_prepare(sgk_solver* s) {
+    if (s->prec != SGK_MIXED) return;
+    const long long m = (long long)s->nspecies * s->Q.full_size;
+    if (df_reaction(s)) vk_convert(s->ctx, reinterpret_cast<const dfloat*>(s->q64.p), s->q32.p, m);
+    else vk_convert(s->ctx, s->q64.p, s->q32.p, m);
+}
+
 // q = p - dt/2 J_F(U) p (stacked FP64); with pq also pq = p.q
 void apply_newton_matrix(sgk_solver* s, const double* pv, double* q, double* pq = nullptr) {
     const long long N = s->n * s->nspecies;
@@ -627,23 +662,21 @@ int newton(sgk_solver* s) {
     launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p, s->fcnt.p + FC_NORM,
                  s->scal.p + 6, (StepCtl*)nullptr, 0.0);
     const double wnorm = read_scalar(s, s->scal.p + 6);
-    const double stop = s->opts.tol * std::max(1.0, wnorm);
-    const double floor_accept = 1e-7 * std::max(1.0, wnorm);
-    double prev = INFINITY;
+    double stop = 0.0;  // relative to max(||W||, ||G(W)||), set at the first evaluation
     for (int it = 0; it <= s->opts.max_iter; ++it) {
         run_graph(s, s->g_resid, KC_VECTOR, [&]() {
             evalF(s, s->U.p, s->Fv.p, s->dt);
             launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                          (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID, s->scal.p + 7,
-                         (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0, 0);
+                         (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0);
         });
         const double g = read_scalar(s, s->scal.p + 7);
         s->stats.last_newton_residual = g;
         if (!std::isfinite(g)) break;
+        if (it == 0) stop = s->opts.tol * std::max(wnorm, g);
         if (g <= stop) return SGK_OK;
-        if (s->prec == SGK_MIXED && it >= 1 && g > 0.5 * prev && g <= floor_accept) return SGK_OK;
         if (it == s->opts.max_iter) break;
-        prev = g;
+        jac_prepare(s);
         int inner = 0;
         if (s->nspecies == 1) cg_solve(s, s->G.p, s->cg_x.p, inner);
         else gmres_solve_host(s, s->G.p, s->cg_x.p, inner);
@@ -709,6 +742,13 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, 
     if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
 }
 
+// exp(dt H) e_1 and W = gamma V y of species 0 after its Arnoldi process
+// ran outside the solver (batched launch)
+void solver_krylov_finish(sgk_solver* s, int species, double* W) {
+    krylov_finish(s->ctx, krylov_work<double>(s, species), W, s->n, s->M, s->dt);
+    if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
+}
+
 // ------------------------------------------------ device-driven step ---
 //
 // With graphs on and one species (CG) or no reaction, a whole IIF2 step is
@@ -716,8 +756,7 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, 
 // while-nodes whose conditions are set by one-thread control kernels from the
 // residual norms, so a step needs one host synchronisation (to read the
 // outcome) instead of one per Newton and CG iteration.  The control logic is
-// that of the host loop: stop at ||G|| <= tol max(1, ||W||), the mixed-mode
-// acceptance of a stagnating residual below 1e-7 max(1, ||W||), at most
+// that of the host loop: stop at ||G|| <= tol max(||W||, ||G(W)||), at most
 // max_iter corrections, CG to a relative residual inner_tol.
 
 namespace {
@@ -771,7 +810,13 @@ bool step_graph_eligible(const sgk_solver* s) {
     return s->use_graphs && s->scheme == SGK_IIF2 && (!s->has_rx || s->nspecies == 1);
 }
 
-void build_step_graph(sgk_solver* s) {
+// part: STEP_WHOLE (one graph per step), or the two halves of a step whose
+// Arnoldi process runs elsewhere (a batched launch): STEP_PRE (state copy,
+// predictor, v) and STEP_POST (exp(dt H) e_1, the combination, the Newton
+// solve); one species only for the halves.
+enum { STEP_WHOLE = 0, STEP_PRE = 1, STEP_POST = 2 };
+
+void build_step_graph(sgk_solver* s, int part = STEP_WHOLE) {
     sgk_ctx* ctx = s->ctx;
     const long long n = s->n, N = n * s->nspecies;
     const double dt2 = 0.5 * s->dt;
@@ -783,6 +828,7 @@ void build_step_graph(sgk_solver* s) {
     ctx->capturing = true;
     SGK_CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     try {
+      if (part != STEP_POST) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         if (s->has_rx) {
             // F(U^n) for the predictor, unless the last step left it in Fv
@@ -803,10 +849,16 @@ void build_step_graph(sgk_solver* s) {
             SGK_CUDA_CHECK(
                 cudaMemcpyAsync(s->vv.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         }
-        for (int sp = 0; sp < s->nspecies; ++sp) solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n);
+      }
+      if (part == STEP_PRE) {
+        s->n_pre = ctx->launches - before;
+      } else {
+        if (part == STEP_WHOLE)
+            for (int sp = 0; sp < s->nspecies; ++sp) solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n);
+        else
+            solver_krylov_finish(s, 0, s->W.p);
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         if (s->has_rx) {
-            const int mixed = s->prec == SGK_MIXED ? 1 : 0;
             double* const rr = s->scal.p + 2;
             double* const rr_new = s->scal.p + 3;
             double* const pq = s->scal.p + 4;
@@ -816,7 +868,7 @@ void build_step_graph(sgk_solver* s) {
                 evalF(s, s->U.p, s->Fv.p, s->dt);
                 launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                              (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID,
-                             s->scal.p + 7, ctl, h, s->opts.max_iter, mixed);
+                             s->scal.p + 7, ctl, h, s->opts.max_iter);
             };
             int64_t mark = 0;
             capture_while(
@@ -829,6 +881,7 @@ void build_step_graph(sgk_solver* s) {
                 [&](cudaGraphConditionalHandle hn) {
                     s->n_prefix = ctx->launches - before;
                     mark = ctx->launches;
+                    jac_prepare(s);
                     double* x = s->cg_x.p;
                     double* r = s->cg_r.p;
                     double* pv = s->cg_p.p;
@@ -861,6 +914,7 @@ void build_step_graph(sgk_solver* s) {
         } else {
             s->n_prefix = ctx->launches - before;
         }
+      }
     } catch (...) {
         cudaStreamEndCapture(ctx->stream, &graph);
         if (graph) cudaGraphDestroy(graph);
@@ -872,7 +926,8 @@ void build_step_graph(sgk_solver* s) {
     ctx->capturing = false;
     ctx->launches = before;
     SGK_CUDA_CHECK(e);
-    const cudaError_t ei = cudaGraphInstantiate(&s->g_step.exec, graph, 0);
+    GraphCache& g = part == STEP_WHOLE ? s->g_step : (part == STEP_PRE ? s->g_pre : s->g_post);
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     SGK_CUDA_CHECK(ei);
 }
@@ -887,15 +942,62 @@ struct StepRecord {
 
 }  // namespace
 
+// Copies of a launched step's outcome to its host record.
+static void step_record(sgk_solver* s, int slot);
+
 // Queues one device-driven step (graph launch and the copies of its
 // outcome) without waiting.
 void solver_step_launch(sgk_solver* s, int slot) {
     sgk_ctx* ctx = s->ctx;
     if (!s->g_step.exec) build_step_graph(s);
-    StepRecord* h = static_cast<StepRecord*>(s->hrec) + slot;
     write_time(s);
-    KTimer kt(ctx, KC_KRYLOV);
-    SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
+    {
+        KTimer kt(ctx, KC_KRYLOV);
+        SGK_CUDA_CHECK(cudaGraphLaunch(s->g_step.exec, ctx->stream));
+    }
+    s->split_last = false;
+    step_record(s, slot);
+}
+
+bool solver_split_eligible(const sgk_solver* s) {
+    return solver_device_steps(s) && s->nspecies == 1 && s->persistent;
+}
+
+ArnJob solver_arnoldi_job(sgk_solver* s) {
+    ArnJob j;
+    j.ctx = s->ctx;
+    j.op = s->ops[0];
+    j.pw.w_alt = s->w64b.p;
+    j.pw.Z = s->zbuf.p;
+    j.pw.pbuf = s->pbuf.p;
+    j.pw.bar = s->pbar.p;
+    j.pw.G = s->arn_G;
+    j.pw.bounds = s->abounds.p;
+    j.pw.E = s->aE;
+    j.pw.list_ent = s->alist;
+    j.kw = krylov_work<double>(s, 0);
+    j.v = s->vv.p;
+    j.n = s->n;
+    j.M = s->M;
+    return j;
+}
+
+void solver_step_launch_pre(sgk_solver* s) {
+    if (!s->g_pre.exec) build_step_graph(s, STEP_PRE);
+    write_time(s);
+    SGK_CUDA_CHECK(cudaGraphLaunch(s->g_pre.exec, s->ctx->stream));
+}
+
+void solver_step_launch_post(sgk_solver* s, int slot) {
+    if (!s->g_post.exec) build_step_graph(s, STEP_POST);
+    SGK_CUDA_CHECK(cudaGraphLaunch(s->g_post.exec, s->ctx->stream));
+    s->split_last = true;
+    step_record(s, slot);
+}
+
+static void step_record(sgk_solver* s, int slot) {
+    sgk_ctx* ctx = s->ctx;
+    StepRecord* h = static_cast<StepRecord*>(s->hrec) + slot;
     if (s->has_rx)
         SGK_CUDA_CHECK(cudaMemcpyAsync(&h->c, s->ctl.p, sizeof(StepCtl), cudaMemcpyDeviceToHost, ctx->stream));
     SGK_CUDA_CHECK(cudaMemcpyAsync(h->ks, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
@@ -914,7 +1016,8 @@ int solver_step_finish(sgk_solver* s, int slot, const double* restore) {
     StepCtl c{};
     if (s->has_rx) c = h->c;
     int rc = s->has_rx ? c.status : SGK_OK;
-    count_launch(ctx, (int)(s->n_prefix - (s->has_rx && c.pred_skipped ? s->n_predf : 0) +
+    count_launch(ctx, (int)((s->split_last ? s->n_pre : 0) + s->n_prefix -
+                            (s->has_rx && c.pred_skipped ? s->n_predf : 0) +
                             c.newton_iters * (s->n_cgpre + s->n_adv + s->n_resid) + c.inner_iters * s->n_cgbody));
     s->stats.newton_iters += c.newton_iters;
     s->stats.inner_iters += c.inner_iters;
@@ -1219,7 +1322,11 @@ void solver_alloc(sgk_solver* s) {
     s->ctl.alloc(sizeof(StepCtl));
     SGK_CUDA_CHECK(cudaMallocHost(&s->hrec, SGK_ASYNC_SLOTS * sizeof(StepRecord)));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->ctl.p, 0, sizeof(StepCtl), s->ctx->stream));
-    s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && n <= arnoldi_persistent_max_n(s->ctx);
+    // the persistent kernel's gather holds the diagonal terms only: an
+    // operator with mixed-derivative terms takes the launch-sequence path
+    bool cross = false;
+    for (int sp = 0; sp < S; ++sp) cross = cross || s->ops[sp]->npairs > 0;
+    s->persistent = std::getenv("SGK_NO_PERSISTENT") == nullptr && !cross && n <= arnoldi_persistent_max_n(s->ctx);
     if (s->persistent) {
         s->w64b.alloc(n);
         s->zbuf.alloc((size_t)(M + 1) * n);
@@ -1257,8 +1364,10 @@ void solver_alloc(sgk_solver* s) {
         s->cg_p.alloc(N);
         s->cg_q.alloc(N);
         const long long qsize = (2 * S + 1) * s->Q.full_size + 2 * S * n;
+        // FP64 buffers for F (both modes) and, in mixed mode, FP32 buffers
+        // for the Jacobian products
+        s->q64.alloc(qsize);
         if (s->prec == SGK_FP64) {
-            s->q64.alloc(qsize);
             s->jw64.alloc(N);
         } else {
             s->q32.alloc(qsize);

@@ -75,22 +75,30 @@ _SIGS = {
     "sgk_ctx_destroy": (ctypes.c_int, [_P]),
     "sgk_last_error": (ctypes.c_char_p, [_P]),
     "sgk_ctx_launch_count": (ctypes.c_int64, [_P]),
+    "sgk_binary_arch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "sgk_ctx_profile": (ctypes.c_int, [_P, ctypes.c_uint]),
     "sgk_ctx_profile_read": (ctypes.c_int, [_P, _c_double_p, _c_i64_p]),
     "sgk_index_build": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
     "sgk_index_destroy": (ctypes.c_int, [_P]),
     "sgk_index_dof": (ctypes.c_int64, [_P]),
+    "sgk_dof": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "sgk_estimate_work": (ctypes.c_double, [ctypes.c_int] * 6),
+    "sgk_partition": (ctypes.c_int, [ctypes.c_int, _c_double_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sgk_index_ntuples": (ctypes.c_int64, [_P]),
     "sgk_index_export": (ctypes.c_int, [_P, _c_i32_p, _c_i64_p, ctypes.c_int64]),
     "sgk_index_lookup": (ctypes.c_int, [_P, _c_i32_p, ctypes.c_int64, _c_i64_p]),
     "sgk_operator_assemble": (ctypes.c_int, [_P, _P, _c_double_p, ctypes.c_int, ctypes.c_double,
                                              ctypes.POINTER(_P)]),
+    "sgk_operator_assemble_full": (ctypes.c_int, [_P, _P, _c_double_p, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.POINTER(_P)]),
     "sgk_operator_destroy": (ctypes.c_int, [_P]),
     "sgk_operator_madds": (ctypes.c_int64, [_P]),
     "sgk_operator_export_1d": (ctypes.c_int, [_P, _c_double_p, ctypes.c_int64]),
     "sgk_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "sgk_project_separable": (ctypes.c_int, [_P, _P, ctypes.c_int, _c_double_p, _c_int_p, _c_int_p,
                                              ctypes.c_double, _P]),
+    "sgk_dirichlet_load": (ctypes.c_int, [_P, _P, _c_double_p, ctypes.c_double, ctypes.c_int, _c_double_p, _c_int_p,
+                                          _c_int_p, ctypes.c_double, _P]),
     "sgk_solver_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(sgk_reaction),
                                          ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.POINTER(sgk_newton_opts), ctypes.POINTER(_P)]),
@@ -128,6 +136,8 @@ _SIGS = {
     "sgk_batch_count": (ctypes.c_int, [_P]),
     "sgk_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int64]),
     "sgk_batch_destroy": (ctypes.c_int, [_P]),
+    "sgk_batch_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sgk_batch_launches": (ctypes.c_int64, [_P]),
 }
 EXPM_NOALLOC_MAX_M = 64
 
@@ -240,6 +250,16 @@ class IndexSet:
         self.ctx.check(sgk_project_separable(self.ctx.h, self.h, len(amp), _dptr(amp), _iptr(wavenum),
                                              _iptr(kind), float(const), out_ptr))
 
+    def dirichlet_load(self, kappa, amp, wavenum, kind, const, out_ptr, sigma=20.0):
+        """Load vector of the boundary data const + sum_t amp_t prod_m g(2 pi w x_m)
+        into the device array at out_ptr (dof doubles)."""
+        kap = np.ascontiguousarray(kappa, dtype=np.float64)
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        wavenum = np.ascontiguousarray(wavenum, dtype=np.int32).reshape(-1)
+        kind = np.ascontiguousarray(kind, dtype=np.int32).reshape(-1)
+        self.ctx.check(sgk_dirichlet_load(self.ctx.h, self.h, _dptr(kap), float(sigma), len(amp), _dptr(amp),
+                                          _iptr(wavenum), _iptr(kind), float(const), out_ptr))
+
     def close(self):
         if self.h:
             sgk_index_destroy(self.h)
@@ -248,10 +268,16 @@ class IndexSet:
 
 class Operator:
     def __init__(self, ctx, idx, kappa, bc=SGK_PERIODIC, sigma=20.0):
+        """kappa: the d diagonal entries of a diagonal diffusion tensor, or
+        a full d x d symmetric positive definite tensor."""
         self.ctx, self.idx = ctx, idx
         kap = np.ascontiguousarray(kappa, dtype=np.float64)
         self.h = _P()
-        ctx.check(sgk_operator_assemble(ctx.h, idx.h, _dptr(kap), int(bc), float(sigma), ctypes.byref(self.h)))
+        if kap.ndim == 2:
+            ctx.check(sgk_operator_assemble_full(ctx.h, idx.h, _dptr(kap.reshape(-1)), int(bc), float(sigma),
+                                                 ctypes.byref(self.h)))
+        else:
+            ctx.check(sgk_operator_assemble(ctx.h, idx.h, _dptr(kap), int(bc), float(sigma), ctypes.byref(self.h)))
         self.H = (idx.k + 1) << idx.n
 
     def madds(self):
@@ -369,17 +395,23 @@ class Solver:
 
 
 def dof_of(d, n, k):
-    """Coefficients per species of the sparse grid (d, level n, degree k):
-    the sum over level tuples |l|_1 <= n of prod_m (k+1) 2^max(l_m - 1, 0)."""
-    cnt = [1] + [0] * n
-    for _ in range(d):
-        nxt = [0] * (n + 1)
-        for s_, c in enumerate(cnt):
-            if c:
-                for lv in range(n + 1 - s_):
-                    nxt[s_ + lv] += c * ((k + 1) << max(lv - 1, 0))
-        cnt = nxt
-    return sum(cnt)
+    """Coefficients per species of the sparse grid (d, level n, degree k),
+    from the library's host-side count (sgk_dof)."""
+    load()
+    v = sgk_dof(int(d), int(n), int(k))
+    if v < 0:
+        raise SgkError(SGK_EINVAL, "sgk_dof: d, n or k out of range")
+    return int(v)
+
+
+def binary_arch():
+    """Architecture of the loaded device code (103 for sm_103a)."""
+    load()
+    a = ctypes.c_int(0)
+    rc = sgk_binary_arch(ctypes.byref(a))
+    if rc != SGK_OK:
+        raise SgkError(rc, "sgk_binary_arch")
+    return a.value
 
 
 class Server:
@@ -474,13 +506,18 @@ class Batch:
     """Independent IIF2 problems stepped together (sgk_batch_*); instances
     are workload dicts as for Server."""
 
-    def __init__(self, device=0, streams=8, slice_len=0):
+    def __init__(self, device=0, streams=8, slice_len=0, fused=True):
         load()
         self.h = _P()
         rc = sgk_batch_create(int(device), int(streams), int(slice_len), ctypes.byref(self.h))
         if rc:
             raise SgkError(rc, "sgk_batch_create failed")
+        sgk_batch_set_fused(self.h, 1 if fused else 0)
         self.nspecies = []
+
+    def launches(self):
+        """Kernels of the batched Arnoldi path so far."""
+        return int(sgk_batch_launches(self.h))
 
     def add(self, cfg, precision=SGK_MIXED, init_coeffs=None):
         q, keep = Server.request(cfg, precision, init_coeffs)

@@ -1,6 +1,7 @@
-"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
-every entry point declared in include/sgkiif.h (no compute calls: there is no
-GPU here).  The binding declares exactly the header's functions."""
+"""Checks of the C ABI: the library builds, loads, and exports every entry
+point declared in include/sgkiif.h, and the binding declares exactly the
+header's functions (CPU, no compute calls); on a GPU, the runtime loads the
+sm_103a image of its kernels."""
 import os
 import re
 
@@ -41,10 +42,22 @@ def test_binding_matches_header():
     assert sgkiif.exported_symbols() == header_functions()
 
 
-def test_library_is_built_for_sm103a(lib):
+@pytest.mark.gpu
+def test_loaded_device_code_is_sm103(lib):
+    # the runtime's view of the image it loaded for the library's kernels
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
     from paper_1810_11111_gb300 import sgkiif
-    data = open(sgkiif.LIB_PATH, "rb").read()
-    assert b"sm_103a" in data or b"sm_103" in data
+    assert sgkiif.binary_arch() == 103
+
+
+def test_host_dof_count_matches_closed_form(lib):
+    from oracle.index_set import IndexSet as OIndex
+    from paper_1810_11111_gb300 import sgkiif
+    for d, n, k in [(1, 0, 1), (2, 4, 1), (3, 6, 2), (4, 9, 3), (6, 3, 2)]:
+        assert sgkiif.dof_of(d, n, k) == OIndex(d, n, k).dof
+    assert sgkiif.sgk_dof(0, 3, 1) == -1 and sgkiif.sgk_dof(2, 13, 1) == -1 and sgkiif.sgk_dof(2, 3, 4) == -1
 
 
 def test_context_creation_without_gpu_fails_cleanly(lib):

@@ -4,8 +4,12 @@ On the GPU: every instance of a mixed batch (2D/3D/4D cubic reaction in
 FP64 and mixed precision, pure diffusion, a two-species system that takes
 the host-driven path) matches the same problem solved alone through the
 solver API within the parity tolerance of its precision (1e-10 FP64, 1e-6
-mixed; the persistent Arnoldi grid differs, so sums run in another order),
-and the batch's results do not depend on its stream count (bitwise).
+mixed; the persistent Arnoldi grid differs, so sums run in another order);
+the batch's results do not depend on its stream count (bitwise); the
+batched Arnoldi launches (one persistent cooperative launch per kernel
+class, CTAs walking (instance, slice) work lists) give bitwise the results
+of every instance's own whole-step graph, also when many instances of one
+class must share the CTAs in turn.
 """
 import numpy as np
 import pytest
@@ -41,13 +45,14 @@ INSTANCES = [
 ]
 
 
-def run_batch(streams, steps):
-    b = sgkiif.Batch(0, streams=streams)
-    for cfg, prec in INSTANCES:
+def run_batch(streams, steps, fused=True, instances=INSTANCES):
+    b = sgkiif.Batch(0, streams=streams, fused=fused)
+    for cfg, prec in instances:
         b.add(cfg, prec)
     rc, st = b.step(steps)
     assert rc == sgkiif.SGK_OK and all(s == sgkiif.SGK_OK for s in st)
-    out = [np.concatenate(b.state(i)) for i in range(len(INSTANCES))]
+    out = [np.concatenate(b.state(i)) for i in range(len(instances))]
+    assert (b.launches() > 0) == fused
     b.close()
     return out
 
@@ -66,5 +71,22 @@ def test_batch_matches_instances_alone():
 def test_batch_independent_of_stream_count():
     a = run_batch(1, 2)
     b = run_batch(5, 2)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_batched_launch_equals_whole_step_graphs():
+    a = run_batch(3, 2, fused=True)
+    b = run_batch(3, 2, fused=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_batched_launch_with_more_instances_than_sms():
+    # 60 small 2D instances (1024 coefficients, 3 CTAs each: 180 CTAs, more
+    # than the SMs): CTAs take several instances in turn from their work lists
+    many = [(cubic(2, 6, 1, 100 + i, 10.0 + i), sgkiif.SGK_MIXED) for i in range(60)]
+    a = run_batch(8, 2, fused=True, instances=many)
+    b = run_batch(8, 2, fused=False, instances=many)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)

@@ -10,8 +10,8 @@ Tolerances (relative, coefficient 2-norm unless stated):
     for steps; component checks carry FP32 bounds stated in each test.
 Sizes span several work tiles and ragged fiber lengths; the 3D cubic
 workload at level 6 (the benchmarked configuration) is compared with a
-stored oracle step (tests/golden/cubic3d_step1.npz, written by
-tests/golden/make_cubic3d_step.py) and, for the reaction term and its
+stored oracle run (tests/golden/cubic3d_steps.npz, written by
+tests/golden/make_full_size.py) and, for the reaction term and its
 Jacobian, with the oracle's full vectors.
 """
 import os
@@ -166,6 +166,86 @@ def test_matvec_fp32(ctx64, d, n, k, bc):
     assert rel(yd.double().cpu().numpy(), want) <= 1e-5
     op.close()
     idx.close()
+
+
+# ------------------------------------- full constant diffusion tensor ---
+
+def _spd(d, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((d, d))
+    K = 0.3 * (B @ B.T) / d + np.diag(rng.uniform(0.2, 0.8, d))
+    return 0.5 * (K + K.T)
+
+
+FULLK_CASES = [(2, 4, 1, PERIODIC), (2, 5, 2, DIRICHLET0), (3, 3, 2, PERIODIC), (3, 4, 1, DIRICHLET0),
+               (4, 3, 1, PERIODIC), (2, 3, 3, PERIODIC)]
+
+
+@pytest.mark.parametrize("d,n,k,bc", FULLK_CASES)
+def test_full_tensor_matvec_matches_oracle(ctx64, d, n, k, bc):
+    # the diagonal gather plus the mixed-derivative terms of every pair,
+    # against the oracle's matrix-free general operator (itself equal to the
+    # dense restricted matrix); FP64 and FP32
+    from oracle.operator import cross_blocks_1d, sparse_matvec_general
+    K = _spd(d, 10 * d + n + k)
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    op = sgkiif.Operator(ctx64, idx, K, bc)
+    ref = OIndex(d, n, k)
+    P, E = cross_blocks_1d(n, k, bc)
+    x = np.random.default_rng(d + n).standard_normal(idx.dof)
+    want = sparse_matvec_general(ref, sipg_1d(n, k, bc), P, E, K, x)
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    op.matvec(xd.data_ptr(), yd.data_ptr(), sgkiif.SGK_FP64)
+    torch.cuda.synchronize()
+    assert rel(yd.cpu().numpy(), want) <= 1e-12
+    x32 = x.astype(np.float32)
+    want32 = sparse_matvec_general(ref, sipg_1d(n, k, bc), P, E, K, x32.astype(np.float64))
+    xf = dev(x32.astype(np.float64), torch.float32)
+    yf = torch.empty_like(xf)
+    op.matvec(xf.data_ptr(), yf.data_ptr(), sgkiif.SGK_MIXED)
+    torch.cuda.synchronize()
+    assert rel(yf.double().cpu().numpy(), want32) <= 1e-5
+    op.close()
+    idx.close()
+
+
+def test_full_tensor_is_rejected_unless_spd(ctx64):
+    idx = sgkiif.IndexSet(ctx64, 2, 3, 1)
+    for bad in (np.array([[1.0, 0.2], [0.3, 1.0]]), np.array([[1.0, 2.0], [2.0, 1.0]])):
+        h = sgkiif._P()
+        assert sgkiif.sgk_operator_assemble_full(ctx64.h, idx.h, bad.reshape(-1).ctypes.data_as(sgkiif._c_double_p),
+                                                 0, 20.0, sgkiif.ctypes.byref(h)) == sgkiif.SGK_EINVAL
+    idx.close()
+
+
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_full_tensor_steps_match_oracle(precision):
+    # IIF2 with a full SPD tensor and a cubic reaction: the Krylov projection
+    # of the general operator (launch-sequence Arnoldi) and Newton
+    from oracle.operator import cross_blocks_1d, sparse_matvec_general
+    d, n, k = 3, 4, 2
+    K = _spd(d, 7)
+    rng = np.random.default_rng(8)
+    amp, wn, kind = workloads.fourier_modes(rng, d)
+    cfg = dict(d=d, n=n, k=k, kappas=[K], reaction=workloads.reaction_terms(workloads.CUBIC, 20.0), M=30,
+               dt=0.005, init=[dict(amp=amp, wavenum=wn, kind=kind, const=0.0)])
+    prob = Problem(cfg, precision)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(3)
+    got = prob.state()[0]
+    idx = OIndex(d, n, k)
+    S = sipg_1d(n, k)
+    P, E = cross_blocks_1d(n, k)
+
+    class GeneralK(IIF2Solver):
+        def A(self, s):
+            return lambda x: sparse_matvec_general(idx, S, P, E, K, x)
+
+    want = GeneralK(idx, S, [np.diag(K)], cfg["reaction"], cfg["dt"], cfg["M"]).run(U0, 3)[0]
+    assert rel(got, want) <= (1e-10 if precision == sgkiif.SGK_FP64 else 1e-6)
+    prob.close()
 
 
 # ----------------------------------------------------------- projection ---
@@ -558,6 +638,58 @@ def test_source_steps_match_oracle(name, ex, k, N, scheme, precision):
     prob.close()
 
 
+# ------------------------------------------ non-zero Dirichlet data ---
+
+DIRICHLET_LOAD_CASES = [(1, 4, 1), (2, 3, 2), (2, 4, 3), (3, 3, 1), (3, 2, 2)]
+
+
+@pytest.mark.parametrize("d,N,k", DIRICHLET_LOAD_CASES)
+def test_dirichlet_load_matches_oracle(ctx64, d, N, k):
+    # b_a = -int_{dOmega} (k grad v_a . n - sigma/h v_a) g ds for data that
+    # restricts a separable trig sum plus a constant
+    from oracle.boundary import dirichlet_load, trig_terms
+    rng = np.random.default_rng(70 + 10 * d + N + k)
+    amp = rng.uniform(-1.0, 1.0, 3)
+    wavenum = rng.integers(1, 4, (3, d)).astype(np.int32)
+    kind = rng.integers(0, 2, (3, d)).astype(np.int32)
+    kind[0] = 1  # a term that is non-zero on every face
+    kappa = rng.uniform(0.2, 1.5, d)
+    idx = sgkiif.IndexSet(ctx64, d, N, k)
+    out = torch.empty(idx.dof, dtype=torch.float64, device=DEV)
+    idx.dirichlet_load(kappa, amp, wavenum, kind, 0.7, out.data_ptr())
+    want = dirichlet_load(OIndex(d, N, k), kappa, trig_terms(d, amp, wavenum, kind, 0.7))
+    assert rel(out.cpu().numpy(), want) <= 1e-12
+    idx.close()
+
+
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_nonzero_dirichlet_steps_match_oracle(precision):
+    # u = g on the boundary with g(x, t) = e^{lam t} prod cos(2 pi x_m) (the
+    # boundary values of the heat solution of that form), a cubic reaction,
+    # IIF2 steps: the load enters as the source term (lam, b)
+    from oracle.boundary import dirichlet_load, trig_terms
+    d, N, k = 2, 4, 2
+    kap = [0.3, 0.3]
+    lam = -0.3 * 4 * np.pi ** 2 * d
+    wn, cos = np.ones((1, d), np.int32), np.ones((1, d), np.int32)
+    cfg = dict(d=d, n=N, k=k, kappas=[kap], reaction=workloads.reaction_terms(workloads.CUBIC, 5.0), M=25,
+               dt=0.01, init=[dict(amp=np.array([1.0]), wavenum=wn, kind=cos)])
+    prob = Problem(cfg, precision, bc=sgkiif.SGK_DIRICHLET0)
+    b = torch.empty(prob.dof, dtype=torch.float64, device=DEV)
+    prob.idx.dirichlet_load(kap, [1.0], wn, cos, 0.0, b.data_ptr())
+    prob.solver.set_source(0, [lam], b.data_ptr())
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(4)
+    got = prob.state()[0]
+    idx = OIndex(d, N, k)
+    bo = dirichlet_load(idx, kap, trig_terms(d, [1.0], wn, cos))
+    want = IIF2Solver(idx, sipg_1d(N, k, DIRICHLET0), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                      sources=[[(lam, bo)]]).run(U0, 4)[0]
+    assert rel(got, want) <= (1e-10 if precision == sgkiif.SGK_FP64 else 1e-6)
+    prob.close()
+
+
 def test_source_reaction_eval_and_errors():
     cfg, bc, _ = _example23_cfg(2, 2, 2, 4, sgkiif.SGK_IIF2)
     prob = Problem(cfg, sgkiif.SGK_FP64, bc=bc)
@@ -772,10 +904,11 @@ def test_dirichlet_heat_steps():
 # ------------------------------------------ full-size benchmark workload ---
 
 def _golden():
-    path = os.path.join(GOLDEN, "cubic3d_step1.npz")
+    path = os.path.join(GOLDEN, "cubic3d_steps.npz")
     if not os.path.exists(path):
-        pytest.skip("golden step not generated")
-    return np.load(path)
+        pytest.skip("golden run not generated")
+    g = np.load(path)
+    return {"U0": g["U0"][0], "U1": g["U1"][0]}
 
 
 @pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-10), (sgkiif.SGK_MIXED, 1e-6)])
@@ -789,10 +922,11 @@ def test_cubic3d_full_size_step(precision, tol):
     prob.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-12), (sgkiif.SGK_MIXED, 1e-5)])
-def test_cubic3d_full_size_reaction_and_jacobian(precision, tol):
+@pytest.mark.parametrize("precision,tol_f,tol_j", [(sgkiif.SGK_FP64, 1e-12, 1e-12), (sgkiif.SGK_MIXED, 1e-12, 1e-5)])
+def test_cubic3d_full_size_reaction_and_jacobian(precision, tol_f, tol_j):
     # the oracle's reaction pass at level 6 takes seconds, so the whole vector
-    # is compared (F and J at the stored initial state)
+    # is compared (F and J at the stored initial state); F is FP64-accurate in
+    # both modes (double-float passes in mixed), J is FP32 in mixed
     cfg = workloads.cubic3d()
     g = _golden()
     d, n, k = cfg["d"], cfg["n"], cfg["k"]
@@ -807,12 +941,58 @@ def test_cubic3d_full_size_reaction_and_jacobian(precision, tol):
     sol.jacobian_apply(Ud.data_ptr(), Wd.data_ptr(), Jd.data_ptr())
     torch.cuda.synchronize()
     R = Reaction(OIndex(d, n, k), cfg["reaction"])
-    assert rel(Fd.cpu().numpy(), R.F([g["U0"]])[0]) <= tol
-    assert rel(Jd.cpu().numpy(), R.J([g["U0"]], [w])[0]) <= tol
+    assert rel(Fd.cpu().numpy(), R.F([g["U0"]])[0]) <= tol_f
+    assert rel(Jd.cpu().numpy(), R.J([g["U0"]], [w])[0]) <= tol_j
     sol.close()
     op.close()
     idx.close()
     ctx.close()
+
+
+def _golden_run(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip("golden run not generated")
+    return np.load(path)
+
+
+def _rel_species(got, want):
+    got, want = np.stack(got), np.asarray(want)
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-10), (sgkiif.SGK_MIXED, 1e-6)])
+def test_cubic3d_full_size_20_steps_match_oracle(precision, tol):
+    # the benchmarked workload over its whole configured solve (20 steps,
+    # device-driven step graphs), against the oracle's states after steps
+    # 1, 5, 10 and 20 (tests/golden/make_full_size.py)
+    g = _golden_run("cubic3d_steps.npz")
+    prob = Problem(workloads.cubic3d(), precision)
+    prob.reset()
+    assert np.abs(prob.U0[0].cpu().numpy() - g["U0"][0]).max() <= 1e-13
+    done = 0
+    for step in (1, 5, 10, 20):
+        prob.solver.step(step - done)
+        done = step
+        assert _rel_species(prob.state(), g["U%d" % step]) <= tol, step
+    prob.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(sgkiif.SGK_FP64, 1e-10), (sgkiif.SGK_MIXED, 1e-6)])
+def test_schnak2d_full_size_steps_match_oracle(precision, tol):
+    # the two-species Schnakenberg workload at its stated size (d = 2,
+    # level 8, degree 2, M = 40, dt = 0.05; Newton with GMRES) against the
+    # oracle's states after steps 1, 5 and 10
+    g = _golden_run("schnak2d_steps.npz")
+    prob = Problem(workloads.schnak2d(), precision)
+    prob.reset()
+    assert np.abs(np.stack([u.cpu().numpy() for u in prob.U0]) - g["U0"]).max() == 0.0
+    done = 0
+    for step in (1, 5, 10):
+        prob.solver.step(step - done)
+        done = step
+        assert _rel_species(prob.state(), g["U%d" % step]) <= tol, step
+    prob.close()
 
 
 # ---------------------------------------------------------- error paths ---
