@@ -46,6 +46,10 @@ def parse():
                     help="instances of the batched leg (0 skips it)")
     ap.add_argument("--no-matvec", action="store_true", help="skip the large stand-alone matvec leg")
     ap.add_argument("--no-iif3", action="store_true", help="skip the IIF3 leg")
+    ap.add_argument("--no-schnak", action="store_true", help="skip the two-species 200-step leg")
+    ap.add_argument("--served-rates", default="1",
+                    help="comma-separated arrival rates of the served leg, as multiples of the one-at-a-time "
+                         "capacity (e.g. 0.5,1,2)")
     return ap.parse_args()
 
 
@@ -318,7 +322,6 @@ def native(args, rank, world, local_rank):
     bytes_algo, flops_algo = None, None
     if dominant == "cell_quadrature":
         last = sizes[d - 1]
-        bytes_algo = (nF * 2 * S * last + nJ * 3 * S * last) * elem
         cells = (1 << N) ** d
         pencils = (1 << N) ** (d - 1)
         P = kp1 ** (d - 1)
@@ -326,7 +329,26 @@ def native(args, rank, world, local_rank):
         pyr = 2 * kp1 * kp1 * ((1 << (N + 1)) - 2)                  # FMAs per fiber and direction
         fma_F = cells * S * 2 * fwd + pencils * (S * P + S * P) * pyr
         fma_J = cells * S * 3 * fwd + pencils * (2 * S * P + S * P) * pyr
-        flops_algo = 2.0 * (nF * fma_F + nJ * fma_J)
+        # passes of the profiled steps (host-driven: the predictor's F is
+        # evaluated at the first step and reused after it): in mixed mode
+        # the F passes that decide (predictor, residuals after a correction)
+        # run in double-float, the first residual of every step and the
+        # Jacobian products in FP32; in FP64 mode every pass is FP64
+        newton = ps1["newton_iters"] - ps0["newton_iters"]
+        if prec == sgkiif.SGK_MIXED:
+            nF_df, nF_32 = 1 + newton, args.steps
+            bytes_algo = (nF_df * 2 * S * last * 8 + nF_32 * 2 * S * last * 4 + nJ * 3 * S * last * 4)
+            # FP32 issue slots: one per FP32 multiply-add; a double-float
+            # multiply-add is 12 FP32 operations (4 for the product, 8 for
+            # the TwoSum addition; sgk_dfloat.h)
+            slots = nF_df * fma_F * 12 + nF_32 * fma_F + nJ * fma_J
+            flops_algo = 2.0 * slots
+            pass_mix = {"double_float_F": nF_df, "fp32_F": nF_32, "fp32_J": nJ}
+        else:
+            nF_64 = 1 + newton + args.steps
+            bytes_algo = (nF_64 * 2 * S * last + nJ * 3 * S * last) * 8
+            flops_algo = 2.0 * (nF_64 * fma_F + nJ * fma_J)
+            pass_mix = {"fp64_F": nF_64, "fp64_J": nJ}
     elif dominant in ("to_finest", "from_finest"):
         bytes_algo = (nF + nJ) * S * sum(sizes[i] + sizes[i + 1] for i in range(d - 1)) * elem
     elif dominant == "matvec":
@@ -382,11 +404,17 @@ def native(args, rank, world, local_rank):
                                          "the basis stays in shared memory and L2")
         elif flops_algo:
             clock = (clk or {}).get("sm_max_mhz") or 2070.0
-            peak = 152 * 128 * 2 * clock * 1e6 / 1e12
+            mixed = prec == sgkiif.SGK_MIXED
+            peak = 152 * 128 * 2 * clock * 1e6 / 1e12 if mixed else 1.25
             achieved = flops_algo / t / 1e12
             roofline = dict(common, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                            frac=achieved / peak,
-                            peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                            frac=achieved / peak, passes=pass_mix,
+                            work_model="FP32-pipe flops: 2 per FP32 multiply-add, 24 per double-float "
+                                       "multiply-add (12 FP32 operations); algorithmic multiply-adds of the "
+                                       "sum-factorised quadrature and the two-scale pyramids of the last "
+                                       "direction" if mixed else "FP64 flops, 2 per multiply-add",
+                            peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock" if mixed
+                            else "nominal FP64 rate of the part (1.25 TFLOP/s)",
                             algorithmic_flops_per_launch=flops_algo / nl,
                             algorithmic_bytes_per_launch=bytes_algo / nl,
                             hbm_view={"achieved_gbs": bytes_algo / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
@@ -423,6 +451,8 @@ def native(args, rank, world, local_rank):
         out["matvec"] = matvec_leg(peaks, peak_kind)
     if world == 1 and not args.no_iif3:
         out["iif3"] = iif3_leg(cfg, args)
+    if world == 1 and not args.no_schnak:
+        out["schnak2d"] = schnak_leg(args)
     if args.batch_instances > 0:
         out["batched"] = batched_leg(args, dist, rank, world)
     if world == 1 and args.served_requests > 0:
@@ -477,6 +507,56 @@ def iif3_leg(cfg, args):
     return out
 
 
+# ------------------------------------------------- two-species leg ---
+
+def schnak_leg(args):
+    """The two-species Schnakenberg workload at its configured size (d = 2,
+    level 8, degree 2, 11 520 coefficients per species, kappa 0.01 / 0.5,
+    M = 40, dt = 0.05, 200 IIF2 steps; Newton with GMRES, host-driven
+    steps), mixed and FP64, device-timed over all 200 steps; the mixed
+    state after 10 steps against the oracle's (tests/golden/schnak2d_steps.npz)
+    and after 200 steps against the FP64 GPU path."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif, workloads
+    from paper_1810_11111_gb300.runner import Problem
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    cfg = workloads.schnak2d()
+    nsteps = cfg["steps"]
+    golden = os.path.join(ROOT, "tests", "golden", "schnak2d_steps.npz")
+    g = np.load(golden) if os.path.exists(golden) else None
+    out = {"workload": "schnak2d: u_t = 0.01 Lap u + 0.1 - u + u^2 v, v_t = 0.5 Lap v + 0.9 - u^2 v, periodic, "
+                       "level 8, degree 2, M 40, dt 0.05, %d IIF2 steps (GMRES)" % nsteps}
+    finals = {}
+    for name, prec in (("mixed", sgkiif.SGK_MIXED), ("fp64", sgkiif.SGK_FP64)):
+        prob = Problem(cfg, prec)
+        prob.reset()
+        prob.solver.step(1)  # graph capture of every phase
+        prob.reset()
+        prob.solver.step(10)
+        if g is not None:
+            want = g["U10"]
+            got = np.stack(prob.state())
+            out[name + "_rel_l2_vs_oracle_step10"] = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        prob.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        prob.solver.step(nsteps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        finals[name] = np.concatenate(prob.state())
+        st = prob.solver.stats()
+        out[name] = {"ms_per_step": ms / nsteps, "dof_steps_per_s": prob.dof * 2 * nsteps / (ms / 1e3),
+                     "newton_iters": st["newton_iters"], "inner_iters": st["inner_iters"]}
+        prob.close()
+    out["rel_l2_mixed_vs_fp64_after_%d_steps" % nsteps] = float(
+        np.linalg.norm(finals["mixed"] - finals["fp64"]) / np.linalg.norm(finals["fp64"]))
+    return out
+
+
 # ----------------------------------------------------------- matvec leg ---
 
 def matvec_leg(peaks, peak_kind):
@@ -528,6 +608,29 @@ def matvec_leg(peaks, peak_kind):
     return out
 
 
+# ------------------------------------------------------- conditioning ---
+
+def fp64_sensitivity(cfg, steps, seed=31):
+    """Relative change of the FP64 GPU result after `steps` IIF2 steps when
+    the initial state is perturbed by 1e-14 relative (seeded): how far
+    rounding at that level moves the answer of this instance."""
+    from paper_1810_11111_gb300 import sgkiif
+    from paper_1810_11111_gb300.runner import Problem
+    rng = np.random.default_rng(seed)
+    outs = []
+    for perturb in (False, True):
+        p = Problem(cfg, sgkiif.SGK_FP64)
+        p.reset()
+        if perturb:
+            for s_ in range(p.nspecies):
+                u = p.U0[s_].cpu().numpy()
+                p.solver.set_state(s_, u * (1.0 + 1e-14 * rng.standard_normal(u.shape)))
+        p.solver.step(steps)
+        outs.append(np.concatenate(p.state()))
+        p.close()
+    return float(np.linalg.norm(outs[1] - outs[0]) / max(np.linalg.norm(outs[0]), 1e-300))
+
+
 # ---------------------------------------------------------- batched leg ---
 
 def batched_leg(args, dist=None, rank=0, world=1):
@@ -556,21 +659,15 @@ def batched_leg(args, dist=None, rank=0, world=1):
     # batched Arnoldi launches (default) and, for comparison, every instance
     # in its own whole-step graph on the same 8 streams
     runs = ((8, sgkiif.SGK_MIXED, "mixed"), (8, sgkiif.SGK_MIXED, "mixed_per_instance_graphs"),
-            (8, sgkiif.SGK_FP64, "fp64"), (8, sgkiif.SGK_FP64, "fp64_perturbed"))
+            (8, sgkiif.SGK_FP64, "fp64"))
     if world > 1:
         runs = runs[:1]
-    rng = np.random.default_rng(31)
     # every run takes 1 + steps steps from the initial states: one untimed
     # (graph capture, first launches), then the timed ones
     for streams, prec, name in runs:
         b = sgkiif.Batch(0, streams=streams, fused=name != "mixed_per_instance_graphs")
-        for i, c in enumerate(insts):
-            if name == "fp64_perturbed":
-                b.add(c, prec, init_coeffs=[u * (1.0 + 1e-14 * rng.standard_normal(u.shape)) for u in u0s[i]])
-            else:
-                b.add(c, prec)
-        if name == "fp64":
-            u0s = [b.state(i) for i in range(len(insts))]
+        for c in insts:
+            b.add(c, prec)
         rc, _ = b.step(1)
         torch.cuda.synchronize()
         if dist is not None:
@@ -594,7 +691,11 @@ def batched_leg(args, dist=None, rank=0, world=1):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
     errs = np.array([rel(m, f) for m, f in zip(states["mixed"], states["fp64"])])
-    sens = np.array([rel(p, f) for p, f in zip(states["fp64_perturbed"], states["fp64"])])
+    # conditioning of the instances above the budget (each solved alone in
+    # FP64 from its initial state and from a 1e-14 perturbation of it)
+    sens = np.zeros(len(insts))
+    for i in np.nonzero(errs > 1e-6)[0]:
+        sens[i] = fp64_sensitivity(insts[i], 1 + steps)
     ill = sens > 1e-8
     well = ~ill
     return dict(workload="batch: %d scalar cubic instances (seed 3; d 2-4, level 5-8, degree 1-2, kappa_i ~ "
@@ -618,10 +719,11 @@ def batched_leg(args, dist=None, rank=0, world=1):
                                 "ill_conditioned": [{"instance": int(i), "rel_l2_mixed_vs_fp64": float(errs[i]),
                                                      "fp64_change_under_1e-14_input_perturbation": float(sens[i])}
                                                     for i in np.nonzero(ill)[0]],
-                                "note": "per instance after the timed steps; ill-conditioned = the FP64 result "
-                                        "itself moves by more than 1e-8 when the initial state is perturbed by "
-                                        "1e-14 relative (an M = 30 Krylov projection far from converged at "
-                                        "dt rho(A) ~ 1e4 amplifies rounding-level perturbations)"},
+                                "note": "per instance after the timed steps; every instance above 1e-6 is "
+                                        "solved again alone in FP64 from its initial state perturbed by 1e-14 "
+                                        "relative: ill-conditioned = the FP64 result itself moves by more than "
+                                        "1e-8 (an M = 30 Krylov projection far from converged at dt rho(A) ~ 1e4 "
+                                        "amplifies rounding-level perturbations)"},
                 timing="host wall clock around the batch steps (each step waits for every stream)")
 
 
@@ -670,42 +772,78 @@ def served_leg(args):
     srv.close()
     lat_m, wall_m = one_at_a_time(sgkiif.SGK_MIXED)
     mean_service_s = wall_m / len(reqs)
-    rate = 1.0 / mean_service_s  # offered load = the one-at-a-time capacity
-    arrivals = workloads.poisson_arrivals(len(reqs), rate, seed=4)
-    srv = sgkiif.Server(0, workers=args.served_workers)
-    t0 = time.perf_counter()
-    tickets = []
-    for r, ta in zip(reqs, arrivals):
-        delay = ta - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(srv.submit(r, sgkiif.SGK_MIXED))
-    lat, outs_served = [], []
-    for t, cap in zip(tickets, caps):
-        out, info = srv.wait(t, cap=cap)
-        lat.append(record(info))
-        outs_served.append(out)
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
+    capacity_rate = 1.0 / mean_service_s  # requests/s one at a time
+
+    def serve(rate):
+        """Requests arriving as a Poisson stream at `rate` per second (all at
+        t = 0 when rate is None); returns summary, outputs, server stats."""
+        arrivals = workloads.poisson_arrivals(len(reqs), rate, seed=4) if rate else [0.0] * len(reqs)
+        srv = sgkiif.Server(0, workers=args.served_workers)
+        t0 = time.perf_counter()
+        tickets = []
+        for r, ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(r, sgkiif.SGK_MIXED))
+        lat, outs = [], []
+        for t, cap in zip(tickets, caps):
+            out, info = srv.wait(t, cap=cap)
+            lat.append(record(info))
+            outs.append(out)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return summary(lat, wall), outs, st
+
+    rates = [float(x) for x in args.served_rates.split(",") if x.strip()]
+    by_rate = {}
+    outs_served = None
+    for r_mult in rates:
+        summ, outs, st = serve(r_mult * capacity_rate)
+        by_rate["%gx" % r_mult] = dict(summ, rate_per_s=r_mult * capacity_rate, max_concurrent=st["max_concurrent"],
+                                       peak_reserved_gb=st["peak_reserved_bytes"] / 1e9)
+        if outs_served is None:
+            outs_served = outs
+    sat, outs_sat, st_sat = serve(None)
     outs64 = []
     lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64)
-    err = max(float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
-              for m, f in zip(outs_served, outs64) if m.size and f.size)
-    served = summary(lat, wall)
+
+    def rel(m, f):
+        return float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
+
+    errs = [rel(m, f) for m, f in zip(outs_sat, outs64) if m.size and f.size]
+    over = [i for i, e in enumerate(errs) if e > 1e-6]
+    ill = [{"request": i, "rel_l2_mixed_vs_fp64": errs[i],
+            "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(reqs[i], reqs[i]["steps"])}
+           for i in over]
+    first = by_rate["%gx" % rates[0]] if rates else sat
     base64 = summary(lat64, wall64)
-    return dict(served,
+    mixed1 = summary(lat_m, wall_m)
+    return dict(first,
                 workload="served: %d requests (seed 4; d 3-4, level 6-9, degree 1-3, cubic or Schnakenberg, "
                          "10-100 IIF2 steps, M 30, dt 0.005; draws above 512 MB of finest-grid FP64 nodal "
                          "values rejected: %d of %d)" % (len(reqs), rejected, len(reqs) + rejected),
                 precision="mixed", workers=args.served_workers, arrival="poisson",
-                rate_per_s=rate, offered_load="one-at-a-time mixed capacity",
-                max_concurrent=st["max_concurrent"], peak_reserved_gb=st["peak_reserved_bytes"] / 1e9,
-                one_at_a_time_mixed=summary(lat_m, wall_m),
+                offered_load="multiples of the one-at-a-time mixed capacity (%.3f requests/s)" % capacity_rate,
+                by_rate=by_rate,
+                saturation=dict(sat, note="every request submitted at t = 0: the server's capacity",
+                                max_concurrent=st_sat["max_concurrent"]),
+                one_at_a_time_mixed=mixed1,
                 one_at_a_time_fp64=base64,
-                speedup_vs_fp64_one_at_a_time=served["dof_steps_per_s"] / base64["dof_steps_per_s"],
+                speedup_vs_fp64_one_at_a_time=first["dof_steps_per_s"] / base64["dof_steps_per_s"],
+                saturation_vs_one_at_a_time_mixed=sat["dof_steps_per_s"] / mixed1["dof_steps_per_s"],
                 failed_requests=len(failures), first_failure=failures[0] if failures else None,
-                max_rel_l2_vs_fp64=err)
+                max_rel_l2_vs_fp64=max(errs) if errs else None,
+                above_1e_6=len(over),
+                max_rel_l2_vs_fp64_well_conditioned=max([e for i, e in enumerate(errs)
+                                                        if not any(x["request"] == i and
+                                                                   x["fp64_change_under_1e-14_input_perturbation"]
+                                                                   > 1e-8 for x in ill)], default=None),
+                conditioning_of_requests_above_1e_6=ill,
+                note="mixed results of the saturation run against the FP64 one-at-a-time results; a request "
+                     "whose FP64 result moves by more than 1e-8 under a 1e-14 input perturbation is "
+                     "ill-conditioned at this precision")
 
 
 # --------------------------------------------------------- oracle timing ---

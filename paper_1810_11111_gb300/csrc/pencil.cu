@@ -60,19 +60,46 @@ struct Poly {
 template <typename T, int S, bool JAC>
 struct PointEval;
 
+template <typename T>
+__device__ __forceinline__ bool is_zero(const T& v) {
+    return v == T(0);
+}
+template <>
+__device__ __forceinline__ bool is_zero<dfloat>(const dfloat& v) {
+    return v.hi == 0.0f && v.lo == 0.0f;
+}
+
+// Horner's rule that skips the zero coefficients (the reactions are sparse
+// polynomials, e.g. -c u^3): the tests are on kernel parameters, uniform
+// over the grid, and adding an exact zero is exact, so the value is bitwise
+// that of the dense rule
+template <typename T>
+__device__ __forceinline__ T horner_sparse(const T (&c)[PDEG], const T& u) {
+    T f = T(0);
+    bool started = false;
+#pragma unroll
+    for (int e = PDEG - 1; e >= 0; --e) {
+        if (started) f = f * u;
+        if (!is_zero(c[e])) {
+            f = started ? f + c[e] : c[e];
+            started = true;
+        }
+    }
+    return f;
+}
+
 template <typename T, bool JAC>
 struct PointEval<T, 1, JAC> {
     __device__ __forceinline__ static void run(const Poly<T, 1>& P, const T (&u)[1], const T (&w)[1], T (&o)[1]) {
         if (!JAC) {
-            T f = P.c[0][PDEG - 1];
-#pragma unroll
-            for (int e = PDEG - 2; e >= 0; --e) f = f * u[0] + P.c[0][e];
-            o[0] = f;
+            o[0] = horner_sparse<T>(P.c[0], u[0]);
         } else {
-            T df = T(PDEG - 1) * P.c[0][PDEG - 1];
+            // f'(u) = sum_{e >= 1} e c_e u^{e-1}
+            T dc[PDEG];
 #pragma unroll
-            for (int e = PDEG - 2; e >= 1; --e) df = df * u[0] + T(e) * P.c[0][e];
-            o[0] = df * w[0];
+            for (int e = 0; e + 1 < PDEG; ++e) dc[e] = T(e + 1) * P.c[0][e + 1];
+            dc[PDEG - 1] = T(0);
+            o[0] = horner_sparse<T>(dc, u[0]) * w[0];
         }
     }
 };

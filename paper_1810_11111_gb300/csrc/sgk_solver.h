@@ -67,7 +67,7 @@ struct sgk_solver {
     // GMRES (systems)
     DevBuf<double> gm_V, gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_report;
     bool use_graphs = true;
-    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_cg;
+    GraphCache g_krylov[SGK_MAX_SPECIES], g_pred, g_pred_f, g_resid, g_resid0, g_cg;
     GraphCache g_krylovh[SGK_MAX_SPECIES][SGK_IIF_MAX_ORDER - 2];  // the history projections of IIFr
     // Fv holds F(U) for the current U (a host-driven or device-driven step
     // ended with an accepted residual evaluation there); cleared whenever U

@@ -60,13 +60,16 @@ __device__ __forceinline__ void newton_init(StepCtl* c, double wnorm, double tol
 }
 
 // returns 1 to take another Newton correction
-__device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_iter) {
+// first_low: this evaluation's F ran in FP32 (the first residual of a mixed
+// step, which only seeds the first correction): it never accepts
+__device__ __forceinline__ unsigned newton_decide(StepCtl* c, double g, int max_iter, int first_low) {
     c->last_g = g;
     // the stop is relative to the stage's scale, max(||W||, ||G(W)||), fixed
     // at the first evaluation (U = W)
     if (c->it == 0) c->stop = c->tol * fmax(c->wnorm, g);
     unsigned go = 0;
     if (!isfinite(g)) c->status = SGK_ENEWTON;
+    else if (first_low && c->it == 0) go = 1;
     else if (g <= c->stop) c->status = SGK_OK;
     else if (c->it >= max_iter) c->status = SGK_ENEWTON;
     else go = 1;
@@ -199,7 +202,7 @@ __global__ void norm_init_kernel(const double* __restrict__ W, long long n, doub
 __global__ void residual_norm_kernel(const double* __restrict__ U, const double* __restrict__ F,
                                      const double* __restrict__ W, double c, double* __restrict__ G, long long n,
                                      double* partials, unsigned* cnt, double* out, StepCtl* ctl,
-                                     cudaGraphConditionalHandle h, int max_iter) {
+                                     cudaGraphConditionalHandle h, int max_iter, int first_low) {
     double acc = 0.0;
     SGK_GRID_STRIDE(i, n) {
         const double g = U[i] - c * F[i] - W[i];
@@ -209,7 +212,7 @@ __global__ void residual_norm_kernel(const double* __restrict__ U, const double*
     finish_sum(acc, partials, cnt, [&](double t) {
         const double g = sqrt(t);
         *out = g;
-        if (ctl) cudaGraphSetConditional(h, newton_decide(ctl, g, max_iter));
+        if (ctl) cudaGraphSetConditional(h, newton_decide(ctl, g, max_iter, first_low));
     });
 }
 
@@ -486,9 +489,24 @@ bool df_reaction(const sgk_solver* s) { return s->prec == SGK_MIXED && s->Q.fuse
 
 // F(U, t^n + toff): the reaction passes (about 1e-14 relative accuracy in
 // both precision modes), then the source terms in FP64
-void evalF(sgk_solver* s, const double* U, double* F, double toff) {
-    if (df_reaction(s)) evalF_df(s, U, F);
-    else evalF_T<double>(s, U, F);
+//
+// In mixed mode the FP32 Jacobian passes that follow read an FP32 copy of
+// the transformed U, made here.  lo: a mixed-mode F that only seeds a
+// Newton correction and never decides acceptance runs in FP32 (and leaves
+// its FP32 transform for the Jacobian passes directly).
+void evalF(sgk_solver* s, const double* U, double* F, double toff, bool lo = false) {
+    if (lo && s->prec == SGK_MIXED) {
+        evalF_T<float>(s, U, F);
+    } else if (df_reaction(s)) {
+        evalF_df(s, U, F);
+    } else {
+        evalF_T<double>(s, U, F);
+    }
+    if (s->prec == SGK_MIXED && !lo) {
+        const long long m = (long long)s->nspecies * s->Q.full_size;
+        if (df_reaction(s)) vk_convert(s->ctx, reinterpret_cast<const dfloat*>(s->q64.p), s->q32.p, m);
+        else vk_convert(s->ctx, s->q64.p, s->q32.p, m);
+    }
     if (!s->has_src) return;
     const long long n = s->n;
     for (int sp = 0; sp < s->nspecies; ++sp) {
@@ -512,7 +530,8 @@ void write_time(sgk_solver* s) {
 
 // destroys every cached graph (they are captured again on next use)
 void drop_graphs(sgk_solver* s) {
-    for (GraphCache* g : {&s->g_step, &s->g_pre, &s->g_post, &s->g_pred, &s->g_pred_f, &s->g_resid, &s->g_cg}) {
+    for (GraphCache* g :
+         {&s->g_step, &s->g_pre, &s->g_post, &s->g_pred, &s->g_pred_f, &s->g_resid, &s->g_resid0, &s->g_cg}) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         *g = GraphCache{};
     }
@@ -524,16 +543,6 @@ void drop_graphs(sgk_solver* s) {
             g = GraphCache{};
         }
     }
-}
-
-// Before the Jacobian products of an inner solve: in mixed mode the FP32
-// passes read an FP32 copy of the transformed U that the last F evaluation
-// (FP64, at the same U) left in the FP64 buffers.
-void jac_prepare(sgk_solver* s) {
-    if (s->prec != SGK_MIXED) return;
-    const long long m = (long long)s->nspecies * s->Q.full_size;
-    if (df_reaction(s)) vk_convert(s->ctx, reinterpret_cast<const dfloat*>(s->q64.p), s->q32.p, m);
-    else vk_convert(s->ctx, s->q64.p, s->q32.p, m);
 }
 
 // q = p - dt/2 J_F(U) p (stacked FP64); with pq also pq = p.q
@@ -663,20 +672,23 @@ int newton(sgk_solver* s) {
                  s->scal.p + 6, (StepCtl*)nullptr, 0.0);
     const double wnorm = read_scalar(s, s->scal.p + 6);
     double stop = 0.0;  // relative to max(||W||, ||G(W)||), set at the first evaluation
+    // mixed mode: the first residual (at W) runs in FP32 and only seeds the
+    // first correction; every residual that can accept runs accurately
+    const bool first_low = s->prec == SGK_MIXED;
     for (int it = 0; it <= s->opts.max_iter; ++it) {
-        run_graph(s, s->g_resid, KC_VECTOR, [&]() {
-            evalF(s, s->U.p, s->Fv.p, s->dt);
+        const bool lo = first_low && it == 0;
+        run_graph(s, lo ? s->g_resid0 : s->g_resid, KC_VECTOR, [&]() {
+            evalF(s, s->U.p, s->Fv.p, s->dt, lo);
             launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                          (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID, s->scal.p + 7,
-                         (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0);
+                         (StepCtl*)nullptr, cudaGraphConditionalHandle{}, 0, 0);
         });
         const double g = read_scalar(s, s->scal.p + 7);
         s->stats.last_newton_residual = g;
         if (!std::isfinite(g)) break;
         if (it == 0) stop = s->opts.tol * std::max(wnorm, g);
-        if (g <= stop) return SGK_OK;
+        if (!lo && g <= stop) return SGK_OK;
         if (it == s->opts.max_iter) break;
-        jac_prepare(s);
         int inner = 0;
         if (s->nspecies == 1) cg_solve(s, s->G.p, s->cg_x.p, inner);
         else gmres_solve_host(s, s->G.p, s->cg_x.p, inner);
@@ -864,24 +876,21 @@ void build_step_graph(sgk_solver* s, int part = STEP_WHOLE) {
             double* const pq = s->scal.p + 4;
             launch_fused(s, N, "norm", norm_init_kernel, (const double*)s->W.p, N, s->partials.p,
                          s->fcnt.p + FC_NORM, s->scal.p + 6, ctl, s->opts.tol);
-            auto resid = [&](cudaGraphConditionalHandle h) {
-                evalF(s, s->U.p, s->Fv.p, s->dt);
+            // mixed mode: the first residual (at W) in FP32, never accepting
+            const int first_low = s->prec == SGK_MIXED ? 1 : 0;
+            auto resid = [&](cudaGraphConditionalHandle h, bool lo) {
+                evalF(s, s->U.p, s->Fv.p, s->dt, lo);
                 launch_fused(s, N, "residual", residual_norm_kernel, (const double*)s->U.p, (const double*)s->Fv.p,
                              (const double*)s->W.p, dt2, s->G.p, N, s->partials.p, s->fcnt.p + FC_RESID,
-                             s->scal.p + 7, ctl, h, s->opts.max_iter);
+                             s->scal.p + 7, ctl, h, s->opts.max_iter, lo ? first_low : 0);
             };
             int64_t mark = 0;
             capture_while(
                 ctx, s->aux[0],
-                [&](cudaGraphConditionalHandle h) {
-                    mark = ctx->launches;
-                    resid(h);
-                    s->n_resid = ctx->launches - mark;
-                },
+                [&](cudaGraphConditionalHandle h) { resid(h, first_low != 0); },
                 [&](cudaGraphConditionalHandle hn) {
                     s->n_prefix = ctx->launches - before;
                     mark = ctx->launches;
-                    jac_prepare(s);
                     double* x = s->cg_x.p;
                     double* r = s->cg_r.p;
                     double* pv = s->cg_p.p;
@@ -909,7 +918,9 @@ void build_step_graph(sgk_solver* s, int part = STEP_WHOLE) {
                     launch_fused(s, N, "newton_step", newton_step_kernel, s->U.p, (const double*)x, N,
                                  s->fcnt.p + FC_STEP, ctl);
                     s->n_adv = ctx->launches - mark;
-                    resid(hn);
+                    mark = ctx->launches;
+                    resid(hn, false);
+                    s->n_resid = ctx->launches - mark;
                 });
         } else {
             s->n_prefix = ctx->launches - before;
@@ -1388,10 +1399,9 @@ void solver_alloc(sgk_solver* s) {
 
 sgk_solver::~sgk_solver() {
     if (hrec) cudaFreeHost(hrec);
-    if (g_step.exec) cudaGraphExecDestroy(g_step.exec);
     for (cudaStream_t& a : aux)
         if (a) cudaStreamDestroy(a);
-    for (GraphCache* g : {&g_pred, &g_pred_f, &g_resid, &g_cg})
+    for (GraphCache* g : {&g_step, &g_pre, &g_post, &g_pred, &g_pred_f, &g_resid, &g_resid0, &g_cg})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     for (auto& gs : g_krylovh)
         for (auto& g : gs)
