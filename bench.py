@@ -134,13 +134,14 @@ def layout_sizes(d, n, k):
 
 # DRAM bytes (read + write) of one launch from the committed ncu captures of
 # the current kernels (cold, L2 flushed by ncu before the launch); a key is
-# removed when the kernel changes.  Jacobian pencil launch, keyed by (d,
-# level, degree, precision): profiles/pencil_kernel_cubic3d_l6k2_fp32.md
-PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56661504 + 58112}
+# removed when the kernel changes.  Double-float F pencil launch (the
+# dominant kernel of the cell-quadrature class in mixed mode), keyed by (d,
+# level, degree, precision): profiles/pencil_kernel_cubic3d_l6k2_dfloat.md
+PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 56773376 + 11996160}
 # one persistent Arnoldi launch (one exponential), keyed by (d, level,
 # degree, M, precision): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md (the
 # mixed-precision variant, double-float gather)
-ARNOLDI_TRAFFIC = {(3, 6, 2, 30, "mixed"): 6503168 + 59392}
+ARNOLDI_TRAFFIC = {(3, 6, 2, 30, "mixed"): 6501120 + 49664}
 
 
 def pencil_q(cfg):
@@ -420,8 +421,8 @@ def native(args, rank, world, local_rank):
                             hbm_view={"achieved_gbs": bytes_algo / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
                                       "frac": bytes_algo / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_kind},
                             traffic=PENCIL_TRAFFIC.get((d, N, cfg["k"], args.precision)),
-                            traffic_note="dram read + write of one Jacobian launch, ncu cold capture "
-                                         "(profiles/pencil_kernel_cubic3d_l6k2_fp32.md); null when no capture "
+                            traffic_note="dram read + write of one double-float F launch, ncu cold capture "
+                                         "(profiles/pencil_kernel_cubic3d_l6k2_dfloat.md); null when no capture "
                                          "of the current kernel exists")
         else:
             achieved = bytes_algo / t / 1e9
@@ -731,8 +732,10 @@ def batched_leg(args, dist=None, rank=0, world=1):
 
 def served_leg(args):
     """Poisson stream of whole solve requests through the request server
-    (continuous batching over worker streams, memory admission), against the
-    same requests one at a time.  Latency is submit -> result on the host,
+    (the engine batches the single-species requests step by step on the
+    batched Arnoldi launches, workers take the systems; memory admission),
+    at each arrival rate of --served-rates and all at once (saturation),
+    against the same requests one at a time.  Latency is submit -> result on the host,
     measured by the server; throughput counts DOF x species x steps of all
     requests over first submission -> last completion."""
     from paper_1810_11111_gb300 import sgkiif, workloads
@@ -774,11 +777,11 @@ def served_leg(args):
     mean_service_s = wall_m / len(reqs)
     capacity_rate = 1.0 / mean_service_s  # requests/s one at a time
 
-    def serve(rate):
+    def serve(rate, engine=True):
         """Requests arriving as a Poisson stream at `rate` per second (all at
         t = 0 when rate is None); returns summary, outputs, server stats."""
         arrivals = workloads.poisson_arrivals(len(reqs), rate, seed=4) if rate else [0.0] * len(reqs)
-        srv = sgkiif.Server(0, workers=args.served_workers)
+        srv = sgkiif.Server(0, workers=args.served_workers, engine=engine)
         t0 = time.perf_counter()
         tickets = []
         for r, ta in zip(reqs, arrivals):
@@ -806,6 +809,7 @@ def served_leg(args):
         if outs_served is None:
             outs_served = outs
     sat, outs_sat, st_sat = serve(None)
+    sat_workers, _, _ = serve(None, engine=False)
     outs64 = []
     lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64)
 
@@ -829,6 +833,8 @@ def served_leg(args):
                 by_rate=by_rate,
                 saturation=dict(sat, note="every request submitted at t = 0: the server's capacity",
                                 max_concurrent=st_sat["max_concurrent"]),
+                saturation_workers_only=dict(sat_workers, note="the same with the engine off: every request "
+                                                               "on a worker thread"),
                 one_at_a_time_mixed=mixed1,
                 one_at_a_time_fp64=base64,
                 speedup_vs_fp64_one_at_a_time=first["dof_steps_per_s"] / base64["dof_steps_per_s"],

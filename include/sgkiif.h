@@ -397,17 +397,20 @@ int sgk_expm_e1_noalloc(int m, const double* X_dev, double tau, double* y_dev, v
  * the scheme of eq. krylov5, one per request) as they arrive.  The paper has
  * no counterpart; this is the service around the method.
  *
- * Continuous batching: a server owns nworkers worker threads, each with its
- * own CUDA stream on one device.  A submitted request waits in a queue until
- * a worker is idle and its estimated device memory (sgk_estimate_bytes) fits
- * in what the admitted requests leave of the budget; requests are admitted in
- * arrival order, except that a request that does not fit yet lets later ones
- * that do fit go first unless it has waited longer than the aging limit.
- * Admitted requests run concurrently, their kernels overlapping on the GPU;
- * each keeps its Krylov basis and state on the device until it finishes, and
- * its memory returns to the budget when it does.  Results do not depend on
- * what else runs: a request gives the same coefficients alone and in a mix
- * on a server with the same worker count. */
+ * Continuous batching: a server owns an engine thread (see
+ * sgk_server_set_engine) and nworkers worker threads, each with its own CUDA
+ * stream on one device.  A submitted request waits in a queue until the
+ * engine has room (single-species requests) or a worker is idle (the others),
+ * and its estimated device memory (sgk_estimate_bytes) fits in what the
+ * admitted requests leave of the budget; requests are admitted in arrival
+ * order, except that a request that does not fit yet lets later ones that do
+ * fit go first unless it has waited longer than the aging limit.  Admitted
+ * requests run concurrently: the engine's requests step together in batched
+ * launches, the workers' kernels overlap with them on the GPU; each keeps
+ * its Krylov basis and state on the device until it finishes, and its memory
+ * returns to the budget when it does.  Results do not depend on what else
+ * runs: a request gives the same coefficients alone and in a mix on a server
+ * with the same worker count and engine setting. */
 typedef struct sgk_server sgk_server;
 
 /* Initial data of one species: coefficients (host, dof doubles) if coeffs is
@@ -484,6 +487,19 @@ int sgk_partition(int count, const double* cost, int nparts, int* part_of);
  * aging_ms: how long a request that does not fit may be overtaken (<= 0:
  * 2000 ms).  Errors: SGK_EINVAL, SGK_ECUDA, SGK_ENOMEM. */
 int sgk_server_create(int device, int nworkers, int64_t mem_budget_bytes, double aging_ms, sgk_server** out);
+/* The server's engine (on by default): single-species requests with d in
+ * 2..4 are not given to a worker but join a running batch, stepped one IIF2
+ * step per tick for all of its requests together (iteration-level
+ * continuous batching): per request a pre-Krylov CUDA graph, then one
+ * persistent cooperative Arnoldi launch per kernel class for all of them
+ * (as sgk_batch), then per request a post-Krylov graph with the Newton
+ * solve.  Requests join between ticks once admitted (same memory rule) and
+ * leave after their last step; their result info reports worker -1.
+ * Systems (host-driven GMRES) stay with the workers.  on = 0 sends every
+ * request to the workers; max_requests > 0 caps the requests in the engine
+ * at once (default 64).  Takes effect for requests admitted after the call.
+ * Errors: SGK_EINVAL. */
+int sgk_server_set_engine(sgk_server* srv, int on, int max_requests);
 /* Queue a request; every host array it points to is copied before the call
  * returns.  *ticket identifies it.  Errors: SGK_EINVAL (bad request),
  * SGK_ENOMEM (its estimate exceeds the whole budget: rejected). */

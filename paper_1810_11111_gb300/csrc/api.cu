@@ -1,6 +1,7 @@
 // C ABI of libsgkiif (declared and documented in include/sgkiif.h).  Every
 // entry point catches errors and turns them into a status code; the message
 // is kept on the context.
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -442,6 +443,8 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
         }
         set_device(ctx);
         std::unique_ptr<sgk_solver> s(new sgk_solver());
+        static std::atomic<uint64_t> next_uid{1};
+        s->uid = next_uid.fetch_add(1);
         s->ctx = ctx;
         s->idx = idx;
         s->nspecies = nspecies;

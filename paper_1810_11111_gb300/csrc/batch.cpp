@@ -24,6 +24,7 @@
 
 #include "sgk_internal.h"
 #include "sgk_quad.h"
+#include "sgk_batchcore.h"
 #include "sgk_krylov.h"
 #include "sgk_solver.h"
 
@@ -47,30 +48,101 @@ struct Instance {
 
 }  // namespace
 
+BatchCore::~BatchCore() {
+    arnoldi_batch_free(plan);
+    for (cudaStream_t st : streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (evb) cudaEventDestroy(evb);
+    if (bstream) cudaStreamDestroy(bstream);
+}
+
+int BatchCore::init(int dev, int nstreams) {
+    device = dev;
+    for (int i = 0; i < nstreams; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (st) cudaStreamDestroy(st);
+            return SGK_ECUDA;
+        }
+        streams.push_back(st);
+        ev.push_back(e);
+    }
+    int optin = 0;
+    if (cudaStreamCreateWithFlags(&bstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evb, cudaEventDisableTiming) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SGK_ECUDA;
+    }
+    smem_optin = (size_t)optin;
+    return SGK_OK;
+}
+
+void batch_core_tick(BatchCore& core, const std::vector<sgk_solver*>& sols, std::vector<int>& status) {
+    status.assign(sols.size(), SGK_OK);
+    // the split solvers share the batched Arnoldi launches; the plan is
+    // rebuilt when that set changes
+    std::vector<sgk_solver*> split;
+    std::vector<uint64_t> split_uid;
+    std::vector<int> split_idx, queued;
+    if (core.fused)
+        for (size_t i = 0; i < sols.size(); ++i)
+            if (solver_split_eligible(sols[i]) && arnoldi_batch_supports(solver_arnoldi_job(sols[i]))) {
+                split.push_back(sols[i]);
+                split_uid.push_back(sols[i]->uid);
+                split_idx.push_back((int)i);
+            }
+    if (split_uid != core.plan_set) {
+        arnoldi_batch_free(core.plan);
+        core.plan = nullptr;
+        core.plan_set.clear();
+        if (!split.empty()) {
+            std::vector<ArnJob> jobs;
+            for (sgk_solver* s : split) jobs.push_back(solver_arnoldi_job(s));
+            core.plan = arnoldi_batch_plan(jobs, core.num_sms, core.smem_optin, core.bstream);
+            core.plan_set = split_uid;
+        }
+    }
+    if (!split.empty()) {
+        for (sgk_solver* s : split) solver_step_launch_pre(s);
+        for (size_t i = 0; i < core.streams.size(); ++i) {
+            SGK_CUDA_CHECK(cudaEventRecord(core.ev[i], core.streams[i]));
+            SGK_CUDA_CHECK(cudaStreamWaitEvent(core.bstream, core.ev[i], 0));
+        }
+        core.launches += arnoldi_batch_launch(core.plan, core.bstream);
+        SGK_CUDA_CHECK(cudaEventRecord(core.evb, core.bstream));
+        for (cudaStream_t st : core.streams) SGK_CUDA_CHECK(cudaStreamWaitEvent(st, core.evb, 0));
+        for (size_t k = 0; k < split.size(); ++k) {
+            solver_step_launch_post(split[k]);
+            queued.push_back(split_idx[k]);
+        }
+    }
+    // the other device-driven steps, whole
+    for (size_t i = 0; i < sols.size(); ++i) {
+        if (std::find(split_idx.begin(), split_idx.end(), (int)i) != split_idx.end()) continue;
+        if (solver_device_steps(sols[i])) {
+            solver_step_launch(sols[i]);
+            queued.push_back((int)i);
+        }
+    }
+    for (cudaStream_t st : core.streams) SGK_CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int i : queued) status[i] = solver_step_finish(sols[i]);
+    for (size_t i = 0; i < sols.size(); ++i)
+        if (!solver_device_steps(sols[i])) status[i] = sgk_solver_step(sols[i], 1);
+}
+
 struct sgk_batch {
     int device = 0;
     int slice_len = 384;
-    bool fused = true;  // batched Arnoldi launches (else whole-step graphs per instance)
-    std::vector<cudaStream_t> streams;
-    cudaStream_t bstream = nullptr;  // the batched Arnoldi launches
-    std::vector<cudaEvent_t> ev;     // one per stream, joins them into bstream
-    cudaEvent_t evb = nullptr;       // forks bstream back to the streams
-    int num_sms = 0;
-    size_t smem_optin = 0;
+    BatchCore core;
     std::vector<std::unique_ptr<Instance>> inst;
-    ArnBatchPlan* plan = nullptr;
-    std::vector<Instance*> plan_set;  // instances of the plan, in job order
-    int64_t batched_launches = 0;
-    ~sgk_batch() {
-        arnoldi_batch_free(plan);
-        inst.clear();
-        for (cudaStream_t s : streams)
-            if (s) cudaStreamDestroy(s);
-        for (cudaEvent_t e : ev)
-            if (e) cudaEventDestroy(e);
-        if (evb) cudaEventDestroy(evb);
-        if (bstream) cudaStreamDestroy(bstream);
-    }
+    ~sgk_batch() { inst.clear(); }
 };
 
 extern "C" {
@@ -87,26 +159,8 @@ int sgk_batch_create(int device, int nstreams, int slice_len, sgk_batch** out) {
     if (!b) return SGK_ENOMEM;
     b->device = device;
     if (slice_len > 0) b->slice_len = slice_len;
-    for (int i = 0; i < nstreams; ++i) {
-        cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return SGK_ECUDA;
-        }
-        b->streams.push_back(s);
-        b->ev.push_back(e);
-    }
-    int optin = 0;
-    if (cudaStreamCreateWithFlags(&b->bstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->evb, cudaEventDisableTiming) != cudaSuccess ||
-        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return SGK_ECUDA;
-    }
-    b->smem_optin = (size_t)optin;
+    const int rc = b->core.init(device, nstreams);
+    if (rc != SGK_OK) return rc;
     *out = b.release();
     return SGK_OK;
 }
@@ -119,8 +173,8 @@ int sgk_batch_add(sgk_batch* b, const sgk_request* q, int* index) {
     std::unique_ptr<Instance> in(new (std::nothrow) Instance());
     if (!in) return SGK_ENOMEM;
     in->S = S;
-    in->stream = (int)(b->inst.size() % b->streams.size());
-    int rc = sgk_ctx_create(&in->ctx, b->device, b->streams[in->stream], q->precision);
+    in->stream = (int)(b->inst.size() % b->core.streams.size());
+    int rc = sgk_ctx_create(&in->ctx, b->device, b->core.streams[in->stream], q->precision);
     if (rc != SGK_OK) return rc;
     rc = sgk_index_build(in->ctx, q->d, q->n, q->k, &in->idx);
     if (rc != SGK_OK) return rc;
@@ -157,11 +211,11 @@ int sgk_batch_add(sgk_batch* b, const sgk_request* q, int* index) {
 
 int sgk_batch_set_fused(sgk_batch* b, int on) {
     if (!b) return SGK_EINVAL;
-    b->fused = on != 0;
+    b->core.fused = on != 0;
     return SGK_OK;
 }
 
-int64_t sgk_batch_launches(const sgk_batch* b) { return b ? b->batched_launches : -1; }
+int64_t sgk_batch_launches(const sgk_batch* b) { return b ? b->core.launches : -1; }
 
 int sgk_batch_step(sgk_batch* b, int nsteps, int* status) {
     if (!b || nsteps < 0) return SGK_EINVAL;
@@ -169,51 +223,17 @@ int sgk_batch_step(sgk_batch* b, int nsteps, int* status) {
     int first = SGK_OK;
     try {
         for (int step = 0; step < nsteps; ++step) {
-            // the split instances share the batched Arnoldi launches; the
-            // plan is rebuilt when that set changes (an instance failed)
-            std::vector<Instance*> split, queued;
-            if (b->fused)
-                for (auto& in : b->inst)
-                    if (in->status == SGK_OK && solver_split_eligible(in->sol) &&
-                        arnoldi_batch_supports(solver_arnoldi_job(in->sol)))
-                        split.push_back(in.get());
-            if (split != b->plan_set) {
-                arnoldi_batch_free(b->plan);
-                b->plan = nullptr;
-                b->plan_set.clear();
-                if (!split.empty()) {
-                    std::vector<ArnJob> jobs;
-                    for (Instance* in : split) jobs.push_back(solver_arnoldi_job(in->sol));
-                    b->plan = arnoldi_batch_plan(jobs, b->num_sms, b->smem_optin, b->bstream);
-                    b->plan_set = split;
-                }
-            }
-            if (!split.empty()) {
-                for (Instance* in : split) solver_step_launch_pre(in->sol);
-                for (size_t i = 0; i < b->streams.size(); ++i) {
-                    SGK_CUDA_CHECK(cudaEventRecord(b->ev[i], b->streams[i]));
-                    SGK_CUDA_CHECK(cudaStreamWaitEvent(b->bstream, b->ev[i], 0));
-                }
-                b->batched_launches += arnoldi_batch_launch(b->plan, b->bstream);
-                SGK_CUDA_CHECK(cudaEventRecord(b->evb, b->bstream));
-                for (cudaStream_t s : b->streams) SGK_CUDA_CHECK(cudaStreamWaitEvent(s, b->evb, 0));
-                for (Instance* in : split) {
-                    solver_step_launch_post(in->sol);
-                    queued.push_back(in);
-                }
-            }
-            // the other device-driven steps, whole
-            for (auto& in : b->inst) {
-                if (in->status != SGK_OK || std::find(split.begin(), split.end(), in.get()) != split.end()) continue;
-                if (solver_device_steps(in->sol)) {
-                    solver_step_launch(in->sol);
-                    queued.push_back(in.get());
-                }
-            }
-            for (cudaStream_t s : b->streams) SGK_CUDA_CHECK(cudaStreamSynchronize(s));
-            for (Instance* in : queued) in->status = solver_step_finish(in->sol);
+            std::vector<sgk_solver*> sols;
+            std::vector<Instance*> act;
             for (auto& in : b->inst)
-                if (in->status == SGK_OK && !solver_device_steps(in->sol)) in->status = sgk_solver_step(in->sol, 1);
+                if (in->status == SGK_OK) {
+                    sols.push_back(in->sol);
+                    act.push_back(in.get());
+                }
+            if (sols.empty()) break;
+            std::vector<int> st;
+            batch_core_tick(b->core, sols, st);
+            for (size_t i = 0; i < act.size(); ++i) act[i]->status = st[i];
         }
     } catch (const SgkError& e) {
         return e.code;

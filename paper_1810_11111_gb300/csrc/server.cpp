@@ -29,6 +29,7 @@
 
 #include <cuda_runtime.h>
 
+#include "sgk_batchcore.h"
 #include "sgk_internal.h"
 #include "sgk_quad.h"
 
@@ -135,34 +136,76 @@ struct sgk_server {
     int64_t reserved = 0, peak_reserved = 0;
     int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
     int running = 0, max_concurrent = 0;
+    // the engine: single-species requests (d 2..4) stepped together, one
+    // batch step of all of them per tick (batch_core_tick), joining and
+    // leaving at tick boundaries
+    bool engine_on = true;
+    int eng_max = 64;                           // most requests in the engine at once
+    std::deque<std::shared_ptr<Req>> eng_new;   // admitted, not yet set up
+    int eng_count = 0;                          // admitted to the engine and not finished
+    std::condition_variable cv_eng;
+    std::thread eng_thread;
 
-    // under mu: assign queued requests to idle workers
+    static bool engine_eligible(const Req& r) { return r.S == 1 && r.d >= 2 && r.d <= 4; }
+
+    // under mu: admit queued requests in arrival order, each to the engine
+    // (when eligible and it has room) or to an idle worker, while its
+    // memory estimate fits what the running requests leave of the budget;
+    // a request that does not fit is overtaken by later ones until it has
+    // waited past the aging limit, after which it blocks everything behind it
     void admit_locked() {
         const auto now = Clock::now();
-        for (int w = 0; w < nworkers; ++w) {
-            if (slot[w]) continue;
-            std::shared_ptr<Req> pick;
-            for (auto it = queue.begin(); it != queue.end(); ++it) {
-                if (reserved + (*it)->est <= budget) {
-                    pick = *it;
-                    queue.erase(it);
-                    break;
+        for (auto it = queue.begin(); it != queue.end();) {
+            const std::shared_ptr<Req> r = *it;
+            const bool fits = reserved + r->est <= budget;
+            const bool eng = engine_on && engine_eligible(*r);
+            int w = -1;
+            if (!eng)
+                for (int i = 0; i < nworkers && w < 0; ++i)
+                    if (!slot[i]) w = i;
+            const bool room = eng ? eng_count < eng_max : w >= 0;
+            if (fits && room) {
+                it = queue.erase(it);
+                r->t_admit = now;
+                reserved += r->est;
+                peak_reserved = std::max(peak_reserved, reserved);
+                ++running;
+                max_concurrent = std::max(max_concurrent, running);
+                if (eng) {
+                    eng_new.push_back(r);
+                    ++eng_count;
+                } else {
+                    slot[w] = r;
                 }
-                // an aged request that does not fit blocks everything behind it
-                if (ms_between((*it)->t_submit, now) > aging_ms) break;
+                continue;
             }
-            if (!pick) break;
-            pick->t_admit = now;
-            reserved += pick->est;
-            peak_reserved = std::max(peak_reserved, reserved);
-            slot[w] = pick;
-            ++running;
-            max_concurrent = std::max(max_concurrent, running);
+            if (!fits && ms_between(r->t_submit, now) > aging_ms) break;
+            ++it;
         }
         cv_work.notify_all();
+        cv_eng.notify_all();
+    }
+
+    // under mu: a request's outcome, its memory back to the budget, the
+    // next admissions
+    void finish_locked(const std::shared_ptr<Req>& r, int rc, const std::string& err, int worker) {
+        r->info.status = rc;
+        r->info.worker = worker;
+        std::snprintf(r->info.error, sizeof(r->info.error), "%s", err.c_str());
+        r->t_done = Clock::now();
+        r->info.queue_ms = ms_between(r->t_submit, r->t_admit);
+        r->info.run_ms = ms_between(r->t_admit, r->t_done);
+        r->info.latency_ms = ms_between(r->t_submit, r->t_done);
+        r->done = true;
+        reserved -= r->est;
+        --running;
+        ++completed;
+        if (rc != SGK_OK) ++failed;
+        admit_locked();
     }
 
     void worker(int w);
+    void engine();
 };
 
 namespace {
@@ -271,25 +314,188 @@ void sgk_server::worker(int w) {
         }
         {
             std::lock_guard<std::mutex> lk(mu);
-            r->info.status = rc;
-            r->info.worker = w;
-            std::snprintf(r->info.error, sizeof(r->info.error), "%s", err.c_str());
-            r->t_done = Clock::now();
-            r->info.queue_ms = ms_between(r->t_submit, r->t_admit);
-            r->info.run_ms = ms_between(r->t_admit, r->t_done);
-            r->info.latency_ms = ms_between(r->t_submit, r->t_done);
-            r->done = true;
-            reserved -= r->est;
-            --running;
-            ++completed;
-            if (rc != SGK_OK) ++failed;
             slot[w] = nullptr;
-            admit_locked();
+            finish_locked(r, rc, err, w);
         }
         cv_done.notify_all();
     }
     for (sgk_ctx* c : ctx) sgk_ctx_destroy(c);
     if (stream) cudaStreamDestroy(stream);
+}
+
+namespace {
+
+// A request in the engine: its own context (on one of the engine's
+// streams), index set, operator and solver, and the steps taken so far.
+struct Live {
+    std::shared_ptr<Req> r;
+    sgk_ctx* ctx = nullptr;
+    sgk_index* idx = nullptr;
+    sgk_op* op = nullptr;
+    sgk_solver* sol = nullptr;
+    int64_t done = 0;
+    ~Live() {
+        sgk_solver_destroy(sol);
+        sgk_operator_destroy(op);
+        sgk_index_destroy(idx);
+        sgk_ctx_destroy(ctx);
+    }
+};
+
+// Sets a request up on stream st; SGK_OK or the failing call's status.
+int engine_setup(int device, cudaStream_t st, Live& L, std::string& err, int num_sms) {
+    Req& r = *L.r;
+    int rc = sgk_ctx_create(&L.ctx, device, st, r.prec);
+    if (rc != SGK_OK) {
+        err = "engine context";
+        return rc;
+    }
+    auto chk = [&](int code) {
+        if (code != SGK_OK && err.empty())
+            err = L.ctx->last_error.empty() ? "status " + std::to_string(code) : L.ctx->last_error;
+        return code;
+    };
+    const int64_t dof = level_dof(r.d, r.n, r.k);
+    // the Arnoldi grid sized to the DOF (slices of at most 384 coefficients)
+    // and the batched kernels' lane count, so that no tuning runs stall the
+    // engine's other requests
+    L.ctx->persist_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms, (dof + 383) / 384));
+    L.ctx->arn_G_fixed = 8;
+    rc = chk(sgk_index_build(L.ctx, r.d, r.n, r.k, &L.idx));
+    if (rc == SGK_OK) rc = chk(sgk_operator_assemble(L.ctx, L.idx, r.kappa.data(), r.bc, 20.0, &L.op));
+    if (rc == SGK_OK) {
+        sgk_reaction f{};
+        f.nspecies = 1;
+        f.nmono = r.nmono;
+        f.species = r.rx_species.data();
+        f.coef = r.rx_coef.data();
+        f.exps = r.rx_exps.data();
+        rc = chk(sgk_solver_create(L.ctx, 1, &L.op, &f, SGK_IIF2, r.M, r.dt, nullptr, &L.sol));
+    }
+    if (rc != SGK_OK) return rc;
+    const InitCopy& in = r.init[0];
+    if (!in.coeffs.empty()) {
+        rc = (int64_t)in.coeffs.size() == dof ? chk(sgk_solver_set_state(L.sol, 0, in.coeffs.data(), 0))
+                                              : chk(SGK_EINVAL);
+    } else {
+        try {
+            DevBuf<double> u0(dof);
+            rc = chk(sgk_project_separable(L.ctx, L.idx, (int)in.amp.size(), in.amp.data(), in.wavenum.data(),
+                                           in.kind.data(), in.const_term, u0.p));
+            if (rc == SGK_OK) rc = chk(sgk_solver_set_state(L.sol, 0, u0.p, 1));
+            SGK_CUDA_CHECK(cudaStreamSynchronize(st));
+        } catch (const SgkError& e) {
+            rc = e.code;
+            err = e.msg;
+        }
+    }
+    return rc;
+}
+
+}  // namespace
+
+void sgk_server::engine() {
+    cudaSetDevice(device);
+    BatchCore core;
+    const bool ok = core.init(device, 8) == SGK_OK;
+    std::vector<std::unique_ptr<Live>> live;
+    int next_stream = 0;
+    auto retire = [&](std::unique_ptr<Live>& L, int rc, const std::string& err) {
+        if (rc == SGK_OK && L->sol) {
+            Req& r = *L->r;
+            const int64_t dof = L->idx->dof;
+            sgk_stats st{};
+            sgk_solver_stats(L->sol, &st);
+            r.info.steps = st.steps;
+            r.info.newton_iters = st.newton_iters;
+            r.info.inner_iters = st.inner_iters;
+            r.info.dof = dof;
+            r.result.resize((size_t)dof);
+            rc = sgk_solver_get_state(L->sol, 0, r.result.data(), dof, 0);
+        }
+        std::shared_ptr<Req> r = L->r;
+        L.reset();  // device memory back before the budget is
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            --eng_count;
+            finish_locked(r, rc, err, -1);
+        }
+        cv_done.notify_all();
+    };
+    for (;;) {
+        std::deque<std::shared_ptr<Req>> fresh;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_eng.wait(lk, [&] { return !eng_new.empty() || !live.empty() || (stopping && queue.empty()); });
+            if (eng_new.empty() && live.empty()) break;
+            fresh.swap(eng_new);
+        }
+        // join: set the new requests up between ticks
+        for (auto& r : fresh) {
+            std::unique_ptr<Live> L(new Live());
+            L->r = r;
+            std::string err;
+            int rc = SGK_ECUDA;
+            if (ok) {
+                cudaStream_t st = core.streams[next_stream++ % core.streams.size()];
+                alloc_stream() = st;  // the request's buffers stream-ordered on its stream
+                try {
+                    rc = engine_setup(device, st, *L, err, core.num_sms);
+                } catch (const std::exception& e) {
+                    rc = SGK_ECUDA;
+                    err = e.what();
+                }
+                alloc_stream() = nullptr;
+            } else {
+                err = "engine could not create its streams";
+            }
+            if (rc != SGK_OK || r->nsteps == 0) {
+                if (L->ctx) alloc_stream() = L->ctx->stream;
+                retire(L, rc, err);
+                alloc_stream() = nullptr;
+            } else {
+                live.push_back(std::move(L));
+            }
+        }
+        if (live.empty()) continue;
+        // one step of every live request
+        std::vector<sgk_solver*> sols;
+        for (auto& L : live) sols.push_back(L->sol);
+        std::vector<int> status;
+        std::string tick_err;
+        // the batched plan's buffers (rebuilt when the set changes) stream-
+        // ordered on the batch stream, so that freeing them does not wait
+        // for the workers' streams
+        alloc_stream() = core.bstream;
+        try {
+            batch_core_tick(core, sols, status);
+            alloc_stream() = nullptr;
+        } catch (const SgkError& e) {
+            alloc_stream() = nullptr;
+            status.assign(sols.size(), e.code);
+            tick_err = e.msg;
+        } catch (const std::exception& e) {
+            alloc_stream() = nullptr;
+            status.assign(sols.size(), SGK_ECUDA);
+            tick_err = e.what();
+        }
+        // leave: finished or failed requests
+        for (size_t i = 0; i < live.size(); ++i) {
+            std::unique_ptr<Live>& L = live[i];
+            if (status[i] == SGK_OK) ++L->done;
+            if (status[i] != SGK_OK || L->done >= L->r->nsteps) {
+                std::string err = tick_err;
+                if (status[i] != SGK_OK && err.empty())
+                    err = L->ctx->last_error.empty() ? "step status " + std::to_string(status[i])
+                                                     : L->ctx->last_error;
+                alloc_stream() = L->ctx->stream;
+                retire(L, status[i], err);
+                alloc_stream() = nullptr;
+            }
+        }
+        live.erase(std::remove_if(live.begin(), live.end(), [](const std::unique_ptr<Live>& L) { return !L; }),
+                   live.end());
+    }
 }
 
 // ------------------------------------------------------------------ C ABI ---
@@ -352,13 +558,16 @@ int sgk_server_create(int device, int nworkers, int64_t mem_budget_bytes, double
     srv->slot.assign(nworkers, nullptr);
     try {
         for (int w = 0; w < nworkers; ++w) srv->threads.emplace_back([s = srv.get(), w] { s->worker(w); });
+        srv->eng_thread = std::thread([s = srv.get()] { s->engine(); });
     } catch (...) {
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             srv->stopping = true;
         }
         srv->cv_work.notify_all();
+        srv->cv_eng.notify_all();
         for (auto& t : srv->threads) t.join();
+        if (srv->eng_thread.joinable()) srv->eng_thread.join();
         return SGK_ENOMEM;
     }
     *out = srv.release();
@@ -479,8 +688,18 @@ int sgk_server_destroy(sgk_server* srv) {
         srv->stopping = true;
     }
     srv->cv_work.notify_all();
+    srv->cv_eng.notify_all();
     for (auto& t : srv->threads) t.join();
+    if (srv->eng_thread.joinable()) srv->eng_thread.join();
     delete srv;
+    return SGK_OK;
+}
+
+int sgk_server_set_engine(sgk_server* srv, int on, int max_requests) {
+    if (!srv || max_requests < 0) return SGK_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->engine_on = on != 0;
+    if (max_requests > 0) srv->eng_max = max_requests;
     return SGK_OK;
 }
 

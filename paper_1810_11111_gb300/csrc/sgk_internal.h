@@ -121,6 +121,7 @@ struct sgk_ctx {
     bool own_stream = false;  // stream created by the library (caller passed NULL)
     bool capturing = false;   // a CUDA graph is being captured on the stream
     int persist_ctas = 0;     // CTAs of the persistent Arnoldi kernel (0 = one per SM)
+    int arn_G_fixed = 0;      // lanes per output of its matvec (0 = autotuned per solver)
     double* hscal = nullptr;  // pinned host scalars (16) for step-control reads
     // event timing
     unsigned prof_mask = 0;

@@ -15,6 +15,10 @@ struct GraphCache {
 };
 
 struct sgk_solver {
+    // serial number, never reused in the process (a destroyed solver's
+    // address can be handed to a new one; plans that hold device pointers
+    // of their solvers are keyed by this)
+    uint64_t uid = 0;
     sgk_ctx* ctx = nullptr;
     const sgk_index* idx = nullptr;
     int nspecies = 1;

@@ -1362,7 +1362,9 @@ void solver_alloc(sgk_solver* s) {
         pw.bounds = s->abounds.p;
         pw.E = s->aE;
         pw.list_ent = s->alist;
-        s->arn_G = arnoldi_autotune(s->ctx, s->ops[0], pw, krylov_work<double>(s, 0), s->W.p, n, M);
+        s->arn_G = s->ctx->arn_G_fixed > 0
+                       ? s->ctx->arn_G_fixed
+                       : arnoldi_autotune(s->ctx, s->ops[0], pw, krylov_work<double>(s, 0), s->W.p, n, M);
         SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * S * sizeof(unsigned), s->ctx->stream));
     }
     SGK_CUDA_CHECK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(unsigned), s->ctx->stream));

@@ -123,6 +123,7 @@ _SIGS = {
     "sgk_estimate_bytes": (ctypes.c_int64, [ctypes.c_int] * 7),
     "sgk_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                          ctypes.POINTER(_P)]),
+    "sgk_server_set_engine": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "sgk_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(sgk_request), _c_i64_p]),
     "sgk_server_poll": (ctypes.c_int, [_P, ctypes.c_int64]),
     "sgk_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(sgk_result_info),
@@ -419,13 +420,16 @@ class Server:
     workload dicts as in workloads.py; results are species-stacked FP64
     coefficients with the server's timing record."""
 
-    def __init__(self, device=0, workers=4, mem_budget_bytes=0, aging_ms=0.0):
+    def __init__(self, device=0, workers=4, mem_budget_bytes=0, aging_ms=0.0, engine=True, engine_max=0):
         load()
         self.h = _P()
         rc = sgk_server_create(int(device), int(workers), int(mem_budget_bytes), float(aging_ms),
                                ctypes.byref(self.h))
         if rc:
             raise SgkError(rc, "sgk_server_create failed")
+        rc = sgk_server_set_engine(self.h, 1 if engine else 0, int(engine_max))
+        if rc:
+            raise SgkError(rc, "sgk_server_set_engine failed")
 
     @staticmethod
     def request(cfg, precision, init_coeffs=None):

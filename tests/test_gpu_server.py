@@ -8,7 +8,13 @@ Checks, on the GPU:
     of its precision (1e-10 FP64, 1e-6 mixed);
   * requests overlap (more than one runs at once) when the budget allows;
   * the memory admission serialises requests when only one fits, and
-    rejects a request larger than the whole budget.
+    rejects a request larger than the whole budget;
+  * the engine (iteration-level continuous batching of the single-species
+    requests on the batched Arnoldi launches) runs several requests at once,
+    reports them as engine requests, gives each the same coefficients alone
+    and in a mix, and matches the worker path and the direct solver path
+    within the parity tolerance; requests that arrive while others are
+    stepping join the running batch.
 """
 import numpy as np
 import pytest
@@ -53,8 +59,9 @@ def direct(cfg, prec):
     return out
 
 
-def test_same_alone_and_in_mix():
-    srv = sgkiif.Server(0, workers=3)
+@pytest.mark.parametrize("engine", [True, False])
+def test_same_alone_and_in_mix(engine):
+    srv = sgkiif.Server(0, workers=3, engine=engine)
     alone = []
     for cfg, prec in MIX:
         t = srv.submit(cfg, prec)
@@ -93,3 +100,46 @@ def test_admission_by_memory():
     assert e.value.code == sgkiif.SGK_ENOMEM
     assert srv.stats()["rejected"] == 1
     srv.close()
+
+
+def test_engine_batches_requests_and_matches_workers():
+    reqs = [(cubic(3, 5, 2, 6 + i, 40 + i), sgkiif.SGK_MIXED) for i in range(5)] + \
+           [(cubic(2, 6, 1, 4 + i, 50 + i), sgkiif.SGK_FP64) for i in range(3)]
+    caps = [4 * sgkiif.dof_of(c["d"], c["n"], c["k"]) for c, _ in reqs]
+    srv = sgkiif.Server(0, workers=2, engine=True)
+    tickets = [srv.submit(c, p) for c, p in reqs]
+    eng = [srv.wait(t, cap=cap) for t, cap in zip(tickets, caps)]
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 0 and st["max_concurrent"] >= 2
+    assert all(info["worker"] == -1 and info["steps"] == c["steps"] for (_, info), (c, _) in zip(eng, reqs))
+    srv = sgkiif.Server(0, workers=2, engine=False)
+    wrk = [srv.wait(srv.submit(c, p), cap=cap) for (c, p), cap in zip(reqs, caps)]
+    srv.close()
+    for (c, p), (a, _), (b, _) in zip(reqs, eng, wrk):
+        tol = 1e-10 if p == sgkiif.SGK_FP64 else 1e-6
+        assert rel(a, b) <= tol and rel(a, direct(c, p)) <= tol
+
+
+def test_engine_admits_requests_while_stepping():
+    import time
+    srv = sgkiif.Server(0, workers=1, engine=True)
+    long_req = cubic(3, 5, 2, 400, 61)
+    s0 = time.perf_counter()
+    t0 = srv.submit(long_req, sgkiif.SGK_MIXED)
+    time.sleep(0.1)  # the long request is being set up or stepping
+    short = [cubic(2, 5, 1, 3, 62 + i) for i in range(3)]
+    s1 = time.perf_counter()
+    ts = [srv.submit(c, sgkiif.SGK_MIXED) for c in short]
+    outs = [srv.wait(t, cap=4 * sgkiif.dof_of(c["d"], c["n"], c["k"])) for t, c in zip(ts, short)]
+    out0, info0 = srv.wait(t0, cap=4 * sgkiif.dof_of(3, 5, 2))
+    srv.close()
+    assert info0["status"] == sgkiif.SGK_OK and info0["steps"] == 400
+    done_long = s0 * 1e3 + info0["latency_ms"]
+    for (out, info), c in zip(outs, short):
+        assert info["status"] == sgkiif.SGK_OK and info["worker"] == -1
+        # admitted at once and finished while the long request was still
+        # stepping: they joined its batch instead of waiting behind it
+        assert info["queue_ms"] < 50.0
+        assert s1 * 1e3 + info["latency_ms"] < done_long
+        assert rel(out, direct(c, sgkiif.SGK_MIXED)) <= 1e-6
