@@ -148,8 +148,11 @@ struct Quad {
     static constexpr int NS = N / KP1;
     // the innermost level (whose body is the point evaluation, where most
     // of the arithmetic is) is unrolled so that its Gauss-table entries are
-    // compile-time operands; the outer levels stay loops
-    static constexpr int UNROLL = DIM == D - 1 ? Q : 1;
+    // compile-time operands; the outer levels stay loops.  In double-float
+    // the unrolled code outgrows the instruction cache (fetch stalls led the
+    // profile), so that level stays a loop too: measured 0.66 against
+    // 0.76 ms per F pass at level 6 together with the register cap below
+    static constexpr int UNROLL = (DIM == D - 1 && !std::is_same<T, dfloat>::value) ? Q : 1;
     __device__ __forceinline__ static void run(const QuadTab<T>& tb, const Poly<T, S>& P, const T (&Cu)[S][N],
                                                const T (&Cw)[S][N], T (&M)[S][N], T wt) {
 #pragma unroll UNROLL
@@ -359,9 +362,12 @@ __device__ __forceinline__ void bwd_subtree(T* Mb, T* Y, int f, int j, int Lhi, 
 
 // Register limit per element type: 128 for FP32 (eight 64-thread CTAs per
 // SM, no spills; a 96-register cap with spills measured slower), the
-// architectural 255 for FP64 (its cell loops need them).
+// architectural 255 for FP64 (its cell loops need them), and 128 for
+// double-float (eight CTAs per SM, as many as shared memory allows; a few
+// spills, but 128, 144, 168, 192 and 216 measured 0.66, 0.68, 0.68, 0.72
+// and 0.73 ms per F pass at level 6).
 template <typename T, int D, int KP1, int Q, int S, bool JAC>
-__global__ void __maxnreg__(sizeof(T) == 4 ? 128 : 255)
+__global__ void __maxnreg__((sizeof(T) == 4 || std::is_same<T, dfloat>::value) ? 128 : 255)
     pencil_kernel(const PencilArgs args, const QuadTab<T> tb, const Filt<T, KP1> F, const Poly<T, S> poly) {
     constexpr int P = Pow<KP1, D - 1>::v;  // fibers per species and set
     constexpr int PS = P | 1;              // odd fiber stride in shared memory
