@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-matvec", action="store_true", help="skip the large stand-alone matvec leg")
     ap.add_argument("--no-iif3", action="store_true", help="skip the IIF3 leg")
     ap.add_argument("--no-schnak", action="store_true", help="skip the two-species 200-step leg")
+    ap.add_argument("--served-no-fp64", action="store_true",
+                    help="skip the FP64 one-at-a-time baseline of the served leg (and its accuracy check)")
     ap.add_argument("--served-rates", default="1",
                     help="comma-separated arrival rates of the served leg, as multiples of the one-at-a-time "
                          "capacity (e.g. 0.5,1,2)")
@@ -397,6 +399,9 @@ def native(args, rank, world, local_rank):
                                       "matvec_arith": "double-float on the FP32 pipe" if mixed else "FP64",
                                       "fp32_peak_tflops": fp32_peak,
                                       "fp32_peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                                      "measured_fp64_peak_tflops": alu_peaks_tflops()["fp64"],
+                                      "measured_fp32_peak_tflops": alu_peaks_tflops()["fp32"],
+                                      "measured_peak_method": ALU_PROBE,
                                       "busy_frac": alu_s / (t / nl)},
                             traffic=ARNOLDI_TRAFFIC.get((d, N, cfg["k"], cfg["M"], args.precision)),
                             traffic_note="dram read + write of one launch, ncu cold capture "
@@ -408,8 +413,10 @@ def native(args, rank, world, local_rank):
             mixed = prec == sgkiif.SGK_MIXED
             peak = 152 * 128 * 2 * clock * 1e6 / 1e12 if mixed else 1.25
             achieved = flops_algo / t / 1e12
+            meas = alu_peaks_tflops()["fp32" if mixed else "fp64"]
             roofline = dict(common, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
                             frac=achieved / peak, passes=pass_mix,
+                            measured_peak=meas, frac_of_measured=achieved / meas, measured_peak_method=ALU_PROBE,
                             work_model="FP32-pipe flops: 2 per FP32 multiply-add, 24 per double-float "
                                        "multiply-add (12 FP32 operations); algorithmic multiply-adds of the "
                                        "sum-factorised quadrature and the two-scale pyramids of the last "
@@ -445,7 +452,8 @@ def native(args, rank, world, local_rank):
            "host_wall_s": wall,
            "profiled_pass_ms_per_step": prof_ms / args.steps,
            "solver": {"newton_iters": st1["newton_iters"] - st0["newton_iters"],
-                      "inner_iters": nJ, "last_m_eff": st1["last_m_eff"]},
+                      "inner_iters": nJ, "last_m_eff": st1["last_m_eff"],
+                      "max_krylov_err_est": st1["max_krylov_err_est"]},
            "kernel_ms_per_step": {c: round(v[0] / args.steps, 4) for c, v in kprof.items() if v[1] > 0}}
     prob.close()
     if world == 1 and not args.no_matvec:
@@ -551,11 +559,33 @@ def schnak_leg(args):
         finals[name] = np.concatenate(prob.state())
         st = prob.solver.stats()
         out[name] = {"ms_per_step": ms / nsteps, "dof_steps_per_s": prob.dof * 2 * nsteps / (ms / 1e3),
-                     "newton_iters": st["newton_iters"], "inner_iters": st["inner_iters"]}
+                     "newton_iters": st["newton_iters"], "inner_iters": st["inner_iters"],
+                     "max_krylov_err_est": st["max_krylov_err_est"]}
         prob.close()
     out["rel_l2_mixed_vs_fp64_after_%d_steps" % nsteps] = float(
         np.linalg.norm(finals["mixed"] - finals["fp64"]) / np.linalg.norm(finals["fp64"]))
     return out
+
+
+# ------------------------------------------------------ measured peaks ---
+
+_ALU = {}
+
+
+def alu_peaks_tflops():
+    """FMA peaks of the FP32 and FP64 pipes measured on this device by the
+    library's probe kernel (sgk_alu_peak: independent FMA chains, best of 5
+    launches), in TFLOP/s; taken once, outside every timed region."""
+    if not _ALU:
+        from paper_1810_11111_gb300 import sgkiif
+        import torch
+        dev = torch.cuda.current_device()
+        _ALU["fp32"] = sgkiif.alu_peak(dev, "fp32") / 1e12
+        _ALU["fp64"] = sgkiif.alu_peak(dev, "fp64") / 1e12
+    return _ALU
+
+
+ALU_PROBE = "sgk_alu_peak: 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, best of 5 launches"
 
 
 # ----------------------------------------------------------- matvec leg ---
@@ -599,7 +629,9 @@ def matvec_leg(peaks, peak_kind):
         es = x.element_size()
         tf = 2.0 * madds / t / 1e12
         gbs = 2.0 * dof * es / t / 1e9
+        meas = alu_peaks_tflops()[name]
         out[name] = {"us_per_matvec": t * 1e6, "achieved_tflops": tf, "peak_tflops": peak, "frac_alu": tf / peak,
+                     "measured_peak_tflops": meas, "frac_alu_of_measured": tf / meas, "measured_peak_method": ALU_PROBE,
                      "algorithmic_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_hbm": gbs / peaks["hbm_gbs"],
                      "hbm_peak_source": peak_kind}
     out["bound"] = "FP64 pipe (the part's FP64 rate is ~50x below what HBM feeds at this arithmetic intensity)"
@@ -677,6 +709,8 @@ def batched_leg(args, dist=None, rank=0, world=1):
         rc2, st = b.step(steps)
         wall = time.perf_counter() - t0
         states[name] = [np.concatenate(b.state(i)) for i in range(len(insts))]
+        if name == "mixed":
+            kest = np.array([b.stats(i)["max_krylov_err_est"] for i in range(len(insts))])
         res[name] = dict(dof_steps_per_s=work_per_step * steps / wall, wall_s=wall,
                          failed=sum(1 for x in st if x != sgkiif.SGK_OK), status=max(rc, rc2),
                          batched_arnoldi_launches=b.launches())
@@ -718,13 +752,19 @@ def batched_leg(args, dist=None, rank=0, world=1):
                                 "max_well_conditioned": float(errs[well].max()) if well.any() else None,
                                 "above_1e-6_well_conditioned": int((errs[well] > 1e-6).sum()),
                                 "ill_conditioned": [{"instance": int(i), "rel_l2_mixed_vs_fp64": float(errs[i]),
-                                                     "fp64_change_under_1e-14_input_perturbation": float(sens[i])}
+                                                     "fp64_change_under_1e-14_input_perturbation": float(sens[i]),
+                                                     "krylov_err_est": float(kest[i])}
                                                     for i in np.nonzero(ill)[0]],
                                 "note": "per instance after the timed steps; every instance above 1e-6 is "
                                         "solved again alone in FP64 from its initial state perturbed by 1e-14 "
                                         "relative: ill-conditioned = the FP64 result itself moves by more than "
                                         "1e-8 (an M = 30 Krylov projection far from converged at dt rho(A) ~ 1e4 "
                                         "amplifies rounding-level perturbations)"},
+                krylov_err_est={"median": float(np.median(kest)), "max": float(kest.max()),
+                                "above_1e-6": int((kest > 1e-6).sum()),
+                                "max_well_conditioned": float(kest[well].max()) if well.any() else None,
+                                "note": "largest a-posteriori estimate h_{m+1,m} |[exp(dt H) e1]_m| / "
+                                        "||exp(dt H) e1|| of each instance's projections over its mixed steps"},
                 timing="host wall clock around the batch steps (each step waits for every stream)")
 
 
@@ -744,9 +784,13 @@ def served_leg(args):
 
     failures = []
 
-    def record(info):
+    kest = {}
+
+    def record(info, i=None):
         if info["status"] != sgkiif.SGK_OK:
             failures.append("status %d: %s" % (info["status"], info["error"]))
+        if i is not None:
+            kest[i] = info["krylov_err_est"]
         return info["latency_ms"]
 
     caps = [4 * sgkiif.dof_of(r["d"], r["n"], r["k"]) for r in reqs]
@@ -777,7 +821,7 @@ def served_leg(args):
     mean_service_s = wall_m / len(reqs)
     capacity_rate = 1.0 / mean_service_s  # requests/s one at a time
 
-    def serve(rate, engine=True):
+    def serve(rate, engine=True, keep_est=False):
         """Requests arriving as a Poisson stream at `rate` per second (all at
         t = 0 when rate is None); returns summary, outputs, server stats."""
         arrivals = workloads.poisson_arrivals(len(reqs), rate, seed=4) if rate else [0.0] * len(reqs)
@@ -790,9 +834,9 @@ def served_leg(args):
                 time.sleep(delay)
             tickets.append(srv.submit(r, sgkiif.SGK_MIXED))
         lat, outs = [], []
-        for t, cap in zip(tickets, caps):
+        for i, (t, cap) in enumerate(zip(tickets, caps)):
             out, info = srv.wait(t, cap=cap)
-            lat.append(record(info))
+            lat.append(record(info, i if keep_est else None))
             outs.append(out)
         wall = time.perf_counter() - t0
         st = srv.stats()
@@ -808,10 +852,10 @@ def served_leg(args):
                                        peak_reserved_gb=st["peak_reserved_bytes"] / 1e9)
         if outs_served is None:
             outs_served = outs
-    sat, outs_sat, st_sat = serve(None)
+    sat, outs_sat, st_sat = serve(None, keep_est=True)
     sat_workers, _, _ = serve(None, engine=False)
     outs64 = []
-    lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64)
+    lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64) if not args.served_no_fp64 else ([0.0], 0.0)
 
     def rel(m, f):
         return float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
@@ -819,10 +863,11 @@ def served_leg(args):
     errs = [rel(m, f) for m, f in zip(outs_sat, outs64) if m.size and f.size]
     over = [i for i, e in enumerate(errs) if e > 1e-6]
     ill = [{"request": i, "rel_l2_mixed_vs_fp64": errs[i],
-            "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(reqs[i], reqs[i]["steps"])}
+            "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(reqs[i], reqs[i]["steps"]),
+            "krylov_err_est": kest.get(i)}
            for i in over]
     first = by_rate["%gx" % rates[0]] if rates else sat
-    base64 = summary(lat64, wall64)
+    base64 = summary(lat64, wall64) if not args.served_no_fp64 else None
     mixed1 = summary(lat_m, wall_m)
     return dict(first,
                 workload="served: %d requests (seed 4; d 3-4, level 6-9, degree 1-3, cubic or Schnakenberg, "
@@ -837,7 +882,7 @@ def served_leg(args):
                                                                "on a worker thread"),
                 one_at_a_time_mixed=mixed1,
                 one_at_a_time_fp64=base64,
-                speedup_vs_fp64_one_at_a_time=first["dof_steps_per_s"] / base64["dof_steps_per_s"],
+                speedup_vs_fp64_one_at_a_time=first["dof_steps_per_s"] / base64["dof_steps_per_s"] if base64 else None,
                 saturation_vs_one_at_a_time_mixed=sat["dof_steps_per_s"] / mixed1["dof_steps_per_s"],
                 failed_requests=len(failures), first_failure=failures[0] if failures else None,
                 max_rel_l2_vs_fp64=max(errs) if errs else None,
@@ -847,6 +892,11 @@ def served_leg(args):
                                                                    x["fp64_change_under_1e-14_input_perturbation"]
                                                                    > 1e-8 for x in ill)], default=None),
                 conditioning_of_requests_above_1e_6=ill,
+                krylov_err_est={"median": float(np.median(list(kest.values()))) if kest else None,
+                                "max": max(kest.values()) if kest else None,
+                                "above_1e_6": sum(1 for v in kest.values() if v > 1e-6),
+                                "note": "per request of the saturation run: the largest a-posteriori Krylov "
+                                        "error estimate over its steps"},
                 note="mixed results of the saturation run against the FP64 one-at-a-time results; a request "
                      "whose FP64 result moves by more than 1e-8 under a 1e-14 input perturbation is "
                      "ill-conditioned at this precision")

@@ -102,6 +102,17 @@ int64_t sgk_ctx_launch_count(const sgk_ctx* ctx);
  * (null arch), SGK_ECUDA (no device, or no image of the kernels loads on
  * it). */
 int sgk_binary_arch(int* arch);
+/* Measured arithmetic peak of one pipe (no counterpart in the paper; the
+ * denominator of the ALU-bound rooflines).  Runs a kernel of independent
+ * fused multiply-add chains (8 per thread, 8 CTAs of 256 threads per SM, on a
+ * private stream of `device`, about 20 ms per launch, 3 untimed and 5 timed
+ * launches) and writes the best timed rate in flop/s (2 per FMA) to
+ * *flops_per_s.  kind: SGK_PEAK_FP32_FMA or SGK_PEAK_FP64_FMA.  Allocates
+ * and frees a small device buffer; synchronises with its own events only.
+ * Errors: SGK_EINVAL (null out, unknown kind, no such device), SGK_ECUDA. */
+#define SGK_PEAK_FP32_FMA 0
+#define SGK_PEAK_FP64_FMA 1
+int sgk_alu_peak(int device, int kind, double* flops_per_s);
 /* Kernel timing for benchmarks (no counterpart in the paper).  While bit i of
  * mask is set, every launch of kernel class i is bracketed by two CUDA events
  * on the context's stream.  Classes: 0 SIPG matvec, 1 change of basis to the
@@ -322,6 +333,20 @@ int sgk_solver_set_source(sgk_solver* s, int species, int nterms, const double* 
  * equals the current time. */
 int sgk_solver_set_time(sgk_solver* s, double t);
 int sgk_solver_get_time(const sgk_solver* s, double* t);
+/* Sub-projections of the exponential (an extension: the paper takes one
+ * projection of dimension M per exponential, eq. krylov8).  With substeps =
+ * s > 1 every exp(tau A) v of the following steps (also sgk_krylov_expv) is
+ * the semigroup product exp((tau/s) A)^s v taken as s successive
+ * projections of dimension M, each of a time span tau/s.  Its error falls
+ * steeply with the span when tau rho(A) is large; the cost is s Arnoldi
+ * processes.  Use it where the a-posteriori estimate (sgk_stats) is above
+ * the accuracy wanted.  1 <= substeps <= SGK_MAX_KRYLOV_SUBSTEPS; 1 restores
+ * the paper's method.  A solver with substeps > 1 steps with its own
+ * Arnoldi launches inside sgk_batch (not the batched ones).  Drains queued
+ * steps; allocates one more vector of dof doubles on first use.  Errors:
+ * SGK_EINVAL (null, substeps out of range), SGK_ENOMEM. */
+#define SGK_MAX_KRYLOV_SUBSTEPS 64
+int sgk_solver_set_krylov_substeps(sgk_solver* s, int substeps);
 
 typedef struct sgk_stats {
     int64_t steps;           /* steps taken since creation */
@@ -331,6 +356,15 @@ typedef struct sgk_stats {
     int64_t krylov_breakdowns; /* of which truncated by happy breakdown */
     int last_m_eff;          /* Krylov dimension of the last exponential */
     double last_newton_residual;
+    /* A-posteriori estimate of the Krylov projection's error in the last
+     * step (largest over species, over the step's exponentials and over
+     * their sub-projections), relative to the projected result:
+     * h_{m+1,m} |e_m^T exp(dt H_m) e_1| / ||exp(dt H_m) e_1|| (the
+     * residual-type estimate of Saad 1992; 0 after a happy breakdown).  The
+     * paper takes a fixed M with no error control (Section 3); this reports
+     * how far that M is from converged without changing the method. */
+    double last_krylov_err_est;
+    double max_krylov_err_est;  /* the largest of those over all steps taken */
 } sgk_stats;
 int sgk_solver_stats(const sgk_solver* s, sgk_stats* out);
 
@@ -346,7 +380,9 @@ int sgk_reaction_eval(sgk_solver* s, const double* u_dev, double* f_dev);
 int sgk_jacobian_apply(sgk_solver* s, const double* u_dev, const double* w_dev, double* jw_dev);
 /* w = gamma V_M exp(dt H_M) e_1 ~ exp(dt A_s) v for species s (eqs.
  * krylov7-krylov8, Arnoldi with classical Gram-Schmidt applied twice).
- * m_eff (host, may be NULL) receives the Krylov dimension used.
+ * m_eff (host, may be NULL) receives the Krylov dimension used.  With
+ * sub-projections (sgk_solver_set_krylov_substeps) w is their product and
+ * m_eff, like sgk_krylov_export, describes the last of them.
  * Synchronises.  SGK_ETIMEOUT: a grid barrier of the persistent Arnoldi
  * kernel ran out of time (w is then undefined; the solver stays usable).
  * Setting the environment variable SGK_TEST_BARRIER_STALL makes those
@@ -450,6 +486,7 @@ typedef struct sgk_result_info {
     int worker;              /* worker that ran it */
     int64_t newton_iters, inner_iters;
     char error[160];         /* error text when status != SGK_OK, else empty */
+    double krylov_err_est;   /* largest a-posteriori Krylov error estimate over its steps (sgk_stats) */
 } sgk_result_info;
 
 typedef struct sgk_server_stats {
@@ -555,6 +592,8 @@ int64_t sgk_batch_dof(const sgk_batch* b, int index);
 int sgk_batch_count(const sgk_batch* b);
 /* Copy one species' coefficients of an instance to host memory (cap >= dof). */
 int sgk_batch_get_state(const sgk_batch* b, int index, int species, double* out, int64_t cap);
+/* Statistics of one instance's solver (as sgk_solver_stats). */
+int sgk_batch_stats(const sgk_batch* b, int index, sgk_stats* out);
 int sgk_batch_destroy(sgk_batch* b);
 /* on = 0: run every instance's Arnoldi process inside its own whole-step
  * graph instead of the batched launches (for comparison); default 1. */

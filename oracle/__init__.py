@@ -22,7 +22,9 @@ reaction   reaction term F(U) and its Jacobian by finest-grid Gauss quadrature
            (Section 4 implementation remarks, Section 5)
 krylov     Arnoldi with re-orthogonalised Gram-Schmidt, Pade(13) expm with
            scaling and squaring, Krylov approximation of exp(dt A) v
-           (eqs. krylov7-krylov8, Section 3)
+           (eqs. krylov7-krylov8, Section 3); two extensions the paper does
+           not have: Saad's (1992) a-posteriori error estimate and the
+           exponential as a product of sub-projections
 iif        Newton solve and the IIF2 time step (eq. krylov5, Example 3)
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``

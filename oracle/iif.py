@@ -45,7 +45,7 @@ the paper is silent:
 """
 import numpy as np
 
-from .krylov import BREAKDOWN_TOL, krylov_expv
+from .krylov import BREAKDOWN_TOL, krylov_expv_substeps
 from .operator import sparse_matvec
 from .reaction import Reaction
 
@@ -137,12 +137,14 @@ def gmres(apply, b, tol=INNER_TOL, maxit=INNER_MAX, restart=GMRES_RESTART):
 class IIF2Solver:
     """Sparse-grid Krylov IIF2 DG solver (Sections 2-3)."""
 
-    def __init__(self, idx, S, kappas, reaction, dt, M, sources=None, t0=0.0):
+    def __init__(self, idx, S, kappas, reaction, dt, M, sources=None, t0=0.0, substeps=1):
         """S: 1D SIPG matrix; kappas: per species, a length-d diagonal;
         sources: per species a list of (lambda, S_m) pairs (the source
         P s(., t) = sum_m e^{lambda t} S_m), or None; t0: the time of the
-        state passed to run()."""
+        state passed to run(); substeps: every exponential as that many
+        successive projections (an extension; 1 is the paper's method)."""
         self.idx, self.S, self.dt, self.M = idx, S, dt, M
+        self.substeps = int(substeps)
         self.kappas = [np.asarray(k, dtype=np.float64) for k in kappas]
         self.nspecies = len(self.kappas)
         self.reaction = reaction
@@ -156,6 +158,10 @@ class IIF2Solver:
 
     def A(self, s):
         return lambda x: sparse_matvec(self.idx, self.S, self.kappas[s], x)
+
+    def expv(self, s, v, tau):
+        """exp(tau A_s) v by Krylov projection (eq. krylov8); (w, m_eff)."""
+        return krylov_expv_substeps(self.A(s), v, tau, self.M, self.substeps)
 
     def F(self, U, t):
         """F(U, t) = P f(u_h) + P s(., t)."""
@@ -210,7 +216,7 @@ class IIF2Solver:
         W = []
         for s in range(self.nspecies):
             v = U[s] + dt2 * Fn[s]
-            w, m_eff = krylov_expv(self.A(s), v, self.dt, self.M)
+            w, m_eff = self.expv(s, v, self.dt)
             self.stats["m_eff"].append(m_eff)
             W.append(w)
         return self.finish(W, dt2)
@@ -249,8 +255,8 @@ class IIF3Solver(IIF2Solver):
             return Unew
         W = []
         for s in range(self.nspecies):
-            w1, m1 = krylov_expv(self.A(s), U[s] + (2.0 / 3.0) * dt * Fn[s], dt, self.M)
-            w2, m2 = krylov_expv(self.A(s), self.F_prev[s], 2.0 * dt, self.M)
+            w1, m1 = self.expv(s, U[s] + (2.0 / 3.0) * dt * Fn[s], dt)
+            w2, m2 = self.expv(s, self.F_prev[s], 2.0 * dt)
             self.stats["m_eff"] += [m1, m2]
             W.append(w1 - (dt / 12.0) * w2)
         self.F_prev = Fn
@@ -292,10 +298,10 @@ class IIFSolver(IIF2Solver):
         alpha = iif_alpha(r)
         W = []
         for s in range(self.nspecies):
-            w, m = krylov_expv(self.A(s), U[s] + alpha[1] * dt * Fn[s], dt, self.M)
+            w, m = self.expv(s, U[s] + alpha[1] * dt * Fn[s], dt)
             self.stats["m_eff"].append(m)
             for i in range(1, r - 1):
-                wi, mi = krylov_expv(self.A(s), self.F_hist[i - 1][s], (i + 1) * dt, self.M)
+                wi, mi = self.expv(s, self.F_hist[i - 1][s], (i + 1) * dt)
                 self.stats["m_eff"].append(mi)
                 w = w + alpha[i + 1] * dt * wi
             W.append(w)

@@ -86,3 +86,35 @@ def krylov_expv(matvec, v, dt, M):
         return np.zeros_like(v), 0
     E = expm_pade13(dt * H[:m_eff, :m_eff])
     return gamma * (V[:, :m_eff] @ E[:, 0]), m_eff
+
+
+def krylov_error_estimate(H, m_eff, dt):
+    """A-posteriori estimate of the relative error of gamma V_m exp(dt H_m)
+    e_1 (an extension: the paper takes M fixed with no error control).
+
+    Saad, SIAM J. Numer. Anal. 29 (1992), Section 5: the projected solution
+    w_m(t) = gamma V_m exp(t H_m) e_1 satisfies w_m' = A w_m - r(t) with the
+    residual r(t) = gamma h_{m+1,m} [exp(t H_m) e_1]_m v_{m+1}; the span dt
+    times the residual at its end, relative to the result, is
+        dt h_{m+1,m} |[exp(dt H_m) e_1]_m| / ||exp(dt H_m) e_1||.
+    0 when nothing was projected; 1 when the projected result underflowed to
+    zero (the projection lost it)."""
+    if m_eff == 0:
+        return 0.0
+    y = expm_pade13(dt * H[:m_eff, :m_eff])[:, 0]
+    ny = float(np.linalg.norm(y))
+    if ny == 0.0:
+        return 1.0
+    return abs(dt * H[m_eff, m_eff - 1] * y[m_eff - 1]) / ny
+
+
+def krylov_expv_substeps(matvec, v, dt, M, substeps):
+    """exp(dt A) v as `substeps` successive projections (eq. krylov8) over
+    dt / substeps each: the semigroup property exp(dt A) = exp((dt/s) A)^s.
+    An extension, not in the paper (which takes one projection per
+    exponential); substeps = 1 is krylov_expv.  Returns (w, m_eff of the
+    last projection)."""
+    w, m_eff = v, 0
+    for _ in range(substeps):
+        w, m_eff = krylov_expv(matvec, w, dt / substeps, M)
+    return w, m_eff

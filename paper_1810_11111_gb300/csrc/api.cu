@@ -636,6 +636,18 @@ int sgk_solver_set_time(sgk_solver* s, double t) {
     });
 }
 
+int sgk_solver_set_krylov_substeps(sgk_solver* s, int substeps) {
+    if (!s) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        SGK_REQUIRE(substeps >= 1 && substeps <= SGK_MAX_KRYLOV_SUBSTEPS, SGK_EINVAL,
+                    "krylov substeps must be 1..SGK_MAX_KRYLOV_SUBSTEPS");
+        set_device(s->ctx);
+        solver_drain(s);
+        solver_set_krylov_substeps(s, substeps);
+        return SGK_OK;
+    });
+}
+
 int sgk_solver_get_time(const sgk_solver* s, double* t) {
     if (!s || !t) return SGK_EINVAL;
     return guarded(s->ctx, [&]() {

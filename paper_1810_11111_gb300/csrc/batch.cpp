@@ -259,6 +259,11 @@ int sgk_batch_get_state(const sgk_batch* b, int index, int species, double* out,
     return sgk_solver_get_state(in.sol, species, out, cap, 0);
 }
 
+int sgk_batch_stats(const sgk_batch* b, int index, sgk_stats* out) {
+    if (!b || !out || index < 0 || index >= (int)b->inst.size()) return SGK_EINVAL;
+    return sgk_solver_stats(b->inst[index]->sol, out);
+}
+
 int sgk_batch_destroy(sgk_batch* b) {
     delete b;
     return SGK_OK;

@@ -857,12 +857,29 @@ __global__ void __cluster_dims__(XCL, 1, 1) __launch_bounds__(XTH, 1)
 // W = gamma V[:, :m_eff] y  (FP64 accumulation, four chains over the
 // columns: FP64 dependent latency is long on this part)
 template <typename T>
-__global__ void combine_kernel(const T* __restrict__ V, long long ldv, const KrylovScalars* __restrict__ ks,
-                               const double* __restrict__ y, double* __restrict__ W, long long n) {
+__global__ void combine_kernel(const T* __restrict__ V, long long ldv, KrylovScalars* __restrict__ ks,
+                               const double* __restrict__ y, double* __restrict__ W, long long n,
+                               const double* __restrict__ H, int M, double tau) {
     __shared__ double ys[SGK_MAX_KRYLOV + 1];
     const int m = ks->m_eff;
     const double g = ks->gamma;
     for (int c = threadIdx.x; c < m; c += blockDim.x) ys[c] = y[c] * g;
+    // a-posteriori error estimate of the Krylov approximation, relative to
+    // the result: tau h_{m+1,m} |[exp(tau H_m) e_1]_m| / ||exp(tau H_m) e_1||
+    // (Saad, SIAM J. Numer. Anal. 29 (1992), Section 5: the residual of the
+    // projected ODE at the end of the span, times the span).  A projection
+    // whose result underflowed to zero without a breakdown has lost it: 1
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double est = 0.0;
+        if (m >= 1 && !ks->breakdown && ks->gamma > 0.0) {
+            double yy = 0.0;
+            for (int c = 0; c < m; ++c) yy += y[c] * y[c];
+            const double beta = H[(long long)m * M + (m - 1)];
+            est = yy > 0.0 ? fabs(tau * beta * y[m - 1]) / sqrt(yy) : 1.0;
+        }
+        ks->err_est = est;
+        ks->err_max = fmax(ks->err_max, est);
+    }
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -1303,7 +1320,7 @@ void krylov_finish(sgk_ctx* ctx, const KrylovWork<double>& kw, double* W, long l
     expm_e1(ctx, kw.H, M, &kw.ks->m_eff, 0, dt, kw.expm_ws, kw.y);
     {
         KTimer kt(ctx, KC_VECTOR);
-        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
+        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n, kw.H, M, dt);
     }
     check_launch("combine");
     count_launch(ctx);
@@ -1315,7 +1332,7 @@ void krylov_expv_persistent(sgk_ctx* ctx, const sgk_op* op, const PersistentWork
     expm_e1(ctx, kw.H, M, &kw.ks->m_eff, 0, dt, kw.expm_ws, kw.y);
     {
         KTimer kt(ctx, KC_VECTOR);
-        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n);
+        combine_kernel<double><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, kw.ks, kw.y, W, n, kw.H, M, dt);
     }
     check_launch("combine");
     count_launch(ctx);
@@ -1367,7 +1384,7 @@ void krylov_expv_dev(sgk_ctx* ctx, const KrylovWork<T>& kw, const std::function<
     expm_e1(ctx, kw.H, M, &ks->m_eff, 0, dt, kw.expm_ws, kw.y);
     {
         KTimer kt(ctx, KC_VECTOR);
-        combine_kernel<T><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, ks, kw.y, W, n);
+        combine_kernel<T><<<combine_grid(ctx, n), 128, 0, ctx->stream>>>(kw.V, n, ks, kw.y, W, n, kw.H, M, dt);
     }
     check_launch("combine");
     count_launch(ctx);

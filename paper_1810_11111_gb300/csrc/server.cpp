@@ -261,6 +261,7 @@ int run_request(sgk_ctx* ctx, Req& r, std::string& err) {
         sgk_solver_stats(sol, &st);
         r.info.steps = st.steps;
         r.info.newton_iters = st.newton_iters;
+        r.info.krylov_err_est = st.max_krylov_err_est;
         r.info.inner_iters = st.inner_iters;
         if (rc == SGK_OK) {
             r.result.resize((size_t)r.S * dof);
@@ -408,6 +409,7 @@ void sgk_server::engine() {
             sgk_solver_stats(L->sol, &st);
             r.info.steps = st.steps;
             r.info.newton_iters = st.newton_iters;
+            r.info.krylov_err_est = st.max_krylov_err_est;
             r.info.inner_iters = st.inner_iters;
             r.info.dof = dof;
             r.result.resize((size_t)dof);

@@ -17,6 +17,14 @@ struct KrylovScalars {
     int m_eff;      // Krylov dimension reached
     int breakdown;  // 1 if truncated by happy breakdown
     int pad;
+    // a-posteriori estimate of the projection's error relative to the
+    // result: h_{m+1,m} |e_m^T exp(tau H_m) e_1| / ||exp(tau H_m) e_1||
+    // (0 after a happy breakdown, where the projection is exact)
+    double err_est;
+    // the largest err_est since the solver last cleared it: a step clears
+    // it at its start, so it holds the largest over the step's projections
+    // (every exponential and every sub-projection of one)
+    double err_max;
 };
 
 struct PadeCoef {

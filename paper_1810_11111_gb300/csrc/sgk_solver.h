@@ -54,6 +54,10 @@ struct sgk_solver {
     DevBuf<float> V32, w32;
     DevBuf<double> Hm, h1, h2, ky, scal, partials, expm_ws;
     DevBuf<KrylovScalars> ks;
+    // exp(tau A) v as ksub successive projections of tau / ksub (1: the
+    // paper's single projection); ktmp is their intermediate vector
+    int ksub = 1;
+    DevBuf<double> ktmp;
     DevBuf<unsigned> counters;
     DevBuf<unsigned> fcnt;  // arrival counters of the fused Newton / CG kernels (zero between launches)
     // persistent Arnoldi: second work vector, partial sums, per species a
@@ -141,6 +145,9 @@ int solver_step(sgk_solver* s, int nsteps);
 void solver_eval_reaction(sgk_solver* s, const double* U, double* F);
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw);
 void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau = -1.0);
+// exp(tau A) v as ksub >= 1 successive projections of tau / ksub from the
+// next step on (drops the cached graphs when it changes)
+void solver_set_krylov_substeps(sgk_solver* s, int ksub);
 // replaces the source terms of one species (coeffs_dev: nterms * n device values)
 void solver_set_source(sgk_solver* s, int species, int nterms, const double* lambda, const double* coeffs_dev);
 void solver_set_time(sgk_solver* s, double t);

@@ -730,12 +730,15 @@ void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, doub
 }
 
 // W = exp(tau A_s) v by the Krylov projection (tau < 0: tau = dt)
-void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau) {
-    if (tau < 0.0) tau = s->dt;
+namespace {
+
+// One Krylov projection W = gamma V_M exp(tau H_M) e_1 (eq. krylov8) of v.
+void krylov_projection(sgk_solver* s, int species, const double* v, double* W, double tau) {
     const sgk_op* op = s->ops[species];
     const long long n = s->n;
-    // FP64 in both precision modes: an FP32 matvec inside Arnoldi costs a few
-    // 1e-6 of relative accuracy per exponential on these stiff operators
+    // the matvec inside Arnoldi is FP64 or double-float (mixed mode, in the
+    // persistent kernel): an FP32 matvec costs a few 1e-6 of relative
+    // accuracy per exponential on these stiff operators
     if (s->persistent) {
         PersistentWork pw;
         pw.w_alt = s->w64b.p;
@@ -751,7 +754,42 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, 
         auto mv = [op](const double* x, double* y) { op_matvec<double>(op, x, y); };
         krylov_expv_dev<double>(s->ctx, krylov_work<double>(s, species), mv, v, W, n, s->M, tau);
     }
+}
+
+// KrylovScalars::err_max = 0 for every species (the start of a step)
+__global__ void krylov_est_clear_kernel(KrylovScalars* ks, int nspecies) {
+    if (threadIdx.x < nspecies) ks[threadIdx.x].err_max = 0.0;
+}
+
+}  // namespace
+
+void krylov_est_clear(sgk_solver* s) {
+    krylov_est_clear_kernel<<<1, 32, 0, s->ctx->stream>>>(s->ks.p, s->nspecies);
+    check_launch("krylov_est_clear");
+    count_launch(s->ctx);
+}
+
+// exp(tau A) v: the paper's single projection, or with ksub > 1 the
+// semigroup product exp(tau A) = exp((tau / ksub) A)^ksub taken as ksub
+// successive projections, the last of which writes W
+void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, double tau) {
+    if (tau < 0.0) tau = s->dt;
+    const int ns = s->ksub;
+    const double* src = v;
+    for (int i = 0; i < ns; ++i) {
+        double* dst = ((ns - 1 - i) & 1) ? s->ktmp.p : W;
+        krylov_projection(s, species, src, dst, tau / ns);
+        src = dst;
+    }
     if (!s->use_graphs || !s->ctx->capturing) s->stats.krylov_calls += 1;
+}
+
+void solver_set_krylov_substeps(sgk_solver* s, int ksub) {
+    if (ksub > 1 && s->ktmp.n < (size_t)s->n) s->ktmp.alloc(s->n);
+    if (ksub != s->ksub) {
+        s->ksub = ksub;
+        drop_graphs(s);
+    }
 }
 
 // exp(dt H) e_1 and W = gamma V y of species 0 after its Arnoldi process
@@ -842,6 +880,7 @@ void build_step_graph(sgk_solver* s, int part = STEP_WHOLE) {
     try {
       if (part != STEP_POST) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        krylov_est_clear(s);
         if (s->has_rx) {
             // F(U^n) for the predictor, unless the last step left it in Fv
             capture_cond(
@@ -971,7 +1010,7 @@ void solver_step_launch(sgk_solver* s, int slot) {
 }
 
 bool solver_split_eligible(const sgk_solver* s) {
-    return solver_device_steps(s) && s->nspecies == 1 && s->persistent;
+    return solver_device_steps(s) && s->nspecies == 1 && s->persistent && s->ksub == 1;
 }
 
 ArnJob solver_arnoldi_job(sgk_solver* s) {
@@ -1034,10 +1073,13 @@ int solver_step_finish(sgk_solver* s, int slot, const double* restore) {
     s->stats.inner_iters += c.inner_iters;
     if (s->has_rx) s->stats.last_newton_residual = c.last_g;
     s->stats.krylov_calls += s->nspecies;
+    s->stats.last_krylov_err_est = 0.0;
     for (int sp = 0; sp < s->nspecies; ++sp) {
         s->stats.krylov_breakdowns += h->ks[sp].breakdown;
         s->stats.last_m_eff = h->ks[sp].m_eff;
+        s->stats.last_krylov_err_est = std::max(s->stats.last_krylov_err_est, h->ks[sp].err_max);
     }
+    s->stats.max_krylov_err_est = std::max(s->stats.max_krylov_err_est, s->stats.last_krylov_err_est);
     bool timed_out = false;
     if (s->persistent)
         for (int sp = 0; sp < s->nspecies; ++sp) timed_out = timed_out || h->flags[2 * sp + 1] != 0u;
@@ -1181,6 +1223,7 @@ int solver_step(sgk_solver* s, int nsteps) {
     };
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        krylov_est_clear(s);
         write_time(s);
         // IIFr (eqs. krylov3, krylov4) at the highest order r the history
         // allows: W = exp(dt A)(U^n + alpha_0 dt F(U^n)) + sum_{i=1}^{r-2}
@@ -1247,10 +1290,13 @@ int solver_step(sgk_solver* s, int nsteps) {
             SGK_CUDA_CHECK(cudaMemsetAsync(s->pbar.p, 0, 2 * s->nspecies * sizeof(unsigned), ctx->stream));
             rc = SGK_ETIMEOUT;
         }
+        s->stats.last_krylov_err_est = 0.0;
         for (int sp = 0; sp < s->nspecies; ++sp) {
             s->stats.krylov_breakdowns += ks[sp].breakdown;
             s->stats.last_m_eff = ks[sp].m_eff;
+            s->stats.last_krylov_err_est = std::max(s->stats.last_krylov_err_est, ks[sp].err_max);
         }
+        s->stats.max_krylov_err_est = std::max(s->stats.max_krylov_err_est, s->stats.last_krylov_err_est);
         if (rc != SGK_OK) {
             SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
                                            ctx->stream));

@@ -17,6 +17,7 @@ SGK_PERIODIC, SGK_DIRICHLET0 = 0, 1
 SGK_IIF2 = 2
 SGK_IIF3 = 3
 SGK_IIF_MAX_ORDER = 6
+SGK_PEAK_FP32_FMA, SGK_PEAK_FP64_FMA = 0, 1
 MAX_SPECIES = 4
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsgkiif.so")
@@ -40,7 +41,8 @@ class sgk_newton_opts(ctypes.Structure):
 class sgk_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64),
                 ("krylov_calls", ctypes.c_int64), ("krylov_breakdowns", ctypes.c_int64),
-                ("last_m_eff", ctypes.c_int), ("last_newton_residual", ctypes.c_double)]
+                ("last_m_eff", ctypes.c_int), ("last_newton_residual", ctypes.c_double),
+                ("last_krylov_err_est", ctypes.c_double), ("max_krylov_err_est", ctypes.c_double)]
 
 
 class sgk_init(ctypes.Structure):
@@ -59,7 +61,8 @@ class sgk_result_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("nspecies", ctypes.c_int), ("dof", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("est_bytes", ctypes.c_int64), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("worker", ctypes.c_int),
-                ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64), ("error", ctypes.c_char * 160)]
+                ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64), ("error", ctypes.c_char * 160),
+                ("krylov_err_est", ctypes.c_double)]
 
 
 class sgk_server_stats(ctypes.Structure):
@@ -76,6 +79,7 @@ _SIGS = {
     "sgk_last_error": (ctypes.c_char_p, [_P]),
     "sgk_ctx_launch_count": (ctypes.c_int64, [_P]),
     "sgk_binary_arch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
+    "sgk_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sgk_ctx_profile": (ctypes.c_int, [_P, ctypes.c_uint]),
     "sgk_ctx_profile_read": (ctypes.c_int, [_P, _c_double_p, _c_i64_p]),
     "sgk_index_build": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
@@ -113,6 +117,7 @@ _SIGS = {
     "sgk_solver_wait": (ctypes.c_int, [_P]),
     "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
     "sgk_solver_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "sgk_solver_set_krylov_substeps": (ctypes.c_int, [_P, ctypes.c_int]),
     "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),
     "sgk_reaction_eval": (ctypes.c_int, [_P, _P, _P]),
     "sgk_jacobian_apply": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -137,6 +142,7 @@ _SIGS = {
     "sgk_batch_count": (ctypes.c_int, [_P]),
     "sgk_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int64]),
     "sgk_batch_destroy": (ctypes.c_int, [_P]),
+    "sgk_batch_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(sgk_stats)]),
     "sgk_batch_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
     "sgk_batch_launches": (ctypes.c_int64, [_P]),
 }
@@ -345,6 +351,11 @@ class Solver:
     def set_time(self, t):
         self.ctx.check(sgk_solver_set_time(self.h, float(t)))
 
+    def set_krylov_substeps(self, substeps):
+        """exp(tau A) v as `substeps` successive projections of tau/substeps
+        (1: the paper's single projection)."""
+        self.ctx.check(sgk_solver_set_krylov_substeps(self.h, int(substeps)))
+
     def get_time(self):
         t = ctypes.c_double()
         self.ctx.check(sgk_solver_get_time(self.h, ctypes.byref(t)))
@@ -413,6 +424,17 @@ def binary_arch():
     if rc != SGK_OK:
         raise SgkError(rc, "sgk_binary_arch")
     return a.value
+
+
+def alu_peak(device=0, kind="fp32"):
+    """Measured FMA peak of the FP32 or FP64 pipe in flop/s (sgk_alu_peak)."""
+    load()
+    k = {"fp32": SGK_PEAK_FP32_FMA, "fp64": SGK_PEAK_FP64_FMA}[kind]
+    out = ctypes.c_double(0.0)
+    rc = sgk_alu_peak(int(device), k, ctypes.byref(out))
+    if rc != SGK_OK:
+        raise SgkError(rc, "sgk_alu_peak")
+    return out.value
 
 
 class Server:
@@ -522,6 +544,13 @@ class Batch:
     def launches(self):
         """Kernels of the batched Arnoldi path so far."""
         return int(sgk_batch_launches(self.h))
+
+    def stats(self, i):
+        st = sgk_stats()
+        rc = sgk_batch_stats(self.h, int(i), ctypes.byref(st))
+        if rc:
+            raise SgkError(rc, "sgk_batch_stats failed")
+        return {f: getattr(st, f) for f, _ in sgk_stats._fields_}
 
     def add(self, cfg, precision=SGK_MIXED, init_coeffs=None):
         q, keep = Server.request(cfg, precision, init_coeffs)

@@ -71,6 +71,21 @@ def test_context_creation_without_gpu_fails_cleanly(lib):
     assert sgkiif.sgk_ctx_create(ctypes.byref(h), 0, None, 0) == sgkiif.SGK_ECUDA
 
 
+def test_alu_peak_rejects_bad_arguments(lib):
+    import ctypes
+
+    import torch
+    from paper_1810_11111_gb300 import sgkiif
+    out = ctypes.c_double(0.0)
+    assert sgkiif.sgk_alu_peak(0, sgkiif.SGK_PEAK_FP32_FMA, None) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_alu_peak(0, 7, ctypes.byref(out)) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_alu_peak(-1, sgkiif.SGK_PEAK_FP64_FMA, ctypes.byref(out)) in (sgkiif.SGK_EINVAL,
+                                                                                     sgkiif.SGK_ECUDA)
+    if not torch.cuda.is_available():
+        assert sgkiif.sgk_alu_peak(0, sgkiif.SGK_PEAK_FP64_FMA, ctypes.byref(out)) in (sgkiif.SGK_EINVAL,
+                                                                                        sgkiif.SGK_ECUDA)
+
+
 def test_iif_alpha_is_adams_moulton(lib):
     # eq. krylov4's weights are the Adams-Moulton coefficients (the same
     # Lagrange integrals; textbook values), computed by the library's host code

@@ -45,16 +45,17 @@ INSTANCES = [
 ]
 
 
-def run_batch(streams, steps, fused=True, instances=INSTANCES):
+def run_batch(streams, steps, fused=True, instances=INSTANCES, with_est=False):
     b = sgkiif.Batch(0, streams=streams, fused=fused)
     for cfg, prec in instances:
         b.add(cfg, prec)
     rc, st = b.step(steps)
     assert rc == sgkiif.SGK_OK and all(s == sgkiif.SGK_OK for s in st)
     out = [np.concatenate(b.state(i)) for i in range(len(instances))]
+    est = [b.stats(i)["max_krylov_err_est"] for i in range(len(instances))]
     assert (b.launches() > 0) == fused
     b.close()
-    return out
+    return (out, est) if with_est else out
 
 
 def test_batch_matches_instances_alone():
@@ -76,10 +77,12 @@ def test_batch_independent_of_stream_count():
 
 
 def test_batched_launch_equals_whole_step_graphs():
-    a = run_batch(3, 2, fused=True)
-    b = run_batch(3, 2, fused=False)
+    a, ea = run_batch(3, 2, fused=True, with_est=True)
+    b, eb = run_batch(3, 2, fused=False, with_est=True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+    # the a-posteriori Krylov estimates come out of the same projections
+    assert ea == eb and all(np.isfinite(e) and e >= 0.0 for e in ea)
 
 
 def test_batched_launch_with_more_instances_than_sms():

@@ -23,7 +23,8 @@ torch = pytest.importorskip("torch")
 
 from oracle.iif import IIF2Solver, IIF3Solver, IIFSolver  # noqa: E402
 from oracle.index_set import IndexSet as OIndex  # noqa: E402
-from oracle.krylov import expm_pade13, krylov_expv  # noqa: E402
+from oracle.krylov import (arnoldi_cgs2, expm_pade13, krylov_error_estimate, krylov_expv,  # noqa: E402
+                           krylov_expv_substeps)
 from oracle.operator import DIRICHLET0, PERIODIC, sipg_1d, sparse_matvec  # noqa: E402
 from oracle.projection import project_separable  # noqa: E402
 from oracle.reaction import Reaction  # noqa: E402
@@ -993,6 +994,129 @@ def test_schnak2d_full_size_steps_match_oracle(precision, tol):
         done = step
         assert _rel_species(prob.state(), g["U%d" % step]) <= tol, step
     prob.close()
+
+
+def _heat2d_dense():
+    from oracle.operator import dense_sparse_operator
+    base = workloads.heat2d()
+    idx = OIndex(2, base["n"], base["k"])
+    S = sipg_1d(base["n"], base["k"])
+    kap = base["kappas"][0]
+    return base, idx, S, kap, dense_sparse_operator(idx, S, kap)
+
+
+@pytest.mark.parametrize("dt,M", [(1e-4, 20), (1e-3, 20), (5e-3, 30), (1.0, 8)])
+def test_krylov_error_estimate_matches_oracle(dt, M):
+    # heat2d's operator (F = 0): a step is one projection exp(dt A) U, here
+    # of a seeded random state (every mode present).  The solver's estimate
+    # dt h_{m+1,m} |e_m^T exp(dt H) e_1| / ||exp(dt H) e_1|| against the
+    # oracle's from its own Arnoldi process: tiny where M = 20 converges
+    # (dt rho(A) ~ 6), equal to the oracle's where the projection is short
+    # of convergence, and large (the result lost) at dt rho(A) ~ 6e4, M = 8
+    from scipy.linalg import expm
+    base, idx, S, kap, A = _heat2d_dense()
+    U0 = np.random.default_rng(12).standard_normal(idx.dof)
+    prob = Problem(dict(base, dt=dt, M=M), sgkiif.SGK_FP64)
+    prob.reset()
+    prob.solver.set_state(0, U0)
+    prob.solver.step(1)
+    st = prob.solver.stats()
+    got = prob.state()[0]
+    prob.close()
+    est = st["last_krylov_err_est"]
+    assert est == st["max_krylov_err_est"]
+    V, H, gamma, m = arnoldi_cgs2(lambda x: sparse_matvec(idx, S, kap, x), U0, M)
+    want_est = krylov_error_estimate(H, m, dt)
+    err = rel(got, expm(dt * A) @ U0)
+    if want_est < 1e-8:
+        assert est < 1e-8 and err < 1e-10
+    elif dt < 1.0:
+        assert abs(est - want_est) <= 1e-6 * want_est
+        assert err <= est
+    else:
+        assert est > 1e-2 and err > 1e-2
+
+
+@pytest.mark.parametrize("sub", [1, 4, 16])
+def test_krylov_substeps_match_oracle(ctx64, sub):
+    # exp(dt A) v as `sub` successive projections of dt/sub (d 2, level 5,
+    # degree 1, M = 8 at dt rho(A) ~ 240: one projection is far from
+    # converged, 16 are close)
+    d, n, k, M, dt = 2, 5, 1, 8, 0.1
+    kap = [1.0, 1.0]
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    op = sgkiif.Operator(ctx64, idx, kap)
+    sol = sgkiif.Solver(ctx64, [op], [[]], M, dt)
+    sol.set_krylov_substeps(sub)
+    v = np.random.default_rng(3).standard_normal(idx.dof)
+    vd = dev(v)
+    wd = torch.empty_like(vd)
+    m_eff = sol.krylov_expv(0, vd.data_ptr(), wd.data_ptr())
+    ref = OIndex(d, n, k)
+    want, m_ref = krylov_expv_substeps(lambda x: sparse_matvec(ref, sipg_1d(n, k), kap, x), v, dt, M, sub)
+    assert m_eff == m_ref
+    assert rel(wd.cpu().numpy(), want) <= 1e-10
+    sol.close()
+    op.close()
+    idx.close()
+
+
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_iif2_steps_with_substeps_match_oracle(precision):
+    # cubic 3D (level 3, degree 2) with every exponential taken as 4
+    # sub-projections, against the oracle's IIF2 with the same sub-projections
+    cfg = workloads.cubic3d(n=3, k=2)
+    nsteps, sub = 3, 4
+    prob = Problem(cfg, precision)
+    prob.solver.set_krylov_substeps(sub)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(nsteps)
+    got = prob.state()
+    st = prob.solver.stats()
+    prob.close()
+    idx = OIndex(cfg["d"], cfg["n"], cfg["k"])
+    ref = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                     substeps=sub)
+    want = ref.run(U0, nsteps)
+    assert rel(got[0], want[0]) <= (1e-10 if precision == sgkiif.SGK_FP64 else 1e-6)
+    assert st["steps"] == nsteps and np.isfinite(st["max_krylov_err_est"])
+
+
+def test_substeps_lower_the_krylov_error_estimate():
+    # heat2d at dt rho(A) ~ 60 with M = 8: one projection is off by ~0.2;
+    # 8 and 64 sub-projections bring the error and the estimate (the largest
+    # over the sub-projections) down together
+    from scipy.linalg import expm
+    base, idx, S, kap, A = _heat2d_dense()
+    U0 = np.random.default_rng(12).standard_normal(idx.dof)
+    dt = 1e-3
+    want = expm(dt * A) @ U0
+    out = []
+    for sub in (1, 8, 64):
+        prob = Problem(dict(base, dt=dt, M=8), sgkiif.SGK_FP64)
+        prob.solver.set_krylov_substeps(sub)
+        prob.reset()
+        prob.solver.set_state(0, U0)
+        prob.solver.step(1)
+        out.append((prob.solver.stats()["last_krylov_err_est"], rel(prob.state()[0], want)))
+        prob.close()
+    assert out[0][1] > 1e-2 and out[-1][1] < 1e-8
+    for (e0, r0), (e1, r1) in zip(out, out[1:]):
+        assert e1 < e0 and r1 < r0
+
+
+# -------------------------------------------------------- measured peaks ---
+
+def test_alu_peak_probe_is_plausible():
+    # the FMA probe behind the ALU rooflines: this part's FP32 pipe issues
+    # 128 FMAs per SM per cycle (about 80 TFLOP/s at 2 GHz on 152 SMs) and its
+    # FP64 pipe about 1/64 of that; bounds wide enough for any clock state
+    f32 = sgkiif.alu_peak(0, "fp32")
+    f64 = sgkiif.alu_peak(0, "fp64")
+    assert 30e12 < f32 < 100e12
+    assert 0.3e12 < f64 < 3e12
+    assert f64 < f32 / 8
 
 
 # ---------------------------------------------------------- error paths ---

@@ -80,6 +80,27 @@ def test_linear_reaction_closed_form():
     assert sol.stats["newton"] == [1]
 
 
+def test_linear_reaction_closed_form_with_substeps():
+    # the same closed form with a Krylov dimension far below the space's
+    # (M = 8 of 80) at dt rho(A) ~ 16: one projection misses it by ~1e-3,
+    # 64 sub-projections of dt/64 (exp(dt A) = exp((dt/64) A)^64) reach it
+    idx = IndexSet(2, 3, 1)
+    S = sipg_1d(3, 1)
+    kap = [1.0, 0.7]
+    b, dt = 40.0, 1e-3
+    U0 = np.random.default_rng(2).standard_normal(idx.dof)
+    E = sla.expm(dt * dense_sparse_operator(idx, S, kap))
+    ref = E @ ((1 - b * dt / 2) * U0) / (1 + b * dt / 2)
+    errs = {}
+    for sub in (1, 64):
+        sol = IIF2Solver(idx, S, [kap], [[(-b, (1,))]], dt, 8, substeps=sub)
+        U1 = sol.run([U0], 1)[0]
+        errs[sub] = np.linalg.norm(U1 - ref) / np.linalg.norm(ref)
+        assert sol.stats["m_eff"] == [8]
+    assert errs[1] > 1e-4
+    assert errs[64] < 1e-11
+
+
 def test_example1_against_table4():
     d = 2
     errs = []

@@ -19,7 +19,8 @@ import scipy.linalg as sla
 
 from oracle.basis import alpert_coefficients, gauss_legendre, hier_eval
 from oracle.index_set import IndexSet
-from oracle.krylov import arnoldi_cgs2, expm_pade13, krylov_expv, pade_coefficients
+from oracle.krylov import (arnoldi_cgs2, expm_pade13, krylov_error_estimate, krylov_expv, krylov_expv_substeps,
+                           pade_coefficients)
 from oracle.operator import dense_sparse_operator, sipg_1d, sparse_matvec
 from oracle.projection import project_separable
 from oracle.reaction import Reaction
@@ -83,6 +84,60 @@ def test_krylov_full_dimension_is_exact():
     w, m_eff = krylov_expv(lambda x: sparse_matvec(idx, S, kap, x), v, dt, idx.dof)
     ref = sla.expm(dt * A) @ v
     assert np.linalg.norm(w - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_krylov_substeps_converge_to_the_exponential():
+    # exp(dt A) = exp((dt/s) A)^s: with M = 8 fixed, one projection at
+    # dt rho(A) ~ 16 is off by ~1e-2 while 64 sub-projections of dt/64 reach
+    # the dense exponential to rounding; the error falls with every
+    # refinement (each sub-span's projection converges superlinearly)
+    idx, S, A, kap = _heat_setup(2, 3, 1)
+    assert idx.dof == 80
+    mv = lambda x: sparse_matvec(idx, S, kap, x)  # noqa: E731
+    v = np.random.default_rng(3).standard_normal(idx.dof)
+    dt = 1e-3
+    ref = sla.expm(dt * A) @ v
+    w1, m1 = krylov_expv(mv, v, dt, 8)
+    ws, ms = krylov_expv_substeps(mv, v, dt, 8, 1)
+    assert np.array_equal(w1, ws) and m1 == ms == 8
+    errs = [np.linalg.norm(krylov_expv_substeps(mv, v, dt, 8, s)[0] - ref) / np.linalg.norm(ref)
+            for s in (1, 4, 16, 64)]
+    assert errs[0] > 1e-3
+    assert all(b < a / 10 for a, b in zip(errs, errs[1:]))
+    assert errs[-1] <= 1e-12
+
+
+@pytest.mark.parametrize("dt,M", [(1e-3, 8), (1e-3, 20), (1e-2, 30), (5e-3, 30), (2e-4, 12)])
+def test_krylov_error_estimate_bounds_the_error(dt, M):
+    # on this dissipative operator the estimate lies above the true error of
+    # the projection against the dense exponential, by less than two orders
+    # of magnitude, across converged and unconverged spans
+    idx, S, A, kap = _heat_setup(2, 4, 1, (1.0, 1.0))
+    mv = lambda x: sparse_matvec(idx, S, kap, x)  # noqa: E731
+    v = np.random.default_rng(12).standard_normal(idx.dof)
+    V, H, gamma, m = arnoldi_cgs2(mv, v, M)
+    w, _ = krylov_expv(mv, v, dt, M)
+    ref = sla.expm(dt * A) @ v
+    err = np.linalg.norm(w - ref) / np.linalg.norm(ref)
+    est = krylov_error_estimate(H, m, dt)
+    assert err > 1e-9  # every case here is short of convergence
+    assert err <= est <= 100 * err
+
+
+def test_krylov_error_estimate_vanishes_on_breakdown_and_converges():
+    idx, S, A, kap = _heat_setup(2, 3, 2)
+    mv = lambda x: sparse_matvec(idx, S, kap, x)  # noqa: E731
+    v = np.zeros(idx.dof)
+    v[0] = 2.5
+    V, H, gamma, m = arnoldi_cgs2(mv, v, 20)
+    assert m == 1 and krylov_error_estimate(H, m, 0.1) <= 1e-12
+    v = np.random.default_rng(4).standard_normal(idx.dof)
+    ests = []
+    for M in (4, 8, 16, 32):
+        V, H, gamma, m = arnoldi_cgs2(mv, v, M)
+        ests.append(krylov_error_estimate(H, m, 1e-4))
+    assert all(b < a for a, b in zip(ests, ests[1:]))
+    assert ests[-1] < 1e-12
 
 
 def test_krylov_breakdown_on_constant_mode():
