@@ -643,7 +643,7 @@ def matvec_leg(peaks, peak_kind):
 
 # ------------------------------------------------------- conditioning ---
 
-def fp64_sensitivity(cfg, steps, seed=31):
+def fp64_sensitivity(cfg, steps, seed=31, substeps=1):
     """Relative change of the FP64 GPU result after `steps` IIF2 steps when
     the initial state is perturbed by 1e-14 relative (seeded): how far
     rounding at that level moves the answer of this instance."""
@@ -653,6 +653,7 @@ def fp64_sensitivity(cfg, steps, seed=31):
     outs = []
     for perturb in (False, True):
         p = Problem(cfg, sgkiif.SGK_FP64)
+        p.solver.set_krylov_substeps(substeps)
         p.reset()
         if perturb:
             for s_ in range(p.nspecies):
@@ -662,6 +663,29 @@ def fp64_sensitivity(cfg, steps, seed=31):
         outs.append(np.concatenate(p.state()))
         p.close()
     return float(np.linalg.norm(outs[1] - outs[0]) / max(np.linalg.norm(outs[0]), 1e-300))
+
+
+def with_substeps(cfg, steps, substeps):
+    """The instance solved alone in both precisions with every exponential
+    taken as `substeps` sub-projections: mixed vs FP64, the FP64 result's
+    sensitivity to a 1e-14 input perturbation, and the largest Krylov error
+    estimate of the FP64 run."""
+    from paper_1810_11111_gb300 import sgkiif
+    from paper_1810_11111_gb300.runner import Problem
+    outs, est = {}, None
+    for prec in (sgkiif.SGK_FP64, sgkiif.SGK_MIXED):
+        p = Problem(cfg, prec)
+        p.solver.set_krylov_substeps(substeps)
+        p.reset()
+        p.solver.step(steps)
+        outs[prec] = np.concatenate(p.state())
+        if prec == sgkiif.SGK_FP64:
+            est = p.solver.stats()["max_krylov_err_est"]
+        p.close()
+    f, m = outs[sgkiif.SGK_FP64], outs[sgkiif.SGK_MIXED]
+    return {"substeps": substeps, "krylov_err_est": est,
+            "rel_l2_mixed_vs_fp64": float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300)),
+            "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(cfg, steps, substeps=substeps)}
 
 
 # ---------------------------------------------------------- batched leg ---
@@ -753,7 +777,9 @@ def batched_leg(args, dist=None, rank=0, world=1):
                                 "above_1e-6_well_conditioned": int((errs[well] > 1e-6).sum()),
                                 "ill_conditioned": [{"instance": int(i), "rel_l2_mixed_vs_fp64": float(errs[i]),
                                                      "fp64_change_under_1e-14_input_perturbation": float(sens[i]),
-                                                     "krylov_err_est": float(kest[i])}
+                                                     "krylov_err_est": float(kest[i]),
+                                                     "with_substeps": [with_substeps(insts[i], 1 + steps, sub)
+                                                                       for sub in (8, 64)]}
                                                     for i in np.nonzero(ill)[0]],
                                 "note": "per instance after the timed steps; every instance above 1e-6 is "
                                         "solved again alone in FP64 from its initial state perturbed by 1e-14 "
@@ -864,7 +890,8 @@ def served_leg(args):
     over = [i for i, e in enumerate(errs) if e > 1e-6]
     ill = [{"request": i, "rel_l2_mixed_vs_fp64": errs[i],
             "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(reqs[i], reqs[i]["steps"]),
-            "krylov_err_est": kest.get(i)}
+            "krylov_err_est": kest.get(i),
+            "with_substeps": [with_substeps(reqs[i], reqs[i]["steps"], sub) for sub in (8, 64)]}
            for i in over]
     first = by_rate["%gx" % rates[0]] if rates else sat
     base64 = summary(lat64, wall64) if not args.served_no_fp64 else None
