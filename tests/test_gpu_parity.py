@@ -434,25 +434,29 @@ def test_reaction_and_jacobian_fp64(ctx64, d, n, k, rx):
     idx.close()
 
 
-@pytest.mark.parametrize("d,n,k", [(3, 3, 2), (3, 1, 2), (4, 3, 1), (2, 5, 2)])
-def test_reaction_fp32(ctx32, d, n, k):
-    rx = workloads.reaction_terms(workloads.CUBIC, 100.0)
+@pytest.mark.parametrize("d,n,k,rx", RX_CASES)
+def test_reaction_mixed(ctx32, d, n, k, rx):
+    # mixed mode: F in double-float arithmetic on the fused pencil shapes
+    # (FP64 elsewhere), the Jacobian product in FP32
+    S = len(rx)
     idx = sgkiif.IndexSet(ctx32, d, n, k)
-    op = sgkiif.Operator(ctx32, idx, [1.0] * d)
-    sol = sgkiif.Solver(ctx32, [op], rx, 10, 0.01)
+    ops = [sgkiif.Operator(ctx32, idx, [1.0] * d) for _ in range(S)]
+    sol = sgkiif.Solver(ctx32, ops, rx, 10, 0.01)
     rng = np.random.default_rng(6)
-    U = 0.3 * rng.standard_normal(idx.dof)
-    W = rng.standard_normal(idx.dof)
-    Ud, Wd = dev(U), dev(W)
+    U = [(1.0 if s == 0 else 0.9) * (np.arange(idx.dof) == 0) + 0.3 * rng.standard_normal(idx.dof)
+         for s in range(S)]
+    W = [rng.standard_normal(idx.dof) for _ in range(S)]
+    Ud, Wd = dev(np.concatenate(U)), dev(np.concatenate(W))
     Fd, Jd = torch.empty_like(Ud), torch.empty_like(Ud)
     sol.reaction_eval(Ud.data_ptr(), Fd.data_ptr())
     sol.jacobian_apply(Ud.data_ptr(), Wd.data_ptr(), Jd.data_ptr())
     torch.cuda.synchronize()
     R = Reaction(OIndex(d, n, k), rx)
-    assert rel(Fd.cpu().numpy(), R.F([U])[0]) <= 1e-5
-    assert rel(Jd.cpu().numpy(), R.J([U], [W])[0]) <= 1e-5
+    assert rel(Fd.cpu().numpy(), np.concatenate(R.F(U))) <= 1e-12
+    assert rel(Jd.cpu().numpy(), np.concatenate(R.J(U, W))) <= 1e-5
     sol.close()
-    op.close()
+    for o in ops:
+        o.close()
     idx.close()
 
 
