@@ -347,6 +347,20 @@ int sgk_solver_get_time(const sgk_solver* s, double* t);
  * SGK_EINVAL (null, substeps out of range), SGK_ENOMEM. */
 #define SGK_MAX_KRYLOV_SUBSTEPS 64
 int sgk_solver_set_krylov_substeps(sgk_solver* s, int substeps);
+/* Accuracy guard on the Krylov projections (an extension, as above).  With
+ * tol > 0, every synchronous sgk_solver_step compares the a-posteriori
+ * estimate of its projections (sgk_stats) with tol and, while it is larger
+ * and the sub-projections number less than max_substeps, doubles them (as
+ * sgk_solver_set_krylov_substeps, kept for the following steps) and takes
+ * the step's exponentials again: IIF2 steps run as one graph restart from
+ * their starting state, the host-driven steps (systems, IIF3 and higher)
+ * redo their exponentials before the Newton stage.  The count of doublings
+ * is sgk_stats.krylov_refinements.  Queued steps (sgk_solver_step_async),
+ * batches and the server report the estimate without acting on it.  tol = 0
+ * turns the guard off (the default).  Drains queued steps.  Errors:
+ * SGK_EINVAL (null, tol negative or not finite, max_substeps outside
+ * 1..SGK_MAX_KRYLOV_SUBSTEPS). */
+int sgk_solver_set_krylov_tolerance(sgk_solver* s, double tol, int max_substeps);
 
 typedef struct sgk_stats {
     int64_t steps;           /* steps taken since creation */
@@ -365,6 +379,8 @@ typedef struct sgk_stats {
      * how far that M is from converged without changing the method. */
     double last_krylov_err_est;
     double max_krylov_err_est;  /* the largest of those over all steps taken */
+    int krylov_substeps;        /* sub-projections per exponential now (1: the paper's method) */
+    int64_t krylov_refinements; /* times the accuracy guard doubled them */
 } sgk_stats;
 int sgk_solver_stats(const sgk_solver* s, sgk_stats* out);
 

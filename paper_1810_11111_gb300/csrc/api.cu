@@ -574,6 +574,7 @@ int sgk_solver_stats(const sgk_solver* s, sgk_stats* out) {
         set_device(s->ctx);
         solver_drain(const_cast<sgk_solver*>(s));
         *out = s->stats;
+        out->krylov_substeps = s->ksub;
         return SGK_OK;
     });
 }
@@ -644,6 +645,20 @@ int sgk_solver_set_krylov_substeps(sgk_solver* s, int substeps) {
         set_device(s->ctx);
         solver_drain(s);
         solver_set_krylov_substeps(s, substeps);
+        return SGK_OK;
+    });
+}
+
+int sgk_solver_set_krylov_tolerance(sgk_solver* s, double tol, int max_substeps) {
+    if (!s) return SGK_EINVAL;
+    return guarded(s->ctx, [&]() {
+        SGK_REQUIRE(std::isfinite(tol) && tol >= 0.0, SGK_EINVAL, "krylov tolerance must be finite and >= 0");
+        SGK_REQUIRE(max_substeps >= 1 && max_substeps <= SGK_MAX_KRYLOV_SUBSTEPS, SGK_EINVAL,
+                    "max substeps must be 1..SGK_MAX_KRYLOV_SUBSTEPS");
+        set_device(s->ctx);
+        solver_drain(s);
+        s->ktol = tol;
+        s->kmax = max_substeps;
         return SGK_OK;
     });
 }

@@ -58,6 +58,11 @@ struct sgk_solver {
     // paper's single projection); ktmp is their intermediate vector
     int ksub = 1;
     DevBuf<double> ktmp;
+    // accuracy guard of synchronous steps: while the step's estimate is
+    // above ktol (> 0), its exponentials are taken again with twice the
+    // sub-projections, up to kmax
+    double ktol = 0.0;
+    int kmax = 1;
     DevBuf<unsigned> counters;
     DevBuf<unsigned> fcnt;  // arrival counters of the fused Newton / CG kernels (zero between launches)
     // persistent Arnoldi: second work vector, partial sums, per species a

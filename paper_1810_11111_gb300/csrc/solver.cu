@@ -786,6 +786,7 @@ void solver_krylov_expv(sgk_solver* s, int species, const double* v, double* W, 
 
 void solver_set_krylov_substeps(sgk_solver* s, int ksub) {
     if (ksub > 1 && s->ktmp.n < (size_t)s->n) s->ktmp.alloc(s->n);
+    s->stats.krylov_substeps = ksub;
     if (ksub != s->ksub) {
         s->ksub = ksub;
         drop_graphs(s);
@@ -1203,14 +1204,35 @@ namespace {
 
 }  // namespace
 
+// The accuracy guard of synchronous steps: true when the projections just
+// taken missed the tolerance and the sub-projections can still be doubled
+// (doubles them)
+static bool krylov_refine(sgk_solver* s) {
+    if (!(s->ktol > 0.0) || !(s->stats.last_krylov_err_est > s->ktol) || s->ksub >= s->kmax) return false;
+    solver_set_krylov_substeps(s, std::min(2 * s->ksub, s->kmax));
+    s->stats.krylov_refinements += 1;
+    return true;
+}
+
 int solver_step(sgk_solver* s, int nsteps) {
     sgk_ctx* ctx = s->ctx;
     if (solver_device_steps(s)) {
+        const long long N = s->n * s->nspecies;
         for (int step = 0; step < nsteps; ++step) {
-            solver_step_launch(s);
-            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
-            const int rc = solver_step_finish(s);
-            if (rc != SGK_OK) return rc;
+            for (;;) {
+                solver_step_launch(s);
+                SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+                const int rc = solver_step_finish(s);
+                if (rc != SGK_OK) return rc;
+                if (!krylov_refine(s)) break;
+                // take the step again from its starting state (an IIF2 step
+                // keeps no history beyond U and t)
+                SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                               ctx->stream));
+                solver_state_changed(s);
+                s->t -= s->dt;
+                s->stats.steps -= 1;
+            }
         }
         return SGK_OK;
     }
@@ -1223,7 +1245,6 @@ int solver_step(sgk_solver* s, int nsteps) {
     };
     for (int step = 0; step < nsteps; ++step) {
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->Uprev.p, s->U.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        krylov_est_clear(s);
         write_time(s);
         // IIFr (eqs. krylov3, krylov4) at the highest order r the history
         // allows: W = exp(dt A)(U^n + alpha_0 dt F(U^n)) + sum_{i=1}^{r-2}
@@ -1251,19 +1272,36 @@ int solver_step(sgk_solver* s, int nsteps) {
                                                ctx->stream));
             }
         });
-        for (int sp = 0; sp < s->nspecies; ++sp) {
-            run_graph(s, s->g_krylov[sp], KC_KRYLOV,
-                      [&]() { solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n); });
-            s->stats.krylov_calls += s->use_graphs ? 1 : 0;
-        }
-        for (int i = 1; i <= r - 2; ++i)
+        // the step's exponentials; with the accuracy guard on, taken again
+        // with twice the sub-projections while their estimate misses the
+        // tolerance (nothing of the state has changed yet)
+        for (;;) {
+            krylov_est_clear(s);
             for (int sp = 0; sp < s->nspecies; ++sp) {
-                run_graph(s, s->g_krylovh[sp][i - 1], KC_KRYLOV, [&]() {
-                    solver_krylov_expv(s, sp, s->Fhist.p + (i - 1) * N + sp * n, s->W2.p + sp * n, (i + 1) * s->dt);
-                    vk_axpby(ctx, 1.0, s->W.p + sp * n, alpha[i + 1] * s->dt, s->W2.p + sp * n, s->W.p + sp * n, n);
-                });
+                run_graph(s, s->g_krylov[sp], KC_KRYLOV,
+                          [&]() { solver_krylov_expv(s, sp, s->vv.p + sp * n, s->W.p + sp * n); });
                 s->stats.krylov_calls += s->use_graphs ? 1 : 0;
             }
+            for (int i = 1; i <= r - 2; ++i)
+                for (int sp = 0; sp < s->nspecies; ++sp) {
+                    run_graph(s, s->g_krylovh[sp][i - 1], KC_KRYLOV, [&]() {
+                        solver_krylov_expv(s, sp, s->Fhist.p + (i - 1) * N + sp * n, s->W2.p + sp * n,
+                                           (i + 1) * s->dt);
+                        vk_axpby(ctx, 1.0, s->W.p + sp * n, alpha[i + 1] * s->dt, s->W2.p + sp * n,
+                                 s->W.p + sp * n, n);
+                    });
+                    s->stats.krylov_calls += s->use_graphs ? 1 : 0;
+                }
+            if (!(s->ktol > 0.0)) break;
+            KrylovScalars kq[SGK_MAX_SPECIES];
+            SGK_CUDA_CHECK(cudaMemcpyAsync(kq, s->ks.p, s->nspecies * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+            SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            s->stats.last_krylov_err_est = 0.0;
+            for (int sp = 0; sp < s->nspecies; ++sp)
+                s->stats.last_krylov_err_est = std::max(s->stats.last_krylov_err_est, kq[sp].err_max);
+            if (!krylov_refine(s)) break;
+        }
         // F(U^n) becomes F(U^{n-1}) of the next step if this one succeeds
         if (r_full > 2)
             SGK_CUDA_CHECK(
@@ -1349,6 +1387,7 @@ void iif_alpha(int r, double* alpha) {
 void solver_alloc(sgk_solver* s) {
     const long long n = s->n, S = s->nspecies, N = n * S;
     const int M = s->M;
+    s->stats.krylov_substeps = s->ksub;
     s->U.alloc(N);
     s->Uprev.alloc(N);
     s->W.alloc(N);

@@ -42,7 +42,8 @@ class sgk_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("newton_iters", ctypes.c_int64), ("inner_iters", ctypes.c_int64),
                 ("krylov_calls", ctypes.c_int64), ("krylov_breakdowns", ctypes.c_int64),
                 ("last_m_eff", ctypes.c_int), ("last_newton_residual", ctypes.c_double),
-                ("last_krylov_err_est", ctypes.c_double), ("max_krylov_err_est", ctypes.c_double)]
+                ("last_krylov_err_est", ctypes.c_double), ("max_krylov_err_est", ctypes.c_double),
+                ("krylov_substeps", ctypes.c_int), ("krylov_refinements", ctypes.c_int64)]
 
 
 class sgk_init(ctypes.Structure):
@@ -118,6 +119,7 @@ _SIGS = {
     "sgk_solver_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
     "sgk_solver_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "sgk_solver_set_krylov_substeps": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sgk_solver_set_krylov_tolerance": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int]),
     "sgk_solver_stats": (ctypes.c_int, [_P, ctypes.POINTER(sgk_stats)]),
     "sgk_reaction_eval": (ctypes.c_int, [_P, _P, _P]),
     "sgk_jacobian_apply": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -355,6 +357,11 @@ class Solver:
         """exp(tau A) v as `substeps` successive projections of tau/substeps
         (1: the paper's single projection)."""
         self.ctx.check(sgk_solver_set_krylov_substeps(self.h, int(substeps)))
+
+    def set_krylov_tolerance(self, tol, max_substeps=64):
+        """Accuracy guard of synchronous steps: double the sub-projections
+        while the step's Krylov estimate is above tol (0: off)."""
+        self.ctx.check(sgk_solver_set_krylov_tolerance(self.h, float(tol), int(max_substeps)))
 
     def get_time(self):
         t = ctypes.c_double()

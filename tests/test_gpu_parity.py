@@ -1087,6 +1087,60 @@ def test_iif2_steps_with_substeps_match_oracle(precision):
     assert st["steps"] == nsteps and np.isfinite(st["max_krylov_err_est"])
 
 
+@pytest.mark.parametrize("precision", [sgkiif.SGK_FP64, sgkiif.SGK_MIXED])
+def test_krylov_tolerance_guard_refines_to_the_oracle(precision):
+    # heat2d at dt rho(A) ~ 60 with M = 8 (one graph per IIF2 step): the
+    # guard doubles the sub-projections until the step's estimate meets
+    # 1e-6, retaking the step from its starting state; the result is the
+    # oracle's product of that many projections and within the tolerance of
+    # the dense exponential
+    from scipy.linalg import expm
+    base, idx, S, kap, A = _heat2d_dense()
+    U0 = np.random.default_rng(12).standard_normal(idx.dof)
+    dt, M = 1e-3, 8
+    prob = Problem(dict(base, dt=dt, M=M), precision)
+    prob.solver.set_krylov_tolerance(1e-6, 64)
+    prob.reset()
+    prob.solver.set_state(0, U0)
+    prob.solver.step(1)
+    st = prob.solver.stats()
+    got = prob.state()[0]
+    t = prob.solver.get_time()
+    prob.close()
+    sub = st["krylov_substeps"]
+    assert sub in (2, 4, 8, 16, 32, 64) and st["krylov_refinements"] == int(np.log2(sub))
+    assert st["steps"] == 1 and abs(t - dt) < 1e-15
+    assert st["last_krylov_err_est"] <= 1e-6
+    want, _ = krylov_expv_substeps(lambda x: sparse_matvec(idx, S, kap, x), U0, dt, M, sub)
+    assert rel(got, want) <= (1e-10 if precision == sgkiif.SGK_FP64 else 1e-6)
+    assert rel(got, expm(dt * A) @ U0) <= 1e-6
+
+
+@pytest.mark.parametrize("scheme", [sgkiif.SGK_IIF2, sgkiif.SGK_IIF3])
+def test_krylov_tolerance_guard_on_host_driven_steps(scheme):
+    # a two-species system (GMRES; host-driven steps): the guard redoes the
+    # step's exponentials before the Newton stage; one step against the
+    # oracle with the sub-projections the guard settled on
+    cfg = dict(workloads.schnak2d(n=5, k=1, steps=1, seed=45), scheme=scheme)
+    prob = Problem(cfg, sgkiif.SGK_FP64)
+    prob.solver.set_krylov_tolerance(1e-9, 64)
+    prob.reset()
+    U0 = [u.cpu().numpy() for u in prob.U0]
+    prob.solver.step(1)
+    st = prob.solver.stats()
+    got = prob.state()
+    prob.close()
+    sub = st["krylov_substeps"]
+    assert sub > 1 and st["krylov_refinements"] == int(np.log2(sub))
+    assert st["last_krylov_err_est"] <= 1e-9 or sub == 64
+    idx = OIndex(cfg["d"], cfg["n"], cfg["k"])
+    ref = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                     substeps=sub)
+    want = ref.run(U0, 1)
+    for g, w in zip(got, want):
+        assert rel(g, w) <= 1e-10
+
+
 def test_substeps_lower_the_krylov_error_estimate():
     # heat2d at dt rho(A) ~ 60 with M = 8: one projection is off by ~0.2;
     # 8 and 64 sub-projections bring the error and the estimate (the largest
