@@ -355,9 +355,12 @@ int sgk_solver_set_krylov_substeps(sgk_solver* s, int substeps);
  * the step's exponentials again: IIF2 steps run as one graph restart from
  * their starting state, the host-driven steps (systems, IIF3 and higher)
  * redo their exponentials before the Newton stage.  The count of doublings
- * is sgk_stats.krylov_refinements.  Queued steps (sgk_solver_step_async),
- * batches and the server report the estimate without acting on it.  tol = 0
- * turns the guard off (the default).  Drains queued steps.  Errors:
+ * is sgk_stats.krylov_refinements.  Batches and the server apply it to the
+ * instances and requests that set sgk_request.krylov_tol: a rolled-back step
+ * is taken again in the next batch step, which then still gives every
+ * instance its nsteps steps.  Queued steps (sgk_solver_step_async) report
+ * the estimate without acting on it.  tol = 0 turns the guard off (the
+ * default).  Drains queued steps.  Errors:
  * SGK_EINVAL (null, tol negative or not finite, max_substeps outside
  * 1..SGK_MAX_KRYLOV_SUBSTEPS). */
 int sgk_solver_set_krylov_tolerance(sgk_solver* s, double tol, int max_substeps);
@@ -488,6 +491,8 @@ typedef struct sgk_request {
     int nsteps;              /* >= 0 IIF2 steps */
     int precision;           /* SGK_FP64 | SGK_MIXED */
     sgk_init init[SGK_MAX_SPECIES];
+    double krylov_tol;       /* > 0: the Krylov accuracy guard (sgk_solver_set_krylov_tolerance); 0: off */
+    int krylov_max_substeps; /* its limit, 1 .. SGK_MAX_KRYLOV_SUBSTEPS (ignored when krylov_tol = 0) */
 } sgk_request;
 
 typedef struct sgk_result_info {
@@ -595,14 +600,18 @@ typedef struct sgk_batch sgk_batch;
 
 /* Errors: SGK_EINVAL, SGK_ECUDA (no such device or stream creation failed). */
 int sgk_batch_create(int device, int nstreams, int slice_len, sgk_batch** out);
-/* Add an instance described by req (its nsteps is ignored); host arrays are
- * read during the call.  *index receives the instance number (0, 1, ...).
- * Errors: as sgk_index_build / sgk_operator_assemble / sgk_solver_create. */
+/* Add an instance described by req (its nsteps is ignored; its krylov_tol
+ * and krylov_max_substeps set the instance's accuracy guard); host arrays
+ * are read during the call.  *index receives the instance number (0, 1,
+ * ...).  Errors: as sgk_index_build / sgk_operator_assemble /
+ * sgk_solver_create / sgk_solver_set_krylov_tolerance. */
 int sgk_batch_add(sgk_batch* b, const sgk_request* req, int* index);
 /* Take nsteps steps of every active instance.  status (may be NULL) receives
  * per instance the status of its last step; an instance whose step fails is
- * rolled back to the start of that step and takes no further steps.  Returns
- * SGK_OK if every instance succeeded, else the first failing status. */
+ * rolled back to the start of that step and takes no further steps.  A step
+ * that an instance's accuracy guard rolls back is taken again in a later
+ * batch step of the same call.  Returns SGK_OK if every instance succeeded,
+ * else the first failing status. */
 int sgk_batch_step(sgk_batch* b, int nsteps, int* status);
 int64_t sgk_batch_dof(const sgk_batch* b, int index);
 int sgk_batch_count(const sgk_batch* b);

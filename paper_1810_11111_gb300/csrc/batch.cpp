@@ -132,7 +132,10 @@ void batch_core_tick(BatchCore& core, const std::vector<sgk_solver*>& sols, std:
         }
     }
     for (cudaStream_t st : core.streams) SGK_CUDA_CHECK(cudaStreamSynchronize(st));
-    for (int i : queued) status[i] = solver_step_finish(sols[i]);
+    for (int i : queued) {
+        status[i] = solver_step_finish(sols[i]);
+        if (status[i] == SGK_OK && solver_step_retake(sols[i])) status[i] = BATCH_STEP_RETAKE;
+    }
     for (size_t i = 0; i < sols.size(); ++i)
         if (!solver_device_steps(sols[i])) status[i] = sgk_solver_step(sols[i], 1);
 }
@@ -187,6 +190,10 @@ int sgk_batch_add(sgk_batch* b, const sgk_request* q, int* index) {
     if (rc != SGK_OK) return rc;
     rc = sgk_solver_create(in->ctx, S, in->ops, &q->reaction, SGK_IIF2, q->krylov_m, q->dt, nullptr, &in->sol);
     if (rc != SGK_OK) return rc;
+    if (q->krylov_tol != 0.0) {
+        rc = sgk_solver_set_krylov_tolerance(in->sol, q->krylov_tol, q->krylov_max_substeps);
+        if (rc != SGK_OK) return rc;
+    }
     try {
         DevBuf<double> u0(dof);
         for (int s = 0; s < S && rc == SGK_OK; ++s) {
@@ -222,18 +229,25 @@ int sgk_batch_step(sgk_batch* b, int nsteps, int* status) {
     cudaSetDevice(b->device);
     int first = SGK_OK;
     try {
-        for (int step = 0; step < nsteps; ++step) {
+        // steps left per instance: a step the accuracy guard rolled back is
+        // taken again in the next tick
+        std::vector<int> left(b->inst.size(), nsteps);
+        for (;;) {
             std::vector<sgk_solver*> sols;
-            std::vector<Instance*> act;
-            for (auto& in : b->inst)
-                if (in->status == SGK_OK) {
-                    sols.push_back(in->sol);
-                    act.push_back(in.get());
+            std::vector<size_t> act;
+            for (size_t i = 0; i < b->inst.size(); ++i)
+                if (b->inst[i]->status == SGK_OK && left[i] > 0) {
+                    sols.push_back(b->inst[i]->sol);
+                    act.push_back(i);
                 }
             if (sols.empty()) break;
             std::vector<int> st;
             batch_core_tick(b->core, sols, st);
-            for (size_t i = 0; i < act.size(); ++i) act[i]->status = st[i];
+            for (size_t k = 0; k < act.size(); ++k) {
+                if (st[k] == BATCH_STEP_RETAKE) continue;
+                b->inst[act[k]]->status = st[k];
+                left[act[k]] -= 1;
+            }
         }
     } catch (const SgkError& e) {
         return e.code;

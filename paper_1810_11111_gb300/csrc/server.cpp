@@ -52,6 +52,8 @@ struct Req {
     int64_t ticket = 0;
     int d = 0, n = 0, k = 0, S = 1, bc = SGK_PERIODIC, M = 0, nsteps = 0, prec = SGK_FP64;
     double dt = 0.0;
+    double ktol = 0.0;  // Krylov accuracy guard (0: off) and its limit
+    int kmax = 1;
     std::vector<double> kappa;  // S x d
     int nmono = 0;
     std::vector<int> rx_species, rx_exps;
@@ -234,6 +236,7 @@ int run_request(sgk_ctx* ctx, Req& r, std::string& err) {
         f.coef = r.rx_coef.data();
         f.exps = r.rx_exps.data();
         rc = chk(sgk_solver_create(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, &sol));
+        if (rc == SGK_OK && r.ktol > 0.0) rc = chk(sgk_solver_set_krylov_tolerance(sol, r.ktol, r.kmax));
     }
     const int64_t dof = idx ? idx->dof : 0;
     if (rc == SGK_OK) {
@@ -372,6 +375,7 @@ int engine_setup(int device, cudaStream_t st, Live& L, std::string& err, int num
         f.coef = r.rx_coef.data();
         f.exps = r.rx_exps.data();
         rc = chk(sgk_solver_create(L.ctx, 1, &L.op, &f, SGK_IIF2, r.M, r.dt, nullptr, &L.sol));
+        if (rc == SGK_OK && r.ktol > 0.0) rc = chk(sgk_solver_set_krylov_tolerance(L.sol, r.ktol, r.kmax));
     }
     if (rc != SGK_OK) return rc;
     const InitCopy& in = r.init[0];
@@ -484,6 +488,7 @@ void sgk_server::engine() {
         // leave: finished or failed requests
         for (size_t i = 0; i < live.size(); ++i) {
             std::unique_ptr<Live>& L = live[i];
+            if (status[i] == BATCH_STEP_RETAKE) continue;  // the step is taken again next tick
             if (status[i] == SGK_OK) ++L->done;
             if (status[i] != SGK_OK || L->done >= L->r->nsteps) {
                 std::string err = tick_err;
@@ -583,7 +588,9 @@ int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
     if (S < 1 || S > SGK_MAX_SPECIES || q->d < 1 || q->d > SGK_MAX_DIM || q->n < 0 || q->n > SGK_MAX_LEVEL ||
         q->k < 1 || q->k > 3 || q->krylov_m < 1 || q->krylov_m > SGK_MAX_KRYLOV || !(q->dt > 0) || q->nsteps < 0 ||
         !q->kappa || (q->precision != SGK_FP64 && q->precision != SGK_MIXED) ||
-        (q->bc != SGK_PERIODIC && q->bc != SGK_DIRICHLET0))
+        (q->bc != SGK_PERIODIC && q->bc != SGK_DIRICHLET0) || !std::isfinite(q->krylov_tol) ||
+        q->krylov_tol < 0.0 ||
+        (q->krylov_tol > 0.0 && (q->krylov_max_substeps < 1 || q->krylov_max_substeps > SGK_MAX_KRYLOV_SUBSTEPS)))
         return SGK_EINVAL;
     if (q->reaction.nmono < 0 || q->reaction.nmono > SGK_MAX_MONO ||
         (q->reaction.nmono > 0 &&
@@ -599,6 +606,8 @@ int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
     r->dt = q->dt;
     r->nsteps = q->nsteps;
     r->prec = q->precision;
+    r->ktol = q->krylov_tol;
+    r->kmax = q->krylov_tol > 0.0 ? q->krylov_max_substeps : 1;
     r->kappa.assign(q->kappa, q->kappa + (size_t)S * q->d);
     r->nmono = q->reaction.nmono;
     if (r->nmono > 0) {

@@ -31,11 +31,17 @@ struct BatchCore {
     int init(int device, int nstreams);
 };
 
+// Status of a solver's step in a tick whose Krylov accuracy guard asked for
+// more sub-projections: the step was rolled back (state, time and step
+// count as before it) and is to be taken again in the next tick
+constexpr int BATCH_STEP_RETAKE = -1;
+
 // One step of every solver in sols, each on its context's stream (one of
 // core.streams): the split ones (solver_split_eligible, batched-Arnoldi
 // class) share the batched Arnoldi launches between their pre- and
 // post-Krylov graphs; other device-driven ones take whole-step graphs; the
 // host-driven ones step alone after the others.  status[i] receives the
-// status of solver i's step (a failed step is rolled back by the solver).
+// status of solver i's step (a failed step is rolled back by the solver;
+// BATCH_STEP_RETAKE: rolled back by the accuracy guard).
 // The host waits for every stream once.  Throws SgkError on CUDA errors.
 void batch_core_tick(BatchCore& core, const std::vector<sgk_solver*>& sols, std::vector<int>& status);

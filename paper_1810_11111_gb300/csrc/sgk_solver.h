@@ -129,6 +129,10 @@ void solver_set_state(sgk_solver* s, int species, const double* src_dev);
 // to roll back to on failure (null: the step graph's own copy)
 void solver_step_launch(sgk_solver* s, int slot = 0);
 int solver_step_finish(sgk_solver* s, int slot = 0, const double* restore = nullptr);
+// After a successful device-driven step finished by solver_step_finish: if
+// the Krylov accuracy guard wants more sub-projections (and doubles them),
+// the step is rolled back (state, time, step count) and true is returned.
+bool solver_step_retake(sgk_solver* s);
 // The same device-driven step with its Arnoldi process run by the caller
 // (one species, persistent Arnoldi): solver_step_launch_pre queues the state
 // copy, the predictor and v = U + dt/2 F(U); the caller then runs the

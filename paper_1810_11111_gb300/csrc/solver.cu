@@ -1214,25 +1214,28 @@ static bool krylov_refine(sgk_solver* s) {
     return true;
 }
 
+bool solver_step_retake(sgk_solver* s) {
+    if (!krylov_refine(s)) return false;
+    // back to the step's starting state (a device-driven IIF2 step keeps no
+    // history beyond U and t)
+    SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, s->n * s->nspecies * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   s->ctx->stream));
+    solver_state_changed(s);
+    s->t -= s->dt;
+    s->stats.steps -= 1;
+    return true;
+}
+
 int solver_step(sgk_solver* s, int nsteps) {
     sgk_ctx* ctx = s->ctx;
     if (solver_device_steps(s)) {
-        const long long N = s->n * s->nspecies;
         for (int step = 0; step < nsteps; ++step) {
-            for (;;) {
+            do {
                 solver_step_launch(s);
                 SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
                 const int rc = solver_step_finish(s);
                 if (rc != SGK_OK) return rc;
-                if (!krylov_refine(s)) break;
-                // take the step again from its starting state (an IIF2 step
-                // keeps no history beyond U and t)
-                SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->Uprev.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
-                                               ctx->stream));
-                solver_state_changed(s);
-                s->t -= s->dt;
-                s->stats.steps -= 1;
-            }
+            } while (solver_step_retake(s));
         }
         return SGK_OK;
     }

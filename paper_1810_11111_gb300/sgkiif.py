@@ -55,7 +55,8 @@ class sgk_request(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int), ("nspecies", ctypes.c_int),
                 ("bc", ctypes.c_int), ("kappa", _c_double_p), ("reaction", sgk_reaction),
                 ("krylov_m", ctypes.c_int), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
-                ("precision", ctypes.c_int), ("init", sgk_init * MAX_SPECIES)]
+                ("precision", ctypes.c_int), ("init", sgk_init * MAX_SPECIES),
+                ("krylov_tol", ctypes.c_double), ("krylov_max_substeps", ctypes.c_int)]
 
 
 class sgk_result_info(ctypes.Structure):
@@ -476,6 +477,8 @@ class Server:
         q.kappa = _dptr(kap)
         q.reaction = rx
         q.krylov_m, q.dt, q.nsteps, q.precision = int(cfg["M"]), float(cfg["dt"]), int(cfg["steps"]), int(precision)
+        q.krylov_tol = float(cfg.get("krylov_tol", 0.0))
+        q.krylov_max_substeps = int(cfg.get("krylov_max_substeps", 64))
         if init_coeffs is None and any("noise_seed" in i for i in cfg["init"]):
             from .workloads import coefficient_noise
             init_coeffs = coefficient_noise(cfg["init"][0]["noise_seed"], dof_of(d, cfg["n"], cfg["k"]), S,

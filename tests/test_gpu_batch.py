@@ -93,3 +93,35 @@ def test_batched_launch_with_more_instances_than_sms():
     b = run_batch(8, 2, fused=False, instances=many)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_batch_accuracy_guard_matches_guarded_solver():
+    # instances with the Krylov accuracy guard (M = 10, tolerance 1e-9, at
+    # most 32 sub-projections): a step the guard rolls back is taken again
+    # in a later tick, every instance still takes its 3 steps, and each
+    # equals the same problem stepped alone with the guard, having settled
+    # on the same sub-projection count
+    insts = [(dict(cubic(2, 6, 1, 60 + i, 20.0 + 10 * i), M=10, krylov_tol=1e-9, krylov_max_substeps=32), prec)
+             for i, prec in enumerate([sgkiif.SGK_MIXED, sgkiif.SGK_FP64, sgkiif.SGK_MIXED])]
+    insts.append((cubic(3, 4, 2, 63), sgkiif.SGK_MIXED))  # no guard: stays in the batched Arnoldi launch
+    b = sgkiif.Batch(0, streams=3)
+    for cfg, prec in insts:
+        b.add(cfg, prec)
+    rc, st = b.step(3)
+    assert rc == sgkiif.SGK_OK and all(x == sgkiif.SGK_OK for x in st)
+    got = [np.concatenate(b.state(i)) for i in range(len(insts))]
+    bst = [b.stats(i) for i in range(len(insts))]
+    b.close()
+    for (cfg, prec), g, sb in zip(insts, got, bst):
+        p = Problem(cfg, prec)
+        if cfg.get("krylov_tol"):
+            p.solver.set_krylov_tolerance(cfg["krylov_tol"], cfg["krylov_max_substeps"])
+        p.reset()
+        p.solver.step(3)
+        want = np.concatenate(p.state())
+        ps = p.solver.stats()
+        p.close()
+        assert sb["steps"] == ps["steps"] == 3
+        assert sb["krylov_substeps"] == ps["krylov_substeps"]
+        assert (sb["krylov_substeps"] > 1) == bool(cfg.get("krylov_tol"))
+        assert rel(g, want) <= (1e-10 if prec == sgkiif.SGK_FP64 else 1e-6)

@@ -143,3 +143,39 @@ def test_engine_admits_requests_while_stepping():
         assert info["queue_ms"] < 50.0
         assert s1 * 1e3 + info["latency_ms"] < done_long
         assert rel(out, direct(c, sgkiif.SGK_MIXED)) <= 1e-6
+
+
+def test_accuracy_guard_through_engine_and_workers():
+    # requests that set the Krylov accuracy guard (M = 10, tolerance 1e-9):
+    # through the engine (a rolled-back step is taken again in the next tick)
+    # and through the workers (synchronous steps), each equals the problem
+    # stepped alone with the guard and reports all its steps
+    reqs = [(dict(cubic(2, 6, 1, 4 + i, 70 + i), M=10, krylov_tol=1e-9, krylov_max_substeps=32), prec)
+            for i, prec in enumerate([sgkiif.SGK_MIXED, sgkiif.SGK_FP64])]
+
+    def guarded(cfg, prec):
+        p = Problem(cfg, prec)
+        p.solver.set_krylov_tolerance(cfg["krylov_tol"], cfg["krylov_max_substeps"])
+        p.reset()
+        p.solver.step(cfg["steps"])
+        out = np.concatenate(p.state())
+        p.close()
+        return out
+
+    for engine in (True, False):
+        srv = sgkiif.Server(0, workers=2, engine=engine)
+        res = [srv.wait(srv.submit(c, p), cap=4 * sgkiif.dof_of(c["d"], c["n"], c["k"])) for c, p in reqs]
+        srv.close()
+        for (c, p), (out, info) in zip(reqs, res):
+            assert info["status"] == sgkiif.SGK_OK and info["steps"] == c["steps"]
+            assert (info["worker"] == -1) == engine
+            assert rel(out, guarded(c, p)) <= (1e-10 if p == sgkiif.SGK_FP64 else 1e-6)
+
+
+def test_request_guard_fields_are_validated():
+    srv = sgkiif.Server(0, workers=1)
+    bad = dict(cubic(2, 4, 1, 2, 80), krylov_tol=1e-6, krylov_max_substeps=0)
+    with pytest.raises(sgkiif.SgkError) as e:
+        srv.submit(bad, sgkiif.SGK_FP64)
+    assert e.value.code == sgkiif.SGK_EINVAL
+    srv.close()
