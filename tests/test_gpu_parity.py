@@ -1191,6 +1191,43 @@ def test_invalid_arguments_are_rejected(ctx64):
     idx.close()
 
 
+def test_krylov_accuracy_settings_are_validated(ctx64):
+    idx = sgkiif.IndexSet(ctx64, 2, 3, 1)
+    op = sgkiif.Operator(ctx64, idx, [1.0, 1.0])
+    sol = sgkiif.Solver(ctx64, [op], [[]], 8, 0.01)
+    h = sol.h
+    for sub in (0, -1, 65):
+        assert sgkiif.sgk_solver_set_krylov_substeps(h, sub) == sgkiif.SGK_EINVAL
+    for tol, mx in ((-1e-6, 8), (float("nan"), 8), (float("inf"), 8), (1e-6, 0), (1e-6, 65)):
+        assert sgkiif.sgk_solver_set_krylov_tolerance(h, tol, mx) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_solver_set_krylov_substeps(None, 2) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_solver_set_krylov_tolerance(None, 1e-6, 8) == sgkiif.SGK_EINVAL
+    # the largest count is accepted
+    sol.set_krylov_substeps(64)
+    assert sol.stats()["krylov_substeps"] == 64
+    sol.close()
+    op.close()
+    idx.close()
+    # the breakdown of projections that span the whole space (dimension 32 <
+    # M = 40) gives an estimate of exactly zero, and the product of such
+    # (exact) projections is the oracle's
+    idx = sgkiif.IndexSet(ctx64, 2, 2, 1)
+    op = sgkiif.Operator(ctx64, idx, [1.0, 1.0])
+    sol = sgkiif.Solver(ctx64, [op], [[]], 40, 0.01)
+    sol.set_krylov_substeps(4)
+    v = np.random.default_rng(9).standard_normal(idx.dof)
+    sol.set_state(0, v)
+    sol.step(1)
+    st = sol.stats()
+    assert idx.dof == 32 and st["last_krylov_err_est"] == 0.0 and st["krylov_breakdowns"] >= 1
+    ref = OIndex(2, 2, 1)
+    want, _ = krylov_expv_substeps(lambda x: sparse_matvec(ref, sipg_1d(2, 1), [1.0, 1.0], x), v, 0.01, 40, 4)
+    assert rel(sol.get_state(0), want) <= 1e-10
+    sol.close()
+    op.close()
+    idx.close()
+
+
 def test_newton_failure_rolls_back():
     # one Newton correction cannot reach a residual of 1e-300
     cfg = dict(workloads.cubic3d(n=3, k=1), opts={"max_iter": 1, "tol": 1e-300})
