@@ -122,6 +122,29 @@ def test_matvec_fp64(ctx64, d, n, k, bc):
     idx.close()
 
 
+@pytest.mark.parametrize("d,n,k,bc", [(4, 9, 3, PERIODIC), (4, 8, 2, PERIODIC), (3, 9, 3, DIRICHLET0)])
+def test_matvec_fp64_at_the_largest_served_shapes(ctx64, d, n, k, bc):
+    # the largest served shape (d 4, level 9, degree 3: 6.8 M coefficients,
+    # an operator beyond 2^24 entries, so the gather walks the CSR rows),
+    # the largest batched one and a Dirichlet one, in the launch the bench
+    # times; every output against the oracle
+    idx = sgkiif.IndexSet(ctx64, d, n, k)
+    kap = [1.0, 0.5, 0.1, 0.7][:d]
+    op = sgkiif.Operator(ctx64, idx, kap, bc)
+    x = np.random.default_rng(d * 100 + n + k).standard_normal(idx.dof)
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    op.matvec(xd.data_ptr(), yd.data_ptr(), sgkiif.SGK_FP64)
+    torch.cuda.synchronize()
+    got = yd.cpu().numpy()
+    op.close()
+    idx.close()
+    want = sparse_matvec(OIndex(d, n, k), sipg_1d(n, k, bc), kap, x)
+    assert got.size == want.size == sgkiif.dof_of(d, n, k)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    assert rel(got, want) <= 1e-12
+
+
 @pytest.mark.parametrize("d,n,k,bc", MATVEC_CASES)
 def test_matvec_madds_count(ctx64, d, n, k, bc):
     # the operator's multiply-add count: for every coefficient and direction,
@@ -304,7 +327,11 @@ def _krylov_problem(ctx, d, n, k, M, reaction=None):
 
 
 @pytest.mark.parametrize("d,n,k,M", [(2, 4, 1, 20), (3, 4, 2, 30), (2, 6, 1, 40), (1, 3, 1, 8), (3, 6, 2, 30),
-                                     (2, 8, 2, 40), (4, 3, 1, 64)])
+                                     (2, 8, 2, 40), (4, 3, 1, 64),
+                                     # the largest batched and served shapes:
+                                     # slices too long for shared memory, so
+                                     # V, Z and the gathers go through L2
+                                     (4, 8, 2, 10), (4, 9, 3, 8)])
 def test_krylov_expv_fp64(ctx64, d, n, k, M):
     idx = sgkiif.IndexSet(ctx64, d, n, k)
     kap = [1.0, 0.5, 0.1, 0.7][:d]
