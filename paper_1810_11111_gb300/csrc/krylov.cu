@@ -23,7 +23,6 @@ namespace {
 
 constexpr double THETA13 = 5.371920351148152;  // Higham (2005), Table 2.3
 
-__device__ __forceinline__ double warp_sum(double v) { return warp_sum_f64(v); }
 __device__ __forceinline__ double block_sum(double v, double* sh) { return block_sum_f64(v, sh); }
 
 template <typename TA, typename TB>
@@ -128,35 +127,6 @@ __global__ void scale_vec_kernel(const T* __restrict__ x, T* __restrict__ y, lon
     const T a = (T)(*s);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = x[i] * a;
-}
-
-// Column j of H from the two Gram-Schmidt passes, the norm of the remainder,
-// the breakdown test and 1 / h_{j+1,j}.
-__global__ void arnoldi_finalize_kernel(int j, int M, const double* __restrict__ h1, const double* __restrict__ h2,
-                                        const double* __restrict__ wnorm2, double* __restrict__ H,
-                                        KrylovScalars* __restrict__ ks) {
-    if (ks->stop) return;
-    double f = ks->fro2;
-    if (j >= 1) {
-        const double sub = H[(long long)j * M + (j - 1)];
-        f += sub * sub;
-    }
-    for (int i = 0; i <= j; ++i) {
-        const double v = h1[i] + h2[i];
-        H[(long long)i * M + j] = v;
-        f += v * v;
-    }
-    ks->fro2 = f;
-    const double beta = sqrt(*wnorm2);
-    H[(long long)(j + 1) * M + j] = beta;
-    if (beta <= 1e-12 * sqrt(f)) {
-        ks->m_eff = j + 1;
-        ks->stop = 1;
-        ks->breakdown = 1;
-    } else {
-        ks->inv_beta = 1.0 / beta;
-        ks->m_eff = j + 1;
-    }
 }
 
 // ------------------------------------------- fused Gram-Schmidt kernels ---

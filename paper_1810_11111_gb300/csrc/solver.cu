@@ -582,7 +582,6 @@ KrylovWork<T> krylov_work(sgk_solver* s, int species) {
 }
 
 void cg_solve(sgk_solver* s, const double* G, double* x, int& iters) {
-    sgk_ctx* ctx = s->ctx;
     const long long N = s->n * s->nspecies;
     double* r = s->cg_r.p;
     double* pv = s->cg_p.p;
