@@ -131,40 +131,11 @@ __global__ void scale_vec_kernel(const T* __restrict__ x, T* __restrict__ y, lon
 
 // ------------------------------------------- fused Gram-Schmidt kernels ---
 //
-// FP64 adds have a 64-cycle dependent latency on this GPU, so reductions
-// keep several independent chains per thread: up to CH column sums at once,
-// reduced over the warp with interleaved shuffles.  Each kernel ends its
-// grid-wide reduction in the last block to finish (a counter in global
-// memory); that block sums the per-block partials in a fixed order, so the
-// result is deterministic.
-
-constexpr int CH = 8;
-
-// Block-wide sums of CH values per thread; results valid in threads 0..CH-1
-// (thread j holds the sum of value j).  sh: CH * 32 doubles.
-__device__ __forceinline__ void block_sum_multi(double (&v)[CH], double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int j = 0; j < CH; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < CH; ++j) sh[j * 32 + wid] = v[j];
-    __syncthreads();
-    if (threadIdx.x < CH) {
-        double a = 0.0, b = 0.0;
-        int w = 0;
-        for (; w + 1 < nw; w += 2) {
-            a += sh[threadIdx.x * 32 + w];
-            b += sh[threadIdx.x * 32 + w + 1];
-        }
-        if (w < nw) a += sh[threadIdx.x * 32 + w];
-        v[0] = a + b;
-    }
-    __syncthreads();
-}
+// FP64 adds have a long dependent latency on this GPU, so reductions keep
+// several independent chains per thread.  Each kernel ends its grid-wide
+// reduction in the last block to finish (a counter in global memory); that
+// block sums the per-block partials in a fixed order, so the result is
+// deterministic.
 
 // Each block owns GS_E consecutive elements (one per thread), stages the
 // (updated) vector slice in shared memory, and gives every warp whole
