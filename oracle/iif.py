@@ -34,7 +34,8 @@ the paper is silent:
   * initial guess U = W;
   * Newton matrix I - dt/2 J_F(U), J_F(U) w = P(f'(u_h) w_h);
   * inner solver: conjugate gradients for a scalar equation (the matrix is
-    symmetric), restarted GMRES(50) with Givens rotations for systems; both
+    symmetric), restarted GMRES(50) with Givens rotations for systems and
+    for the interpolation form of F (module interp: J is not symmetric); both
     start from 0 and stop at relative residual INNER_TOL or INNER_MAX steps;
   * outer stop relative to the scale of the stage: ||G(U)||_2 <= NEWTON_TOL
     max(||W||_2, ||G(W)||_2) (the second term only matters when W = 0), at
@@ -45,6 +46,7 @@ the paper is silent:
 """
 import numpy as np
 
+from .interp import InterpReaction
 from .krylov import BREAKDOWN_TOL, krylov_expv_substeps
 from .operator import sparse_matvec
 from .reaction import Reaction
@@ -137,19 +139,25 @@ def gmres(apply, b, tol=INNER_TOL, maxit=INNER_MAX, restart=GMRES_RESTART):
 class IIF2Solver:
     """Sparse-grid Krylov IIF2 DG solver (Sections 2-3)."""
 
-    def __init__(self, idx, S, kappas, reaction, dt, M, sources=None, t0=0.0, substeps=1):
+    def __init__(self, idx, S, kappas, reaction, dt, M, sources=None, t0=0.0, substeps=1,
+                 reaction_form="quadrature"):
         """S: 1D SIPG matrix; kappas: per species, a length-d diagonal;
         sources: per species a list of (lambda, S_m) pairs (the source
         P s(., t) = sum_m e^{lambda t} S_m), or None; t0: the time of the
         state passed to run(); substeps: every exponential as that many
-        successive projections (an extension; 1 is the paper's method)."""
+        successive projections (an extension; 1 is the paper's method);
+        reaction_form: "quadrature" (the paper's finest-grid F, module
+        reaction) or "interp" (the sparse-grid interpolation form of module
+        interp, a deviation from the paper)."""
         self.idx, self.S, self.dt, self.M = idx, S, dt, M
         self.substeps = int(substeps)
         self.kappas = [np.asarray(k, dtype=np.float64) for k in kappas]
         self.nspecies = len(self.kappas)
         self.reaction = reaction
         self.has_reaction = any(len(t) for t in reaction)
-        self.rx = Reaction(idx, reaction) if self.has_reaction else None
+        assert reaction_form in ("quadrature", "interp")
+        rx_cls = InterpReaction if reaction_form == "interp" else Reaction
+        self.rx = rx_cls(idx, reaction) if self.has_reaction else None
         self.sources = sources if sources is not None else [[] for _ in range(self.nspecies)]
         self.has_source = any(len(t) for t in self.sources)
         self.has_F = self.has_reaction or self.has_source
@@ -200,7 +208,7 @@ class IIF2Solver:
                 Jx = self.J(U, xs)
                 return np.concatenate([xs[s] - dt2 * Jx[s] for s in range(self.nspecies)])
 
-            if self.nspecies == 1:
+            if self.nspecies == 1 and getattr(self.rx, "symmetric", True):
                 delta, inner = cg(apply, -G)
             else:
                 delta, inner = gmres(apply, -G)
