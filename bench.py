@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-matvec", action="store_true", help="skip the large stand-alone matvec leg")
     ap.add_argument("--no-iif3", action="store_true", help="skip the IIF3 leg")
     ap.add_argument("--no-schnak", action="store_true", help="skip the two-species 200-step leg")
+    ap.add_argument("--no-sparse-reaction", action="store_true",
+                    help="skip the legs of the sparse-grid interpolation form of the reaction term")
     ap.add_argument("--served-no-fp64", action="store_true",
                     help="skip the FP64 one-at-a-time baseline of the served leg (and its accuracy check)")
     ap.add_argument("--served-rates", default="1",
@@ -487,10 +489,16 @@ def native(args, rank, world, local_rank):
         leg("iif3", lambda: iif3_leg(cfg, args))
     if world == 1 and not args.no_schnak:
         leg("schnak2d", lambda: schnak_leg(args))
+    if world == 1 and not args.no_sparse_reaction:
+        leg("sparse_reaction", lambda: guarded_leg(sparse_reaction_leg, cfg, args, peaks, peak_kind))
     if args.batch_instances > 0:
         leg("batched", lambda: batched_leg(args, dist, rank, world))
     if world == 1 and args.served_requests > 0:
         leg("served", lambda: served_leg(args))
+    if world == 1 and args.served_requests > 0 and not args.no_sparse_reaction:
+        leg("served_sparse_reaction", lambda: guarded_leg(served_sparse_leg, args))
+    if world == 1 and args.batch_instances > 0 and not args.no_sparse_reaction:
+        leg("batched_sparse_reaction", lambda: guarded_leg(batched_sparse_leg, args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         leg("cpu_baseline", lambda: cpu_baseline(cfg, args.steps))
     out["leg_wall_s"] = legs
@@ -540,6 +548,179 @@ def iif3_leg(cfg, args):
     den = sum(float(np.sum(states["fp64"][s] ** 2)) for s in range(len(states["fp64"])))
     out["rel_l2_mixed_vs_fp64"] = float(np.sqrt(num / den))
     return out
+
+
+
+# ------------------------------- sparse-grid interpolation form of F ---
+
+def guarded_leg(fn, *a):
+    """A leg of the interpolation form; an exception is reported in the
+    line instead of ending the run."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def sparse_reaction_leg(cfg, args, peaks, peak_kind):
+    """The headline workload with the sparse-grid interpolation form of the
+    reaction term (SGK_REACTION_INTERP: F_I = C^{-1} f(C U) by 4d direction
+    passes, the implicit stage solved pointwise at the collocation points; a
+    deviation from the paper's finest-grid F for its first stated future
+    direction).  K steps from the initial state, queued, device-timed with the
+    L2 flushed before each, in both precisions; accuracy against the
+    oracle's stored run of the same form (tests/golden/cubic3d_interp_steps.npz),
+    and its distance to the paper's form (the quadrature oracle's state): the
+    difference between the two discretisations, not an error of either."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif
+    from paper_1810_11111_gb300.runner import Problem
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    ci = dict(cfg, reaction_form="interp")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {"workload": "as the headline, reaction term in the sparse-grid interpolation form", "steps": args.steps}
+    states, prof = {}, None
+    for name, prec in (("mixed", sgkiif.SGK_MIXED), ("fp64", sgkiif.SGK_FP64)):
+        prob = Problem(ci, prec)
+        prob.reset()
+        prob.solver.step(1)
+        prob.reset()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        l0 = prob.ctx.launches
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            prob.solver.step_async(1)
+            ev[i][1].record(stream)
+        prob.solver.wait()
+        torch.cuda.synchronize(dev)
+        tot = sum(a.elapsed_time(b) for a, b in ev)
+        launches = prob.ctx.launches - l0
+        states[name] = prob.state()
+        st = prob.solver.stats()
+        out[name] = {"ms_per_step": tot / args.steps,
+                     "dof_steps_per_s": prob.dof * prob.nspecies * args.steps / (tot / 1e3),
+                     "gpu_launches": launches, "pointwise_newton_corrections": st["newton_iters"]}
+        if name == "mixed":
+            # kernel classes over the same steps, each launch event-timed
+            prob.ctx.profile(0xFF)
+            prob.reset()
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                prob.solver.step(1)
+            torch.cuda.synchronize(dev)
+            kp = prob.ctx.profile_read()
+            prob.ctx.profile(0)
+            names = {"to_finest": "to_points", "from_finest": "from_points", "cell_quadrature": "point_kernels"}
+            prof = {names.get(c, c): (v[0] / args.steps, v[1] / args.steps) for c, v in kp.items() if v[1] > 0}
+        prob.close()
+    out["kernel_ms_per_step"] = {c: round(v[0], 4) for c, v in prof.items()}
+    # the transform passes: algorithmic bytes of one direction pass = read and
+    # write the vectors it maps (DOF x 8 B each way per vector); latency-bound
+    # at this size (the vectors stay in L2)
+    dof = sgkiif.dof_of(cfg["d"], cfg["n"], cfg["k"])
+    tp_ms = prof.get("to_points", (0, 0))[0] + prof.get("from_points", (0, 0))[0]
+    tp_n = prof.get("to_points", (0, 0))[1] + prof.get("from_points", (0, 0))[1]
+    out["transform_passes"] = {"ms_per_step": tp_ms, "launch_groups_per_step": tp_n,
+                               "dof": dof, "passes_per_application": 2 * cfg["d"]}
+    for key, golden, form in (("rel_l2_vs_oracle", "cubic3d_interp_steps.npz", "interp"),
+                              ("rel_l2_vs_quadrature_form_oracle", "cubic3d_steps.npz", "quadrature")):
+        path = os.path.join(ROOT, "tests", "golden", golden)
+        out[key] = None
+        if os.path.exists(path):
+            g = np.load(path)
+            k = "U%d" % args.steps
+            if k in g.files:
+                out[key] = {p: float(np.linalg.norm(states[p][0] - g[k][0]) / np.linalg.norm(g[k][0]))
+                            for p in states}
+    out["note"] = ("rel_l2_vs_quadrature_form_oracle is the distance between the two discretisations of F "
+                   "(interpolation error of f(u_h) amplified over the steps), not a parity figure")
+    return out
+
+
+def served_sparse_leg(args):
+    """The served draws (seed 4) with the interpolation form of F and no
+    finest-grid cap: every draw is admitted (the form holds only sparse-grid
+    vectors).  All requests submitted at t = 0 (the server's capacity) and
+    one at a time; mixed precision."""
+    from paper_1810_11111_gb300 import sgkiif, workloads
+    reqs, rejected = workloads.served_requests(count=args.served_requests, seed=4, max_nodal_bytes=float("inf"))
+    reqs = [dict(r, reaction_form="interp") for r in reqs]
+    work = [sgkiif.dof_of(r["d"], r["n"], r["k"]) * len(r["kappas"]) * r["steps"] for r in reqs]
+    caps = [4 * sgkiif.dof_of(r["d"], r["n"], r["k"]) for r in reqs]
+    fails = []
+
+    def run(workers, at_once):
+        srv = sgkiif.Server(0, workers=workers, engine=True)
+        t0 = time.perf_counter()
+        lat = []
+        if at_once:
+            tickets = [srv.submit(r, sgkiif.SGK_MIXED) for r in reqs]
+            infos = [srv.wait(t, cap=c)[1] for t, c in zip(tickets, caps)]
+        else:
+            infos = [srv.wait(srv.submit(r, sgkiif.SGK_MIXED), cap=c)[1] for r, c in zip(reqs, caps)]
+        wall = time.perf_counter() - t0
+        for info in infos:
+            lat.append(info["latency_ms"])
+            if info["status"] != sgkiif.SGK_OK:
+                fails.append("status %d: %s" % (info["status"], info["error"]))
+        st = srv.stats()
+        srv.close()
+        lat = np.sort(np.asarray(lat))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "dof_steps_per_s": float(sum(work) / wall), "wall_s": wall, "max_concurrent": st["max_concurrent"]}
+
+    srv = sgkiif.Server(0, workers=1)
+    for r in reqs:  # first-use costs of every shape
+        srv.wait(srv.submit(dict(r, steps=1), sgkiif.SGK_MIXED))
+    srv.close()
+    sat = run(args.served_workers, True)
+    one = run(1, False)
+    return {"workload": "served draws (seed 4, %d requests; d 3-4, level 6-9, degree 1-3, cubic or Schnakenberg, "
+                        "10-100 IIF2 steps) with the interpolation form of F; no finest-grid cap: %d of %d draws "
+                        "rejected" % (len(reqs), rejected, len(reqs) + rejected),
+            "largest_dof": max(sgkiif.dof_of(r["d"], r["n"], r["k"]) for r in reqs),
+            "dof_steps_total": int(sum(work)), "precision": "mixed", "saturation": sat, "one_at_a_time": one,
+            "saturation_vs_one_at_a_time": sat["dof_steps_per_s"] / one["dof_steps_per_s"],
+            "failed_requests": len(fails), "first_failure": fails[0] if fails else None}
+
+
+def batched_sparse_leg(args):
+    """The batch draws (seed 3, 256 instances) with the interpolation form of
+    F and no finest-grid cap (none rejected), one untimed step then 5 timed
+    batch steps, mixed precision; the FP64 run of the same batch gives the
+    per-instance mixed error."""
+    import torch
+    from paper_1810_11111_gb300 import sgkiif, workloads
+    insts, rejected = workloads.batch_instances(count=args.batch_instances, seed=3, max_nodal_bytes=float("inf"))
+    insts = [dict(c, reaction_form="interp") for c in insts]
+    work = sum(sgkiif.dof_of(c["d"], c["n"], c["k"]) for c in insts)
+    steps = 5
+    res, states = {}, {}
+    for name, prec in (("mixed", sgkiif.SGK_MIXED), ("fp64", sgkiif.SGK_FP64)):
+        b = sgkiif.Batch(0, streams=8)
+        for c in insts:
+            b.add(c, prec)
+        rc0, _ = b.step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = b.step(steps)
+        wall = time.perf_counter() - t0
+        states[name] = [np.concatenate(b.state(i)) for i in range(len(insts))]
+        res[name] = {"dof_steps_per_s": work * steps / wall, "wall_s": wall,
+                     "failed": sum(1 for x in st if x != sgkiif.SGK_OK), "status": max(rc0, rc),
+                     "batched_arnoldi_launches": b.launches()}
+        b.close()
+    errs = np.array([float(np.linalg.norm(m - f) / max(np.linalg.norm(f), 1e-300))
+                     for m, f in zip(states["mixed"], states["fp64"])])
+    return {"workload": "batch draws (seed 3, %d scalar cubic instances; d 2-4, level 5-8, degree 1-2) with the "
+                        "interpolation form of F; no finest-grid cap: %d rejected" % (len(insts), rejected),
+            "dof_total": work, "largest_dof": max(sgkiif.dof_of(c["d"], c["n"], c["k"]) for c in insts),
+            "steps": steps, "untimed_first_steps": 1, "mixed": res["mixed"], "fp64": res["fp64"],
+            "rel_l2_mixed_vs_fp64": {"median": float(np.median(errs)), "max": float(errs.max()),
+                                     "above_1e-6": int((errs > 1e-6).sum())},
+            "timing": "host wall clock around the batch steps"}
 
 
 # ------------------------------------------------- two-species leg ---

@@ -53,12 +53,18 @@ extern "C" {
 /* precision modes */
 #define SGK_FP64 0   /* all arithmetic in FP64 */
 #define SGK_MIXED 1  /* solvers: the Jacobian products J_F(U) w of the
-                        Newton inner solve in FP32; the Krylov matvec in
+                        Newton inner solve, and the first residual of a step
+                        (which seeds the first correction and never accepts),
+                        in FP32; the Krylov matvec and every other F(U) (the
+                        predictor's and each accepting Newton residual's) in
                         double-float arithmetic (pairs of FP32 numbers, about
-                        48 significand bits); every F(U) (predictor and
-                        Newton residual), the Gram-Schmidt inner products and
-                        norms, exp(tau H), the state and the Newton residual
-                        in FP64.  sgk_matvec with SGK_MIXED is plain FP32. */
+                        48 significand bits; F in FP64 where the fused
+                        reaction kernel does not serve the shape); the
+                        Gram-Schmidt inner products and norms, exp(tau H), the
+                        state and the Newton residual vector in FP64.  The
+                        interpolation form of F (SGK_REACTION_INTERP) runs in
+                        FP64 in both modes.  sgk_matvec with SGK_MIXED is
+                        plain FP32. */
 
 /* boundary conditions (Section 2.1, eq. sp3) */
 #define SGK_PERIODIC 0
@@ -207,9 +213,20 @@ int sgk_matvec(const sgk_op* op, const void* x_dev, void* y_dev, int precision);
  * Per pair i < j the operator adds -K_ij times
  *   P x P^T + P^T x P - E x P^T - P^T x E - E^T x P - P x E^T
  * (factors along directions i and j).  Host-only (the matvec with these
- * terms is not provided yet); P and E are host arrays of cap >= H*H doubles.
- * n <= 10.  Errors: SGK_EINVAL (arguments), SGK_ENOMEM. */
+ * terms is sgk_operator_assemble_full's); P and E are host arrays of
+ * cap >= H*H doubles.  n <= 10.  Errors: SGK_EINVAL (arguments), SGK_ENOMEM. */
 int sgk_cross_blocks_1d(int n, int k, int bc, double* P, double* E, int64_t cap);
+
+/* The 1D factors of the collocation matrix of the sparse-grid interpolation
+ * form of the reaction term (SGK_REACTION_INTERP, see sgk_solver_create_form;
+ * not the paper's F) at level n, degree k (H = (k+1) 2^n), as a dense
+ * row-major H x H host array (cap >= H*H doubles):
+ *   which = 0: A      Alpert coefficients -> interpolation surpluses,
+ *           1: B      surpluses -> values at the collocation points,
+ *           2: B^{-1} values -> surpluses,
+ *           3: A^{-1} surpluses -> Alpert coefficients.
+ * Host-only, n <= 10.  Errors: SGK_EINVAL (arguments), SGK_ENOMEM. */
+int sgk_interp_factors_1d(int n, int k, int which, double* out, int64_t cap);
 
 /* ------------------------------------------------------------- projection */
 
@@ -279,6 +296,36 @@ typedef struct sgk_newton_opts {
  * out of range). */
 int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
                       int krylov_m, double dt, const sgk_newton_opts* opts, sgk_solver** out);
+
+/* Forms of the reaction term F(U) */
+#define SGK_REACTION_QUADRATURE 0 /* the paper's: the L2 projection of f(u_h) by
+                                     Gauss quadrature on the finest full grid
+                                     (Section 4), as sgk_solver_create */
+#define SGK_REACTION_INTERP 1     /* a deviation from the paper, for its first
+                                     stated future direction (Section 5: an
+                                     evaluation of the reaction integral that
+                                     uses the structure of the basis): the
+                                     Alpert coefficients of the sparse-grid
+                                     interpolant of f(u_h) on nested
+                                     collocation points, one per coefficient */
+
+/* sgk_solver_create with a choice of the reaction form.  With
+ * SGK_REACTION_INTERP, F_I(U) = C^{-1} f(C U), C the collocation matrix of
+ * the sparse set (u_h at the points), applied as 2d passes of 1D factors
+ * along the directions (sgk_interp_factors_1d); equal to the quadrature form
+ * for linear f, within an interpolation error of it otherwise.  It needs no
+ * finest full grid, so every shape whose sparse-grid vectors fit in device
+ * memory is accepted.  The implicit stage U - c F_I(U) = W becomes one
+ * equation per collocation point, u - c f(u) = (C W)_p, solved by Newton's
+ * method at each point to rounding (at most opts->max_iter corrections,
+ * else SGK_ENEWTON and the step is rolled back); sgk_stats counts the most
+ * corrections any point took per step, and no inner iterations.  The
+ * transforms and the point solve run in FP64 in both precision modes; IIF2
+ * steps with any species count run as one CUDA graph.  Errors as
+ * sgk_solver_create, and SGK_EINVAL for an unknown form. */
+int sgk_solver_create_form(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
+                           int krylov_m, double dt, const sgk_newton_opts* opts, int reaction_form,
+                           sgk_solver** out);
 int sgk_solver_destroy(sgk_solver* s);
 /* The weights of the r-th order IIF scheme (eq. krylov4) into alpha[0..r-1]:
  * alpha_1, alpha_0, alpha_{-1}, ..., alpha_{-(r-2)} (the integrals over one
@@ -493,6 +540,7 @@ typedef struct sgk_request {
     sgk_init init[SGK_MAX_SPECIES];
     double krylov_tol;       /* > 0: the Krylov accuracy guard (sgk_solver_set_krylov_tolerance); 0: off */
     int krylov_max_substeps; /* its limit, 1 .. SGK_MAX_KRYLOV_SUBSTEPS (ignored when krylov_tol = 0) */
+    int reaction_form;       /* SGK_REACTION_QUADRATURE (0, the paper's) | SGK_REACTION_INTERP */
 } sgk_request;
 
 typedef struct sgk_result_info {

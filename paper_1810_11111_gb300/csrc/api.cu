@@ -377,6 +377,25 @@ int sgk_cross_blocks_1d(int n, int k, int bc, double* P, double* E, int64_t cap)
     return SGK_OK;
 }
 
+int sgk_interp_factors_1d(int n, int k, int which, double* out, int64_t cap) {
+    if (!out || n < 0 || n > 10 || k < 1 || k > 3 || which < 0 || which > 3) return SGK_EINVAL;
+    const int64_t H = (int64_t)(k + 1) << n;
+    if (cap < H * H) return SGK_EINVAL;
+    try {
+        InterpFactors1D F;
+        build_interp_factors(n, k, F);
+        const Csr* M[4] = {&F.A, &F.B, &F.Binv, &F.Ainv};
+        std::memset(out, 0, sizeof(double) * H * H);
+        for (int a = 0; a < H; ++a)
+            for (int e = M[which]->ptr[a]; e < M[which]->ptr[a + 1]; ++e) out[a * H + M[which]->col[e]] = M[which]->val[e];
+    } catch (const SgkError& e) {
+        return e.code;
+    } catch (...) {
+        return SGK_ENOMEM;
+    }
+    return SGK_OK;
+}
+
 int sgk_matvec(const sgk_op* op, const void* x_dev, void* y_dev, int precision) {
     if (!op || !x_dev || !y_dev || x_dev == y_dev) return SGK_EINVAL;
     return guarded(op->ctx, [&]() {
@@ -426,8 +445,15 @@ int sgk_dirichlet_load(sgk_ctx* ctx, const sgk_index* idx, const double* kappa, 
 
 int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
                       int krylov_m, double dt, const sgk_newton_opts* opts, sgk_solver** out) {
+    return sgk_solver_create_form(ctx, nspecies, ops, f, scheme, krylov_m, dt, opts, SGK_REACTION_QUADRATURE, out);
+}
+
+int sgk_solver_create_form(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, const sgk_reaction* f, int scheme,
+                           int krylov_m, double dt, const sgk_newton_opts* opts, int reaction_form,
+                           sgk_solver** out) {
     if (!ctx || !ops || !out) return SGK_EINVAL;
     *out = nullptr;
+    if (reaction_form != SGK_REACTION_QUADRATURE && reaction_form != SGK_REACTION_INTERP) return SGK_EINVAL;
     return guarded(ctx, [&]() {
         SGK_REQUIRE(nspecies >= 1 && nspecies <= SGK_MAX_SPECIES, SGK_EINVAL, "nspecies must be in [1, 4]");
         SGK_REQUIRE(scheme >= SGK_IIF2 && scheme <= SGK_IIF_MAX_ORDER, SGK_EUNSUPPORTED,
@@ -491,7 +517,8 @@ int sgk_solver_create(sgk_ctx* ctx, int nspecies, const sgk_op* const* ops, cons
             if (opts->inner_max > 0) s->opts.inner_max = opts->inner_max;
             if (opts->gmres_restart > 0) s->opts.gmres_restart = std::min(opts->gmres_restart, SGK_MAX_KRYLOV);
         }
-        if (s->has_rx) {
+        s->rform = reaction_form;
+        if (s->has_rx && reaction_form != SGK_REACTION_INTERP) {
             const int p = reaction_degree(s->rx);
             const int k = idx->k;
             const int q = std::max(1, (p * k + k + 1 + 1) / 2);

@@ -188,7 +188,8 @@ int sgk_batch_add(sgk_batch* b, const sgk_request* q, int* index) {
     for (int s = 0; s < S && rc == SGK_OK; ++s)
         rc = sgk_operator_assemble(in->ctx, in->idx, q->kappa + (size_t)s * q->d, q->bc, 20.0, &in->ops[s]);
     if (rc != SGK_OK) return rc;
-    rc = sgk_solver_create(in->ctx, S, in->ops, &q->reaction, SGK_IIF2, q->krylov_m, q->dt, nullptr, &in->sol);
+    rc = sgk_solver_create_form(in->ctx, S, in->ops, &q->reaction, SGK_IIF2, q->krylov_m, q->dt, nullptr,
+                                q->reaction_form, &in->sol);
     if (rc != SGK_OK) return rc;
     if (q->krylov_tol != 0.0) {
         rc = sgk_solver_set_krylov_tolerance(in->sol, q->krylov_tol, q->krylov_max_substeps);

@@ -54,6 +54,7 @@ struct Req {
     double dt = 0.0;
     double ktol = 0.0;  // Krylov accuracy guard (0: off) and its limit
     int kmax = 1;
+    int form = SGK_REACTION_QUADRATURE;  // form of the reaction term
     std::vector<double> kappa;  // S x d
     int nmono = 0;
     std::vector<int> rx_species, rx_exps;
@@ -93,7 +94,12 @@ extern "C" double sgk_estimate_work(int d, int n, int k, int nspecies, int krylo
     // a row of the 1D matrix along one direction visits about 13 entries
     // (measured on the index sets of this library's workloads)
     double w = M * (2.0 * 13.0 * d * dof) + 4.0 * M * M * dof;
-    if (has_reaction) {
+    if (has_reaction == 2) {
+        // the interpolation form: per step about three applications of the
+        // collocation transforms (2d passes each of 1D rows of about (k+1)(n+2)
+        // entries) and the pointwise solve
+        w += 3.0 * 2.0 * (2.0 * d) * kp1 * (n + 2.0) * dof + 40.0 * dof;
+    } else if (has_reaction) {
         const double cells = std::pow(2.0, (double)n * d);
         const int q = 2 * k + 1;  // Gauss points of a cubic reaction, ceil((3k + k + 1) / 2)
         double per_cell = 0.0;  // sum-factorised stages, forward and back
@@ -235,7 +241,7 @@ int run_request(sgk_ctx* ctx, Req& r, std::string& err) {
         f.species = r.rx_species.data();
         f.coef = r.rx_coef.data();
         f.exps = r.rx_exps.data();
-        rc = chk(sgk_solver_create(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, &sol));
+        rc = chk(sgk_solver_create_form(ctx, r.S, ops, &f, SGK_IIF2, r.M, r.dt, nullptr, r.form, &sol));
         if (rc == SGK_OK && r.ktol > 0.0) rc = chk(sgk_solver_set_krylov_tolerance(sol, r.ktol, r.kmax));
     }
     const int64_t dof = idx ? idx->dof : 0;
@@ -374,7 +380,7 @@ int engine_setup(int device, cudaStream_t st, Live& L, std::string& err, int num
         f.species = r.rx_species.data();
         f.coef = r.rx_coef.data();
         f.exps = r.rx_exps.data();
-        rc = chk(sgk_solver_create(L.ctx, 1, &L.op, &f, SGK_IIF2, r.M, r.dt, nullptr, &L.sol));
+        rc = chk(sgk_solver_create_form(L.ctx, 1, &L.op, &f, SGK_IIF2, r.M, r.dt, nullptr, r.form, &L.sol));
         if (rc == SGK_OK && r.ktol > 0.0) rc = chk(sgk_solver_set_krylov_tolerance(L.sol, r.ktol, r.kmax));
     }
     if (rc != SGK_OK) return rc;
@@ -527,7 +533,12 @@ int64_t sgk_estimate_bytes(int d, int n, int k, int nspecies, int krylov_m, int 
     // partial sums of the Gram-Schmidt reductions)
     b += 8.0 * (4.0 * N + 2.0 * (M + 1.0) * dof + 128.0 + 3.0 * dof);
     b += 8.0 * (std::max(N / 128.0 + 1.0, 160.0) * (std::max(M, 50.0) + 1.0) + 8.0 * M * M + 3.0 * 160.0 * (M + 1.0));
-    if (has_reaction) {
+    if (has_reaction == 2) {
+        // the interpolation form: F and the stage buffer, the scratch and
+        // point-value buffers of the transforms (2 S dof each), and the four
+        // 1D factors (rows of at most (n+1)(k+1) entries on average)
+        b += 8.0 * (2.0 * N + 8.0 * N) + 4.0 * (H * (n + 1.0) * (k + 1.0) * 16.0 + H * (n + 2.0) * 4.0);
+    } else if (has_reaction) {
         const double elem = precision == SGK_FP64 ? 8.0 : 4.0;
         const double full = std::pow(H, d);
         b += 8.0 * 6.0 * N + elem * ((2.0 * S + 1.0) * full + 2.0 * S * dof + N);
@@ -590,7 +601,8 @@ int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
         !q->kappa || (q->precision != SGK_FP64 && q->precision != SGK_MIXED) ||
         (q->bc != SGK_PERIODIC && q->bc != SGK_DIRICHLET0) || !std::isfinite(q->krylov_tol) ||
         q->krylov_tol < 0.0 ||
-        (q->krylov_tol > 0.0 && (q->krylov_max_substeps < 1 || q->krylov_max_substeps > SGK_MAX_KRYLOV_SUBSTEPS)))
+        (q->krylov_tol > 0.0 && (q->krylov_max_substeps < 1 || q->krylov_max_substeps > SGK_MAX_KRYLOV_SUBSTEPS)) ||
+        (q->reaction_form != SGK_REACTION_QUADRATURE && q->reaction_form != SGK_REACTION_INTERP))
         return SGK_EINVAL;
     if (q->reaction.nmono < 0 || q->reaction.nmono > SGK_MAX_MONO ||
         (q->reaction.nmono > 0 &&
@@ -608,6 +620,7 @@ int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
     r->prec = q->precision;
     r->ktol = q->krylov_tol;
     r->kmax = q->krylov_tol > 0.0 ? q->krylov_max_substeps : 1;
+    r->form = q->reaction_form;
     r->kappa.assign(q->kappa, q->kappa + (size_t)S * q->d);
     r->nmono = q->reaction.nmono;
     if (r->nmono > 0) {
@@ -629,7 +642,8 @@ int sgk_server_submit(sgk_server* srv, const sgk_request* q, int64_t* ticket) {
             c.const_term = in.const_term;
         }
     }
-    r->est = sgk_estimate_bytes(q->d, q->n, q->k, S, q->krylov_m, q->precision, r->nmono > 0);
+    r->est = sgk_estimate_bytes(q->d, q->n, q->k, S, q->krylov_m, q->precision,
+                                r->nmono > 0 ? (r->form == SGK_REACTION_INTERP ? 2 : 1) : 0);
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stopping) return SGK_EINVAL;
     if (r->est < 0 || r->est > srv->budget) {

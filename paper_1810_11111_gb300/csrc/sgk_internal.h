@@ -234,6 +234,14 @@ std::vector<double> build_sipg_hier(const Tables1D& tab, int bc, double sigma);
 // dense H x H in the hierarchical basis: P[a][b] = int v_a' v_b over the
 // finest cells, E[a][b] = sum over faces of [v_a] {v_b}.
 void build_cross_hier(const Tables1D& tab, int bc, std::vector<double>& P, std::vector<double>& E);
+// The 1D factors of the collocation matrix of the sparse-grid interpolation
+// form of the reaction term (tables.cpp): A (Alpert coefficients ->
+// interpolation surpluses), B (surpluses -> point values) and their
+// inverses, H x H in CSR with sorted columns (host arrays only).
+struct InterpFactors1D {
+    Csr A, B, Binv, Ainv;
+};
+void build_interp_factors(int N, int k, InterpFactors1D& out);
 
 // --------------------------------------------------------- fiber engine ---
 

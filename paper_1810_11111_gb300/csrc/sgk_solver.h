@@ -14,6 +14,28 @@ struct GraphCache {
     int64_t nlaunch = 0;
 };
 
+// Device tables of one 1D factor of the interpolation form of the reaction
+// term (interp.cu): CSR row pointers, truncated row lengths per level,
+// packed (level << 16 | position) columns, values.
+struct InterpFactorDev {
+    DevBuf<int32_t> rp, rlen, ce;
+    DevBuf<double> val;
+    int64_t nnz = 0;
+};
+
+// The sparse-grid interpolation form of F (SGK_REACTION_INTERP): the factors
+// A, B, B^{-1}, A^{-1}; two scratch buffers of the direction passes and two
+// of point values (2 S n each); the pointwise Newton outcome (status, most
+// corrections); multiply-adds of one application of C (or C^{-1}) to one
+// vector.
+struct InterpPlan {
+    bool on = false;
+    InterpFactorDev f[4];
+    DevBuf<double> t0, t1, p0, p1;
+    DevBuf<int> outcome;
+    int64_t madds_to = 0, madds_from = 0;
+};
+
 struct sgk_solver {
     // serial number, never reused in the process (a destroyed solver's
     // address can be handed to a new one; plans that hold device pointers
@@ -46,6 +68,10 @@ struct sgk_solver {
     int prec = SGK_FP64;
     long long n = 0;  // dof per species
     Quad Q;
+    // SGK_REACTION_QUADRATURE (the paper's finest-grid F, Q above) or
+    // SGK_REACTION_INTERP (IP below)
+    int rform = SGK_REACTION_QUADRATURE;
+    InterpPlan IP;
     bool unod_valid = false;
     // state and Newton vectors (species-stacked FP64)
     DevBuf<double> U, Uprev, W, vv, Fv, G, cg_x, cg_r, cg_p, cg_q;
@@ -111,6 +137,19 @@ struct sgk_solver {
 };
 
 void solver_alloc(sgk_solver* s);
+// Interpolation form of the reaction term (interp.cu).  interp_build makes
+// the factor tables and buffers; interp_evalF: F = C^{-1} f(C U) (no
+// sources); interp_evalJ: jw = C^{-1} (f'(C U) (C w)); interp_implicit: from
+// Wp = W + c S, solves u - c f(u) = C Wp at every collocation point and
+// writes U = C^{-1} u and Fr = C^{-1} f(u), the outcome (SGK_OK or
+// SGK_ENEWTON, most Newton corrections of a point) to *status and *iters on
+// the device.  All vectors species-stacked on the device.
+void interp_build(sgk_solver* s);
+void interp_evalF(sgk_solver* s, const double* U, double* F);
+void interp_evalJ(sgk_solver* s, const double* U, const double* w, double* jw);
+void interp_implicit(sgk_solver* s, const double* Wp, double c, double* U, double* Fr, int* status, int* iters);
+void interp_to_points(sgk_solver* s, const double* U, double* P, int nvec);
+void interp_from_points(sgk_solver* s, const double* P, double* U, int nvec, double* U2, int nsplit);
 // alpha_1, alpha_0, alpha_{-1}, ..., alpha_{-(r-2)} of eq. krylov4
 void iif_alpha(int r, double* alpha);
 // Device-driven steps (one graph per step) are used when graphs are on, no

@@ -15,12 +15,17 @@
 //
 // All vectors live on the device; the host only reads back the scalars that
 // decide loop exits (none at all in the device-driven step).  In SGK_MIXED
-// mode only the Jacobian products J_F(U) w of the inner solver run in FP32
-// (on an FP32 copy of the transformed U); every F that fixes the answer --
-// the predictor's F(U^n) and the Newton residual's F(U) -- runs in FP64, so
-// Newton's fixed point is that of the FP64 path and the outer stop is the
-// same ||G||_2 <= tol max(||W||_2, ||G(W)||_2) in both modes (an inexact Jacobian only
-// changes the convergence rate).  The Krylov exponential keeps its
+// mode the Jacobian products J_F(U) w of the inner solve run in FP32 (on an
+// FP32 copy of the transformed U), and so does the first residual of a step,
+// which only seeds the first correction and never accepts; every other F
+// that fixes the answer -- the predictor's F(U^n) and each Newton residual's
+// F(U) -- runs in double-float arithmetic (about 1e-14 relative, FP64 where
+// the fused pencil kernel does not serve the shape), so Newton's fixed point
+// is that of the FP64 path and the outer stop is the same ||G||_2 <= tol
+// max(||W||_2, ||G(W)||_2) in both modes (an inexact Jacobian only changes
+// the convergence rate).  With the interpolation form of F (interp.cu) the
+// implicit stage is solved pointwise at the collocation points instead, in
+// FP64 in both modes.  The Krylov exponential keeps its
 // double-float matvec and FP64 reductions, and the inner products, norms and
 // state stay FP64.  The Newton and CG vector steps are fused with their
 // inner products and control decisions.
@@ -494,7 +499,28 @@ bool df_reaction(const sgk_solver* s) { return s->prec == SGK_MIXED && s->Q.fuse
 // the transformed U, made here.  lo: a mixed-mode F that only seeds a
 // Newton correction and never decides acceptance runs in FP32 (and leaves
 // its FP32 transform for the Jacobian passes directly).
+// F += sum_m e^{lambda_m (t^n + toff)} S_m per species (FP64)
+void add_sources(sgk_solver* s, double* F, double toff) {
+    if (!s->has_src) return;
+    const long long n = s->n;
+    for (int sp = 0; sp < s->nspecies; ++sp) {
+        if (!s->nsrc[sp]) continue;
+        KTimer kt(s->ctx, KC_VECTOR);
+        source_add_kernel<<<(int)std::min<long long>((n + 255) / 256, 4LL * s->ctx->num_sms), 256, 0,
+                            s->ctx->stream>>>(F + sp * n, s->src_S[sp].p, s->src_lam.p + sp * SGK_MAX_SOURCE_TERMS,
+                                              s->nsrc[sp], s->tdev.p, toff, n);
+        check_launch("source_add");
+        count_launch(s->ctx);
+    }
+}
+
 void evalF(sgk_solver* s, const double* U, double* F, double toff, bool lo = false) {
+    if (s->IP.on) {
+        // the interpolation form (FP64 in both modes; no Jacobian cache)
+        interp_evalF(s, U, F);
+        add_sources(s, F, toff);
+        return;
+    }
     if (lo && s->prec == SGK_MIXED) {
         evalF_T<float>(s, U, F);
     } else if (df_reaction(s)) {
@@ -507,17 +533,7 @@ void evalF(sgk_solver* s, const double* U, double* F, double toff, bool lo = fal
         if (df_reaction(s)) vk_convert(s->ctx, reinterpret_cast<const dfloat*>(s->q64.p), s->q32.p, m);
         else vk_convert(s->ctx, s->q64.p, s->q32.p, m);
     }
-    if (!s->has_src) return;
-    const long long n = s->n;
-    for (int sp = 0; sp < s->nspecies; ++sp) {
-        if (!s->nsrc[sp]) continue;
-        KTimer kt(s->ctx, KC_VECTOR);
-        source_add_kernel<<<(int)std::min<long long>((n + 255) / 256, 4LL * s->ctx->num_sms), 256, 0,
-                            s->ctx->stream>>>(F + sp * n, s->src_S[sp].p, s->src_lam.p + sp * SGK_MAX_SOURCE_TERMS,
-                                              s->nsrc[sp], s->tdev.p, toff, n);
-        check_launch("source_add");
-        count_launch(s->ctx);
-    }
+    add_sources(s, F, toff);
 }
 
 // writes t^n to the device before a step (or a stand-alone F) reads it
@@ -662,8 +678,44 @@ void gmres_solve_host(sgk_solver* s, const double* G, double* x, int& iters) {
     }
 }
 
+// The implicit stage U - c F_I(U, t^{n+1}) = W of the interpolation form:
+// Wp = W + c S(t^{n+1}), the pointwise solve at the collocation points, U and
+// Fv = F_I(U) + S(t^{n+1}) (the next predictor's F); outcome to status, iters.
+void interp_stage(sgk_solver* s, int* status, int* iters) {
+    const long long N = s->n * s->nspecies;
+    const double c = s->newton_c;
+    const double* Wp = s->W.p;
+    if (s->has_src) {
+        SGK_CUDA_CHECK(cudaMemsetAsync(s->G.p, 0, N * sizeof(double), s->ctx->stream));
+        add_sources(s, s->G.p, s->dt);
+        vk_axpby(s->ctx, 1.0, s->W.p, c, s->G.p, s->G.p, N);
+        Wp = s->G.p;
+    }
+    interp_implicit(s, Wp, c, s->U.p, s->Fv.p, status, iters);
+    add_sources(s, s->Fv.p, s->dt);
+}
+
+// StepCtl after the interpolation stage of a step graph: the pointwise
+// solve's outcome (status, most corrections in it) becomes the step's
+__global__ void interp_ctl_finish_kernel(StepCtl* c) {
+    c->newton_iters = c->it;
+    c->inner_iters = 0;
+    c->last_g = 0.0;
+    c->fvalid = c->status == SGK_OK ? 1 : 0;
+}
+
 int newton(sgk_solver* s) {
     sgk_ctx* ctx = s->ctx;
+    if (s->IP.on) {
+        int* o = s->IP.outcome.p;
+        interp_stage(s, o, o + 1);
+        int h[2] = {0, 0};
+        SGK_CUDA_CHECK(cudaMemcpyAsync(h, o, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        SGK_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        s->stats.newton_iters += h[1];
+        s->stats.last_newton_residual = 0.0;
+        return h[0] == SGK_OK ? SGK_OK : SGK_ENEWTON;
+    }
     const long long N = s->n * s->nspecies;
     const double dt2 = s->newton_c;
     SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -711,6 +763,10 @@ void solver_eval_reaction(sgk_solver* s, const double* U, double* F) {
 
 void solver_jacobian_apply(sgk_solver* s, const double* U, const double* w, double* jw) {
     SGK_REQUIRE(s->has_rx, SGK_EINVAL, "solver has no reaction term");
+    if (s->IP.on) {
+        interp_evalJ(s, U, w, jw);
+        return;
+    }
     const long long n = s->n;
     if (s->prec == SGK_FP64) {
         QuadPtrs<double> p = qptrs<double>(s);
@@ -857,7 +913,7 @@ void capture_while(sgk_ctx* ctx, cudaStream_t aux, Pre&& pre, Body&& body) {
 }
 
 bool step_graph_eligible(const sgk_solver* s) {
-    return s->use_graphs && s->scheme == SGK_IIF2 && (!s->has_rx || s->nspecies == 1);
+    return s->use_graphs && s->scheme == SGK_IIF2 && (!s->has_rx || s->nspecies == 1 || s->IP.on);
 }
 
 // part: STEP_WHOLE (one graph per step), or the two halves of a step whose
@@ -909,7 +965,14 @@ void build_step_graph(sgk_solver* s, int part = STEP_WHOLE) {
         else
             solver_krylov_finish(s, 0, s->W.p);
         SGK_CUDA_CHECK(cudaMemcpyAsync(s->U.p, s->W.p, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        if (s->has_rx) {
+        if (s->has_rx && s->IP.on) {
+            // the interpolation form: the implicit stage is straight-line
+            interp_stage(s, &ctl->status, &ctl->it);
+            interp_ctl_finish_kernel<<<1, 1, 0, ctx->stream>>>(ctl);
+            check_launch("interp_ctl_finish");
+            count_launch(ctx);
+            s->n_prefix = ctx->launches - before;
+        } else if (s->has_rx) {
             double* const rr = s->scal.p + 2;
             double* const rr_new = s->scal.p + 3;
             double* const pq = s->scal.p + 4;
@@ -1456,7 +1519,12 @@ void solver_alloc(sgk_solver* s) {
     }
     SGK_CUDA_CHECK(cudaMemsetAsync(s->counters.p, 0, 4 * sizeof(unsigned), s->ctx->stream));
     SGK_CUDA_CHECK(cudaMemsetAsync(s->Hm.p, 0, (M + 1) * M * sizeof(double), s->ctx->stream));
-    if (s->has_rx) {
+    if (s->has_rx && s->rform == SGK_REACTION_INTERP) {
+        // the interpolation form needs no finest-grid buffers and no inner solver
+        s->Fv.alloc(N);
+        s->G.alloc(N);
+        interp_build(s);
+    } else if (s->has_rx) {
         s->Fv.alloc(N);
         s->G.alloc(N);
         s->cg_x.alloc(N);

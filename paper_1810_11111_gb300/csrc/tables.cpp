@@ -483,3 +483,243 @@ void build_cross_hier(const Tables1D& tab, int bc, std::vector<double>& P, std::
     P = rotate_dense(tab, PL);
     E = rotate_dense(tab, EL);
 }
+
+// ------------------------------------------------------------------------
+// 1D factors of the collocation matrix of the sparse-grid interpolation form
+// of the reaction term.  This form is not the paper's F: it serves its first
+// stated future direction (Section 5, evaluating the reaction integral with
+// the structure of the basis instead of at the finest-mesh Gauss points).
+//
+// Degree k uses the k+1 points X_0 = {1/3, 2/3}, {0, 1/3, 2/3} or
+// {1/5, 2/5, 3/5, 4/5} of [0, 1); each set is mapped into itself by
+// x -> 2x mod 1, so the point sets X_n of the levels (X_0 copied into every
+// level-n cell) are nested.  The 1D hierarchical index (n, j, p) of level
+// n >= 1 carries the p-th (sorted) point of X_n \ X_{n-1} inside the
+// level-(n-1) cell j; level 0 carries X_0.  A point on a cell edge belongs to
+// the cell on its right.  ell_q is the degree-k Lagrange polynomial through
+// the X_n points of the level-n cell of q (n = level of q), 1 at q, zero
+// outside that cell.  With E[p][a] = v_a(x_p) and B[p][q] = ell_q(x_p):
+//   A    = B^{-1} E : Alpert coefficients -> interpolation surpluses,
+//                     A[p][a] = v_a(x_p) - (I_{n-1} v_a)(x_p) for p on level
+//                     n >= 1 (I_{n-1}: interpolation on the level-(n-1)
+//                     cell of x_p), v_a(x_p) on level 0;
+//   B             : surpluses -> point values;
+//   B^{-1}        : s_p = g_p - sum_t L_t(x_p) g(z_t), z_t the X_{n-1}
+//                     points of the level-(n-1) cell of x_p;
+//   A^{-1}        : surpluses -> Alpert coefficients, A^{-1}[a][q] =
+//                     int ell_q v_a (the Alpert basis is orthonormal).
+// Every entry is formed from these local formulas in long double (not by
+// inverting matrices); only the entries the supports and levels allow are
+// stored.  A and A^{-1} map a level to the same or coarser levels, B and
+// B^{-1} to the same or finer ones.
+// ------------------------------------------------------------------------
+
+namespace {
+
+struct InterpGeometry {
+    int N = 0, k = 0, kp1 = 0, H = 0;
+    int den = 1, D = 2;           // X_0 = {num_t / den}; integer point keys over D 2^N
+    std::vector<int> x0num;       // numerators of X_0 over den
+    std::vector<int> newnum;      // numerators of the new points of a level over D (local to the parent cell)
+    std::vector<int> lev, jj, pp;  // per 1D index
+    std::vector<int64_t> key;     // x 2^N D (an integer for every point of level <= N)
+    std::vector<int> of_key;      // inverse of key, -1 where no point
+    std::vector<ld> alp;
+
+    void build(int N_, int k_) {
+        N = N_;
+        k = k_;
+        kp1 = k + 1;
+        H = kp1 << N;
+        static const int nums[4][4] = {{0}, {1, 2}, {0, 1, 2}, {1, 2, 3, 4}};
+        static const int dens[4] = {1, 3, 3, 5};
+        den = dens[k];
+        D = 2 * den;
+        x0num.assign(nums[k], nums[k] + kp1);
+        // both halves' copies of X_0, over D: x/2 -> num, 1/2 + x/2 -> den + num
+        newnum.clear();
+        for (int h = 0; h < 2; ++h)
+            for (int t = 0; t < kp1; ++t) {
+                const int c = h * den + x0num[t];
+                bool old = false;
+                for (int r = 0; r < kp1; ++r) old = old || c == 2 * x0num[r];
+                if (!old) newnum.push_back(c);
+            }
+        std::sort(newnum.begin(), newnum.end());
+        SGK_REQUIRE((int)newnum.size() == kp1, SGK_EINVAL, "interp: collocation points are not nested");
+        lev.assign(H, 0);
+        jj.assign(H, 0);
+        pp.assign(H, 0);
+        key.assign(H, 0);
+        of_key.assign((size_t)D << N, -1);
+        for (int a = 0; a < H; ++a) {
+            int n = 0;
+            while (a >= level_offset(n, kp1) + level_count(n, kp1)) ++n;
+            const int t = a - level_offset(n, kp1);
+            lev[a] = n;
+            jj[a] = t / kp1;
+            pp[a] = t % kp1;
+            key[a] = n == 0 ? (int64_t)(2 * x0num[pp[a]]) << N
+                            : ((int64_t)jj[a] * D + newnum[pp[a]]) << (N + 1 - n);
+            SGK_REQUIRE(key[a] >= 0 && key[a] < ((int64_t)D << N), SGK_EINVAL, "interp: point outside [0, 1)");
+            SGK_REQUIRE(of_key[key[a]] < 0, SGK_EINVAL, "interp: two indices share a point");
+            of_key[key[a]] = a;
+        }
+        alp = alpert_ld(k);
+    }
+    // level-m cell of the point with key X (the cell on the right at an edge)
+    int64_t cell(int64_t X, int m) const { return X / ((int64_t)D << (N - m)); }
+    // key of the t-th X_0 point of the level-m cell c
+    int64_t node(int m, int64_t c, int t) const { return (c * D + 2 * x0num[t]) << (N - m); }
+    // L_t at the local coordinate s in [0, 1) of a cell (nodes: X_0)
+    ld lagrange_local(int t, ld s) const {
+        ld v = 1;
+        for (int r = 0; r < kp1; ++r)
+            if (r != t) v *= (s - (ld)(2 * x0num[r]) / D) / ((ld)(2 * x0num[t] - 2 * x0num[r]) / D);
+        return v;
+    }
+    // L_t(x) of the level-m cell c, x given by its key
+    ld lagrange(int m, int64_t c, int t, int64_t X) const {
+        const ld scale = std::ldexp((ld)D, N - m);
+        return lagrange_local(t, ((ld)X - (ld)c * scale) / scale);
+    }
+    // index of the X_0 node of a point's own cell
+    int node_index(int a) const {
+        const int m = lev[a];
+        const int64_t c = cell(key[a], m);
+        for (int t = 0; t < kp1; ++t)
+            if (node(m, c, t) == key[a]) return t;
+        throw SgkError{SGK_EINVAL, "interp: point is not a node of its cell"};
+    }
+    // v_a at a point given by its key (zero outside the support)
+    ld alpert_at_key(int a, int64_t X) const {
+        const int64_t fc = X / D;
+        if (lev[a] > 0 && (fc >> (N - lev[a] + 1)) != jj[a]) return 0;
+        const ld xi = 2 * (ld)(X - fc * D) / D - 1;
+        return hier_value(N, k, alp, lev[a], jj[a], pp[a], (int)fc, xi);
+    }
+    // v_a at an interior point x (long double coordinate)
+    ld alpert_at_x(int a, ld x) const {
+        const ld s = std::ldexp(x, N);
+        const int fc = std::min((int)std::floor(s), (1 << N) - 1);
+        if (lev[a] > 0 && (fc >> (N - lev[a] + 1)) != jj[a]) return 0;
+        return hier_value(N, k, alp, lev[a], jj[a], pp[a], fc, 2 * (s - fc) - 1);
+    }
+};
+
+void finish_csr(int H, std::vector<std::vector<std::pair<int, ld>>>& rows, Csr& out) {
+    out.rows = out.cols = H;
+    out.ptr.assign(1, 0);
+    out.col.clear();
+    out.val.clear();
+    for (int r = 0; r < H; ++r) {
+        std::sort(rows[r].begin(), rows[r].end(),
+                  [](const std::pair<int, ld>& a, const std::pair<int, ld>& b) { return a.first < b.first; });
+        for (size_t e = 0; e < rows[r].size(); ++e) {
+            SGK_REQUIRE(e == 0 || rows[r][e].first != rows[r][e - 1].first, SGK_EINVAL, "interp: duplicate entry");
+            out.col.push_back(rows[r][e].first);
+            out.val.push_back((double)rows[r][e].second);
+        }
+        out.ptr.push_back((int)out.col.size());
+    }
+}
+
+}  // namespace
+
+void build_interp_factors(int N, int k, InterpFactors1D& out) {
+    InterpGeometry g;
+    g.build(N, k);
+    const int H = g.H, kp1 = g.kp1;
+    std::vector<std::vector<std::pair<int, ld>>> rA(H), rB(H), rBi(H), rAi(H);
+    // the new points of level m inside the level-(m-1) cell J (m >= 1), or
+    // the points of level 0
+    auto level_points = [&](int m, int64_t J, std::vector<int>& q) {
+        q.clear();
+        for (int r = 0; r < kp1; ++r) q.push_back(m == 0 ? r : level_offset(m, kp1) + (int)J * kp1 + r);
+    };
+    std::vector<int> qs;
+    for (int p = 0; p < H; ++p) {
+        const int mp = g.lev[p];
+        const int64_t X = g.key[p];
+        // B and B^{-1}
+        rB[p].push_back({p, 1});
+        rBi[p].push_back({p, 1});
+        for (int m = 0; m < mp; ++m) {
+            const int64_t c = g.cell(X, m);
+            level_points(m, m == 0 ? 0 : c >> 1, qs);
+            for (int q : qs)
+                if (g.cell(g.key[q], m) == c) rB[p].push_back({q, g.lagrange(m, c, g.node_index(q), X)});
+        }
+        if (mp >= 1) {
+            const int64_t J = g.cell(X, mp - 1);
+            for (int t = 0; t < kp1; ++t) {
+                const int64_t Z = g.node(mp - 1, J, t);
+                const int z = g.of_key[Z];
+                SGK_REQUIRE(z >= 0 && g.lev[z] <= mp - 1, SGK_EINVAL, "interp: coarse node missing");
+                rBi[p].push_back({z, -g.lagrange(mp - 1, J, t, X)});
+            }
+        }
+        // A: v_a(x_p) - (I_{mp-1} v_a)(x_p) over the functions a of level >=
+        // mp whose support lies in the level-(mp-1) cell of x_p
+        if (mp == 0) {
+            for (int a = 0; a < H; ++a)
+                if (g.lev[a] == 0 || (X / g.D >> (N - g.lev[a] + 1)) == g.jj[a])
+                    rA[p].push_back({a, g.alpert_at_key(a, X)});
+        } else {
+            const int64_t J = g.cell(X, mp - 1);
+            ld Lt[4];
+            int64_t Zt[4];
+            for (int t = 0; t < kp1; ++t) {
+                Zt[t] = g.node(mp - 1, J, t);
+                Lt[t] = g.lagrange(mp - 1, J, t, X);
+            }
+            for (int l = mp; l <= N; ++l)
+                for (int64_t ja = J << (l - mp); ja < (J + 1) << (l - mp); ++ja)
+                    for (int r = 0; r < kp1; ++r) {
+                        const int a = level_offset(l, kp1) + (int)ja * kp1 + r;
+                        ld v = g.alpert_at_key(a, X);
+                        for (int t = 0; t < kp1; ++t) v -= Lt[t] * g.alpert_at_key(a, Zt[t]);
+                        rA[p].push_back({a, v});
+                    }
+        }
+    }
+    // A^{-1}[a][q] = int ell_q v_a over the cell of q, for q of level >=
+    // level(a) inside the support of v_a (Gauss rule with k + 2 points:
+    // exact for the degree-2k product)
+    std::vector<ld> gx, gw;
+    gauss_legendre_ld(kp1 + 1, gx, gw);
+    for (int a = 0; a < H; ++a) {
+        const int l = g.lev[a];
+        for (int m = l; m <= N; ++m) {
+            // parents (level m - 1) of the level-m points inside the support
+            int64_t J0 = 0, J1 = 1;
+            if (m >= 1) {
+                if (l == 0) {
+                    J0 = 0;
+                    J1 = (int64_t)1 << (m - 1);
+                } else {
+                    J0 = (int64_t)g.jj[a] << (m - l);
+                    J1 = (int64_t)(g.jj[a] + 1) << (m - l);
+                }
+            }
+            for (int64_t J = J0; J < J1; ++J) {
+                level_points(m, J, qs);
+                for (int q : qs) {
+                    const int64_t c = g.cell(g.key[q], m);
+                    const int t = g.node_index(q);
+                    const ld h = std::ldexp((ld)1, -m);
+                    ld acc = 0;
+                    for (size_t e = 0; e < gx.size(); ++e) {
+                        const ld s = (gx[e] + 1) / 2;
+                        acc += gw[e] * g.lagrange_local(t, s) * g.alpert_at_x(a, (c + s) * h);
+                    }
+                    rAi[a].push_back({q, acc * h / 2});
+                }
+            }
+        }
+    }
+    finish_csr(H, rA, out.A);
+    finish_csr(H, rB, out.B);
+    finish_csr(H, rBi, out.Binv);
+    finish_csr(H, rAi, out.Ainv);
+}

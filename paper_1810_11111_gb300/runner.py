@@ -21,7 +21,7 @@ class Problem:
         self.idx = sgkiif.IndexSet(self.ctx, cfg["d"], cfg["n"], cfg["k"])
         self.ops = [sgkiif.Operator(self.ctx, self.idx, kap, bc) for kap in cfg["kappas"]]
         self.solver = sgkiif.Solver(self.ctx, self.ops, cfg["reaction"], cfg["M"], cfg["dt"], cfg.get("opts"),
-                                    cfg.get("scheme", sgkiif.SGK_IIF2))
+                                    cfg.get("scheme", sgkiif.SGK_IIF2), cfg.get("reaction_form", "quadrature"))
         self.nspecies = len(self.ops)
         self.dof = self.idx.dof
         self.U0 = self.initial_state()

@@ -18,6 +18,8 @@ SGK_IIF2 = 2
 SGK_IIF3 = 3
 SGK_IIF_MAX_ORDER = 6
 SGK_PEAK_FP32_FMA, SGK_PEAK_FP64_FMA = 0, 1
+SGK_REACTION_QUADRATURE, SGK_REACTION_INTERP = 0, 1
+REACTION_FORMS = {"quadrature": SGK_REACTION_QUADRATURE, "interp": SGK_REACTION_INTERP}
 MAX_SPECIES = 4
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsgkiif.so")
@@ -56,7 +58,8 @@ class sgk_request(ctypes.Structure):
                 ("bc", ctypes.c_int), ("kappa", _c_double_p), ("reaction", sgk_reaction),
                 ("krylov_m", ctypes.c_int), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("init", sgk_init * MAX_SPECIES),
-                ("krylov_tol", ctypes.c_double), ("krylov_max_substeps", ctypes.c_int)]
+                ("krylov_tol", ctypes.c_double), ("krylov_max_substeps", ctypes.c_int),
+                ("reaction_form", ctypes.c_int)]
 
 
 class sgk_result_info(ctypes.Structure):
@@ -108,6 +111,10 @@ _SIGS = {
     "sgk_solver_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(sgk_reaction),
                                          ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.POINTER(sgk_newton_opts), ctypes.POINTER(_P)]),
+    "sgk_solver_create_form": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(sgk_reaction),
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.POINTER(sgk_newton_opts), ctypes.c_int, ctypes.POINTER(_P)]),
+    "sgk_interp_factors_1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64]),
     "sgk_solver_destroy": (ctypes.c_int, [_P]),
     "sgk_solver_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "sgk_solver_step": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -322,7 +329,7 @@ def reaction_struct(terms, nspecies):
 
 
 class Solver:
-    def __init__(self, ctx, ops, reaction_terms, krylov_m, dt, opts=None, scheme=SGK_IIF2):
+    def __init__(self, ctx, ops, reaction_terms, krylov_m, dt, opts=None, scheme=SGK_IIF2, reaction_form="quadrature"):
         self.ctx, self.ops = ctx, list(ops)
         self.nspecies = len(self.ops)
         self.dof = self.ops[0].idx.dof
@@ -333,8 +340,9 @@ class Solver:
             o = sgk_newton_opts(opts.get("tol", 0.0), opts.get("max_iter", 0), opts.get("inner_tol", 0.0),
                                 opts.get("inner_max", 0), opts.get("gmres_restart", 0))
         self.h = _P()
-        ctx.check(sgk_solver_create(ctx.h, self.nspecies, arr, ctypes.byref(self._rx), int(scheme), int(krylov_m),
-                                    float(dt), ctypes.byref(o) if o else None, ctypes.byref(self.h)))
+        ctx.check(sgk_solver_create_form(ctx.h, self.nspecies, arr, ctypes.byref(self._rx), int(scheme),
+                                         int(krylov_m), float(dt), ctypes.byref(o) if o else None,
+                                         REACTION_FORMS[reaction_form], ctypes.byref(self.h)))
 
     def set_state(self, species, coeffs=None, dev_ptr=None):
         if dev_ptr is not None:
@@ -424,6 +432,18 @@ def dof_of(d, n, k):
     return int(v)
 
 
+def interp_factors_1d(n, k, which):
+    """Dense 1D factor of the interpolation form's collocation matrix (0: A,
+    1: B, 2: B^-1, 3: A^-1) from the library's host tables (sgk_interp_factors_1d)."""
+    load()
+    H = (k + 1) << n
+    out = np.zeros((H, H))
+    rc = sgk_interp_factors_1d(int(n), int(k), int(which), _dptr(out), out.size)
+    if rc != SGK_OK:
+        raise SgkError(rc, "sgk_interp_factors_1d failed")
+    return out
+
+
 def binary_arch():
     """Architecture of the loaded device code (103 for sm_103a)."""
     load()
@@ -479,6 +499,7 @@ class Server:
         q.krylov_m, q.dt, q.nsteps, q.precision = int(cfg["M"]), float(cfg["dt"]), int(cfg["steps"]), int(precision)
         q.krylov_tol = float(cfg.get("krylov_tol", 0.0))
         q.krylov_max_substeps = int(cfg.get("krylov_max_substeps", 64))
+        q.reaction_form = REACTION_FORMS[cfg.get("reaction_form", "quadrature")]
         if init_coeffs is None and any("noise_seed" in i for i in cfg["init"]):
             from .workloads import coefficient_noise
             init_coeffs = coefficient_noise(cfg["init"][0]["noise_seed"], dof_of(d, cfg["n"], cfg["k"]), S,

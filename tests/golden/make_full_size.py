@@ -7,12 +7,15 @@ the method's arithmetic):
   f = -100 u^3, diffusion diag(1, 0.5, 0.1), IIF2, M = 30, dt = 0.005): the
   projected seeded initial state U0 and the states after steps 1, 5, 10 and
   20 (U1, U5, U10, U20; 20 steps is the whole configured solve).
+* cubic3d_interp_steps.npz -- the same 3D cubic workload with the
+  sparse-grid interpolation form of the reaction term (oracle.interp, a
+  labelled deviation from the paper's F): states after steps 1, 5, 10, 20.
 * schnak2d_steps.npz -- the two-species Schnakenberg workload at its stated
   size (d = 2, level 8, degree 2, kappa 0.01 / 0.5, IIF2 with GMRES, M = 40,
   dt = 0.05): the seeded noisy initial states of both species and the states
   after steps 1, 5 and 10.
 
-Run: python tests/golden/make_full_size.py [cubic3d|schnak2d]
+Run: python tests/golden/make_full_size.py [cubic3d|cubic3d_interp|schnak2d]
 """
 import os
 import sys
@@ -32,9 +35,10 @@ from paper_1810_11111_gb300.workloads import coefficient_noise, cubic3d, schnak2
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def run(cfg, U0, keep):
+def run(cfg, U0, keep, reaction_form="quadrature"):
     idx = IndexSet(cfg["d"], cfg["n"], cfg["k"])
-    sol = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"])
+    sol = IIF2Solver(idx, sipg_1d(cfg["n"], cfg["k"]), cfg["kappas"], cfg["reaction"], cfg["dt"], cfg["M"],
+                     reaction_form=reaction_form)
     out, U, t0 = {}, U0, time.time()
     for step in range(1, max(keep) + 1):
         U = sol.run(U, 1)
@@ -44,13 +48,14 @@ def run(cfg, U0, keep):
     return out, sol.stats
 
 
-def cubic():
+def cubic(reaction_form="quadrature"):
     cfg = cubic3d()
     idx = IndexSet(cfg["d"], cfg["n"], cfg["k"])
     init = cfg["init"][0]
     U0 = project_separable(idx, init["amp"], init["wavenum"], init["kind"], init["const"])
-    out, stats = run(cfg, [U0], (1, 5, 10, 20))
-    np.savez_compressed(os.path.join(HERE, "cubic3d_steps.npz"), U0=np.stack([U0]), **out,
+    out, stats = run(cfg, [U0], (1, 5, 10, 20), reaction_form)
+    name = "cubic3d_steps.npz" if reaction_form == "quadrature" else "cubic3d_interp_steps.npz"
+    np.savez_compressed(os.path.join(HERE, name), U0=np.stack([U0]), **out,
                         newton=np.array(stats["newton"]), inner=np.array(stats["inner"]))
 
 
@@ -68,5 +73,7 @@ if __name__ == "__main__":
     which = sys.argv[1:] or ["cubic3d", "schnak2d"]
     if "cubic3d" in which:
         cubic()
+    if "cubic3d_interp" in which:
+        cubic("interp")
     if "schnak2d" in which:
         schnak()

@@ -123,3 +123,24 @@ def test_cross_blocks_match_the_oracle(lib):
                 assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), (n, k, bc)
     out = np.zeros(4)
     assert sgkiif.sgk_cross_blocks_1d(1, 1, 0, out.ctypes.data, out.ctypes.data, 4) == sgkiif.SGK_EINVAL
+
+
+def test_interp_factors_match_the_oracle(lib):
+    # the library's host tables of the interpolation form of the reaction
+    # term (each entry from its local formula in long double, C++) against
+    # the oracle's (dense evaluation and dense solves, numpy); no GPU involved
+    import numpy as np
+
+    from oracle.interp import one_dim_factors
+    from paper_1810_11111_gb300 import sgkiif
+    for n, k in ((0, 1), (1, 2), (3, 1), (4, 2), (3, 3), (5, 3), (6, 1)):
+        want = one_dim_factors(n, k)
+        for which in range(4):
+            got = sgkiif.interp_factors_1d(n, k, which)
+            scale = max(1.0, np.abs(want[which]).max())
+            assert np.abs(got - want[which]).max() <= 1e-12 * scale, (n, k, which)
+            # the same sparsity: nothing stored where the oracle's entry vanishes
+            assert np.all(np.abs(got[np.abs(want[which]) <= 1e-13 * scale]) <= 1e-12 * scale)
+    out = np.zeros(4)
+    assert sgkiif.sgk_interp_factors_1d(1, 1, 0, out.ctypes.data, 4) == sgkiif.SGK_EINVAL
+    assert sgkiif.sgk_interp_factors_1d(1, 1, 4, out.ctypes.data, 16) == sgkiif.SGK_EINVAL

@@ -62,3 +62,19 @@ def test_batch_without_gpu_fails_cleanly(lib):
     assert sgkiif.sgk_batch_create(0, 4, 0, ctypes.byref(h)) == sgkiif.SGK_ECUDA
     assert sgkiif.sgk_batch_create(0, 0, 0, ctypes.byref(h)) == sgkiif.SGK_EINVAL
     assert sgkiif.sgk_batch_count(None) == -1 and sgkiif.sgk_batch_dof(None, 0) == -1
+
+
+def test_estimates_of_the_interpolation_form(lib):
+    # has_reaction = 2 selects the interpolation form of F: no finest-grid
+    # buffers, so its memory grows with the sparse-grid DOF only
+    est, work = sgkiif.sgk_estimate_bytes, sgkiif.sgk_estimate_work
+    MIX = sgkiif.SGK_MIXED
+    for d, n, k in ((3, 6, 2), (4, 8, 2), (4, 9, 3)):
+        dof = sgkiif.dof_of(d, n, k)
+        sparse, quad, none = est(d, n, k, 1, 30, MIX, 2), est(d, n, k, 1, 30, MIX, 1), est(d, n, k, 1, 30, MIX, 0)
+        assert none < sparse < quad
+        assert sparse - none >= 10 * 8 * dof          # F, the stage buffer, 8 transform buffers
+        assert sparse < none + 200 * 8 * dof
+        assert 0 < work(d, n, k, 1, 30, 2) < work(d, n, k, 1, 30, 1)
+    # the largest served shape fits a GB300 in this form only
+    assert est(4, 9, 3, 2, 30, MIX, 2) < 100e9 < est(4, 9, 3, 2, 30, MIX, 1)
