@@ -48,76 +48,104 @@ struct SgtArgs {
 
 // y = (I x .. x T x .. x I) x along direction dir on the sparse set, for
 // nvec vectors stacked with stride ld; output vector v goes to y + v ld for
-// v < nsplit and to y2 + (v - nsplit) ld otherwise.  One thread per output.
-template <int D, int KP1>
+// v < nsplit and to y2 + (v - nsplit) ld otherwise.  G consecutive lanes
+// share one output (G divides 32): lane r takes the row entries r, r + G, ...
+// in two chains, four loads issued before their multiply-adds, and the G
+// partial sums are added by XOR shuffles in a fixed order.  G > 1 shortens
+// the longest rows' dependent chains (the level-0 rows of A and A^{-1} walk
+// the whole fiber), which bound a launch on small index sets; G = 1 keeps
+// the per-output decoding cheapest where the FP64 pipe is the bound.
+template <int D, int KP1, int G>
 __global__ void __launch_bounds__(256) sgt_kernel(SgtArgs a, int dir, int nvec, int64_t ld,
                                                   const double* __restrict__ x, double* __restrict__ y,
                                                   double* __restrict__ y2, int nsplit) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n) return;
-    int lo = a.chunk[g >> 8], hi = a.chunk[(g >> 8) + 1];
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.offsets[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    const int t = lo;
-    int64_t e = g - a.offsets[t];
-    int lv[D], sh[D], cnt[D], c[D];
-    int sum = 0;
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-        lv[m] = a.levels[t * D + m];
-        sum += lv[m];
-        sh[m] = lv[m] > 0 ? lv[m] - 1 : 0;
-        cnt[m] = KP1 << sh[m];
-    }
-#pragma unroll
-    for (int m = D - 1; m >= 0; --m) {
-        const int64_t q = (e >> sh[m]) / KP1;
-        c[m] = (int)(e - q * cnt[m]);
-        e = q;
-    }
-    int64_t o = 0, in = 0, I = 1;
-    int cd = 0, ldir = 0;
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-        if (m < dir) o = o * cnt[m] + c[m];
-        if (m == dir) {
-            cd = c[m];
-            ldir = lv[m];
+    // 32-bit index arithmetic: the index set has at most 2^30 coefficients
+    // (checked when the tables are built)
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
+    const int r = (int)(threadIdx.x & (G - 1));
+    const bool live = g < a.n;
+    if (G == 1 && !live) return;
+    int q0 = 0, qe = 0;
+    const int64_t* __restrict__ base = a.cb;
+    int oI = 0, in = 0, I = 1;
+    if (live) {
+        int lo = a.chunk[g >> 8], hi = a.chunk[(g >> 8) + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.offsets[mid] <= g) lo = mid;
+            else hi = mid - 1;
         }
-    }
+        const int t = lo;
+        int e = g - (int)a.offsets[t];
+        int lv[D], sh[D], cnt[D], c[D];
+        int sum = 0;
 #pragma unroll
-    for (int m = D - 1; m >= 0; --m)
-        if (m > dir) {
-            in += (int64_t)c[m] * I;
-            I *= cnt[m];
+        for (int m = 0; m < D; ++m) {
+            lv[m] = a.levels[t * D + m];
+            sum += lv[m];
+            sh[m] = lv[m] > 0 ? lv[m] - 1 : 0;
+            cnt[m] = KP1 << sh[m];
         }
-    const int nl = a.N + 1;
-    const int np = a.N - (sum - ldir);
-    const int ai = (ldir ? (KP1 << (ldir - 1)) : 0) + cd;
-    const int q0 = a.rp[ai], qe = q0 + a.rlen[ai * nl + np];
-    const int64_t* __restrict__ base = a.cb + ((int64_t)t * D + dir) * nl;
-    const int64_t oI = o * I * KP1;
+#pragma unroll
+        for (int m = D - 1; m >= 0; --m) {
+            const int q = (e >> sh[m]) / KP1;
+            c[m] = e - q * cnt[m];
+            e = q;
+        }
+        int o = 0, cd = 0, ldir = 0;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            if (m < dir) o = o * cnt[m] + c[m];
+            if (m == dir) {
+                cd = c[m];
+                ldir = lv[m];
+            }
+        }
+#pragma unroll
+        for (int m = D - 1; m >= 0; --m)
+            if (m > dir) {
+                in += c[m] * I;
+                I *= cnt[m];
+            }
+        const int nl = a.N + 1;
+        const int np = a.N - (sum - ldir);
+        const int ai = (ldir ? (KP1 << (ldir - 1)) : 0) + cd;
+        q0 = a.rp[ai];
+        qe = q0 + a.rlen[ai * nl + np];
+        base = a.cb + ((int64_t)t * D + dir) * nl;
+        oI = o * I * KP1;
+    }
+    // index of the source coefficient of a packed (level, position) entry
+    auto src = [&](int pk) {
+        const int lb = pk >> 16;
+        return (int)base[lb] + (lb ? (oI << (lb - 1)) : oI) + (pk & 0xffff) * I + in;
+    };
     for (int v = 0; v < nvec; ++v) {
         const double* __restrict__ xv = x + v * ld;
         double s0 = 0.0, s1 = 0.0;
-        int q = q0;
-        for (; q + 1 < qe; q += 2) {
-            const int p0 = a.ce[q], p1 = a.ce[q + 1];
-            const int l0 = p0 >> 16, l1 = p1 >> 16;
-            const int64_t a0 = base[l0] + (l0 ? (oI << (l0 - 1)) : oI) + (int64_t)(p0 & 0xffff) * I + in;
-            const int64_t a1 = base[l1] + (l1 ? (oI << (l1 - 1)) : oI) + (int64_t)(p1 & 0xffff) * I + in;
-            s0 += a.val[q] * xv[a0];
-            s1 += a.val[q + 1] * xv[a1];
+        int q = q0 + r;
+        for (; q + 3 * G < qe; q += 4 * G) {
+            const double x0 = xv[src(a.ce[q])], x1 = xv[src(a.ce[q + G])];
+            const double x2 = xv[src(a.ce[q + 2 * G])], x3 = xv[src(a.ce[q + 3 * G])];
+            s0 += a.val[q] * x0;
+            s1 += a.val[q + G] * x1;
+            s0 += a.val[q + 2 * G] * x2;
+            s1 += a.val[q + 3 * G] * x3;
         }
-        if (q < qe) {
-            const int p0 = a.ce[q], l0 = p0 >> 16;
-            s0 += a.val[q] * xv[base[l0] + (l0 ? (oI << (l0 - 1)) : oI) + (int64_t)(p0 & 0xffff) * I + in];
+        if (q + G < qe) {
+            const double x0 = xv[src(a.ce[q])], x1 = xv[src(a.ce[q + G])];
+            s0 += a.val[q] * x0;
+            s1 += a.val[q + G] * x1;
+            q += 2 * G;
         }
-        double* out = v < nsplit ? y + v * ld : y2 + (v - nsplit) * ld;
-        out[g] = s0 + s1;
+        if (q < qe) s0 += a.val[q] * xv[src(a.ce[q])];
+        double t = s0 + s1;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (live && r == 0) {
+            double* out = v < nsplit ? y + v * ld : y2 + (v - nsplit) * ld;
+            out[g] = t;
+        }
     }
 }
 
@@ -261,6 +289,9 @@ __global__ void interp_newton_kernel(ReactionDev rx, double c, const double* __r
     }
 }
 
+// largest index set whose transform passes use eight lanes per output
+constexpr int64_t SGT_WIDE_MAX_N = int64_t(1) << 18;
+
 SgtArgs sgt_args(const sgk_solver* s, int which) {
     const sgk_op* op = s->ops[0];
     const sgk_index* idx = s->idx;
@@ -283,14 +314,19 @@ template <int D>
 void launch_sgt_d(const sgk_solver* s, int which, int dir, int nvec, const double* x, double* y, double* y2,
                   int nsplit) {
     const SgtArgs a = sgt_args(s, which);
-    const unsigned blocks = (unsigned)((a.n + 255) / 256);
     cudaStream_t st = s->ctx->stream;
+    // eight lanes per output on small index sets (latency-bound launches),
+    // one on large ones (FP64-pipe-bound)
+    const bool wide = a.n <= SGT_WIDE_MAX_N;
+    const unsigned blocks = (unsigned)((a.n * (wide ? 8 : 1) + 255) / 256);
+#define SGK_SGT(KP, GG) sgt_kernel<D, KP, GG><<<blocks, 256, 0, st>>>(a, dir, nvec, a.n, x, y, y2, nsplit)
     switch (s->idx->k + 1) {
-        case 2: sgt_kernel<D, 2><<<blocks, 256, 0, st>>>(a, dir, nvec, a.n, x, y, y2, nsplit); break;
-        case 3: sgt_kernel<D, 3><<<blocks, 256, 0, st>>>(a, dir, nvec, a.n, x, y, y2, nsplit); break;
-        case 4: sgt_kernel<D, 4><<<blocks, 256, 0, st>>>(a, dir, nvec, a.n, x, y, y2, nsplit); break;
+        case 2: if (wide) SGK_SGT(2, 8); else SGK_SGT(2, 1); break;
+        case 3: if (wide) SGK_SGT(3, 8); else SGK_SGT(3, 1); break;
+        case 4: if (wide) SGK_SGT(4, 8); else SGK_SGT(4, 1); break;
         default: throw SgkError{SGK_EUNSUPPORTED, "interp: degree must be 1..3"};
     }
+#undef SGK_SGT
 }
 
 void launch_sgt(sgk_solver* s, int which, int dir, int nvec, const double* x, double* y, double* y2, int nsplit) {
@@ -388,6 +424,8 @@ void interp_implicit(sgk_solver* s, const double* Wp, double c, double* U, doubl
 void interp_build(sgk_solver* s) {
     const sgk_index* idx = s->idx;
     const int N = idx->n, kp1 = idx->k + 1, nl = N + 1, H = kp1 << N;
+    SGK_REQUIRE(idx->dof <= (int64_t(1) << 30), SGK_EUNSUPPORTED,
+                "interpolation form: at most 2^30 coefficients per species");
     InterpFactors1D F;
     build_interp_factors(N, idx->k, F);
     const Csr* mats[4] = {&F.A, &F.B, &F.Binv, &F.Ainv};
