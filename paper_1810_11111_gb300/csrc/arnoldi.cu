@@ -9,7 +9,10 @@
 // matvec and the first projection need no barrier between them.  Two grid
 // barriers per step publish (1) V^T w, (2) V^T w' together with ||w'||^2
 // (the norm of w'' follows by Pythagoras; near breakdown a third barrier
-// sums it explicitly).  The cross-CTA sums are exact: every CTA adds its
+// sums it explicitly); with the double-float matvec one more barrier at the
+// start publishes the pairs of v / gamma for the first gathers (pairs of
+// FP32 numbers cannot hold an unnormalised v of tiny magnitude).  The
+// cross-CTA sums are exact: every CTA adds its
 // partials, as 128-bit fixed-point integers, into integer accumulators with
 // atomic adds, and after the barrier every CTA reads the same totals, so all
 // CTAs hold bitwise equal h1, h2 and beta and take the same breakdown

@@ -390,12 +390,8 @@ __device__ __forceinline__ void arnoldi_body(const GmvArgs<double, D>& ga, const
     // first atomics follow the second)
     if (b == 0)
         for (int i = threadIdx.x; i < 3 * FX_SET; i += PT) a.acc[i] = 0ull;
-    // gamma = ||v||; with the double-float matvec, v's pairs for the first
-    // gathers go to w1 (free until the second step writes it)
-    for (int u = threadIdx.x; u < ne; u += PT) {
-        wsb0[u] = a.v[lo + u];
-        if (DF) reinterpret_cast<float2*>(a.w1)[lo + u] = df_to_float2(df_from_double(a.v[lo + u]));
-    }
+    // gamma = ||v||
+    for (int u = threadIdx.x; u < ne; u += PT) wsb0[u] = a.v[lo + u];
     __syncthreads();
     slice_norm2(wsb0, ne, red, P2 + b);
     if (!barrier()) return;
@@ -424,6 +420,20 @@ __device__ __forceinline__ void arnoldi_body(const GmvArgs<double, D>& ga, const
         const double y = wsb0[u] * scale;
         a.V[lo + u] = y;
         if (Vs) Vs[u] = y;
+        // with the double-float matvec the first gathers read the pairs of
+        // v / gamma from w1 (free until the second step writes it): pairs of
+        // FP32 numbers have FP32's exponent range, so the pairs of an
+        // unnormalised v would lose their low parts below about 1e-30 and
+        // their values below about 1e-38
+        if (DF) reinterpret_cast<float2*>(a.w1)[lo + u] = df_to_float2(df_from_double(y));
+    }
+    if (DF) {
+        // one more barrier publishes the pairs; the first product is then
+        // A v_0 itself (scale 1)
+        if (!barrier()) return;
+        scale = 1.0;
+        if (threadIdx.x == 0) s_scaldf = df_to_float2(df_from_double(1.0));
+        __syncthreads();
     }
     // the next matvec gathers x (written by all CTAs) and forms
     // A v_j = scale (A x - corr), corr = sum_c hp_c A v_c over the previous

@@ -401,6 +401,26 @@ def test_persistent_barrier_timeout_is_reported(ctx64, monkeypatch):
     idx.close()
 
 
+@pytest.mark.parametrize("form", ["quadrature", "interp"])
+def test_mixed_steps_of_a_tiny_state(form):
+    # double-float pairs have FP32's exponent range (smallest normal number
+    # about 1.2e-38); the Krylov matvec's first gathers take the pairs of
+    # the normalised vector, so a state far below that range steps in mixed
+    # precision as it does in FP64
+    cfg = dict(workloads.cubic3d(n=3, k=2), reaction_form=form)
+    out = {}
+    for prec in (sgkiif.SGK_FP64, sgkiif.SGK_MIXED):
+        prob = Problem(cfg, prec)
+        prob.reset()
+        U0 = prob.U0[0].cpu().numpy() * 1e-40
+        prob.solver.set_state(0, U0)
+        prob.solver.step(3)
+        out[prec] = prob.state()[0]
+        prob.close()
+    assert 0.0 < np.linalg.norm(out[sgkiif.SGK_FP64]) < 1e-39
+    assert rel(out[sgkiif.SGK_MIXED], out[sgkiif.SGK_FP64]) <= 1e-6
+
+
 def test_krylov_breakdown_constant_mode(ctx64):
     idx = sgkiif.IndexSet(ctx64, 3, 3, 2)
     op = sgkiif.Operator(ctx64, idx, [1.0, 1.0, 1.0])
