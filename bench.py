@@ -661,10 +661,12 @@ def served_sparse_leg(args):
         else:
             infos = [srv.wait(srv.submit(r, sgkiif.SGK_MIXED), cap=c)[1] for r, c in zip(reqs, caps)]
         wall = time.perf_counter() - t0
-        for info in infos:
+        for i, info in enumerate(infos):
             lat.append(info["latency_ms"])
             if info["status"] != sgkiif.SGK_OK:
-                fails.append("status %d: %s" % (info["status"], info["error"]))
+                q = reqs[i]
+                fails.append("request %d (%s, d %d, level %d, degree %d): status %d: %s after %d steps"
+                             % (i, q["name"], q["d"], q["n"], q["k"], info["status"], info["error"], info["steps"]))
         st = srv.stats()
         srv.close()
         lat = np.sort(np.asarray(lat))
