@@ -145,7 +145,7 @@ PENCIL_TRAFFIC = {(3, 6, 2, "mixed"): 57394944 + 13584896}
 # one persistent Arnoldi launch (one exponential), keyed by (d, level,
 # degree, M, precision): profiles/arnoldi_kernel_cubic3d_l6k2_m30.md (the
 # mixed-precision variant, double-float gather)
-ARNOLDI_TRAFFIC = {(3, 6, 2, 30, "mixed"): 6501120 + 49664}
+ARNOLDI_TRAFFIC = {(3, 6, 2, 30, "mixed"): 6501376 + 54016}
 
 
 def pencil_q(cfg):
