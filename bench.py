@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-schnak", action="store_true", help="skip the two-species 200-step leg")
     ap.add_argument("--no-sparse-reaction", action="store_true",
                     help="skip the legs of the sparse-grid interpolation form of the reaction term")
+    ap.add_argument("--full-comparisons", action="store_true",
+                    help="also run the comparison runs kept out of the default line for time: the batch with every "
+                         "instance in its own whole-step graph, the served saturation run with the engine off, "
+                         "the served requests above 1e-6 re-solved from perturbed inputs and with sub-projections, "
+                         "and the interpolation form's served requests one at a time")
     ap.add_argument("--served-no-fp64", action="store_true",
                     help="skip the FP64 one-at-a-time baseline of the served leg (and its accuracy check)")
     ap.add_argument("--served-rates", default="1",
@@ -479,8 +484,12 @@ def native(args, rank, world, local_rank):
     legs = {}  # host wall seconds of every leg after the headline one
 
     def leg(name, fn):
+        # a leg that raises is reported in the line; the headline stands
         t0 = time.perf_counter()
-        out[name] = fn()
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
         legs[name] = round(time.perf_counter() - t0, 1)
 
     if world == 1 and not args.no_matvec:
@@ -678,13 +687,13 @@ def served_sparse_leg(args):
         srv.wait(srv.submit(dict(r, steps=1), sgkiif.SGK_MIXED))
     srv.close()
     sat = run(args.served_workers, True)
-    one = run(1, False)
+    one = run(1, False) if args.full_comparisons else None
     return {"workload": "served draws (seed 4, %d requests; d 3-4, level 6-9, degree 1-3, cubic or Schnakenberg, "
                         "10-100 IIF2 steps) with the interpolation form of F; no finest-grid cap: %d of %d draws "
                         "rejected" % (len(reqs), rejected, len(reqs) + rejected),
             "largest_dof": max(sgkiif.dof_of(r["d"], r["n"], r["k"]) for r in reqs),
             "dof_steps_total": int(sum(work)), "precision": "mixed", "saturation": sat, "one_at_a_time": one,
-            "saturation_vs_one_at_a_time": sat["dof_steps_per_s"] / one["dof_steps_per_s"],
+            "saturation_vs_one_at_a_time": sat["dof_steps_per_s"] / one["dof_steps_per_s"] if one else None,
             "failed_requests": len(fails), "first_failure": fails[0] if fails else None}
 
 
@@ -935,6 +944,8 @@ def batched_leg(args, dist=None, rank=0, world=1):
     # in its own whole-step graph on the same 8 streams
     runs = ((8, sgkiif.SGK_MIXED, "mixed"), (8, sgkiif.SGK_MIXED, "mixed_per_instance_graphs"),
             (8, sgkiif.SGK_FP64, "fp64"))
+    if not args.full_comparisons:
+        runs = (runs[0], runs[2])
     if world > 1:
         runs = runs[:1]
     # every run takes 1 + steps steps from the initial states: one untimed
@@ -982,11 +993,13 @@ def batched_leg(args, dist=None, rank=0, world=1):
                 precision="mixed", dof_total=work_per_step, steps=steps, untimed_first_steps=1, streams=8,
                 dof_steps_per_s=res["mixed"]["dof_steps_per_s"], wall_s=res["mixed"]["wall_s"],
                 batched_arnoldi_launches=res["mixed"]["batched_arnoldi_launches"],
-                per_instance_graphs_dof_steps_per_s=res["mixed_per_instance_graphs"]["dof_steps_per_s"],
+                per_instance_graphs_dof_steps_per_s=res["mixed_per_instance_graphs"]["dof_steps_per_s"]
+                if "mixed_per_instance_graphs" in res else None,
                 speedup_vs_per_instance_graphs=res["mixed"]["dof_steps_per_s"] /
-                res["mixed_per_instance_graphs"]["dof_steps_per_s"],
+                res["mixed_per_instance_graphs"]["dof_steps_per_s"] if "mixed_per_instance_graphs" in res else None,
                 batched_equals_per_instance_bitwise=all(
-                    np.array_equal(x, y) for x, y in zip(states["mixed"], states["mixed_per_instance_graphs"])),
+                    np.array_equal(x, y) for x, y in zip(states["mixed"], states["mixed_per_instance_graphs"]))
+                if "mixed_per_instance_graphs" in res else None,
                 failed_instances=res["mixed"]["failed"], fp64_dof_steps_per_s=res["fp64"]["dof_steps_per_s"],
                 rel_l2_vs_fp64={"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
                                 "max": float(errs.max()), "above_1e-6": int((errs > 1e-6).sum()),
@@ -1097,7 +1110,7 @@ def served_leg(args):
         if outs_served is None:
             outs_served = outs
     sat, outs_sat, st_sat = serve(None, keep_est=True)
-    sat_workers, _, _ = serve(None, engine=False)
+    sat_workers = serve(None, engine=False)[0] if args.full_comparisons else None
     outs64 = []
     lat64, wall64 = one_at_a_time(sgkiif.SGK_FP64, outs64) if not args.served_no_fp64 else ([0.0], 0.0)
 
@@ -1106,11 +1119,13 @@ def served_leg(args):
 
     errs = [rel(m, f) for m, f in zip(outs_sat, outs64) if m.size and f.size]
     over = [i for i, e in enumerate(errs) if e > 1e-6]
+    # the conditioning of the requests above 1e-6 (FP64 re-solves from a
+    # perturbed input and with sub-projections) runs with --full-comparisons
     ill = [{"request": i, "rel_l2_mixed_vs_fp64": errs[i],
             "fp64_change_under_1e-14_input_perturbation": fp64_sensitivity(reqs[i], reqs[i]["steps"]),
             "krylov_err_est": kest.get(i),
             "with_substeps": [with_substeps(reqs[i], reqs[i]["steps"], sub) for sub in (8, 64)]}
-           for i in over]
+           for i in over] if args.full_comparisons else None
     first = by_rate["%gx" % rates[0]] if rates else sat
     base64 = summary(lat64, wall64) if not args.served_no_fp64 else None
     mixed1 = summary(lat_m, wall_m)
@@ -1123,7 +1138,8 @@ def served_leg(args):
                 by_rate=by_rate,
                 saturation=dict(sat, note="every request submitted at t = 0: the server's capacity",
                                 max_concurrent=st_sat["max_concurrent"]),
-                saturation_workers_only=dict(sat_workers, note="the same with the engine off: every request "
+                saturation_workers_only=None if sat_workers is None else dict(
+                    sat_workers, note="the same with the engine off: every request "
                                                                "on a worker thread"),
                 one_at_a_time_mixed=mixed1,
                 one_at_a_time_fp64=base64,
@@ -1135,8 +1151,12 @@ def served_leg(args):
                 max_rel_l2_vs_fp64_well_conditioned=max([e for i, e in enumerate(errs)
                                                         if not any(x["request"] == i and
                                                                    x["fp64_change_under_1e-14_input_perturbation"]
-                                                                   > 1e-8 for x in ill)], default=None),
-                conditioning_of_requests_above_1e_6=ill,
+                                                                   > 1e-8 for x in ill)], default=None)
+                if ill is not None else None,
+                conditioning_of_requests_above_1e_6=ill if ill is not None else
+                "not run (--full-comparisons): each request above 1e-6 re-solved in FP64 from a 1e-14-perturbed "
+                "input and with 8 and 64 sub-projections",
+                krylov_err_est_of_requests_above_1e_6={i: kest.get(i) for i in over},
                 krylov_err_est={"median": float(np.median(list(kest.values()))) if kest else None,
                                 "max": max(kest.values()) if kest else None,
                                 "above_1e_6": sum(1 for v in kest.values() if v > 1e-6),
