@@ -18,7 +18,10 @@ def instance_cost(cfg, steps=None):
     """Estimated work of a workload dict (as workloads.batch_instances /
     served_requests): per-step estimate times its steps."""
     sgkiif.load()
+    # 0: no reaction, 1: the paper's finest-grid form, 2: the interpolation form
     has_rx = int(any(len(t) for t in cfg["reaction"]))
+    if has_rx and cfg.get("reaction_form", "quadrature") == "interp":
+        has_rx = 2
     w = sgkiif.sgk_estimate_work(cfg["d"], cfg["n"], cfg["k"], len(cfg["kappas"]), cfg["M"], has_rx)
     if w < 0:
         raise sgkiif.SgkError(sgkiif.SGK_EINVAL, "sgk_estimate_work: invalid shape")

@@ -128,3 +128,14 @@ def test_work_estimate_orders_shapes(lib):
     assert est(3, 6, 2, 1, 30, 1) > est(3, 5, 2, 1, 30, 1) > est(2, 5, 2, 1, 30, 1)
     assert est(3, 6, 2, 1, 30, 1) > est(3, 6, 2, 1, 30, 0) > est(3, 6, 2, 1, 20, 0)
     assert est(2, 8, 2, 2, 40, 1) == pytest.approx(2 * est(2, 8, 2, 1, 40, 1))
+
+
+def test_interpolation_form_costs_less_to_shard():
+    # the partitioner's cost of an instance follows its reaction form: the
+    # interpolation form has no finest-grid passes
+    from paper_1810_11111_gb300 import sharding, workloads
+    cfg = workloads.cubic3d()
+    quad = sharding.instance_cost(cfg)
+    interp = sharding.instance_cost(dict(cfg, reaction_form="interp"))
+    none = sharding.instance_cost(dict(cfg, reaction=[[]]))
+    assert none < interp < quad
