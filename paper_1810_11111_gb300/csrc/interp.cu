@@ -430,8 +430,6 @@ void interp_build(sgk_solver* s) {
     build_interp_factors(N, idx->k, F);
     const Csr* mats[4] = {&F.A, &F.B, &F.Binv, &F.Ainv};
     cudaStream_t st = s->ctx->stream;
-    const int d = idx->d;
-    s->IP.madds_to = s->IP.madds_from = 0;
     for (int w = 0; w < 4; ++w) {
         const Csr& M = *mats[w];
         SGK_REQUIRE(M.rows == H && (int)M.ptr.size() == H + 1, SGK_EINVAL, "interp: factor size mismatch");
@@ -447,30 +445,11 @@ void interp_build(sgk_solver* s) {
                 ce[q] = (lb << 16) | (b - level_offset(lb, kp1));
                 for (int L = lb; L < nl; ++L) rl[(size_t)a * nl + L] += 1;
             }
-        // multiply-adds of the d passes of this factor: per (tuple, direction)
-        // the truncated rows of its positions times the other directions' extent
-        int64_t madds = 0;
-        for (int64_t t = 0; t < idx->ntuples; ++t) {
-            const int32_t* l = &idx->levels[t * d];
-            int sum = 0;
-            for (int m = 0; m < d; ++m) sum += l[m];
-            for (int i = 0; i < d; ++i) {
-                int64_t blk = 1;
-                for (int m = 0; m < d; ++m)
-                    if (m != i) blk *= level_count(l[m], kp1);
-                const int np = N - (sum - l[i]);
-                int64_t rows = 0;
-                for (int c = 0; c < level_count(l[i], kp1); ++c) rows += rl[(size_t)(level_offset(l[i], kp1) + c) * nl + np];
-                madds += rows * blk;
-            }
-        }
-        (w < 2 ? s->IP.madds_to : s->IP.madds_from) += madds;
         InterpFactorDev& D = s->IP.f[w];
         D.rp.upload(M.ptr, st);
         D.rlen.upload(rl, st);
         D.ce.upload(ce, st);
         D.val.upload(M.val, st);
-        D.nnz = (int64_t)M.col.size();
         SGK_CUDA_CHECK(cudaStreamSynchronize(st));  // the host vectors go out of scope
     }
     const size_t NS = (size_t)s->nspecies * idx->dof;

@@ -20,20 +20,17 @@ struct GraphCache {
 struct InterpFactorDev {
     DevBuf<int32_t> rp, rlen, ce;
     DevBuf<double> val;
-    int64_t nnz = 0;
 };
 
 // The sparse-grid interpolation form of F (SGK_REACTION_INTERP): the factors
 // A, B, B^{-1}, A^{-1}; two scratch buffers of the direction passes and two
 // of point values (2 S n each); the pointwise Newton outcome (status, most
-// corrections); multiply-adds of one application of C (or C^{-1}) to one
-// vector.
+// corrections).
 struct InterpPlan {
     bool on = false;
     InterpFactorDev f[4];
     DevBuf<double> t0, t1, p0, p1;
     DevBuf<int> outcome;
-    int64_t madds_to = 0, madds_from = 0;
 };
 
 struct sgk_solver {
