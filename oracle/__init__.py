@@ -26,6 +26,10 @@ krylov     Arnoldi with re-orthogonalised Gram-Schmidt, Pade(13) expm with
            not have: Saad's (1992) a-posteriori error estimate and the
            exponential as a product of sub-projections
 iif        Newton solve and the IIF2 time step (eq. krylov5, Example 3)
+interp     the sparse-grid interpolation form of the reaction term (a
+           deviation from the paper for its first stated future direction)
+combination the combination-technique form of the reaction term (a second
+           such deviation; no GPU counterpart yet)
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, library routines, invariants or printed paper values;

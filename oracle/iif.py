@@ -46,6 +46,7 @@ the paper is silent:
 """
 import numpy as np
 
+from .combination import CombinationReaction
 from .interp import InterpReaction
 from .krylov import BREAKDOWN_TOL, krylov_expv_substeps
 from .operator import sparse_matvec
@@ -147,16 +148,16 @@ class IIF2Solver:
         state passed to run(); substeps: every exponential as that many
         successive projections (an extension; 1 is the paper's method);
         reaction_form: "quadrature" (the paper's finest-grid F, module
-        reaction) or "interp" (the sparse-grid interpolation form of module
-        interp, a deviation from the paper)."""
+        reaction), "interp" (the sparse-grid interpolation form of module
+        interp) or "combination" (the combination-technique form of module
+        combination); the last two are deviations from the paper."""
         self.idx, self.S, self.dt, self.M = idx, S, dt, M
         self.substeps = int(substeps)
         self.kappas = [np.asarray(k, dtype=np.float64) for k in kappas]
         self.nspecies = len(self.kappas)
         self.reaction = reaction
         self.has_reaction = any(len(t) for t in reaction)
-        assert reaction_form in ("quadrature", "interp")
-        rx_cls = InterpReaction if reaction_form == "interp" else Reaction
+        rx_cls = {"quadrature": Reaction, "interp": InterpReaction, "combination": CombinationReaction}[reaction_form]
         self.rx = rx_cls(idx, reaction) if self.has_reaction else None
         self.sources = sources if sources is not None else [[] for _ in range(self.nspecies)]
         self.has_source = any(len(t) for t in self.sources)
