@@ -9,6 +9,8 @@ direction, not built on the GPU).
 * J_C against central differences of F_C.
 * On the cubic workload's data F_C is far closer to the quadrature F than
   the interpolation form (module interp) at the same level.
+* For smooth data F_C approaches the quadrature F at order k + 1; an IIF2
+  step with it (GMRES Newton) converges.
 """
 import numpy as np
 import pytest
@@ -83,3 +85,16 @@ def test_iif2_step_with_the_combination_form_runs_newton_to_tolerance():
     U1 = sol.run([U0], 2)[0]
     assert np.all(np.isfinite(U1)) and np.linalg.norm(U1) < np.linalg.norm(U0)
     assert all(n >= 1 for n in sol.stats["newton"])
+
+
+@pytest.mark.parametrize("k,Ns", [(1, (5, 6, 7)), (2, (5, 6, 7)), (3, (4, 5, 6))])
+def test_converges_to_the_quadrature_form_at_order(k, Ns):
+    rx = [[(-1.0, (3,))]]
+    errs = []
+    for N in Ns:
+        idx = IndexSet(2, N, k)
+        U = project_separable(idx, [1.0], [[1, 1]], [[0, 1]], 0.3)
+        Fq = Reaction(idx, rx).F([U])[0]
+        errs.append(np.linalg.norm(CombinationReaction(idx, rx).F([U])[0] - Fq) / np.linalg.norm(Fq))
+    assert errs[-1] < errs[-2] < errs[-3]
+    assert errs[-2] / errs[-1] > 0.6 * 2 ** (k + 1), errs

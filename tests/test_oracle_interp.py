@@ -19,6 +19,8 @@ for the first future direction of Section 5).
   P1 errors within a factor 2 of the printed ones at order > 1.8 (as the
   paper's F); P2 errors within a factor 5 at order > 1.5 (the interpolation
   error of u^2 is larger than the projection's at these levels).
+* For smooth data F_I approaches the paper's F at order k + 1 (d = 2,
+  degrees 1-3, a cubic f).
 """
 import os
 import sys
@@ -147,3 +149,19 @@ def test_example3_with_interpolated_reaction(k, Ns, factor, min_order):
         errs.append(e)
     for e0, e1 in zip(errs, errs[1:]):
         assert np.log2(e0 / e1) > min_order, (k, errs)
+
+
+@pytest.mark.parametrize("k,Ns", [(1, (5, 6, 7)), (2, (5, 6, 7)), (3, (4, 5, 6))])
+def test_converges_to_the_quadrature_form_at_order(k, Ns):
+    # for smooth data F_I approaches the paper's L2-projected F at the
+    # interpolation order k + 1 (the last refinement divides the difference
+    # by more than 0.6 * 2^(k+1)); a wrong point set or factor breaks this
+    rx = [[(-1.0, (3,))]]
+    errs = []
+    for N in Ns:
+        idx = IndexSet(2, N, k)
+        U = project_separable(idx, [1.0], [[1, 1]], [[0, 1]], 0.3)
+        Fq = Reaction(idx, rx).F([U])[0]
+        errs.append(np.linalg.norm(InterpReaction(idx, rx).F([U])[0] - Fq) / np.linalg.norm(Fq))
+    assert errs[-1] < errs[-2] < errs[-3]
+    assert errs[-2] / errs[-1] > 0.6 * 2 ** (k + 1), errs
